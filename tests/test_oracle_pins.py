@@ -1,0 +1,247 @@
+"""Pins for the CPU oracle: each test checks it against something other than
+itself -- a hand-worked example, exhaustive enumeration with Python's own
+sort and os.path.commonprefix, the literal pointer trie of Algorithms 1-4,
+the ultrametric property (Theorem 1) and the descent lemma (App. A).
+
+A plausible mistake in the oracle (a dropped tie-break, a reversed order, an
+off-by-one LCP, a wrong pad, an unstable sort) fails at least one of these.
+"""
+import itertools
+import os
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+import trie_checker as T
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_example.txt")
+
+
+def _parse_golden():
+    S, cases, sorted_case = [], [], None
+    with open(GOLDEN) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            tag, rest = line.split(" ", 1)
+            if tag == "S":
+                S.append([int(x) for x in rest.split()])
+            elif tag == "Q":
+                q, k, ids, lcps = [p.strip() for p in rest.split("|")]
+                cases.append(([int(x) for x in q.split()], int(k),
+                              [int(x) for x in ids.split()], [int(x) for x in lcps.split()]))
+            elif tag == "SORTED":
+                ids, H = [p.strip() for p in rest.split("|")]
+                sorted_case = ([int(x) for x in ids.split()], [int(x) for x in H.split()])
+    return np.array(S, np.uint8), cases, sorted_case
+
+
+def _brute(S, q, k):
+    """Independent route: os.path.commonprefix + Python's sorted()."""
+    lc = [len(os.path.commonprefix([tuple(int(x) for x in s), tuple(int(x) for x in q)]))
+          for s in S]
+    order = sorted(range(len(S)), key=lambda i: (-lc[i], i))[:k]
+    ids = order + [-1] * (k - len(order))
+    lcs = [lc[i] for i in order] + [0] * (k - len(order))
+    return ids, lcs
+
+
+def test_hand_example_topk():
+    S, cases, _ = _parse_golden()
+    for q, k, ids, lcps in cases:
+        got_ids, got_lcp = oracle.topk(S, np.array(q, np.uint8), k)
+        assert got_ids.tolist() == ids, (q, k)
+        assert got_lcp.tolist() == lcps, (q, k)
+
+
+def test_hand_example_sorted_index():
+    S, _, (ids, H) = _parse_golden()
+    got_ids, got_H = oracle.sorted_index(S)
+    assert got_ids.tolist() == ids
+    assert got_H.tolist() == H
+
+
+def test_hand_example_batch_matches_single():
+    S, cases, _ = _parse_golden()
+    Qs = np.array([c[0] for c in cases], np.uint8)
+    ids, lc = oracle.topk_batch(S, Qs, 9, threads=3)
+    for r, (q, _, _, _) in enumerate(cases):
+        i1, l1 = oracle.topk(S, np.array(q, np.uint8), 9)
+        assert ids[r].tolist() == i1.tolist() and lc[r].tolist() == l1.tolist()
+
+
+@pytest.mark.parametrize("sigma,L", [(2, 1), (2, 2), (2, 3), (2, 4), (3, 1), (3, 2), (3, 3)])
+def test_exhaustive_small_alphabets(sigma, L):
+    """Every query in Sigma^L, random multisets N <= 12, every k in 1..N+2."""
+    rng = random.Random(sigma * 100 + L)
+    all_q = list(itertools.product(range(sigma), repeat=L))
+    for trial in range(6):
+        N = rng.randint(0, 12)
+        S = np.array([[rng.randrange(sigma) for _ in range(L)] for _ in range(N)],
+                     np.uint8).reshape(N, L)
+        root = T.build(S)
+        for q in all_q:
+            qa = np.array(q, np.uint8)
+            for k in range(1, N + 3):
+                got_ids, got_lcp = oracle.topk(S, qa, k)
+                b_ids, b_lcp = _brute(S, q, k)
+                t_ids, t_lcp = T.topk_by_trie(root, q, k, N)
+                assert got_ids.tolist() == b_ids == t_ids, (S.tolist(), q, k)
+                assert got_lcp.tolist() == b_lcp == t_lcp, (S.tolist(), q, k)
+
+
+def test_uint16_tokens_high_values():
+    """Unsigned order and LCP with tokens near 0xFFFF (uint16)."""
+    S = np.array([[0xFFFF, 1, 2], [0xFFFF, 1, 3], [0x7FFF, 1, 2], [0, 0, 0], [0xFFFF, 1, 2]],
+                 np.uint16)
+    q = np.array([0xFFFF, 1, 2], np.uint16)
+    ids, lc = oracle.topk(S, q, 5)
+    assert ids.tolist() == [0, 4, 1, 2, 3]
+    assert lc.tolist() == [3, 3, 2, 0, 0]
+    sid, H = oracle.sorted_index(S)
+    assert sid.tolist() == [3, 2, 0, 4, 1]
+    assert H.tolist() == [0, 0, 0, 3, 2]
+
+
+def test_lcp_invariants_and_ultrametric():
+    """LCP(q,q)=L, symmetry, and Theorem 1: LCP(s,u) >= min(LCP(s,t), LCP(t,u))."""
+    rng = np.random.default_rng(7)
+    for L, tb in ((1, 1), (5, 1), (9, 2), (33, 2)):
+        dt = np.uint8 if tb == 1 else np.uint16
+        X = rng.integers(0, 3, size=(60, L)).astype(dt)
+        for _ in range(300):
+            a, b, c = X[rng.integers(0, 60, 3)]
+            assert oracle.lcp(a, a) == L
+            assert oracle.lcp(a, b) == oracle.lcp(b, a)
+            assert oracle.lcp(a, c) >= min(oracle.lcp(a, b), oracle.lcp(b, c))
+
+
+def _random_prefixy(rng, N, L, sigma, dt):
+    """Rows sharing prefixes: random walks down a small random tree."""
+    base = rng.integers(0, sigma, size=(max(N // 4, 1), L))
+    rows = base[rng.integers(0, base.shape[0], N)].copy()
+    cut = rng.integers(0, L + 1, N)
+    for i in range(N):
+        rows[i, cut[i]:] = rng.integers(0, sigma, L - cut[i])
+    return rows.astype(dt)
+
+
+@pytest.mark.parametrize("L,tb,sigma", [(4, 1, 3), (7, 1, 4), (12, 2, 5), (3, 2, 70000 // 2)])
+def test_sorted_index_against_python_sort(L, tb, sigma):
+    rng = np.random.default_rng(L * 13 + tb)
+    dt = np.uint8 if tb == 1 else np.uint16
+    sigma = min(sigma, 256 if tb == 1 else 65536)
+    S = _random_prefixy(rng, 500, L, sigma, dt)
+    ids, H = oracle.sorted_index(S)
+    expect = sorted(range(len(S)), key=lambda i: (tuple(int(x) for x in S[i]), i))
+    assert ids.tolist() == expect
+    for p in range(len(S)):
+        if p == 0:
+            assert H[p] == 0
+        else:
+            cp = os.path.commonprefix([tuple(S[ids[p - 1]].tolist()), tuple(S[ids[p]].tolist())])
+            assert H[p] == len(cp)
+
+
+def test_sorted_order_invariants():
+    """Contiguity of {p : LCP(q, row p) >= d}; range-min of H equals range LCP;
+    and the count with LCP >= d equals the trie subtree size on q's path
+    (Algorithm 2)."""
+    rng = np.random.default_rng(3)
+    L = 6
+    S = _random_prefixy(rng, 300, L, 3, np.uint8)
+    ids, H = oracle.sorted_index(S)
+    rows = S[ids]
+    root = T.build(S)
+    # range minimum of H over (i, j] equals LCP(row i, row j)
+    for _ in range(400):
+        i, j = sorted(rng.integers(0, len(S), 2))
+        if i == j:
+            continue
+        assert H[i + 1:j + 1].min() == oracle.lcp(rows[i], rows[j])
+    for _ in range(100):
+        q = rng.integers(0, 3, L).astype(np.uint8)
+        lam = np.array([oracle.lcp(q, r) for r in rows])
+        path = T.descend(root, q)
+        for d in range(L + 1):
+            where = np.nonzero(lam >= d)[0]
+            if len(where):
+                assert where[-1] - where[0] + 1 == len(where)  # contiguous
+            if d < len(path):
+                assert len(where) == path[d].size  # Algorithm 2 subtree size
+            else:
+                assert len(where) == 0
+
+
+def test_descent_lemma_and_bfs_lcp_column():
+    """App. A: after descending to depth d, items outside T_v have LCP < d
+    (strict).  When |T_v| >= k, the LCP column of literal Algorithm 4 (BFS
+    order) equals the oracle's LCP column."""
+    rng = np.random.default_rng(11)
+    L = 5
+    S = _random_prefixy(rng, 200, L, 3, np.uint8)
+    root = T.build(S)
+    checked = 0
+    for _ in range(300):
+        q = rng.integers(0, 3, L).astype(np.uint8)
+        path = T.descend(root, q)
+        v, d = path[-1], len(path) - 1
+        inside = set(T.items_in(v))
+        for i in range(len(S)):
+            if i not in inside:
+                assert oracle.lcp(q, S[i]) < d
+        k = int(rng.integers(1, 12))
+        if v.size >= k:
+            bfs = T.collect_bfs(v, k)
+            _, o_lcp = oracle.topk(S, q, k)
+            assert [oracle.lcp(q, S[i]) for i in bfs] == o_lcp.tolist()
+            checked += 1
+    assert checked > 20
+
+
+def test_k1_member_query():
+    """k=1 with q in S returns (smallest id holding q, L) -- the distinguishing
+    query of the space lower bound's argument (Sec. 4.1)."""
+    rng = np.random.default_rng(5)
+    S = rng.integers(0, 2, size=(64, 6)).astype(np.uint8)
+    for i in range(64):
+        ids, lc = oracle.topk(S, S[i], 1)
+        first = min(j for j in range(64) if (S[j] == S[i]).all())
+        assert ids[0] == first and lc[0] == 6
+
+
+def test_empty_and_degenerate():
+    S = np.zeros((0, 3), np.uint8)
+    ids, lc = oracle.topk(S, np.array([1, 2, 3], np.uint8), 4)
+    assert ids.tolist() == [-1] * 4 and lc.tolist() == [0] * 4
+    S = np.ones((5, 3), np.uint8)  # all identical
+    ids, lc = oracle.topk(S, np.array([1, 1, 1], np.uint8), 3)
+    assert ids.tolist() == [0, 1, 2] and lc.tolist() == [3, 3, 3]
+    ids, lc = oracle.topk(S, np.array([1, 1, 2], np.uint8), 7)
+    assert ids.tolist() == [0, 1, 2, 3, 4, -1, -1] and lc.tolist() == [2] * 5 + [0, 0]
+    with pytest.raises(ValueError):
+        oracle.topk(S, np.array([1, 1, 1], np.uint8), 0)
+
+
+def test_workload_generators_are_deterministic_and_shaped():
+    """Inputs are seeded: regenerating gives identical bytes; shapes match."""
+    import workloads as W
+    a = W.make_dataset("tree16_u8", N=500, Q=50)
+    b = W.make_dataset("tree16_u8", N=500, Q=50)
+    assert (a[0] == b[0]).all() and (a[1] == b[1]).all() and a[2] == 10
+    assert a[0].dtype == np.uint8 and a[0].max() < 16
+    # 4-ary tree over the first 8 positions: at most 4 children per prefix
+    S = a[0]
+    for d in range(8):
+        kids = {}
+        for r in S:
+            kids.setdefault(tuple(r[:d]), set()).add(int(r[d]))
+        assert max(len(v) for v in kids.values()) <= 4
+    z = W.make_dataset("zipf500k_L32", N=2000, Q=100)
+    assert z[0].dtype == np.uint16 and z[0].shape == (2000, 32) and z[0].max() < 1024
+    g = W.GncStream(sensors=10, seed=5)
+    r0 = g.step()
+    assert r0.shape == (10, 8) and r0[:, 2:].max() <= 9
