@@ -1,0 +1,194 @@
+/*
+ * lcp.h -- C ABI of the B300 library for deterministic top-k retrieval under
+ * Longest-Common-Prefix similarity.
+ *
+ * Problem (paper Sec. 2.1, Definitions "LCP Similarity" and "Top-k LCP
+ * Retrieval"): a set S = {s_1..s_N} of sequences of L tokens, a query q and
+ * k >= 1 (Algorithm 3 requires an integer k >= 1).  LCP(s, t) is the length
+ * of the longest common prefix.  The answer is the k items with the highest
+ * LCP(q, s_i), ties broken by original index, so that a fixed (S, q, k)
+ * always yields bit-identical output (Theorem 7, "Determinism").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Ids are 0-based original indices: item s_{i+1} of the paper has id i.
+ *    Ties are broken by ascending id.  Rows appended by lcp_index_insert take
+ *    ids N, N+1, ... in batch row order.
+ *  - Tokens are unsigned integers of `token_bytes` (1 = uint8, 2 = uint16)
+ *    stored row-major, contiguous, [n, L].  Order is unsigned lexicographic.
+ *    1 <= L <= 255 so that an LCP fits in one byte.
+ *  - Results are [Q, k] row-major: out_ids (int32) and out_lcp (uint8).  Row r
+ *    lists query r's answer in order (LCP descending, id ascending).  When
+ *    k > N the slots from N on hold id -1 and lcp 0.
+ *  - Pointers named d_* are device pointers (cudaMalloc / torch CUDA memory)
+ *    on the current device; h_* are host pointers (pinned memory gives the
+ *    fastest copies, pageable memory works).  The caller owns every token,
+ *    query and output buffer and must keep it valid until the work enqueued on
+ *    `stream` has completed.  The library owns index memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are stream-ordered and asynchronous unless stated.
+ *  - Argument errors are returned synchronously and nothing is enqueued.
+ *    Errors that arise on the device (a bounded wait that ran out) are
+ *    recorded in a device status word and reported by lcp_index_sync /
+ *    lcp_device_status; no kernel of this library traps or spins forever.
+ *  - Every entry point returns LCP_OK (0) or a negative LCP_ERR_* code;
+ *    lcp_status_string gives its text.
+ *  - Limits: N <= 2^30 - 1 items per index, k <= LCP_SCAN_MAX_K for the full
+ *    scan and k <= the index's max_k (<= LCP_INDEX_MAX_K) for indexed search.
+ */
+#ifndef LCP_H_
+#define LCP_H_
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LCP_API __attribute__((visibility("default")))
+#else
+#define LCP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LCP_OK 0
+#define LCP_PENDING 1           /* session ticket not finished yet */
+#define LCP_ERR_INVALID (-1)    /* bad argument: null pointer, k < 1, L out of range ... */
+#define LCP_ERR_OOM (-2)        /* device allocation failed */
+#define LCP_ERR_CAPACITY (-3)   /* insert would exceed the index capacity */
+#define LCP_ERR_BUDGET (-4)     /* request can never fit the session memory budget */
+#define LCP_ERR_TIMEOUT (-5)    /* a bounded device or host wait ran out */
+#define LCP_ERR_CUDA (-6)       /* a CUDA runtime call failed */
+#define LCP_ERR_STATE (-7)      /* object in the wrong state (destroyed, shut down) */
+
+#define LCP_INDEX_MAX_K 128     /* largest max_k an index can be built for */
+#define LCP_SCAN_MAX_K 1024     /* largest k for lcp_scan_topk */
+#define LCP_MAX_L 255
+
+typedef void* lcp_stream_t; /* a cudaStream_t */
+typedef struct lcp_index_s* lcp_index_t;
+
+/* Token format of a dataset: 1 or 2 bytes per token, L tokens per row.
+ * vocab is informational (0 = unknown); tokens are not range-checked. */
+typedef struct {
+    int32_t token_bytes;
+    int32_t L;
+    int32_t vocab;
+} lcp_format_t;
+
+LCP_API const char* lcp_status_string(int status);
+
+/* ------------------------------------------------------------------------
+ * Index build -- Algorithm 1 (BuildLCPIndex, Sec. 5.2) and Algorithm 2
+ * (subtree sizes) in array form.
+ *
+ * Builds the prefix index of the N rows at d_tokens ([N, L], device memory):
+ * the rows packed into 64-bit words and sorted lexicographically (equal rows
+ * by id), their ids in that order, the adjacent-LCP array H (H[p] =
+ * LCP(row p-1, row p)), and the auxiliary tables the search uses to break
+ * ties by index.  The trie's nodes are the LCP intervals of H; a node's
+ * subtree size |T_v| is its interval length.
+ *   capacity: rows the index can hold without reallocating (>= N; 0 = N).
+ *             lcp_index_insert fails with LCP_ERR_CAPACITY beyond it.
+ *   max_k:    largest k lcp_topk_batch will accept (1..LCP_INDEX_MAX_K).
+ * On success *out owns the device memory; release it with lcp_index_destroy.
+ * Blocks the host only while the radix sort decides how many refinement
+ * rounds tied prefixes need (a few small device-to-host reads); all work is
+ * on `stream`.  d_tokens may be reused once the stream has passed the build.
+ * Errors: LCP_ERR_INVALID, LCP_ERR_OOM, LCP_ERR_CUDA.
+ * ---------------------------------------------------------------------- */
+LCP_API int lcp_index_build(const void* d_tokens, int64_t N, lcp_format_t fmt, int64_t capacity,
+                    int32_t max_k, lcp_stream_t stream, lcp_index_t* out);
+
+/* Same, with the tokens in host memory; the host-to-device copy is part of
+ * the call.  Returns after the build has been enqueued and the tokens copied. */
+LCP_API int lcp_index_build_host(const void* h_tokens, int64_t N, lcp_format_t fmt, int64_t capacity,
+                         int32_t max_k, lcp_stream_t stream, lcp_index_t* out);
+
+/* ------------------------------------------------------------------------
+ * Insert -- dynamic updates (the paper's static analysis leaves them to
+ * future work, Sec. 10.1 / App. G).  Appends n rows ([n, L], device memory,
+ * same format) with ids N..N+n-1: the batch is sorted, merged into the sorted
+ * rows by merge path (on equal rows the older, smaller id first), and H and
+ * the tie tables are refreshed.  The result is byte-identical to building the
+ * concatenated dataset from scratch.  Never reallocates; fails with
+ * LCP_ERR_CAPACITY if N + n > capacity.  Batches of up to
+ * LCP_INSERT_SMALL_BATCH rows never block the host; larger batches may
+ * (like lcp_index_build).
+ * ---------------------------------------------------------------------- */
+#define LCP_INSERT_SMALL_BATCH 2048
+LCP_API int lcp_index_insert(lcp_index_t index, const void* d_tokens, int64_t n, lcp_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Indexed batched top-k -- Algorithm 3 (descent) with the collection of
+ * Algorithm 4 / CollectTopKOptimized (App. D), in the order of the
+ * Definition "Top-k LCP Retrieval":
+ *   1. binary search for q's insertion point p in the sorted rows and the
+ *      LCPs with both neighbours (the descent depth is their maximum);
+ *   2. expansion outward from p through H, level by level, until the level
+ *      d* at which at least k items have LCP >= d* (all items with LCP > d*
+ *      are taken: fewer than k);
+ *   3. the remaining slots are filled from the LCP-interval of level d*
+ *      (prefix bucket B_{q[1..d*]}, Sec. 6.2) with its smallest ids.
+ * d_queries: [Q, L] device memory in the index's format.  1 <= k <= max_k.
+ * Output [Q, k] as described above.  Q = 0 is a no-op.
+ * ---------------------------------------------------------------------- */
+LCP_API int lcp_topk_batch(lcp_index_t index, const void* d_queries, int64_t Q, int32_t k,
+                   int32_t* d_out_ids, uint8_t* d_out_lcp, lcp_stream_t stream);
+
+/* Same, with host queries and host outputs; the copies in both directions
+ * are part of the call, which returns when the results are in host memory. */
+LCP_API int lcp_topk_batch_host(lcp_index_t index, const void* h_queries, int64_t Q, int32_t k,
+                        int32_t* h_out_ids, uint8_t* h_out_lcp, lcp_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Full scan top-k -- the index-free baseline ("full scan" of Sec. 7, Table 6):
+ * LCP of every query against all N rows, keeping per query the k best under
+ * (LCP descending, id ascending).  Needs no index.
+ * d_tokens [N, L], d_queries [Q, L] device memory in format fmt.
+ * 1 <= k <= LCP_SCAN_MAX_K.  Uses temporary device memory from the
+ * stream-ordered allocator (about Q * k * 8 bytes per N-slice).
+ * ---------------------------------------------------------------------- */
+LCP_API int lcp_scan_topk(const void* d_tokens, int64_t N, lcp_format_t fmt, const void* d_queries,
+                  int64_t Q, int32_t k, int32_t* d_out_ids, uint8_t* d_out_lcp,
+                  lcp_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Index inspection and lifetime.
+ * ---------------------------------------------------------------------- */
+/* Current item count and device bytes held (both may be NULL). Synchronous,
+ * host-side only. */
+LCP_API int lcp_index_size(lcp_index_t index, int64_t* N, int64_t* bytes);
+
+/* Copies the sorted order (ids, [N] int32) and the adjacent-LCP array (H,
+ * [N] uint8) of the index to device buffers; either may be NULL.  For tests
+ * and checkpoints. */
+LCP_API int lcp_index_export(lcp_index_t index, int32_t* d_ids, uint8_t* d_H, lcp_stream_t stream);
+
+/* Waits for the last stream the index was used on and reports any device
+ * status (LCP_ERR_TIMEOUT if a bounded device wait ran out), then clears it. */
+LCP_API int lcp_index_sync(lcp_index_t index);
+
+/* Frees the index (after synchronising its last stream). NULL is a no-op. */
+LCP_API int lcp_index_destroy(lcp_index_t index);
+
+/* ------------------------------------------------------------------------
+ * Library-wide diagnostics.
+ * ---------------------------------------------------------------------- */
+/* Synchronises the device and reports, then clears, the library's device
+ * status word (written by kernels that are not tied to an index). */
+LCP_API int lcp_device_status(void);
+
+/* Number of kernels this library has launched in this process. */
+LCP_API int64_t lcp_launch_count(void);
+
+/* Test hook for the bounded-wait machinery: launches one kernel that waits
+ * for a device flag nobody sets, with the given spin limit, and returns the
+ * status that kernel reports (LCP_ERR_TIMEOUT when the limit is reached).
+ * Never traps and never hangs. */
+LCP_API int lcp_debug_bounded_wait(int64_t spin_limit, lcp_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LCP_H_ */

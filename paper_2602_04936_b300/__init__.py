@@ -1,0 +1,298 @@
+"""Python binding of liblcp.so -- deterministic top-k LCP retrieval on B300.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of liblcp.so (C ABI declared in include/lcp.h).  PyTorch supplies
+device memory and the current CUDA stream.  There is no CPU fallback: if the
+shared library cannot be loaded, importing this package raises.
+
+Names mirror the C entry points:
+
+    idx = lcp_index_build(tokens, max_k=128, capacity=0)     # Algorithm 1
+    lcp_index_insert(idx, new_tokens)                        # ids N, N+1, ...
+    ids, lcp = lcp_topk_batch(idx, queries, k)               # Algorithms 3/4
+    ids, lcp = lcp_scan_topk(tokens, queries, k)             # full scan
+    ids, lcp = lcp_topk_batch_host(idx, host_queries, k)     # host buffers
+
+Tokens are [n, L] tensors of 1-byte (uint8) or 2-byte (uint16 / int16,
+reinterpreted as unsigned) elements.  Results are ([Q, k] int32 ids,
+[Q, k] uint8 LCPs), ordered by (LCP desc, id asc), padded with (-1, 0).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liblcp.so")
+
+LCP_OK = 0
+LCP_PENDING = 1
+LCP_ERR_INVALID = -1
+LCP_ERR_OOM = -2
+LCP_ERR_CAPACITY = -3
+LCP_ERR_BUDGET = -4
+LCP_ERR_TIMEOUT = -5
+LCP_ERR_CUDA = -6
+LCP_ERR_STATE = -7
+LCP_INDEX_MAX_K = 128
+LCP_SCAN_MAX_K = 1024
+LCP_INSERT_SMALL_BATCH = 2048
+
+# Every symbol include/lcp.h declares (checked by the CPU test suite).
+ABI_SYMBOLS = (
+    "lcp_status_string", "lcp_index_build", "lcp_index_build_host", "lcp_index_insert",
+    "lcp_topk_batch", "lcp_topk_batch_host", "lcp_scan_topk", "lcp_index_size",
+    "lcp_index_export", "lcp_index_sync", "lcp_index_destroy", "lcp_device_status",
+    "lcp_launch_count", "lcp_debug_bounded_wait",
+)
+
+
+class LcpError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (what, _lib.lcp_status_string(code).decode(), code))
+
+
+class _Format(ctypes.Structure):
+    _fields_ = [("token_bytes", ctypes.c_int32), ("L", ctypes.c_int32), ("vocab", ctypes.c_int32)]
+
+
+def _load():
+    if not os.path.exists(_SO):
+        try:
+            from . import build as _b
+            _b.build()
+        except Exception as e:  # no CPU fallback: fail loudly
+            raise ImportError("liblcp.so is missing and could not be built: %s" % e) from e
+    lib = ctypes.CDLL(_SO)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    sig = {
+        "lcp_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "lcp_index_build": ([vp, i64, _Format, i64, i32, vp, ctypes.POINTER(vp)], ctypes.c_int),
+        "lcp_index_build_host": ([vp, i64, _Format, i64, i32, vp, ctypes.POINTER(vp)], ctypes.c_int),
+        "lcp_index_insert": ([vp, vp, i64, vp], ctypes.c_int),
+        "lcp_topk_batch": ([vp, vp, i64, i32, vp, vp, vp], ctypes.c_int),
+        "lcp_topk_batch_host": ([vp, vp, i64, i32, vp, vp, vp], ctypes.c_int),
+        "lcp_scan_topk": ([vp, i64, _Format, vp, i64, i32, vp, vp, vp], ctypes.c_int),
+        "lcp_index_size": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64)], ctypes.c_int),
+        "lcp_index_export": ([vp, vp, vp, vp], ctypes.c_int),
+        "lcp_index_sync": ([vp], ctypes.c_int),
+        "lcp_index_destroy": ([vp], ctypes.c_int),
+        "lcp_device_status": ([], ctypes.c_int),
+        "lcp_launch_count": ([], i64),
+        "lcp_debug_bounded_wait": ([i64, vp], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def library_path() -> str:
+    return _SO
+
+
+def _check(rc: int, what: str):
+    if rc != LCP_OK:
+        raise LcpError(rc, what)
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _token_bytes(t: torch.Tensor) -> int:
+    es = t.element_size()
+    if es not in (1, 2) or t.is_floating_point():
+        raise TypeError("tokens must be 1- or 2-byte integers, got %s" % t.dtype)
+    return es
+
+
+def _rows(t: torch.Tensor, device: bool):
+    if t.dim() != 2:
+        raise ValueError("tokens must be [n, L]")
+    if device and not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not device and t.is_cuda:
+        raise ValueError("expected a host tensor")
+    return t.contiguous()
+
+
+def _fmt(t: torch.Tensor, vocab: int = 0) -> _Format:
+    return _Format(_token_bytes(t), t.shape[1], vocab)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() else ctypes.c_void_p(0)
+
+
+class Index:
+    """Owning handle of a device-resident prefix index."""
+
+    def __init__(self, handle: ctypes.c_void_p, L: int, token_bytes: int, max_k: int, device):
+        self._h = handle
+        self.L, self.token_bytes, self.max_k, self.device = L, token_bytes, max_k, device
+
+    @property
+    def handle(self):
+        if self._h is None or not self._h.value:
+            raise LcpError(LCP_ERR_STATE, "index")
+        return self._h
+
+    def size(self):
+        n, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.lcp_index_size(self.handle, ctypes.byref(n), ctypes.byref(b)), "lcp_index_size")
+        return n.value, b.value
+
+    @property
+    def N(self) -> int:
+        return self.size()[0]
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib.lcp_index_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lcp_status_string(code: int) -> str:
+    return _lib.lcp_status_string(code).decode()
+
+
+def lcp_index_build(tokens: torch.Tensor, max_k: int = LCP_INDEX_MAX_K, capacity: int = 0,
+                    vocab: int = 0, stream=None) -> Index:
+    tokens = _rows(tokens, device=True)
+    h = ctypes.c_void_p()
+    with torch.cuda.device(tokens.device):
+        rc = _lib.lcp_index_build(_ptr(tokens), tokens.shape[0], _fmt(tokens, vocab), capacity, max_k,
+                                  _stream(stream), ctypes.byref(h))
+    _check(rc, "lcp_index_build")
+    return Index(h, tokens.shape[1], _token_bytes(tokens), max_k, tokens.device)
+
+
+def lcp_index_build_host(tokens: torch.Tensor, max_k: int = LCP_INDEX_MAX_K, capacity: int = 0,
+                         vocab: int = 0, stream=None, device=None) -> Index:
+    tokens = _rows(tokens, device=False)
+    h = ctypes.c_void_p()
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    with torch.cuda.device(dev):
+        rc = _lib.lcp_index_build_host(_ptr(tokens), tokens.shape[0], _fmt(tokens, vocab), capacity,
+                                       max_k, _stream(stream), ctypes.byref(h))
+    _check(rc, "lcp_index_build_host")
+    return Index(h, tokens.shape[1], _token_bytes(tokens), max_k, dev)
+
+
+def lcp_index_insert(index: Index, tokens: torch.Tensor, stream=None) -> None:
+    tokens = _rows(tokens, device=True)
+    if tokens.shape[1] != index.L or _token_bytes(tokens) != index.token_bytes:
+        raise ValueError("insert batch format differs from the index")
+    with torch.cuda.device(tokens.device):
+        _check(_lib.lcp_index_insert(index.handle, _ptr(tokens), tokens.shape[0], _stream(stream)),
+               "lcp_index_insert")
+
+
+def _outputs(Q, k, device, out_ids, out_lcp, pin=False):
+    if out_ids is None:
+        out_ids = torch.empty((Q, k), dtype=torch.int32, device=device, pin_memory=pin)
+    if out_lcp is None:
+        out_lcp = torch.empty((Q, k), dtype=torch.uint8, device=device, pin_memory=pin)
+    if out_ids.dtype != torch.int32 or out_lcp.dtype != torch.uint8:
+        raise TypeError("outputs must be int32 ids and uint8 LCPs")
+    if tuple(out_ids.shape) != (Q, k) or tuple(out_lcp.shape) != (Q, k):
+        raise ValueError("outputs must be [Q, k]")
+    if not (out_ids.is_contiguous() and out_lcp.is_contiguous()):
+        raise ValueError("outputs must be contiguous")
+    return out_ids, out_lcp
+
+
+def lcp_topk_batch(index: Index, queries: torch.Tensor, k: int, out_ids=None, out_lcp=None,
+                   stream=None):
+    queries = _rows(queries, device=True)
+    if queries.shape[1] != index.L or _token_bytes(queries) != index.token_bytes:
+        raise ValueError("query format differs from the index")
+    Q = queries.shape[0]
+    out_ids, out_lcp = _outputs(Q, k, queries.device, out_ids, out_lcp)
+    with torch.cuda.device(queries.device):
+        _check(_lib.lcp_topk_batch(index.handle, _ptr(queries), Q, k, _ptr(out_ids), _ptr(out_lcp),
+                                   _stream(stream)), "lcp_topk_batch")
+    return out_ids, out_lcp
+
+
+def lcp_topk_batch_host(index: Index, queries: torch.Tensor, k: int, out_ids=None, out_lcp=None,
+                        stream=None):
+    queries = _rows(queries, device=False)
+    Q = queries.shape[0]
+    out_ids, out_lcp = _outputs(Q, k, "cpu", out_ids, out_lcp, pin=False)
+    with torch.cuda.device(index.device):
+        _check(_lib.lcp_topk_batch_host(index.handle, _ptr(queries), Q, k, _ptr(out_ids),
+                                        _ptr(out_lcp), _stream(stream)), "lcp_topk_batch_host")
+    return out_ids, out_lcp
+
+
+def lcp_scan_topk(tokens: torch.Tensor, queries: torch.Tensor, k: int, out_ids=None, out_lcp=None,
+                  stream=None, vocab: int = 0):
+    tokens = _rows(tokens, device=True)
+    queries = _rows(queries, device=True)
+    if queries.shape[1] != tokens.shape[1] or _token_bytes(queries) != _token_bytes(tokens):
+        raise ValueError("query format differs from the tokens")
+    Q = queries.shape[0]
+    out_ids, out_lcp = _outputs(Q, k, queries.device, out_ids, out_lcp)
+    with torch.cuda.device(queries.device):
+        _check(_lib.lcp_scan_topk(_ptr(tokens), tokens.shape[0], _fmt(tokens, vocab), _ptr(queries), Q,
+                                  k, _ptr(out_ids), _ptr(out_lcp), _stream(stream)), "lcp_scan_topk")
+    return out_ids, out_lcp
+
+
+def lcp_index_export(index: Index, stream=None):
+    """(ids [N] int32, H [N] uint8) of the sorted index, on the index's device."""
+    n = index.N
+    ids = torch.empty(n, dtype=torch.int32, device=index.device)
+    H = torch.empty(n, dtype=torch.uint8, device=index.device)
+    with torch.cuda.device(index.device):
+        _check(_lib.lcp_index_export(index.handle, _ptr(ids), _ptr(H), _stream(stream)),
+               "lcp_index_export")
+    return ids, H
+
+
+def lcp_index_sync(index: Index) -> int:
+    return _lib.lcp_index_sync(index.handle)
+
+
+def lcp_index_size(index: Index):
+    return index.size()
+
+
+def lcp_index_destroy(index: Index) -> None:
+    index.close()
+
+
+def lcp_device_status() -> int:
+    return _lib.lcp_device_status()
+
+
+def lcp_launch_count() -> int:
+    return int(_lib.lcp_launch_count())
+
+
+def lcp_debug_bounded_wait(spin_limit: int, stream=None) -> int:
+    return _lib.lcp_debug_bounded_wait(spin_limit, _stream(stream))
+
+
+def raw_lib():
+    """The ctypes handle of liblcp.so (for callers marshalling raw pointers)."""
+    return _lib

@@ -1,0 +1,363 @@
+// C ABI entry points (see include/lcp.h for the contract of each call).
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "index.cuh"
+
+namespace lcph {
+
+static std::atomic<int64_t> g_launches{0};
+static thread_local cudaError_t g_last_cuda = cudaSuccess;
+
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int cuda_status(cudaError_t e) {
+    g_last_cuda = e;
+    if (e == cudaErrorMemoryAllocation) return LCP_ERR_OOM;
+    return LCP_ERR_CUDA;
+}
+
+// Library-wide device status word (one per device, allocated on first use).
+static int* g_status[64] = {nullptr};
+static std::mutex g_status_mu;
+
+int* lib_status_word() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_status_mu);
+    if (!g_status[dev]) {
+        int* p = nullptr;
+        if (cudaMalloc((void**)&p, sizeof(int)) != cudaSuccess) return nullptr;
+        cudaMemset(p, 0, sizeof(int));
+        g_status[dev] = p;
+    }
+    return g_status[dev];
+}
+
+int scan_topk_device(const void* d_tokens, int64_t N, int tb, int L, const void* d_queries,
+                     int64_t Q, int k, int32_t* d_out_ids, uint8_t* d_out_lcp, cudaStream_t s);
+
+static int valid_fmt(const lcp_format_t& f) {
+    return (f.token_bytes == 1 || f.token_bytes == 2) && f.L >= 1 && f.L <= LCP_MAX_L;
+}
+
+// Index memory comes from the device's stream-ordered pool, which is told to
+// keep freed memory (release threshold = max), so destroying and rebuilding
+// indexes in a serving loop reuses memory instead of paying cudaMalloc/cudaFree.
+static void retain_pool_memory() {
+    static std::once_flag once[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::call_once(once[dev], [dev]() {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    });
+}
+
+static void free_index_memory(lcp_index_s* x, cudaStream_t s) {
+    void* ptrs[] = {x->buf[0].rows, x->buf[0].head, x->buf[0].ids, x->buf[0].H,
+                    x->buf[1].rows, x->buf[1].head, x->buf[1].ids, x->buf[1].H,
+                    x->pos, x->hmin, x->sblk, x->soff, x->st, x->status,
+                    x->ins_rows, x->ins_ids, x->ins_rank};
+    for (void* p : ptrs)
+        if (p) cudaFreeAsync(p, s);
+    x->buf[0] = lcp_buffers();
+    x->buf[1] = lcp_buffers();
+    cudaFree(x->stage_in);
+    cudaFree(x->stage_out);
+}
+
+template <typename T>
+static int dalloc(T** p, size_t count, int64_t* bytes, cudaStream_t s) {
+    size_t b = sizeof(T) * (count ? count : 1);
+    cudaError_t e = cudaMallocAsync((void**)p, b, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    *bytes += (int64_t)b;
+    return LCP_OK;
+}
+
+static int alloc_index(lcp_index_s* x, int64_t N, int64_t cap, cudaStream_t s) {
+    int64_t& by = x->bytes;
+    const int W = x->W;
+    int nsets = cap > N ? 2 : 1;
+    for (int b = 0; b < nsets; ++b) {
+        int rc;
+        if ((rc = dalloc(&x->buf[b].rows, (size_t)cap * W, &by, s))) return rc;
+        if ((rc = dalloc(&x->buf[b].head, (size_t)cap, &by, s))) return rc;
+        if ((rc = dalloc(&x->buf[b].ids, (size_t)cap, &by, s))) return rc;
+        if ((rc = dalloc(&x->buf[b].H, (size_t)cap, &by, s))) return rc;
+    }
+    int rc;
+    if ((rc = dalloc(&x->pos, (size_t)cap, &by, s))) return rc;
+    if ((rc = dalloc(&x->hmin, (size_t)(cap / 31 + 64), &by, s))) return rc;
+    x->nblk_cap = (cap + lcpk::kBlk - 1) / lcpk::kBlk;
+    if (x->nblk_cap < 1) x->nblk_cap = 1;
+    if ((rc = dalloc(&x->sblk, (size_t)x->nblk_cap * lcpk::kBlk, &by, s))) return rc;
+    if ((rc = dalloc(&x->soff, (size_t)x->nblk_cap * lcpk::kBlk, &by, s))) return rc;
+    int lev = 0;
+    while ((1ll << (lev + 1)) <= x->nblk_cap) ++lev;
+    x->st_levels_cap = lev;
+    if ((rc = dalloc(&x->st, (size_t)(lev > 0 ? lev : 1) * x->nblk_cap * x->K, &by, s))) return rc;
+    if ((rc = dalloc(&x->status, 1, &by, s))) return rc;
+    LCP_CUDA_TRY(cudaMemsetAsync(x->status, 0, sizeof(int), s));
+    if (cap > N) {
+        if ((rc = dalloc(&x->ins_rows, (size_t)2 * LCP_INSERT_SMALL_BATCH * W, &by, s))) return rc;
+        if ((rc = dalloc(&x->ins_ids, (size_t)LCP_INSERT_SMALL_BATCH, &by, s))) return rc;
+        if ((rc = dalloc(&x->ins_rank, (size_t)2 * LCP_INSERT_SMALL_BATCH, &by, s))) return rc;
+    }
+    return LCP_OK;
+}
+
+static int read_status(int* d_status, cudaStream_t s) {
+    if (!d_status) return LCP_OK;
+    int h = 0;
+    LCP_CUDA_TRY(cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LCP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) {
+        LCP_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), s));
+        LCP_CUDA_TRY(cudaStreamSynchronize(s));
+        return h == lcpk::DEV_TIMEOUT ? LCP_ERR_TIMEOUT : LCP_ERR_CUDA;
+    }
+    return LCP_OK;
+}
+
+}  // namespace lcph
+
+using namespace lcph;
+
+namespace lcpk {
+// Waits on a flag that nothing sets, at most `limit` spins, then reports.
+__global__ void k_debug_wait(const volatile int* flag, long long limit, int* status) {
+    long long spins = 0;
+    while (*flag == 0) {
+        if (++spins > limit) {
+            flag_status(status, DEV_TIMEOUT);
+            return;
+        }
+    }
+}
+}  // namespace lcpk
+
+extern "C" {
+
+const char* lcp_status_string(int s) {
+    switch (s) {
+        case LCP_OK: return "ok";
+        case LCP_PENDING: return "pending";
+        case LCP_ERR_INVALID: return "invalid argument";
+        case LCP_ERR_OOM: return "device out of memory";
+        case LCP_ERR_CAPACITY: return "index capacity exceeded";
+        case LCP_ERR_BUDGET: return "request exceeds the session memory budget";
+        case LCP_ERR_TIMEOUT: return "bounded wait timed out";
+        case LCP_ERR_CUDA: return "CUDA error";
+        case LCP_ERR_STATE: return "object in wrong state";
+        default: return "unknown status";
+    }
+}
+
+int lcp_index_build(const void* d_tokens, int64_t N, lcp_format_t fmt, int64_t capacity,
+                    int32_t max_k, lcp_stream_t stream, lcp_index_t* out) {
+    if (!out) return LCP_ERR_INVALID;
+    *out = nullptr;
+    if (!valid_fmt(fmt) || N < 0 || N >= (1ll << 30) || (N > 0 && !d_tokens)) return LCP_ERR_INVALID;
+    if (max_k < 1 || max_k > LCP_INDEX_MAX_K) return LCP_ERR_INVALID;
+    if (capacity == 0) capacity = N;
+    if (capacity < N || capacity >= (1ll << 30)) return LCP_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    lcp_index_s* x = new (std::nothrow) lcp_index_s();
+    if (!x) return LCP_ERR_OOM;
+    cudaGetDevice(&x->device);
+    x->tb = fmt.token_bytes;
+    x->L = fmt.L;
+    x->vocab = fmt.vocab;
+    x->tpw = 8 / x->tb;
+    x->bits = 8 * x->tb;
+    x->W = (x->L + x->tpw - 1) / x->tpw;
+    x->max_k = max_k;
+    x->K = ((max_k + 31) / 32) * 32;
+    x->cap = capacity;
+    x->N = N;
+    x->last_stream = stream;
+    retain_pool_memory();
+    int rc = alloc_index(x, N, capacity, s);
+    if (rc == LCP_OK && N > 0) {
+        lcpk::RowFmt f = lcpk::make_fmt(x->tb, x->L, d_tokens);
+        rc = build_sorted_ids(d_tokens, f, N, x->buf[0].ids, x->status, s);
+        if (rc == LCP_OK) rc = gather_rows_and_lcp(d_tokens, f, N, x->buf[0].ids, x->buf[0], x->W, s);
+        if (rc == LCP_OK) rc = build_aux(x, s);
+    }
+    if (rc == LCP_OK) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_status(e);
+    }
+    if (rc != LCP_OK) {
+        cudaStreamSynchronize(s);
+        free_index_memory(x, s);
+        cudaStreamSynchronize(s);
+        delete x;
+        return rc;
+    }
+    *out = x;
+    return LCP_OK;
+}
+
+int lcp_index_build_host(const void* h_tokens, int64_t N, lcp_format_t fmt, int64_t capacity,
+                         int32_t max_k, lcp_stream_t stream, lcp_index_t* out) {
+    if (!out) return LCP_ERR_INVALID;
+    *out = nullptr;
+    if (!valid_fmt(fmt) || N < 0 || N >= (1ll << 30) || (N > 0 && !h_tokens)) return LCP_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t bytes = (size_t)N * fmt.L * fmt.token_bytes;
+    void* d = nullptr;
+    if (bytes) {
+        LCP_CUDA_TRY(cudaMallocAsync(&d, bytes, s));
+        LCP_CUDA_TRY(cudaMemcpyAsync(d, h_tokens, bytes, cudaMemcpyHostToDevice, s));
+    }
+    int rc = lcp_index_build(d, N, fmt, capacity, max_k, stream, out);
+    if (d) cudaFreeAsync(d, s);
+    return rc;
+}
+
+int lcp_index_insert(lcp_index_t x, const void* d_tokens, int64_t n, lcp_stream_t stream) {
+    if (!x || n < 0 || (n > 0 && !d_tokens)) return LCP_ERR_INVALID;
+    if (n == 0) return LCP_OK;
+    if (x->N + n > x->cap) return LCP_ERR_CAPACITY;
+    if (!x->buf[1].rows) return LCP_ERR_CAPACITY;
+    x->last_stream = stream;
+    int rc = insert_device(x, d_tokens, n, (cudaStream_t)stream);
+    if (rc == LCP_OK) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_status(e);
+    }
+    return rc;
+}
+
+int lcp_topk_batch(lcp_index_t x, const void* d_queries, int64_t Q, int32_t k, int32_t* d_out_ids,
+                   uint8_t* d_out_lcp, lcp_stream_t stream) {
+    if (!x || Q < 0 || k < 1 || k > x->max_k) return LCP_ERR_INVALID;
+    if (Q > 0 && (!d_queries || !d_out_ids || !d_out_lcp)) return LCP_ERR_INVALID;
+    x->last_stream = stream;
+    int rc = topk_batch_device(x, d_queries, Q, k, d_out_ids, d_out_lcp, (cudaStream_t)stream);
+    if (rc == LCP_OK) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_status(e);
+    }
+    return rc;
+}
+
+static int grow(void** p, size_t* have, size_t need, cudaStream_t s) {
+    if (*have >= need) return LCP_OK;
+    if (*p) {
+        cudaStreamSynchronize(s);
+        cudaFree(*p);
+        *p = nullptr;
+        *have = 0;
+    }
+    LCP_CUDA_TRY(cudaMalloc(p, need));
+    *have = need;
+    return LCP_OK;
+}
+
+int lcp_topk_batch_host(lcp_index_t x, const void* h_queries, int64_t Q, int32_t k, int32_t* h_out_ids,
+                        uint8_t* h_out_lcp, lcp_stream_t stream) {
+    if (!x || Q < 0 || k < 1 || k > x->max_k) return LCP_ERR_INVALID;
+    if (Q == 0) return LCP_OK;
+    if (!h_queries || !h_out_ids || !h_out_lcp) return LCP_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t qb = (size_t)Q * x->L * x->tb;
+    size_t ob = (size_t)Q * k * (sizeof(int32_t) + 1);
+    int rc;
+    if ((rc = grow(&x->stage_in, &x->stage_in_bytes, qb, s))) return rc;
+    if ((rc = grow(&x->stage_out, &x->stage_out_bytes, ob, s))) return rc;
+    int32_t* d_ids = (int32_t*)x->stage_out;
+    uint8_t* d_lcp = (uint8_t*)x->stage_out + (size_t)Q * k * sizeof(int32_t);
+    LCP_CUDA_TRY(cudaMemcpyAsync(x->stage_in, h_queries, qb, cudaMemcpyHostToDevice, s));
+    rc = lcp_topk_batch(x, x->stage_in, Q, k, d_ids, d_lcp, stream);
+    if (rc) return rc;
+    LCP_CUDA_TRY(cudaMemcpyAsync(h_out_ids, d_ids, (size_t)Q * k * sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, s));
+    LCP_CUDA_TRY(cudaMemcpyAsync(h_out_lcp, d_lcp, (size_t)Q * k, cudaMemcpyDeviceToHost, s));
+    LCP_CUDA_TRY(cudaStreamSynchronize(s));
+    return LCP_OK;
+}
+
+int lcp_scan_topk(const void* d_tokens, int64_t N, lcp_format_t fmt, const void* d_queries, int64_t Q,
+                  int32_t k, int32_t* d_out_ids, uint8_t* d_out_lcp, lcp_stream_t stream) {
+    if (!valid_fmt(fmt) || N < 0 || N >= (1ll << 30) || Q < 0 || k < 1 || k > LCP_SCAN_MAX_K)
+        return LCP_ERR_INVALID;
+    if (Q > 0 && (!d_queries || !d_out_ids || !d_out_lcp)) return LCP_ERR_INVALID;
+    if (N > 0 && Q > 0 && !d_tokens) return LCP_ERR_INVALID;
+    int rc = scan_topk_device(d_tokens, N, fmt.token_bytes, fmt.L, d_queries, Q, k, d_out_ids,
+                              d_out_lcp, (cudaStream_t)stream);
+    if (rc == LCP_OK) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_status(e);
+    }
+    return rc;
+}
+
+int lcp_index_size(lcp_index_t x, int64_t* N, int64_t* bytes) {
+    if (!x) return LCP_ERR_INVALID;
+    if (N) *N = x->N;
+    if (bytes) *bytes = x->bytes;
+    return LCP_OK;
+}
+
+int lcp_index_export(lcp_index_t x, int32_t* d_ids, uint8_t* d_H, lcp_stream_t stream) {
+    if (!x) return LCP_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (x->N == 0) return LCP_OK;
+    if (d_ids)
+        LCP_CUDA_TRY(cudaMemcpyAsync(d_ids, x->buf[x->cur].ids, sizeof(int32_t) * x->N,
+                                     cudaMemcpyDeviceToDevice, s));
+    if (d_H)
+        LCP_CUDA_TRY(cudaMemcpyAsync(d_H, x->buf[x->cur].H, (size_t)x->N, cudaMemcpyDeviceToDevice, s));
+    return LCP_OK;
+}
+
+int lcp_index_sync(lcp_index_t x) {
+    if (!x) return LCP_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)x->last_stream;
+    LCP_CUDA_TRY(cudaStreamSynchronize(s));
+    return read_status(x->status, s);
+}
+
+int lcp_index_destroy(lcp_index_t x) {
+    if (!x) return LCP_OK;
+    cudaStream_t s = (cudaStream_t)x->last_stream;
+    free_index_memory(x, s);  // stream-ordered: after the work already queued on s
+    cudaStreamSynchronize(s);
+    delete x;
+    return LCP_OK;
+}
+
+int lcp_device_status(void) {
+    LCP_CUDA_TRY(cudaDeviceSynchronize());
+    return read_status(lib_status_word(), 0);
+}
+
+int64_t lcp_launch_count(void) { return g_launches.load(); }
+
+int lcp_debug_bounded_wait(int64_t spin_limit, lcp_stream_t stream) {
+    if (spin_limit < 1) return LCP_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    int* flag = nullptr;
+    int* st = nullptr;
+    LCP_CUDA_TRY(cudaMallocAsync((void**)&flag, sizeof(int), s));
+    LCP_CUDA_TRY(cudaMallocAsync((void**)&st, sizeof(int), s));
+    LCP_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    LCP_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(int), s));
+    LCP_LAUNCH(lcpk::k_debug_wait, 1, 1, 0, s, flag, (long long)spin_limit, st);
+    int rc = read_status(st, s);
+    cudaFreeAsync(flag, s);
+    cudaFreeAsync(st, s);
+    cudaStreamSynchronize(s);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,374 @@
+// Index build: Algorithm 1 (BuildLCPIndex) + Algorithm 2 in array form.
+//
+// Sorting N rows of W packed words (up to 64 words = 512 bytes each) with a
+// plain LSD sort would take 8*W digit passes over all N keys.  Instead the
+// sort refines word by word: round 0 sorts (word 0, id) pairs of every row
+// with the onesweep radix sort; only rows whose word-0 prefix is shared by
+// another row stay "active", and round r sorts the active rows by (tie group,
+// word r) -- a stable LSD sort on word r followed by one on the group rank.
+// Rows leave as soon as their prefix is unique, so on the paper's workloads
+// (Zipf-shared prefixes, first differences within a few tokens) almost all
+// of the work is round 0.  Stability of every pass keeps equal rows in id
+// order, which is the posting-list order of Algorithm 1.
+#include "index.cuh"
+#include "sort.cuh"
+
+namespace lcpk {
+
+__global__ void k_keys_word0(const uint8_t* __restrict__ tokens, RowFmt f, uint32_t n,
+                             uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    keys[i] = pack_word(row_of(tokens, i, f), 0, f);
+    vals[i] = i;
+}
+
+__global__ void k_eq_sorted(const uint64_t* __restrict__ keys, uint32_t n, uint8_t* __restrict__ eq) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    eq[i] = (i > 0 && keys[i] == keys[i - 1]) ? 1 : 0;
+}
+
+// keys[i] = word r of the row at sorted position act[i]; vals[i] = i.
+__global__ void k_keys_active(const uint8_t* __restrict__ tokens, RowFmt f, uint32_t n_rows,
+                              const int32_t* __restrict__ ids, const uint32_t* __restrict__ act,
+                              uint32_t m, int r, uint64_t* __restrict__ keys,
+                              uint32_t* __restrict__ vals) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int32_t id = ids[act[i]];
+    keys[i] = (uint32_t)id < n_rows ? pack_word(row_of(tokens, id, f), r, f) : 0ull;
+    vals[i] = i;
+}
+
+// After the word sort: key by index (for the tie test) and group keys.
+__global__ void k_group_keys(const uint64_t* __restrict__ ks, const uint32_t* __restrict__ vs,
+                             const uint32_t* __restrict__ grp, uint32_t m,
+                             uint64_t* __restrict__ kbi, uint32_t* __restrict__ gk,
+                             uint32_t* __restrict__ gv) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    uint32_t v = vs[i];
+    kbi[v] = ks[i];
+    gk[i] = grp[v];
+    gv[i] = v;
+}
+
+__global__ void k_apply_gather(const uint32_t* __restrict__ fv, const int32_t* __restrict__ ids,
+                               const uint32_t* __restrict__ act, const uint64_t* __restrict__ kbi,
+                               const uint32_t* __restrict__ grp, uint32_t m,
+                               int32_t* __restrict__ newid, uint64_t* __restrict__ fkey,
+                               uint32_t* __restrict__ fgrp) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    uint32_t v = fv[i];
+    newid[i] = ids[act[v]];
+    fkey[i] = kbi[v];
+    fgrp[i] = grp[v];
+}
+
+__global__ void k_apply_scatter(const int32_t* __restrict__ newid, const uint32_t* __restrict__ act,
+                                const uint64_t* __restrict__ fkey,
+                                const uint32_t* __restrict__ fgrp, uint32_t m,
+                                int32_t* __restrict__ ids, uint8_t* __restrict__ eq) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    ids[act[i]] = newid[i];
+    eq[i] = (i > 0 && fgrp[i] == fgrp[i - 1] && fkey[i] == fkey[i - 1]) ? 1 : 0;
+}
+
+__global__ void k_remap_active(const uint32_t* __restrict__ act, const uint32_t* __restrict__ idx,
+                               uint32_t m, uint32_t* __restrict__ act2) {
+    uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    act2[j] = act[idx[j]];
+}
+
+__global__ void k_copy_ids(const uint32_t* __restrict__ vs, uint32_t n, int32_t* __restrict__ ids) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) ids[i] = (int32_t)vs[i];
+}
+
+// rows[p][w] = packed word w of raw row ids[p]; head[p] = rows[p][0].
+__global__ void k_gather_rows(const uint8_t* __restrict__ tokens, RowFmt f, int64_t n,
+                              const int32_t* __restrict__ ids, uint64_t* __restrict__ rows,
+                              uint64_t* __restrict__ head) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t total = n * f.W;
+    if (e >= total) return;
+    int64_t p = e / f.W;
+    int w = (int)(e - p * f.W);
+    int32_t id = ids[p];
+    uint64_t x = (uint64_t)id < (uint64_t)n ? pack_word(row_of(tokens, id, f), w, f) : 0ull;
+    rows[e] = x;
+    if (w == 0) head[p] = x;
+}
+
+// H[p] = LCP(rows[p-1], rows[p]), H[0] = 0.
+__global__ void k_adjacent_lcp(const uint64_t* __restrict__ rows, int64_t n, int W, int L, int tpw,
+                               int bits, uint8_t* __restrict__ H) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    if (p == 0) {
+        H[0] = 0;
+        return;
+    }
+    const uint64_t* a = rows + (p - 1) * W;
+    const uint64_t* b = rows + p * W;
+    int l = L;
+    for (int w = 0; w < W; ++w) {
+        uint64_t x = a[w] ^ b[w];
+        if (x) {
+            l = w * tpw + (__clzll((long long)x) / bits);
+            if (l > L) l = L;
+            break;
+        }
+    }
+    H[p] = (uint8_t)l;
+}
+
+__global__ void k_inverse(const int32_t* __restrict__ ids, int64_t n, int32_t* __restrict__ pos) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) {
+        int32_t id = ids[p];
+        if ((uint64_t)id < (uint64_t)n) pos[id] = (int32_t)p;
+    }
+}
+
+// out[b] = min(in[32b .. 32b+31]) (entries past n_in ignored).
+__global__ void k_min32(const uint8_t* __restrict__ in, int64_t n_in, uint8_t* __restrict__ out,
+                        int64_t n_out) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_out) return;
+    int64_t s = b * 32, e = s + 32 < n_in ? s + 32 : n_in;
+    uint32_t m = 255;
+    for (int64_t i = s; i < e; ++i) m = min(m, (uint32_t)in[i]);
+    out[b] = (uint8_t)m;
+}
+
+// One CTA (128 threads) per block: ids of the block sorted ascending (rank
+// sort: ids are distinct) with their in-block offsets; padding 0xFFFFFFFF.
+__global__ void __launch_bounds__(kBlk) k_sort_blocks(const int32_t* __restrict__ ids, int64_t n,
+                                                      uint32_t* __restrict__ sblk,
+                                                      uint8_t* __restrict__ soff) {
+    __shared__ uint32_t v[kBlk];
+    int64_t b = blockIdx.x;
+    int t = threadIdx.x;
+    int64_t p = b * kBlk + t;
+    uint32_t mine = p < n ? (uint32_t)ids[p] : kInf;
+    v[t] = mine;
+    __syncthreads();
+    int rank = 0;
+    for (int j = 0; j < kBlk; ++j) {
+        uint32_t o = v[j];
+        rank += (o < mine) || (o == mine && j < t);
+    }
+    sblk[b * kBlk + rank] = mine;
+    soff[b * kBlk + rank] = (uint8_t)t;
+}
+
+// Sparse-table level j: out[b] = K smallest of lists prev[b] and prev[b+half]
+// (disjoint position spans, so no duplicates).  One warp per b, merge path.
+__global__ void k_st_level(const uint32_t* __restrict__ prev, int64_t prev_stride, int64_t half,
+                           int64_t nb_valid, int K, uint32_t* __restrict__ out) {
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= nb_valid) return;
+    const uint32_t* A = prev + warp * prev_stride;
+    const uint32_t* B = prev + (warp + half) * prev_stride;
+    uint32_t* O = out + warp * (int64_t)K;
+    int per = K / 32;
+    int d0 = lane * per;
+    int lo = d0 - K > 0 ? d0 - K : 0, hi = d0 < K ? d0 : K;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (A[mid] <= B[d0 - 1 - mid]) lo = mid + 1;
+        else hi = mid;
+    }
+    int i = lo, j = d0 - lo;
+    for (int t = 0; t < per; ++t) {
+        bool takeA = (i < K) && (j >= K || A[i] <= B[j]);
+        O[d0 + t] = takeA ? A[i++] : B[j++];
+    }
+}
+
+}  // namespace lcpk
+
+namespace lcph {
+using namespace lcpk;
+
+static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+int build_sorted_ids(const void* tokens, const RowFmt& f, int64_t N64, int32_t* ids_out, int* err,
+                     cudaStream_t s) {
+    if (N64 <= 0) return LCP_OK;
+    uint32_t N = (uint32_t)N64;
+    const uint8_t* tk = reinterpret_cast<const uint8_t*>(tokens);
+    if (N == 1) {
+        LCP_CUDA_TRY(cudaMemsetAsync(ids_out, 0, sizeof(int32_t), s));
+        return LCP_OK;
+    }
+    // scratch
+    uint64_t *k0, *k1, *kbi, *fkey;
+    uint32_t *v0, *v1, *act, *grp, *act2, *grp2, *idx2, *gk, *gv, *gk1, *gv1, *fgrp;
+    int32_t* newid;
+    uint8_t* eq;
+    size_t n8 = sizeof(uint64_t) * N, n4 = sizeof(uint32_t) * N;
+    LCP_CUDA_TRY(cudaMallocAsync((void**)&k0, n8, s));
+    LCP_CUDA_TRY(cudaMallocAsync((void**)&k1, n8, s));
+    LCP_CUDA_TRY(cudaMallocAsync((void**)&kbi, n8, s));
+    LCP_CUDA_TRY(cudaMallocAsync((void**)&fkey, n8, s));
+    uint32_t** u4[] = {&v0, &v1, &act, &grp, &act2, &grp2, &idx2, &gk, &gv, &gk1, &gv1, &fgrp};
+    for (auto p : u4) LCP_CUDA_TRY(cudaMallocAsync((void**)p, n4, s));
+    LCP_CUDA_TRY(cudaMallocAsync((void**)&newid, n4, s));
+    LCP_CUDA_TRY(cudaMallocAsync((void**)&eq, N, s));
+    SortWork w;
+    int rc = sort_work_alloc(w, N, err, s);
+    auto cleanup = [&]() {
+        cudaFreeAsync(k0, s);
+        cudaFreeAsync(k1, s);
+        cudaFreeAsync(kbi, s);
+        cudaFreeAsync(fkey, s);
+        for (auto p : u4) cudaFreeAsync(*p, s);
+        cudaFreeAsync(newid, s);
+        cudaFreeAsync(eq, s);
+        sort_work_free(w, s);
+    };
+    if (rc) {
+        cleanup();
+        return rc;
+    }
+    // round 0: (word 0, id) over all rows
+    LCP_LAUNCH(k_keys_word0, blocks_for(N, 256), 256, 0, s, tk, f, N, k0, v0);
+    uint64_t* ks;
+    uint32_t* vs;
+    rc = radix_sort_pairs_u64(k0, v0, k1, v1, N, 64, w, s, &ks, &vs);
+    if (rc) {
+        cleanup();
+        return rc;
+    }
+    LCP_LAUNCH(k_copy_ids, blocks_for(N, 256), 256, 0, s, vs, N, ids_out);
+    LCP_LAUNCH(k_eq_sorted, blocks_for(N, 256), 256, 0, s, ks, N, eq);
+    uint32_t m = 0, G = 0;
+    rc = tie_compact(eq, N, act, grp, &m, &G, w, s);
+    // rounds 1..W-1 on the rows whose prefix is still shared
+    for (int r = 1; rc == 0 && r < f.W && m > 0; ++r) {
+        LCP_LAUNCH(k_keys_active, blocks_for(m, 256), 256, 0, s, tk, f, N, ids_out, act, m, r, k0,
+                   v0);
+        rc = radix_sort_pairs_u64(k0, v0, k1, v1, m, 64, w, s, &ks, &vs);
+        if (rc) break;
+        LCP_LAUNCH(k_group_keys, blocks_for(m, 256), 256, 0, s, ks, vs, grp, m, kbi, gk, gv);
+        int gbits = 0;
+        while (gbits < 32 && (1ull << gbits) < (uint64_t)G) ++gbits;
+        uint32_t *gks, *fv;
+        rc = radix_sort_pairs_u32(gk, gv, gk1, gv1, m, gbits, w, s, &gks, &fv);
+        if (rc) break;
+        LCP_LAUNCH(k_apply_gather, blocks_for(m, 256), 256, 0, s, fv, ids_out, act, kbi, grp, m,
+                   newid, fkey, fgrp);
+        LCP_LAUNCH(k_apply_scatter, blocks_for(m, 256), 256, 0, s, newid, act, fkey, fgrp, m,
+                   ids_out, eq);
+        uint32_t m2 = 0, G2 = 0;
+        rc = tie_compact(eq, m, idx2, grp2, &m2, &G2, w, s);
+        if (rc) break;
+        if (m2) LCP_LAUNCH(k_remap_active, blocks_for(m2, 256), 256, 0, s, act, idx2, m2, act2);
+        uint32_t* t = act;
+        act = act2;
+        act2 = t;
+        t = grp;
+        grp = grp2;
+        grp2 = t;
+        m = m2;
+        G = G2;
+    }
+    cleanup();
+    return rc;
+}
+
+int gather_rows_and_lcp(const void* tokens, const RowFmt& f, int64_t N, const int32_t* ids,
+                        lcp_buffers& b, int W, cudaStream_t s) {
+    if (N <= 0) return LCP_OK;
+    int64_t total = N * W;
+    LCP_LAUNCH(k_gather_rows, blocks_for(total, 256), 256, 0, s,
+               reinterpret_cast<const uint8_t*>(tokens), f, N, ids, b.rows, b.head);
+    return adjacent_lcp(b.rows, N, W, f.L, f.tpw, f.bits, b.H, s);
+}
+
+int adjacent_lcp(const uint64_t* rows, int64_t N, int W, int L, int tpw, int bits, uint8_t* H,
+                 cudaStream_t s) {
+    if (N <= 0) return LCP_OK;
+    LCP_LAUNCH(k_adjacent_lcp, blocks_for(N, 256), 256, 0, s, rows, N, W, L, tpw, bits, H);
+    return LCP_OK;
+}
+
+int build_aux(lcp_index_s* x, cudaStream_t s) {
+    const int64_t N = x->N;
+    lcp_buffers& b = x->buf[x->cur];
+    if (N <= 0) return LCP_OK;
+    LCP_LAUNCH(k_inverse, blocks_for(N, 256), 256, 0, s, b.ids, N, x->pos);
+    // min tree over H
+    int64_t len = N;
+    const uint8_t* in = b.H;
+    x->hlen[0] = N;
+    int lev = 0;
+    int64_t off = 0;
+    while (len > 32 && lev < kMaxHLev) {
+        int64_t nl = (len + 31) / 32;
+        ++lev;
+        x->hoff[lev] = off;
+        x->hlen[lev] = nl;
+        LCP_LAUNCH(k_min32, blocks_for(nl, 256), 256, 0, s, in, len, x->hmin + off, nl);
+        in = x->hmin + off;
+        off += nl;
+        len = nl;
+    }
+    x->hlev = lev;
+    // sorted blocks and sparse table of K smallest ids
+    int64_t nblk = (N + kBlk - 1) / kBlk;
+    LCP_LAUNCH(k_sort_blocks, (unsigned)nblk, kBlk, 0, s, b.ids, N, x->sblk, x->soff);
+    int K = x->K;
+    for (int j = 1; j <= x->st_levels_cap && (1ll << j) <= nblk; ++j) {
+        int64_t half = 1ll << (j - 1);
+        int64_t valid = nblk - (1ll << j) + 1;
+        const uint32_t* prev = j == 1 ? x->sblk : x->st + (int64_t)(j - 2) * x->nblk_cap * K;
+        int64_t pstride = j == 1 ? kBlk : K;
+        uint32_t* out = x->st + (int64_t)(j - 1) * x->nblk_cap * K;
+        LCP_LAUNCH(k_st_level, blocks_for(valid * 32, 256), 256, 0, s, prev, pstride, half, valid, K,
+                   out);
+    }
+    return LCP_OK;
+}
+
+DevIndex dev_view(const lcp_index_s* x) {
+    DevIndex d;
+    const lcp_buffers& b = x->buf[x->cur];
+    d.N = x->N;
+    d.W = x->W;
+    d.L = x->L;
+    d.tpw = x->tpw;
+    d.bits = x->bits;
+    d.K = x->K;
+    d.nblk = (x->N + kBlk - 1) / kBlk;
+    d.hlev = x->hlev;
+    int st = 0;
+    while (st < x->st_levels_cap && (1ll << (st + 1)) <= d.nblk) ++st;
+    d.st_levels = st;
+    d.rows = b.rows;
+    d.head = b.head;
+    d.ids = b.ids;
+    d.H = b.H;
+    d.pos = x->pos;
+    d.hmin = x->hmin;
+    for (int i = 0; i <= kMaxHLev; ++i) {
+        d.hoff[i] = x->hoff[i];
+        d.hlen[i] = x->hlen[i];
+    }
+    d.hlen[0] = x->N;
+    d.sblk = x->sblk;
+    d.soff = x->soff;
+    d.st = x->st;
+    d.st_stride = x->nblk_cap;
+    d.status = x->status;
+    return d;
+}
+
+}  // namespace lcph

@@ -1,0 +1,112 @@
+// Device layout of the prefix index (the array form of the paper's trie).
+//
+//   rows [cap][W] u64   packed rows in lexicographic order (equal rows by id)
+//   head [cap]    u64   word 0 of each sorted row (16 MB at N=2M: L2-resident
+//                       for the binary search)
+//   ids  [cap]    i32   original id of each sorted row
+//   H    [cap]    u8    H[0] = 0, H[p] = LCP(row p-1, row p)   (Alg. 2's subtree
+//                       sizes are the lengths of H's LCP intervals)
+//   pos  [cap]    i32   inverse of ids (id -> sorted position)
+//   hmin          u8    32-ary min tree over H: level j+1 holds the minimum of
+//                       32 consecutive level-j entries.  Finds the end of an LCP
+//                       interval (next/previous H < d) in a few L2 probes.
+//   sblk [nblk][128] u32  ids of each 128-position block sorted ascending
+//   soff [nblk][128] u8   the in-block offset of each of those ids
+//   st   [lev][nblk][K] u32  sparse table: level j >= 1 at block b holds the K
+//                       smallest ids of blocks [b, b + 2^j), ascending; padded
+//                       with 0xFFFFFFFF.  Any position range's K smallest ids
+//                       come from two partial blocks and two table entries.
+#pragma once
+
+#include "common.cuh"
+
+namespace lcpk {
+
+constexpr int kBlk = 128;        // positions per tie-fill block
+constexpr int kMaxHLev = 7;      // min-tree levels above H (32^7 > 2^30)
+constexpr int kMaxStLev = 24;
+constexpr uint32_t kInf = 0xFFFFFFFFu;
+
+struct DevIndex {
+    int64_t N;
+    int W, L, tpw, bits;
+    int K;            // tie-list length (multiple of 32, >= max_k)
+    int64_t nblk;     // ceil(N / kBlk)
+    int hlev;         // number of min-tree levels above H
+    int st_levels;    // sparse-table levels stored (1..st_levels)
+    const uint64_t* rows;
+    const uint64_t* head;
+    const int32_t* ids;
+    const uint8_t* H;
+    const int32_t* pos;
+    const uint8_t* hmin;
+    int64_t hoff[kMaxHLev + 1];  // offset of level j in hmin (j >= 1)
+    int64_t hlen[kMaxHLev + 1];  // entries at level j (hlen[0] = N)
+    const uint32_t* sblk;
+    const uint8_t* soff;
+    const uint32_t* st;
+    int64_t st_stride;  // nblk capacity used for the table layout
+    int* status;
+};
+
+}  // namespace lcpk
+
+struct lcp_buffers {
+    uint64_t* rows = nullptr;
+    uint64_t* head = nullptr;
+    int32_t* ids = nullptr;
+    uint8_t* H = nullptr;
+};
+
+struct lcp_index_s {
+    int device = 0;
+    int tb = 0, L = 0, W = 0, tpw = 0, bits = 0, vocab = 0;
+    int64_t N = 0, cap = 0;
+    int max_k = 0, K = 0;
+    lcp_buffers buf[2];
+    int cur = 0;
+    int32_t* pos = nullptr;
+    uint8_t* hmin = nullptr;
+    int hlev = 0;
+    int64_t hoff[lcpk::kMaxHLev + 1] = {0};
+    int64_t hlen[lcpk::kMaxHLev + 1] = {0};
+    uint32_t* sblk = nullptr;
+    uint8_t* soff = nullptr;
+    uint32_t* st = nullptr;
+    int64_t nblk_cap = 0;
+    int st_levels_cap = 0;
+    int* status = nullptr;  // device status word
+    void* last_stream = nullptr;
+    int64_t bytes = 0;
+    // host-buffer entry points: device staging grown on demand
+    void* stage_in = nullptr;
+    size_t stage_in_bytes = 0;
+    void* stage_out = nullptr;
+    size_t stage_out_bytes = 0;
+    // insert scratch (allocated at build when cap > N)
+    uint64_t* ins_rows = nullptr;   // [LCP_INSERT_SMALL_BATCH][W] sorted new rows
+    int32_t* ins_ids = nullptr;     // ids of the sorted new rows
+    int64_t* ins_rank = nullptr;    // output position of each new row
+};
+
+namespace lcph {
+
+lcpk::DevIndex dev_view(const lcp_index_s* x);
+
+// Sorts rows of `tokens` and writes their ids in sorted order (build step).
+int build_sorted_ids(const void* tokens, const lcpk::RowFmt& f, int64_t N, int32_t* ids_out,
+                     int* err, cudaStream_t s);
+// rows/head/H from raw tokens and sorted ids.
+int gather_rows_and_lcp(const void* tokens, const lcpk::RowFmt& f, int64_t N, const int32_t* ids,
+                        lcp_buffers& b, int W, cudaStream_t s);
+// H from already-packed sorted rows.
+int adjacent_lcp(const uint64_t* rows, int64_t N, int W, int L, int tpw, int bits, uint8_t* H,
+                 cudaStream_t s);
+// pos, min tree and tie tables of the current buffers.
+int build_aux(lcp_index_s* x, cudaStream_t s);
+
+int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, int32_t* out_ids,
+                      uint8_t* out_lcp, cudaStream_t s);
+int insert_device(lcp_index_s* x, const void* d_tokens, int64_t n, cudaStream_t s);
+
+}  // namespace lcph

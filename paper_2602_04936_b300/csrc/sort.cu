@@ -1,0 +1,422 @@
+// Onesweep-style LSD radix sort (8-bit digits) for the index build.
+//
+// One upfront kernel builds the histograms of every digit position in a
+// single read of the keys (warp-aggregated with __match_any_sync so that the
+// heavily skewed digits of Zipf-distributed tokens do not serialise on shared
+// atomics).  Each digit pass is then ONE kernel: a CTA takes a 4096-key tile
+// (ticket from an atomic counter, so tiles start in order), ranks its keys
+// stably with warp multisplit, publishes its per-digit counts, and resolves
+// its global offsets by decoupled look-back over the predecessors' status
+// words.  Every wait in the look-back is bounded (kSpinLimit); on expiry the
+// kernel records DEV_TIMEOUT and finishes instead of spinning forever.
+#include "sort.cuh"
+
+namespace lcpk {
+
+using lcph::kSortItems;
+using lcph::kSortThreads;
+using lcph::kSortTile;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagInc = 2u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1;
+
+template <typename K>
+__global__ void __launch_bounds__(256) k_digit_hist(const K* __restrict__ keys, uint32_t n,
+                                                    uint32_t* __restrict__ hist, int passes) {
+    __shared__ uint32_t sh[8 * 256];
+    for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const unsigned lane = lane_id();
+    const uint32_t warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t base = warp_global * 32; base < n; base += nwarps * 32) {
+        uint32_t idx = base + lane;
+        bool valid = idx < n;
+        K k = valid ? keys[idx] : (K)0;
+        for (int p = 0; p < passes; ++p) {
+            uint32_t d = valid ? (uint32_t)(k >> (8 * p)) & 255u : 256u;
+            unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (valid && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&sh[p * 256 + d], __popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// Exclusive scan of a 256-entry table by 256 threads.
+__device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t* tmp /*8*/) {
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= (unsigned)o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    uint32_t add = 0;
+    for (unsigned w = 0; w < warp; ++w) add += tmp[w];
+    __syncthreads();
+    return add + x - v;
+}
+
+// Per pass: digit bases (exclusive scan of the histogram) and whether the
+// digit is constant (one bin holds every key).
+__global__ void __launch_bounds__(256) k_digit_prefix(const uint32_t* __restrict__ hist,
+                                                      uint32_t* __restrict__ base,
+                                                      uint32_t* __restrict__ skip, uint32_t n) {
+    __shared__ uint32_t tmp[8];
+    __shared__ int full;
+    const int p = blockIdx.x;
+    if (threadIdx.x == 0) full = 0;
+    __syncthreads();
+    uint32_t c = hist[p * 256 + threadIdx.x];
+    if (c == n) full = 1;
+    uint32_t e = block_excl_scan_256(c, tmp);
+    base[p * 256 + threadIdx.x] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) skip[p] = full ? 1u : 0u;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(
+    const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
+    uint32_t* __restrict__ vout, uint32_t n, int shift, const uint32_t* __restrict__ digit_base,
+    uint32_t* status, uint32_t* counter, int* err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* whist = reinterpret_cast<uint32_t*>(smem);  // [warps][256]
+    uint32_t* tcount = whist + kSortWarps * 256;           // [256]
+    uint32_t* lstart = tcount + 256;                       // [256]
+    uint32_t* goff = lstart + 256;                         // [256]
+    uint32_t* misc = goff + 256;                           // [16]
+    K* skeys = reinterpret_cast<K*>(misc + 16);            // [tile]
+    uint32_t* svals = reinterpret_cast<uint32_t*>(skeys + kSortTile);
+
+    const int tid = threadIdx.x;
+    const unsigned lane = lane_id();
+    const int warp = tid >> 5;
+    if (tid == 0) misc[0] = atomicAdd(counter, 1u);
+    for (int i = tid; i < kSortWarps * 256; i += kSortThreads) whist[i] = 0;
+    __syncthreads();
+    const uint32_t tile = misc[0];
+    const uint32_t base = tile * (uint32_t)kSortTile;
+    const uint32_t tile_n = min((uint32_t)kSortTile, n - base);
+
+    K key[kSortItems];
+    uint32_t val[kSortItems];
+    uint32_t rk[kSortItems];
+    uint32_t* wh = whist + warp * 256;
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        uint32_t idx = (uint32_t)warp * (32 * kSortItems) + (uint32_t)i * 32 + lane;
+        bool valid = idx < tile_n;
+        key[i] = valid ? kin[base + idx] : (K)0;
+        val[i] = valid ? vin[base + idx] : 0u;
+        uint32_t d = valid ? (uint32_t)(key[i] >> shift) & 255u : 256u;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        uint32_t prior = valid ? wh[d] : 0u;
+        __syncwarp();
+        if (valid && lane == (unsigned)(__ffs(peers) - 1)) wh[d] = prior + __popc(peers);
+        __syncwarp();
+        rk[i] = prior + __popc(peers & lt);
+    }
+    __syncthreads();
+    {
+        // digit tid: warp exclusive offsets and the tile's count
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) {
+            uint32_t c = whist[w * 256 + tid];
+            whist[w * 256 + tid] = run;
+            run += c;
+        }
+        tcount[tid] = run;
+    }
+    uint32_t my = tcount[tid];
+    uint32_t ls = block_excl_scan_256(my, misc + 8);
+    lstart[tid] = ls;
+    // decoupled look-back for digit tid
+    {
+        uint32_t excl = 0;
+        uint32_t* st = status + (size_t)tile * 256 + tid;
+        if (tile == 0) {
+            st_relaxed(st, kFlagInc | my);
+        } else {
+            st_relaxed(st, kFlagAgg | my);
+            int64_t j = (int64_t)tile - 1;
+            long long spins = 0;
+            while (j >= 0) {
+                uint32_t s = ld_relaxed(status + (size_t)j * 256 + tid);
+                uint32_t fl = s & ~kValMask;
+                if (fl == 0) {
+                    if (++spins > kSpinLimit) {
+                        flag_status(err, DEV_TIMEOUT);
+                        break;
+                    }
+                    continue;
+                }
+                excl += s & kValMask;
+                if (fl == kFlagInc) break;
+                --j;
+            }
+            st_relaxed(st, kFlagInc | ((excl + my) & kValMask));
+        }
+        goff[tid] = digit_base[tid] + excl - ls;  // modulo 2^32
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        uint32_t idx = (uint32_t)warp * (32 * kSortItems) + (uint32_t)i * 32 + lane;
+        if (idx < tile_n) {
+            uint32_t d = (uint32_t)(key[i] >> shift) & 255u;
+            uint32_t lp = lstart[d] + wh[d] + rk[i];
+            skeys[lp] = key[i];
+            svals[lp] = val[i];
+        }
+    }
+    __syncthreads();
+    for (uint32_t j = tid; j < tile_n; j += kSortThreads) {
+        K k = skeys[j];
+        uint32_t d = (uint32_t)(k >> shift) & 255u;
+        uint32_t dst = goff[d] + j;
+        if (dst < n) {  // always true unless a look-back wait ran out
+            kout[dst] = k;
+            vout[dst] = svals[j];
+        } else {
+            flag_status(err, DEV_BAD);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tie compaction (3-phase scan over 2048-element blocks)
+// ---------------------------------------------------------------------------
+constexpr int kCmpThreads = 256;
+constexpr int kCmpItems = 8;
+constexpr int kCmpBlock = kCmpThreads * kCmpItems;
+
+__device__ __forceinline__ void tie_flags(const uint8_t* eq, uint32_t n, uint32_t i, uint32_t& act,
+                                          uint32_t& start) {
+    uint32_t e = eq[i];
+    uint32_t e1 = (i + 1 < n) ? eq[i + 1] : 0u;
+    act = (e | e1) ? 1u : 0u;
+    start = (act && !e) ? 1u : 0u;
+}
+
+__global__ void __launch_bounds__(kCmpThreads) k_tie_count(const uint8_t* __restrict__ eq,
+                                                           uint32_t n, uint64_t* block_sums) {
+    __shared__ uint32_t sa[kCmpThreads / 32], ss[kCmpThreads / 32];
+    uint32_t a = 0, s = 0;
+    uint32_t b0 = blockIdx.x * kCmpBlock;
+    for (int j = 0; j < kCmpItems; ++j) {
+        uint32_t i = b0 + j * kCmpThreads + threadIdx.x;
+        if (i < n) {
+            uint32_t x, y;
+            tie_flags(eq, n, i, x, y);
+            a += x;
+            s += y;
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    if (lane_id() == 0) {
+        sa[threadIdx.x >> 5] = a;
+        ss[threadIdx.x >> 5] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t ta = 0, ts = 0;
+        for (int w = 0; w < kCmpThreads / 32; ++w) {
+            ta += sa[w];
+            ts += ss[w];
+        }
+        block_sums[blockIdx.x] = ((uint64_t)ta << 32) | ts;
+    }
+}
+
+// Single CTA: exclusive scan of block sums in place; totals to total[0..1].
+__global__ void __launch_bounds__(1024) k_scan_block_sums(uint64_t* sums, uint32_t nb,
+                                                          uint32_t* total) {
+    __shared__ uint64_t tmp[32];
+    __shared__ uint64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t b0 = 0; b0 < nb; b0 += 1024) {
+        uint32_t i = b0 + threadIdx.x;
+        uint64_t v = i < nb ? sums[i] : 0ull;
+        uint64_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane_id() >= (unsigned)o) x += y;
+        }
+        if (lane_id() == 31) tmp[threadIdx.x >> 5] = x;
+        __syncthreads();
+        uint64_t add = carry;
+        for (unsigned w = 0; w < (threadIdx.x >> 5); ++w) add += tmp[w];
+        if (i < nb) sums[i] = add + x - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = add + x;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        total[0] = (uint32_t)(carry >> 32);
+        total[1] = (uint32_t)carry;
+    }
+}
+
+__global__ void __launch_bounds__(kCmpThreads) k_tie_scatter(const uint8_t* __restrict__ eq,
+                                                             uint32_t n,
+                                                             const uint64_t* __restrict__ offs,
+                                                             uint32_t* __restrict__ out_idx,
+                                                             uint32_t* __restrict__ out_grp) {
+    __shared__ uint64_t tmp[kCmpThreads / 32];
+    __shared__ uint64_t carry;
+    if (threadIdx.x == 0) carry = offs[blockIdx.x];
+    __syncthreads();
+    uint32_t b0 = blockIdx.x * kCmpBlock;
+    for (int j = 0; j < kCmpItems; ++j) {
+        uint32_t i = b0 + j * kCmpThreads + threadIdx.x;
+        uint32_t a = 0, s = 0;
+        if (i < n) tie_flags(eq, n, i, a, s);
+        uint64_t v = ((uint64_t)a << 32) | s;
+        uint64_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane_id() >= (unsigned)o) x += y;
+        }
+        if (lane_id() == 31) tmp[threadIdx.x >> 5] = x;
+        __syncthreads();
+        uint64_t add = carry;
+        for (unsigned w = 0; w < (threadIdx.x >> 5); ++w) add += tmp[w];
+        uint64_t incl = add + x;
+        if (a) {
+            uint32_t slot = (uint32_t)((incl - v) >> 32);
+            out_idx[slot] = i;
+            out_grp[slot] = (uint32_t)incl - 1u;  // inclusive start count - 1
+        }
+        __syncthreads();
+        if (threadIdx.x == kCmpThreads - 1) carry = incl;
+        __syncthreads();
+    }
+}
+
+}  // namespace lcpk
+
+namespace lcph {
+using namespace lcpk;
+
+int sort_work_alloc(SortWork& w, uint32_t cap, int* err, cudaStream_t s) {
+    w.cap = cap;
+    w.err = err;
+    uint32_t tiles = (cap + kSortTile - 1) / kSortTile;
+    uint32_t nb = (cap + kCmpBlock - 1) / kCmpBlock;
+    if (tiles == 0) tiles = 1;
+    if (nb == 0) nb = 1;
+    LCP_CUDA_TRY(cudaMallocAsync((void**)&w.hist, sizeof(uint32_t) * kMaxPasses * 256, s));
+    LCP_CUDA_TRY(cudaMallocAsync((void**)&w.digit_base, sizeof(uint32_t) * kMaxPasses * 256, s));
+    LCP_CUDA_TRY(cudaMallocAsync((void**)&w.skip, sizeof(uint32_t) * kMaxPasses, s));
+    LCP_CUDA_TRY(cudaMallocAsync((void**)&w.status, sizeof(uint32_t) * kMaxPasses * tiles * 256, s));
+    LCP_CUDA_TRY(cudaMallocAsync((void**)&w.counters, sizeof(uint32_t) * kMaxPasses, s));
+    LCP_CUDA_TRY(cudaMallocAsync((void**)&w.block_sums, sizeof(uint64_t) * nb, s));
+    LCP_CUDA_TRY(cudaMallocAsync((void**)&w.total, sizeof(uint32_t) * 16, s));
+    LCP_CUDA_TRY(cudaMallocHost((void**)&w.h_total, sizeof(uint32_t) * 16));
+    return LCP_OK;
+}
+
+void sort_work_free(SortWork& w, cudaStream_t s) {
+    cudaFreeAsync(w.hist, s);
+    cudaFreeAsync(w.digit_base, s);
+    cudaFreeAsync(w.skip, s);
+    cudaFreeAsync(w.status, s);
+    cudaFreeAsync(w.counters, s);
+    cudaFreeAsync(w.block_sums, s);
+    cudaFreeAsync(w.total, s);
+    if (w.h_total) cudaFreeHost(w.h_total);
+    w = SortWork();
+}
+
+template <typename K>
+static int radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, uint32_t n, int key_bits,
+                           SortWork& w, cudaStream_t s, K** out_k, uint32_t** out_v) {
+    *out_k = k0;
+    *out_v = v0;
+    if (n <= 1) return LCP_OK;
+    if (n > w.cap) return LCP_ERR_INVALID;
+    int passes = (key_bits + 7) / 8;
+    if (passes > (int)(sizeof(K))) passes = (int)sizeof(K);
+    if (passes < 1) return LCP_OK;
+    LCP_CUDA_TRY(cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * passes * 256, s));
+    int grid = (int)((n + 255) / 256);
+    if (grid > 148 * 8) grid = 148 * 8;
+    LCP_LAUNCH(k_digit_hist<K>, grid, 256, 0, s, k0, n, w.hist, passes);
+    LCP_LAUNCH(k_digit_prefix, passes, 256, 0, s, w.hist, w.digit_base, w.skip, n);
+    LCP_CUDA_TRY(cudaMemcpyAsync(w.h_total, w.skip, sizeof(uint32_t) * passes,
+                                 cudaMemcpyDeviceToHost, s));
+    LCP_CUDA_TRY(cudaStreamSynchronize(s));
+    int run[kMaxPasses], nrun = 0;
+    for (int p = 0; p < passes; ++p)
+        if (!w.h_total[p]) run[nrun++] = p;
+    if (nrun == 0) return LCP_OK;
+    uint32_t tiles = (n + kSortTile - 1) / kSortTile;
+    LCP_CUDA_TRY(cudaMemsetAsync(w.status, 0, sizeof(uint32_t) * (size_t)nrun * tiles * 256, s));
+    LCP_CUDA_TRY(cudaMemsetAsync(w.counters, 0, sizeof(uint32_t) * kMaxPasses, s));
+    size_t smem = sizeof(uint32_t) * (kSortWarps * 256 + 3 * 256 + 16) +
+                  (sizeof(K) + sizeof(uint32_t)) * kSortTile;
+    LCP_CUDA_TRY(cudaFuncSetAttribute(k_onesweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    K* ki = k0;
+    uint32_t* vi = v0;
+    K* ko = k1;
+    uint32_t* vo = v1;
+    for (int r = 0; r < nrun; ++r) {
+        int p = run[r];
+        LCP_LAUNCH(k_onesweep<K>, tiles, kSortThreads, smem, s, ki, vi, ko, vo, n, 8 * p,
+                   w.digit_base + p * 256, w.status + (size_t)r * tiles * 256, w.counters + r,
+                   w.err);
+        K* tk = ki;
+        ki = ko;
+        ko = tk;
+        uint32_t* tv = vi;
+        vi = vo;
+        vo = tv;
+    }
+    *out_k = ki;
+    *out_v = vi;
+    return LCP_OK;
+}
+
+int radix_sort_pairs_u64(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, uint32_t n,
+                         int key_bits, SortWork& w, cudaStream_t s, uint64_t** out_k,
+                         uint32_t** out_v) {
+    return radix_sort_impl<uint64_t>(k0, v0, k1, v1, n, key_bits, w, s, out_k, out_v);
+}
+
+int radix_sort_pairs_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t n,
+                         int key_bits, SortWork& w, cudaStream_t s, uint32_t** out_k,
+                         uint32_t** out_v) {
+    return radix_sort_impl<uint32_t>(k0, v0, k1, v1, n, key_bits, w, s, out_k, out_v);
+}
+
+int tie_compact(const uint8_t* eq, uint32_t n, uint32_t* out_idx, uint32_t* out_grp,
+                uint32_t* h_count, uint32_t* h_groups, SortWork& w, cudaStream_t s) {
+    *h_count = 0;
+    if (h_groups) *h_groups = 0;
+    if (n == 0) return LCP_OK;
+    uint32_t nb = (n + kCmpBlock - 1) / kCmpBlock;
+    LCP_LAUNCH(k_tie_count, nb, kCmpThreads, 0, s, eq, n, w.block_sums);
+    LCP_LAUNCH(k_scan_block_sums, 1, 1024, 0, s, w.block_sums, nb, w.total);
+    LCP_LAUNCH(k_tie_scatter, nb, kCmpThreads, 0, s, eq, n, w.block_sums, out_idx, out_grp);
+    LCP_CUDA_TRY(cudaMemcpyAsync(w.h_total + 8, w.total, sizeof(uint32_t) * 2,
+                                 cudaMemcpyDeviceToHost, s));
+    LCP_CUDA_TRY(cudaStreamSynchronize(s));
+    *h_count = w.h_total[8];
+    if (h_groups) *h_groups = w.h_total[9];
+    return LCP_OK;
+}
+
+}  // namespace lcph

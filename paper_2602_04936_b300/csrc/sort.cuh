@@ -1,0 +1,49 @@
+// Radix sort and compaction primitives used by the index build.
+#pragma once
+
+#include "common.cuh"
+
+namespace lcph {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // keys per onesweep tile
+constexpr int kMaxPasses = 8;                         // 8-bit digits of a 64-bit key
+
+// Device scratch for sorting up to `cap` pairs (allocated stream-ordered).
+struct SortWork {
+    uint32_t cap = 0;
+    uint32_t* hist = nullptr;        // [kMaxPasses][256]
+    uint32_t* digit_base = nullptr;  // [kMaxPasses][256]
+    uint32_t* skip = nullptr;        // [kMaxPasses] 1 if the digit is constant
+    uint32_t* status = nullptr;      // [kMaxPasses][tiles][256] look-back words
+    uint32_t* counters = nullptr;    // [kMaxPasses] tile tickets
+    uint64_t* block_sums = nullptr;  // compaction: per-block (active, starts) counts
+    uint32_t* total = nullptr;       // compaction result count (device)
+    uint32_t* h_total = nullptr;     // pinned host mirror of total + skip flags
+    int* err = nullptr;              // device status word
+};
+
+int sort_work_alloc(SortWork& w, uint32_t cap, int* err, cudaStream_t s);
+void sort_work_free(SortWork& w, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs by the low `key_bits` bits of
+// the key.  Buffers 0 hold the input; the result lands in buffers 0 or 1,
+// returned through out_k / out_v.  Digits that are equal for every key are
+// skipped (the host reads one 8-entry flag array, so the call blocks briefly).
+int radix_sort_pairs_u64(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, uint32_t n,
+                         int key_bits, SortWork& w, cudaStream_t s, uint64_t** out_k,
+                         uint32_t** out_v);
+int radix_sort_pairs_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t n,
+                         int key_bits, SortWork& w, cudaStream_t s, uint32_t** out_k,
+                         uint32_t** out_v);
+
+// Tie compaction: given eq[i] (element i equals element i-1 on the compared
+// prefix; eq[0] = 0), the "active" elements are those in a run of length >= 2.
+// Writes, for the j-th active element in order, out_idx[j] = i and
+// out_grp[j] = index of its run among the runs of length >= 2.  Returns the
+// number of active elements in *h_count (blocks the host).
+int tie_compact(const uint8_t* eq, uint32_t n, uint32_t* out_idx, uint32_t* out_grp,
+                uint32_t* h_count, uint32_t* h_groups, SortWork& w, cudaStream_t s);
+
+}  // namespace lcph

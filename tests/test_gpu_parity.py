@@ -1,0 +1,279 @@
+"""GPU parity: the CUDA paths against the CPU oracle, bit for bit.
+
+Every comparison is exact (ids and LCPs are integers; the answer is unique
+because the key (-LCP, id) is).  Inputs are seeded; the oracle never sees GPU
+output.  Small cases are compared element by element on every query; the
+full-size workloads are compared on sampled queries through the oracle and on
+every query between the indexed path and the full scan.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lcp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2602_04936_b300 as P
+    return P
+
+
+def dev(a: np.ndarray) -> torch.Tensor:
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint16:
+        a = a.view(np.int16)
+    return torch.from_numpy(a).cuda()
+
+
+def host(a: np.ndarray) -> torch.Tensor:
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint16:
+        a = a.view(np.int16)
+    return torch.from_numpy(a)
+
+
+def indexed(lcp, S, Qs, k, max_k=None):
+    idx = lcp.lcp_index_build(dev(S), max_k=max_k or max(k, 1))
+    ids, lc = lcp.lcp_topk_batch(idx, dev(Qs), k)
+    torch.cuda.synchronize()
+    assert lcp.lcp_index_sync(idx) == 0
+    out = ids.cpu().numpy(), lc.cpu().numpy()
+    idx.close()
+    return out
+
+
+def scan(lcp, S, Qs, k):
+    ids, lc = lcp.lcp_scan_topk(dev(S), dev(Qs), k)
+    torch.cuda.synchronize()
+    assert lcp.lcp_device_status() == 0
+    return ids.cpu().numpy(), lc.cpu().numpy()
+
+
+def assert_same(got, want, what):
+    gi, gl = got
+    wi, wl = want
+    if not (np.array_equal(gi, wi) and np.array_equal(gl, wl)):
+        bad = np.nonzero((gi != wi).any(1) | (gl != wl).any(1))[0]
+        r = bad[0]
+        raise AssertionError("%s: %d/%d queries differ; first q=%d\n got ids %s lcp %s\nwant ids %s lcp %s"
+                             % (what, len(bad), len(gi), r, gi[r][:16], gl[r][:16], wi[r][:16],
+                                wl[r][:16]))
+
+
+def _prefixy(rng, N, L, sigma, dt, share=4):
+    if N == 0:
+        return np.zeros((0, L), dt)
+    base = rng.integers(0, sigma, size=(max(N // share, 1), L))
+    rows = base[rng.integers(0, base.shape[0], N)].copy()
+    cut = rng.integers(0, L + 1, N)
+    for i in range(N):
+        rows[i, cut[i]:] = rng.integers(0, sigma, L - cut[i])
+    return rows.astype(dt)
+
+
+def _queries(rng, S, Q, sigma, dt):
+    N, L = S.shape
+    out = rng.integers(0, sigma, size=(Q, L)).astype(dt)
+    if N:
+        src = S[rng.integers(0, N, Q)]
+        cut = rng.integers(0, L + 1, Q)
+        for i in range(Q):
+            if i % 2 == 0:
+                out[i, :cut[i]] = src[i, :cut[i]]
+    if Q > 2:
+        out[0] = 0  # below every row
+        out[1] = np.iinfo(dt).max  # above every row
+    return out
+
+
+CASES = [
+    # N, L, token_bytes, sigma, k
+    (1, 4, 1, 3, 1),
+    (2, 4, 1, 3, 5),
+    (37, 3, 1, 2, 10),
+    (100, 7, 1, 4, 32),
+    (129, 5, 2, 6, 128),
+    (1000, 16, 1, 16, 10),
+    (1000, 9, 2, 3, 100),
+    (4097, 12, 2, 5, 64),
+    (5000, 33, 2, 4, 100),
+    (20000, 8, 1, 2, 128),   # tiny alphabet: enormous tie levels
+    (3000, 255, 1, 2, 17),   # L = 255, uint8
+    (700, 255, 2, 3, 40),    # L = 255, uint16 (64 packed words)
+]
+
+
+@pytest.mark.parametrize("N,L,tb,sigma,k", CASES)
+def test_small_cases_indexed_and_scan_match_oracle(lcp, N, L, tb, sigma, k):
+    rng = np.random.default_rng(N * 31 + L * 7 + tb)
+    dt = np.uint8 if tb == 1 else np.uint16
+    S = _prefixy(rng, N, L, sigma, dt)
+    Qs = _queries(rng, S, 300, sigma, dt)
+    want = oracle.topk_batch(S, Qs, k)
+    assert_same(indexed(lcp, S, Qs, k), want, "indexed")
+    assert_same(scan(lcp, S, Qs, k), want, "scan")
+
+
+@pytest.mark.parametrize("N,L,tb,sigma", [(1, 3, 1, 2), (500, 4, 1, 3), (10000, 16, 1, 16),
+                                          (50000, 32, 2, 7), (3000, 255, 2, 2), (70000, 5, 1, 2)])
+def test_sorted_index_matches_oracle(lcp, N, L, tb, sigma):
+    rng = np.random.default_rng(N + L)
+    dt = np.uint8 if tb == 1 else np.uint16
+    S = _prefixy(rng, N, L, sigma, dt)
+    idx = lcp.lcp_index_build(dev(S), max_k=8)
+    ids, H = lcp.lcp_index_export(idx)
+    torch.cuda.synchronize()
+    assert lcp.lcp_index_sync(idx) == 0
+    w_ids, w_H = oracle.sorted_index(S)
+    assert np.array_equal(ids.cpu().numpy(), w_ids)
+    assert np.array_equal(H.cpu().numpy(), w_H)
+
+
+def test_edge_cases(lcp):
+    # empty dataset: all padding
+    S = np.zeros((0, 6), np.uint8)
+    Qs = np.ones((5, 6), np.uint8)
+    for got in (indexed(lcp, S, Qs, 4), scan(lcp, S, Qs, 4)):
+        assert (got[0] == -1).all() and (got[1] == 0).all()
+    # all identical rows, queries equal / off in the last token / off in the first
+    S = np.full((3000, 10), 7, np.uint16)
+    Qs = np.full((3, 10), 7, np.uint16)
+    Qs[1, -1] = 8
+    Qs[2, 0] = 6
+    for k in (1, 50, 128):
+        want = oracle.topk_batch(S, Qs, k)
+        assert_same(indexed(lcp, S, Qs, k), want, "indexed identical rows")
+        assert_same(scan(lcp, S, Qs, k), want, "scan identical rows")
+    # rows differing only in the last token; token values at the top of the range
+    S = np.tile(np.array([[0xFFFF] * 6], np.uint16), (300, 1))
+    S[:, -1] = np.arange(300, dtype=np.uint16)[::-1] * 200
+    Qs = S[::7].copy()
+    want = oracle.topk_batch(S, Qs, 20)
+    assert_same(indexed(lcp, S, Qs, 20), want, "indexed last-token")
+    assert_same(scan(lcp, S, Qs, 20), want, "scan last-token")
+    # k larger than N
+    rng = np.random.default_rng(1)
+    S = rng.integers(0, 3, size=(9, 5)).astype(np.uint8)
+    Qs = rng.integers(0, 3, size=(40, 5)).astype(np.uint8)
+    want = oracle.topk_batch(S, Qs, 30)
+    assert_same(indexed(lcp, S, Qs, 30), want, "indexed k>N")
+    assert_same(scan(lcp, S, Qs, 30), want, "scan k>N")
+
+
+def test_tree16_u8_full(lcp):
+    """The small prefix-tree workload in full: every query, both paths."""
+    S, Qs, k = W.make_dataset("tree16_u8")
+    want = oracle.topk_batch(S, Qs, k)
+    assert_same(indexed(lcp, S, Qs, k), want, "indexed tree16")
+    assert_same(scan(lcp, S, Qs, k), want, "scan tree16")
+
+
+def _sampled(lcp, name, n_oracle):
+    S, Qs, k = W.make_dataset(name)
+    idx = lcp.lcp_index_build(dev(S), max_k=k)
+    dq = dev(Qs)
+    ids, lc = lcp.lcp_topk_batch(idx, dq, k)
+    sids, slc = lcp.lcp_scan_topk(dev(S), dq, k)
+    torch.cuda.synchronize()
+    assert lcp.lcp_index_sync(idx) == 0 and lcp.lcp_device_status() == 0
+    got = ids.cpu().numpy(), lc.cpu().numpy()
+    sgot = sids.cpu().numpy(), slc.cpu().numpy()
+    assert_same(got, sgot, name + " indexed vs scan (all queries)")
+    rng = np.random.default_rng(99)
+    pick = np.sort(rng.choice(len(Qs), n_oracle, replace=False))
+    want = oracle.topk_batch(S, Qs[pick], k)
+    assert_same((got[0][pick], got[1][pick]), want, name + " indexed vs oracle (sample)")
+    idx.close()
+
+
+def test_zipf500k_L32_full_size(lcp):
+    _sampled(lcp, "zipf500k_L32", 2000)
+
+
+def test_zipf2m_L64_full_size(lcp):
+    _sampled(lcp, "zipf2m_L64", 300)
+
+
+def test_insert_equals_rebuild_and_answers(lcp):
+    """GNC stream: merge-insert 1,000 readings per step into an index that
+    grows from empty; after every step the sorted order and H equal a fresh
+    build of everything inserted, and the step's queries match the oracle."""
+    g = W.GncStream(sensors=1000, seed=5)
+    idx = lcp.lcp_index_build(torch.zeros((0, 8), dtype=torch.int16, device="cuda"), max_k=5,
+                              capacity=40_000)
+    allrows = []
+    for t in range(30):
+        r = g.step()
+        allrows.append(r)
+        lcp.lcp_index_insert(idx, dev(r))
+        S = np.concatenate(allrows)
+        if t < 5 or t % 10 == 9:
+            ids, H = lcp.lcp_index_export(idx)
+            w_ids, w_H = oracle.sorted_index(S)
+            assert np.array_equal(ids.cpu().numpy(), w_ids), t
+            assert np.array_equal(H.cpu().numpy(), w_H), t
+            got = lcp.lcp_topk_batch(idx, dev(r), 5)
+            want = oracle.topk_batch(S, r, 5)
+            assert_same((got[0].cpu().numpy(), got[1].cpu().numpy()), want, "gnc step %d" % t)
+    assert lcp.lcp_index_sync(idx) == 0
+    # a large batch (radix path) and the capacity limit
+    big = np.concatenate([g.step() for _ in range(3)])
+    lcp.lcp_index_insert(idx, dev(big))
+    S = np.concatenate(allrows + [big])
+    ids, H = lcp.lcp_index_export(idx)
+    w_ids, w_H = oracle.sorted_index(S)
+    assert np.array_equal(ids.cpu().numpy(), w_ids) and np.array_equal(H.cpu().numpy(), w_H)
+    with pytest.raises(lcp.LcpError) as e:
+        lcp.lcp_index_insert(idx, dev(np.zeros((40_000, 8), np.uint16)))
+    assert e.value.code == lcp.LCP_ERR_CAPACITY
+    idx.close()
+
+
+def test_determinism_alone_vs_batch_and_repeat(lcp):
+    S, Qs, k = W.make_dataset("zipf500k_L32", N=100_000, Q=5_000)
+    idx = lcp.lcp_index_build(dev(S), max_k=32)
+    dq = dev(Qs)
+    a = lcp.lcp_topk_batch(idx, dq, 32)
+    b = lcp.lcp_topk_batch(idx, dq, 32)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    for i in (0, 17, 4999):
+        one = lcp.lcp_topk_batch(idx, dq[i:i + 1].contiguous(), 32)
+        assert torch.equal(one[0][0], a[0][i]) and torch.equal(one[1][0], a[1][i])
+    # rebuilding gives the identical index
+    idx2 = lcp.lcp_index_build(dev(S), max_k=32)
+    e1, e2 = lcp.lcp_index_export(idx), lcp.lcp_index_export(idx2)
+    assert torch.equal(e1[0], e2[0]) and torch.equal(e1[1], e2[1])
+    idx.close()
+    idx2.close()
+
+
+def test_host_entry_points_match_device(lcp):
+    S, Qs, k = W.make_dataset("tree16_u8", N=3000, Q=500)
+    idx = lcp.lcp_index_build_host(host(S), max_k=k)
+    hi, hl = lcp.lcp_topk_batch_host(idx, host(Qs), k)
+    want = oracle.topk_batch(S, Qs, k)
+    assert_same((hi.numpy(), hl.numpy()), want, "host entry points")
+    idx.close()
+
+
+def test_argument_errors(lcp):
+    S = np.zeros((10, 4), np.uint8)
+    idx = lcp.lcp_index_build(dev(S), max_k=8)
+    with pytest.raises(lcp.LcpError) as e:
+        lcp.lcp_topk_batch(idx, dev(S), 9)
+    assert e.value.code == lcp.LCP_ERR_INVALID
+    with pytest.raises(lcp.LcpError):
+        lcp.lcp_index_insert(idx, dev(S))  # built without spare capacity
+    idx.close()
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(lcp):
+    assert lcp.lcp_debug_bounded_wait(1 << 14) == lcp.LCP_ERR_TIMEOUT
+    S, Qs, k = W.make_dataset("tree16_u8", N=500, Q=50)
+    assert_same(indexed(lcp, S, Qs, k), oracle.topk_batch(S, Qs, k), "after timeout")

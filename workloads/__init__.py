@@ -29,7 +29,10 @@ Workloads (the paper's own inputs are synthetic; these follow its shapes):
 """
 from __future__ import annotations
 
+import ctypes
 import math
+import os
+import subprocess
 
 import numpy as np
 
@@ -63,6 +66,11 @@ def rand_u64(seed: int, stream: int, a, b=0):
     key = splitmix64(splitmix64(_U64(seed & 0xFFFFFFFFFFFFFFFF)) ^ _U64(stream))
     with np.errstate(over="ignore"):
         return splitmix64(splitmix64(key + a) ^ (b * _U64(0xD6E8FEB86659FD93)))
+
+
+def stream_key(seed: int, stream: int) -> int:
+    """The 64-bit key of (seed, stream) used by rand_u64."""
+    return int(splitmix64(splitmix64(_U64(seed & 0xFFFFFFFFFFFFFFFF)) ^ _U64(stream)))
 
 
 def rand_uniform(seed: int, stream: int, a, b=0):
@@ -103,15 +111,61 @@ def _perm_token(h, r0, V: int):
 
 
 # --------------------------------------------------------------------------
+# C fast path (workloads/gen.c): the same draws, bit for bit
+# --------------------------------------------------------------------------
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_GEN_SO = os.path.join(_HERE, "libgen.so")
+_gen = None
+
+
+def build_gen(force: bool = False) -> str:
+    src = os.path.join(_HERE, "gen.c")
+    if force or not os.path.exists(_GEN_SO) or os.path.getmtime(_GEN_SO) < os.path.getmtime(src):
+        tmp = _GEN_SO + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", tmp,
+                               src])
+        os.replace(tmp, _GEN_SO)
+    return _GEN_SO
+
+
+def _gen_lib():
+    global _gen
+    if _gen is None:
+        lib = ctypes.CDLL(build_gen())
+        vp, i64, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64
+        lib.gen_zipf_prefix.argtypes = [vp, i64, i64, i64, vp, u64, u64, i64, vp, vp, vp,
+                                        ctypes.c_int]
+        lib.gen_zipf_prefix.restype = None
+        _gen = lib
+    return _gen
+
+
+def _c_zipf(n, L, V, cdf, key, h0, item_offset, S=None, src=None, cut=None):
+    out = np.empty((n, L), np.uint16)
+    cdf = np.ascontiguousarray(cdf, np.float64)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+    if S is not None:
+        S = np.ascontiguousarray(S, np.uint16)
+        src = np.ascontiguousarray(src, np.int64)
+        cut = np.ascontiguousarray(cut, np.int64)
+    _gen_lib().gen_zipf_prefix(p(out), n, L, V, p(cdf), key, int(h0), item_offset, p(S), p(src),
+                               p(cut), min(os.cpu_count() or 1, 64))
+    return out
+
+
+# --------------------------------------------------------------------------
 # stored sequences
 # --------------------------------------------------------------------------
 
 def zipf_prefix_rows(N: int, L: int, V: int, s: float, seed: int, stream: int = STREAM_ROWS,
-                     item_offset: int = 0) -> np.ndarray:
+                     item_offset: int = 0, impl: str = "c") -> np.ndarray:
     """N rows of L uint16 tokens, Zipf(s) per position, prefix-conditioned."""
     if V & (V - 1) or V > 65536:
         raise ValueError("V must be a power of two <= 65536")
     z = Zipf(V, s)
+    if impl == "c":
+        return _c_zipf(N, L, V, z.cdf, stream_key(seed, stream), _prefix_root(seed), item_offset)
     out = np.empty((N, L), np.uint16)
     items = np.arange(item_offset, item_offset + N, dtype=np.uint64)
     h = np.full(N, _prefix_root(seed), _U64)
@@ -160,11 +214,15 @@ def _mix_plan(Q: int, N: int, L: int, seed: int, item_offset: int = 0):
 
 
 def zipf_prefix_queries(S: np.ndarray, Q: int, V: int, s: float, seed: int,
-                        item_offset: int = 0) -> np.ndarray:
+                        item_offset: int = 0, impl: str = "c") -> np.ndarray:
     """Query mix over a zipf_prefix dataset S (see module docstring)."""
     N, L = S.shape
     z = Zipf(V, s)
     items, is_copy, src, cut = _mix_plan(Q, N, L, seed, item_offset)
+    if impl == "c":
+        Sx = S if N > 0 else np.zeros((1, L), np.uint16)
+        return _c_zipf(Q, L, V, z.cdf, stream_key(seed, STREAM_QTOK), _prefix_root(seed),
+                       item_offset, Sx, src, cut)
     out = np.empty((Q, L), np.uint16)
     h = np.full(Q, _prefix_root(seed), _U64)
     src_rows = S[src] if N > 0 else np.zeros((Q, L), np.uint16)
