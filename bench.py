@@ -1,0 +1,475 @@
+#!/usr/bin/env python3
+"""Benchmark: top-k LCP queries/s and p99 latency, indexed vs full scan, on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (default): N = 2,000,000 stored sequences, L = 64 uint16 tokens,
+vocabulary 32,768, Zipf(1.05) prefix-conditioned, 1,000,000 queries (half
+copies of stored rows with a re-drawn suffix, half fresh draws), k = 100.
+
+One step = one pass of the indexed hot path over the batch: build the prefix
+index from the resident token rows (pack, radix sort, gather + adjacent LCP,
+tie tables) and answer all Q queries (search, expansion, tie fill, output).
+`value` = Q / step time.  Beside it, in the same run and under the same
+timing rules: the full scan of the same Q queries (the comparison path),
+per-batch p50/p99 latency of both paths, and the insert-then-query stream
+(1,000 sensors, 1,000 steps, index growing to 1,000,000 rows).
+
+Timing: CUDA events on the launching stream, synchronize + barrier on both
+sides, max over ranks; inputs (256 MB tokens, 128 MB queries) are larger
+than the 126 MB L2.  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "top-k LCP queries/s & p99 latency, indexed vs full-scan on 1 B300, bit-exact"
+UNIT = "queries/s"
+WORKLOAD = "zipf2m_L64"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--queries", type=int, default=0, help="override Q (profiling cases)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip latency / insert / e2e / cpu legs (profiling runs)")
+    return ap.parse_args()
+
+
+def config_of(name):
+    w = W.WORKLOADS[name]
+    return {"workload": name, "N": w["N"], "L": w["L"],
+            "token": "uint8" if w["token_bytes"] == 1 else "uint16", "vocab": w["vocab"],
+            "zipf_s": w.get("s"), "Q": w["Q"], "k": w["k"], "seed": w["seed"],
+            "query_mix": "50% stored copies with suffix re-drawn from a uniform cut, 50% fresh",
+            "step": "index build from resident tokens + indexed top-k of all Q queries",
+            "l2": "no flush: inputs larger than L2 (tokens %d MB, queries %d MB)" % (
+                w["N"] * w["L"] * w["token_bytes"] >> 20, w["Q"] * w["L"] * w["token_bytes"] >> 20)}
+
+
+def to_dev(a, device):
+    import torch
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint16:
+        a = a.view(np.int16)
+    return torch.from_numpy(a).to(device)
+
+
+def pinned(a):
+    import torch
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint16:
+        a = a.view(np.int16)
+    return torch.from_numpy(a).pin_memory()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+            return
+        t0 = time.time()  # wait for the sampler's first line before timing starts
+        while time.time() - t0 < 3.0 and os.path.getsize(self.path) == 0:
+            time.sleep(0.05)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+                pw.append(float(p[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "samples": len(sm),
+                "power_w_max": max(pw), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas: no collective on the data path)
+# ---------------------------------------------------------------------------
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# ---------------------------------------------------------------------------
+def oracle_rate(S, Qs, k, budget_s=12.0, max_q=4096):
+    import oracle
+    threads = os.cpu_count() or 1
+    n = max(threads, 8)
+    done, elapsed = 0, 0.0
+    while True:
+        t0 = time.perf_counter()
+        oracle.topk_batch(S, Qs[done:done + n], k, threads=threads)
+        dt = time.perf_counter() - t0
+        done += n
+        elapsed += dt
+        if elapsed >= budget_s or done + 2 * n > min(max_q, len(Qs)):
+            break
+        n *= 2
+    return done / elapsed, done, elapsed, threads
+
+
+def search_algorithmic_bytes(N, L, tb, k):
+    """Bytes one query of the indexed search must touch:
+    the query row, one 32-byte sector per binary-search level, the H bytes
+    and ids of about k items around the insertion point, and its k (id, lcp)
+    results."""
+    return L * tb + math.ceil(math.log2(max(N, 2))) * 32 + k * 5 + k * 5
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("search.cu", "index.cuh", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2602_04936_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs"), "measured"
+    return 6400.0, "fallback"
+
+
+def committed_traffic(kernel):
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel)
+    if not d or d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+# ---------------------------------------------------------------------------
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_2602_04936_b300 as lcp
+
+    device = torch.device("cuda", local)
+    cfg = config_of(args.workload)
+    w = W.WORKLOADS[args.workload]
+    N, L, tb, Q, k = w["N"], w["L"], w["token_bytes"], w["Q"], w["k"]
+    if args.queries:
+        Q = args.queries
+        cfg["Q"] = Q
+    S = W.zipf_prefix_rows(N, L, w["vocab"], w["s"], w["seed"])
+    # weak scaling: every rank answers its own query batch against a full replica
+    Qs = W.zipf_prefix_queries(S, Q, w["vocab"], w["s"], w["seed"], item_offset=rank * Q)
+    dS, dQ = to_dev(S, device), to_dev(Qs, device)
+    out_ids = torch.empty((Q, k), dtype=torch.int32, device=device)
+    out_lcp = torch.empty((Q, k), dtype=torch.uint8, device=device)
+    stream = torch.cuda.current_stream(device)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        idx = lcp.lcp_index_build(dS, max_k=k)
+        if ev is not None:
+            ev[1].record(stream)
+        lcp.lcp_topk_batch(idx, dQ, k, out_ids, out_lcp)
+        if ev is not None:
+            ev[2].record(stream)
+        idx.close()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    rc = lcp.lcp_device_status()
+    if rc:
+        raise RuntimeError("device status after warm-up: %s" % lcp.lcp_status_string(rc))
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(local)
+    clk.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = lcp.lcp_launch_count()
+    t_start.record(stream)
+    for i in range(args.steps):
+        step(evs[i])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    launches = lcp.lcp_launch_count() - launches0
+    barrier(world)
+    clocks = clk.stop()
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), world)
+    ms_step = total_ms / args.steps
+    value = world * Q / (ms_step / 1e3)
+    build_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+    query_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+
+    # roofline of the dominant kernel: the indexed search (one launch per call)
+    peak, peak_kind = measured_peaks()
+    per_q = search_algorithmic_bytes(N, L, tb, k)
+    achieved = Q * per_q / (query_ms / 1e3) / 1e9
+    traffic = committed_traffic("k_topk_search")
+    roofline = {"kernel": "k_topk_search", "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.4 TB/s",
+                "traffic": traffic, "algorithmic_bytes_per_launch": Q * per_q,
+                "bytes_per_query": per_q, "launch_ms": round(query_ms, 4)}
+
+    paths = {"indexed": {"build_ms": round(build_ms, 3), "query_ms": round(query_ms, 3),
+                         "qps_query_only": round(Q / (query_ms / 1e3), 1),
+                         "build_rows_per_s": round(N / (build_ms / 1e3), 1)}}
+    line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
+            "data": "synthetic", "config": dict(cfg, parallelism="replicas x%d (queries sharded)" % world),
+            "gpu_launches": int(launches), "roofline": roofline, "clocks": clocks, "paths": paths}
+
+    if not args.no_extras:
+        # full scan of the same batch (comparison path)
+        reps = 2
+        sc = []
+        for r in range(reps + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            sids, slc = lcp.lcp_scan_topk(dS, dQ, k)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if r:
+                sc.append(a.elapsed_time(b))
+            if a.elapsed_time(b) > 20_000:
+                break
+        scan_ms = float(np.mean(sc)) if sc else float(a.elapsed_time(b))
+        # the two paths agree on every query
+        idx = lcp.lcp_index_build(dS, max_k=k)
+        lcp.lcp_topk_batch(idx, dQ, k, out_ids, out_lcp)
+        torch.cuda.synchronize()
+        same = bool(torch.equal(out_ids, sids) and torch.equal(out_lcp, slc))
+        paths["full_scan"] = {"ms": round(scan_ms, 3), "qps": round(Q / (scan_ms / 1e3), 1),
+                              "identical_to_indexed": same}
+        paths["indexed_vs_full_scan_speedup_query_only"] = round(scan_ms / query_ms, 1)
+        # per-batch latency (CUDA events around each call)
+        lat = {"indexed": {}, "full_scan": {}}
+        for bs, ri, rs in ((1, 1000, 100), (32, 1000, 50), (1024, 200, 10), (32768, 50, 3)):
+            for name, reps_, fn in (("indexed", ri, lambda q: lcp.lcp_topk_batch(idx, q, k)),
+                                    ("full_scan", rs, lambda q: lcp.lcp_scan_topk(dS, q, k))):
+                times = []
+                for r in range(reps_ + 2):
+                    off = (r * 7919 * bs) % (Q - bs)
+                    q = dQ[off:off + bs]
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    fn(q)
+                    b.record(stream)
+                    b.synchronize()
+                    if r >= 2:
+                        times.append(a.elapsed_time(b))
+                lat[name][str(bs)] = {"p50": round(float(np.percentile(times, 50)), 4),
+                                      "p99": round(float(np.percentile(times, 99)), 4),
+                                      "reps": len(times)}
+        paths["latency_ms"] = lat
+        idx.close()
+        del sids, slc
+        # insert-then-query stream (1,000 sensors x 1,000 steps)
+        g = W.GncStream(sensors=1000, seed=5)
+        steps = [g.step() for _ in range(1000)]
+        dsteps = to_dev(np.stack(steps), device)
+        gi = lcp.lcp_index_build(torch.zeros((0, 8), dtype=torch.int16, device=device), max_k=5,
+                                 capacity=1_000_000)
+        gids = torch.empty((1000, 5), dtype=torch.int32, device=device)
+        glcp = torch.empty((1000, 5), dtype=torch.uint8, device=device)
+        gev = [torch.cuda.Event(enable_timing=True) for _ in range(1001)]
+        torch.cuda.synchronize()
+        gev[0].record(stream)
+        for t in range(1000):
+            lcp.lcp_index_insert(gi, dsteps[t])
+            lcp.lcp_topk_batch(gi, dsteps[t], 5, gids, glcp)
+            gev[t + 1].record(stream)
+        torch.cuda.synchronize()
+        st = np.array([gev[t].elapsed_time(gev[t + 1]) for t in range(1000)])
+        paths["insert_gnc"] = {"steps": 1000, "final_N": gi.N, "steps_per_s": round(1e3 / st.mean(), 1),
+                               "p50_ms": round(float(np.percentile(st, 50)), 4),
+                               "p99_ms": round(float(np.percentile(st, 99)), 4),
+                               "last_step_ms": round(float(st[-1]), 4)}
+        gi.close()
+        del dsteps
+        # end to end through the host-buffer ABI (copies inside the timed region)
+        hS, hQ = pinned(S), pinned(Qs)
+        hid = torch.empty((Q, k), dtype=torch.int32).pin_memory()
+        hlc = torch.empty((Q, k), dtype=torch.uint8).pin_memory()
+
+        def e2e_step():
+            ix = lcp.lcp_index_build_host(hS, max_k=k, device=device)
+            lcp.lcp_topk_batch_host(ix, hQ, k, hid, hlc)
+            ix.close()
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world) / args.steps
+        line["e2e"] = {"value": round(world * Q / e2e_s, 1), "unit": UNIT,
+                       "ms_per_step": round(e2e_s * 1e3, 3),
+                       "h2d_bytes_per_step": int(S.nbytes + Qs.nbytes),
+                       "d2h_bytes_per_step": int(Q * k * 5),
+                       "api": "lcp_index_build_host + lcp_topk_batch_host"}
+        # CPU oracle on the host cores (rank 0 only)
+        if rank == 0:
+            qps, n, el, thr = oracle_rate(S, Qs, k)
+            line["cpu_baseline"] = {"value": round(qps, 2), "unit": UNIT, "cores": thr, "kind": "oracle",
+                                    "sample": "first %d queries of the batch against all %d rows "
+                                              "(%.1f s)" % (n, N, el)}
+    return line
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle, as it stands, on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    import oracle
+    cfg = config_of(args.workload)
+    w = W.WORKLOADS[args.workload]
+    N, L, Q, k = w["N"], w["L"], w["Q"], w["k"]
+    S = W.zipf_prefix_rows(N, L, w["vocab"], w["s"], w["seed"])
+    Qs = W.zipf_prefix_queries(S, Q, w["vocab"], w["s"], w["seed"])
+    threads = os.cpu_count() or 1
+    # calibrate the per-step sample so that warmup + steps take ~2 minutes
+    t0 = time.perf_counter()
+    oracle.topk_batch(S, Qs[:threads], k, threads=threads)
+    per_q = (time.perf_counter() - t0) / threads
+    budget = 120.0 / max(args.steps + args.warmup, 1)
+    n = int(max(threads, min(20000, budget / max(per_q, 1e-6))))
+    off = 0
+    for _ in range(args.warmup):
+        oracle.topk_batch(S, Qs[off:off + n], k, threads=threads)
+        off = (off + n) % (Q - n)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.topk_batch(S, Qs[off:off + n], k, threads=threads)
+        off = (off + n) % (Q - n)
+    el = time.perf_counter() - t0
+    value = n * args.steps / el
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+            "config": cfg,
+            "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "%d queries per step against all %d rows" % (n, N)},
+            "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        line = run_reference(args, world, rank)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    world, rank, local = dist_setup(args)
+    line = run_ours(args, world, rank, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
