@@ -195,8 +195,7 @@ def oracle_rate(S, Qs, k, budget_s=12.0, max_q=4096):
 
 
 def search_algorithmic_bytes(N, L, tb, k):
-    """Bytes one query of the indexed search must touch:
-    the query row, one 32-byte sector per binary-search level, the H bytes
+    """Bytes one query of the indexed search must touch: the query row, one 32-byte sector per binary-search level, the H bytes
     and ids of about k items around the insertion point, and its k (id, lcp)
     results."""
     return L * tb + math.ceil(math.log2(max(N, 2))) * 32 + k * 5 + k * 5
