@@ -154,6 +154,29 @@ LCP_API int lcp_scan_topk(const void* d_tokens, int64_t N, lcp_format_t fmt, con
                   lcp_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Full scan top-k without any device allocation.  The paper has no
+ * counterpart; this is a deployment variant of lcp_scan_topk for callers that
+ * cannot allocate device memory when they call in (a real-time control loop
+ * that must not block in the allocator, code restricted to start-up
+ * allocation, host code inside a stream capture in global mode).  Same
+ * arguments and results as lcp_scan_topk.
+ *
+ * Scratch: a fixed array of LCP_SCAN_NOALLOC_SCRATCH_BYTES inside the
+ * library's device image, held by every GPU that loads the library until the
+ * process exits.  A call needs round_up(N * 8, 256) + Q * k * 8 bytes of it;
+ * larger requests return LCP_ERR_INVALID without enqueuing anything (split
+ * the query batch).  The call allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) -- make that first call
+ * before any stream capture.  Every call shares the one array: calls that
+ * overlap on the GPU race, so order them (one stream, or events).
+ * ---------------------------------------------------------------------- */
+#define LCP_SCAN_NOALLOC_SCRATCH_BYTES (32u << 20)
+LCP_API int lcp_scan_topk_noalloc(const void* d_tokens, int64_t N, lcp_format_t fmt,
+                                  const void* d_queries, int64_t Q, int32_t k, int32_t* d_out_ids,
+                                  uint8_t* d_out_lcp, lcp_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Index inspection and lifetime.
  * ---------------------------------------------------------------------- */
 /* Current item count and device bytes held (both may be NULL). Synchronous,

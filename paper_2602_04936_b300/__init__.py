@@ -45,7 +45,7 @@ ABI_SYMBOLS = (
     "lcp_status_string", "lcp_index_build", "lcp_index_build_host", "lcp_index_insert",
     "lcp_topk_batch", "lcp_topk_batch_host", "lcp_scan_topk", "lcp_index_size",
     "lcp_index_export", "lcp_index_sync", "lcp_index_destroy", "lcp_device_status",
-    "lcp_launch_count", "lcp_debug_bounded_wait",
+    "lcp_launch_count", "lcp_debug_bounded_wait", "lcp_scan_topk_noalloc",
 )
 
 
@@ -60,11 +60,11 @@ class _Format(ctypes.Structure):
 
 
 def _load():
-    if not os.path.exists(_SO):
-        try:
-            from . import build as _b
-            _b.build()
-        except Exception as e:  # no CPU fallback: fail loudly
+    try:  # (re)build when a source is newer than liblcp.so; a no-op otherwise
+        from . import build as _b
+        _b.build()
+    except Exception as e:
+        if not os.path.exists(_SO):  # no CPU fallback: fail loudly
             raise ImportError("liblcp.so is missing and could not be built: %s" % e) from e
     lib = ctypes.CDLL(_SO)
     vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
@@ -83,6 +83,7 @@ def _load():
         "lcp_device_status": ([], ctypes.c_int),
         "lcp_launch_count": ([], i64),
         "lcp_debug_bounded_wait": ([i64, vp], ctypes.c_int),
+        "lcp_scan_topk_noalloc": ([vp, i64, _Format, vp, i64, i32, vp, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -255,6 +256,21 @@ def lcp_scan_topk(tokens: torch.Tensor, queries: torch.Tensor, k: int, out_ids=N
     with torch.cuda.device(queries.device):
         _check(_lib.lcp_scan_topk(_ptr(tokens), tokens.shape[0], _fmt(tokens, vocab), _ptr(queries), Q,
                                   k, _ptr(out_ids), _ptr(out_lcp), _stream(stream)), "lcp_scan_topk")
+    return out_ids, out_lcp
+
+
+def lcp_scan_topk_noalloc(tokens: torch.Tensor, queries: torch.Tensor, k: int, out_ids, out_lcp,
+                          stream=None, vocab: int = 0):
+    """Full scan into caller-provided outputs, using only the library's fixed
+    device scratch (no allocation in the library call; see include/lcp.h)."""
+    tokens = _rows(tokens, device=True)
+    queries = _rows(queries, device=True)
+    Q = queries.shape[0]
+    out_ids, out_lcp = _outputs(Q, k, queries.device, out_ids, out_lcp)
+    with torch.cuda.device(queries.device):
+        _check(_lib.lcp_scan_topk_noalloc(_ptr(tokens), tokens.shape[0], _fmt(tokens, vocab),
+                                          _ptr(queries), Q, k, _ptr(out_ids), _ptr(out_lcp),
+                                          _stream(stream)), "lcp_scan_topk_noalloc")
     return out_ids, out_lcp
 
 

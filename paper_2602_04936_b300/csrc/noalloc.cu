@@ -1,0 +1,111 @@
+// Full scan top-k that allocates nothing.
+//
+// Some callers cannot allocate device memory when they call in: a real-time
+// control loop (the paper's guidance/navigation example) must not block in
+// the allocator, whose calls can synchronise the device and have no latency
+// bound; code written to rules that allow allocation only at start-up; and
+// host code issuing work inside a stream capture in global mode, where
+// cudaMalloc is not permitted.  lcp_scan_topk takes its temporaries from the
+// stream-ordered allocator; this entry point instead runs the same kernels on
+// a fixed scratch array that lives in the library's device image.
+//
+// The array is a file-scope __device__ variable, so every GPU that loads the
+// library holds it (LCP_SCAN_NOALLOC_SCRATCH_BYTES) until the process exits.
+// Host code cannot use its name as a device address; the address is looked
+// up once per device with cudaGetSymbolAddress on the first call made on
+// that device.
+#include <mutex>
+
+#include "scan.cuh"
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_scan_scratch[LCP_SCAN_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMergeCapNA = 4096;  // keys one merge CTA sorts (as in scan.cu)
+constexpr int kThreadsNA = 128;    // threads of k_scan_partial (its launch bound)
+
+struct ScratchSlot {
+    std::once_flag once;
+    void* ptr = nullptr;
+    cudaError_t err = cudaSuccess;
+};
+ScratchSlot g_slots[64];
+
+// Device address of g_scan_scratch on the current device (set-up on the first
+// call per device).
+cudaError_t scratch_address(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    ScratchSlot& s = g_slots[dev];
+    std::call_once(s.once, [&s]() { s.err = cudaGetSymbolAddress(&s.ptr, g_scan_scratch); });
+    *out = s.ptr;
+    return s.err;
+}
+
+}  // namespace
+
+extern "C" int lcp_scan_topk_noalloc(const void* d_tokens, int64_t N, lcp_format_t fmt,
+                                     const void* d_queries, int64_t Q, int32_t k, int32_t* d_out_ids,
+                                     uint8_t* d_out_lcp, lcp_stream_t stream) {
+    using namespace lcpk;
+    if ((fmt.token_bytes != 1 && fmt.token_bytes != 2) || fmt.L < 1 || fmt.L > LCP_MAX_L || N < 0 ||
+        N >= (1ll << 30) || Q < 0 || k < 1 || k > LCP_SCAN_MAX_K)
+        return LCP_ERR_INVALID;
+    if (Q > 0 && (!d_queries || !d_out_ids || !d_out_lcp)) return LCP_ERR_INVALID;
+    if (N > 0 && Q > 0 && !d_tokens) return LCP_ERR_INVALID;
+    if (Q == 0) return LCP_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (N == 0) {
+        LCP_CUDA_TRY(cudaMemsetAsync(d_out_ids, 0xFF, sizeof(int32_t) * (size_t)Q * k, s));
+        LCP_CUDA_TRY(cudaMemsetAsync(d_out_lcp, 0, (size_t)Q * k, s));
+        return LCP_OK;
+    }
+    // Scratch layout: [plane 0: N words][heaps: S lists x Q x k keys].  One
+    // merge pass reads the heaps and writes the outputs, so S is capped at the
+    // number of lists one merge CTA can sort.
+    int kp2 = 1;
+    while (kp2 < k) kp2 <<= 1;
+    const int64_t G = kMergeCapNA / kp2 > 0 ? kMergeCapNA / kp2 : 1;
+    const uint64_t cap = (uint64_t)LCP_SCAN_NOALLOC_SCRATCH_BYTES;
+    const uint64_t plane_bytes = ((uint64_t)N * 8 + 255) & ~255ull;
+    const uint64_t list_bytes = (uint64_t)Q * (uint64_t)k * 8;
+    if (plane_bytes + list_bytes > cap) return LCP_ERR_INVALID;  // too large even with one slice
+    const int64_t qtiles = (Q + kThreadsNA - 1) / kThreadsNA;
+    int64_t S = (148 * 8 + qtiles - 1) / qtiles;
+    int64_t maxS = (N + 1023) / 1024;
+    int64_t fitS = (int64_t)((cap - plane_bytes) / list_bytes);
+    if (S > maxS) S = maxS;
+    if (S > G) S = G;
+    if (S > fitS) S = fitS;
+    if (S < 1) S = 1;
+    const int64_t slice = (N + S - 1) / S;
+    S = (N + slice - 1) / slice;
+
+    void* base = nullptr;
+    LCP_CUDA_TRY(scratch_address(&base));
+    uint64_t* plane0 = reinterpret_cast<uint64_t*>(base);
+    uint64_t* heaps = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(base) + plane_bytes);
+    // Nothing in the scratch needs to start at zero: plane 0 is written in
+    // full by the pack kernel and every heap slot is written by the scan
+    // kernel before the merge reads it.  Calls that overlap on the GPU share
+    // the array and race; callers must order them (one stream, or events).
+    RowFmt f = make_fmt(fmt.token_bytes, fmt.L, d_tokens);
+    RowFmt qf = make_fmt(fmt.token_bytes, fmt.L, d_queries);
+    LCP_LAUNCH(k_pack_plane0, (unsigned)((N + 255) / 256), 256, 0, s,
+               reinterpret_cast<const uint8_t*>(d_tokens), f, N, plane0);
+    dim3 grid((unsigned)qtiles, (unsigned)S);
+    LCP_LAUNCH(k_scan_partial, grid, kThreadsNA, 0, s, reinterpret_cast<const uint8_t*>(d_tokens),
+               plane0, f, N, reinterpret_cast<const uint8_t*>(d_queries), qf, Q, k, slice, heaps);
+    int P = 1;
+    while (P < S * k) P <<= 1;
+    LCP_CUDA_TRY(cudaFuncSetAttribute(k_scan_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(uint64_t) * kMergeCapNA * 2)));
+    dim3 mg((unsigned)Q, 1);
+    LCP_LAUNCH(k_scan_merge, mg, 256, sizeof(uint64_t) * P, s, heaps, Q, k, (int)S, (int)S, P,
+               (uint64_t*)nullptr, 1, d_out_ids, d_out_lcp);
+    LCP_CUDA_TRY(cudaGetLastError());
+    return LCP_OK;
+}

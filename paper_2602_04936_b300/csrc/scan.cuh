@@ -1,0 +1,20 @@
+// Declarations of the full-scan kernels defined in scan.cu, for callers in
+// other translation units that supply their own scratch memory.
+#pragma once
+
+#include "common.cuh"
+
+namespace lcpk {
+
+__global__ void k_pack_plane0(const uint8_t* __restrict__ tokens, RowFmt f, int64_t n,
+                              uint64_t* __restrict__ plane0);
+
+__global__ void k_scan_partial(const uint8_t* __restrict__ tokens, const uint64_t* __restrict__ plane0,
+                               RowFmt f, int64_t N, const uint8_t* __restrict__ queries, RowFmt qf,
+                               int64_t Q, int k, int64_t slice, uint64_t* __restrict__ heaps);
+
+__global__ void k_scan_merge(const uint64_t* __restrict__ in, int64_t Q, int k, int nlists, int G,
+                             int P, uint64_t* __restrict__ out, int final_pass,
+                             int32_t* __restrict__ out_ids, uint8_t* __restrict__ out_lcp);
+
+}  // namespace lcpk
