@@ -62,7 +62,9 @@ static void retain_pool_memory() {
 static void free_index_memory(lcp_index_s* x, cudaStream_t s) {
     void* ptrs[] = {x->buf[0].rows, x->buf[0].head, x->buf[0].ids, x->buf[0].H,
                     x->buf[1].rows, x->buf[1].head, x->buf[1].ids, x->buf[1].H,
-                    x->pos, x->hmin, x->sblk, x->soff, x->st, x->status,
+                    x->pos, x->hmin, x->sblk, x->soff, x->st, x->bkt, x->status,
+                    x->tbl, x->slot_flag, x->slot_lo, x->slot_hi, x->slot_list, x->tlists,
+                    x->tl_lo, x->tl_hi, x->tl_sums, x->tl_total,
                     x->ins_rows, x->ins_ids, x->ins_rank};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, s);
@@ -103,6 +105,22 @@ static int alloc_index(lcp_index_s* x, int64_t N, int64_t cap, cudaStream_t s) {
     while ((1ll << (lev + 1)) <= x->nblk_cap) ++lev;
     x->st_levels_cap = lev;
     if ((rc = dalloc(&x->st, (size_t)(lev > 0 ? lev : 1) * x->nblk_cap * x->K, &by, s))) return rc;
+    if ((rc = dalloc(&x->bkt, ((size_t)1 << x->bits) + 1, &by, s))) return rc;
+    // heavy-node tie lists: one table row per 128-row sample, one list per node
+    x->nsamp_cap = (cap + lcpk::kBlk - 1) / lcpk::kBlk;
+    if (x->nsamp_cap < 1) x->nsamp_cap = 1;
+    const size_t nslots = (size_t)x->nsamp_cap * (size_t)(x->L + 1);
+    x->nlists_cap = 4 * x->nsamp_cap + 64;
+    if ((rc = dalloc(&x->tbl, nslots, &by, s))) return rc;
+    if ((rc = dalloc(&x->slot_flag, nslots, &by, s))) return rc;
+    if ((rc = dalloc(&x->slot_lo, nslots, &by, s))) return rc;
+    if ((rc = dalloc(&x->slot_hi, nslots, &by, s))) return rc;
+    if ((rc = dalloc(&x->slot_list, nslots, &by, s))) return rc;
+    if ((rc = dalloc(&x->tl_sums, (nslots + 2047) / 2048, &by, s))) return rc;
+    if ((rc = dalloc(&x->tl_total, 4, &by, s))) return rc;
+    if ((rc = dalloc(&x->tlists, (size_t)x->nlists_cap * x->K, &by, s))) return rc;
+    if ((rc = dalloc(&x->tl_lo, (size_t)x->nlists_cap, &by, s))) return rc;
+    if ((rc = dalloc(&x->tl_hi, (size_t)x->nlists_cap, &by, s))) return rc;
     if ((rc = dalloc(&x->status, 1, &by, s))) return rc;
     LCP_CUDA_TRY(cudaMemsetAsync(x->status, 0, sizeof(int), s));
     if (cap > N) {

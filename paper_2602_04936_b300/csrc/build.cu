@@ -167,6 +167,19 @@ __global__ void __launch_bounds__(kBlk) k_sort_blocks(const int32_t* __restrict_
     soff[b * kBlk + rank] = (uint8_t)t;
 }
 
+// Depth-1 buckets: bkt[t] = first sorted position whose first token is >= t,
+// for t in [0, 2^bits]; row p writes the entries between its predecessor's
+// first token and its own, the (virtual) row N closes the table.
+__global__ void k_buckets(const uint64_t* __restrict__ head, int64_t n, int bits,
+                          int32_t* __restrict__ bkt) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > n) return;
+    const int64_t ntok = 1ll << bits;
+    const int64_t t = p < n ? (int64_t)(head[p] >> (64 - bits)) : ntok;
+    const int64_t tprev = p > 0 ? (int64_t)(head[p - 1] >> (64 - bits)) : -1;
+    for (int64_t u = tprev + 1; u <= t; ++u) bkt[u] = (int32_t)p;
+}
+
 // Sparse-table level j: out[b] = K smallest of lists prev[b] and prev[b+half]
 // (disjoint position spans, so no duplicates).  One warp per b, merge path.
 __global__ void k_st_level(const uint32_t* __restrict__ prev, int64_t prev_stride, int64_t half,
@@ -305,6 +318,7 @@ int build_aux(lcp_index_s* x, cudaStream_t s) {
     lcp_buffers& b = x->buf[x->cur];
     if (N <= 0) return LCP_OK;
     LCP_LAUNCH(k_inverse, blocks_for(N, 256), 256, 0, s, b.ids, N, x->pos);
+    LCP_LAUNCH(k_buckets, blocks_for(N + 1, 256), 256, 0, s, b.head, N, x->bits, x->bkt);
     // min tree over H
     int64_t len = N;
     const uint8_t* in = b.H;
@@ -335,7 +349,7 @@ int build_aux(lcp_index_s* x, cudaStream_t s) {
         LCP_LAUNCH(k_st_level, blocks_for(valid * 32, 256), 256, 0, s, prev, pstride, half, valid, K,
                    out);
     }
-    return LCP_OK;
+    return build_tie_lists(x, s);
 }
 
 DevIndex dev_view(const lcp_index_s* x) {
@@ -367,6 +381,10 @@ DevIndex dev_view(const lcp_index_s* x) {
     d.soff = x->soff;
     d.st = x->st;
     d.st_stride = x->nblk_cap;
+    d.bkt = x->bkt;
+    d.tbl = x->tbl;
+    d.tlists = x->tlists;
+    d.L1 = x->L + 1;
     d.status = x->status;
     return d;
 }

@@ -16,6 +16,15 @@
 //                       smallest ids of blocks [b, b + 2^j), ascending; padded
 //                       with 0xFFFFFFFF.  Any position range's K smallest ids
 //                       come from two partial blocks and two table entries.
+//   bkt  [2^bits + 1] i32  depth-1 buckets (TAL's prefix partition with d = 1,
+//                       Sec. 6): rows whose first token is t occupy sorted
+//                       positions [bkt[t], bkt[t+1]).
+//   tbl  [N/128][L+1] i32  tie lists of heavy trie nodes: the LCP interval of
+//                       depth d around sample position 128*s, if it holds more
+//                       than 128 rows, has its K smallest ids (ascending) in
+//                       tlists[tbl[s][d]]; -1 otherwise.  Every trie node of
+//                       more than 128 rows contains a sample, so the indexed
+//                       search finds the level-d* list with one lookup.
 #pragma once
 
 #include "common.cuh"
@@ -46,6 +55,10 @@ struct DevIndex {
     const uint8_t* soff;
     const uint32_t* st;
     int64_t st_stride;  // nblk capacity used for the table layout
+    const int32_t* bkt;
+    const int32_t* tbl;
+    const uint32_t* tlists;
+    int L1;  // L + 1: row length of tbl
     int* status;
 };
 
@@ -73,6 +86,19 @@ struct lcp_index_s {
     uint32_t* sblk = nullptr;
     uint8_t* soff = nullptr;
     uint32_t* st = nullptr;
+    int32_t* bkt = nullptr;
+    // heavy-node tie lists
+    int32_t* tbl = nullptr;        // [nsamp_cap][L+1]
+    uint8_t* slot_flag = nullptr;  // [nsamp_cap][L+1] canonical (sample, depth) slots
+    int32_t* slot_lo = nullptr;    // interval of each canonical slot
+    int32_t* slot_hi = nullptr;
+    int32_t* slot_list = nullptr;  // list index of each canonical slot
+    uint32_t* tlists = nullptr;    // [nlists_cap][K]
+    int32_t* tl_lo = nullptr;      // interval of each list
+    int32_t* tl_hi = nullptr;
+    uint64_t* tl_sums = nullptr;   // scan block sums
+    uint32_t* tl_total = nullptr;  // number of canonical slots (device)
+    int64_t nsamp_cap = 0, nlists_cap = 0;
     int64_t nblk_cap = 0;
     int st_levels_cap = 0;
     int* status = nullptr;  // device status word
@@ -104,6 +130,8 @@ int adjacent_lcp(const uint64_t* rows, int64_t N, int W, int L, int tpw, int bit
                  cudaStream_t s);
 // pos, min tree and tie tables of the current buffers.
 int build_aux(lcp_index_s* x, cudaStream_t s);
+// heavy-node tie lists (needs the min tree, sorted blocks and sparse table).
+int build_tie_lists(lcp_index_s* x, cudaStream_t s);
 
 int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, int32_t* out_ids,
                       uint8_t* out_lcp, cudaStream_t s);

@@ -3,488 +3,269 @@
 //
 // Per warp, 32 queries:
 //   1. lane-per-query binary search on the L2-resident head array (word 0 of
-//      every sorted row): p0 = first row with head >= q0, p1 = first with
-//      head > q0.  32 independent searches per warp keep many probes in flight.
+//      every sorted row): p0 = first row with head >= q0; a gallop from p0
+//      finds p1 = first row with head > q0.  When no row shares word 0 with
+//      the query (p0 == p1), the insertion point is p0 and both neighbours'
+//      LCPs follow from their heads alone.
 //   then warp-per-query, for each of the 32:
-//   2. lower bound p inside [p0, p1) on the full rows (one coalesced row per
-//      probe), and lL = LCP(q, row p-1), lR = LCP(q, row p).  max(lL, lR) is
-//      the descent depth d of Algorithm 3.
+//   2. (only if p1 > p0) lower bound p inside [p0, p1) on the full rows, one
+//      coalesced row per probe, and lL = LCP(q, row p-1), lR = LCP(q, row p);
+//      max(lL, lR) is the descent depth of Algorithm 3.
 //   3. expansion: along each side the LCP of row j with q is the running
 //      minimum of H towards p (descent lemma, App. A).  32-item chunks are
-//      loaded from the side whose next LCP is larger, until the k-th largest
-//      loaded LCP d* is >= everything not yet loaded.  Items with LCP > d*
-//      (fewer than k; the set A = interval of level d*+1) are all taken.
+//      loaded, first from both sides at once, then from the side whose next
+//      LCP is larger, until at least k loaded items have an LCP no smaller
+//      than anything not loaded; d* is then the k-th largest loaded LCP.
+//      Items with LCP > d* (the set A, fewer than k) are all taken.
 //   4. the interval [lo, hi) of level d* (the prefix bucket of q[1..d*],
-//      Sec. 6.2) is closed with the 32-ary min tree over H, its smallest ids
-//      come from two partial blocks and two sparse-table lists, A's members
-//      are skipped, and the first k - |A| fill the remaining slots in
-//      ascending id order (ties by index).
-//   5. A is sorted by (LCP desc, id asc) in shared memory and the row of k
-//      (id, lcp) results is written with coalesced stores.
-#include "index.cuh"
+//      Sec. 6.2) is closed with the 32-ary min tree over H (left and right
+//      searches interleaved), its smallest ids come from up to two partial
+//      blocks and two sparse-table lists, A's members are skipped, and the
+//      first k - |A| fill the remaining slots in ascending id order.
+//   5. A is sorted by (LCP desc, id asc) in registers (warp bitonic network)
+//      and the k (id, lcp) results are written with coalesced stores.
+#include "search.cuh"
 
 namespace lcpk {
 
-constexpr int kSearchWarps = 4;
-constexpr int kMaxW = 64;
-constexpr int kKMax = LCP_INDEX_MAX_K;
-constexpr int kSide = kKMax + 64;  // loaded items per side never exceed k + 32
+// ---- expansion chunk loads ----
 
-struct alignas(16) QWarp {
-    uint64_t q[kMaxW];
-    uint64_t akey[kKMax];
-    uint32_t lid[kSide];
-    uint32_t rid[kSide];
-    uint32_t src[4][kKMax];
-    uint32_t m1[2 * kKMax];
-    uint32_t m2[2 * kKMax];
-    uint8_t llam[kSide];
-    uint8_t rlam[kSide];
-};
-
-// ---- warp-wide comparisons against the query held in shared memory ----
-
-// -1 if row < q, 0 if equal, +1 if row > q; *lcp receives LCP(q, row).
-__device__ __forceinline__ int warp_cmp_row(const uint64_t* __restrict__ row, const uint64_t* q,
-                                            const DevIndex& ix, int* lcp) {
+// Loads up to 32 items on one side starting `n` items away from p; returns
+// the count.  Left: positions p-1-n-lane; right: positions p+n+lane.
+template <bool LEFT>
+__device__ __forceinline__ void issue_chunk(const DevIndex& ix, int64_t p, int n, int64_t avail, int l0,
+                                            int& h, uint32_t& id, bool& ok) {
     const unsigned lane = lane_id();
-    for (int w0 = 0; w0 < ix.W; w0 += 32) {
-        int w = w0 + (int)lane;
-        uint64_t a = 0, b = 0;
-        if (w < ix.W) {
-            a = row[w];
-            b = q[w];
-        }
-        unsigned ne = __ballot_sync(0xffffffffu, a != b);
-        if (ne) {
-            int f = __ffs(ne) - 1;
-            uint64_t ra = __shfl_sync(0xffffffffu, a, f);
-            uint64_t qb = __shfl_sync(0xffffffffu, b, f);
-            int l = (w0 + f) * ix.tpw + (__clzll((long long)(ra ^ qb)) / ix.bits);
-            *lcp = l < ix.L ? l : ix.L;
-            return ra < qb ? -1 : 1;
-        }
+    ok = (int64_t)n + lane < avail;
+    h = 255;
+    id = 0;
+    if (ok) {
+        const int64_t x = LEFT ? p - 1 - n - (int64_t)lane : p + n + (int64_t)lane;
+        h = (n == 0 && lane == 0) ? l0 : (int)ix.H[LEFT ? x + 1 : x];
+        id = (uint32_t)ix.ids[x];
     }
-    *lcp = ix.L;
-    return 0;
 }
 
-// ---- min tree over H: next / previous position with H < d ----
-
-__device__ __forceinline__ const uint8_t* hlevel(const DevIndex& ix, int lev) {
-    return lev == 0 ? ix.H : ix.hmin + ix.hoff[lev];
-}
-
-// Smallest x >= from with H[x] < d, or N.
-__device__ int64_t next_less(const DevIndex& ix, int64_t from, int d) {
+__device__ __forceinline__ int finish_chunk(int h, uint32_t id, bool ok, int n, int64_t avail,
+                                            uint32_t* ids, uint8_t* lam) {
     const unsigned lane = lane_id();
-    if (from >= ix.N) return ix.N;
-    int64_t idx = from;
-    int lev = 0;
-    for (;;) {
-        const uint8_t* arr = hlevel(ix, lev);
-        int64_t len = ix.hlen[lev];
-        int64_t g0 = (idx >> 5) << 5;
-        int64_t e = g0 + lane;
-        bool ok = e >= idx && e < len && (int)arr[e] < d;
-        unsigned m = __ballot_sync(0xffffffffu, ok);
-        if (m) {
-            idx = g0 + __ffs(m) - 1;
-            break;
-        }
-        if (lev == ix.hlev) return ix.N;
-        idx = (idx >> 5) + 1;
-        ++lev;
-        if (idx >= ix.hlen[lev]) return ix.N;
+    if (n > 0) h = min(h, (int)lam[n - 1]);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, h, o);
+        if (lane >= (unsigned)o) h = min(h, y);
     }
-    while (lev > 0) {
-        --lev;
-        const uint8_t* arr = hlevel(ix, lev);
-        int64_t len = ix.hlen[lev];
-        int64_t g0 = idx << 5;
-        int64_t e = g0 + lane;
-        bool ok = e < len && (int)arr[e] < d;
-        unsigned m = __ballot_sync(0xffffffffu, ok);
-        if (!m) {  // cannot happen for a consistent tree
-            flag_status(ix.status, DEV_BAD);
-            return ix.N;
-        }
-        idx = g0 + __ffs(m) - 1;
-    }
-    return idx;
-}
-
-// Largest x <= from with H[x] < d, or -1.
-__device__ int64_t prev_less(const DevIndex& ix, int64_t from, int d) {
-    const unsigned lane = lane_id();
-    if (from < 0) return -1;
-    int64_t idx = from;
-    int lev = 0;
-    for (;;) {
-        const uint8_t* arr = hlevel(ix, lev);
-        int64_t len = ix.hlen[lev];
-        int64_t g0 = (idx >> 5) << 5;
-        int64_t e = g0 + lane;
-        bool ok = e <= idx && e < len && (int)arr[e] < d;
-        unsigned m = __ballot_sync(0xffffffffu, ok);
-        if (m) {
-            idx = g0 + 31 - __clz(m);
-            break;
-        }
-        if (lev == ix.hlev) return -1;
-        idx = (idx >> 5) - 1;
-        ++lev;
-        if (idx < 0) return -1;
-    }
-    while (lev > 0) {
-        --lev;
-        const uint8_t* arr = hlevel(ix, lev);
-        int64_t len = ix.hlen[lev];
-        int64_t g0 = idx << 5;
-        int64_t e = g0 + lane;
-        bool ok = e < len && (int)arr[e] < d;
-        unsigned m = __ballot_sync(0xffffffffu, ok);
-        if (!m) {
-            flag_status(ix.status, DEV_BAD);
-            return -1;
-        }
-        idx = g0 + 31 - __clz(m);
-    }
-    return idx;
-}
-
-// ---- small warp utilities over shared memory ----
-
-// Number of leading entries of a non-increasing array that are >= d.
-__device__ __forceinline__ int count_ge(const uint8_t* a, int n, int d) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if ((int)a[mid] >= d) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
-// k-th largest value of the union of two non-increasing arrays (1 <= k <= na+nb).
-__device__ __forceinline__ int kth_largest(const uint8_t* a, int na, const uint8_t* b, int nb, int k) {
-    int lo = k - nb > 0 ? k - nb : 0;
-    int hi = k < na ? k : na;
-    while (lo < hi) {
-        int i = (lo + hi) >> 1;
-        if (a[i] > b[k - i - 1]) lo = i + 1;
-        else hi = i;
-    }
-    int i = lo, j = k - lo;
-    int va = i > 0 ? (int)a[i - 1] : 1 << 20;
-    int vb = j > 0 ? (int)b[j - 1] : 1 << 20;
-    return va < vb ? va : vb;
-}
-
-// First nout entries of the merge of sorted a[0..na) and b[0..nb).
-__device__ __forceinline__ void warp_merge(const uint32_t* a, int na, const uint32_t* b, int nb,
-                                           uint32_t* out, int nout) {
-    const int lane = (int)lane_id();
-    int per = (nout + 31) >> 5;
-    int d0 = lane * per;
-    if (d0 < nout) {
-        int lo = d0 - nb > 0 ? d0 - nb : 0, hi = d0 < na ? d0 : na;
-        while (lo < hi) {
-            int mid = (lo + hi) >> 1;
-            if (a[mid] <= b[d0 - 1 - mid]) lo = mid + 1;
-            else hi = mid;
-        }
-        int i = lo, j = d0 - lo;
-        int end = d0 + per < nout ? d0 + per : nout;
-        for (int t = d0; t < end; ++t) {
-            bool takeA = (i < na) && (j >= nb || a[i] <= b[j]);
-            out[t] = takeA ? a[i++] : b[j++];
-        }
+    if (ok) {
+        ids[n + lane] = id;
+        lam[n + lane] = (uint8_t)h;
     }
     __syncwarp();
+    const int64_t got = avail - n < 32 ? avail - n : 32;
+    return (int)got;
 }
 
-// Copies up to `need` ids of sorted block b whose in-block offset lies in
-// [o1, o2), in ascending id order.  Returns the count.
-__device__ __forceinline__ int load_partial(const DevIndex& ix, int64_t b, int o1, int o2,
-                                            uint32_t* dst, int need) {
+// Id-order probe for a large tie level: walks ids 0, 1, 2, ... through pos[]
+// (the low ids' positions are hot in L2 for every query), keeping ids whose
+// sorted position lies in [lov, hiv) but outside A = [loc, hic).  Ascending
+// by construction.  At most 8 rounds of 256 ids; returns false when that did
+// not find kp of them (the caller then uses the sparse-table path).
+__device__ bool probe_ids(const DevIndex& ix, int64_t lov, int64_t hiv, int64_t loc, int64_t hic,
+                          int kp, uint32_t* dst, int* ntake) {
     const unsigned lane = lane_id();
+    const unsigned lt = lanemask_lt();
     int cnt = 0;
-    for (int base = 0; base < kBlk && cnt < need; base += 32) {
-        int t = base + (int)lane;
-        uint32_t id = ix.sblk[b * kBlk + t];
-        int off = ix.soff[b * kBlk + t];
-        bool keep = id != kInf && off >= o1 && off < o2;
-        unsigned m = __ballot_sync(0xffffffffu, keep);
-        int r = cnt + __popc(m & lanemask_lt());
-        if (keep && r < need) dst[r] = id;
-        cnt += __popc(m);
-    }
-    __syncwarp();
-    return cnt < need ? cnt : need;
-}
-
-// Copies up to `need` leading valid ids of a sorted list.
-__device__ __forceinline__ int load_list(const uint32_t* __restrict__ list, int len, uint32_t* dst,
-                                         int need) {
-    const unsigned lane = lane_id();
-    int n = need < len ? need : len;
-    int cnt = 0;
-    for (int base = 0; base < n; base += 32) {
-        int t = base + (int)lane;
-        uint32_t id = t < n ? list[t] : kInf;
-        if (t < n) dst[t] = id;
-        cnt += __popc(__ballot_sync(0xffffffffu, t < n && id != kInf));
-    }
-    __syncwarp();
-    return cnt;
-}
-
-// In-place removal of adjacent duplicates from a[0..n); returns new length.
-__device__ __forceinline__ int warp_dedupe(const uint32_t* a, int n, uint32_t* out) {
-    const unsigned lane = lane_id();
-    int cnt = 0;
-    for (int base = 0; base < n; base += 32) {
-        int t = base + (int)lane;
-        bool keep = t < n && (t == 0 || a[t] != a[t - 1]);
-        unsigned m = __ballot_sync(0xffffffffu, keep);
-        if (keep) out[cnt + __popc(m & lanemask_lt())] = a[t];
-        cnt += __popc(m);
-    }
-    __syncwarp();
-    return cnt;
-}
-
-// The `need` smallest ids of sorted positions [lo, hi) into S.src[0].
-__device__ int smallest_ids(const DevIndex& ix, int64_t lo, int64_t hi, int need, QWarp& S) {
-    const int64_t bl0 = lo / kBlk, bh0 = (hi - 1) / kBlk;
-    if (bl0 == bh0) return load_partial(ix, bl0, (int)(lo - bl0 * kBlk), (int)(hi - bl0 * kBlk), S.src[0], need);
-    int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-    int64_t bl = bl0, br = bh0 + 1;  // full blocks [bl, br)
-    if (lo % kBlk) {
-        c0 = load_partial(ix, bl0, (int)(lo % kBlk), kBlk, S.src[0], need);
-        bl = bl0 + 1;
-    }
-    if (hi != ix.N && (hi % kBlk)) {
-        c3 = load_partial(ix, bh0, 0, (int)(hi % kBlk), S.src[3], need);
-        br = bh0;
-    }
-    if (br > bl) {
-        int64_t span = br - bl;
-        int j = 63 - __clzll((long long)span);
-        const uint32_t* l1;
-        const uint32_t* l2;
-        int len;
-        if (j == 0) {
-            l1 = ix.sblk + bl * kBlk;
-            l2 = ix.sblk + (br - 1) * kBlk;
-            len = kBlk;
-        } else {
-            size_t lb = (size_t)(j - 1) * (size_t)ix.st_stride * (size_t)ix.K;
-            l1 = ix.st + lb + (size_t)bl * ix.K;
-            l2 = ix.st + lb + (size_t)(br - (1ll << j)) * ix.K;
-            len = ix.K;
+    int64_t base = 0;
+    for (int round = 0; round < 8 && base < ix.N; ++round, base += 256) {
+        int32_t ps[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int64_t id = base + lane + 32 * e;
+            ps[e] = id < ix.N ? ix.pos[id] : -1;
         }
-        c1 = load_list(l1, len, S.src[1], need);
-        if (span != (1ll << j)) c2 = load_list(l2, len, S.src[2], need);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int64_t x = ps[e];
+            const bool keep = x >= lov && x < hiv && (x < loc || x >= hic);
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            const int r = cnt + __popc(m & lt);
+            if (keep && r < kp) dst[r] = (uint32_t)(base + lane + 32 * e);
+            cnt += __popc(m);
+        }
+        if (cnt >= kp) {
+            __syncwarp();
+            *ntake = kp;
+            return true;
+        }
     }
-    // X = dedupe(merge(src1, src2)) in m2, Y = merge(src0, src3) in m1, M = merge(X, Y) in src0
-    int cx;
-    if (c2) {
-        warp_merge(S.src[1], c1, S.src[2], c2, S.m1, c1 + c2);
-        cx = warp_dedupe(S.m1, c1 + c2, S.m2);
-    } else {
-        for (int t = (int)lane_id(); t < c1; t += 32) S.m2[t] = S.src[1][t];
-        __syncwarp();
-        cx = c1;
+    __syncwarp();
+    if (base >= ix.N) {  // every id probed
+        *ntake = cnt;
+        return true;
     }
-    if (cx > need) cx = need;
-    int cy = c0 + c3 < need ? c0 + c3 : need;
-    warp_merge(S.src[0], c0, S.src[3], c3, S.m1, cy);
-    int cm = cx + cy < need ? cx + cy : need;
-    warp_merge(S.m2, cx, S.m1, cy, S.src[0], cm);
-    return cm;
+    return false;
 }
 
 // ---- one query, whole warp ----
 
-__device__ void topk_one(const DevIndex& ix, QWarp& S, const uint8_t* qrow, const RowFmt& qf,
-                         int64_t P0, int64_t P1, int k, int32_t* __restrict__ oid,
-                         uint8_t* __restrict__ olcp) {
+template <typename KT>
+__device__ void topk_one(const DevIndex& ix, QWarp& S, const uint8_t* qrow, const RowFmt& qf, int64_t P0,
+                         int64_t P1, int lL_head, int lR_head, int tok0, int k,
+                         int32_t* __restrict__ oid, uint8_t* __restrict__ olcp) {
     const unsigned lane = lane_id();
     const int64_t N = ix.N;
-    for (int w = (int)lane; w < ix.W; w += 32) S.q[w] = pack_word(qrow, w, qf);
-    __syncwarp();
-    // 2. lower bound inside the equal-head range, then both neighbours' LCPs
-    int64_t lo = P0, hi = P1;
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        int l;
-        if (warp_cmp_row(ix.rows + mid * ix.W, S.q, ix, &l) < 0) lo = mid + 1;
-        else hi = mid;
-    }
-    const int64_t p = lo;
-    int lL = -1, lR = -1;
-    if (p > 0) warp_cmp_row(ix.rows + (p - 1) * ix.W, S.q, ix, &lL);
-    if (p < N) warp_cmp_row(ix.rows + p * ix.W, S.q, ix, &lR);
-    // 3. expansion
-    int nL = 0, nR = 0, dstar = 0;
-    const int64_t availL = p, availR = N - p;
-    for (;;) {
-        int bL = nL < availL ? (nL == 0 ? lL : (int)S.llam[nL - 1]) : -1;
-        int bR = nR < availR ? (nR == 0 ? lR : (int)S.rlam[nR - 1]) : -1;
-        int F = bL > bR ? bL : bR;
-        if (nL + nR >= k) {
-            int v = kth_largest(S.llam, nL, S.rlam, nR, k);
-            if (v >= F) {
-                dstar = v;
-                break;
-            }
+    int64_t p = P0;
+    int lL = lL_head, lR = lR_head;
+    if (P1 > P0) {
+        // 2. lower bound inside the equal-head range, then both neighbours' LCPs
+        for (int w = (int)lane; w < ix.W; w += 32) S.q[w] = pack_word(qrow, w, qf);
+        __syncwarp();
+        int64_t lo = P0, hi = P1;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            int l;
+            if (warp_cmp_row(ix.rows + mid * ix.W, S.q, ix, &l) < 0) lo = mid + 1;
+            else hi = mid;
         }
-        if (F < 0) {
-            dstar = 0;  // all N < k items loaded
+        p = lo;
+        warp_lcp_neighbours(ix, p, S.q, &lL, &lR);
+    }
+    // 3. expansion
+    const int64_t availL = p, availR = N - p;
+    int nL = 0, nR = 0, dstar = 0;
+    {
+        int hl, hr;
+        uint32_t il, ir;
+        bool okl, okr;
+        issue_chunk<true>(ix, p, 0, availL, lL, hl, il, okl);
+        issue_chunk<false>(ix, p, 0, availR, lR, hr, ir, okr);
+        nL += finish_chunk(hl, il, okl, 0, availL, S.lid, S.llam);
+        nR += finish_chunk(hr, ir, okr, 0, availR, S.rid, S.rlam);
+    }
+    for (;;) {
+        const int bL = nL < availL ? (int)S.llam[nL - 1] : -1;
+        const int bR = nR < availR ? (int)S.rlam[nR - 1] : -1;
+        const int F = bL > bR ? bL : bR;
+        if (F < 0) {  // every item loaded
+            dstar = nL + nR >= k ? kth_largest(S.llam, nL, S.rlam, nR, k) : 0;
             break;
         }
+        // loaded items with LCP >= F (the side holding F counts entirely)
+        const int cnt = bL >= bR ? nL + count_ge(S.rlam, nR, F) : nR + count_ge(S.llam, nL, F);
+        if (cnt >= k) {
+            dstar = kth_largest(S.llam, nL, S.rlam, nR, k);
+            break;
+        }
+        int h;
+        uint32_t id;
+        bool ok;
         if (bL >= bR) {
             if (nL + 32 > kSide) {
                 flag_status(ix.status, DEV_BAD);
                 break;
             }
-            int64_t x = p - 1 - nL - (int64_t)lane;
-            bool ok = (int64_t)nL + lane < availL;
-            int h = 255;
-            uint32_t id = 0;
-            if (ok) {
-                h = (nL == 0 && lane == 0) ? lL : (int)ix.H[x + 1];
-                id = (uint32_t)ix.ids[x];
-            }
-            if (nL > 0) h = min(h, (int)S.llam[nL - 1]);
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, h, o);
-                if (lane >= (unsigned)o) h = min(h, y);
-            }
-            if (ok) {
-                S.lid[nL + lane] = id;
-                S.llam[nL + lane] = (uint8_t)h;
-            }
-            int64_t got = availL - nL < 32 ? availL - nL : 32;
-            __syncwarp();
-            nL += (int)got;
+            issue_chunk<true>(ix, p, nL, availL, lL, h, id, ok);
+            nL += finish_chunk(h, id, ok, nL, availL, S.lid, S.llam);
         } else {
             if (nR + 32 > kSide) {
                 flag_status(ix.status, DEV_BAD);
                 break;
             }
-            int64_t x = p + nR + (int64_t)lane;
-            bool ok = (int64_t)nR + lane < availR;
-            int h = 255;
-            uint32_t id = 0;
-            if (ok) {
-                h = (nR == 0 && lane == 0) ? lR : (int)ix.H[x];
-                id = (uint32_t)ix.ids[x];
-            }
-            if (nR > 0) h = min(h, (int)S.rlam[nR - 1]);
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, h, o);
-                if (lane >= (unsigned)o) h = min(h, y);
-            }
-            if (ok) {
-                S.rid[nR + lane] = id;
-                S.rlam[nR + lane] = (uint8_t)h;
-            }
-            int64_t got = availR - nR < 32 ? availR - nR : 32;
-            __syncwarp();
-            nR += (int)got;
+            issue_chunk<false>(ix, p, nR, availR, lR, h, id, ok);
+            nR += finish_chunk(h, id, ok, nR, availR, S.rid, S.rlam);
         }
     }
-    // A = loaded items with LCP > d*; interval of level d*
+    // A = loaded items with LCP > d*; interval [lov, hiv) of level d*
     const int aL = count_ge(S.llam, nL, dstar + 1);
     const int aR = count_ge(S.rlam, nR, dstar + 1);
     const int nA = aL + aR;
-    int64_t lov, hiv;
-    if (dstar == 0) {
-        lov = 0;
-        hiv = N;
-    } else {
-        int vL = count_ge(S.llam, nL, dstar);
-        int vR = count_ge(S.rlam, nR, dstar);
-        if (vL < nL || nL == availL) lov = p - vL;
-        else {
-            int64_t x = prev_less(ix, p - nL, dstar);
-            lov = x < 0 ? 0 : x;
-        }
-        if (vR < nR || nR == availR) hiv = p + vR;
-        else hiv = next_less(ix, p + nR, dstar);
+    int64_t lov = 0, hiv = N;
+    if (dstar == 1) {  // depth-1 bucket of q's first token
+        lov = ix.bkt[tok0];
+        hiv = ix.bkt[tok0 + 1];
+    } else if (dstar > 1) {
+        const int vL = count_ge(S.llam, nL, dstar);
+        const int vR = count_ge(S.rlam, nR, dstar);
+        const bool knownL = vL < nL || nL == availL;
+        const bool knownR = vR < nR || nR == availR;
+        int64_t xl = -1, xr = N;
+        find_bounds(ix, p - nL, !knownL, p + nR, !knownR, dstar, &xl, &xr);
+        lov = knownL ? p - vL : (xl < 0 ? 0 : xl);
+        hiv = knownR ? p + vR : xr;
     }
     const int64_t nT = (hiv - lov) - nA;
     int kp = k - nA;
     if ((int64_t)kp > nT) kp = (int)nT;
     // 4. tie fill: first kp ids of the level-d* interval outside A
     int ntake = 0;
-    if (kp > 0) {
-        int need = nA + kp;
-        int cm = smallest_ids(ix, lov, hiv, need, S);
-        const int64_t loc = p - aL, hic = p + aR;
-        for (int base = 0; base < cm && ntake < kp; base += 32) {
-            int t = base + (int)lane;
-            uint32_t id = t < cm ? S.src[0][t] : kInf;
-            bool keep = false;
-            if (t < cm) {
-                int64_t ps = ix.pos[id];
-                keep = ps < loc || ps >= hic;
+    bool filled = kp <= 0;
+    const int64_t loc = p - aL, hic = p + aR;
+    // a tie level holding a large share of all rows: probe ids in order
+    // (expected <= 6 chunks of 128 ids)
+    if (!filled && (int64_t)kp * N <= nT * 768) filled = probe_ids(ix, lov, hiv, loc, hic, kp, S.m1, &ntake);
+    // a heavy trie node: its precomputed K smallest ids, minus A's members
+    if (!filled && hiv - lov > kBlk) {
+        const int64_t smp = (lov + kBlk - 1) / kBlk;
+        const int li = ix.tbl[smp * ix.L1 + dstar];
+        if (li >= 0) {
+            const uint32_t* list = ix.tlists + (size_t)li * ix.K;
+            const int need = nA + kp;
+            uint32_t v[4];
+            bool keep[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int t = (int)lane + 32 * e;
+                v[e] = t < need ? list[t] : kInf;
             }
-            unsigned m = __ballot_sync(0xffffffffu, keep);
-            int r = ntake + __popc(m & lanemask_lt());
-            if (keep && r < kp) S.m1[r] = id;
-            ntake += __popc(m);
+            int64_t ps[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) ps[e] = v[e] != kInf ? (int64_t)ix.pos[v[e]] : -1;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) keep[e] = v[e] != kInf && (ps[e] < loc || ps[e] >= hic);
+            ntake = compact4(v, keep, S.m1, kp);
+            __syncwarp();
+            filled = true;
         }
-        if (ntake > kp) ntake = kp;
+    }
+    if (!filled) {
+        const int need = nA + kp;
+        const int cm = smallest_ids(ix, lov, hiv, need, S);
+        uint32_t v[4];
+        bool keep[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int t = (int)lane + 32 * e;
+            v[e] = t < cm ? S.src[0][t] : kInf;
+        }
+        int64_t ps[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) ps[e] = v[e] != kInf ? (int64_t)ix.pos[v[e]] : -1;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) keep[e] = v[e] != kInf && (ps[e] < loc || ps[e] >= hic);
+        __syncwarp();
+        ntake = compact4(v, keep, S.m1, kp);
         __syncwarp();
     }
-    // 5. sort A by (LCP desc, id asc)
-    int P = 1;
-    while (P < nA) P <<= 1;
-    for (int t = (int)lane; t < P; t += 32) {
-        uint64_t key = ~0ull;
-        if (t < aL) key = ((uint64_t)(255 - S.llam[t]) << 32) | S.lid[t];
-        else if (t < nA) key = ((uint64_t)(255 - S.rlam[t - aL]) << 32) | S.rid[t - aL];
-        S.akey[t] = key;
+    // 5. A sorted by (LCP desc, id asc), then the tie fill, then padding
+    if (nA > 0) {
+        if (nA <= 32) sort_and_write_A<1, KT>(S, aL, nA, oid, olcp);
+        else if (nA <= 64) sort_and_write_A<2, KT>(S, aL, nA, oid, olcp);
+        else sort_and_write_A<4, KT>(S, aL, nA, oid, olcp);
     }
-    __syncwarp();
-    for (int size = 2; size <= P; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = (int)lane; t < P; t += 32) {
-                int u = t ^ stride;
-                if (u > t) {
-                    uint64_t a = S.akey[t], b = S.akey[u];
-                    bool up = (t & size) == 0;
-                    if ((a > b) == up) {
-                        S.akey[t] = b;
-                        S.akey[u] = a;
-                    }
-                }
-            }
-            __syncwarp();
-        }
-    }
-    for (int r = (int)lane; r < k; r += 32) {
+    for (int r = nA + (int)lane; r < k; r += 32) {
         int32_t id = -1;
         uint8_t l = 0;
-        if (r < nA) {
-            uint64_t key = S.akey[r];
-            id = (int32_t)(uint32_t)key;
-            l = (uint8_t)(255 - (int)(key >> 32));
-        } else if (r < nA + ntake) {
+        if (r < nA + ntake) {
             id = (int32_t)S.m1[r - nA];
             l = (uint8_t)dstar;
         }
-        oid[r] = id;
-        olcp[r] = l;
+        __stcs(oid + r, (int)id);
+        __stcs(reinterpret_cast<char*>(olcp) + r, (char)l);
     }
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(kSearchWarps * 32) k_topk_search(DevIndex ix,
+template <typename KT>
+__global__ void __launch_bounds__(kSearchWarps * 32, 8) k_topk_search(DevIndex ix,
                                                                    const uint8_t* __restrict__ queries,
                                                                    RowFmt qf, int64_t Q, int k,
                                                                    int32_t* __restrict__ out_ids,
@@ -495,30 +276,51 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_topk_search(DevIndex ix,
     QWarp& S = sm[warp];
     const int64_t wq0 = ((int64_t)blockIdx.x * kSearchWarps + warp) * 32;
     if (wq0 >= Q) return;
-    // 1. lane-per-query search on head
+    // 1. lane-per-query search on head: lower bound, then gallop to the upper bound
     const int64_t myq = wq0 + lane;
     const bool has = myq < Q;
-    uint64_t q0 = has ? pack_word(row_of(queries, myq, qf), 0, qf) : 0;
-    int64_t lo = 0, hi = ix.N;
+    const uint64_t q0 = has ? pack_word(row_of(queries, myq, qf), 0, qf) : 0;
+    const int64_t N = ix.N;
+    int64_t lo = 0, hi = N;
     while (lo < hi) {
         int64_t mid = (lo + hi) >> 1;
         if (ix.head[mid] < q0) lo = mid + 1;
         else hi = mid;
     }
     const int64_t p0 = lo;
-    hi = ix.N;
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (ix.head[mid] <= q0) lo = mid + 1;
-        else hi = mid;
+    int64_t p1 = p0;
+    if (p0 < N && ix.head[p0] == q0) {
+        int64_t step = 1, last = p0;  // head[last] == q0
+        while (last + step < N && ix.head[last + step] == q0) {
+            last += step;
+            step <<= 1;
+        }
+        lo = last + 1;
+        hi = last + step < N ? last + step : N;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (ix.head[mid] <= q0) lo = mid + 1;
+            else hi = mid;
+        }
+        p1 = lo;
     }
-    const int64_t p1 = lo;
+    // neighbours' LCPs from the heads when no row shares word 0 with q
+    int lLh = -1, lRh = -1;
+    if (p1 == p0) {  // heads differ from q0, so the first differing word is word 0
+        if (p0 > 0) lLh = __clzll((long long)(ix.head[p0 - 1] ^ q0)) / ix.bits;
+        if (p0 < N) lRh = __clzll((long long)(ix.head[p0] ^ q0)) / ix.bits;
+    }
+    const int tok = (int)(q0 >> (64 - ix.bits));
     for (int j = 0; j < 32; ++j) {
         const int64_t qi = wq0 + j;
         if (qi >= Q) break;
         const int64_t P0 = __shfl_sync(0xffffffffu, p0, j);
         const int64_t P1 = __shfl_sync(0xffffffffu, p1, j);
-        topk_one(ix, S, row_of(queries, qi, qf), qf, P0, P1, k, out_ids + qi * k, out_lcp + qi * k);
+        const int l0 = __shfl_sync(0xffffffffu, lLh, j);
+        const int r0 = __shfl_sync(0xffffffffu, lRh, j);
+        const int t0 = __shfl_sync(0xffffffffu, tok, j);
+        topk_one<KT>(ix, S, row_of(queries, qi, qf), qf, P0, P1, l0, r0, t0, k, out_ids + qi * k,
+                     out_lcp + qi * k);
     }
 }
 
@@ -539,8 +341,14 @@ int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, i
     RowFmt qf = make_fmt(x->tb, x->L, d_queries);
     int64_t warps = (Q + 31) / 32;
     unsigned grid = (unsigned)((warps + kSearchWarps - 1) / kSearchWarps);
-    LCP_LAUNCH(k_topk_search, grid, kSearchWarps * 32, 0, s, ix,
-               reinterpret_cast<const uint8_t*>(d_queries), qf, Q, k, out_ids, out_lcp);
+    const uint8_t* q = reinterpret_cast<const uint8_t*>(d_queries);
+    if (x->N <= (1ll << 24)) {
+        LCP_LAUNCH(k_topk_search<uint32_t>, grid, kSearchWarps * 32, 0, s, ix, q, qf, Q, k, out_ids,
+                   out_lcp);
+    } else {
+        LCP_LAUNCH(k_topk_search<uint64_t>, grid, kSearchWarps * 32, 0, s, ix, q, qf, Q, k, out_ids,
+                   out_lcp);
+    }
     return LCP_OK;
 }
 

@@ -310,6 +310,15 @@ __global__ void __launch_bounds__(kCmpThreads) k_tie_scatter(const uint8_t* __re
 namespace lcph {
 using namespace lcpk;
 
+// Small pinned host buffer for the few counts the host reads back during a
+// sort, allocated once per process per thread (cudaFreeHost would synchronise
+// the whole device, so it is never freed per build).
+static uint32_t* pinned_words() {
+    static thread_local uint32_t* buf = nullptr;
+    if (!buf && cudaMallocHost((void**)&buf, sizeof(uint32_t) * 16) != cudaSuccess) buf = nullptr;
+    return buf;
+}
+
 int sort_work_alloc(SortWork& w, uint32_t cap, int* err, cudaStream_t s) {
     w.cap = cap;
     w.err = err;
@@ -324,7 +333,8 @@ int sort_work_alloc(SortWork& w, uint32_t cap, int* err, cudaStream_t s) {
     LCP_CUDA_TRY(cudaMallocAsync((void**)&w.counters, sizeof(uint32_t) * kMaxPasses, s));
     LCP_CUDA_TRY(cudaMallocAsync((void**)&w.block_sums, sizeof(uint64_t) * nb, s));
     LCP_CUDA_TRY(cudaMallocAsync((void**)&w.total, sizeof(uint32_t) * 16, s));
-    LCP_CUDA_TRY(cudaMallocHost((void**)&w.h_total, sizeof(uint32_t) * 16));
+    w.h_total = pinned_words();
+    if (!w.h_total) return LCP_ERR_OOM;
     return LCP_OK;
 }
 
@@ -336,7 +346,6 @@ void sort_work_free(SortWork& w, cudaStream_t s) {
     cudaFreeAsync(w.counters, s);
     cudaFreeAsync(w.block_sums, s);
     cudaFreeAsync(w.total, s);
-    if (w.h_total) cudaFreeHost(w.h_total);
     w = SortWork();
 }
 

@@ -245,3 +245,15 @@ def test_workload_generators_are_deterministic_and_shaped():
     g = W.GncStream(sensors=10, seed=5)
     r0 = g.step()
     assert r0.shape == (10, 8) and r0[:, 2:].max() <= 9
+
+
+def test_zipf_generator_c_path_matches_numpy_reference():
+    """workloads/gen.c draws exactly what the numpy definition draws."""
+    import workloads as W
+    for N, L, V, s in [(1500, 32, 1024, 1.1), (800, 64, 32768, 1.05), (300, 8, 16, 1.0)]:
+        a = W.zipf_prefix_rows(N, L, V, s, 7, impl="c")
+        b = W.zipf_prefix_rows(N, L, V, s, 7, impl="numpy")
+        assert np.array_equal(a, b)
+        qa = W.zipf_prefix_queries(a, 400, V, s, 7, impl="c")
+        qb = W.zipf_prefix_queries(a, 400, V, s, 7, impl="numpy")
+        assert np.array_equal(qa, qb)
