@@ -36,6 +36,18 @@ int* lib_status_word() {
     return g_status[dev];
 }
 
+int sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (!cache[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = n > 0 ? n : 148;
+    }
+    return cache[dev];
+}
+
 int scan_topk_device(const void* d_tokens, int64_t N, int tb, int L, const void* d_queries,
                      int64_t Q, int k, int32_t* d_out_ids, uint8_t* d_out_lcp, cudaStream_t s);
 

@@ -10,7 +10,7 @@
 // (Zipf-shared prefixes, first differences within a few tokens) almost all
 // of the work is round 0.  Stability of every pass keeps equal rows in id
 // order, which is the posting-list order of Algorithm 1.
-#include "index.cuh"
+#include "search.cuh"
 #include "sort.cuh"
 
 namespace lcpk {
@@ -84,6 +84,105 @@ __global__ void k_remap_active(const uint32_t* __restrict__ act, const uint32_t*
     act2[j] = act[idx[j]];
 }
 
+// Tie groups after round 0: gstart[g] = first index (in the active list) of
+// group g, gstart[G] = m.
+__global__ void k_group_starts(const uint32_t* __restrict__ grp, uint32_t m, uint32_t G,
+                               uint32_t* __restrict__ gstart) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    if (i == 0 || grp[i] != grp[i - 1]) gstart[grp[i]] = i;
+    if (i == 0) gstart[G] = m;
+}
+
+// Lexicographic comparison of two raw rows from word w0 on, then by id.
+__device__ __forceinline__ bool row_less(const uint8_t* __restrict__ tokens, const RowFmt& f, int w0,
+                                         int32_t a, int32_t b) {
+    const uint8_t* ra = row_of(tokens, a, f);
+    const uint8_t* rb = row_of(tokens, b, f);
+    for (int w = w0; w < f.W; ++w) {
+        const uint64_t x = pack_word(ra, w, f), y = pack_word(rb, w, f);
+        if (x != y) return x < y;
+    }
+    return a < b;
+}
+
+// Orders two rows of one tie group: by word 1 (given), then the later words,
+// then id.  Word 0 is equal inside a group.
+__device__ __forceinline__ bool tie_less(const uint8_t* __restrict__ tokens, const RowFmt& f,
+                                         uint64_t ka, int32_t a, uint64_t kb, int32_t b) {
+    if (ka != kb) return ka < kb;
+    return row_less(tokens, f, 2, a, b);  // rare: equal on word 1 too
+}
+
+// Groups of at most 32 rows: one warp loads each row's word 1 once, ranks the
+// rows with shuffles, and writes them back in order.  Larger groups are listed
+// for k_group_sort_mid (<= 512 rows) or counted for the LSD rounds.
+__global__ void __launch_bounds__(128) k_group_sort_small(const uint8_t* __restrict__ tokens, RowFmt f,
+                                                          const uint32_t* __restrict__ gstart, uint32_t G,
+                                                          const uint32_t* __restrict__ act,
+                                                          int32_t* __restrict__ ids,
+                                                          uint32_t* __restrict__ big_list,
+                                                          uint32_t* __restrict__ big_count,
+                                                          uint32_t* __restrict__ huge_count) {
+    const uint32_t g = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (g >= G) return;
+    const unsigned lane = lane_id();
+    const uint32_t gs = gstart[g], n = gstart[g + 1] - gs;
+    if (n > 32) {
+        if (lane == 0) {
+            if (n <= 512) big_list[atomicAdd(big_count, 1u)] = g;
+            else atomicAdd(huge_count, n);
+        }
+        return;
+    }
+    const int32_t my = lane < n ? ids[act[gs + lane]] : 0;
+    const uint64_t key = lane < n ? pack_word(row_of(tokens, my, f), 1, f) : 0ull;
+    uint32_t rank = 0;
+    for (uint32_t j = 0; j < n; ++j) {
+        const int32_t oid = __shfl_sync(0xffffffffu, my, j);
+        const uint64_t ok = __shfl_sync(0xffffffffu, key, j);
+        if (lane < n && j != lane && tie_less(tokens, f, ok, oid, key, my)) ++rank;
+    }
+    __syncwarp();
+    if (lane < n) ids[act[gs + rank]] = my;
+}
+
+// Groups of 33..512 rows: one CTA, word-1 keys staged in shared memory.
+__global__ void __launch_bounds__(256) k_group_sort_mid(const uint8_t* __restrict__ tokens, RowFmt f,
+                                                        const uint32_t* __restrict__ gstart,
+                                                        const uint32_t* __restrict__ act,
+                                                        int32_t* __restrict__ ids,
+                                                        const uint32_t* __restrict__ big_list,
+                                                        const uint32_t* __restrict__ big_count) {
+    __shared__ int32_t sid[512];
+    __shared__ uint64_t skey[512];
+    if (blockIdx.x >= *big_count) return;
+    const uint32_t g = big_list[blockIdx.x];
+    const uint32_t gs = gstart[g], n = gstart[g + 1] - gs;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const int32_t id = ids[act[gs + i]];
+        sid[i] = id;
+        skey[i] = pack_word(row_of(tokens, id, f), 1, f);
+    }
+    __syncthreads();
+    uint32_t rank[2];
+    for (int r = 0; r < 2; ++r) {
+        const uint32_t i = threadIdx.x + r * 256;
+        rank[r] = 0;
+        if (i < n) {
+            const uint64_t ki = skey[i];
+            const int32_t ii = sid[i];
+            for (uint32_t j = 0; j < n; ++j)
+                if (j != i && tie_less(tokens, f, skey[j], sid[j], ki, ii)) ++rank[r];
+        }
+    }
+    __syncthreads();
+    for (int r = 0; r < 2; ++r) {
+        const uint32_t i = threadIdx.x + r * 256;
+        if (i < n) ids[act[gs + rank[r]]] = sid[i];
+    }
+}
+
 __global__ void k_copy_ids(const uint32_t* __restrict__ vs, uint32_t n, int32_t* __restrict__ ids) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) ids[i] = (int32_t)vs[i];
@@ -102,6 +201,27 @@ __global__ void k_gather_rows(const uint8_t* __restrict__ tokens, RowFmt f, int6
     uint64_t x = (uint64_t)id < (uint64_t)n ? pack_word(row_of(tokens, id, f), w, f) : 0ull;
     rows[e] = x;
     if (w == 0) head[p] = x;
+}
+
+// Same with two words per thread and 16-byte accesses (rows of an even number
+// of words, 16-byte aligned raw rows and output).
+__global__ void k_gather_rows_v2(const uint8_t* __restrict__ tokens, RowFmt f, int64_t n,
+                                 const int32_t* __restrict__ ids, uint64_t* __restrict__ rows,
+                                 uint64_t* __restrict__ head) {
+    const int half = f.W >> 1;
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * half) return;
+    const int64_t p = e / half;
+    const int h = (int)(e - p * half);
+    const int32_t id = ids[p];
+    ulonglong2 v = make_ulonglong2(0ull, 0ull);
+    if ((uint64_t)id < (uint64_t)n) {
+        const ulonglong2 raw = __ldg(reinterpret_cast<const ulonglong2*>(row_of(tokens, id, f)) + h);
+        v.x = msb_first(raw.x, f.tb);
+        v.y = msb_first(raw.y, f.tb);
+    }
+    reinterpret_cast<ulonglong2*>(rows)[e] = v;
+    if (h == 0) head[p] = v.x;
 }
 
 // H[p] = LCP(rows[p-1], rows[p]), H[0] = 0.
@@ -146,52 +266,68 @@ __global__ void k_min32(const uint8_t* __restrict__ in, int64_t n_in, uint8_t* _
     out[b] = (uint8_t)m;
 }
 
-// One CTA (128 threads) per block: ids of the block sorted ascending (rank
-// sort: ids are distinct) with their in-block offsets; padding 0xFFFFFFFF.
-__global__ void __launch_bounds__(kBlk) k_sort_blocks(const int32_t* __restrict__ ids, int64_t n,
-                                                      uint32_t* __restrict__ sblk,
-                                                      uint8_t* __restrict__ soff) {
-    __shared__ uint32_t v[kBlk];
-    int64_t b = blockIdx.x;
-    int t = threadIdx.x;
-    int64_t p = b * kBlk + t;
-    uint32_t mine = p < n ? (uint32_t)ids[p] : kInf;
-    v[t] = mine;
-    __syncthreads();
-    int rank = 0;
-    for (int j = 0; j < kBlk; ++j) {
-        uint32_t o = v[j];
-        rank += (o < mine) || (o == mine && j < t);
+// One warp per 128-position block: (id, offset) keys sorted ascending with the
+// register bitonic network; positions past n become padding (0xFFFFFFFF).
+__global__ void __launch_bounds__(128) k_sort_blocks(const int32_t* __restrict__ ids, int64_t n,
+                                                     int64_t nblk, uint32_t* __restrict__ sblk,
+                                                     uint8_t* __restrict__ soff) {
+    const int64_t b = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (b >= nblk) return;
+    const int lane = (int)lane_id();
+    uint64_t v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int off = lane * 4 + e;
+        const int64_t p = b * kBlk + off;
+        v[e] = p < n ? (((uint64_t)(uint32_t)ids[p] << 8) | (uint64_t)off) : ~0ull;
     }
-    sblk[b * kBlk + rank] = mine;
-    soff[b * kBlk + rank] = (uint8_t)t;
+    warp_bitonic<4, uint64_t>(v);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int t = lane * 4 + e;
+        sblk[b * kBlk + t] = v[e] == ~0ull ? kInf : (uint32_t)(v[e] >> 8);
+        soff[b * kBlk + t] = (uint8_t)(v[e] & 255u);
+    }
 }
 
 // Depth-1 buckets: bkt[t] = first sorted position whose first token is >= t,
-// for t in [0, 2^bits]; row p writes the entries between its predecessor's
-// first token and its own, the (virtual) row N closes the table.
+// for t in [0, 2^bits] (bkt[2^bits] = n): one binary search on head per token.
 __global__ void k_buckets(const uint64_t* __restrict__ head, int64_t n, int bits,
                           int32_t* __restrict__ bkt) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p > n) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t ntok = 1ll << bits;
-    const int64_t t = p < n ? (int64_t)(head[p] >> (64 - bits)) : ntok;
-    const int64_t tprev = p > 0 ? (int64_t)(head[p - 1] >> (64 - bits)) : -1;
-    for (int64_t u = tprev + 1; u <= t; ++u) bkt[u] = (int32_t)p;
+    if (t > ntok) return;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)(head[mid] >> (64 - bits)) < t) lo = mid + 1;
+        else hi = mid;
+    }
+    bkt[t] = (int32_t)lo;
 }
 
 // Sparse-table level j: out[b] = K smallest of lists prev[b] and prev[b+half]
-// (disjoint position spans, so no duplicates).  One warp per b, merge path.
-__global__ void k_st_level(const uint32_t* __restrict__ prev, int64_t prev_stride, int64_t half,
-                           int64_t nb_valid, int K, uint32_t* __restrict__ out) {
-    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
+// (disjoint position spans, so no duplicates).  One warp per b: both lists
+// are staged in shared memory with coalesced loads, then merged by merge path.
+__global__ void __launch_bounds__(256) k_st_level(const uint32_t* __restrict__ prev, int64_t prev_stride,
+                                                  int64_t half, int64_t nb_valid, int K,
+                                                  uint32_t* __restrict__ out) {
+    __shared__ uint32_t buf[8][2 * LCP_INDEX_MAX_K];
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (warp >= nb_valid) return;
-    const uint32_t* A = prev + warp * prev_stride;
-    const uint32_t* B = prev + (warp + half) * prev_stride;
+    uint32_t* A = buf[threadIdx.x >> 5];
+    uint32_t* B = A + K;
+    const uint32_t* ga = prev + warp * prev_stride;
+    const uint32_t* gb = prev + (warp + half) * prev_stride;
+    for (int t = lane; t < K; t += 32) {
+        A[t] = ga[t];
+        B[t] = gb[t];
+    }
+    __syncwarp();
     uint32_t* O = out + warp * (int64_t)K;
-    int per = K / 32;
-    int d0 = lane * per;
+    const int per = K / 32;
+    const int d0 = lane * per;
     int lo = d0 - K > 0 ? d0 - K : 0, hi = d0 < K ? d0 : K;
     while (lo < hi) {
         int mid = (lo + hi) >> 1;
@@ -264,6 +400,25 @@ int build_sorted_ids(const void* tokens, const RowFmt& f, int64_t N64, int32_t* 
     LCP_LAUNCH(k_eq_sorted, blocks_for(N, 256), 256, 0, s, ks, N, eq);
     uint32_t m = 0, G = 0;
     rc = tie_compact(eq, N, act, grp, &m, &G, w, s);
+    // Rows tied on word 0: small groups are ranked directly on their
+    // remaining words; only groups of more than 512 rows (if any) need the
+    // word-by-word LSD rounds below.
+    if (rc == 0 && m > 0 && f.W > 1) {
+        uint32_t* gstart = idx2;          // G + 1 <= m + 1 <= N entries
+        uint32_t* big_list = act2;        // free until the LSD rounds
+        uint32_t* cnt = w.total + 2;      // [0] big groups, [1] rows in huge groups
+        LCP_CUDA_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), s));
+        LCP_LAUNCH(k_group_starts, blocks_for(m, 256), 256, 0, s, grp, m, G, gstart);
+        LCP_LAUNCH(k_group_sort_small, blocks_for(G, 4), 128, 0, s, tk, f, gstart, G, act, ids_out,
+                   big_list, cnt, cnt + 1);
+        LCP_LAUNCH(k_group_sort_mid, blocks_for(m, 33), 256, 0, s, tk, f, gstart, act, ids_out, big_list,
+                   cnt);
+        LCP_CUDA_TRY(cudaMemcpyAsync(w.h_total + 10, cnt + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        LCP_CUDA_TRY(cudaStreamSynchronize(s));
+        if (w.h_total[10] == 0) m = 0;  // every tie resolved
+    } else if (f.W == 1) {
+        m = 0;  // one word: rows tied on it are equal and already in id order
+    }
     // rounds 1..W-1 on the rows whose prefix is still shared
     for (int r = 1; rc == 0 && r < f.W && m > 0; ++r) {
         LCP_LAUNCH(k_keys_active, blocks_for(m, 256), 256, 0, s, tk, f, N, ids_out, act, m, r, k0,
@@ -300,9 +455,16 @@ int build_sorted_ids(const void* tokens, const RowFmt& f, int64_t N64, int32_t* 
 int gather_rows_and_lcp(const void* tokens, const RowFmt& f, int64_t N, const int32_t* ids,
                         lcp_buffers& b, int W, cudaStream_t s) {
     if (N <= 0) return LCP_OK;
-    int64_t total = N * W;
-    LCP_LAUNCH(k_gather_rows, blocks_for(total, 256), 256, 0, s,
-               reinterpret_cast<const uint8_t*>(tokens), f, N, ids, b.rows, b.head);
+    const bool vec = f.aligned8 && (W % 2 == 0) && (f.row_bytes % 16 == 0) &&
+                     ((reinterpret_cast<uintptr_t>(tokens) & 15) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(b.rows) & 15) == 0);
+    if (vec) {
+        LCP_LAUNCH(k_gather_rows_v2, blocks_for(N * (W / 2), 256), 256, 0, s,
+                   reinterpret_cast<const uint8_t*>(tokens), f, N, ids, b.rows, b.head);
+    } else {
+        LCP_LAUNCH(k_gather_rows, blocks_for(N * W, 256), 256, 0, s,
+                   reinterpret_cast<const uint8_t*>(tokens), f, N, ids, b.rows, b.head);
+    }
     return adjacent_lcp(b.rows, N, W, f.L, f.tpw, f.bits, b.H, s);
 }
 
@@ -318,7 +480,7 @@ int build_aux(lcp_index_s* x, cudaStream_t s) {
     lcp_buffers& b = x->buf[x->cur];
     if (N <= 0) return LCP_OK;
     LCP_LAUNCH(k_inverse, blocks_for(N, 256), 256, 0, s, b.ids, N, x->pos);
-    LCP_LAUNCH(k_buckets, blocks_for(N + 1, 256), 256, 0, s, b.head, N, x->bits, x->bkt);
+    LCP_LAUNCH(k_buckets, blocks_for((1ll << x->bits) + 1, 256), 256, 0, s, b.head, N, x->bits, x->bkt);
     // min tree over H
     int64_t len = N;
     const uint8_t* in = b.H;
@@ -338,7 +500,7 @@ int build_aux(lcp_index_s* x, cudaStream_t s) {
     x->hlev = lev;
     // sorted blocks and sparse table of K smallest ids
     int64_t nblk = (N + kBlk - 1) / kBlk;
-    LCP_LAUNCH(k_sort_blocks, (unsigned)nblk, kBlk, 0, s, b.ids, N, x->sblk, x->soff);
+    LCP_LAUNCH(k_sort_blocks, (unsigned)((nblk + 3) / 4), 128, 0, s, b.ids, N, nblk, x->sblk, x->soff);
     int K = x->K;
     for (int j = 1; j <= x->st_levels_cap && (1ll << j) <= nblk; ++j) {
         int64_t half = 1ll << (j - 1);

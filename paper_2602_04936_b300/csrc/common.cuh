@@ -119,6 +119,7 @@ namespace lcph {
 void count_launch(int n = 1);
 int cuda_status(cudaError_t e);  // maps to LCP_ERR_* and records the last error text
 int* lib_status_word();          // device pointer to the library-wide status word
+int sm_count();                  // multiprocessors of the current device (cached)
 }  // namespace lcph
 
 #define LCP_LAUNCH(kern, grid, block, smem, stream, ...)                 \

@@ -267,18 +267,19 @@ __device__ void topk_one(const DevIndex& ix, QWarp& S, const uint8_t* qrow, cons
 template <typename KT>
 __global__ void __launch_bounds__(kSearchWarps * 32, 8) k_topk_search(DevIndex ix,
                                                                    const uint8_t* __restrict__ queries,
-                                                                   RowFmt qf, int64_t Q, int k,
+                                                                   RowFmt qf, int64_t Q, int k, int qpw,
                                                                    int32_t* __restrict__ out_ids,
                                                                    uint8_t* __restrict__ out_lcp) {
     __shared__ QWarp sm[kSearchWarps];
     const int warp = threadIdx.x >> 5;
     const unsigned lane = lane_id();
     QWarp& S = sm[warp];
-    const int64_t wq0 = ((int64_t)blockIdx.x * kSearchWarps + warp) * 32;
+    const int64_t wq0 = ((int64_t)blockIdx.x * kSearchWarps + warp) * qpw;
     if (wq0 >= Q) return;
-    // 1. lane-per-query search on head: lower bound, then gallop to the upper bound
+    // 1. lane-per-query search on head (lanes < qpw): lower bound, then gallop
+    //    to the upper bound
     const int64_t myq = wq0 + lane;
-    const bool has = myq < Q;
+    const bool has = (int)lane < qpw && myq < Q;
     const uint64_t q0 = has ? pack_word(row_of(queries, myq, qf), 0, qf) : 0;
     const int64_t N = ix.N;
     int64_t lo = 0, hi = N;
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 8) k_topk_search(DevIndex i
         if (p0 < N) lRh = __clzll((long long)(ix.head[p0] ^ q0)) / ix.bits;
     }
     const int tok = (int)(q0 >> (64 - ix.bits));
-    for (int j = 0; j < 32; ++j) {
+    for (int j = 0; j < qpw; ++j) {
         const int64_t qi = wq0 + j;
         if (qi >= Q) break;
         const int64_t P0 = __shfl_sync(0xffffffffu, p0, j);
@@ -339,14 +340,20 @@ int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, i
     }
     DevIndex ix = dev_view(x);
     RowFmt qf = make_fmt(x->tb, x->L, d_queries);
-    int64_t warps = (Q + 31) / 32;
+    // queries per warp: 32 for large batches (phase 1 uses every lane); fewer
+    // for small batches so that the batch still spreads over every SM
+    const int64_t full = (int64_t)sm_count() * 32;  // resident warps at full occupancy
+    int qpw = (int)((Q + full - 1) / full);
+    if (qpw < 1) qpw = 1;
+    if (qpw > 32) qpw = 32;
+    int64_t warps = (Q + qpw - 1) / qpw;
     unsigned grid = (unsigned)((warps + kSearchWarps - 1) / kSearchWarps);
     const uint8_t* q = reinterpret_cast<const uint8_t*>(d_queries);
     if (x->N <= (1ll << 24)) {
-        LCP_LAUNCH(k_topk_search<uint32_t>, grid, kSearchWarps * 32, 0, s, ix, q, qf, Q, k, out_ids,
+        LCP_LAUNCH(k_topk_search<uint32_t>, grid, kSearchWarps * 32, 0, s, ix, q, qf, Q, k, qpw, out_ids,
                    out_lcp);
     } else {
-        LCP_LAUNCH(k_topk_search<uint64_t>, grid, kSearchWarps * 32, 0, s, ix, q, qf, Q, k, out_ids,
+        LCP_LAUNCH(k_topk_search<uint64_t>, grid, kSearchWarps * 32, 0, s, ix, q, qf, Q, k, qpw, out_ids,
                    out_lcp);
     }
     return LCP_OK;

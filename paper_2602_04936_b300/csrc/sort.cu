@@ -1,14 +1,14 @@
-// Onesweep-style LSD radix sort (8-bit digits) for the index build.
+// LSD radix sort (8-bit digits) for the index build.
 //
 // One upfront kernel builds the histograms of every digit position in a
-// single read of the keys (warp-aggregated with __match_any_sync so that the
-// heavily skewed digits of Zipf-distributed tokens do not serialise on shared
-// atomics).  Each digit pass is then ONE kernel: a CTA takes a 4096-key tile
-// (ticket from an atomic counter, so tiles start in order), ranks its keys
-// stably with warp multisplit, publishes its per-digit counts, and resolves
-// its global offsets by decoupled look-back over the predecessors' status
-// words.  Every wait in the look-back is bounded (kSpinLimit); on expiry the
-// kernel records DEV_TIMEOUT and finishes instead of spinning forever.
+// single read of the keys (warp-aggregated, so that the heavily skewed digits
+// of Zipf-distributed tokens do not serialise on shared memory); digits that are constant over all keys are skipped, decided on
+// the device.  Each remaining pass is reduce-then-scan: per-tile digit counts,
+// one exclusive scan per digit over the tiles, then a kernel that ranks its
+// tile stably (warp multisplit), stages it in shared memory by digit and
+// writes it out in coalesced runs.  No CTA waits for another: a chained scan
+// with look-back serialises the first wave of tiles that start together, and
+// a sort pass has only one or two waves.
 #include "sort.cuh"
 
 namespace lcpk {
@@ -21,13 +21,33 @@ constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
 
+// Digit histograms of every pass in one read.  Each warp counts into its own
+// shared-memory copy (warp-aggregated: lanes with equal digits are found with
+// ballots and one of them adds the group's count, so a hot digit costs one
+// update per warp instead of 32); each CTA writes its partial histogram, and
+// k_hist_reduce sums the partials (no contended atomics).
+// Lanes of the warp whose 8-bit digit equals this lane's (invalid lanes are
+// never peers).  Eight ballots: much cheaper than __match_any_sync.
+__device__ __forceinline__ unsigned digit_peers(uint32_t d, bool valid) {
+    unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const unsigned m = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? m : ~m;
+    }
+    return valid ? peers : 0u;
+}
+
 template <typename K>
 __global__ void __launch_bounds__(256) k_digit_hist(const K* __restrict__ keys, uint32_t n,
-                                                    uint32_t* __restrict__ hist, int passes) {
-    __shared__ uint32_t sh[8 * 256];
-    for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) sh[i] = 0;
+                                                    uint32_t* __restrict__ partial, int passes) {
+    extern __shared__ uint32_t wsh[];  // [8 warps][passes][256]
+    const int nw = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < nw * passes * 256; i += blockDim.x) wsh[i] = 0;
     __syncthreads();
     const unsigned lane = lane_id();
+    uint32_t* mine = wsh + (threadIdx.x >> 5) * passes * 256;
     const uint32_t warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t base = warp_global * 32; base < n; base += nwarps * 32) {
@@ -35,14 +55,27 @@ __global__ void __launch_bounds__(256) k_digit_hist(const K* __restrict__ keys, 
         bool valid = idx < n;
         K k = valid ? keys[idx] : (K)0;
         for (int p = 0; p < passes; ++p) {
-            uint32_t d = valid ? (uint32_t)(k >> (8 * p)) & 255u : 256u;
-            unsigned peers = __match_any_sync(0xffffffffu, d);
-            if (valid && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&sh[p * 256 + d], __popc(peers));
+            const uint32_t d = (uint32_t)(k >> (8 * p)) & 255u;
+            const unsigned peers = digit_peers(d, valid);
+            if (valid && lane == (unsigned)(__ffs(peers) - 1)) mine[p * 256 + d] += __popc(peers);
+            __syncwarp();
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x)
-        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
+        uint32_t t = 0;
+        for (int w = 0; w < nw; ++w) t += wsh[w * passes * 256 + i];
+        partial[(size_t)blockIdx.x * passes * 256 + i] = t;
+    }
+}
+
+__global__ void k_hist_reduce(const uint32_t* __restrict__ partial, int nparts, int bins,
+                              uint32_t* __restrict__ hist) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= bins) return;
+    uint32_t t = 0;
+    for (int b = 0; b < nparts; ++b) t += partial[(size_t)b * bins + i];
+    hist[i] = t;
 }
 
 // Exclusive scan of a 256-entry table by 256 threads.
@@ -80,11 +113,115 @@ __global__ void __launch_bounds__(256) k_digit_prefix(const uint32_t* __restrict
     if (threadIdx.x == 0) skip[p] = full ? 1u : 0u;
 }
 
+// Pass plan on the device: a pass whose digit is constant is skipped, so the
+// ping-pong buffer each pass reads depends on how many passes ran before it.
+// sel[p] = 1 if pass p reads buffer 1; sel[8] = 1 if the result is in buffer 1.
+__global__ void k_pass_plan(const uint32_t* __restrict__ skip, int passes, uint32_t* __restrict__ sel) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    uint32_t cur = 0;
+    for (int p = 0; p < passes; ++p) {
+        sel[p] = cur;
+        if (!skip[p]) cur ^= 1u;
+    }
+    sel[8] = cur;
+}
+
+// Moves the result into buffer 0 when an odd number of passes ran.
 template <typename K>
-__global__ void __launch_bounds__(kSortThreads) k_onesweep(
-    const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
-    uint32_t* __restrict__ vout, uint32_t n, int shift, const uint32_t* __restrict__ digit_base,
-    uint32_t* status, uint32_t* counter, int* err) {
+__global__ void k_result_to_buf0(const uint32_t* __restrict__ sel, const K* __restrict__ k1,
+                                 const uint32_t* __restrict__ v1, K* __restrict__ k0,
+                                 uint32_t* __restrict__ v0, uint32_t n) {
+    if (!sel[8]) return;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        k0[i] = k1[i];
+        v0[i] = v1[i];
+    }
+}
+
+// Per-tile digit counts of pass `pass`: counts[d * tiles + tile].
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) k_tile_counts(const K* kb0, const K* kb1, uint32_t n,
+                                                              int pass, const uint32_t* __restrict__ skip,
+                                                              const uint32_t* __restrict__ sel,
+                                                              uint32_t* __restrict__ counts, uint32_t tiles) {
+    if (skip[pass]) return;
+    __shared__ uint32_t wh[kSortWarps][256];
+    const K* __restrict__ kin = sel[pass] ? kb1 : kb0;
+    const int tid = threadIdx.x;
+    const unsigned lane = lane_id();
+    const int warp = tid >> 5;
+    for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&wh[0][0])[i] = 0;
+    const uint32_t tile = blockIdx.x;
+    const uint32_t base = tile * (uint32_t)kSortTile;
+    const uint32_t tile_n = min((uint32_t)kSortTile, n - base);
+    const int shift = 8 * pass;
+    K kk[kSortItems];
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const uint32_t idx = (uint32_t)warp * (32 * kSortItems) + (uint32_t)i * 32 + lane;
+        kk[i] = idx < tile_n ? kin[base + idx] : (K)0;
+    }
+    __syncthreads();  // zeroed counters visible
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const uint32_t idx = (uint32_t)warp * (32 * kSortItems) + (uint32_t)i * 32 + lane;
+        const bool valid = idx < tile_n;
+        const uint32_t d = (uint32_t)(kk[i] >> shift) & 255u;
+        const unsigned peers = digit_peers(d, valid);
+        if (valid && lane == (unsigned)(__ffs(peers) - 1)) wh[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    uint32_t t = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) t += wh[w][tid];
+    counts[(size_t)tid * tiles + tile] = t;
+}
+
+// Exclusive scan of each digit's counts over the tiles, offset by the digit's
+// global base: one CTA per digit.
+__global__ void __launch_bounds__(1024) k_tile_scan(int pass, const uint32_t* __restrict__ skip,
+                                                    uint32_t* __restrict__ counts, uint32_t tiles,
+                                                    const uint32_t* __restrict__ digit_base_all) {
+    if (skip[pass]) return;
+    __shared__ uint32_t tmp[32];
+    __shared__ uint32_t carry;
+    const int d = blockIdx.x;
+    uint32_t* col = counts + (size_t)d * tiles;
+    if (threadIdx.x == 0) carry = digit_base_all[pass * 256 + d];
+    __syncthreads();
+    for (uint32_t b0 = 0; b0 < tiles; b0 += 1024) {
+        const uint32_t i = b0 + threadIdx.x;
+        const uint32_t v = i < tiles ? col[i] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane_id() >= (unsigned)o) x += y;
+        }
+        if (lane_id() == 31) tmp[threadIdx.x >> 5] = x;
+        __syncthreads();
+        uint32_t add = carry;
+        for (unsigned w = 0; w < (threadIdx.x >> 5); ++w) add += tmp[w];
+        if (i < tiles) col[i] = add + x - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = add + x;
+        __syncthreads();
+    }
+}
+
+// Stable scatter of one tile for pass `pass`, at the offsets from k_tile_scan.
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
+    K* kb0, uint32_t* vb0, K* kb1, uint32_t* vb1, uint32_t n, int pass, const uint32_t* __restrict__ skip,
+    const uint32_t* __restrict__ sel, const uint32_t* __restrict__ offsets, uint32_t tiles, int* err) {
+    if (skip[pass]) return;  // constant digit: nothing moves
+    const bool from1 = sel[pass] != 0;
+    const K* __restrict__ kin = from1 ? kb1 : kb0;
+    const uint32_t* __restrict__ vin = from1 ? vb1 : vb0;
+    K* __restrict__ kout = from1 ? kb0 : kb1;
+    uint32_t* __restrict__ vout = from1 ? vb0 : vb1;
+    const int shift = 8 * pass;
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* whist = reinterpret_cast<uint32_t*>(smem);  // [warps][256]
     uint32_t* tcount = whist + kSortWarps * 256;           // [256]
@@ -97,26 +234,35 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const int tid = threadIdx.x;
     const unsigned lane = lane_id();
     const int warp = tid >> 5;
-    if (tid == 0) misc[0] = atomicAdd(counter, 1u);
-    for (int i = tid; i < kSortWarps * 256; i += kSortThreads) whist[i] = 0;
-    __syncthreads();
-    const uint32_t tile = misc[0];
+    const uint32_t tile = blockIdx.x;
     const uint32_t base = tile * (uint32_t)kSortTile;
     const uint32_t tile_n = min((uint32_t)kSortTile, n - base);
-
+    // every global load of the tile is issued before any ranking work
+    const uint32_t toff = offsets[(size_t)tid * tiles + tile];
     K key[kSortItems];
     uint32_t val[kSortItems];
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const uint32_t idx = (uint32_t)warp * (32 * kSortItems) + (uint32_t)i * 32 + lane;
+        key[i] = idx < tile_n ? kin[base + idx] : (K)0;
+    }
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const uint32_t idx = (uint32_t)warp * (32 * kSortItems) + (uint32_t)i * 32 + lane;
+        val[i] = idx < tile_n ? vin[base + idx] : 0u;
+    }
+    for (int i = tid; i < kSortWarps * 256; i += kSortThreads) whist[i] = 0;
+    __syncthreads();
+
     uint32_t rk[kSortItems];
     uint32_t* wh = whist + warp * 256;
     const unsigned lt = lanemask_lt();
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
-        uint32_t idx = (uint32_t)warp * (32 * kSortItems) + (uint32_t)i * 32 + lane;
-        bool valid = idx < tile_n;
-        key[i] = valid ? kin[base + idx] : (K)0;
-        val[i] = valid ? vin[base + idx] : 0u;
-        uint32_t d = valid ? (uint32_t)(key[i] >> shift) & 255u : 256u;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t idx = (uint32_t)warp * (32 * kSortItems) + (uint32_t)i * 32 + lane;
+        const bool valid = idx < tile_n;
+        const uint32_t d = (uint32_t)(key[i] >> shift) & 255u;
+        const unsigned peers = digit_peers(d, valid);
         uint32_t prior = valid ? wh[d] : 0u;
         __syncwarp();
         if (valid && lane == (unsigned)(__ffs(peers) - 1)) wh[d] = prior + __popc(peers);
@@ -138,34 +284,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     uint32_t my = tcount[tid];
     uint32_t ls = block_excl_scan_256(my, misc + 8);
     lstart[tid] = ls;
-    // decoupled look-back for digit tid
-    {
-        uint32_t excl = 0;
-        uint32_t* st = status + (size_t)tile * 256 + tid;
-        if (tile == 0) {
-            st_relaxed(st, kFlagInc | my);
-        } else {
-            st_relaxed(st, kFlagAgg | my);
-            int64_t j = (int64_t)tile - 1;
-            long long spins = 0;
-            while (j >= 0) {
-                uint32_t s = ld_relaxed(status + (size_t)j * 256 + tid);
-                uint32_t fl = s & ~kValMask;
-                if (fl == 0) {
-                    if (++spins > kSpinLimit) {
-                        flag_status(err, DEV_TIMEOUT);
-                        break;
-                    }
-                    continue;
-                }
-                excl += s & kValMask;
-                if (fl == kFlagInc) break;
-                --j;
-            }
-            st_relaxed(st, kFlagInc | ((excl + my) & kValMask));
-        }
-        goff[tid] = digit_base[tid] + excl - ls;  // modulo 2^32
-    }
+    goff[tid] = toff - ls;  // modulo 2^32
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
@@ -327,9 +446,11 @@ int sort_work_alloc(SortWork& w, uint32_t cap, int* err, cudaStream_t s) {
     if (tiles == 0) tiles = 1;
     if (nb == 0) nb = 1;
     LCP_CUDA_TRY(cudaMallocAsync((void**)&w.hist, sizeof(uint32_t) * kMaxPasses * 256, s));
+    LCP_CUDA_TRY(cudaMallocAsync((void**)&w.hist_parts, sizeof(uint32_t) * kHistParts * kMaxPasses * 256, s));
     LCP_CUDA_TRY(cudaMallocAsync((void**)&w.digit_base, sizeof(uint32_t) * kMaxPasses * 256, s));
     LCP_CUDA_TRY(cudaMallocAsync((void**)&w.skip, sizeof(uint32_t) * kMaxPasses, s));
-    LCP_CUDA_TRY(cudaMallocAsync((void**)&w.status, sizeof(uint32_t) * kMaxPasses * tiles * 256, s));
+    LCP_CUDA_TRY(cudaMallocAsync((void**)&w.sel, sizeof(uint32_t) * (kMaxPasses + 1), s));
+    LCP_CUDA_TRY(cudaMallocAsync((void**)&w.status, sizeof(uint32_t) * tiles * 256, s));
     LCP_CUDA_TRY(cudaMallocAsync((void**)&w.counters, sizeof(uint32_t) * kMaxPasses, s));
     LCP_CUDA_TRY(cudaMallocAsync((void**)&w.block_sums, sizeof(uint64_t) * nb, s));
     LCP_CUDA_TRY(cudaMallocAsync((void**)&w.total, sizeof(uint32_t) * 16, s));
@@ -340,8 +461,10 @@ int sort_work_alloc(SortWork& w, uint32_t cap, int* err, cudaStream_t s) {
 
 void sort_work_free(SortWork& w, cudaStream_t s) {
     cudaFreeAsync(w.hist, s);
+    cudaFreeAsync(w.hist_parts, s);
     cudaFreeAsync(w.digit_base, s);
     cudaFreeAsync(w.skip, s);
+    cudaFreeAsync(w.sel, s);
     cudaFreeAsync(w.status, s);
     cudaFreeAsync(w.counters, s);
     cudaFreeAsync(w.block_sums, s);
@@ -349,6 +472,7 @@ void sort_work_free(SortWork& w, cudaStream_t s) {
     w = SortWork();
 }
 
+// Sync-free LSD radix sort: the result always ends in buffers 0.
 template <typename K>
 static int radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, uint32_t n, int key_bits,
                            SortWork& w, cudaStream_t s, K** out_k, uint32_t** out_v) {
@@ -359,43 +483,29 @@ static int radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, uint32_t n,
     int passes = (key_bits + 7) / 8;
     if (passes > (int)(sizeof(K))) passes = (int)sizeof(K);
     if (passes < 1) return LCP_OK;
-    LCP_CUDA_TRY(cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * passes * 256, s));
-    int grid = (int)((n + 255) / 256);
-    if (grid > 148 * 8) grid = 148 * 8;
-    LCP_LAUNCH(k_digit_hist<K>, grid, 256, 0, s, k0, n, w.hist, passes);
+    int grid = (int)((n + 2047) / 2048);
+    if (grid > kHistParts) grid = kHistParts;
+    const size_t hsm = sizeof(uint32_t) * 8 * passes * 256;
+    LCP_CUDA_TRY(cudaFuncSetAttribute(k_digit_hist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
+    LCP_LAUNCH(k_digit_hist<K>, grid, 256, hsm, s, k0, n, w.hist_parts, passes);
+    LCP_LAUNCH(k_hist_reduce, (passes * 256 + 255) / 256, 256, 0, s, w.hist_parts, grid, passes * 256, w.hist);
     LCP_LAUNCH(k_digit_prefix, passes, 256, 0, s, w.hist, w.digit_base, w.skip, n);
-    LCP_CUDA_TRY(cudaMemcpyAsync(w.h_total, w.skip, sizeof(uint32_t) * passes,
-                                 cudaMemcpyDeviceToHost, s));
-    LCP_CUDA_TRY(cudaStreamSynchronize(s));
-    int run[kMaxPasses], nrun = 0;
-    for (int p = 0; p < passes; ++p)
-        if (!w.h_total[p]) run[nrun++] = p;
-    if (nrun == 0) return LCP_OK;
-    uint32_t tiles = (n + kSortTile - 1) / kSortTile;
-    LCP_CUDA_TRY(cudaMemsetAsync(w.status, 0, sizeof(uint32_t) * (size_t)nrun * tiles * 256, s));
-    LCP_CUDA_TRY(cudaMemsetAsync(w.counters, 0, sizeof(uint32_t) * kMaxPasses, s));
-    size_t smem = sizeof(uint32_t) * (kSortWarps * 256 + 3 * 256 + 16) +
-                  (sizeof(K) + sizeof(uint32_t)) * kSortTile;
+    LCP_LAUNCH(k_pass_plan, 1, 32, 0, s, w.skip, passes, w.sel);
+    const uint32_t tiles = (n + kSortTile - 1) / kSortTile;
+    const size_t smem = sizeof(uint32_t) * (kSortWarps * 256 + 3 * 256 + 16) +
+                        (sizeof(K) + sizeof(uint32_t)) * kSortTile;
     LCP_CUDA_TRY(cudaFuncSetAttribute(k_onesweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-    K* ki = k0;
-    uint32_t* vi = v0;
-    K* ko = k1;
-    uint32_t* vo = v1;
-    for (int r = 0; r < nrun; ++r) {
-        int p = run[r];
-        LCP_LAUNCH(k_onesweep<K>, tiles, kSortThreads, smem, s, ki, vi, ko, vo, n, 8 * p,
-                   w.digit_base + p * 256, w.status + (size_t)r * tiles * 256, w.counters + r,
-                   w.err);
-        K* tk = ki;
-        ki = ko;
-        ko = tk;
-        uint32_t* tv = vi;
-        vi = vo;
-        vo = tv;
+    for (int p = 0; p < passes; ++p) {
+        LCP_LAUNCH(k_tile_counts<K>, tiles, kSortThreads, 0, s, k0, k1, n, p, w.skip, w.sel, w.status,
+                   tiles);
+        LCP_LAUNCH(k_tile_scan, 256, 1024, 0, s, p, w.skip, w.status, tiles, w.digit_base);
+        LCP_LAUNCH(k_onesweep<K>, tiles, kSortThreads, smem, s, k0, v0, k1, v1, n, p, w.skip, w.sel,
+                   w.status, tiles, w.err);
     }
-    *out_k = ki;
-    *out_v = vi;
+    unsigned cg = (unsigned)((n + 255) / 256);
+    if (cg > (unsigned)sm_count() * 8) cg = sm_count() * 8;
+    LCP_LAUNCH(k_result_to_buf0<K>, cg, 256, 0, s, w.sel, k1, v1, k0, v0, n);
     return LCP_OK;
 }
 

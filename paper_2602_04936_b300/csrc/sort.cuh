@@ -6,18 +6,21 @@
 namespace lcph {
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
+constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per onesweep tile
 constexpr int kMaxPasses = 8;                         // 8-bit digits of a 64-bit key
+constexpr int kHistParts = 296;                       // CTAs of the histogram kernel (max)
 
 // Device scratch for sorting up to `cap` pairs (allocated stream-ordered).
 struct SortWork {
     uint32_t cap = 0;
     uint32_t* hist = nullptr;        // [kMaxPasses][256]
+    uint32_t* hist_parts = nullptr;  // [kHistParts][kMaxPasses][256] per-CTA partials
     uint32_t* digit_base = nullptr;  // [kMaxPasses][256]
     uint32_t* skip = nullptr;        // [kMaxPasses] 1 if the digit is constant
-    uint32_t* status = nullptr;      // [kMaxPasses][tiles][256] look-back words
-    uint32_t* counters = nullptr;    // [kMaxPasses] tile tickets
+    uint32_t* sel = nullptr;         // [kMaxPasses + 1] ping-pong plan (device-decided)
+    uint32_t* status = nullptr;      // [256][tiles] per-tile digit counts, then offsets
+    uint32_t* counters = nullptr;    // unused (kept for layout)
     uint64_t* block_sums = nullptr;  // compaction: per-block (active, starts) counts
     uint32_t* total = nullptr;       // compaction result count (device)
     uint32_t* h_total = nullptr;     // pinned host mirror of total + skip flags
@@ -28,9 +31,9 @@ int sort_work_alloc(SortWork& w, uint32_t cap, int* err, cudaStream_t s);
 void sort_work_free(SortWork& w, cudaStream_t s);
 
 // Stable LSD radix sort of (key, value) pairs by the low `key_bits` bits of
-// the key.  Buffers 0 hold the input; the result lands in buffers 0 or 1,
-// returned through out_k / out_v.  Digits that are equal for every key are
-// skipped (the host reads one 8-entry flag array, so the call blocks briefly).
+// the key.  Buffers 0 hold the input and receive the result (out_k / out_v
+// point at them); buffers 1 are scratch.  Digits equal for every key are
+// skipped on the device; the call never waits for the device.
 int radix_sort_pairs_u64(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, uint32_t n,
                          int key_bits, SortWork& w, cudaStream_t s, uint64_t** out_k,
                          uint32_t** out_v);
