@@ -76,7 +76,7 @@ static void free_index_memory(lcp_index_s* x, cudaStream_t s) {
                     x->buf[1].rows, x->buf[1].head, x->buf[1].ids, x->buf[1].H,
                     x->pos, x->hmin, x->sblk, x->soff, x->st, x->bkt, x->status,
                     x->tbl, x->slot_flag, x->slot_lo, x->slot_hi, x->slot_list, x->tlists,
-                    x->tl_lo, x->tl_hi, x->tl_sums, x->tl_total,
+                    x->tl_lo, x->tl_hi, x->tl_sums, x->tl_total, x->tlpos, x->bkt_list,
                     x->ins_rows, x->ins_ids, x->ins_rank};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, s);
@@ -131,6 +131,8 @@ static int alloc_index(lcp_index_s* x, int64_t N, int64_t cap, cudaStream_t s) {
     if ((rc = dalloc(&x->tl_sums, (nslots + 2047) / 2048, &by, s))) return rc;
     if ((rc = dalloc(&x->tl_total, 4, &by, s))) return rc;
     if ((rc = dalloc(&x->tlists, (size_t)x->nlists_cap * x->K, &by, s))) return rc;
+    if ((rc = dalloc(&x->tlpos, (size_t)x->nlists_cap * x->K, &by, s))) return rc;
+    if ((rc = dalloc(&x->bkt_list, (size_t)1 << x->bits, &by, s))) return rc;
     if ((rc = dalloc(&x->tl_lo, (size_t)x->nlists_cap, &by, s))) return rc;
     if ((rc = dalloc(&x->tl_hi, (size_t)x->nlists_cap, &by, s))) return rc;
     if ((rc = dalloc(&x->status, 1, &by, s))) return rc;

@@ -546,6 +546,8 @@ DevIndex dev_view(const lcp_index_s* x) {
     d.bkt = x->bkt;
     d.tbl = x->tbl;
     d.tlists = x->tlists;
+    d.tlpos = x->tlpos;
+    d.bkt_list = x->bkt_list;
     d.L1 = x->L + 1;
     d.status = x->status;
     return d;

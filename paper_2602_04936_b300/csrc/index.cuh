@@ -22,9 +22,13 @@
 //   tbl  [N/128][L+1] i32  tie lists of heavy trie nodes: the LCP interval of
 //                       depth d around sample position 128*s, if it holds more
 //                       than 128 rows, has its K smallest ids (ascending) in
-//                       tlists[tbl[s][d]]; -1 otherwise.  Every trie node of
+//                       tlists[tbl[s][d]] and their sorted positions in
+//                       tlpos[tbl[s][d]]; -1 otherwise.  Every trie node of
 //                       more than 128 rows contains a sample, so the indexed
 //                       search finds the level-d* list with one lookup.
+//   bkt_list [2^bits] i32  the list of each depth-1 bucket (-1 if light), so
+//                       that the common d* = 1 case reads bounds and list
+//                       number in one round trip.
 #pragma once
 
 #include "common.cuh"
@@ -58,6 +62,8 @@ struct DevIndex {
     const int32_t* bkt;
     const int32_t* tbl;
     const uint32_t* tlists;
+    const int32_t* tlpos;
+    const int32_t* bkt_list;
     int L1;  // L + 1: row length of tbl
     int* status;
 };
@@ -94,6 +100,8 @@ struct lcp_index_s {
     int32_t* slot_hi = nullptr;
     int32_t* slot_list = nullptr;  // list index of each canonical slot
     uint32_t* tlists = nullptr;    // [nlists_cap][K]
+    int32_t* tlpos = nullptr;      // [nlists_cap][K] sorted position of each entry
+    int32_t* bkt_list = nullptr;   // [2^bits] list of each depth-1 bucket
     int32_t* tl_lo = nullptr;      // interval of each list
     int32_t* tl_hi = nullptr;
     uint64_t* tl_sums = nullptr;   // scan block sums

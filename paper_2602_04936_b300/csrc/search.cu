@@ -105,41 +105,126 @@ __device__ bool probe_ids(const DevIndex& ix, int64_t lov, int64_t hiv, int64_t 
     return false;
 }
 
-// ---- one query, whole warp ----
+// ---- the query's position: one lane per query ----
 
-template <typename KT>
-__device__ void topk_one(const DevIndex& ix, QWarp& S, const uint8_t* qrow, const RowFmt& qf, int64_t P0,
-                         int64_t P1, int lL_head, int lR_head, int tok0, int k,
-                         int32_t* __restrict__ oid, uint8_t* __restrict__ olcp) {
-    const unsigned lane = lane_id();
+// Compares a sorted row with the query from word w0 on: -1 row < q, 0 equal,
+// +1 row > q; *lcp = LCP(q, row) (given that words before w0 are equal).
+__device__ __forceinline__ int lane_cmp_from(const DevIndex& ix, const uint64_t* __restrict__ row,
+                                             const uint8_t* qrow, const RowFmt& qf, int w0, int* lcp) {
+    for (int w = w0; w < ix.W; ++w) {
+        const uint64_t a = row[w], b = pack_word(qrow, w, qf);
+        if (a != b) {
+            const int l = w * ix.tpw + (__clzll((long long)(a ^ b)) / ix.bits);
+            *lcp = l < ix.L ? l : ix.L;
+            return a < b ? -1 : 1;
+        }
+    }
+    *lcp = ix.L;
+    return 0;
+}
+
+// Algorithm 3's descent in array form, by one lane: the insertion point p
+// (first row >= q) and the LCPs of q with rows p-1 and p (-1 where absent).
+// Word 0 alone decides everything unless some row shares it with q; then a
+// binary search inside that equal-head range compares the later words.
+__device__ __forceinline__ void lane_locate(const DevIndex& ix, const uint8_t* qrow, const RowFmt& qf,
+                                            uint64_t q0, int64_t* p_out, int* lL_out, int* lR_out) {
     const int64_t N = ix.N;
-    int64_t p = P0;
-    int lL = lL_head, lR = lR_head;
-    if (P1 > P0) {
-        // 2. lower bound inside the equal-head range, then both neighbours' LCPs
-        for (int w = (int)lane; w < ix.W; w += 32) S.q[w] = pack_word(qrow, w, qf);
-        __syncwarp();
-        int64_t lo = P0, hi = P1;
+    int64_t lo = 0, hi = N;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (ix.head[mid] < q0) lo = mid + 1;
+        else hi = mid;
+    }
+    const int64_t p0 = lo;
+    int64_t p1 = p0;
+    if (p0 < N && ix.head[p0] == q0) {  // gallop to the end of the equal-head range
+        int64_t step = 1, last = p0;
+        while (last + step < N && ix.head[last + step] == q0) {
+            last += step;
+            step <<= 1;
+        }
+        lo = last + 1;
+        hi = last + step < N ? last + step : N;
         while (lo < hi) {
-            int64_t mid = (lo + hi) >> 1;
+            const int64_t mid = (lo + hi) >> 1;
+            if (ix.head[mid] <= q0) lo = mid + 1;
+            else hi = mid;
+        }
+        p1 = lo;
+    }
+    int64_t p = p0;
+    if (p1 > p0) {
+        lo = p0;
+        hi = p1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
             int l;
-            if (warp_cmp_row(ix.rows + mid * ix.W, S.q, ix, &l) < 0) lo = mid + 1;
+            if (lane_cmp_from(ix, ix.rows + mid * ix.W, qrow, qf, 1, &l) < 0) lo = mid + 1;
             else hi = mid;
         }
         p = lo;
-        warp_lcp_neighbours(ix, p, S.q, &lL, &lR);
     }
+    int lL = -1, lR = -1;
+    if (p > 0) {
+        if (p - 1 >= p0) lane_cmp_from(ix, ix.rows + (p - 1) * ix.W, qrow, qf, 1, &lL);
+        else lL = __clzll((long long)(ix.head[p - 1] ^ q0)) / ix.bits;
+    }
+    if (p < N) {
+        if (p < p1) lane_cmp_from(ix, ix.rows + p * ix.W, qrow, qf, 1, &lR);
+        else lR = __clzll((long long)(ix.head[p] ^ q0)) / ix.bits;
+    }
+    *p_out = p;
+    *lL_out = lL;
+    *lR_out = lR;
+}
+
+// Position record of one query, written by k_topk_locate.
+struct alignas(16) QLoc {
+    int64_t p;
+    int16_t lL, lR;
+    int32_t tok0;
+};
+
+__global__ void __launch_bounds__(256) k_topk_locate(DevIndex ix, const uint8_t* __restrict__ queries,
+                                                     RowFmt qf, int64_t Q, QLoc* __restrict__ loc) {
+    const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= Q) return;
+    const uint8_t* qrow = row_of(queries, qi, qf);
+    const uint64_t q0 = pack_word(qrow, 0, qf);
+    int64_t p;
+    int lL, lR;
+    lane_locate(ix, qrow, qf, q0, &p, &lL, &lR);
+    QLoc r;
+    r.p = p;
+    r.lL = (int16_t)lL;
+    r.lR = (int16_t)lR;
+    r.tok0 = (int32_t)(q0 >> (64 - ix.bits));
+    loc[qi] = r;
+}
+
+// ---- one query, whole warp ----
+
+template <typename KT>
+__device__ void topk_one(const DevIndex& ix, QWarp& S, int64_t p, int lL, int lR, int tok0, int k,
+                         int32_t* __restrict__ oid, uint8_t* __restrict__ olcp) {
+    const unsigned lane = lane_id();
+    const int64_t N = ix.N;
     // 3. expansion
     const int64_t availL = p, availR = N - p;
     int nL = 0, nR = 0, dstar = 0;
-    {
-        int hl, hr;
-        uint32_t il, ir;
-        bool okl, okr;
+    {  // first round: 64 rows per side, all four chunks in flight at once
+        int hl, hr, hl2, hr2;
+        uint32_t il, ir, il2, ir2;
+        bool okl, okr, okl2, okr2;
         issue_chunk<true>(ix, p, 0, availL, lL, hl, il, okl);
         issue_chunk<false>(ix, p, 0, availR, lR, hr, ir, okr);
+        issue_chunk<true>(ix, p, 32, availL, lL, hl2, il2, okl2);
+        issue_chunk<false>(ix, p, 32, availR, lR, hr2, ir2, okr2);
         nL += finish_chunk(hl, il, okl, 0, availL, S.lid, S.llam);
         nR += finish_chunk(hr, ir, okr, 0, availR, S.rid, S.rlam);
+        if (nL == 32) nL += finish_chunk(hl2, il2, okl2, 32, availL, S.lid, S.llam);
+        if (nR == 32) nR += finish_chunk(hr2, ir2, okr2, 32, availR, S.rid, S.rlam);
     }
     for (;;) {
         const int bL = nL < availL ? (int)S.llam[nL - 1] : -1;
@@ -179,9 +264,11 @@ __device__ void topk_one(const DevIndex& ix, QWarp& S, const uint8_t* qrow, cons
     const int aR = count_ge(S.rlam, nR, dstar + 1);
     const int nA = aL + aR;
     int64_t lov = 0, hiv = N;
-    if (dstar == 1) {  // depth-1 bucket of q's first token
+    int li = -2;  // tie list of the level-d* node (-2: not looked up yet)
+    if (dstar == 1) {  // depth-1 bucket of q's first token, bounds and list in one trip
         lov = ix.bkt[tok0];
         hiv = ix.bkt[tok0 + 1];
+        li = ix.bkt_list[tok0];
     } else if (dstar > 1) {
         const int vL = count_ge(S.llam, nL, dstar);
         const int vR = count_ge(S.rlam, nR, dstar);
@@ -202,23 +289,23 @@ __device__ void topk_one(const DevIndex& ix, QWarp& S, const uint8_t* qrow, cons
     // a tie level holding a large share of all rows: probe ids in order
     // (expected <= 6 chunks of 128 ids)
     if (!filled && (int64_t)kp * N <= nT * 768) filled = probe_ids(ix, lov, hiv, loc, hic, kp, S.m1, &ntake);
-    // a heavy trie node: its precomputed K smallest ids, minus A's members
+    // a heavy trie node: its precomputed K smallest ids (with their sorted
+    // positions), minus A's members
     if (!filled && hiv - lov > kBlk) {
-        const int64_t smp = (lov + kBlk - 1) / kBlk;
-        const int li = ix.tbl[smp * ix.L1 + dstar];
+        if (li == -2) li = ix.tbl[((lov + kBlk - 1) / kBlk) * ix.L1 + dstar];
         if (li >= 0) {
             const uint32_t* list = ix.tlists + (size_t)li * ix.K;
+            const int32_t* lpos = ix.tlpos + (size_t)li * ix.K;
             const int need = nA + kp;
             uint32_t v[4];
+            int32_t ps[4];
             bool keep[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int t = (int)lane + 32 * e;
                 v[e] = t < need ? list[t] : kInf;
+                ps[e] = t < need ? lpos[t] : -1;
             }
-            int64_t ps[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) ps[e] = v[e] != kInf ? (int64_t)ix.pos[v[e]] : -1;
 #pragma unroll
             for (int e = 0; e < 4; ++e) keep[e] = v[e] != kInf && (ps[e] < loc || ps[e] >= hic);
             ntake = compact4(v, keep, S.m1, kp);
@@ -248,7 +335,6 @@ __device__ void topk_one(const DevIndex& ix, QWarp& S, const uint8_t* qrow, cons
     // 5. A sorted by (LCP desc, id asc), then the tie fill, then padding
     if (nA > 0) {
         if (nA <= 32) sort_and_write_A<1, KT>(S, aL, nA, oid, olcp);
-        else if (nA <= 64) sort_and_write_A<2, KT>(S, aL, nA, oid, olcp);
         else sort_and_write_A<4, KT>(S, aL, nA, oid, olcp);
     }
     for (int r = nA + (int)lane; r < k; r += 32) {
@@ -265,63 +351,19 @@ __device__ void topk_one(const DevIndex& ix, QWarp& S, const uint8_t* qrow, cons
 }
 
 template <typename KT>
-__global__ void __launch_bounds__(kSearchWarps * 32, 8) k_topk_search(DevIndex ix,
-                                                                   const uint8_t* __restrict__ queries,
-                                                                   RowFmt qf, int64_t Q, int k, int qpw,
-                                                                   int32_t* __restrict__ out_ids,
-                                                                   uint8_t* __restrict__ out_lcp) {
+__global__ void __launch_bounds__(kSearchWarps * 32, 8) k_topk_answer(DevIndex ix, const QLoc* __restrict__ loc,
+                                                                      int64_t Q, int k, int qpw,
+                                                                      int32_t* __restrict__ out_ids,
+                                                                      uint8_t* __restrict__ out_lcp) {
     __shared__ QWarp sm[kSearchWarps];
     const int warp = threadIdx.x >> 5;
-    const unsigned lane = lane_id();
     QWarp& S = sm[warp];
     const int64_t wq0 = ((int64_t)blockIdx.x * kSearchWarps + warp) * qpw;
-    if (wq0 >= Q) return;
-    // 1. lane-per-query search on head (lanes < qpw): lower bound, then gallop
-    //    to the upper bound
-    const int64_t myq = wq0 + lane;
-    const bool has = (int)lane < qpw && myq < Q;
-    const uint64_t q0 = has ? pack_word(row_of(queries, myq, qf), 0, qf) : 0;
-    const int64_t N = ix.N;
-    int64_t lo = 0, hi = N;
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (ix.head[mid] < q0) lo = mid + 1;
-        else hi = mid;
-    }
-    const int64_t p0 = lo;
-    int64_t p1 = p0;
-    if (p0 < N && ix.head[p0] == q0) {
-        int64_t step = 1, last = p0;  // head[last] == q0
-        while (last + step < N && ix.head[last + step] == q0) {
-            last += step;
-            step <<= 1;
-        }
-        lo = last + 1;
-        hi = last + step < N ? last + step : N;
-        while (lo < hi) {
-            int64_t mid = (lo + hi) >> 1;
-            if (ix.head[mid] <= q0) lo = mid + 1;
-            else hi = mid;
-        }
-        p1 = lo;
-    }
-    // neighbours' LCPs from the heads when no row shares word 0 with q
-    int lLh = -1, lRh = -1;
-    if (p1 == p0) {  // heads differ from q0, so the first differing word is word 0
-        if (p0 > 0) lLh = __clzll((long long)(ix.head[p0 - 1] ^ q0)) / ix.bits;
-        if (p0 < N) lRh = __clzll((long long)(ix.head[p0] ^ q0)) / ix.bits;
-    }
-    const int tok = (int)(q0 >> (64 - ix.bits));
     for (int j = 0; j < qpw; ++j) {
         const int64_t qi = wq0 + j;
         if (qi >= Q) break;
-        const int64_t P0 = __shfl_sync(0xffffffffu, p0, j);
-        const int64_t P1 = __shfl_sync(0xffffffffu, p1, j);
-        const int l0 = __shfl_sync(0xffffffffu, lLh, j);
-        const int r0 = __shfl_sync(0xffffffffu, lRh, j);
-        const int t0 = __shfl_sync(0xffffffffu, tok, j);
-        topk_one<KT>(ix, S, row_of(queries, qi, qf), qf, P0, P1, l0, r0, t0, k, out_ids + qi * k,
-                     out_lcp + qi * k);
+        const QLoc r = loc[qi];
+        topk_one<KT>(ix, S, r.p, r.lL, r.lR, r.tok0, k, out_ids + qi * k, out_lcp + qi * k);
     }
 }
 
@@ -340,22 +382,26 @@ int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, i
     }
     DevIndex ix = dev_view(x);
     RowFmt qf = make_fmt(x->tb, x->L, d_queries);
-    // queries per warp: 32 for large batches (phase 1 uses every lane); fewer
-    // for small batches so that the batch still spreads over every SM
+    const uint8_t* q = reinterpret_cast<const uint8_t*>(d_queries);
+    QLoc* loc = nullptr;
+    LCP_CUDA_TRY(cudaMallocAsync((void**)&loc, sizeof(QLoc) * (size_t)Q, s));
+    LCP_LAUNCH(k_topk_locate, (unsigned)((Q + 255) / 256), 256, 0, s, ix, q, qf, Q, loc);
+    // queries per warp: 32 for large batches; fewer for small batches so that
+    // the batch still spreads over every SM
     const int64_t full = (int64_t)sm_count() * 32;  // resident warps at full occupancy
     int qpw = (int)((Q + full - 1) / full);
     if (qpw < 1) qpw = 1;
     if (qpw > 32) qpw = 32;
-    int64_t warps = (Q + qpw - 1) / qpw;
-    unsigned grid = (unsigned)((warps + kSearchWarps - 1) / kSearchWarps);
-    const uint8_t* q = reinterpret_cast<const uint8_t*>(d_queries);
+    const int64_t warps = (Q + qpw - 1) / qpw;
+    const unsigned grid = (unsigned)((warps + kSearchWarps - 1) / kSearchWarps);
     if (x->N <= (1ll << 24)) {
-        LCP_LAUNCH(k_topk_search<uint32_t>, grid, kSearchWarps * 32, 0, s, ix, q, qf, Q, k, qpw, out_ids,
+        LCP_LAUNCH(k_topk_answer<uint32_t>, grid, kSearchWarps * 32, 0, s, ix, loc, Q, k, qpw, out_ids,
                    out_lcp);
     } else {
-        LCP_LAUNCH(k_topk_search<uint64_t>, grid, kSearchWarps * 32, 0, s, ix, q, qf, Q, k, qpw, out_ids,
+        LCP_LAUNCH(k_topk_answer<uint64_t>, grid, kSearchWarps * 32, 0, s, ix, loc, Q, k, qpw, out_ids,
                    out_lcp);
     }
+    LCP_CUDA_TRY(cudaFreeAsync(loc, s));
     return LCP_OK;
 }
 

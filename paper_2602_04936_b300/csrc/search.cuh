@@ -14,7 +14,7 @@ constexpr int kKMax = LCP_INDEX_MAX_K;
 constexpr int kSide = kKMax + 64;  // loaded items per side stay below k + 32
 
 struct alignas(16) QWarp {
-    uint64_t q[kMaxW];
+
     uint32_t lid[kSide];
     uint32_t rid[kSide];
     uint32_t src[4][kKMax];

@@ -141,14 +141,29 @@ __global__ void __launch_bounds__(256) k_flag_assign(const uint8_t* __restrict__
 __global__ void __launch_bounds__(kTlWarps * 32) k_node_lists(DevIndex ix, const uint32_t* __restrict__ total,
                                                               int64_t cap, const int32_t* __restrict__ tl_lo,
                                                               const int32_t* __restrict__ tl_hi,
-                                                              uint32_t* __restrict__ lists) {
+                                                              uint32_t* __restrict__ lists,
+                                                              int32_t* __restrict__ lpos) {
     __shared__ QWarp sm[kTlWarps];
     const int64_t w = (int64_t)blockIdx.x * kTlWarps + (threadIdx.x >> 5);
     const int64_t m = *total < (uint64_t)cap ? (int64_t)*total : cap;
     if (w >= m) return;
     QWarp& S = sm[threadIdx.x >> 5];
     const int cm = smallest_ids(ix, tl_lo[w], tl_hi[w], ix.K, S);
-    for (int t = (int)lane_id(); t < ix.K; t += 32) lists[w * ix.K + t] = t < cm ? S.src[0][t] : kInf;
+    for (int t = (int)lane_id(); t < ix.K; t += 32) {
+        const uint32_t id = t < cm ? S.src[0][t] : kInf;
+        lists[w * ix.K + t] = id;
+        lpos[w * ix.K + t] = id != kInf ? ix.pos[id] : -1;
+    }
+}
+
+// List of each depth-1 bucket (its interval at depth 1), -1 if light.
+__global__ void k_bucket_lists(DevIndex ix, int64_t ntok, int32_t* __restrict__ bkt_list) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntok) return;
+    const int64_t lo = ix.bkt[t], hi = ix.bkt[t + 1];
+    int32_t li = -1;
+    if (hi - lo > kBlk) li = ix.tbl[((lo + kBlk - 1) / kBlk) * ix.L1 + 1];
+    bkt_list[t] = li;
 }
 
 __global__ void k_remap_tbl(int32_t* __restrict__ tbl, int64_t n, const int32_t* __restrict__ slot_list) {
@@ -180,8 +195,10 @@ int build_tie_lists(lcp_index_s* x, cudaStream_t s) {
     LCP_LAUNCH(k_flag_assign, (unsigned)nb, 256, 0, s, x->slot_flag, nslots, x->tl_sums, x->slot_lo,
                x->slot_hi, x->nlists_cap, x->slot_list, x->tl_lo, x->tl_hi);
     LCP_LAUNCH(k_node_lists, (unsigned)((x->nlists_cap + kTlWarps - 1) / kTlWarps), kTlWarps * 32, 0, s,
-               ix, x->tl_total, x->nlists_cap, x->tl_lo, x->tl_hi, x->tlists);
+               ix, x->tl_total, x->nlists_cap, x->tl_lo, x->tl_hi, x->tlists, x->tlpos);
     LCP_LAUNCH(k_remap_tbl, (unsigned)((nslots + 255) / 256), 256, 0, s, x->tbl, nslots, x->slot_list);
+    const int64_t ntok = 1ll << x->bits;
+    LCP_LAUNCH(k_bucket_lists, (unsigned)((ntok + 255) / 256), 256, 0, s, ix, ntok, x->bkt_list);
     return LCP_OK;
 }
 
