@@ -259,9 +259,22 @@ __device__ void topk_one(const DevIndex& ix, QWarp& S, int64_t p, int lL, int lR
             nR += finish_chunk(h, id, ok, nR, availR, S.rid, S.rlam);
         }
     }
-    // A = loaded items with LCP > d*; interval [lov, hiv) of level d*
-    const int aL = count_ge(S.llam, nL, dstar + 1);
-    const int aR = count_ge(S.rlam, nR, dstar + 1);
+    // A = loaded items with LCP > d*; interval [lov, hiv) of level d*.
+    // Counts of loaded items with LCP > d* (aX) and >= d* (vX) per side, by
+    // ballots over the non-increasing LCP arrays.
+    int aL = 0, aR = 0, vL = 0, vR = 0;
+    for (int b = 0; b < nL; b += 32) {
+        const int t = b + (int)lane;
+        const int l = t < nL ? (int)S.llam[t] : -1;
+        aL += __popc(__ballot_sync(0xffffffffu, l > dstar));
+        vL += __popc(__ballot_sync(0xffffffffu, l >= dstar));
+    }
+    for (int b = 0; b < nR; b += 32) {
+        const int t = b + (int)lane;
+        const int l = t < nR ? (int)S.rlam[t] : -1;
+        aR += __popc(__ballot_sync(0xffffffffu, l > dstar));
+        vR += __popc(__ballot_sync(0xffffffffu, l >= dstar));
+    }
     const int nA = aL + aR;
     int64_t lov = 0, hiv = N;
     int li = -2;  // tie list of the level-d* node (-2: not looked up yet)
@@ -270,8 +283,6 @@ __device__ void topk_one(const DevIndex& ix, QWarp& S, int64_t p, int lL, int lR
         hiv = ix.bkt[tok0 + 1];
         li = ix.bkt_list[tok0];
     } else if (dstar > 1) {
-        const int vL = count_ge(S.llam, nL, dstar);
-        const int vR = count_ge(S.rlam, nR, dstar);
         const bool knownL = vL < nL || nL == availL;
         const bool knownR = vR < nR || nR == availR;
         int64_t xl = -1, xr = N;
