@@ -378,6 +378,8 @@ def run_ours(args, world, rank, local):
                                "last_step_ms": round(float(st[-1]), 4)}
         gi.close()
         del dsteps
+        # serving: six resident indexes, Poisson arrivals, native open-loop replay
+        paths["serving"] = serving_leg(lcp, device, to_dev)
         # end to end through the host-buffer ABI (copies inside the timed region)
         hS, hQ = pinned(S), pinned(Qs)
         hid = torch.empty((Q, k), dtype=torch.int32).pin_memory()
@@ -408,6 +410,74 @@ def run_ours(args, world, rank, local):
                                     "sample": "first %d queries of the batch against all %d rows "
                                               "(%.1f s)" % (n, N, el)}
     return line
+
+
+def serving_leg(lcp, device, to_dev, duration_s=1.5, budget=256 << 20, streams=8, max_inflight=64):
+    """Six resident zipf-prefix indexes (N, L) in SERVING_INDEXES; requests
+    arrive Poisson at 20k/s with log-uniform batch sizes in [1, 4096], k in
+    {1, 10, 100} and a uniformly drawn index; admission by a device-memory
+    budget; latency = completion - scheduled arrival."""
+    import torch
+    w = W.WORKLOADS["serving6"]
+    V, s_, seed, rate = w["vocab"], w["s"], w["seed"], w["rate"]
+    indexes, pools = [], []
+    for i, (N, L) in enumerate(W.SERVING_INDEXES):
+        S = W.zipf_prefix_rows(N, L, V, s_, seed * 100 + i)
+        pool = W.zipf_prefix_queries(S, 16_384, V, s_, seed * 100 + i)
+        indexes.append(lcp.lcp_index_build(to_dev(S, device), max_k=100))
+        pools.append(pinned(pool))
+    n_req = int(rate * duration_s)
+    rq = W.serving_requests(n_req, rate, len(indexes), seed)
+    arena_bytes = 512 << 20
+    arena = torch.empty(arena_bytes, dtype=torch.uint8).pin_memory()
+    base = arena.data_ptr()
+    sess = lcp.Session(mem_budget=budget, max_inflight=max_inflight, streams=streams)
+    slots = [sess.add_index(ix) for ix in indexes]
+    reqs, off, layout, wrap_at = [], 0, [], 0
+    rng = np.random.default_rng(seed)
+    for i in range(n_req):
+        j, Q, k = int(rq["index"][i]), int(rq["n_queries"][i]), int(rq["k"][i])
+        qoff = int(rng.integers(0, 16_384 - Q + 1))
+        need = (Q * k * 5 + 255) & ~255  # 256-byte aligned output slots
+        if off + need > arena_bytes:
+            off, wrap_at = 0, i
+        qp = pools[j].data_ptr() + qoff * pools[j].shape[1] * 2
+        reqs.append(lcp.ReplayRequest(float(rq["arrival_s"][i]), slots[j], k, Q, qp, base + off,
+                                      base + off + Q * k * 4))
+        layout.append((j, qoff, Q, k, off))
+        off += need
+    torch.cuda.synchronize()
+    launches0 = lcp.lcp_launch_count()
+    try:
+        rc, lat, wall = sess.replay(reqs, timeout_s=120.0)
+        launches = lcp.lcp_launch_count() - launches0
+        st = sess.stats()
+    finally:
+        sess.close()
+    # the last requests' outputs are still in the arena: check them against
+    # the same request served alone
+    same = True
+    for i in range(max(n_req - 40, wrap_at), n_req):  # outputs not overwritten since
+        j, qoff, Q, k, o = layout[i]
+        if lat[i] < 0:
+            continue
+        alone = lcp.lcp_topk_batch(indexes[j], pools[j][qoff:qoff + Q].to(device), k)
+        got = arena[o:o + Q * k * 4].view(torch.int32).view(Q, k)
+        same = same and bool(torch.equal(got, alone[0].cpu()))
+    ok = lat[lat >= 0]
+    done_q = int(sum(reqs[i].Q for i in range(n_req) if lat[i] >= 0))
+    res = {"requests": n_req, "rate_per_s": rate, "completed": int(len(ok)), "rejected": int(st["rejected"]),
+           "queries": done_q, "qps": round(done_q / wall, 1) if wall > 0 else None,
+           "requests_per_s": round(len(ok) / wall, 1) if wall > 0 else None,
+           "latency_ms": {"p50": round(float(np.percentile(ok, 50)) * 1e3, 4),
+                          "p99": round(float(np.percentile(ok, 99)) * 1e3, 4),
+                          "p99.9": round(float(np.percentile(ok, 99.9)) * 1e3, 4)},
+           "mem_budget": budget, "mem_peak": int(st["mem_peak"]), "streams": streams,
+           "max_inflight": max_inflight, "kernel_launches": int(launches),
+           "results_equal_alone": same, "rc": int(rc)}
+    for ix in indexes:
+        ix.close()
+    return res
 
 
 # ---------------------------------------------------------------------------

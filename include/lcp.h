@@ -177,6 +177,75 @@ LCP_API int lcp_scan_topk_noalloc(const void* d_tokens, int64_t N, lcp_format_t 
                                   uint8_t* d_out_lcp, lcp_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Serving session -- continuous batching over resident indexes.  Not in the
+ * paper (its sustained benchmark, Sec. 7 Table 4, serves one query at a
+ * time); this is the serving layer around lcp_topk_batch.
+ *
+ * A session holds several built indexes (lcp_session_add_index; the caller
+ * keeps ownership and must not destroy them before the session).  Each
+ * submitted request (host queries [Q, L] in the index's format, k, host
+ * outputs [Q, k]) needs Q*(L*token_bytes + 16 + 5*k) bytes of device memory
+ * while in flight.  Requests are admitted in arrival order while at most
+ * max_inflight are on the GPU and their memory fits mem_budget; the rest wait
+ * and are admitted as earlier requests complete, so requests that arrive
+ * while others run join them on the GPU (spread over `streams` CUDA streams,
+ * where their copies and kernels overlap).  A request whose memory alone
+ * exceeds mem_budget is rejected with LCP_ERR_BUDGET.  Each result is
+ * exactly what lcp_topk_batch returns for that request alone.
+ * Host query and output buffers must stay valid until the request's ticket
+ * completes; pinned host memory makes the copies asynchronous.
+ * All calls are thread-safe.  dry_run = 1 runs the admission logic without a
+ * device (requests complete on the next poll), for testing the policy.
+ * ---------------------------------------------------------------------- */
+typedef struct lcp_session_s* lcp_session_t;
+typedef struct {
+    int64_t mem_budget;    /* device bytes for requests in flight (> 0) */
+    int32_t max_inflight;  /* requests on the GPU at once (>= 1) */
+    int32_t streams;       /* CUDA streams (1..64) */
+    int32_t dry_run;       /* 1: no device work (policy tests) */
+} lcp_session_cfg_t;
+typedef struct {
+    int64_t submitted, admitted, completed, rejected;
+    int64_t inflight, pending;
+    int64_t mem_in_use, mem_peak;
+} lcp_session_stats_t;
+
+LCP_API int lcp_session_create(const lcp_session_cfg_t* cfg, lcp_session_t* out);
+/* Registers an index; *slot receives its number (0, 1, ...). */
+LCP_API int lcp_session_add_index(lcp_session_t session, lcp_index_t index, int32_t* slot);
+/* Queues a request; *ticket identifies it.  Never blocks on the device. */
+LCP_API int lcp_session_submit(lcp_session_t session, int32_t slot, const void* h_queries, int64_t Q,
+                               int32_t k, int32_t* h_out_ids, uint8_t* h_out_lcp, uint64_t* ticket);
+/* Advances the session (retires finished requests, admits waiting ones) and
+ * reports the ticket: LCP_OK when its results are in the host buffers,
+ * LCP_PENDING if it is not done within timeout_ms (0 = just check), or the
+ * request's error.  A ticket reports LCP_OK once; later polls return
+ * LCP_ERR_INVALID. */
+LCP_API int lcp_session_poll(lcp_session_t session, uint64_t ticket, int32_t timeout_ms);
+LCP_API int lcp_session_stats(lcp_session_t session, lcp_session_stats_t* stats);
+/* Waits for requests on the GPU (up to 10 s), cancels waiting ones, frees
+ * the session.  Returns LCP_ERR_TIMEOUT if the wait ran out. */
+LCP_API int lcp_session_destroy(lcp_session_t session);
+
+/* Open-loop load driver: submits reqs[i] when its arrival time (seconds from
+ * the call's start, non-decreasing) comes, polls completions, and writes
+ * latency_s[i] = completion time - scheduled arrival time (so a driver that
+ * falls behind is charged for it); a rejected request gets -1.  *wall_s is
+ * the time from the first arrival to the last completion.  Blocks until
+ * every request is done or timeout_s passes (LCP_ERR_TIMEOUT). */
+typedef struct {
+    double arrival_s;
+    int32_t slot;
+    int32_t k;
+    int64_t Q;
+    const void* h_queries;
+    int32_t* h_out_ids;
+    uint8_t* h_out_lcp;
+} lcp_replay_req_t;
+LCP_API int lcp_session_replay(lcp_session_t session, const lcp_replay_req_t* reqs, int64_t n,
+                               double timeout_s, double* latency_s, double* wall_s);
+
+/* ------------------------------------------------------------------------
  * Index inspection and lifetime.
  * ---------------------------------------------------------------------- */
 /* Current item count and device bytes held (both may be NULL). Synchronous,
@@ -188,11 +257,15 @@ LCP_API int lcp_index_size(lcp_index_t index, int64_t* N, int64_t* bytes);
  * and checkpoints. */
 LCP_API int lcp_index_export(lcp_index_t index, int32_t* d_ids, uint8_t* d_H, lcp_stream_t stream);
 
-/* Waits for the last stream the index was used on and reports any device
- * status (LCP_ERR_TIMEOUT if a bounded device wait ran out), then clears it. */
+/* Waits for the index's most recent operation (on whichever stream it was
+ * issued; the index records an event of its own after each call) and
+ * reports any device status (LCP_ERR_TIMEOUT if a bounded device wait ran
+ * out), then clears it. */
 LCP_API int lcp_index_sync(lcp_index_t index);
 
-/* Frees the index (after synchronising its last stream). NULL is a no-op. */
+/* Frees the index.  It may have been used on several streams, some perhaps
+ * destroyed since, so this waits for the whole device first.  NULL is a
+ * no-op. */
 LCP_API int lcp_index_destroy(lcp_index_t index);
 
 /* ------------------------------------------------------------------------

@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import sys
 
 import torch
 
@@ -46,6 +47,8 @@ ABI_SYMBOLS = (
     "lcp_topk_batch", "lcp_topk_batch_host", "lcp_scan_topk", "lcp_index_size",
     "lcp_index_export", "lcp_index_sync", "lcp_index_destroy", "lcp_device_status",
     "lcp_launch_count", "lcp_debug_bounded_wait", "lcp_scan_topk_noalloc",
+    "lcp_session_create", "lcp_session_add_index", "lcp_session_submit", "lcp_session_poll",
+    "lcp_session_stats", "lcp_session_destroy", "lcp_session_replay",
 )
 
 
@@ -57,6 +60,22 @@ class LcpError(RuntimeError):
 
 class _Format(ctypes.Structure):
     _fields_ = [("token_bytes", ctypes.c_int32), ("L", ctypes.c_int32), ("vocab", ctypes.c_int32)]
+
+
+class SessionConfig(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
+                ("streams", ctypes.c_int32), ("dry_run", ctypes.c_int32)]
+
+
+class ReplayRequest(ctypes.Structure):
+    _fields_ = [("arrival_s", ctypes.c_double), ("slot", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("Q", ctypes.c_int64), ("h_queries", ctypes.c_void_p), ("h_out_ids", ctypes.c_void_p),
+                ("h_out_lcp", ctypes.c_void_p)]
+
+
+class SessionStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "admitted", "completed", "rejected",
+                                                "inflight", "pending", "mem_in_use", "mem_peak")]
 
 
 def _load():
@@ -84,6 +103,16 @@ def _load():
         "lcp_launch_count": ([], i64),
         "lcp_debug_bounded_wait": ([i64, vp], ctypes.c_int),
         "lcp_scan_topk_noalloc": ([vp, i64, _Format, vp, i64, i32, vp, vp, vp], ctypes.c_int),
+        "lcp_session_create": ([ctypes.POINTER(SessionConfig), ctypes.POINTER(vp)], ctypes.c_int),
+        "lcp_session_add_index": ([vp, vp, ctypes.POINTER(i32)], ctypes.c_int),
+        "lcp_session_submit": ([vp, i32, vp, i64, i32, vp, vp, ctypes.POINTER(ctypes.c_uint64)],
+                               ctypes.c_int),
+        "lcp_session_poll": ([vp, ctypes.c_uint64, i32], ctypes.c_int),
+        "lcp_session_stats": ([vp, ctypes.POINTER(SessionStats)], ctypes.c_int),
+        "lcp_session_destroy": ([vp], ctypes.c_int),
+        "lcp_session_replay": ([vp, ctypes.POINTER(ReplayRequest), i64, ctypes.c_double,
+                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+                               ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -165,6 +194,8 @@ class Index:
         self._h = None
 
     def __del__(self):
+        if sys.is_finalizing():  # CUDA may already be torn down: leak, do not call in
+            return
         try:
             self.close()
         except Exception:
@@ -307,6 +338,92 @@ def lcp_launch_count() -> int:
 
 def lcp_debug_bounded_wait(spin_limit: int, stream=None) -> int:
     return _lib.lcp_debug_bounded_wait(spin_limit, _stream(stream))
+
+
+class Session:
+    """Serving session over resident indexes (see include/lcp.h).
+
+    submit() takes host tensors (pinned memory keeps it asynchronous) and
+    returns a ticket; poll() reports LCP_OK / LCP_PENDING / an error code.
+    The session keeps references to its indexes and to in-flight buffers.
+    """
+
+    def __init__(self, mem_budget: int, max_inflight: int = 64, streams: int = 4,
+                 dry_run: bool = False):
+        cfg = SessionConfig(mem_budget, max_inflight, streams, 1 if dry_run else 0)
+        self._h = ctypes.c_void_p()
+        _check(_lib.lcp_session_create(ctypes.byref(cfg), ctypes.byref(self._h)), "lcp_session_create")
+        self._indexes = []
+        self._live = {}
+
+    def add_index(self, index) -> int:
+        slot = ctypes.c_int32()
+        h = index.handle if index is not None else ctypes.c_void_p(0)
+        _check(_lib.lcp_session_add_index(self._h, h, ctypes.byref(slot)), "lcp_session_add_index")
+        self._indexes.append(index)
+        return slot.value
+
+    def submit(self, slot: int, queries, k: int, out_ids=None, out_lcp=None) -> int:
+        """Queues a request; returns its ticket.  Raises LcpError (code
+        LCP_ERR_BUDGET when the request can never fit the budget)."""
+        Q = queries.shape[0] if queries is not None else 0
+        if queries is not None:
+            queries = _rows(queries, device=False)
+        if out_ids is None:
+            out_ids = torch.empty((Q, k), dtype=torch.int32, pin_memory=torch.cuda.is_available())
+        if out_lcp is None:
+            out_lcp = torch.empty((Q, k), dtype=torch.uint8, pin_memory=torch.cuda.is_available())
+        t = ctypes.c_uint64()
+        _check(_lib.lcp_session_submit(self._h, slot, _ptr(queries), Q, k, _ptr(out_ids), _ptr(out_lcp),
+                                       ctypes.byref(t)), "lcp_session_submit")
+        self._live[t.value] = (queries, out_ids, out_lcp)
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = 0) -> int:
+        rc = _lib.lcp_session_poll(self._h, ticket, timeout_ms)
+        if rc != LCP_PENDING:
+            self._live.pop(ticket, None)
+        return rc
+
+    def result(self, ticket: int, timeout_ms: int = 10_000):
+        """Waits for a ticket and returns its (ids, lcp) host tensors."""
+        bufs = self._live.get(ticket)
+        rc = self.poll(ticket, timeout_ms)
+        if rc != LCP_OK:
+            raise LcpError(rc, "lcp_session_poll")
+        return bufs[1], bufs[2]
+
+    def replay(self, reqs, timeout_s: float = 120.0):
+        """Open-loop replay of ReplayRequest records (see lcp_session_replay).
+        Returns (rc, latencies in seconds (numpy), wall seconds)."""
+        import numpy as np
+        n = len(reqs)
+        arr = (ReplayRequest * n)(*reqs)
+        lat = (ctypes.c_double * max(n, 1))()
+        wall = ctypes.c_double()
+        rc = _lib.lcp_session_replay(self._h, arr, n, timeout_s, lat, ctypes.byref(wall))
+        return rc, np.ctypeslib.as_array(lat)[:n].copy(), wall.value
+
+    def stats(self) -> dict:
+        st = SessionStats()
+        _check(_lib.lcp_session_stats(self._h, ctypes.byref(st)), "lcp_session_stats")
+        return {n: getattr(st, n) for n, _ in SessionStats._fields_}
+
+    def close(self) -> int:
+        rc = LCP_OK
+        if self._h is not None and self._h.value:
+            rc = _lib.lcp_session_destroy(self._h)
+        self._h = None
+        self._live.clear()
+        return rc
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def raw_lib():

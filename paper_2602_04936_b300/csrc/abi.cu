@@ -71,6 +71,8 @@ static void retain_pool_memory() {
     });
 }
 
+// Frees with cudaFreeAsync on stream s (the build's own stream on failure) or,
+// with s == nullptr and the device idle, synchronously.
 static void free_index_memory(lcp_index_s* x, cudaStream_t s) {
     void* ptrs[] = {x->buf[0].rows, x->buf[0].head, x->buf[0].ids, x->buf[0].H,
                     x->buf[1].rows, x->buf[1].head, x->buf[1].ids, x->buf[1].H,
@@ -79,7 +81,10 @@ static void free_index_memory(lcp_index_s* x, cudaStream_t s) {
                     x->tl_lo, x->tl_hi, x->tl_sums, x->tl_total, x->tlpos, x->bkt_list,
                     x->ins_rows, x->ins_ids, x->ins_rank};
     for (void* p : ptrs)
-        if (p) cudaFreeAsync(p, s);
+        if (p) {
+            if (s) cudaFreeAsync(p, s);
+            else cudaFree(p);
+        }
     x->buf[0] = lcp_buffers();
     x->buf[1] = lcp_buffers();
     cudaFree(x->stage_in);
@@ -145,14 +150,18 @@ static int alloc_index(lcp_index_s* x, int64_t N, int64_t cap, cudaStream_t s) {
     return LCP_OK;
 }
 
+// Reads and clears a device status word (s == nullptr: blocking copies).
 static int read_status(int* d_status, cudaStream_t s) {
     if (!d_status) return LCP_OK;
     int h = 0;
-    LCP_CUDA_TRY(cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    LCP_CUDA_TRY(cudaStreamSynchronize(s));
-    if (h) {
-        LCP_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), s));
+    if (s) {
+        LCP_CUDA_TRY(cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
         LCP_CUDA_TRY(cudaStreamSynchronize(s));
+    } else {
+        LCP_CUDA_TRY(cudaMemcpy(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    }
+    if (h) {
+        LCP_CUDA_TRY(cudaMemset(d_status, 0, sizeof(int)));
         return h == lcpk::DEV_TIMEOUT ? LCP_ERR_TIMEOUT : LCP_ERR_CUDA;
     }
     return LCP_OK;
@@ -214,8 +223,11 @@ int lcp_index_build(const void* d_tokens, int64_t N, lcp_format_t fmt, int64_t c
     x->K = ((max_k + 31) / 32) * 32;
     x->cap = capacity;
     x->N = N;
-    x->last_stream = stream;
     retain_pool_memory();
+    if (cudaEventCreateWithFlags(&x->done_ev, cudaEventDisableTiming) != cudaSuccess) {
+        delete x;
+        return LCP_ERR_CUDA;
+    }
     int rc = alloc_index(x, N, capacity, s);
     if (rc == LCP_OK && N > 0) {
         lcpk::RowFmt f = lcpk::make_fmt(x->tb, x->L, d_tokens);
@@ -231,9 +243,11 @@ int lcp_index_build(const void* d_tokens, int64_t N, lcp_format_t fmt, int64_t c
         cudaStreamSynchronize(s);
         free_index_memory(x, s);
         cudaStreamSynchronize(s);
+        cudaEventDestroy(x->done_ev);
         delete x;
         return rc;
     }
+    cudaEventRecord(x->done_ev, s);
     *out = x;
     return LCP_OK;
 }
@@ -260,12 +274,12 @@ int lcp_index_insert(lcp_index_t x, const void* d_tokens, int64_t n, lcp_stream_
     if (n == 0) return LCP_OK;
     if (x->N + n > x->cap) return LCP_ERR_CAPACITY;
     if (!x->buf[1].rows) return LCP_ERR_CAPACITY;
-    x->last_stream = stream;
     int rc = insert_device(x, d_tokens, n, (cudaStream_t)stream);
     if (rc == LCP_OK) {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_status(e);
     }
+    cudaEventRecord(x->done_ev, (cudaStream_t)stream);
     return rc;
 }
 
@@ -273,12 +287,12 @@ int lcp_topk_batch(lcp_index_t x, const void* d_queries, int64_t Q, int32_t k, i
                    uint8_t* d_out_lcp, lcp_stream_t stream) {
     if (!x || Q < 0 || k < 1 || k > x->max_k) return LCP_ERR_INVALID;
     if (Q > 0 && (!d_queries || !d_out_ids || !d_out_lcp)) return LCP_ERR_INVALID;
-    x->last_stream = stream;
     int rc = topk_batch_device(x, d_queries, Q, k, d_out_ids, d_out_lcp, (cudaStream_t)stream);
     if (rc == LCP_OK) {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_status(e);
     }
+    cudaEventRecord(x->done_ev, (cudaStream_t)stream);
     return rc;
 }
 
@@ -354,16 +368,17 @@ int lcp_index_export(lcp_index_t x, int32_t* d_ids, uint8_t* d_H, lcp_stream_t s
 
 int lcp_index_sync(lcp_index_t x) {
     if (!x) return LCP_ERR_INVALID;
-    cudaStream_t s = (cudaStream_t)x->last_stream;
-    LCP_CUDA_TRY(cudaStreamSynchronize(s));
-    return read_status(x->status, s);
+    LCP_CUDA_TRY(cudaEventSynchronize(x->done_ev));
+    return read_status(x->status, nullptr);
 }
 
 int lcp_index_destroy(lcp_index_t x) {
     if (!x) return LCP_OK;
-    cudaStream_t s = (cudaStream_t)x->last_stream;
-    free_index_memory(x, s);  // stream-ordered: after the work already queued on s
-    cudaStreamSynchronize(s);
+    // the index may have been used on several streams (some perhaps already
+    // destroyed by their owner): wait for the whole device, then free
+    cudaDeviceSynchronize();
+    free_index_memory(x, nullptr);
+    cudaEventDestroy(x->done_ev);
     delete x;
     return LCP_OK;
 }

@@ -110,7 +110,7 @@ struct lcp_index_s {
     int64_t nblk_cap = 0;
     int st_levels_cap = 0;
     int* status = nullptr;  // device status word
-    void* last_stream = nullptr;
+    cudaEvent_t done_ev = nullptr;  // recorded after each operation on the caller's stream
     int64_t bytes = 0;
     // host-buffer entry points: device staging grown on demand
     void* stage_in = nullptr;

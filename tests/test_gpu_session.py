@@ -1,0 +1,73 @@
+"""Serving session on the GPU: requests against several resident indexes,
+admitted under a memory budget and overlapped on several streams; every
+result equals the same request served alone (lcp_topk_batch) and the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lcp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2602_04936_b300 as P
+    return P
+
+
+def _dev(a):
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint16:
+        a = a.view(np.int16)
+    return torch.from_numpy(a).cuda()
+
+
+def _pinned(a):
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint16:
+        a = a.view(np.int16)
+    return torch.from_numpy(a).pin_memory()
+
+
+def test_session_mix_equals_alone(lcp):
+    rng = np.random.default_rng(4)
+    specs = [(3_000, 16, 1024, 1.1), (50_000, 32, 32768, 1.05), (200_000, 64, 32768, 1.05)]
+    data, idxs = [], []
+    for i, (N, L, V, s) in enumerate(specs):
+        S = W.zipf_prefix_rows(N, L, V, s, 40 + i)
+        Qs = W.zipf_prefix_queries(S, 6_000, V, s, 40 + i)
+        data.append((S, Qs))
+        idxs.append(lcp.lcp_index_build(_dev(S), max_k=100))
+    sess = lcp.Session(mem_budget=8 << 20, max_inflight=6, streams=4)
+    slots = [sess.add_index(ix) for ix in idxs]
+    reqs = []
+    for r in range(60):
+        j = int(rng.integers(0, 3))
+        Q = int(np.exp(rng.uniform(0, np.log(2000))))
+        k = int(rng.choice([1, 10, 100]))
+        off = int(rng.integers(0, 6_000 - Q))
+        q = data[j][1][off:off + Q]
+        t = sess.submit(slots[j], _pinned(q), k)
+        reqs.append((t, j, q, k))
+    with pytest.raises(lcp.LcpError) as e:  # 1M queries x k=100 can never fit 8 MB
+        sess.submit(slots[0], _pinned(np.zeros((100_000, 16), np.uint16)), 100)
+    assert e.value.code == lcp.LCP_ERR_BUDGET
+    for n, (t, j, q, k) in enumerate(reqs):
+        ids, lc = sess.result(t)
+        alone = lcp.lcp_topk_batch(idxs[j], _dev(q), k)
+        assert np.array_equal(ids.numpy(), alone[0].cpu().numpy()), n
+        assert np.array_equal(lc.numpy(), alone[1].cpu().numpy()), n
+        if n % 10 == 0:
+            w_ids, w_lcp = oracle.topk_batch(data[j][0], q[:50], k)
+            assert np.array_equal(ids.numpy()[:50], w_ids) and np.array_equal(lc.numpy()[:50], w_lcp)
+    st = sess.stats()
+    assert st["completed"] == 60 and st["rejected"] == 1 and st["inflight"] == 0
+    assert st["mem_peak"] <= 8 << 20
+    assert sess.close() == lcp.LCP_OK
+    for ix in idxs:
+        assert lcp.lcp_index_sync(ix) == 0
+        ix.close()
