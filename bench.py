@@ -139,6 +139,90 @@ class ClockSampler:
                 "power_w_max": max(pw), "reasons": sorted(reasons)}
 
 
+def _nvml_handle(device_index):
+    """NVML handle of a CUDA device, matched by UUID (NVML numbers the
+    machine's GPUs, CUDA only the visible ones)."""
+    import pynvml
+    import torch
+    pynvml.nvmlInit()
+    uuid = "GPU-" + str(torch.cuda.get_device_properties(device_index).uuid)
+    try:
+        return pynvml, pynvml.nvmlDeviceGetHandleByUUID(uuid)
+    except Exception:
+        return pynvml, pynvml.nvmlDeviceGetHandleByIndex(device_index)
+
+
+class EnergyMeter:
+    """Device energy from NVML's total-energy counter (millijoules since the
+    driver loaded); None, with the reason kept, where NVML cannot give it."""
+
+    def __init__(self, device_index):
+        self.h, self.error = None, None
+        try:
+            self.nv, h = _nvml_handle(device_index)
+            self.nv.nvmlDeviceGetTotalEnergyConsumption(h)
+            self.h = h
+        except Exception as e:  # noqa: BLE001 - reported in the JSON line
+            self.error = "%s: %s" % (type(e).__name__, e)
+
+    def read_j(self):
+        if self.h is None:
+            return None
+        try:
+            return self.nv.nvmlDeviceGetTotalEnergyConsumption(self.h) / 1e3
+        except Exception:
+            return None
+
+
+class NvmlClockSampler:
+    """SM clock and clock-event reasons read through NVML every 2 ms on a
+    thread: short timed regions get more samples than nvidia-smi's 50 ms."""
+
+    BITS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
+            "sw_power_cap": 0x4}
+
+    def __init__(self, device_index):
+        import threading
+        self.samples, self.h, self.stop_ev = [], None, threading.Event()
+        try:
+            self.nv, self.h = _nvml_handle(device_index)
+            self.max_mhz = self.nv.nvmlDeviceGetMaxClockInfo(self.h, self.nv.NVML_CLOCK_SM)
+        except Exception:
+            self.h = None
+        self.t = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        while not self.stop_ev.is_set():
+            try:
+                mhz = self.nv.nvmlDeviceGetClockInfo(self.h, self.nv.NVML_CLOCK_SM)
+                why = self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+                self.samples.append((mhz, why))
+            except Exception:
+                return
+            time.sleep(0.002)
+
+    def start(self):
+        if self.h is not None:
+            self.t.start()
+
+    def stop(self):
+        if self.h is None:
+            return None
+        self.stop_ev.set()
+        self.t.join(timeout=2)
+        if not self.samples:
+            return None
+        reasons = sorted(n for n, b in self.BITS.items() if any(w & b for _, w in self.samples))
+        return {"sm_mhz": float(np.median([m for m, _ in self.samples])), "sm_max_mhz": self.max_mhz,
+                "samples": len(self.samples), "reasons": reasons}
+
+
+def joules_per(e0, e1, units):
+    if e0 is None or e1 is None or units <= 0:
+        return None
+    return (e1 - e0) / units
+
+
 # ---------------------------------------------------------------------------
 # distributed plumbing (replicas: no collective on the data path)
 # ---------------------------------------------------------------------------
@@ -271,17 +355,26 @@ def run_ours(args, world, rank, local):
     t_end = torch.cuda.Event(enable_timing=True)
     clk = ClockSampler(local)
     clk.start()
+    nclk = NvmlClockSampler(local)
+    nclk.start()
+    meter = EnergyMeter(local)
     barrier(world)
     torch.cuda.synchronize()
     launches0 = lcp.lcp_launch_count()
+    e_start = meter.read_j()
     t_start.record(stream)
     for i in range(args.steps):
         step(evs[i])
     t_end.record(stream)
     torch.cuda.synchronize()
+    e_end = meter.read_j()
     launches = lcp.lcp_launch_count() - launches0
     barrier(world)
     clocks = clk.stop()
+    fine = nclk.stop()
+    if fine is not None:
+        clocks["nvml_2ms"] = fine
+        clocks["reasons"] = sorted(set(clocks.get("reasons", [])) | set(fine["reasons"]))
     total_ms = max_over_ranks(t_start.elapsed_time(t_end), world)
     ms_step = total_ms / args.steps
     value = world * Q / (ms_step / 1e3)
@@ -300,9 +393,13 @@ def run_ours(args, world, rank, local):
                 "traffic": traffic, "algorithmic_bytes_per_launch": Q * per_q,
                 "bytes_per_query": per_q, "launch_ms": round(query_ms, 4)}
 
+    jq = joules_per(e_start, e_end, Q * args.steps)
     paths = {"indexed": {"build_ms": round(build_ms, 3), "query_ms": round(query_ms, 3),
+                         "energy_j_per_query": jq,
                          "qps_query_only": round(Q / (query_ms / 1e3), 1),
                          "build_rows_per_s": round(N / (build_ms / 1e3), 1)}}
+    if meter.h is None:
+        paths["energy_unavailable"] = meter.error
     line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
@@ -313,7 +410,10 @@ def run_ours(args, world, rank, local):
         # full scan of the same batch (comparison path)
         reps = 2
         sc = []
+        e_scan0 = None
         for r in range(reps + 1):
+            if r == 1:
+                e_scan0 = meter.read_j()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             a.record(stream)
@@ -325,13 +425,14 @@ def run_ours(args, world, rank, local):
             if a.elapsed_time(b) > 20_000:
                 break
         scan_ms = float(np.mean(sc)) if sc else float(a.elapsed_time(b))
+        scan_j = joules_per(e_scan0, meter.read_j(), Q * len(sc)) if sc else None
         # the two paths agree on every query
         idx = lcp.lcp_index_build(dS, max_k=k)
         lcp.lcp_topk_batch(idx, dQ, k, out_ids, out_lcp)
         torch.cuda.synchronize()
         same = bool(torch.equal(out_ids, sids) and torch.equal(out_lcp, slc))
         paths["full_scan"] = {"ms": round(scan_ms, 3), "qps": round(Q / (scan_ms / 1e3), 1),
-                              "identical_to_indexed": same}
+                              "energy_j_per_query": scan_j, "identical_to_indexed": same}
         paths["indexed_vs_full_scan_speedup_query_only"] = round(scan_ms / query_ms, 1)
         # per-batch latency (CUDA events around each call)
         lat = {"indexed": {}, "full_scan": {}}
@@ -355,28 +456,49 @@ def run_ours(args, world, rank, local):
         paths["latency_ms"] = lat
         idx.close()
         del sids, slc
-        # insert-then-query stream (1,000 sensors x 1,000 steps)
+        # insert-then-query stream (1,000 sensors x 1,000 steps), issued as
+        # direct calls and as one CUDA graph per step
         g = W.GncStream(sensors=1000, seed=5)
         steps = [g.step() for _ in range(1000)]
         dsteps = to_dev(np.stack(steps), device)
-        gi = lcp.lcp_index_build(torch.zeros((0, 8), dtype=torch.int16, device=device), max_k=5,
-                                 capacity=1_000_000)
         gids = torch.empty((1000, 5), dtype=torch.int32, device=device)
         glcp = torch.empty((1000, 5), dtype=torch.uint8, device=device)
-        gev = [torch.cuda.Event(enable_timing=True) for _ in range(1001)]
-        torch.cuda.synchronize()
-        gev[0].record(stream)
-        for t in range(1000):
-            lcp.lcp_index_insert(gi, dsteps[t])
-            lcp.lcp_topk_batch(gi, dsteps[t], 5, gids, glcp)
-            gev[t + 1].record(stream)
-        torch.cuda.synchronize()
-        st = np.array([gev[t].elapsed_time(gev[t + 1]) for t in range(1000)])
-        paths["insert_gnc"] = {"steps": 1000, "final_N": gi.N, "steps_per_s": round(1e3 / st.mean(), 1),
-                               "p50_ms": round(float(np.percentile(st, 50)), 4),
-                               "p99_ms": round(float(np.percentile(st, 99)), 4),
-                               "last_step_ms": round(float(st[-1]), 4)}
-        gi.close()
+        finals = {}
+        for mode in ("direct", "graph"):
+            gi = lcp.lcp_index_build(torch.zeros((0, 8), dtype=torch.int16, device=device), max_k=5,
+                                     capacity=1_000_000)
+            gstep = lcp.Step(gi, 1000, 1000, 5) if mode == "graph" else None
+            gev = [torch.cuda.Event(enable_timing=True) for _ in range(1001)]
+            torch.cuda.synchronize()
+            e_g0 = meter.read_j()
+            h0 = time.perf_counter()
+            gev[0].record(stream)
+            for t in range(1000):
+                if gstep is None:
+                    lcp.lcp_index_insert(gi, dsteps[t])
+                    lcp.lcp_topk_batch(gi, dsteps[t], 5, gids, glcp)
+                else:
+                    gstep.run(dsteps[t], dsteps[t], gids, glcp)
+                gev[t + 1].record(stream)
+            host_s = time.perf_counter() - h0
+            torch.cuda.synchronize()
+            e_g1 = meter.read_j()
+            st = np.array([gev[t].elapsed_time(gev[t + 1]) for t in range(1000)])
+            rec = {"steps": 1000, "final_N": gi.N, "steps_per_s": round(1e3 / st.mean(), 1),
+                   "p50_ms": round(float(np.percentile(st, 50)), 4),
+                   "p99_ms": round(float(np.percentile(st, 99)), 4),
+                   "last_step_ms": round(float(st[-1]), 4),
+                   "host_issue_ms_per_step": round(host_s, 4),
+                   "energy_j_per_step": joules_per(e_g0, e_g1, 1000)}
+            if gstep is not None:
+                rec["graph_instantiations"] = gstep.stats()[1]
+                gstep.close()
+            finals[mode] = (gids.clone(), glcp.clone())
+            paths["insert_gnc" if mode == "direct" else "insert_gnc_graph"] = rec
+            gi.close()
+        paths["insert_gnc_graph"]["last_step_equal_direct"] = bool(
+            torch.equal(finals["direct"][0], finals["graph"][0])
+            and torch.equal(finals["direct"][1], finals["graph"][1]))
         del dsteps
         # serving: six resident indexes, Poisson arrivals, native open-loop replay
         paths["serving"] = serving_leg(lcp, device, to_dev)

@@ -177,6 +177,29 @@ LCP_API int lcp_scan_topk_noalloc(const void* d_tokens, int64_t N, lcp_format_t 
                                   uint8_t* d_out_lcp, lcp_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Streaming step as a CUDA graph: insert n rows, then answer Q queries --
+ * the guidance/navigation stream of the paper (Sec. 1 Example 1, Sec. 7
+ * Table 7: every control step stores the current sensor readings and
+ * queries them).  Each run captures the step's kernels on a private stream
+ * (nothing executes during capture), updates the instantiated graph in place
+ * (cudaGraphExecUpdate) and launches it on `stream`, so the whole step runs
+ * without per-kernel launch gaps.  When the update is refused -- the number
+ * of kernels changed because N grew past a level boundary of the min tree
+ * or sparse table -- the graph is instantiated anew.
+ * Requires n <= LCP_INSERT_SMALL_BATCH (the insert path that never waits for
+ * the device), room for the rows (else LCP_ERR_CAPACITY), 1 <= k <= max_k.
+ * d_insert [n, L], d_queries [Q, L], d_out_* [Q, k]: device memory.  The step
+ * owns its scratch; the index must outlive it.
+ * ---------------------------------------------------------------------- */
+typedef struct lcp_step_s* lcp_step_t;
+LCP_API int lcp_step_create(lcp_index_t index, int64_t n, int64_t Q, int32_t k, lcp_step_t* out);
+LCP_API int lcp_step_run(lcp_step_t step, const void* d_insert, const void* d_queries, int32_t* d_out_ids,
+                         uint8_t* d_out_lcp, lcp_stream_t stream);
+/* Runs so far and how many of them had to instantiate the graph anew. */
+LCP_API int lcp_step_stats(lcp_step_t step, int64_t* runs, int64_t* instantiations);
+LCP_API int lcp_step_destroy(lcp_step_t step);
+
+/* ------------------------------------------------------------------------
  * Serving session -- continuous batching over resident indexes.  Not in the
  * paper (its sustained benchmark, Sec. 7 Table 4, serves one query at a
  * time); this is the serving layer around lcp_topk_batch.

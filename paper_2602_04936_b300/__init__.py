@@ -49,6 +49,7 @@ ABI_SYMBOLS = (
     "lcp_launch_count", "lcp_debug_bounded_wait", "lcp_scan_topk_noalloc",
     "lcp_session_create", "lcp_session_add_index", "lcp_session_submit", "lcp_session_poll",
     "lcp_session_stats", "lcp_session_destroy", "lcp_session_replay",
+    "lcp_step_create", "lcp_step_run", "lcp_step_stats", "lcp_step_destroy",
 )
 
 
@@ -113,6 +114,10 @@ def _load():
         "lcp_session_replay": ([vp, ctypes.POINTER(ReplayRequest), i64, ctypes.c_double,
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
                                ctypes.c_int),
+        "lcp_step_create": ([vp, i64, i64, i32, ctypes.POINTER(vp)], ctypes.c_int),
+        "lcp_step_run": ([vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "lcp_step_stats": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64)], ctypes.c_int),
+        "lcp_step_destroy": ([vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -338,6 +343,41 @@ def lcp_launch_count() -> int:
 
 def lcp_debug_bounded_wait(spin_limit: int, stream=None) -> int:
     return _lib.lcp_debug_bounded_wait(spin_limit, _stream(stream))
+
+
+class Step:
+    """Insert-then-query streaming step replayed as a CUDA graph (lcp.h)."""
+
+    def __init__(self, index: "Index", n: int, Q: int, k: int):
+        self._h = ctypes.c_void_p()
+        self.index, self.n, self.Q, self.k = index, n, Q, k
+        with torch.cuda.device(index.device):
+            _check(_lib.lcp_step_create(index.handle, n, Q, k, ctypes.byref(self._h)), "lcp_step_create")
+
+    def run(self, inserts: torch.Tensor, queries: torch.Tensor, out_ids=None, out_lcp=None, stream=None):
+        out_ids, out_lcp = _outputs(self.Q, self.k, queries.device, out_ids, out_lcp)
+        with torch.cuda.device(queries.device):
+            _check(_lib.lcp_step_run(self._h, _ptr(inserts.contiguous()), _ptr(queries.contiguous()),
+                                     _ptr(out_ids), _ptr(out_lcp), _stream(stream)), "lcp_step_run")
+        return out_ids, out_lcp
+
+    def stats(self):
+        r, i = ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.lcp_step_stats(self._h, ctypes.byref(r), ctypes.byref(i)), "lcp_step_stats")
+        return r.value, i.value
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib.lcp_step_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Session:

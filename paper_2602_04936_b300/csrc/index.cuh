@@ -141,8 +141,11 @@ int build_aux(lcp_index_s* x, cudaStream_t s);
 // heavy-node tie lists (needs the min tree, sorted blocks and sparse table).
 int build_tie_lists(lcp_index_s* x, cudaStream_t s);
 
+// loc_scratch: caller-owned buffer of search_scratch_bytes(Q) bytes for the
+// per-query position records, or nullptr to use stream-ordered scratch.
 int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, int32_t* out_ids,
-                      uint8_t* out_lcp, cudaStream_t s);
+                      uint8_t* out_lcp, cudaStream_t s, void* loc_scratch = nullptr);
+size_t search_scratch_bytes(int64_t Q);
 int insert_device(lcp_index_s* x, const void* d_tokens, int64_t n, cudaStream_t s);
 
 }  // namespace lcph

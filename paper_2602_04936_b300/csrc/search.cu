@@ -384,7 +384,7 @@ namespace lcph {
 using namespace lcpk;
 
 int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, int32_t* out_ids,
-                      uint8_t* out_lcp, cudaStream_t s) {
+                      uint8_t* out_lcp, cudaStream_t s, void* loc_scratch) {
     if (Q <= 0) return LCP_OK;
     if (x->N == 0) {
         LCP_CUDA_TRY(cudaMemsetAsync(out_ids, 0xFF, sizeof(int32_t) * (size_t)Q * k, s));
@@ -394,8 +394,11 @@ int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, i
     DevIndex ix = dev_view(x);
     RowFmt qf = make_fmt(x->tb, x->L, d_queries);
     const uint8_t* q = reinterpret_cast<const uint8_t*>(d_queries);
-    QLoc* loc = nullptr;
-    LCP_CUDA_TRY(cudaMallocAsync((void**)&loc, sizeof(QLoc) * (size_t)Q, s));
+    // position records: the caller's buffer (a captured graph must not
+    // allocate), else stream-ordered scratch
+    QLoc* loc = reinterpret_cast<QLoc*>(loc_scratch);
+    const bool own = loc == nullptr;
+    if (own) LCP_CUDA_TRY(cudaMallocAsync((void**)&loc, sizeof(QLoc) * (size_t)Q, s));
     LCP_LAUNCH(k_topk_locate, (unsigned)((Q + 255) / 256), 256, 0, s, ix, q, qf, Q, loc);
     // queries per warp: 32 for large batches; fewer for small batches so that
     // the batch still spreads over every SM
@@ -412,8 +415,10 @@ int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, i
         LCP_LAUNCH(k_topk_answer<uint64_t>, grid, kSearchWarps * 32, 0, s, ix, loc, Q, k, qpw, out_ids,
                    out_lcp);
     }
-    LCP_CUDA_TRY(cudaFreeAsync(loc, s));
+    if (own) LCP_CUDA_TRY(cudaFreeAsync(loc, s));
     return LCP_OK;
 }
+
+size_t search_scratch_bytes(int64_t Q) { return sizeof(QLoc) * (size_t)(Q > 0 ? Q : 1); }
 
 }  // namespace lcph

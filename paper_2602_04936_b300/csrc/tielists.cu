@@ -55,6 +55,15 @@ __global__ void __launch_bounds__(kTlWarps * 32) k_heavy_intervals(DevIndex ix, 
     }
 }
 
+// Clears the per-sample node table and the canonical-node flags (one kernel
+// rather than two memsets, so a captured graph keeps its node types).
+__global__ void k_tl_reset(int32_t* __restrict__ tbl, uint8_t* __restrict__ flag, int64_t n) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    tbl[e] = -1;
+    flag[e] = 0;
+}
+
 __global__ void __launch_bounds__(256) k_flag_count(const uint8_t* __restrict__ flag, int64_t n,
                                                     uint64_t* __restrict__ sums) {
     __shared__ uint32_t ws[8];
@@ -184,8 +193,7 @@ int build_tie_lists(lcp_index_s* x, cudaStream_t s) {
     const int64_t nsamp = (N + kBlk - 1) / kBlk;
     const int L1 = x->L + 1;
     const int64_t nslots = nsamp * L1;
-    LCP_CUDA_TRY(cudaMemsetAsync(x->tbl, 0xFF, sizeof(int32_t) * nslots, s));
-    LCP_CUDA_TRY(cudaMemsetAsync(x->slot_flag, 0, (size_t)nslots, s));
+    LCP_LAUNCH(k_tl_reset, (unsigned)((nslots + 255) / 256), 256, 0, s, x->tbl, x->slot_flag, nslots);
     DevIndex ix = dev_view(x);
     LCP_LAUNCH(k_heavy_intervals, (unsigned)((nsamp + kTlWarps - 1) / kTlWarps), kTlWarps * 32, 0, s, ix,
                nsamp, x->tbl, x->slot_flag, x->slot_lo, x->slot_hi);
