@@ -100,6 +100,8 @@ static int dalloc(T** p, size_t count, int64_t* bytes, cudaStream_t s) {
     return LCP_OK;
 }
 
+constexpr int kTieListMinK = 16;
+
 static int alloc_index(lcp_index_s* x, int64_t N, int64_t cap, cudaStream_t s) {
     int64_t& by = x->bytes;
     const int W = x->W;
@@ -123,23 +125,30 @@ static int alloc_index(lcp_index_s* x, int64_t N, int64_t cap, cudaStream_t s) {
     x->st_levels_cap = lev;
     if ((rc = dalloc(&x->st, (size_t)(lev > 0 ? lev : 1) * x->nblk_cap * x->K, &by, s))) return rc;
     if ((rc = dalloc(&x->bkt, ((size_t)1 << x->bits) + 1, &by, s))) return rc;
-    // heavy-node tie lists: one table row per 128-row sample, one list per node
-    x->nsamp_cap = (cap + lcpk::kBlk - 1) / lcpk::kBlk;
-    if (x->nsamp_cap < 1) x->nsamp_cap = 1;
-    const size_t nslots = (size_t)x->nsamp_cap * (size_t)(x->L + 1);
-    x->nlists_cap = 4 * x->nsamp_cap + 64;
-    if ((rc = dalloc(&x->tbl, nslots, &by, s))) return rc;
-    if ((rc = dalloc(&x->slot_flag, nslots, &by, s))) return rc;
-    if ((rc = dalloc(&x->slot_lo, nslots, &by, s))) return rc;
-    if ((rc = dalloc(&x->slot_hi, nslots, &by, s))) return rc;
-    if ((rc = dalloc(&x->slot_list, nslots, &by, s))) return rc;
-    if ((rc = dalloc(&x->tl_sums, (nslots + 2047) / 2048, &by, s))) return rc;
-    if ((rc = dalloc(&x->tl_total, 4, &by, s))) return rc;
-    if ((rc = dalloc(&x->tlists, (size_t)x->nlists_cap * x->K, &by, s))) return rc;
-    if ((rc = dalloc(&x->tlpos, (size_t)x->nlists_cap * x->K, &by, s))) return rc;
+    // heavy-node tie lists: one table row per 128-row sample, one list per
+    // node.  For max_k below kTieListMinK a tie fill from the sparse table
+    // costs about as many loads as one from a list, so the lists (and their
+    // rebuild on every insert) are left out and the search falls back to the
+    // sparse table.
     if ((rc = dalloc(&x->bkt_list, (size_t)1 << x->bits, &by, s))) return rc;
-    if ((rc = dalloc(&x->tl_lo, (size_t)x->nlists_cap, &by, s))) return rc;
-    if ((rc = dalloc(&x->tl_hi, (size_t)x->nlists_cap, &by, s))) return rc;
+    LCP_CUDA_TRY(cudaMemsetAsync(x->bkt_list, 0xFF, sizeof(int32_t) << x->bits, s));
+    if (x->max_k >= kTieListMinK) {
+        x->nsamp_cap = (cap + lcpk::kBlk - 1) / lcpk::kBlk;
+        if (x->nsamp_cap < 1) x->nsamp_cap = 1;
+        const size_t nslots = (size_t)x->nsamp_cap * (size_t)(x->L + 1);
+        x->nlists_cap = 4 * x->nsamp_cap + 64;
+        if ((rc = dalloc(&x->tbl, nslots, &by, s))) return rc;
+        if ((rc = dalloc(&x->slot_flag, nslots, &by, s))) return rc;
+        if ((rc = dalloc(&x->slot_lo, nslots, &by, s))) return rc;
+        if ((rc = dalloc(&x->slot_hi, nslots, &by, s))) return rc;
+        if ((rc = dalloc(&x->slot_list, nslots, &by, s))) return rc;
+        if ((rc = dalloc(&x->tl_sums, (nslots + 2047) / 2048, &by, s))) return rc;
+        if ((rc = dalloc(&x->tl_total, 4, &by, s))) return rc;
+        if ((rc = dalloc(&x->tlists, (size_t)x->nlists_cap * x->K, &by, s))) return rc;
+        if ((rc = dalloc(&x->tlpos, (size_t)x->nlists_cap * x->K, &by, s))) return rc;
+        if ((rc = dalloc(&x->tl_lo, (size_t)x->nlists_cap, &by, s))) return rc;
+        if ((rc = dalloc(&x->tl_hi, (size_t)x->nlists_cap, &by, s))) return rc;
+    }
     if ((rc = dalloc(&x->status, 1, &by, s))) return rc;
     LCP_CUDA_TRY(cudaMemsetAsync(x->status, 0, sizeof(int), s));
     if (cap > N) {
@@ -233,7 +242,7 @@ int lcp_index_build(const void* d_tokens, int64_t N, lcp_format_t fmt, int64_t c
         lcpk::RowFmt f = lcpk::make_fmt(x->tb, x->L, d_tokens);
         rc = build_sorted_ids(d_tokens, f, N, x->buf[0].ids, x->status, s);
         if (rc == LCP_OK) rc = gather_rows_and_lcp(d_tokens, f, N, x->buf[0].ids, x->buf[0], x->W, s);
-        if (rc == LCP_OK) rc = build_aux(x, s);
+        if (rc == LCP_OK) rc = build_aux(x, s, false);
     }
     if (rc == LCP_OK) {
         cudaError_t e = cudaGetLastError();

@@ -266,27 +266,79 @@ __global__ void k_min32(const uint8_t* __restrict__ in, int64_t n_in, uint8_t* _
     out[b] = (uint8_t)m;
 }
 
-// One warp per 128-position block: (id, offset) keys sorted ascending with the
-// register bitonic network; positions past n become padding (0xFFFFFFFF).
-__global__ void __launch_bounds__(128) k_sort_blocks(const int32_t* __restrict__ ids, int64_t n,
-                                                     int64_t nblk, uint32_t* __restrict__ sblk,
-                                                     uint8_t* __restrict__ soff) {
-    const int64_t b = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
-    if (b >= nblk) return;
-    const int lane = (int)lane_id();
+constexpr int kAuxThreads = 1024;
+constexpr int64_t kTreeChunk = 32768;  // H entries per tree CTA: 1024 x 32
+
+struct AuxArgs {
+    const uint8_t* H;
+    int64_t N;
+    uint8_t* hmin;
+    int lev;              // tree levels written here (<= 3)
+    int64_t hoff[3], hlen[3];
+    unsigned tree_ctas;
+    const int32_t* ids;
+    int64_t nblk;
+    uint32_t* sblk;
+    uint8_t* soff;
+};
+
+// Minimum of the 32 H entries starting at s (entries past n count as 255).
+__device__ __forceinline__ uint32_t min32_bytes(const uint8_t* __restrict__ H, int64_t s, int64_t n) {
+    if (s + 32 <= n) {
+        const uint4 a = *reinterpret_cast<const uint4*>(H + s);
+        const uint4 b = *reinterpret_cast<const uint4*>(H + s + 16);
+        uint32_t m = __vminu4(__vminu4(__vminu4(a.x, a.y), __vminu4(a.z, a.w)),
+                              __vminu4(__vminu4(b.x, b.y), __vminu4(b.z, b.w)));
+        m = __vminu4(m, m >> 16);
+        m = __vminu4(m, m >> 8);
+        return m & 255u;
+    }
+    uint32_t m = 255;
+    for (int64_t i = s; i < n && i < s + 32; ++i) m = min(m, (uint32_t)H[i]);
+    return m;
+}
+
+// CTAs below tree_ctas: levels 1..3 of the min tree for 32768 consecutive H
+// entries (thread -> level-1 entry, warp -> level 2, CTA -> level 3).  The
+// rest: one warp per 128-position block, its (id, offset) pairs sorted
+// ascending with the register bitonic network (padding 0xFFFFFFFF).
+__global__ void __launch_bounds__(kAuxThreads) k_aux_tree_blocks(AuxArgs a) {
+    const int lane = (int)lane_id(), warp = threadIdx.x >> 5;
+    if (blockIdx.x < a.tree_ctas) {
+        __shared__ uint32_t wmin[kAuxThreads / 32];
+        const int64_t e1 = (int64_t)blockIdx.x * kAuxThreads + threadIdx.x;  // level-1 entry
+        const uint32_t m1 = e1 < a.hlen[0] ? min32_bytes(a.H, e1 * 32, a.N) : 255u;
+        if (e1 < a.hlen[0]) a.hmin[a.hoff[0] + e1] = (uint8_t)m1;
+        if (a.lev < 2) return;
+        const uint32_t m2 = __reduce_min_sync(0xffffffffu, m1);
+        const int64_t e2 = (int64_t)blockIdx.x * 32 + warp;
+        if (lane == 0) {
+            if (e2 < a.hlen[1]) a.hmin[a.hoff[1] + e2] = (uint8_t)m2;
+            wmin[warp] = m2;
+        }
+        if (a.lev < 3) return;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t m3 = __reduce_min_sync(0xffffffffu, wmin[lane]);
+            if (lane == 0 && (int64_t)blockIdx.x < a.hlen[2]) a.hmin[a.hoff[2] + blockIdx.x] = (uint8_t)m3;
+        }
+        return;
+    }
+    const int64_t b = (int64_t)(blockIdx.x - a.tree_ctas) * (kAuxThreads / 32) + warp;
+    if (b >= a.nblk) return;
     uint64_t v[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const int off = lane * 4 + e;
         const int64_t p = b * kBlk + off;
-        v[e] = p < n ? (((uint64_t)(uint32_t)ids[p] << 8) | (uint64_t)off) : ~0ull;
+        v[e] = p < a.N ? (((uint64_t)(uint32_t)a.ids[p] << 8) | (uint64_t)off) : ~0ull;
     }
     warp_bitonic<4, uint64_t>(v);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const int t = lane * 4 + e;
-        sblk[b * kBlk + t] = v[e] == ~0ull ? kInf : (uint32_t)(v[e] >> 8);
-        soff[b * kBlk + t] = (uint8_t)(v[e] & 255u);
+        a.sblk[b * kBlk + t] = v[e] == ~0ull ? kInf : (uint32_t)(v[e] >> 8);
+        a.soff[b * kBlk + t] = (uint8_t)(v[e] & 255u);
     }
 }
 
@@ -475,32 +527,50 @@ int adjacent_lcp(const uint64_t* rows, int64_t N, int W, int L, int tpw, int bit
     return LCP_OK;
 }
 
-int build_aux(lcp_index_s* x, cudaStream_t s) {
+int build_aux(lcp_index_s* x, cudaStream_t s, bool merged) {
     const int64_t N = x->N;
     lcp_buffers& b = x->buf[x->cur];
     if (N <= 0) return LCP_OK;
-    LCP_LAUNCH(k_inverse, blocks_for(N, 256), 256, 0, s, b.ids, N, x->pos);
-    LCP_LAUNCH(k_buckets, blocks_for((1ll << x->bits) + 1, 256), 256, 0, s, b.head, N, x->bits, x->bkt);
-    // min tree over H
+    if (!merged) {  // an insert's merge pass already wrote pos and the buckets
+        LCP_LAUNCH(k_inverse, blocks_for(N, 256), 256, 0, s, b.ids, N, x->pos);
+        LCP_LAUNCH(k_buckets, blocks_for((1ll << x->bits) + 1, 256), 256, 0, s, b.head, N, x->bits, x->bkt);
+    }
+    // min tree over H: level j+1 = minima of 32 consecutive level-j entries,
+    // built while a level has more than 32 entries
     int64_t len = N;
-    const uint8_t* in = b.H;
     x->hlen[0] = N;
     int lev = 0;
     int64_t off = 0;
     while (len > 32 && lev < kMaxHLev) {
-        int64_t nl = (len + 31) / 32;
+        const int64_t nl = (len + 31) / 32;
         ++lev;
         x->hoff[lev] = off;
         x->hlen[lev] = nl;
-        LCP_LAUNCH(k_min32, blocks_for(nl, 256), 256, 0, s, in, len, x->hmin + off, nl);
-        in = x->hmin + off;
         off += nl;
         len = nl;
     }
     x->hlev = lev;
-    // sorted blocks and sparse table of K smallest ids
-    int64_t nblk = (N + kBlk - 1) / kBlk;
-    LCP_LAUNCH(k_sort_blocks, (unsigned)((nblk + 3) / 4), 128, 0, s, b.ids, N, nblk, x->sblk, x->soff);
+    // levels 1..3 of the tree and the sorted blocks in one launch
+    const int64_t nblk = (N + kBlk - 1) / kBlk;
+    AuxArgs a;
+    a.H = b.H;
+    a.N = N;
+    a.hmin = x->hmin;
+    a.lev = lev < 3 ? lev : 3;
+    for (int j = 1; j <= 3; ++j) {
+        a.hoff[j - 1] = x->hoff[j];
+        a.hlen[j - 1] = j <= lev ? x->hlen[j] : 0;
+    }
+    a.tree_ctas = lev > 0 ? blocks_for(N, kTreeChunk) : 0;
+    a.ids = b.ids;
+    a.nblk = nblk;
+    a.sblk = x->sblk;
+    a.soff = x->soff;
+    LCP_LAUNCH(k_aux_tree_blocks, a.tree_ctas + blocks_for(nblk, kAuxThreads / 32), kAuxThreads, 0, s, a);
+    for (int j = 4; j <= lev; ++j)  // only past 2^20 rows
+        LCP_LAUNCH(k_min32, blocks_for(x->hlen[j], 256), 256, 0, s, x->hmin + x->hoff[j - 1], x->hlen[j - 1],
+                   x->hmin + x->hoff[j], x->hlen[j]);
+    // sparse table of K smallest ids over runs of 2^j blocks
     int K = x->K;
     for (int j = 1; j <= x->st_levels_cap && (1ll << j) <= nblk; ++j) {
         int64_t half = 1ll << (j - 1);

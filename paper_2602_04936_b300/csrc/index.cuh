@@ -137,7 +137,10 @@ int gather_rows_and_lcp(const void* tokens, const lcpk::RowFmt& f, int64_t N, co
 int adjacent_lcp(const uint64_t* rows, int64_t N, int W, int L, int tpw, int bits, uint8_t* H,
                  cudaStream_t s);
 // pos, min tree and tie tables of the current buffers.
-int build_aux(lcp_index_s* x, cudaStream_t s);
+// Rebuilds the derived tables (pos, buckets, min tree, sorted blocks, sparse
+// table, tie lists) from the current buffer set; `merged`: an insert's merge
+// pass already wrote pos and the buckets.
+int build_aux(lcp_index_s* x, cudaStream_t s, bool merged);
 // heavy-node tie lists (needs the min tree, sorted blocks and sparse table).
 int build_tie_lists(lcp_index_s* x, cudaStream_t s);
 

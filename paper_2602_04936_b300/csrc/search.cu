@@ -303,7 +303,7 @@ __device__ void topk_one(const DevIndex& ix, QWarp& S, int64_t p, int lL, int lR
     // a heavy trie node: its precomputed K smallest ids (with their sorted
     // positions), minus A's members
     if (!filled && hiv - lov > kBlk) {
-        if (li == -2) li = ix.tbl[((lov + kBlk - 1) / kBlk) * ix.L1 + dstar];
+        if (li == -2) li = ix.tbl ? ix.tbl[((lov + kBlk - 1) / kBlk) * ix.L1 + dstar] : -1;
         if (li >= 0) {
             const uint32_t* list = ix.tlists + (size_t)li * ix.K;
             const int32_t* lpos = ix.tlpos + (size_t)li * ix.K;
