@@ -52,6 +52,11 @@ def parse_args():
     ap.add_argument("--queries", type=int, default=0, help="override Q (profiling cases)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip latency / insert / e2e / cpu legs (profiling runs)")
+    ap.add_argument("--profile", choices=["search", "gnc"], default=None,
+                    help="run one small fixed case for an ncu capture and exit (no JSON line): "
+                         "'search' builds the workload's index and answers --queries (default "
+                         "100,000) twice; 'gnc' builds 997 sensor-stream steps and runs 3 more "
+                         "insert+query steps inside an NVTX range named 'steps'")
     return ap.parse_args()
 
 
@@ -139,17 +144,43 @@ class ClockSampler:
                 "power_w_max": max(pw), "reasons": sorted(reasons)}
 
 
-def _nvml_handle(device_index):
-    """NVML handle of a CUDA device, matched by UUID (NVML numbers the
-    machine's GPUs, CUDA only the visible ones)."""
-    import pynvml
-    import torch
-    pynvml.nvmlInit()
-    uuid = "GPU-" + str(torch.cuda.get_device_properties(device_index).uuid)
-    try:
-        return pynvml, pynvml.nvmlDeviceGetHandleByUUID(uuid)
-    except Exception:
-        return pynvml, pynvml.nvmlDeviceGetHandleByIndex(device_index)
+class _Nvml:
+    """The few NVML calls the bench needs, through ctypes on the driver's
+    libnvidia-ml (no Python binding is assumed)."""
+
+    CLOCK_SM = 1
+
+    def __init__(self, device_index):
+        import ctypes
+        import torch
+        self.c = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit_v2 failed")
+        self.h = ctypes.c_void_p()
+        uuid = ("GPU-" + str(torch.cuda.get_device_properties(device_index).uuid)).encode()
+        if self.lib.nvmlDeviceGetHandleByUUID(ctypes.c_char_p(uuid), ctypes.byref(self.h)) != 0:
+            if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(device_index), ctypes.byref(self.h)) != 0:
+                raise RuntimeError("no NVML handle for cuda:%d" % device_index)
+
+    def _call(self, fn, ctype, *args):
+        v = ctype()
+        rc = getattr(self.lib, fn)(self.h, *args, self.c.byref(v))
+        if rc != 0:
+            raise RuntimeError("%s returned %d" % (fn, rc))
+        return v.value
+
+    def energy_mj(self):
+        return self._call("nvmlDeviceGetTotalEnergyConsumption", self.c.c_ulonglong)
+
+    def sm_mhz(self):
+        return self._call("nvmlDeviceGetClockInfo", self.c.c_uint, self.c.c_int(self.CLOCK_SM))
+
+    def sm_max_mhz(self):
+        return self._call("nvmlDeviceGetMaxClockInfo", self.c.c_uint, self.c.c_int(self.CLOCK_SM))
+
+    def event_reasons(self):
+        return self._call("nvmlDeviceGetCurrentClocksEventReasons", self.c.c_ulonglong)
 
 
 class EnergyMeter:
@@ -157,19 +188,23 @@ class EnergyMeter:
     driver loaded); None, with the reason kept, where NVML cannot give it."""
 
     def __init__(self, device_index):
-        self.h, self.error = None, None
+        self.nv, self.error = None, None
         try:
-            self.nv, h = _nvml_handle(device_index)
-            self.nv.nvmlDeviceGetTotalEnergyConsumption(h)
-            self.h = h
+            nv = _Nvml(device_index)
+            nv.energy_mj()
+            self.nv = nv
         except Exception as e:  # noqa: BLE001 - reported in the JSON line
             self.error = "%s: %s" % (type(e).__name__, e)
 
+    @property
+    def h(self):
+        return self.nv
+
     def read_j(self):
-        if self.h is None:
+        if self.nv is None:
             return None
         try:
-            return self.nv.nvmlDeviceGetTotalEnergyConsumption(self.h) / 1e3
+            return self.nv.energy_mj() / 1e3
         except Exception:
             return None
 
@@ -183,30 +218,28 @@ class NvmlClockSampler:
 
     def __init__(self, device_index):
         import threading
-        self.samples, self.h, self.stop_ev = [], None, threading.Event()
+        self.samples, self.nv, self.stop_ev = [], None, threading.Event()
         try:
-            self.nv, self.h = _nvml_handle(device_index)
-            self.max_mhz = self.nv.nvmlDeviceGetMaxClockInfo(self.h, self.nv.NVML_CLOCK_SM)
+            self.nv = _Nvml(device_index)
+            self.max_mhz = self.nv.sm_max_mhz()
         except Exception:
-            self.h = None
+            self.nv = None
         self.t = threading.Thread(target=self._run, daemon=True)
 
     def _run(self):
         while not self.stop_ev.is_set():
             try:
-                mhz = self.nv.nvmlDeviceGetClockInfo(self.h, self.nv.NVML_CLOCK_SM)
-                why = self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
-                self.samples.append((mhz, why))
+                self.samples.append((self.nv.sm_mhz(), self.nv.event_reasons()))
             except Exception:
                 return
             time.sleep(0.002)
 
     def start(self):
-        if self.h is not None:
+        if self.nv is not None:
             self.t.start()
 
     def stop(self):
-        if self.h is None:
+        if self.nv is None:
             return None
         self.stop_ev.set()
         self.t.join(timeout=2)
@@ -253,7 +286,8 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -278,11 +312,16 @@ def oracle_rate(S, Qs, k, budget_s=12.0, max_q=4096):
     return done / elapsed, done, elapsed, threads
 
 
-def search_algorithmic_bytes(N, L, tb, k):
-    """Bytes one query of the indexed search must touch: the query row, one 32-byte sector per binary-search level, the H bytes
-    and ids of about k items around the insertion point, and its k (id, lcp)
-    results."""
-    return L * tb + math.ceil(math.log2(max(N, 2))) * 32 + k * 5 + k * 5
+def answer_algorithmic_bytes(k):
+    """Bytes one query's answer kernel must move: its 16-byte position record,
+    the H byte and id of its k winners, and its k (id, lcp) results."""
+    return 16 + k * 5 + k * 5
+
+
+def locate_algorithmic_bytes(N, L, tb):
+    """Bytes one query's locate kernel must move: the query row, one 32-byte
+    sector per binary-search level and its 16-byte position record."""
+    return L * tb + math.ceil(math.log2(max(N, 2))) * 32 + 16
 
 
 def kernel_source_hash():
@@ -300,14 +339,17 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
-def committed_traffic(kernel):
+def committed_traffic(kernel, Q):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/traffic.json), scaled from its captured batch to Q queries;
+    None when the kernel's sources changed since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p)).get(kernel)
     if not d or d.get("source_hash") != kernel_source_hash():
         return None
-    return d.get("dram_bytes_per_launch")
+    return round(d["dram_bytes_per_launch"] * Q / d["queries"])
 
 
 # ---------------------------------------------------------------------------
@@ -361,14 +403,16 @@ def run_ours(args, world, rank, local):
     barrier(world)
     torch.cuda.synchronize()
     launches0 = lcp.lcp_launch_count()
-    e_start = meter.read_j()
+    lcp.lcp_kernel_timing(True)  # per-kernel CUDA events on the launching stream
     t_start.record(stream)
     for i in range(args.steps):
         step(evs[i])
     t_end.record(stream)
     torch.cuda.synchronize()
-    e_end = meter.read_j()
     launches = lcp.lcp_launch_count() - launches0
+    ans_ms, ans_n = lcp.lcp_kernel_time("k_topk_answer")
+    loc_ms, loc_n = lcp.lcp_kernel_time("k_topk_locate")
+    lcp.lcp_kernel_timing(False)
     barrier(world)
     clocks = clk.stop()
     fine = nclk.stop()
@@ -381,19 +425,39 @@ def run_ours(args, world, rank, local):
     build_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
     query_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
 
-    # roofline of the dominant kernel: the indexed search (one launch per call)
+    # roofline of the dominant kernel: the answer half of the indexed search
     peak, peak_kind = measured_peaks()
-    per_q = search_algorithmic_bytes(N, L, tb, k)
-    achieved = Q * per_q / (query_ms / 1e3) / 1e9
-    traffic = committed_traffic("k_topk_search")
-    roofline = {"kernel": "k_topk_search", "bound": "hbm", "achieved": round(achieved, 1),
+    ans_launch_ms = ans_ms / max(ans_n, 1)
+    loc_launch_ms = loc_ms / max(loc_n, 1)
+    per_q = answer_algorithmic_bytes(k)
+    achieved = Q * per_q / (ans_launch_ms / 1e3) / 1e9
+    loc_per_q = locate_algorithmic_bytes(N, L, tb)
+    loc_achieved = Q * loc_per_q / (loc_launch_ms / 1e3) / 1e9
+    roofline = {"kernel": "k_topk_answer", "bound": "hbm", "achieved": round(achieved, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.4 TB/s",
-                "traffic": traffic, "algorithmic_bytes_per_launch": Q * per_q,
-                "bytes_per_query": per_q, "launch_ms": round(query_ms, 4)}
+                "traffic": committed_traffic("k_topk_answer", Q),
+                "algorithmic_bytes_per_launch": Q * per_q, "bytes_per_query": per_q,
+                "launch_ms": round(ans_launch_ms, 4), "launches_timed": ans_n,
+                "timing": "CUDA events around each launch on its stream, timed region",
+                "other_kernels": {"k_topk_locate": {
+                    "launch_ms": round(loc_launch_ms, 4), "bytes_per_query": loc_per_q,
+                    "achieved": round(loc_achieved, 1), "frac": round(loc_achieved / peak, 4)}}}
 
-    jq = joules_per(e_start, e_end, Q * args.steps)
+    # energy: NVML's counter advances in coarse steps, so each figure comes
+    # from its own loop of a couple of seconds (idle gaps excluded)
+    jq = None
+    if meter.h is not None and not args.no_extras:
+        idx_e = lcp.lcp_index_build(dS, max_k=k)
+        reps_e = max(1, int(2000.0 / max(query_ms, 1e-3)))
+        torch.cuda.synchronize()
+        e0 = meter.read_j()
+        for _ in range(reps_e):
+            lcp.lcp_topk_batch(idx_e, dQ, k, out_ids, out_lcp)
+        torch.cuda.synchronize()
+        jq = joules_per(e0, meter.read_j(), Q * reps_e)
+        idx_e.close()
     paths = {"indexed": {"build_ms": round(build_ms, 3), "query_ms": round(query_ms, 3),
                          "energy_j_per_query": jq,
                          "qps_query_only": round(Q / (query_ms / 1e3), 1),
@@ -465,37 +529,47 @@ def run_ours(args, world, rank, local):
         glcp = torch.empty((1000, 5), dtype=torch.uint8, device=device)
         finals = {}
         for mode in ("direct", "graph"):
-            gi = lcp.lcp_index_build(torch.zeros((0, 8), dtype=torch.int16, device=device), max_k=5,
-                                     capacity=1_000_000)
-            gstep = lcp.Step(gi, 1000, 1000, 5) if mode == "graph" else None
-            gev = [torch.cuda.Event(enable_timing=True) for _ in range(1001)]
-            torch.cuda.synchronize()
-            e_g0 = meter.read_j()
-            h0 = time.perf_counter()
-            gev[0].record(stream)
-            for t in range(1000):
-                if gstep is None:
-                    lcp.lcp_index_insert(gi, dsteps[t])
-                    lcp.lcp_topk_batch(gi, dsteps[t], 5, gids, glcp)
+            # the stream runs 5 times from an empty index: timings from the
+            # first run, energy summed over all five (about half a second)
+            e_sum, e_ok = 0.0, meter.h is not None
+            for rep in range(5):
+                gi = lcp.lcp_index_build(torch.zeros((0, 8), dtype=torch.int16, device=device), max_k=5,
+                                         capacity=1_000_000)
+                gstep = lcp.Step(gi, 1000, 1000, 5) if mode == "graph" else None
+                gev = [torch.cuda.Event(enable_timing=True) for _ in range(1001)]
+                torch.cuda.synchronize()
+                e_g0 = meter.read_j()
+                h0 = time.perf_counter()
+                gev[0].record(stream)
+                for t in range(1000):
+                    if gstep is None:
+                        lcp.lcp_index_insert(gi, dsteps[t])
+                        lcp.lcp_topk_batch(gi, dsteps[t], 5, gids, glcp)
+                    else:
+                        gstep.run(dsteps[t], dsteps[t], gids, glcp)
+                    gev[t + 1].record(stream)
+                host_s = time.perf_counter() - h0
+                torch.cuda.synchronize()
+                e_g1 = meter.read_j()
+                if e_g0 is None or e_g1 is None:
+                    e_ok = False
                 else:
-                    gstep.run(dsteps[t], dsteps[t], gids, glcp)
-                gev[t + 1].record(stream)
-            host_s = time.perf_counter() - h0
-            torch.cuda.synchronize()
-            e_g1 = meter.read_j()
-            st = np.array([gev[t].elapsed_time(gev[t + 1]) for t in range(1000)])
-            rec = {"steps": 1000, "final_N": gi.N, "steps_per_s": round(1e3 / st.mean(), 1),
-                   "p50_ms": round(float(np.percentile(st, 50)), 4),
-                   "p99_ms": round(float(np.percentile(st, 99)), 4),
-                   "last_step_ms": round(float(st[-1]), 4),
-                   "host_issue_ms_per_step": round(host_s, 4),
-                   "energy_j_per_step": joules_per(e_g0, e_g1, 1000)}
-            if gstep is not None:
-                rec["graph_instantiations"] = gstep.stats()[1]
-                gstep.close()
-            finals[mode] = (gids.clone(), glcp.clone())
+                    e_sum += e_g1 - e_g0
+                if rep == 0:
+                    st = np.array([gev[t].elapsed_time(gev[t + 1]) for t in range(1000)])
+                    rec = {"steps": 1000, "final_N": gi.N, "steps_per_s": round(1e3 / st.mean(), 1),
+                           "p50_ms": round(float(np.percentile(st, 50)), 4),
+                           "p99_ms": round(float(np.percentile(st, 99)), 4),
+                           "last_step_ms": round(float(st[-1]), 4),
+                           "host_issue_ms_per_step": round(host_s, 4)}
+                    if gstep is not None:
+                        rec["graph_instantiations"] = gstep.stats()[1]
+                    finals[mode] = (gids.clone(), glcp.clone())
+                if gstep is not None:
+                    gstep.close()
+                gi.close()
+            rec["energy_j_per_step"] = e_sum / 5000 if e_ok else None
             paths["insert_gnc" if mode == "direct" else "insert_gnc_graph"] = rec
-            gi.close()
         paths["insert_gnc_graph"]["last_step_equal_direct"] = bool(
             torch.equal(finals["direct"][0], finals["graph"][0])
             and torch.equal(finals["direct"][1], finals["graph"][1]))
@@ -642,8 +716,42 @@ def run_reference(args, world, rank):
                     "d2h_bytes_per_step": 0}}
 
 
+def run_profile(args):
+    """Small fixed cases for ncu captures (the timing of record is the bench)."""
+    import torch
+    import paper_2602_04936_b300 as lcp
+    device = torch.device("cuda", 0)
+    if args.profile == "search":
+        w = W.WORKLOADS[args.workload]
+        Q = args.queries or 100_000
+        S = W.zipf_prefix_rows(w["N"], w["L"], w["vocab"], w["s"], w["seed"])
+        Qs = W.zipf_prefix_queries(S, Q, w["vocab"], w["s"], w["seed"])
+        idx = lcp.lcp_index_build(to_dev(S, device), max_k=w["k"])
+        dQ = to_dev(Qs, device)
+        for _ in range(2):
+            lcp.lcp_topk_batch(idx, dQ, w["k"])
+        torch.cuda.synchronize()
+        idx.close()
+    else:
+        g = W.GncStream(sensors=1000, seed=5)
+        steps = to_dev(np.stack([g.step() for _ in range(1000)]), device)
+        ix = lcp.lcp_index_build(steps[:997].reshape(-1, 8), max_k=5, capacity=1_000_000)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("steps")
+        for t in range(997, 1000):
+            lcp.lcp_index_insert(ix, steps[t])
+            lcp.lcp_topk_batch(ix, steps[t], 5)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        ix.close()
+    print("profile case %s done" % args.profile, flush=True)
+
+
 def main():
     args = parse_args()
+    if args.profile:
+        run_profile(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -177,6 +177,24 @@ LCP_API int lcp_scan_topk_noalloc(const void* d_tokens, int64_t N, lcp_format_t 
                                   uint8_t* d_out_lcp, lcp_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Sharded index: merge of per-shard answers.  The rows are partitioned by
+ * original-id range over P shards (shard s holds global ids h_bases[s] ..),
+ * each shard's index answers the same Q queries with its local ids, and this
+ * call merges the P answers into the global top k.  Each shard row is ordered
+ * by (LCP desc, id asc) as lcp_topk_batch returns it, so the global answer is
+ * the k smallest keys (255 - lcp) << 32 | (base + id) over all shards -- the
+ * same bytes a single index over all rows returns (Definition "Top-k LCP
+ * Retrieval"; keys are unique).  The paper runs one index; the sharded
+ * layout is this library's.
+ * d_ids [P, Q, k] int32 and d_lcp [P, Q, k] uint8: device, shard-major, as
+ * P stacked lcp_topk_batch outputs (padding id -1 allowed); h_bases [P]: host,
+ * 0 <= base < 2^31; d_out_* [Q, k]: device.  1 <= P <= LCP_SHARD_MAX.
+ * ---------------------------------------------------------------------- */
+#define LCP_SHARD_MAX 32
+LCP_API int lcp_shard_merge(const int32_t* d_ids, const uint8_t* d_lcp, int32_t P, const int64_t* h_bases,
+                            int64_t Q, int32_t k, int32_t* d_out_ids, uint8_t* d_out_lcp, lcp_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Streaming step as a CUDA graph: insert n rows, then answer Q queries --
  * the guidance/navigation stream of the paper (Sec. 1 Example 1, Sec. 7
  * Table 7: every control step stores the current sensor readings and
@@ -300,6 +318,16 @@ LCP_API int lcp_device_status(void);
 
 /* Number of kernels this library has launched in this process. */
 LCP_API int64_t lcp_launch_count(void);
+
+/* Per-kernel timing for profiling (the paper has no counterpart).  While
+ * enabled, the search, scan and insert kernels are bracketed by CUDA events
+ * on their launching stream (not inside a stream capture); enabling clears
+ * the accumulated figures.  lcp_kernel_time waits for the recorded events
+ * and returns the total device time and launch count of the kernels whose
+ * name starts with `prefix` (e.g. "k_topk_answer").  Adds two event records
+ * per launch, so leave it off where launch overhead matters. */
+LCP_API int lcp_kernel_timing(int enable);
+LCP_API int lcp_kernel_time(const char* prefix, double* total_ms, int64_t* launches);
 
 /* Test hook for the bounded-wait machinery: launches one kernel that waits
  * for a device flag nobody sets, with the given spin limit, and returns the

@@ -47,9 +47,10 @@ ABI_SYMBOLS = (
     "lcp_topk_batch", "lcp_topk_batch_host", "lcp_scan_topk", "lcp_index_size",
     "lcp_index_export", "lcp_index_sync", "lcp_index_destroy", "lcp_device_status",
     "lcp_launch_count", "lcp_debug_bounded_wait", "lcp_scan_topk_noalloc",
+    "lcp_kernel_timing", "lcp_kernel_time",
     "lcp_session_create", "lcp_session_add_index", "lcp_session_submit", "lcp_session_poll",
     "lcp_session_stats", "lcp_session_destroy", "lcp_session_replay",
-    "lcp_step_create", "lcp_step_run", "lcp_step_stats", "lcp_step_destroy",
+    "lcp_step_create", "lcp_step_run", "lcp_step_stats", "lcp_step_destroy", "lcp_shard_merge",
 )
 
 
@@ -102,6 +103,9 @@ def _load():
         "lcp_index_destroy": ([vp], ctypes.c_int),
         "lcp_device_status": ([], ctypes.c_int),
         "lcp_launch_count": ([], i64),
+        "lcp_kernel_timing": ([ctypes.c_int], ctypes.c_int),
+        "lcp_kernel_time": ([ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)],
+                            ctypes.c_int),
         "lcp_debug_bounded_wait": ([i64, vp], ctypes.c_int),
         "lcp_scan_topk_noalloc": ([vp, i64, _Format, vp, i64, i32, vp, vp, vp], ctypes.c_int),
         "lcp_session_create": ([ctypes.POINTER(SessionConfig), ctypes.POINTER(vp)], ctypes.c_int),
@@ -118,6 +122,7 @@ def _load():
         "lcp_step_run": ([vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "lcp_step_stats": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64)], ctypes.c_int),
         "lcp_step_destroy": ([vp], ctypes.c_int),
+        "lcp_shard_merge": ([vp, vp, i32, ctypes.POINTER(i64), i64, i32, vp, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -341,8 +346,42 @@ def lcp_launch_count() -> int:
     return int(_lib.lcp_launch_count())
 
 
+def lcp_kernel_timing(enable: bool) -> None:
+    """Per-kernel CUDA-event timing on/off (enabling clears the totals)."""
+    _check(_lib.lcp_kernel_timing(1 if enable else 0), "lcp_kernel_timing")
+
+
+def lcp_kernel_time(prefix: str):
+    """(total device ms, launches) of timed kernels whose name starts with prefix."""
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(_lib.lcp_kernel_time(prefix.encode(), ctypes.byref(ms), ctypes.byref(n)), "lcp_kernel_time")
+    return ms.value, n.value
+
+
 def lcp_debug_bounded_wait(spin_limit: int, stream=None) -> int:
     return _lib.lcp_debug_bounded_wait(spin_limit, _stream(stream))
+
+
+LCP_SHARD_MAX = 32
+
+
+def lcp_shard_merge(ids: torch.Tensor, lcp: torch.Tensor, bases, out_ids=None, out_lcp=None, stream=None):
+    """Global top k from P shard answers: ids/lcp [P, Q, k] (device, each
+    shard's lcp_topk_batch output with local ids), bases = first global id of
+    each shard.  Returns ([Q, k] int32, [Q, k] uint8)."""
+    if ids.dim() != 3 or tuple(lcp.shape) != tuple(ids.shape):
+        raise ValueError("ids and lcp must both be [P, Q, k]")
+    if ids.dtype != torch.int32 or lcp.dtype != torch.uint8:
+        raise TypeError("ids must be int32 and lcp uint8")
+    P, Q, k = ids.shape
+    if len(bases) != P:
+        raise ValueError("one base per shard")
+    hb = (ctypes.c_int64 * P)(*[int(b) for b in bases])
+    out_ids, out_lcp = _outputs(Q, k, ids.device, out_ids, out_lcp)
+    with torch.cuda.device(ids.device):
+        _check(_lib.lcp_shard_merge(_ptr(ids.contiguous()), _ptr(lcp.contiguous()), P, hb, Q, k,
+                                    _ptr(out_ids), _ptr(out_lcp), _stream(stream)), "lcp_shard_merge")
+    return out_ids, out_lcp
 
 
 class Step:

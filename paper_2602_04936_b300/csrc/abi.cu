@@ -1,8 +1,11 @@
 // C ABI entry points (see include/lcp.h for the contract of each call).
 #include <atomic>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
+#include <string>
+#include <vector>
 
 #include "index.cuh"
 
@@ -12,6 +15,55 @@ static std::atomic<int64_t> g_launches{0};
 static thread_local cudaError_t g_last_cuda = cudaSuccess;
 
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// ---- per-kernel event timing ----
+struct KtRec {
+    const char* name;
+    cudaEvent_t a, b;
+};
+static std::atomic<bool> g_kt_on{false};
+static std::mutex g_kt_mu;
+static std::vector<KtRec> g_kt_pending;
+static std::vector<cudaEvent_t> g_kt_pool;
+static std::map<std::string, std::pair<double, int64_t>> g_kt_total;
+
+static cudaEvent_t kt_event() {  // caller holds g_kt_mu
+    cudaEvent_t e = nullptr;
+    if (!g_kt_pool.empty()) {
+        e = g_kt_pool.back();
+        g_kt_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        e = nullptr;
+    }
+    return e;
+}
+
+bool ktime_on() { return g_kt_on.load(std::memory_order_relaxed); }
+
+void* ktime_begin(const char* name, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+    std::lock_guard<std::mutex> lk(g_kt_mu);
+    KtRec* r = new (std::nothrow) KtRec{name, kt_event(), kt_event()};
+    if (!r || !r->a || !r->b) {
+        if (r) {
+            if (r->a) g_kt_pool.push_back(r->a);
+            if (r->b) g_kt_pool.push_back(r->b);
+            delete r;
+        }
+        return nullptr;
+    }
+    cudaEventRecord(r->a, s);
+    return r;
+}
+
+void ktime_end(void* token, cudaStream_t s) {
+    KtRec* r = static_cast<KtRec*>(token);
+    cudaEventRecord(r->b, s);
+    std::lock_guard<std::mutex> lk(g_kt_mu);
+    g_kt_pending.push_back(*r);
+    delete r;
+}
 
 int cuda_status(cudaError_t e) {
     g_last_cuda = e;
@@ -398,6 +450,48 @@ int lcp_device_status(void) {
 }
 
 int64_t lcp_launch_count(void) { return g_launches.load(); }
+
+int lcp_kernel_timing(int enable) {
+    std::lock_guard<std::mutex> lk(g_kt_mu);
+    if (enable) {
+        for (auto& r : g_kt_pending) {
+            cudaEventSynchronize(r.b);
+            g_kt_pool.push_back(r.a);
+            g_kt_pool.push_back(r.b);
+        }
+        g_kt_pending.clear();
+        g_kt_total.clear();
+    }
+    g_kt_on.store(enable != 0);
+    return LCP_OK;
+}
+
+int lcp_kernel_time(const char* prefix, double* total_ms, int64_t* launches) {
+    if (!prefix) return LCP_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(g_kt_mu);
+    for (auto& r : g_kt_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            auto& t = g_kt_total[r.name];
+            t.first += ms;
+            t.second += 1;
+        }
+        g_kt_pool.push_back(r.a);
+        g_kt_pool.push_back(r.b);
+    }
+    g_kt_pending.clear();
+    double ms = 0;
+    int64_t n = 0;
+    const size_t len = strlen(prefix);
+    for (auto& kv : g_kt_total)
+        if (kv.first.compare(0, len, prefix) == 0) {
+            ms += kv.second.first;
+            n += kv.second.second;
+        }
+    if (total_ms) *total_ms = ms;
+    if (launches) *launches = n;
+    return LCP_OK;
+}
 
 int lcp_debug_bounded_wait(int64_t spin_limit, lcp_stream_t stream) {
     if (spin_limit < 1) return LCP_ERR_INVALID;

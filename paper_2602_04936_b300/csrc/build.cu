@@ -358,39 +358,71 @@ __global__ void k_buckets(const uint64_t* __restrict__ head, int64_t n, int bits
     bkt[t] = (int32_t)lo;
 }
 
-// Sparse-table level j: out[b] = K smallest of lists prev[b] and prev[b+half]
-// (disjoint position spans, so no duplicates).  One warp per b: both lists
-// are staged in shared memory with coalesced loads, then merged by merge path.
-__global__ void __launch_bounds__(256) k_st_level(const uint32_t* __restrict__ prev, int64_t prev_stride,
-                                                  int64_t half, int64_t nb_valid, int K,
-                                                  uint32_t* __restrict__ out) {
-    __shared__ uint32_t buf[8][2 * LCP_INDEX_MAX_K];
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= nb_valid) return;
-    uint32_t* A = buf[threadIdx.x >> 5];
-    uint32_t* B = A + K;
-    const uint32_t* ga = prev + warp * prev_stride;
-    const uint32_t* gb = prev + (warp + half) * prev_stride;
-    for (int t = lane; t < K; t += 32) {
-        A[t] = ga[t];
-        B[t] = gb[t];
-    }
-    __syncwarp();
-    uint32_t* O = out + warp * (int64_t)K;
+// First K entries of the merge of the sorted K-lists A and B (smem) into O
+// (smem or global); lane l writes entries [l*K/32, (l+1)*K/32) by merge path.
+__device__ __forceinline__ void merge_k(const uint32_t* A, const uint32_t* B, uint32_t* O, int K, int lane) {
     const int per = K / 32;
     const int d0 = lane * per;
     int lo = d0 - K > 0 ? d0 - K : 0, hi = d0 < K ? d0 : K;
     while (lo < hi) {
-        int mid = (lo + hi) >> 1;
+        const int mid = (lo + hi) >> 1;
         if (A[mid] <= B[d0 - 1 - mid]) lo = mid + 1;
         else hi = mid;
     }
     int i = lo, j = d0 - lo;
     for (int t = 0; t < per; ++t) {
-        bool takeA = (i < K) && (j >= K || A[i] <= B[j]);
+        const bool takeA = (i < K) && (j >= K || A[i] <= B[j]);
         O[d0 + t] = takeA ? A[i++] : B[j++];
     }
+}
+
+constexpr int kStMaxGroup = 3;  // sparse-table levels per launch (K <= 32)
+
+// Sparse-table levels j .. j+g-1 in one launch, one warp per start block i.
+// Level j+r at i is the K smallest of level j-1 at i + m*half for
+// m < 2^(r+1) (disjoint position spans, so no duplicates): the warp merges
+// those lists pairwise up the tree and writes the tree's left spine, which
+// is exactly levels j .. j+g-1 at i.  Lists of other warps' spines are
+// recomputed rather than waited for (2^g - 1 merges instead of g), trading
+// a little arithmetic for g - 1 fewer launches.
+__global__ void __launch_bounds__(256) k_st_levels(const uint32_t* __restrict__ prev, int64_t prev_stride,
+                                                   int64_t half, int g, int K, int64_t level_stride,
+                                                   int64_t valid0, int64_t valid1, int64_t valid2,
+                                                   uint32_t* __restrict__ out0) {
+    extern __shared__ uint32_t st_smem[];
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= valid0) return;
+    uint32_t* base = st_smem + (size_t)(threadIdx.x >> 5) * (g > 1 ? 6 : 3) * K;
+    uint32_t *A = base, *B = base + K, *S0 = base + 2 * K, *S1 = base + 3 * K, *T0 = base + 4 * K,
+             *T1 = base + 5 * K;
+    // level j at i + m*2*half, m = 0 .. 3: merge of prev lists (2m, 2m+1)
+    auto pair = [&](int64_t m, uint32_t* dst) {
+        const uint32_t* ga = prev + (i + 2 * m * half) * prev_stride;
+        const uint32_t* gb = prev + (i + (2 * m + 1) * half) * prev_stride;
+        for (int t = lane; t < K; t += 32) {
+            A[t] = ga[t];
+            B[t] = gb[t];
+        }
+        __syncwarp();
+        merge_k(A, B, dst, K, lane);
+        __syncwarp();
+    };
+    pair(0, S0);
+    for (int t = lane; t < K; t += 32) out0[i * K + t] = S0[t];
+    if (g < 2 || i >= valid1) return;
+    pair(1, S1);
+    merge_k(S0, S1, T0, K, lane);  // level j+1 at i
+    __syncwarp();
+    for (int t = lane; t < K; t += 32) out0[level_stride + i * K + t] = T0[t];
+    if (g < 3 || i >= valid2) return;
+    pair(2, S0);
+    pair(3, S1);
+    merge_k(S0, S1, T1, K, lane);  // level j+1 at i + 4*half
+    __syncwarp();
+    merge_k(T0, T1, S0, K, lane);  // level j+2 at i
+    __syncwarp();
+    for (int t = lane; t < K; t += 32) out0[2 * level_stride + i * K + t] = S0[t];
 }
 
 }  // namespace lcpk
@@ -570,16 +602,23 @@ int build_aux(lcp_index_s* x, cudaStream_t s, bool merged) {
     for (int j = 4; j <= lev; ++j)  // only past 2^20 rows
         LCP_LAUNCH(k_min32, blocks_for(x->hlen[j], 256), 256, 0, s, x->hmin + x->hoff[j - 1], x->hlen[j - 1],
                    x->hmin + x->hoff[j], x->hlen[j]);
-    // sparse table of K smallest ids over runs of 2^j blocks
-    int K = x->K;
-    for (int j = 1; j <= x->st_levels_cap && (1ll << j) <= nblk; ++j) {
-        int64_t half = 1ll << (j - 1);
-        int64_t valid = nblk - (1ll << j) + 1;
-        const uint32_t* prev = j == 1 ? x->sblk : x->st + (int64_t)(j - 2) * x->nblk_cap * K;
-        int64_t pstride = j == 1 ? kBlk : K;
-        uint32_t* out = x->st + (int64_t)(j - 1) * x->nblk_cap * K;
-        LCP_LAUNCH(k_st_level, blocks_for(valid * 32, 256), 256, 0, s, prev, pstride, half, valid, K,
-                   out);
+    // sparse table of K smallest ids over runs of 2^j blocks, g levels per
+    // launch (recomputation grows as 2^g, so g shrinks as K grows)
+    const int K = x->K;
+    const int gmax = K <= 32 ? kStMaxGroup : (K <= 64 ? 2 : 1);
+    const int64_t lstride = x->nblk_cap * K;
+    for (int j = 1; j <= x->st_levels_cap && (1ll << j) <= nblk;) {
+        int g = 1;
+        while (g < gmax && j + g <= x->st_levels_cap && (1ll << (j + g)) <= nblk) ++g;
+        const int64_t half = 1ll << (j - 1);
+        int64_t valid[3] = {0, 0, 0};
+        for (int r = 0; r < g; ++r) valid[r] = nblk - (1ll << (j + r)) + 1;
+        const uint32_t* prev = j == 1 ? x->sblk : x->st + (int64_t)(j - 2) * lstride;
+        const int64_t pstride = j == 1 ? kBlk : K;
+        uint32_t* out = x->st + (int64_t)(j - 1) * lstride;
+        LCP_LAUNCH(k_st_levels, blocks_for(valid[0] * 32, 256), 256, (size_t)8 * (g > 1 ? 6 : 3) * K * sizeof(uint32_t), s,
+                   prev, pstride, half, g, K, lstride, valid[0], valid[1], valid[2], out);
+        j += g;
     }
     return build_tie_lists(x, s);
 }

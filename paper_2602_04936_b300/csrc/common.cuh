@@ -120,12 +120,25 @@ void count_launch(int n = 1);
 int cuda_status(cudaError_t e);  // maps to LCP_ERR_* and records the last error text
 int* lib_status_word();          // device pointer to the library-wide status word
 int sm_count();                  // multiprocessors of the current device (cached)
+// Optional per-kernel timing (lcp_kernel_timing): CUDA events recorded on the
+// launching stream around the kernel; off by default and inside graph capture.
+bool ktime_on();
+void* ktime_begin(const char* name, cudaStream_t s);
+void ktime_end(void* token, cudaStream_t s);
 }  // namespace lcph
 
 #define LCP_LAUNCH(kern, grid, block, smem, stream, ...)                 \
     do {                                                                 \
         kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);        \
         lcph::count_launch();                                            \
+    } while (0)
+
+// LCP_LAUNCH with per-kernel event timing when it is switched on.
+#define LCP_TIMED_LAUNCH(kern, grid, block, smem, stream, ...)                         \
+    do {                                                                               \
+        void* _tk = lcph::ktime_on() ? lcph::ktime_begin(#kern, (stream)) : nullptr;   \
+        LCP_LAUNCH(kern, grid, block, smem, stream, __VA_ARGS__);                      \
+        if (_tk) lcph::ktime_end(_tk, (stream));                                       \
     } while (0)
 
 #define LCP_CUDA_TRY(expr)                                \

@@ -279,7 +279,7 @@ int insert_device(lcp_index_s* x, const void* d_tokens, int64_t n, cudaStream_t 
     lcp_buffers& nb = x->buf[1 - x->cur];
     int rc = LCP_OK;
     if (small) {
-        LCP_LAUNCH(k_ins_place, nblocks(n, 4), 128, 0, s, reinterpret_cast<const uint8_t*>(d_tokens), f, n,
+        LCP_TIMED_LAUNCH(k_ins_place, nblocks(n, 4), 128, 0, s, reinterpret_cast<const uint8_t*>(d_tokens), f, n,
                    ob.rows, ob.head, x->N, srows, sids, np);
     } else {
         LCP_CUDA_TRY(cudaMallocAsync((void**)&srows, sizeof(uint64_t) * n * W, s));
@@ -319,7 +319,7 @@ int insert_device(lcp_index_s* x, const void* d_tokens, int64_t n, cudaStream_t 
         m.ntok = 1ll << x->bits;
         m.old_empty = x->N == 0;
         m.merge_ctas = nblocks(m.total, kMergeRows);
-        LCP_LAUNCH(k_ins_merge, m.merge_ctas + nblocks(m.ntok + 1, kMergeRows), kMergeRows, 0, s, m);
+        LCP_TIMED_LAUNCH(k_ins_merge, m.merge_ctas + nblocks(m.ntok + 1, kMergeRows), kMergeRows, 0, s, m);
         x->cur = 1 - x->cur;
         x->N = m.total;
         rc = build_aux(x, s, /*merged=*/true);

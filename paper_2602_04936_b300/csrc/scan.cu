@@ -207,10 +207,10 @@ int scan_topk_device(const void* d_tokens, int64_t N, int tb, int L, const void*
     uint64_t* heaps = nullptr;
     LCP_CUDA_TRY(cudaMallocAsync((void**)&plane0, sizeof(uint64_t) * N, s));
     LCP_CUDA_TRY(cudaMallocAsync((void**)&heaps, sizeof(uint64_t) * (size_t)S * Q * k, s));
-    LCP_LAUNCH(k_pack_plane0, (unsigned)((N + 255) / 256), 256, 0, s,
+    LCP_TIMED_LAUNCH(k_pack_plane0, (unsigned)((N + 255) / 256), 256, 0, s,
                reinterpret_cast<const uint8_t*>(d_tokens), f, N, plane0);
     dim3 grid((unsigned)qtiles, (unsigned)S);
-    LCP_LAUNCH(k_scan_partial, grid, threads, 0, s, reinterpret_cast<const uint8_t*>(d_tokens),
+    LCP_TIMED_LAUNCH(k_scan_partial, grid, threads, 0, s, reinterpret_cast<const uint8_t*>(d_tokens),
                plane0, f, N, reinterpret_cast<const uint8_t*>(d_queries), qf, Q, k, slice, heaps);
     // merge: groups of G lists until one remains
     int kp2 = 1;
@@ -242,7 +242,7 @@ int scan_topk_device(const void* d_tokens, int64_t N, int tb, int L, const void*
             }
         }
         dim3 mg((unsigned)Q, (unsigned)groups);
-        LCP_LAUNCH(k_scan_merge, mg, 256, smem, s, cur, Q, k, (int)nl, g, P, out,
+        LCP_TIMED_LAUNCH(k_scan_merge, mg, 256, smem, s, cur, Q, k, (int)nl, g, P, out,
                    final_pass ? 1 : 0, d_out_ids, d_out_lcp);
         if (cur != heaps) cudaFreeAsync(cur, s);
         if (final_pass) break;

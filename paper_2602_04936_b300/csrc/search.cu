@@ -203,6 +203,63 @@ __global__ void __launch_bounds__(256) k_topk_locate(DevIndex ix, const uint8_t*
     loc[qi] = r;
 }
 
+// Small batches: one warp per query.  The insertion point p (number of rows
+// < q) is found by a 33-way search -- 32 probes per round, about log_33 N
+// dependent loads instead of log_2 N -- so a batch of a few thousand queries
+// spreads over every SM instead of a few CTAs.
+__device__ __forceinline__ bool row_lt_query(const DevIndex& ix, int64_t m, const uint8_t* qrow,
+                                             const RowFmt& qf, uint64_t q0) {
+    const uint64_t h = ix.head[m];
+    if (h != q0) return h < q0;
+    int l;
+    return lane_cmp_from(ix, ix.rows + m * ix.W, qrow, qf, 1, &l) < 0;
+}
+
+__device__ __forceinline__ int lcp_with_row(const DevIndex& ix, int64_t m, const uint8_t* qrow,
+                                            const RowFmt& qf, uint64_t q0) {
+    const uint64_t h = ix.head[m];
+    if (h != q0) return __clzll((long long)(h ^ q0)) / ix.bits;
+    int l;
+    lane_cmp_from(ix, ix.rows + m * ix.W, qrow, qf, 1, &l);
+    return l;
+}
+
+__global__ void __launch_bounds__(256) k_topk_locate_warp(DevIndex ix, const uint8_t* __restrict__ queries,
+                                                          RowFmt qf, int64_t Q, QLoc* __restrict__ loc) {
+    const int64_t qi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (qi >= Q) return;
+    const unsigned lane = lane_id();
+    const uint8_t* qrow = row_of(queries, qi, qf);
+    const uint64_t q0 = pack_word(qrow, 0, qf);
+    int64_t lo = 0, hi = ix.N;  // rows < q form the prefix [0, p), p in [lo, hi]
+    while (hi - lo > 32) {
+        const int64_t m = lo + ((hi - lo) * (int64_t)(lane + 1)) / 33;
+        const int c = __popc(__ballot_sync(0xffffffffu, row_lt_query(ix, m, qrow, qf, q0)));
+        const int64_t mlast = __shfl_sync(0xffffffffu, m, c > 0 ? c - 1 : 0);
+        const int64_t mnext = __shfl_sync(0xffffffffu, m, c < 32 ? c : 31);
+        if (c > 0) lo = mlast + 1;
+        if (c < 32) hi = mnext;
+    }
+    const bool t = lo + (int64_t)lane < hi && row_lt_query(ix, lo + lane, qrow, qf, q0);
+    const int64_t p = lo + __popc(__ballot_sync(0xffffffffu, t));
+    // neighbour LCPs: lane 0 takes row p - 1, lane 1 row p
+    int l = -1;
+    if (lane == 0 && p > 0) l = lcp_with_row(ix, p - 1, qrow, qf, q0);
+    if (lane == 1 && p < ix.N) l = lcp_with_row(ix, p, qrow, qf, q0);
+    const int lR = __shfl_sync(0xffffffffu, l, 1);
+    if (lane == 0) {
+        QLoc r;
+        r.p = p;
+        r.lL = (int16_t)l;
+        r.lR = (int16_t)lR;
+        r.tok0 = (int32_t)(q0 >> (64 - ix.bits));
+        loc[qi] = r;
+    }
+}
+
+// Batches up to this size locate with a warp per query (see above).
+constexpr int64_t kWarpLocateMaxQ = 8192;
+
 // ---- one query, whole warp ----
 
 template <typename KT>
@@ -345,7 +402,7 @@ __device__ void topk_one(const DevIndex& ix, QWarp& S, int64_t p, int lL, int lR
     }
     // 5. A sorted by (LCP desc, id asc), then the tie fill, then padding
     if (nA > 0) {
-        if (nA <= 32) sort_and_write_A<1, KT>(S, aL, nA, oid, olcp);
+        if (nA <= 32) rank_and_write_A<KT>(S, aL, nA, oid, olcp);
         else sort_and_write_A<4, KT>(S, aL, nA, oid, olcp);
     }
     for (int r = nA + (int)lane; r < k; r += 32) {
@@ -399,7 +456,10 @@ int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, i
     QLoc* loc = reinterpret_cast<QLoc*>(loc_scratch);
     const bool own = loc == nullptr;
     if (own) LCP_CUDA_TRY(cudaMallocAsync((void**)&loc, sizeof(QLoc) * (size_t)Q, s));
-    LCP_LAUNCH(k_topk_locate, (unsigned)((Q + 255) / 256), 256, 0, s, ix, q, qf, Q, loc);
+    if (Q <= kWarpLocateMaxQ)
+        LCP_TIMED_LAUNCH(k_topk_locate_warp, (unsigned)((Q + 7) / 8), 256, 0, s, ix, q, qf, Q, loc);
+    else
+        LCP_TIMED_LAUNCH(k_topk_locate, (unsigned)((Q + 255) / 256), 256, 0, s, ix, q, qf, Q, loc);
     // queries per warp: 32 for large batches; fewer for small batches so that
     // the batch still spreads over every SM
     const int64_t full = (int64_t)sm_count() * 32;  // resident warps at full occupancy
@@ -409,10 +469,10 @@ int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, i
     const int64_t warps = (Q + qpw - 1) / qpw;
     const unsigned grid = (unsigned)((warps + kSearchWarps - 1) / kSearchWarps);
     if (x->N <= (1ll << 24)) {
-        LCP_LAUNCH(k_topk_answer<uint32_t>, grid, kSearchWarps * 32, 0, s, ix, loc, Q, k, qpw, out_ids,
+        LCP_TIMED_LAUNCH(k_topk_answer<uint32_t>, grid, kSearchWarps * 32, 0, s, ix, loc, Q, k, qpw, out_ids,
                    out_lcp);
     } else {
-        LCP_LAUNCH(k_topk_answer<uint64_t>, grid, kSearchWarps * 32, 0, s, ix, loc, Q, k, qpw, out_ids,
+        LCP_TIMED_LAUNCH(k_topk_answer<uint64_t>, grid, kSearchWarps * 32, 0, s, ix, loc, Q, k, qpw, out_ids,
                    out_lcp);
     }
     if (own) LCP_CUDA_TRY(cudaFreeAsync(loc, s));

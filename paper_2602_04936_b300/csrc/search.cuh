@@ -88,6 +88,26 @@ __device__ __forceinline__ void warp_bitonic(KT (&v)[E]) {
     }
 }
 
+// A of at most 32 items: lane i holds item i and places it at its rank,
+// the number of items whose key is smaller (keys are distinct: ids differ),
+// found with nA broadcasts -- fewer instructions than a 32-key bitonic
+// network whenever A is small, which it usually is.
+template <typename KT>
+__device__ __forceinline__ void rank_and_write_A(const QWarp& S, int aL, int nA,
+                                                 int32_t* __restrict__ oid,
+                                                 uint8_t* __restrict__ olcp) {
+    const int lane = (int)lane_id();
+    KT key = ~(KT)0;
+    if (lane < aL) key = make_key<KT>(S.llam[lane], S.lid[lane]);
+    else if (lane < nA) key = make_key<KT>(S.rlam[lane - aL], S.rid[lane - aL]);
+    int rank = 0;
+    for (int j = 0; j < nA; ++j) rank += __shfl_sync(0xffffffffu, key, j) < key;
+    if (lane < nA) {
+        __stcs(oid + rank, (int)key_id<KT>(key));
+        __stcs(reinterpret_cast<char*>(olcp) + rank, (char)key_lam<KT>(key));
+    }
+}
+
 // Sorts A (left items [0, aL), right items [0, nA - aL)) and writes the
 // first nA output slots.
 template <int E, typename KT>
