@@ -48,6 +48,10 @@ def _load():
         lib.oracle_topk_batch.restype = i32
         lib.oracle_sorted_index.argtypes = [vp, i64, i32, i32, vp, vp]
         lib.oracle_sorted_index.restype = i32
+        lib.oracle_topk_bfs.argtypes = [vp, i64, i32, i32, vp, i32, vp, vp]
+        lib.oracle_topk_bfs.restype = i32
+        lib.oracle_tal_topk.argtypes = [vp, i64, i32, i32, vp, i32, i32, vp, vp]
+        lib.oracle_tal_topk.restype = i32
         _lib = lib
     return _lib
 
@@ -113,3 +117,33 @@ def sorted_index(S: np.ndarray):
     if rc:
         raise ValueError("oracle_sorted_index rejected its arguments (rc=%d)" % rc)
     return ids, H
+
+
+def _per_query(fn, S, Qs, k, *extra):
+    S = _rows(S)
+    Qs = np.ascontiguousarray(Qs, dtype=S.dtype)
+    if Qs.ndim != 2 or Qs.shape[1] != S.shape[1]:
+        raise ValueError("queries must be [Q, L] with the dataset's L")
+    Q = Qs.shape[0]
+    ids = np.empty((Q, k), np.int32)
+    lc = np.empty((Q, k), np.uint8)
+    for i in range(Q):
+        q = np.ascontiguousarray(Qs[i])
+        rc = fn(_ptr(S), S.shape[0], S.shape[1], S.itemsize, _ptr(q), k, *extra,
+                _ptr(ids[i]), _ptr(lc[i]))
+        if rc:
+            raise ValueError("oracle rejected its arguments (rc=%d)" % rc)
+    return ids, lc
+
+
+def topk_bfs(S: np.ndarray, Qs: np.ndarray, k: int):
+    """Algorithms 3 + 4 literally (BFS order within the deepest node's
+    subtree), per query row: (ids[Q,k] int32, lcp[Q,k] uint8)."""
+    return _per_query(_load().oracle_topk_bfs, S, Qs, k)
+
+
+def tal_topk(S: np.ndarray, Qs: np.ndarray, k: int, d: int):
+    """TAL bucket scan at prefix depth d, per query row: the top k of the
+    items sharing the query's first d symbols, padded."""
+    return _per_query(_load().oracle_tal_topk, S, Qs, k, d)
+

@@ -20,6 +20,21 @@
  *                       order.  When k > N the tail is padded with (id -1, lcp 0).
  *   oracle_topk_batch   The same, for a batch of queries, split over threads (the
  *                       per-query computation is unchanged).
+ *   oracle_topk_bfs     Algorithms 3 + 4 taken literally (the paper's own output
+ *                       order, a variant): descend to the deepest node v on q's
+ *                       path -- its depth d is the largest LCP of q with any
+ *                       stored sequence -- and return the first k items of the
+ *                       subtree T_v in BFS order.  With every sequence of the
+ *                       same length L, items sit only at depth-L leaves, BFS
+ *                       meets those leaves in lexicographic order, and a leaf's
+ *                       posting list is in index order: so the answer is the
+ *                       items with LCP == d, sorted by (sequence, index), cut
+ *                       at k (fewer when |T_v| < k), each with LCP d.
+ *   oracle_tal_topk     Thermal-Aware Logic (Definition "TAL", Sec. 6.2 and the
+ *                       TALRangeScan listing, App. D): the bucket is the items
+ *                       sharing q's first d symbols; only the bucket is scanned
+ *                       and its top k by the Definition "Top-k LCP Retrieval"
+ *                       order are returned (fewer when the bucket holds fewer).
  *   oracle_sorted_index The array form of the trie built by Algorithm 1
  *                       (BuildLCPIndex, Sec. 5.2): item indices ordered by their
  *                       sequence (unsigned lexicographic order of the tokens;
@@ -194,6 +209,69 @@ typedef struct {
     const void* S;
     int L, token_bytes;
 } sort_ctx_t;
+
+static int cmp_items(const void* a, const void* b, void* arg);
+
+/*
+ * Algorithms 3 + 4 for one query (see the header): out_ids[k], out_lcp[k],
+ * padded with (-1, 0) beyond min(k, |T_v|).
+ */
+int oracle_topk_bfs(const void* S, int64_t N, int L, int token_bytes, const void* q, int k,
+                    int32_t* out_ids, uint8_t* out_lcp) {
+    if (k < 1 || L < 1 || L > 255 || (token_bytes != 1 && token_bytes != 2) || N < 0) return -1;
+    int* lam = (int*)malloc(sizeof(int) * (size_t)(N > 0 ? N : 1));
+    int32_t* tv = (int32_t*)malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+    if (!lam || !tv) {
+        free(lam);
+        free(tv);
+        return -2;
+    }
+    int d = 0;
+    for (int64_t i = 0; i < N; i++) {
+        lam[i] = oracle_lcp(row_ptr(S, i, L, token_bytes), q, L, token_bytes);
+        if (lam[i] > d) d = lam[i];
+    }
+    int64_t n = 0;  /* T_v: the items whose LCP reaches the descent depth d */
+    for (int64_t i = 0; i < N; i++)
+        if (lam[i] == d) tv[n++] = (int32_t)i;
+    sort_ctx_t c = {S, L, token_bytes};
+    qsort_r(tv, (size_t)n, sizeof(int32_t), cmp_items, &c);
+    for (int r = 0; r < k; r++) {
+        out_ids[r] = r < n ? tv[r] : -1;
+        out_lcp[r] = r < n ? (uint8_t)d : 0;
+    }
+    free(lam);
+    free(tv);
+    return 0;
+}
+
+/*
+ * TAL for one query with prefix depth d (0 <= d <= L): the top k of the
+ * bucket {i : LCP(S_i, q) >= d} by (LCP desc, index asc), padded.
+ */
+int oracle_tal_topk(const void* S, int64_t N, int L, int token_bytes, const void* q, int k, int d,
+                    int32_t* out_ids, uint8_t* out_lcp) {
+    if (k < 1 || L < 1 || L > 255 || d < 0 || d > L || (token_bytes != 1 && token_bytes != 2) || N < 0)
+        return -1;
+    int* lam = (int*)malloc(sizeof(int) * (size_t)(N > 0 ? N : 1));
+    if (!lam) return -2;
+    for (int64_t i = 0; i < N; i++) lam[i] = oracle_lcp(row_ptr(S, i, L, token_bytes), q, L, token_bytes);
+    int r = 0;
+    /* LCP levels from L down to d; within a level, ascending index */
+    for (int v = L; v >= d && r < k; v--)
+        for (int64_t i = 0; i < N && r < k; i++)
+            if (lam[i] == v) {
+                out_ids[r] = (int32_t)i;
+                out_lcp[r] = (uint8_t)v;
+                r++;
+            }
+    for (; r < k; r++) {
+        out_ids[r] = -1;
+        out_lcp[r] = 0;
+    }
+    free(lam);
+    return 0;
+}
 
 /* Unsigned lexicographic comparison of two stored rows, then by index. */
 static int cmp_items(const void* a, const void* b, void* arg) {

@@ -257,3 +257,46 @@ def test_zipf_generator_c_path_matches_numpy_reference():
         qa = W.zipf_prefix_queries(a, 400, V, s, 7, impl="c")
         qb = W.zipf_prefix_queries(a, 400, V, s, 7, impl="numpy")
         assert np.array_equal(qa, qb)
+
+
+@pytest.mark.parametrize("sigma,L", [(2, 3), (3, 3), (2, 4)])
+def test_bfs_and_tal_against_pointer_trie(sigma, L):
+    """The BFS-order variant (Algorithms 3 + 4) and the TAL bucket scan against
+    the pointer trie, every query in Sigma^L, random multisets N <= 12."""
+    rng = random.Random(sigma * 1000 + L)
+    all_q = np.array(list(itertools.product(range(sigma), repeat=L)), np.uint8).reshape(-1, L)
+    for trial in range(5):
+        N = rng.randint(0, 12)
+        S = np.array([[rng.randrange(sigma) for _ in range(L)] for _ in range(N)],
+                     np.uint8).reshape(N, L)
+        root = T.build(S)
+        for k in (1, 2, 5, 14):
+            b_ids, b_lcp = oracle.topk_bfs(S, all_q, k)
+            for qi, q in enumerate(all_q):
+                t_ids, t_lcp = T.query_bfs(root, q, k)
+                assert b_ids[qi].tolist() == t_ids and b_lcp[qi].tolist() == t_lcp, (S.tolist(), q, k)
+            for d in range(L + 1):
+                a_ids, a_lcp = oracle.tal_topk(S, all_q, k, d)
+                for qi, q in enumerate(all_q):
+                    t_ids, t_lcp = T.tal_by_trie(root, q, k, d)
+                    assert a_ids[qi].tolist() == t_ids and a_lcp[qi].tolist() == t_lcp, (S.tolist(), q, k, d)
+
+
+def test_bfs_and_tal_reduce_to_the_definition():
+    """TAL at depth 0 scans everything, so it is the Definition's top k; a
+    bucket holding >= k items gives the Definition's answer too (every item
+    outside has a smaller LCP).  BFS order differs from the Definition only in
+    which ties it keeps: its LCP column equals the Definition's when |T_v| >= k."""
+    S, Qs, _ = __import__("workloads").make_dataset("tree16_u8", N=600, Q=80)
+    k = 7
+    want_i, want_l = oracle.topk_batch(S, Qs, k)
+    t_i, t_l = oracle.tal_topk(S, Qs, k, 0)
+    assert np.array_equal(t_i, want_i) and np.array_equal(t_l, want_l)
+    for d in (1, 2, 3):
+        t_i, t_l = oracle.tal_topk(S, Qs, k, d)
+        full = (t_i >= 0).all(axis=1)
+        assert full.any() and np.array_equal(t_i[full], want_i[full]) and np.array_equal(t_l[full], want_l[full])
+    b_i, b_l = oracle.topk_bfs(S, Qs, k)
+    full = (b_i >= 0).all(axis=1)
+    assert full.any() and np.array_equal(b_l[full], want_l[full])
+

@@ -5,6 +5,10 @@
 * ``descend``          -- the descent of Algorithm 3 (Query), Sec. 5.3.
 * ``collect_bfs``      -- Algorithm 4 (CollectTopK): BFS from a node, posting
                           lists first, children in sorted symbol order.
+* ``query_bfs``        -- Algorithm 3 + Algorithm 4 as printed: descend, then
+                          CollectTopK from the deepest node reached.
+* ``tal_by_trie``      -- the TAL bucket (items under q's depth-d node) ranked
+                          by the Definition's order, from trie levels.
 * ``topk_by_trie``     -- Definition "Top-k LCP Retrieval" (Sec. 2.1) evaluated
                           through the trie instead of by comparing sequences:
                           the items of T_{v_j} minus T_{v_{j+1}} along q's path
@@ -108,3 +112,31 @@ def topk_by_trie(root, q, k, N):
         out_ids.append(-1)
         out_lcp.append(0)
     return out_ids, out_lcp
+
+
+def query_bfs(root, q, k):
+    """Algorithms 3 + 4: the first k items of T_v in BFS order, v the deepest
+    node on q's path; every item of T_v has LCP = depth(v).  Padded."""
+    path = descend(root, q)
+    d = len(path) - 1
+    ids = collect_bfs(path[-1], k)
+    lcp = [d] * len(ids)
+    return ids + [-1] * (k - len(ids)), lcp + [0] * (k - len(ids))
+
+
+def tal_by_trie(root, q, k, d):
+    """The TAL bucket is T_{v_d} (empty when q's path is shorter than d); its
+    items at trie level j >= d along the path have LCP exactly j."""
+    path = descend(root, q)
+    D = len(path) - 1
+    out_ids, out_lcp = [], []
+    inner = set()
+    for j in range(D, d - 1, -1):
+        level = sorted(set(items_in(path[j])) - inner)
+        for i in level:
+            if len(out_ids) < k:
+                out_ids.append(i)
+                out_lcp.append(j)
+        inner |= set(level)
+    return out_ids + [-1] * (k - len(out_ids)), out_lcp + [0] * (k - len(out_lcp))
+
