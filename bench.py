@@ -576,6 +576,19 @@ def run_ours(args, world, rank, local):
         del dsteps
         # serving: six resident indexes, Poisson arrivals, native open-loop replay
         paths["serving"] = serving_leg(lcp, device, to_dev)
+        # TAL bucket scan (the paper's TAL benchmark shape) and BFS order
+        paths["tal20m"] = tal_leg(lcp, device, meter)
+        idx_b = lcp.lcp_index_build(dS, max_k=k)
+        lcp.lcp_topk_bfs(idx_b, dQ, k, out_ids, out_lcp)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(5):
+            lcp.lcp_topk_bfs(idx_b, dQ, k, out_ids, out_lcp)
+        b.record(stream)
+        b.synchronize()
+        paths["bfs_order"] = {"workload": args.workload, "Q": Q, "k": k, "ms": round(a.elapsed_time(b) / 5, 4),
+                              "qps": round(Q / (a.elapsed_time(b) / 5e3), 1)}
+        idx_b.close()
         # end to end through the host-buffer ABI (copies inside the timed region)
         hS, hQ = pinned(S), pinned(Qs)
         hid = torch.empty((Q, k), dtype=torch.int32).pin_memory()
@@ -606,6 +619,71 @@ def run_ours(args, world, rank, local):
                                     "sample": "first %d queries of the batch against all %d rows "
                                               "(%.1f s)" % (n, N, el)}
     return line
+
+
+def tal_leg(lcp, device, meter):
+    """The paper's TAL benchmark shape (20M items, 256 first-token buckets,
+    10,000 queries): the bucket scan beside the indexed search and the full
+    scan on the same data, all from one resident index."""
+    import torch
+    w = W.WORKLOADS["tal20m"]
+    N, L, Q, k, d = w["N"], w["L"], w["Q"], w["k"], w["depth"]
+    S = W.uniform_rows(N, L, w["vocab"], w["seed"])
+    Qs = W.uniform_rows(Q, L, w["vocab"], w["seed"] + 1000)
+    dS, dQ = to_dev(S, device), to_dev(Qs, device)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    idx = lcp.lcp_index_build(dS, max_k=32)
+    b.record()
+    b.synchronize()
+    rec = {"N": N, "L": L, "Q": Q, "k": k, "depth": d, "buckets": w["vocab"] ** d,
+           "build_ms": round(a.elapsed_time(b), 3)}
+
+    def timed(fn, reps):
+        # enough repetitions for about a second: NVML's energy counter is coarse
+        fn()
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        reps = max(reps, min(40_000, int(1000.0 / max(a.elapsed_time(b), 1e-3)) + 1))
+        e0 = meter.read_j()
+        a.record()
+        for _ in range(reps):
+            out = fn()
+        b.record()
+        b.synchronize()
+        e1 = meter.read_j()
+        return a.elapsed_time(b) / reps, out, joules_per(e0, e1, Q * reps)
+
+    tal_ms, tal_out, tal_j = timed(lambda: lcp.lcp_tal_topk(idx, dQ, k, d), 20)
+    ix_ms, ix_out, ix_j = timed(lambda: lcp.lcp_topk_batch(idx, dQ, k), 200)
+    sc_ms, sc_out, sc_j = timed(lambda: lcp.lcp_scan_topk(dS, dQ, k), 3)
+    rec["tal"] = {"batch_ms": round(tal_ms, 3), "qps": round(Q / (tal_ms / 1e3), 1), "energy_j_per_query": tal_j}
+    rec["indexed"] = {"batch_ms": round(ix_ms, 4), "qps": round(Q / (ix_ms / 1e3), 1), "energy_j_per_query": ix_j}
+    rec["full_scan"] = {"batch_ms": round(sc_ms, 3), "qps": round(Q / (sc_ms / 1e3), 1),
+                        "energy_j_per_query": sc_j}
+    # every bucket holds >= k rows here, so all three agree on every query
+    rec["tal_equals_indexed"] = bool(torch.equal(tal_out[0], ix_out[0]) and torch.equal(tal_out[1], ix_out[1]))
+    rec["indexed_equals_full_scan"] = bool(torch.equal(sc_out[0], ix_out[0]) and torch.equal(sc_out[1], ix_out[1]))
+    # single-query latency (CUDA events per call), p50 / p95 / p99
+    lat = {}
+    for name, fn in (("tal", lambda q: lcp.lcp_tal_topk(idx, q, k, d)),
+                     ("indexed", lambda q: lcp.lcp_topk_batch(idx, q, k))):
+        t = []
+        for r in range(302):
+            q = dQ[r % Q:r % Q + 1]
+            a.record()
+            fn(q)
+            b.record()
+            b.synchronize()
+            if r >= 2:
+                t.append(a.elapsed_time(b))
+        lat[name] = {p: round(float(np.percentile(t, int(p[1:]))), 4) for p in ("p50", "p95", "p99")}
+    rec["latency_ms_batch1"] = lat
+    idx.close()
+    return rec
 
 
 def serving_leg(lcp, device, to_dev, duration_s=1.5, budget=256 << 20, streams=8, max_inflight=64):

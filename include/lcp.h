@@ -177,6 +177,27 @@ LCP_API int lcp_scan_topk_noalloc(const void* d_tokens, int64_t N, lcp_format_t 
                                   uint8_t* d_out_lcp, lcp_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * The paper's own query modes (variants; lcp_topk_batch is the Definition).
+ *
+ * lcp_topk_bfs -- Algorithms 3 + 4 as printed (Sec. 5.3): descend to the
+ *   deepest trie node v on q's path (depth d = the largest LCP of q with any
+ *   row) and return the first k items of T_v in BFS order -- for rows of one
+ *   length L, T_v's items in sorted-row order, equal rows by id -- each with
+ *   LCP d, padded with (-1, 0) when |T_v| < k.  Any k >= 1.
+ * lcp_tal_topk -- Thermal-Aware Logic (Definition "TAL", Sec. 6.2, and the
+ *   TALRangeScan listing, App. D): the bucket is the rows sharing q's first
+ *   `depth` tokens (0 <= depth <= L; B = vocab^depth buckets); only the
+ *   bucket's rows are scanned, and its top k by (LCP desc, id asc) are
+ *   returned, padded when the bucket holds fewer.  1 <= k <= LCP_TAL_MAX_K.
+ * Buffers and errors as lcp_topk_batch.
+ * ---------------------------------------------------------------------- */
+#define LCP_TAL_MAX_K 32
+LCP_API int lcp_topk_bfs(lcp_index_t index, const void* d_queries, int64_t Q, int32_t k, int32_t* d_out_ids,
+                         uint8_t* d_out_lcp, lcp_stream_t stream);
+LCP_API int lcp_tal_topk(lcp_index_t index, const void* d_queries, int64_t Q, int32_t k, int32_t depth,
+                         int32_t* d_out_ids, uint8_t* d_out_lcp, lcp_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Sharded index: merge of per-shard answers.  The rows are partitioned by
  * original-id range over P shards (shard s holds global ids h_bases[s] ..),
  * each shard's index answers the same Q queries with its local ids, and this

@@ -51,6 +51,7 @@ ABI_SYMBOLS = (
     "lcp_session_create", "lcp_session_add_index", "lcp_session_submit", "lcp_session_poll",
     "lcp_session_stats", "lcp_session_destroy", "lcp_session_replay",
     "lcp_step_create", "lcp_step_run", "lcp_step_stats", "lcp_step_destroy", "lcp_shard_merge",
+    "lcp_topk_bfs", "lcp_tal_topk",
 )
 
 
@@ -123,6 +124,8 @@ def _load():
         "lcp_step_stats": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64)], ctypes.c_int),
         "lcp_step_destroy": ([vp], ctypes.c_int),
         "lcp_shard_merge": ([vp, vp, i32, ctypes.POINTER(i64), i64, i32, vp, vp, vp], ctypes.c_int),
+        "lcp_topk_bfs": ([vp, vp, i64, i32, vp, vp, vp], ctypes.c_int),
+        "lcp_tal_topk": ([vp, vp, i64, i32, i32, vp, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -363,6 +366,34 @@ def lcp_debug_bounded_wait(spin_limit: int, stream=None) -> int:
 
 
 LCP_SHARD_MAX = 32
+LCP_TAL_MAX_K = 32
+
+
+def lcp_topk_bfs(index: "Index", queries: torch.Tensor, k: int, out_ids=None, out_lcp=None, stream=None):
+    """Algorithms 3 + 4 as printed: first k items of the deepest node's subtree
+    in BFS (sorted-row) order, each with the descent depth as LCP."""
+    q = _rows(queries, True)
+    if q.shape[1] != index.L or _token_bytes(q) != index.token_bytes:
+        raise ValueError("query format differs from the index")
+    out_ids, out_lcp = _outputs(q.shape[0], k, q.device, out_ids, out_lcp)
+    with torch.cuda.device(q.device):
+        _check(_lib.lcp_topk_bfs(index.handle, _ptr(q), q.shape[0], k, _ptr(out_ids), _ptr(out_lcp),
+                                 _stream(stream)), "lcp_topk_bfs")
+    return out_ids, out_lcp
+
+
+def lcp_tal_topk(index: "Index", queries: torch.Tensor, k: int, depth: int, out_ids=None, out_lcp=None,
+                 stream=None):
+    """TAL bucket scan: top k of the rows sharing each query's first `depth`
+    tokens, found by scanning that bucket only."""
+    q = _rows(queries, True)
+    if q.shape[1] != index.L or _token_bytes(q) != index.token_bytes:
+        raise ValueError("query format differs from the index")
+    out_ids, out_lcp = _outputs(q.shape[0], k, q.device, out_ids, out_lcp)
+    with torch.cuda.device(q.device):
+        _check(_lib.lcp_tal_topk(index.handle, _ptr(q), q.shape[0], k, depth, _ptr(out_ids), _ptr(out_lcp),
+                                 _stream(stream)), "lcp_tal_topk")
+    return out_ids, out_lcp
 
 
 def lcp_shard_merge(ids: torch.Tensor, lcp: torch.Tensor, bases, out_ids=None, out_lcp=None, stream=None):

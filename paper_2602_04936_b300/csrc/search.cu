@@ -179,13 +179,6 @@ __device__ __forceinline__ void lane_locate(const DevIndex& ix, const uint8_t* q
     *lR_out = lR;
 }
 
-// Position record of one query, written by k_topk_locate.
-struct alignas(16) QLoc {
-    int64_t p;
-    int16_t lL, lR;
-    int32_t tok0;
-};
-
 __global__ void __launch_bounds__(256) k_topk_locate(DevIndex ix, const uint8_t* __restrict__ queries,
                                                      RowFmt qf, int64_t Q, QLoc* __restrict__ loc) {
     const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -440,6 +433,13 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 8) k_topk_answer(DevIndex i
 namespace lcph {
 using namespace lcpk;
 
+void launch_locate(const DevIndex& ix, const uint8_t* q, const RowFmt& qf, int64_t Q, QLoc* loc, cudaStream_t s) {
+    if (Q <= kWarpLocateMaxQ)
+        LCP_TIMED_LAUNCH(k_topk_locate_warp, (unsigned)((Q + 7) / 8), 256, 0, s, ix, q, qf, Q, loc);
+    else
+        LCP_TIMED_LAUNCH(k_topk_locate, (unsigned)((Q + 255) / 256), 256, 0, s, ix, q, qf, Q, loc);
+}
+
 int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, int32_t* out_ids,
                       uint8_t* out_lcp, cudaStream_t s, void* loc_scratch) {
     if (Q <= 0) return LCP_OK;
@@ -456,10 +456,7 @@ int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, i
     QLoc* loc = reinterpret_cast<QLoc*>(loc_scratch);
     const bool own = loc == nullptr;
     if (own) LCP_CUDA_TRY(cudaMallocAsync((void**)&loc, sizeof(QLoc) * (size_t)Q, s));
-    if (Q <= kWarpLocateMaxQ)
-        LCP_TIMED_LAUNCH(k_topk_locate_warp, (unsigned)((Q + 7) / 8), 256, 0, s, ix, q, qf, Q, loc);
-    else
-        LCP_TIMED_LAUNCH(k_topk_locate, (unsigned)((Q + 255) / 256), 256, 0, s, ix, q, qf, Q, loc);
+    launch_locate(ix, q, qf, Q, loc, s);
     // queries per warp: 32 for large batches; fewer for small batches so that
     // the batch still spreads over every SM
     const int64_t full = (int64_t)sm_count() * 32;  // resident warps at full occupancy

@@ -13,6 +13,14 @@ constexpr int kMaxW = 64;
 constexpr int kKMax = LCP_INDEX_MAX_K;
 constexpr int kSide = kKMax + 64;  // loaded items per side stay below k + 32
 
+// Position record of one query (insertion point p, LCPs with rows p-1 and
+// p, first token), written by the locate kernels.
+struct alignas(16) QLoc {
+    int64_t p;
+    int16_t lL, lR;
+    int32_t tok0;
+};
+
 struct alignas(16) QWarp {
 
     uint32_t lid[kSide];
@@ -477,3 +485,11 @@ __device__ __forceinline__ int smallest_ids(const DevIndex& ix, int64_t lo, int6
 }
 
 }  // namespace lcpk
+
+namespace lcph {
+// Locates every query of a batch (warp per query for small batches, lane per
+// query otherwise) into loc[Q].
+void launch_locate(const lcpk::DevIndex& ix, const uint8_t* q, const lcpk::RowFmt& qf, int64_t Q,
+                   lcpk::QLoc* loc, cudaStream_t s);
+}  // namespace lcph
+

@@ -245,6 +245,13 @@ def test_workload_generators_are_deterministic_and_shaped():
     g = W.GncStream(sensors=10, seed=5)
     r0 = g.step()
     assert r0.shape == (10, 8) and r0[:, 2:].max() <= 9
+    # uniform rows (TAL shape): deterministic, chunking-independent, every
+    # first-token bucket near n / 256
+    u = W.uniform_rows(51_200, 16, 256, 6)
+    assert np.array_equal(u, W.uniform_rows(51_200, 16, 256, 6, chunk=777))
+    counts = np.bincount(u[:, 0], minlength=256)
+    assert u.dtype == np.uint8 and counts.min() > 120 and counts.max() < 290
+    assert W.uniform_rows(10, 4, 1000, 1).dtype == np.uint16
 
 
 def test_zipf_generator_c_path_matches_numpy_reference():

@@ -47,6 +47,7 @@ STREAM_TREE = 4
 STREAM_GNC = 5
 STREAM_SERVE = 6
 STREAM_PERM = 7
+STREAM_UNIFORM = 8
 
 
 def splitmix64(x):
@@ -318,6 +319,19 @@ def serving_requests(n_requests: int, rate_per_s: float, n_indexes: int, seed: i
     return {"arrival_s": np.cumsum(gaps), "n_queries": n, "k": k, "index": idx}
 
 
+def uniform_rows(n: int, L: int, V: int, seed: int, chunk: int = 1 << 20) -> np.ndarray:
+    """n rows of L tokens, each uniform over 0..V-1 (V <= 65536), drawn
+    counter-based per (row, position); uint8 when V <= 256, else uint16."""
+    dt = np.uint8 if V <= 256 else np.uint16
+    out = np.empty((n, L), dt)
+    pos = np.arange(L, dtype=_U64)
+    for a in range(0, n, chunk):
+        rows = np.arange(a, min(n, a + chunk), dtype=_U64)
+        r = rand_u64(seed, STREAM_UNIFORM, rows[:, None], pos[None, :])
+        out[a:a + len(rows)] = (r % _U64(V)).astype(dt)
+    return out
+
+
 # --------------------------------------------------------------------------
 # the five workloads
 # --------------------------------------------------------------------------
@@ -330,6 +344,9 @@ WORKLOADS = {
                        k=100, seed=3),
     "serving6": dict(vocab=32768, s=1.05, rate=20_000.0, seed=4),
     "gnc1000": dict(sensors=1000, steps=1000, L=8, token_bytes=2, k=5, seed=5),
+    # the paper's TAL benchmark shape: 20M items, 256 prefix buckets (uniform
+    # first token over 256 values, bucket depth 1), 10,000 queries
+    "tal20m": dict(N=20_000_000, L=16, token_bytes=1, vocab=256, depth=1, Q=10_000, k=10, seed=6),
 }
 
 
