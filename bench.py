@@ -738,6 +738,44 @@ def serving_leg(lcp, device, to_dev, duration_s=1.5, budget=256 << 20, streams=8
         alone = lcp.lcp_topk_batch(indexes[j], pools[j][qoff:qoff + Q].to(device), k)
         got = arena[o:o + Q * k * 4].view(torch.int32).view(Q, k)
         same = same and bool(torch.equal(got, alone[0].cpu()))
+    # the same requests through the persistent kernel's work queue, queries
+    # and outputs device-resident (no copies inside the measured latencies)
+    dpools = [p.to(device) for p in pools]
+    darena = torch.empty(arena_bytes, dtype=torch.uint8, device=device)
+    dbase = darena.data_ptr()
+    qreqs = []
+    for i in range(n_req):
+        j, qoff, Q, k, o = layout[i]
+        qp = dpools[j].data_ptr() + qoff * dpools[j].shape[1] * 2
+        qreqs.append(lcp.QueueReplayRequest(reqs[i].arrival_s, indexes[j].handle.value, k, Q, qp, dbase + o,
+                                            dbase + o + Q * k * 4))
+    torch.cuda.synchronize()
+    qu = lcp.Queue(max_requests=1024, max_tasks=1 << 18, idle_ms=20.0)
+    launches0 = lcp.lcp_launch_count()
+    try:
+        qrc, qlat, qwall = qu.replay(qreqs, timeout_s=120.0)
+        qlaunches = lcp.lcp_launch_count() - launches0
+        qst = qu.stats()
+    finally:
+        qu.close()
+    qsame = True
+    for i in range(max(n_req - 40, wrap_at), n_req):
+        j, qoff, Q, k, o = layout[i]
+        if qlat[i] < 0:
+            continue
+        alone = lcp.lcp_topk_batch(indexes[j], dpools[j][qoff:qoff + Q], k)
+        got = darena[o:o + Q * k * 4].view(torch.int32).view(Q, k)
+        qsame = qsame and bool(torch.equal(got, alone[0]))
+    qok = qlat[qlat >= 0]
+    qdone = int(sum(qreqs[i].Q for i in range(n_req) if qlat[i] >= 0))
+    queue_res = {"requests": n_req, "completed": int(len(qok)),
+                 "qps": round(qdone / qwall, 1) if qwall > 0 else None,
+                 "latency_ms": {"p50": round(float(np.percentile(qok, 50)) * 1e3, 4),
+                                "p99": round(float(np.percentile(qok, 99)) * 1e3, 4),
+                                "p99.9": round(float(np.percentile(qok, 99.9)) * 1e3, 4)},
+                 "worker_launches": int(qst["worker_launches"]), "kernel_launches": int(qlaunches),
+                 "queries_and_outputs": "device-resident", "results_equal_alone": qsame, "rc": int(qrc)}
+    del darena, dpools
     ok = lat[lat >= 0]
     done_q = int(sum(reqs[i].Q for i in range(n_req) if lat[i] >= 0))
     res = {"requests": n_req, "rate_per_s": rate, "completed": int(len(ok)), "rejected": int(st["rejected"]),
@@ -748,7 +786,7 @@ def serving_leg(lcp, device, to_dev, duration_s=1.5, budget=256 << 20, streams=8
                           "p99.9": round(float(np.percentile(ok, 99.9)) * 1e3, 4)},
            "mem_budget": budget, "mem_peak": int(st["mem_peak"]), "streams": streams,
            "max_inflight": max_inflight, "kernel_launches": int(launches),
-           "results_equal_alone": same, "rc": int(rc)}
+           "results_equal_alone": same, "rc": int(rc), "persistent_queue": queue_res}
     for ix in indexes:
         ix.close()
     return res

@@ -198,6 +198,59 @@ LCP_API int lcp_tal_topk(lcp_index_t index, const void* d_queries, int64_t Q, in
                          int32_t* d_out_ids, uint8_t* d_out_lcp, lcp_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Persistent search fed by a device work queue (the batched serving path:
+ * requests against several resident indexes of uneven N, L and k run in one
+ * long-lived launch instead of a launch per request).  The paper runs one
+ * query stream per process; the queue is this library's.
+ *
+ * Each request is cut into tasks of whole queries; its records are copied
+ * to a device-memory task ring and the new task count after them, on one
+ * copy stream.  Warps of the persistent kernel claim tasks (compare-and-swap
+ * on a device counter), answer them exactly as lcp_topk_batch does, and
+ * publish the request's ticket to mapped host memory.
+ * Warps that find no work for idle_ms exit; a later submit or poll relaunches
+ * the kernel.  Every device wait is bounded.
+ *
+ * Queries and outputs are device memory and must stay valid until the
+ * ticket completes; the queries must be fully written (their producing
+ * stream synchronized) before submit, since the running kernel cannot wait
+ * on a stream.  The index must not change (insert) while requests against
+ * it are in flight.  Submit returns LCP_ERR_CAPACITY when max_requests
+ * requests or max_tasks tasks are in flight: poll and retry.  Poll returns
+ * LCP_OK once the request is complete, LCP_PENDING at the timeout.
+ * Destroy waits for outstanding requests, then stops the worker.
+ * ---------------------------------------------------------------------- */
+typedef struct lcp_queue_s* lcp_queue_t;
+typedef struct {
+    int32_t max_requests;  /* in flight at once (1 .. 65536) */
+    int32_t max_tasks;     /* task ring entries (1 .. 2^24) */
+    double idle_ms;        /* a warp with no work for this long exits (> 0) */
+    int32_t ctas_per_sm;   /* worker CTAs per SM (1 .. 32) */
+} lcp_queue_cfg_t;
+LCP_API int lcp_queue_create(const lcp_queue_cfg_t* cfg, lcp_queue_t* out);
+LCP_API int lcp_queue_submit(lcp_queue_t q, lcp_index_t index, const void* d_queries, int64_t Q, int32_t k,
+                             int32_t* d_out_ids, uint8_t* d_out_lcp, uint64_t* ticket);
+LCP_API int lcp_queue_poll(lcp_queue_t q, uint64_t ticket, int32_t timeout_ms);
+LCP_API int lcp_queue_stats(lcp_queue_t q, int64_t* inflight, int64_t* worker_launches);
+LCP_API int lcp_queue_destroy(lcp_queue_t q);
+/* Open-loop replay: request i is submitted at arrival_s[i] seconds after the
+ * call starts (later if the queue is full: arrival order is kept); its
+ * latency, completion time minus arrival time in seconds, lands in
+ * latency_s[i] (-1 if rejected or unfinished at timeout_s); *wall_s = time of
+ * the last completion.  Device buffers as for lcp_queue_submit. */
+typedef struct {
+    double arrival_s;
+    lcp_index_t index;
+    int32_t k;
+    int64_t Q;
+    const void* d_queries;
+    int32_t* d_out_ids;
+    uint8_t* d_out_lcp;
+} lcp_queue_replay_req_t;
+LCP_API int lcp_queue_replay(lcp_queue_t q, const lcp_queue_replay_req_t* reqs, int64_t n, double timeout_s,
+                             double* latency_s, double* wall_s);
+
+/* ------------------------------------------------------------------------
  * Sharded index: merge of per-shard answers.  The rows are partitioned by
  * original-id range over P shards (shard s holds global ids h_bases[s] ..),
  * each shard's index answers the same Q queries with its local ids, and this

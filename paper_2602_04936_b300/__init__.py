@@ -52,6 +52,8 @@ ABI_SYMBOLS = (
     "lcp_session_stats", "lcp_session_destroy", "lcp_session_replay",
     "lcp_step_create", "lcp_step_run", "lcp_step_stats", "lcp_step_destroy", "lcp_shard_merge",
     "lcp_topk_bfs", "lcp_tal_topk",
+    "lcp_queue_create", "lcp_queue_submit", "lcp_queue_poll", "lcp_queue_stats", "lcp_queue_destroy",
+    "lcp_queue_replay",
 )
 
 
@@ -74,6 +76,17 @@ class ReplayRequest(ctypes.Structure):
     _fields_ = [("arrival_s", ctypes.c_double), ("slot", ctypes.c_int32), ("k", ctypes.c_int32),
                 ("Q", ctypes.c_int64), ("h_queries", ctypes.c_void_p), ("h_out_ids", ctypes.c_void_p),
                 ("h_out_lcp", ctypes.c_void_p)]
+
+
+class QueueConfig(ctypes.Structure):
+    _fields_ = [("max_requests", ctypes.c_int32), ("max_tasks", ctypes.c_int32), ("idle_ms", ctypes.c_double),
+                ("ctas_per_sm", ctypes.c_int32)]
+
+
+class QueueReplayRequest(ctypes.Structure):
+    _fields_ = [("arrival_s", ctypes.c_double), ("index", ctypes.c_void_p), ("k", ctypes.c_int32),
+                ("Q", ctypes.c_int64), ("d_queries", ctypes.c_void_p), ("d_out_ids", ctypes.c_void_p),
+                ("d_out_lcp", ctypes.c_void_p)]
 
 
 class SessionStats(ctypes.Structure):
@@ -126,6 +139,13 @@ def _load():
         "lcp_shard_merge": ([vp, vp, i32, ctypes.POINTER(i64), i64, i32, vp, vp, vp], ctypes.c_int),
         "lcp_topk_bfs": ([vp, vp, i64, i32, vp, vp, vp], ctypes.c_int),
         "lcp_tal_topk": ([vp, vp, i64, i32, i32, vp, vp, vp], ctypes.c_int),
+        "lcp_queue_create": ([ctypes.POINTER(QueueConfig), ctypes.POINTER(vp)], ctypes.c_int),
+        "lcp_queue_submit": ([vp, vp, vp, i64, i32, vp, vp, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+        "lcp_queue_poll": ([vp, ctypes.c_uint64, i32], ctypes.c_int),
+        "lcp_queue_stats": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64)], ctypes.c_int),
+        "lcp_queue_destroy": ([vp], ctypes.c_int),
+        "lcp_queue_replay": ([vp, ctypes.POINTER(QueueReplayRequest), i64, ctypes.c_double,
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -413,6 +433,71 @@ def lcp_shard_merge(ids: torch.Tensor, lcp: torch.Tensor, bases, out_ids=None, o
         _check(_lib.lcp_shard_merge(_ptr(ids.contiguous()), _ptr(lcp.contiguous()), P, hb, Q, k,
                                     _ptr(out_ids), _ptr(out_lcp), _stream(stream)), "lcp_shard_merge")
     return out_ids, out_lcp
+
+
+class Queue:
+    """Persistent search kernel fed by a work queue (lcp.h): submit requests
+    against any resident index, poll their tickets."""
+
+    def __init__(self, max_requests: int = 256, max_tasks: int = 1 << 16, idle_ms: float = 2.0,
+                 ctas_per_sm: int = 4):
+        self._h = ctypes.c_void_p()
+        cfg = QueueConfig(max_requests, max_tasks, idle_ms, ctas_per_sm)
+        _check(_lib.lcp_queue_create(ctypes.byref(cfg), ctypes.byref(self._h)), "lcp_queue_create")
+        self._live = {}  # ticket -> tensors that must outlive the request
+
+    def submit(self, index: "Index", queries: torch.Tensor, k: int, out_ids=None, out_lcp=None) -> int:
+        """Queries must be device-resident and fully written (stream synchronized)."""
+        q = _rows(queries, True)
+        if q.shape[1] != index.L or _token_bytes(q) != index.token_bytes:
+            raise ValueError("query format differs from the index")
+        out_ids, out_lcp = _outputs(q.shape[0], k, q.device, out_ids, out_lcp)
+        t = ctypes.c_uint64()
+        _check(_lib.lcp_queue_submit(self._h, index.handle, _ptr(q), q.shape[0], k, _ptr(out_ids), _ptr(out_lcp),
+                                     ctypes.byref(t)), "lcp_queue_submit")
+        self._live[t.value] = (index, q, out_ids, out_lcp)
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = 0) -> int:
+        """LCP_OK once complete, LCP_PENDING at the timeout."""
+        return _lib.lcp_queue_poll(self._h, ticket, timeout_ms)
+
+    def result(self, ticket: int, timeout_ms: int = 10_000):
+        """Waits for the request and hands back its (ids, lcp) outputs."""
+        _check(self.poll(ticket, timeout_ms), "lcp_queue_poll")
+        held = self._live.pop(ticket)
+        return held[2], held[3]
+
+    def replay(self, reqs, timeout_s: float = 60.0):
+        """Native open-loop replay of QueueReplayRequest records: (rc,
+        latencies in seconds, wall seconds)."""
+        import numpy as np
+        n = len(reqs)
+        arr = (QueueReplayRequest * n)(*reqs)
+        lat = np.zeros(n, np.float64)
+        wall = ctypes.c_double()
+        rc = _lib.lcp_queue_replay(self._h, arr, n, timeout_s, lat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   ctypes.byref(wall))
+        return rc, lat, wall.value
+
+    def stats(self):
+        n, l = ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.lcp_queue_stats(self._h, ctypes.byref(n), ctypes.byref(l)), "lcp_queue_stats")
+        return {"inflight": n.value, "worker_launches": l.value}
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib.lcp_queue_destroy(self._h)
+            self._live.clear()
+        self._h = None
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Step:

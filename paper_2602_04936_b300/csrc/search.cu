@@ -24,6 +24,8 @@
 //      first k - |A| fill the remaining slots in ascending id order.
 //   5. A is sorted by (LCP desc, id asc) in registers (warp bitonic network)
 //      and the k (id, lcp) results are written with coalesced stores.
+#include <cuda/atomic>
+
 #include "search.cuh"
 
 namespace lcpk {
@@ -217,12 +219,9 @@ __device__ __forceinline__ int lcp_with_row(const DevIndex& ix, int64_t m, const
     return l;
 }
 
-__global__ void __launch_bounds__(256) k_topk_locate_warp(DevIndex ix, const uint8_t* __restrict__ queries,
-                                                          RowFmt qf, int64_t Q, QLoc* __restrict__ loc) {
-    const int64_t qi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (qi >= Q) return;
+// One warp locates one query: p, lL, lR and the first token.
+__device__ __forceinline__ QLoc warp_locate(const DevIndex& ix, const uint8_t* qrow, const RowFmt& qf) {
     const unsigned lane = lane_id();
-    const uint8_t* qrow = row_of(queries, qi, qf);
     const uint64_t q0 = pack_word(qrow, 0, qf);
     int64_t lo = 0, hi = ix.N;  // rows < q form the prefix [0, p), p in [lo, hi]
     while (hi - lo > 32) {
@@ -239,15 +238,20 @@ __global__ void __launch_bounds__(256) k_topk_locate_warp(DevIndex ix, const uin
     int l = -1;
     if (lane == 0 && p > 0) l = lcp_with_row(ix, p - 1, qrow, qf, q0);
     if (lane == 1 && p < ix.N) l = lcp_with_row(ix, p, qrow, qf, q0);
-    const int lR = __shfl_sync(0xffffffffu, l, 1);
-    if (lane == 0) {
-        QLoc r;
-        r.p = p;
-        r.lL = (int16_t)l;
-        r.lR = (int16_t)lR;
-        r.tok0 = (int32_t)(q0 >> (64 - ix.bits));
-        loc[qi] = r;
-    }
+    QLoc r;
+    r.p = p;
+    r.lL = (int16_t)__shfl_sync(0xffffffffu, l, 0);
+    r.lR = (int16_t)__shfl_sync(0xffffffffu, l, 1);
+    r.tok0 = (int32_t)(q0 >> (64 - ix.bits));
+    return r;
+}
+
+__global__ void __launch_bounds__(256) k_topk_locate_warp(DevIndex ix, const uint8_t* __restrict__ queries,
+                                                          RowFmt qf, int64_t Q, QLoc* __restrict__ loc) {
+    const int64_t qi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (qi >= Q) return;
+    const QLoc r = warp_locate(ix, row_of(queries, qi, qf), qf);
+    if (lane_id() == 0) loc[qi] = r;
 }
 
 // Batches up to this size locate with a warp per query (see above).
@@ -428,6 +432,132 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 8) k_topk_answer(DevIndex i
     }
 }
 
+// ---- persistent worker ----
+
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Lane 0: claims the next task id, or returns -1 after idle_ns without one
+// (or at once when stop is set).  Claims are fetch-and-adds on a device
+// counter, taken only when a task looks available; a warp that loses that
+// race holds an id past the published count and waits for it to be
+// published.  If it gives up first, the id is recorded in min_abandoned, and
+// the last warp to leave the launch rewinds the counter to it, so the next
+// launch claims it again; ids processed meanwhile are skipped there (see
+// take_task).  Every wait is bounded: by the idle clock, and by kSpinLimit
+// iterations.
+__device__ int64_t claim_task(const QueueArgs& a) {
+    const volatile int64_t* pub = &a.ctl->published;
+    const volatile int32_t* stop = &a.ctl->stop;
+    long long t0 = global_ns();
+    unsigned ns = 32;
+    long long spin = 0;
+    for (; spin < kSpinLimit; ++spin) {  // until a task looks available
+        if (*(volatile int64_t*)a.claimed < *pub) break;
+        if (*stop || global_ns() - t0 > a.idle_ns) return -1;
+        __nanosleep(ns);
+        if (ns < 8192) ns <<= 1;
+    }
+    if (spin >= kSpinLimit) {
+        flag_status(a.status, DEV_TIMEOUT);
+        return -1;
+    }
+    const int64_t t = (int64_t)atomicAdd((unsigned long long*)a.claimed, 1ull);
+    t0 = global_ns();
+    ns = 32;
+    for (; spin < kSpinLimit; ++spin) {  // until it is published
+        if (t < *pub) {
+            __threadfence();  // records are read after the count that covers them
+            return t;
+        }
+        if (*stop || global_ns() - t0 > a.idle_ns) break;
+        __nanosleep(ns);
+        if (ns < 8192) ns <<= 1;
+    }
+    atomicMin((long long*)a.min_abandoned, (long long)t);
+    if (spin >= kSpinLimit) flag_status(a.status, DEV_TIMEOUT);
+    return -1;
+}
+
+// A task id is answered once: the ring slot remembers the largest id taken
+// from it (ids of one slot only grow: t, t + tcap, ...).
+__device__ __forceinline__ bool take_task(const QueueArgs& a, int64_t t) {
+    return (int64_t)atomicMax((long long*)&a.taken[t % a.tcap], (long long)t) < t;
+}
+
+// The last warp of a launch to leave: rewind past abandoned ids.
+__device__ void leave_launch(const QueueArgs& a) {
+    const unsigned total = gridDim.x * kSearchWarps;
+    if (atomicAdd(a.exited, 1u) != total - 1) return;
+    const int64_t m = *(volatile int64_t*)a.min_abandoned;
+    if (m < *(volatile int64_t*)a.claimed) *(volatile int64_t*)a.claimed = m;
+    *(volatile int64_t*)a.min_abandoned = INT64_MAX;
+    *(volatile unsigned*)a.exited = 0;
+    __threadfence();
+}
+
+// Warps claim tasks until the queue stays empty for idle_ns.  A task's
+// request is copied into the warp's shared memory (index snapshot and
+// pointers), then each query is located and answered exactly as by
+// lcp_topk_batch.  The warp that finishes a request's last task resets its
+// counter and publishes the ticket to host memory after a system fence.
+__global__ void __launch_bounds__(kSearchWarps * 32, 8) k_queue_worker(QueueArgs a) {
+    __shared__ QWarp sm[kSearchWarps];
+    __shared__ QReq rq[kSearchWarps];
+    const int warp = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    QWarp& S = sm[warp];
+    QReq& R = rq[warp];
+    for (;;) {
+        int64_t t = 0;
+        bool mine = false;
+        if (lane == 0) {
+            t = claim_task(a);
+            if (t < 0) leave_launch(a);
+            else mine = take_task(a, t);
+        }
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t < 0) break;
+        if (!__shfl_sync(0xffffffffu, mine, 0)) continue;  // answered before a rewind
+        QTask task;
+        {
+            const volatile QTask* tw = &a.tasks[t % a.tcap];
+            task.q0 = tw->q0;
+            task.q1 = tw->q1;
+            task.slot = tw->slot;
+        }
+        {  // the request record, copied word by word by the warp
+            const volatile uint64_t* src = reinterpret_cast<const volatile uint64_t*>(&a.reqs[task.slot]);
+            uint64_t* dst = reinterpret_cast<uint64_t*>(&R);
+            for (int w = (int)lane; w < (int)(sizeof(QReq) / 8); w += 32) dst[w] = src[w];
+        }
+        __syncwarp();
+        const bool wide = R.ix.N > (1ll << 24);
+        for (int64_t qi = task.q0; qi < task.q1; ++qi) {
+            const QLoc r = warp_locate(R.ix, row_of(R.queries, qi, R.qf), R.qf);
+            int32_t* oid = R.out_ids + qi * R.k;
+            uint8_t* olcp = R.out_lcp + qi * R.k;
+            if (wide) topk_one<uint64_t>(R.ix, S, r.p, r.lL, r.lR, r.tok0, R.k, oid, olcp);
+            else topk_one<uint32_t>(R.ix, S, r.p, r.lL, r.lR, r.tok0, R.k, oid, olcp);
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) {
+            const int n = atomicAdd(&a.done_count[task.slot], 1);
+            if (n == R.ntasks - 1) {
+                a.done_count[task.slot] = 0;
+                __threadfence_system();
+                cuda::atomic_ref<uint64_t, cuda::thread_scope_system>(a.done[task.slot])
+                    .store(R.ticket, cuda::memory_order_release);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 }  // namespace lcpk
 
 namespace lcph {
@@ -438,6 +568,10 @@ void launch_locate(const DevIndex& ix, const uint8_t* q, const RowFmt& qf, int64
         LCP_TIMED_LAUNCH(k_topk_locate_warp, (unsigned)((Q + 7) / 8), 256, 0, s, ix, q, qf, Q, loc);
     else
         LCP_TIMED_LAUNCH(k_topk_locate, (unsigned)((Q + 255) / 256), 256, 0, s, ix, q, qf, Q, loc);
+}
+
+void launch_queue_worker(const QueueArgs& a, unsigned grid, cudaStream_t s) {
+    LCP_LAUNCH(k_queue_worker, grid, kSearchWarps * 32, 0, s, a);
 }
 
 int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, int32_t* out_ids,

@@ -486,7 +486,60 @@ __device__ __forceinline__ int smallest_ids(const DevIndex& ix, int64_t lo, int6
 
 }  // namespace lcpk
 
+namespace lcpk {
+
+// ---- persistent worker fed by a work queue (queue.cu holds the host side) ----
+
+// One request.  The host fills it in pinned memory and copies it, with the
+// request's task records, to device memory on a copy stream; the new task
+// count is copied after them on the same stream, so a worker that sees the
+// count also sees the records.  The worker reads only device memory.
+struct QReq {
+    DevIndex ix;           // snapshot of the index at submission
+    const uint8_t* queries;
+    RowFmt qf;
+    int32_t k;
+    int32_t ntasks;        // tasks the request was cut into
+    int32_t* out_ids;
+    uint8_t* out_lcp;
+    uint64_t ticket;
+};
+
+// One task: queries [q0, q1) of the request in slot `slot`.
+struct QTask {
+    int64_t q0, q1;
+    int32_t slot;
+    int32_t pad;
+};
+
+// Control words in device memory, written by host copies.
+struct QCtl {
+    int64_t published;  // tasks published so far
+    int32_t stop;       // set at shutdown: idle warps exit at once
+    int32_t pad;
+};
+
+struct QueueArgs {
+    const QCtl* ctl;       // device
+    const QReq* reqs;      // device [rcap]
+    const QTask* tasks;    // device [tcap]
+    uint64_t* done;        // mapped host memory [rcap]: ticket of the last completed request per slot
+    int64_t* claimed;        // device: next task id to claim
+    int64_t* min_abandoned;  // device: smallest id given up unpublished in this launch
+    unsigned* exited;        // device: warps of this launch that have left
+    int64_t* taken;          // device: [tcap] largest id taken from each ring slot (-1 at start)
+    int32_t* done_count;   // device: [rcap] finished tasks of the slot's request
+    int rcap, tcap;
+    long long idle_ns;     // a warp that finds no work for this long exits
+    int* status;           // device status word
+};
+
+}  // namespace lcpk
+
 namespace lcph {
+// Launches the persistent worker (grid CTAs of kSearchWarps warps) on s.
+void launch_queue_worker(const lcpk::QueueArgs& a, unsigned grid, cudaStream_t s);
+
 // Locates every query of a batch (warp per query for small batches, lane per
 // query otherwise) into loc[Q].
 void launch_locate(const lcpk::DevIndex& ix, const uint8_t* q, const lcpk::RowFmt& qf, int64_t Q,
