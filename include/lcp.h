@@ -198,6 +198,28 @@ LCP_API int lcp_tal_topk(lcp_index_t index, const void* d_queries, int64_t Q, in
                          int32_t* d_out_ids, uint8_t* d_out_lcp, lcp_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Autotuner for the indexed search's launch shape (the paper has no
+ * counterpart; the shape never changes a result).  lcp_autotune times every
+ * candidate shape -- queries per warp of the answer kernel (1..32) and
+ * lane- or warp-per-query location -- on the caller's sample batch (device
+ * queries, Q >= 1, k <= max_k) with CUDA events on `stream`, synchronously,
+ * and installs the fastest for later lcp_topk_batch calls whose index and
+ * batch fall in the same class: (floor(log2 N), L, token bytes,
+ * floor(log2 Q), k class {1, <=16, <=64, <=128}), process-wide.
+ * lcp_set_search_shape installs a known shape for that class (to reuse a
+ * cached tuning run).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int32_t qpw;          /* queries per warp chosen */
+    int32_t locate_warp;  /* 1: warp per query, 0: lane per query */
+    float best_ms;        /* its time on the sample batch */
+    float default_ms;     /* the untuned heuristic's time */
+} lcp_tune_result_t;
+LCP_API int lcp_autotune(lcp_index_t index, const void* d_queries, int64_t Q, int32_t k, lcp_stream_t stream,
+                         lcp_tune_result_t* best);
+LCP_API int lcp_set_search_shape(lcp_index_t index, int64_t Q, int32_t k, int32_t qpw, int32_t locate_warp);
+
+/* ------------------------------------------------------------------------
  * Persistent search fed by a device work queue (the batched serving path:
  * requests against several resident indexes of uneven N, L and k run in one
  * long-lived launch instead of a launch per request).  The paper runs one

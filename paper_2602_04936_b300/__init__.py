@@ -53,7 +53,7 @@ ABI_SYMBOLS = (
     "lcp_step_create", "lcp_step_run", "lcp_step_stats", "lcp_step_destroy", "lcp_shard_merge",
     "lcp_topk_bfs", "lcp_tal_topk",
     "lcp_queue_create", "lcp_queue_submit", "lcp_queue_poll", "lcp_queue_stats", "lcp_queue_destroy",
-    "lcp_queue_replay",
+    "lcp_queue_replay", "lcp_autotune", "lcp_set_search_shape",
 )
 
 
@@ -87,6 +87,11 @@ class QueueReplayRequest(ctypes.Structure):
     _fields_ = [("arrival_s", ctypes.c_double), ("index", ctypes.c_void_p), ("k", ctypes.c_int32),
                 ("Q", ctypes.c_int64), ("d_queries", ctypes.c_void_p), ("d_out_ids", ctypes.c_void_p),
                 ("d_out_lcp", ctypes.c_void_p)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("qpw", ctypes.c_int32), ("locate_warp", ctypes.c_int32), ("best_ms", ctypes.c_float),
+                ("default_ms", ctypes.c_float)]
 
 
 class SessionStats(ctypes.Structure):
@@ -144,6 +149,8 @@ def _load():
         "lcp_queue_poll": ([vp, ctypes.c_uint64, i32], ctypes.c_int),
         "lcp_queue_stats": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64)], ctypes.c_int),
         "lcp_queue_destroy": ([vp], ctypes.c_int),
+        "lcp_autotune": ([vp, vp, i64, i32, vp, ctypes.POINTER(TuneResult)], ctypes.c_int),
+        "lcp_set_search_shape": ([vp, i64, i32, i32, i32], ctypes.c_int),
         "lcp_queue_replay": ([vp, ctypes.POINTER(QueueReplayRequest), i64, ctypes.c_double,
                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     }
@@ -387,6 +394,21 @@ def lcp_debug_bounded_wait(spin_limit: int, stream=None) -> int:
 
 LCP_SHARD_MAX = 32
 LCP_TAL_MAX_K = 32
+
+
+def lcp_autotune(index: "Index", queries: torch.Tensor, k: int, stream=None) -> dict:
+    """Times every search launch shape on this sample batch and installs the
+    fastest for batches of the same class (see lcp.h)."""
+    q = _rows(queries, True)
+    r = TuneResult()
+    with torch.cuda.device(q.device):
+        _check(_lib.lcp_autotune(index.handle, _ptr(q), q.shape[0], k, _stream(stream), ctypes.byref(r)),
+               "lcp_autotune")
+    return {"qpw": r.qpw, "locate_warp": r.locate_warp, "best_ms": r.best_ms, "default_ms": r.default_ms}
+
+
+def lcp_set_search_shape(index: "Index", Q: int, k: int, qpw: int, locate_warp: int) -> None:
+    _check(_lib.lcp_set_search_shape(index.handle, Q, k, qpw, locate_warp), "lcp_set_search_shape")
 
 
 def lcp_topk_bfs(index: "Index", queries: torch.Tensor, k: int, out_ids=None, out_lcp=None, stream=None):

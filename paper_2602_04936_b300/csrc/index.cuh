@@ -146,8 +146,15 @@ int build_tie_lists(lcp_index_s* x, cudaStream_t s);
 
 // loc_scratch: caller-owned buffer of search_scratch_bytes(Q) bytes for the
 // per-query position records, or nullptr to use stream-ordered scratch.
+// Launch shape of the indexed search (see search.cuh).
+struct SearchShape {
+    int qpw = 32;         // queries per warp of the answer kernel
+    int locate_warp = 0;  // 1: warp-per-query locate, 0: lane-per-query
+};
+
 int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, int32_t* out_ids,
-                      uint8_t* out_lcp, cudaStream_t s, void* loc_scratch = nullptr);
+                      uint8_t* out_lcp, cudaStream_t s, void* loc_scratch = nullptr,
+                      const SearchShape* shape = nullptr);
 size_t search_scratch_bytes(int64_t Q);
 int insert_device(lcp_index_s* x, const void* d_tokens, int64_t n, cudaStream_t s);
 

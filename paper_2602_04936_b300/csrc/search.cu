@@ -26,6 +26,10 @@
 //      and the k (id, lcp) results are written with coalesced stores.
 #include <cuda/atomic>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "search.cuh"
 
 namespace lcpk {
@@ -563,8 +567,53 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 8) k_queue_worker(QueueArgs
 namespace lcph {
 using namespace lcpk;
 
-void launch_locate(const DevIndex& ix, const uint8_t* q, const RowFmt& qf, int64_t Q, QLoc* loc, cudaStream_t s) {
-    if (Q <= kWarpLocateMaxQ)
+// ---- launch shapes: heuristics, overridden by autotuned entries ----
+
+namespace {
+struct TuneKey {
+    int nlog, L, tb, qlog, kb;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(nlog, L, tb, qlog, kb) < std::tie(o.nlog, o.L, o.tb, o.qlog, o.kb);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, SearchShape> g_tune;
+
+int ilog2(int64_t v) { return v <= 1 ? 0 : 63 - __builtin_clzll((unsigned long long)v); }
+TuneKey tune_key(const lcp_index_s* x, int64_t Q, int k) {
+    return {ilog2(x->N), x->L, x->tb, ilog2(Q), k <= 1 ? 0 : (k <= 16 ? 1 : (k <= 64 ? 2 : 3))};
+}
+}  // namespace
+
+SearchShape default_shape(int64_t Q) {
+    SearchShape sh;
+    sh.locate_warp = Q <= kWarpLocateMaxQ ? 1 : 0;
+    // queries per warp: 32 for large batches; fewer for small batches so
+    // that the batch still spreads over every SM
+    const int64_t full = (int64_t)sm_count() * 32;  // resident warps at full occupancy
+    int64_t qpw = (Q + full - 1) / full;
+    sh.qpw = (int)(qpw < 1 ? 1 : (qpw > 32 ? 32 : qpw));
+    return sh;
+}
+
+SearchShape search_shape(const lcp_index_s* x, int64_t Q, int k) {
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(tune_key(x, Q, k));
+        if (it != g_tune.end()) return it->second;
+    }
+    return default_shape(Q);
+}
+
+void set_search_shape(const lcp_index_s* x, int64_t Q, int k, const SearchShape& sh) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[tune_key(x, Q, k)] = sh;
+}
+
+void launch_locate(const DevIndex& ix, const uint8_t* q, const RowFmt& qf, int64_t Q, QLoc* loc, cudaStream_t s,
+                   int warp_mode) {
+    if (warp_mode < 0) warp_mode = Q <= kWarpLocateMaxQ ? 1 : 0;
+    if (warp_mode)
         LCP_TIMED_LAUNCH(k_topk_locate_warp, (unsigned)((Q + 7) / 8), 256, 0, s, ix, q, qf, Q, loc);
     else
         LCP_TIMED_LAUNCH(k_topk_locate, (unsigned)((Q + 255) / 256), 256, 0, s, ix, q, qf, Q, loc);
@@ -575,7 +624,7 @@ void launch_queue_worker(const QueueArgs& a, unsigned grid, cudaStream_t s) {
 }
 
 int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, int32_t* out_ids,
-                      uint8_t* out_lcp, cudaStream_t s, void* loc_scratch) {
+                      uint8_t* out_lcp, cudaStream_t s, void* loc_scratch, const SearchShape* shape) {
     if (Q <= 0) return LCP_OK;
     if (x->N == 0) {
         LCP_CUDA_TRY(cudaMemsetAsync(out_ids, 0xFF, sizeof(int32_t) * (size_t)Q * k, s));
@@ -590,13 +639,9 @@ int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, i
     QLoc* loc = reinterpret_cast<QLoc*>(loc_scratch);
     const bool own = loc == nullptr;
     if (own) LCP_CUDA_TRY(cudaMallocAsync((void**)&loc, sizeof(QLoc) * (size_t)Q, s));
-    launch_locate(ix, q, qf, Q, loc, s);
-    // queries per warp: 32 for large batches; fewer for small batches so that
-    // the batch still spreads over every SM
-    const int64_t full = (int64_t)sm_count() * 32;  // resident warps at full occupancy
-    int qpw = (int)((Q + full - 1) / full);
-    if (qpw < 1) qpw = 1;
-    if (qpw > 32) qpw = 32;
+    const SearchShape sh = shape ? *shape : search_shape(x, Q, k);
+    launch_locate(ix, q, qf, Q, loc, s, sh.locate_warp);
+    const int qpw = sh.qpw;
     const int64_t warps = (Q + qpw - 1) / qpw;
     const unsigned grid = (unsigned)((warps + kSearchWarps - 1) / kSearchWarps);
     if (x->N <= (1ll << 24)) {

@@ -540,9 +540,15 @@ namespace lcph {
 // Launches the persistent worker (grid CTAs of kSearchWarps warps) on s.
 void launch_queue_worker(const lcpk::QueueArgs& a, unsigned grid, cudaStream_t s);
 
-// Locates every query of a batch (warp per query for small batches, lane per
-// query otherwise) into loc[Q].
+// Locates every query of a batch into loc[Q]: warp per query (warp_mode 1),
+// lane per query (0), or by batch size (-1).
 void launch_locate(const lcpk::DevIndex& ix, const uint8_t* q, const lcpk::RowFmt& qf, int64_t Q,
-                   lcpk::QLoc* loc, cudaStream_t s);
+                   lcpk::QLoc* loc, cudaStream_t s, int warp_mode = -1);
+
+// Launch shape of the indexed search: the heuristic, and the process-wide
+// table of autotuned shapes keyed by (log2 N, L, token bytes, log2 Q, k class).
+SearchShape default_shape(int64_t Q);
+SearchShape search_shape(const lcp_index_s* x, int64_t Q, int k);
+void set_search_shape(const lcp_index_s* x, int64_t Q, int k, const SearchShape& sh);
 }  // namespace lcph
 
