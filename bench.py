@@ -313,9 +313,16 @@ def oracle_rate(S, Qs, k, budget_s=12.0, max_q=4096):
 
 
 def answer_algorithmic_bytes(k):
-    """Bytes one query's answer kernel must move: its 16-byte position record,
-    the H byte and id of its k winners, and its k (id, lcp) results."""
-    return 16 + k * 5 + k * 5
+    """Bytes one query's answer (first-half) kernel must move: its 16-byte
+    position record, the H byte and id of its k winners, its k (id, lcp)
+    results, and its 32-byte record for the tie-fill kernel."""
+    return 16 + k * 5 + k * 5 + 32
+
+
+def fill_algorithmic_bytes(k):
+    """The tie-fill kernel: its 32-byte record and at most k (id, lcp) results
+    (the ids it reads come from lists of at most k)."""
+    return 32 + k * 4 + k * 5
 
 
 def locate_algorithmic_bytes(N, L, tb):
@@ -421,6 +428,7 @@ def run_ours(args, world, rank, local):
     launches = lcp.lcp_launch_count() - launches0
     ans_ms, ans_n = lcp.lcp_kernel_time("k_topk_answer")
     loc_ms, loc_n = lcp.lcp_kernel_time("k_topk_locate")
+    fill_ms, fill_n = lcp.lcp_kernel_time("k_topk_fill")
     lcp.lcp_kernel_timing(False)
     barrier(world)
     clocks = clk.stop()
@@ -452,7 +460,11 @@ def run_ours(args, world, rank, local):
                 "timing": "CUDA events around each launch on its stream, timed region",
                 "other_kernels": {"k_topk_locate": {
                     "launch_ms": round(loc_launch_ms, 4), "bytes_per_query": loc_per_q,
-                    "achieved": round(loc_achieved, 1), "frac": round(loc_achieved / peak, 4)}}}
+                    "achieved": round(loc_achieved, 1), "frac": round(loc_achieved / peak, 4)},
+                    "k_topk_fill": {
+                    "launch_ms": round(fill_ms / max(fill_n, 1), 4), "bytes_per_query": fill_algorithmic_bytes(k),
+                    "achieved": round(Q * fill_algorithmic_bytes(k) / (fill_ms / max(fill_n, 1) / 1e3) / 1e9, 1),
+                    "frac": round(Q * fill_algorithmic_bytes(k) / (fill_ms / max(fill_n, 1) / 1e3) / 1e9 / peak, 4)}}}
 
     # energy: NVML's counter advances in coarse steps, so each figure comes
     # from its own loop of a couple of seconds (idle gaps excluded)

@@ -263,9 +263,23 @@ constexpr int64_t kWarpLocateMaxQ = 8192;
 
 // ---- one query, whole warp ----
 
+// What the second half of a query needs from the first: the level-d*
+// interval, A's extent around p, and how many tie ids to add.
+struct alignas(16) FillRec {
+    int32_t lov, hiv;  // level-d* interval [lov, hiv)
+    int32_t loc, hic;  // A = the items at positions [loc, hic) other than the tie level's
+    int16_t nA, kp;    // |A|, tie ids to add
+    int16_t dstar;
+    int16_t pad;
+    int32_t li;        // tie list of the level-d* node (-2: not looked up)
+    int32_t pad2;
+};
+
+// First half of a query (expansion, d*, the level-d* interval, A ordered and
+// written to output slots [0, |A|)).
 template <typename KT>
-__device__ void topk_one(const DevIndex& ix, QWarp& S, int64_t p, int lL, int lR, int tok0, int k,
-                         int32_t* __restrict__ oid, uint8_t* __restrict__ olcp) {
+__device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, QWarp& S, int64_t p, int lL, int lR, int tok0,
+                                               int k, int32_t* __restrict__ oid, uint8_t* __restrict__ olcp) {
     const unsigned lane = lane_id();
     const int64_t N = ix.N;
     // 3. expansion
@@ -351,10 +365,38 @@ __device__ void topk_one(const DevIndex& ix, QWarp& S, int64_t p, int lL, int lR
     const int64_t nT = (hiv - lov) - nA;
     int kp = k - nA;
     if ((int64_t)kp > nT) kp = (int)nT;
-    // 4. tie fill: first kp ids of the level-d* interval outside A
+    // 5a. A sorted by (LCP desc, id asc) into slots [0, nA)
+    if (nA > 0) {
+        if (nA <= 32) rank_and_write_A<KT>(S, aL, nA, oid, olcp);
+        else sort_and_write_A<4, KT>(S, aL, nA, oid, olcp);
+    }
+    FillRec r;
+    r.lov = (int32_t)lov;
+    r.hiv = (int32_t)hiv;
+    r.loc = (int32_t)(p - aL);
+    r.hic = (int32_t)(p + aR);
+    r.nA = (int16_t)nA;
+    r.kp = (int16_t)(kp > 0 ? kp : 0);
+    r.dstar = (int16_t)dstar;
+    r.li = li;
+    r.pad = 0;
+    r.pad2 = 0;
+    return r;
+}
+
+// Second half of a query: 4. the tie fill (first kp ids of the level-d*
+// interval outside A) and 5b. slots [nA, k): the fill, then padding.
+template <typename WA>
+__device__ __forceinline__ void topk_fill(const DevIndex& ix, WA& S, const FillRec& r, int k,
+                                          int32_t* __restrict__ oid, uint8_t* __restrict__ olcp) {
+    const unsigned lane = lane_id();
+    const int64_t N = ix.N;
+    const int64_t lov = r.lov, hiv = r.hiv, loc = r.loc, hic = r.hic;
+    const int nA = r.nA, kp = r.kp, dstar = r.dstar;
+    const int64_t nT = (hiv - lov) - nA;
+    int li = r.li;
     int ntake = 0;
     bool filled = kp <= 0;
-    const int64_t loc = p - aL, hic = p + aR;
     // a tie level holding a large share of all rows: probe ids in order
     // (expected <= 6 chunks of 128 ids)
     if (!filled && (int64_t)kp * N <= nT * 768) filled = probe_ids(ix, lov, hiv, loc, hic, kp, S.m1, &ntake);
@@ -401,29 +443,36 @@ __device__ void topk_one(const DevIndex& ix, QWarp& S, int64_t p, int lL, int lR
         ntake = compact4(v, keep, S.m1, kp);
         __syncwarp();
     }
-    // 5. A sorted by (LCP desc, id asc), then the tie fill, then padding
-    if (nA > 0) {
-        if (nA <= 32) rank_and_write_A<KT>(S, aL, nA, oid, olcp);
-        else sort_and_write_A<4, KT>(S, aL, nA, oid, olcp);
-    }
-    for (int r = nA + (int)lane; r < k; r += 32) {
+    for (int t = nA + (int)lane; t < k; t += 32) {
         int32_t id = -1;
         uint8_t l = 0;
-        if (r < nA + ntake) {
-            id = (int32_t)S.m1[r - nA];
+        if (t < nA + ntake) {
+            id = (int32_t)S.m1[t - nA];
             l = (uint8_t)dstar;
         }
-        __stcs(oid + r, (int)id);
-        __stcs(reinterpret_cast<char*>(olcp) + r, (char)l);
+        __stcs(oid + t, (int)id);
+        __stcs(reinterpret_cast<char*>(olcp) + t, (char)l);
     }
     __syncwarp();
 }
 
+// One query, whole warp (the persistent worker runs both halves in place).
+template <typename KT>
+__device__ __forceinline__ void topk_one(const DevIndex& ix, QWarp& S, int64_t p, int lL, int lR, int tok0, int k,
+                                         int32_t* __restrict__ oid, uint8_t* __restrict__ olcp) {
+    const FillRec r = topk_expand<KT>(ix, S, p, lL, lR, tok0, k, oid, olcp);
+    topk_fill(ix, S, r, k, oid, olcp);
+}
+
+// Batched search, second and third kernels: the two halves of every query,
+// split so that each kernel's code stays small enough for the instruction
+// cache (warps of one kernel sit in different phases at once).
 template <typename KT>
 __global__ void __launch_bounds__(kSearchWarps * 32, 8) k_topk_answer(DevIndex ix, const QLoc* __restrict__ loc,
                                                                       int64_t Q, int k, int qpw,
                                                                       int32_t* __restrict__ out_ids,
-                                                                      uint8_t* __restrict__ out_lcp) {
+                                                                      uint8_t* __restrict__ out_lcp,
+                                                                      FillRec* __restrict__ recs) {
     __shared__ QWarp sm[kSearchWarps];
     const int warp = threadIdx.x >> 5;
     QWarp& S = sm[warp];
@@ -432,7 +481,24 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 8) k_topk_answer(DevIndex i
         const int64_t qi = wq0 + j;
         if (qi >= Q) break;
         const QLoc r = loc[qi];
-        topk_one<KT>(ix, S, r.p, r.lL, r.lR, r.tok0, k, out_ids + qi * k, out_lcp + qi * k);
+        const FillRec f = topk_expand<KT>(ix, S, r.p, r.lL, r.lR, r.tok0, k, out_ids + qi * k, out_lcp + qi * k);
+        if (lane_id() == 0) recs[qi] = f;
+    }
+}
+
+__global__ void __launch_bounds__(kSearchWarps * 32, 12) k_topk_fill(DevIndex ix, const FillRec* __restrict__ recs,
+                                                                    int64_t Q, int k, int qpw,
+                                                                    int32_t* __restrict__ out_ids,
+                                                                    uint8_t* __restrict__ out_lcp) {
+    __shared__ FWarp sm[kSearchWarps];
+    const int warp = threadIdx.x >> 5;
+    FWarp& S = sm[warp];
+    const int64_t wq0 = ((int64_t)blockIdx.x * kSearchWarps + warp) * qpw;
+    for (int j = 0; j < qpw; ++j) {
+        const int64_t qi = wq0 + j;
+        if (qi >= Q) break;
+        const FillRec f = recs[qi];
+        topk_fill(ix, S, f, k, out_ids + qi * k, out_lcp + qi * k);
     }
 }
 
@@ -638,23 +704,25 @@ int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, i
     // allocate), else stream-ordered scratch
     QLoc* loc = reinterpret_cast<QLoc*>(loc_scratch);
     const bool own = loc == nullptr;
-    if (own) LCP_CUDA_TRY(cudaMallocAsync((void**)&loc, sizeof(QLoc) * (size_t)Q, s));
+    if (own) LCP_CUDA_TRY(cudaMallocAsync((void**)&loc, search_scratch_bytes(Q), s));
     const SearchShape sh = shape ? *shape : search_shape(x, Q, k);
     launch_locate(ix, q, qf, Q, loc, s, sh.locate_warp);
     const int qpw = sh.qpw;
     const int64_t warps = (Q + qpw - 1) / qpw;
     const unsigned grid = (unsigned)((warps + kSearchWarps - 1) / kSearchWarps);
+    FillRec* recs = reinterpret_cast<FillRec*>(loc + Q);  // after the position records (16-byte aligned)
     if (x->N <= (1ll << 24)) {
         LCP_TIMED_LAUNCH(k_topk_answer<uint32_t>, grid, kSearchWarps * 32, 0, s, ix, loc, Q, k, qpw, out_ids,
-                   out_lcp);
+                         out_lcp, recs);
     } else {
         LCP_TIMED_LAUNCH(k_topk_answer<uint64_t>, grid, kSearchWarps * 32, 0, s, ix, loc, Q, k, qpw, out_ids,
-                   out_lcp);
+                         out_lcp, recs);
     }
+    LCP_TIMED_LAUNCH(k_topk_fill, grid, kSearchWarps * 32, 0, s, ix, recs, Q, k, qpw, out_ids, out_lcp);
     if (own) LCP_CUDA_TRY(cudaFreeAsync(loc, s));
     return LCP_OK;
 }
 
-size_t search_scratch_bytes(int64_t Q) { return sizeof(QLoc) * (size_t)(Q > 0 ? Q : 1); }
+size_t search_scratch_bytes(int64_t Q) { return (sizeof(QLoc) + sizeof(FillRec)) * (size_t)(Q > 0 ? Q : 1); }
 
 }  // namespace lcph

@@ -31,6 +31,12 @@ struct alignas(16) QWarp {
     uint8_t rlam[kSide];
 };
 
+// The tie fill's work area (a subset of QWarp).
+struct alignas(16) FWarp {
+    uint32_t src[4][kKMax];
+    uint32_t m1[2 * kKMax];
+};
+
 // ---------------------------------------------------------------------------
 // sort keys: (255 - lcp) above the id, so ascending key = (lcp desc, id asc)
 // ---------------------------------------------------------------------------
@@ -381,7 +387,8 @@ __device__ __forceinline__ int compact4(const uint32_t (&v)[4], const bool (&kee
 
 // The `need` smallest ids of sorted positions [lo, hi) into S.src[0]
 // (need <= kKMax).  Returns how many there are (min(need, hi - lo)).
-__device__ __forceinline__ int smallest_ids(const DevIndex& ix, int64_t lo, int64_t hi, int need, QWarp& S) {
+template <typename WA>  // QWarp or FWarp: uses src and m1
+__device__ __forceinline__ int smallest_ids(const DevIndex& ix, int64_t lo, int64_t hi, int need, WA& S) {
     const unsigned lane = lane_id();
     const int64_t bl0 = lo / kBlk, bh0 = (hi - 1) / kBlk;
     // source descriptors
