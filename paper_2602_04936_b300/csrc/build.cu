@@ -472,7 +472,7 @@ int build_sorted_ids(const void* tokens, const RowFmt& f, int64_t N64, int32_t* 
         return rc;
     }
     // round 0: (word 0, id) over all rows
-    LCP_LAUNCH(k_keys_word0, blocks_for(N, 256), 256, 0, s, tk, f, N, k0, v0);
+    LCP_TIMED_LAUNCH(k_keys_word0, blocks_for(N, 256), 256, 0, s, tk, f, N, k0, v0);
     uint64_t* ks;
     uint32_t* vs;
     rc = radix_sort_pairs_u64(k0, v0, k1, v1, N, 64, w, s, &ks, &vs);
@@ -480,8 +480,8 @@ int build_sorted_ids(const void* tokens, const RowFmt& f, int64_t N64, int32_t* 
         cleanup();
         return rc;
     }
-    LCP_LAUNCH(k_copy_ids, blocks_for(N, 256), 256, 0, s, vs, N, ids_out);
-    LCP_LAUNCH(k_eq_sorted, blocks_for(N, 256), 256, 0, s, ks, N, eq);
+    LCP_TIMED_LAUNCH(k_copy_ids, blocks_for(N, 256), 256, 0, s, vs, N, ids_out);
+    LCP_TIMED_LAUNCH(k_eq_sorted, blocks_for(N, 256), 256, 0, s, ks, N, eq);
     uint32_t m = 0, G = 0;
     rc = tie_compact(eq, N, act, grp, &m, &G, w, s);
     // Rows tied on word 0: small groups are ranked directly on their
@@ -492,10 +492,10 @@ int build_sorted_ids(const void* tokens, const RowFmt& f, int64_t N64, int32_t* 
         uint32_t* big_list = act2;        // free until the LSD rounds
         uint32_t* cnt = w.total + 2;      // [0] big groups, [1] rows in huge groups
         LCP_CUDA_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), s));
-        LCP_LAUNCH(k_group_starts, blocks_for(m, 256), 256, 0, s, grp, m, G, gstart);
-        LCP_LAUNCH(k_group_sort_small, blocks_for(G, 4), 128, 0, s, tk, f, gstart, G, act, ids_out,
+        LCP_TIMED_LAUNCH(k_group_starts, blocks_for(m, 256), 256, 0, s, grp, m, G, gstart);
+        LCP_TIMED_LAUNCH(k_group_sort_small, blocks_for(G, 4), 128, 0, s, tk, f, gstart, G, act, ids_out,
                    big_list, cnt, cnt + 1);
-        LCP_LAUNCH(k_group_sort_mid, blocks_for(m, 33), 256, 0, s, tk, f, gstart, act, ids_out, big_list,
+        LCP_TIMED_LAUNCH(k_group_sort_mid, blocks_for(m, 33), 256, 0, s, tk, f, gstart, act, ids_out, big_list,
                    cnt);
         LCP_CUDA_TRY(cudaMemcpyAsync(w.h_total + 10, cnt + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         LCP_CUDA_TRY(cudaStreamSynchronize(s));
@@ -505,24 +505,24 @@ int build_sorted_ids(const void* tokens, const RowFmt& f, int64_t N64, int32_t* 
     }
     // rounds 1..W-1 on the rows whose prefix is still shared
     for (int r = 1; rc == 0 && r < f.W && m > 0; ++r) {
-        LCP_LAUNCH(k_keys_active, blocks_for(m, 256), 256, 0, s, tk, f, N, ids_out, act, m, r, k0,
+        LCP_TIMED_LAUNCH(k_keys_active, blocks_for(m, 256), 256, 0, s, tk, f, N, ids_out, act, m, r, k0,
                    v0);
         rc = radix_sort_pairs_u64(k0, v0, k1, v1, m, 64, w, s, &ks, &vs);
         if (rc) break;
-        LCP_LAUNCH(k_group_keys, blocks_for(m, 256), 256, 0, s, ks, vs, grp, m, kbi, gk, gv);
+        LCP_TIMED_LAUNCH(k_group_keys, blocks_for(m, 256), 256, 0, s, ks, vs, grp, m, kbi, gk, gv);
         int gbits = 0;
         while (gbits < 32 && (1ull << gbits) < (uint64_t)G) ++gbits;
         uint32_t *gks, *fv;
         rc = radix_sort_pairs_u32(gk, gv, gk1, gv1, m, gbits, w, s, &gks, &fv);
         if (rc) break;
-        LCP_LAUNCH(k_apply_gather, blocks_for(m, 256), 256, 0, s, fv, ids_out, act, kbi, grp, m,
+        LCP_TIMED_LAUNCH(k_apply_gather, blocks_for(m, 256), 256, 0, s, fv, ids_out, act, kbi, grp, m,
                    newid, fkey, fgrp);
-        LCP_LAUNCH(k_apply_scatter, blocks_for(m, 256), 256, 0, s, newid, act, fkey, fgrp, m,
+        LCP_TIMED_LAUNCH(k_apply_scatter, blocks_for(m, 256), 256, 0, s, newid, act, fkey, fgrp, m,
                    ids_out, eq);
         uint32_t m2 = 0, G2 = 0;
         rc = tie_compact(eq, m, idx2, grp2, &m2, &G2, w, s);
         if (rc) break;
-        if (m2) LCP_LAUNCH(k_remap_active, blocks_for(m2, 256), 256, 0, s, act, idx2, m2, act2);
+        if (m2) LCP_TIMED_LAUNCH(k_remap_active, blocks_for(m2, 256), 256, 0, s, act, idx2, m2, act2);
         uint32_t* t = act;
         act = act2;
         act2 = t;
@@ -543,10 +543,10 @@ int gather_rows_and_lcp(const void* tokens, const RowFmt& f, int64_t N, const in
                      ((reinterpret_cast<uintptr_t>(tokens) & 15) == 0) &&
                      ((reinterpret_cast<uintptr_t>(b.rows) & 15) == 0);
     if (vec) {
-        LCP_LAUNCH(k_gather_rows_v2, blocks_for(N * (W / 2), 256), 256, 0, s,
+        LCP_TIMED_LAUNCH(k_gather_rows_v2, blocks_for(N * (W / 2), 256), 256, 0, s,
                    reinterpret_cast<const uint8_t*>(tokens), f, N, ids, b.rows, b.head);
     } else {
-        LCP_LAUNCH(k_gather_rows, blocks_for(N * W, 256), 256, 0, s,
+        LCP_TIMED_LAUNCH(k_gather_rows, blocks_for(N * W, 256), 256, 0, s,
                    reinterpret_cast<const uint8_t*>(tokens), f, N, ids, b.rows, b.head);
     }
     return adjacent_lcp(b.rows, N, W, f.L, f.tpw, f.bits, b.H, s);
@@ -555,7 +555,7 @@ int gather_rows_and_lcp(const void* tokens, const RowFmt& f, int64_t N, const in
 int adjacent_lcp(const uint64_t* rows, int64_t N, int W, int L, int tpw, int bits, uint8_t* H,
                  cudaStream_t s) {
     if (N <= 0) return LCP_OK;
-    LCP_LAUNCH(k_adjacent_lcp, blocks_for(N, 256), 256, 0, s, rows, N, W, L, tpw, bits, H);
+    LCP_TIMED_LAUNCH(k_adjacent_lcp, blocks_for(N, 256), 256, 0, s, rows, N, W, L, tpw, bits, H);
     return LCP_OK;
 }
 
@@ -564,8 +564,8 @@ int build_aux(lcp_index_s* x, cudaStream_t s, bool merged) {
     lcp_buffers& b = x->buf[x->cur];
     if (N <= 0) return LCP_OK;
     if (!merged) {  // an insert's merge pass already wrote pos and the buckets
-        LCP_LAUNCH(k_inverse, blocks_for(N, 256), 256, 0, s, b.ids, N, x->pos);
-        LCP_LAUNCH(k_buckets, blocks_for((1ll << x->bits) + 1, 256), 256, 0, s, b.head, N, x->bits, x->bkt);
+        LCP_TIMED_LAUNCH(k_inverse, blocks_for(N, 256), 256, 0, s, b.ids, N, x->pos);
+        LCP_TIMED_LAUNCH(k_buckets, blocks_for((1ll << x->bits) + 1, 256), 256, 0, s, b.head, N, x->bits, x->bkt);
     }
     // min tree over H: level j+1 = minima of 32 consecutive level-j entries,
     // built while a level has more than 32 entries
@@ -598,9 +598,9 @@ int build_aux(lcp_index_s* x, cudaStream_t s, bool merged) {
     a.nblk = nblk;
     a.sblk = x->sblk;
     a.soff = x->soff;
-    LCP_LAUNCH(k_aux_tree_blocks, a.tree_ctas + blocks_for(nblk, kAuxThreads / 32), kAuxThreads, 0, s, a);
+    LCP_TIMED_LAUNCH(k_aux_tree_blocks, a.tree_ctas + blocks_for(nblk, kAuxThreads / 32), kAuxThreads, 0, s, a);
     for (int j = 4; j <= lev; ++j)  // only past 2^20 rows
-        LCP_LAUNCH(k_min32, blocks_for(x->hlen[j], 256), 256, 0, s, x->hmin + x->hoff[j - 1], x->hlen[j - 1],
+        LCP_TIMED_LAUNCH(k_min32, blocks_for(x->hlen[j], 256), 256, 0, s, x->hmin + x->hoff[j - 1], x->hlen[j - 1],
                    x->hmin + x->hoff[j], x->hlen[j]);
     // sparse table of K smallest ids over runs of 2^j blocks, g levels per
     // launch (recomputation grows as 2^g, so g shrinks as K grows)
@@ -616,7 +616,7 @@ int build_aux(lcp_index_s* x, cudaStream_t s, bool merged) {
         const uint32_t* prev = j == 1 ? x->sblk : x->st + (int64_t)(j - 2) * lstride;
         const int64_t pstride = j == 1 ? kBlk : K;
         uint32_t* out = x->st + (int64_t)(j - 1) * lstride;
-        LCP_LAUNCH(k_st_levels, blocks_for(valid[0] * 32, 256), 256, (size_t)8 * (g > 1 ? 6 : 3) * K * sizeof(uint32_t), s,
+        LCP_TIMED_LAUNCH(k_st_levels, blocks_for(valid[0] * 32, 256), 256, (size_t)8 * (g > 1 ? 6 : 3) * K * sizeof(uint32_t), s,
                    prev, pstride, half, g, K, lstride, valid[0], valid[1], valid[2], out);
         j += g;
     }

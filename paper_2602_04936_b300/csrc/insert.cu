@@ -287,13 +287,13 @@ int insert_device(lcp_index_s* x, const void* d_tokens, int64_t n, cudaStream_t 
         LCP_CUDA_TRY(cudaMallocAsync((void**)&np, sizeof(int64_t) * n, s));
         LCP_CUDA_TRY(cudaMallocAsync((void**)&order, sizeof(int32_t) * n, s));
         LCP_CUDA_TRY(cudaMallocAsync((void**)&packed, sizeof(uint64_t) * n * W, s));
-        LCP_LAUNCH(k_ins_pack, nblocks(n * W, 256), 256, 0, s, reinterpret_cast<const uint8_t*>(d_tokens),
+        LCP_TIMED_LAUNCH(k_ins_pack, nblocks(n * W, 256), 256, 0, s, reinterpret_cast<const uint8_t*>(d_tokens),
                    f, n, W, packed);
         rc = build_sorted_ids(d_tokens, f, n, order, x->status, s);
         if (rc == LCP_OK) {
-            LCP_LAUNCH(k_ins_sorted, nblocks(n * W, 256), 256, 0, s, packed, order, n, W, x->N, srows,
+            LCP_TIMED_LAUNCH(k_ins_sorted, nblocks(n * W, 256), 256, 0, s, packed, order, n, W, x->N, srows,
                        sids);
-            LCP_LAUNCH(k_ins_locate, nblocks(n, 128), 128, 0, s, ob.rows, ob.head, x->N, srows, n, W, np);
+            LCP_TIMED_LAUNCH(k_ins_locate, nblocks(n, 128), 128, 0, s, ob.rows, ob.head, x->N, srows, n, W, np);
         }
     }
     if (rc == LCP_OK) {

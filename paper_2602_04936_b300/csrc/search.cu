@@ -52,7 +52,7 @@ __device__ __forceinline__ void issue_chunk(const DevIndex& ix, int64_t p, int n
     }
 }
 
-__device__ __forceinline__ int finish_chunk(int h, uint32_t id, bool ok, int n, int64_t avail,
+__device__ __forceinline__ int finish_chunk(int& h, uint32_t id, bool ok, int n, int64_t avail,
                                             uint32_t* ids, uint8_t* lam) {
     const unsigned lane = lane_id();
     if (n > 0) h = min(h, (int)lam[n - 1]);
@@ -285,7 +285,14 @@ __device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, QWarp& S, int
     // 3. expansion
     const int64_t availL = p, availR = N - p;
     int nL = 0, nR = 0, dstar = 0;
-    {  // first round: 64 rows per side, all four chunks in flight at once
+    // the depth-1 bucket of q's first token, fetched early: d* is 1 for
+    // about half of the queries, and these loads then cost no extra wait
+    const int32_t bk0 = ix.bkt[tok0], bk1 = ix.bkt[tok0 + 1], bkl = ix.bkt_list[tok0];
+    // first round: 64 rows per side, all four chunks in flight at once; the
+    // LCPs stay in registers too (lane l: items l and 32 + l of each side,
+    // -1 where absent) for the decision below
+    int vL0, vL1, vR0, vR1;
+    {
         int hl, hr, hl2, hr2;
         uint32_t il, ir, il2, ir2;
         bool okl, okr, okl2, okr2;
@@ -295,10 +302,62 @@ __device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, QWarp& S, int
         issue_chunk<false>(ix, p, 32, availR, lR, hr2, ir2, okr2);
         nL += finish_chunk(hl, il, okl, 0, availL, S.lid, S.llam);
         nR += finish_chunk(hr, ir, okr, 0, availR, S.rid, S.rlam);
-        if (nL == 32) nL += finish_chunk(hl2, il2, okl2, 32, availL, S.lid, S.llam);
-        if (nR == 32) nR += finish_chunk(hr2, ir2, okr2, 32, availR, S.rid, S.rlam);
+        vL0 = okl ? hl : -1;
+        vR0 = okr ? hr : -1;
+        vL1 = vR1 = -1;
+        if (nL == 32) {
+            nL += finish_chunk(hl2, il2, okl2, 32, availL, S.lid, S.llam);
+            vL1 = okl2 ? hl2 : -1;
+        }
+        if (nR == 32) {
+            nR += finish_chunk(hr2, ir2, okr2, 32, availR, S.rid, S.rlam);
+            vR1 = okr2 ? hr2 : -1;
+        }
     }
-    for (;;) {
+    // Decision after the first round, in registers: the LCP bound of the
+    // unloaded items on each side is the last loaded LCP there; if at least
+    // k loaded items reach the larger bound F (or nothing is left), d* is
+    // the k-th largest loaded LCP -- found by bisection on the value with
+    // ballot counts -- and A's and the tie level's counts follow by ballots.
+    // Otherwise (about one query in seven) the expansion continues below.
+    bool decided = false;
+    int aL = 0, aR = 0, vL = 0, vR = 0;
+    {
+        auto at = [&](int v0, int v1, int i) {  // item i of a side (i < 64)
+            const int a = __shfl_sync(0xffffffffu, v0, i & 31);
+            const int b = __shfl_sync(0xffffffffu, v1, i & 31);
+            return i < 32 ? a : b;
+        };
+        auto cnt_ge = [&](int v) {
+            return __popc(__ballot_sync(0xffffffffu, vL0 >= v)) + __popc(__ballot_sync(0xffffffffu, vL1 >= v)) +
+                   __popc(__ballot_sync(0xffffffffu, vR0 >= v)) + __popc(__ballot_sync(0xffffffffu, vR1 >= v));
+        };
+        const int bL = nL < availL ? at(vL0, vL1, nL - 1) : -1;
+        const int bR = nR < availR ? at(vR0, vR1, nR - 1) : -1;
+        const int F = bL > bR ? bL : bR;
+        bool ok = F < 0;
+        if (!ok) ok = cnt_ge(F) >= k;  // loaded items with LCP >= F (every loaded item of F's side qualifies)
+        if (ok) {
+            if (nL + nR >= k) {
+                // largest v with cnt_ge(v) >= k, v in [0, max loaded LCP]
+                int lo = 0, hi = (lL > lR ? lL : lR) + 1;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (cnt_ge(mid) >= k) lo = mid;
+                    else hi = mid;
+                }
+                dstar = lo;
+            } else {
+                dstar = 0;
+            }
+            aL = __popc(__ballot_sync(0xffffffffu, vL0 > dstar)) + __popc(__ballot_sync(0xffffffffu, vL1 > dstar));
+            aR = __popc(__ballot_sync(0xffffffffu, vR0 > dstar)) + __popc(__ballot_sync(0xffffffffu, vR1 > dstar));
+            vL = __popc(__ballot_sync(0xffffffffu, vL0 >= dstar)) + __popc(__ballot_sync(0xffffffffu, vL1 >= dstar));
+            vR = __popc(__ballot_sync(0xffffffffu, vR0 >= dstar)) + __popc(__ballot_sync(0xffffffffu, vR1 >= dstar));
+            decided = true;
+        }
+    }
+    for (; !decided;) {
         const int bL = nL < availL ? (int)S.llam[nL - 1] : -1;
         const int bR = nR < availR ? (int)S.rlam[nR - 1] : -1;
         const int F = bL > bR ? bL : bR;
@@ -332,28 +391,29 @@ __device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, QWarp& S, int
         }
     }
     // A = loaded items with LCP > d*; interval [lov, hiv) of level d*.
-    // Counts of loaded items with LCP > d* (aX) and >= d* (vX) per side, by
-    // ballots over the non-increasing LCP arrays.
-    int aL = 0, aR = 0, vL = 0, vR = 0;
-    for (int b = 0; b < nL; b += 32) {
-        const int t = b + (int)lane;
-        const int l = t < nL ? (int)S.llam[t] : -1;
-        aL += __popc(__ballot_sync(0xffffffffu, l > dstar));
-        vL += __popc(__ballot_sync(0xffffffffu, l >= dstar));
-    }
-    for (int b = 0; b < nR; b += 32) {
-        const int t = b + (int)lane;
-        const int l = t < nR ? (int)S.rlam[t] : -1;
-        aR += __popc(__ballot_sync(0xffffffffu, l > dstar));
-        vR += __popc(__ballot_sync(0xffffffffu, l >= dstar));
+    // (Past the first round) counts of loaded items with LCP > d* (aX) and
+    // >= d* (vX) per side, by ballots over the non-increasing LCP arrays.
+    if (!decided) {
+        for (int b = 0; b < nL; b += 32) {
+            const int t = b + (int)lane;
+            const int l = t < nL ? (int)S.llam[t] : -1;
+            aL += __popc(__ballot_sync(0xffffffffu, l > dstar));
+            vL += __popc(__ballot_sync(0xffffffffu, l >= dstar));
+        }
+        for (int b = 0; b < nR; b += 32) {
+            const int t = b + (int)lane;
+            const int l = t < nR ? (int)S.rlam[t] : -1;
+            aR += __popc(__ballot_sync(0xffffffffu, l > dstar));
+            vR += __popc(__ballot_sync(0xffffffffu, l >= dstar));
+        }
     }
     const int nA = aL + aR;
     int64_t lov = 0, hiv = N;
     int li = -2;  // tie list of the level-d* node (-2: not looked up yet)
-    if (dstar == 1) {  // depth-1 bucket of q's first token, bounds and list in one trip
-        lov = ix.bkt[tok0];
-        hiv = ix.bkt[tok0 + 1];
-        li = ix.bkt_list[tok0];
+    if (dstar == 1) {  // depth-1 bucket of q's first token (fetched above)
+        lov = bk0;
+        hiv = bk1;
+        li = bkl;
     } else if (dstar > 1) {
         const bool knownL = vL < nL || nL == availL;
         const bool knownR = vR < nR || nR == availR;
@@ -368,6 +428,7 @@ __device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, QWarp& S, int
     // 5a. A sorted by (LCP desc, id asc) into slots [0, nA)
     if (nA > 0) {
         if (nA <= 32) rank_and_write_A<KT>(S, aL, nA, oid, olcp);
+        else if (nA <= 64) sort_and_write_A<2, KT>(S, aL, nA, oid, olcp);
         else sort_and_write_A<4, KT>(S, aL, nA, oid, olcp);
     }
     FillRec r;

@@ -115,7 +115,13 @@ __device__ __forceinline__ void rank_and_write_A(const QWarp& S, int aL, int nA,
     if (lane < aL) key = make_key<KT>(S.llam[lane], S.lid[lane]);
     else if (lane < nA) key = make_key<KT>(S.rlam[lane - aL], S.rid[lane - aL]);
     int rank = 0;
-    for (int j = 0; j < nA; ++j) rank += __shfl_sync(0xffffffffu, key, j) < key;
+    for (int j = 0; j < nA; j += 4) {  // four independent broadcasts per step
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const KT o = __shfl_sync(0xffffffffu, key, (j + u) & 31);
+            rank += (j + u < nA) && o < key;
+        }
+    }
     if (lane < nA) {
         __stcs(oid + rank, (int)key_id<KT>(key));
         __stcs(reinterpret_cast<char*>(olcp) + rank, (char)key_lam<KT>(key));

@@ -487,25 +487,25 @@ static int radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, uint32_t n,
     if (grid > kHistParts) grid = kHistParts;
     const size_t hsm = sizeof(uint32_t) * 8 * passes * 256;
     LCP_CUDA_TRY(cudaFuncSetAttribute(k_digit_hist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
-    LCP_LAUNCH(k_digit_hist<K>, grid, 256, hsm, s, k0, n, w.hist_parts, passes);
-    LCP_LAUNCH(k_hist_reduce, (passes * 256 + 255) / 256, 256, 0, s, w.hist_parts, grid, passes * 256, w.hist);
-    LCP_LAUNCH(k_digit_prefix, passes, 256, 0, s, w.hist, w.digit_base, w.skip, n);
-    LCP_LAUNCH(k_pass_plan, 1, 32, 0, s, w.skip, passes, w.sel);
+    LCP_TIMED_LAUNCH(k_digit_hist<K>, grid, 256, hsm, s, k0, n, w.hist_parts, passes);
+    LCP_TIMED_LAUNCH(k_hist_reduce, (passes * 256 + 255) / 256, 256, 0, s, w.hist_parts, grid, passes * 256, w.hist);
+    LCP_TIMED_LAUNCH(k_digit_prefix, passes, 256, 0, s, w.hist, w.digit_base, w.skip, n);
+    LCP_TIMED_LAUNCH(k_pass_plan, 1, 32, 0, s, w.skip, passes, w.sel);
     const uint32_t tiles = (n + kSortTile - 1) / kSortTile;
     const size_t smem = sizeof(uint32_t) * (kSortWarps * 256 + 3 * 256 + 16) +
                         (sizeof(K) + sizeof(uint32_t)) * kSortTile;
     LCP_CUDA_TRY(cudaFuncSetAttribute(k_onesweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
     for (int p = 0; p < passes; ++p) {
-        LCP_LAUNCH(k_tile_counts<K>, tiles, kSortThreads, 0, s, k0, k1, n, p, w.skip, w.sel, w.status,
+        LCP_TIMED_LAUNCH(k_tile_counts<K>, tiles, kSortThreads, 0, s, k0, k1, n, p, w.skip, w.sel, w.status,
                    tiles);
-        LCP_LAUNCH(k_tile_scan, 256, 1024, 0, s, p, w.skip, w.status, tiles, w.digit_base);
-        LCP_LAUNCH(k_onesweep<K>, tiles, kSortThreads, smem, s, k0, v0, k1, v1, n, p, w.skip, w.sel,
+        LCP_TIMED_LAUNCH(k_tile_scan, 256, 1024, 0, s, p, w.skip, w.status, tiles, w.digit_base);
+        LCP_TIMED_LAUNCH(k_onesweep<K>, tiles, kSortThreads, smem, s, k0, v0, k1, v1, n, p, w.skip, w.sel,
                    w.status, tiles, w.err);
     }
     unsigned cg = (unsigned)((n + 255) / 256);
     if (cg > (unsigned)sm_count() * 8) cg = sm_count() * 8;
-    LCP_LAUNCH(k_result_to_buf0<K>, cg, 256, 0, s, w.sel, k1, v1, k0, v0, n);
+    LCP_TIMED_LAUNCH(k_result_to_buf0<K>, cg, 256, 0, s, w.sel, k1, v1, k0, v0, n);
     return LCP_OK;
 }
 
@@ -527,9 +527,9 @@ int tie_compact(const uint8_t* eq, uint32_t n, uint32_t* out_idx, uint32_t* out_
     if (h_groups) *h_groups = 0;
     if (n == 0) return LCP_OK;
     uint32_t nb = (n + kCmpBlock - 1) / kCmpBlock;
-    LCP_LAUNCH(k_tie_count, nb, kCmpThreads, 0, s, eq, n, w.block_sums);
-    LCP_LAUNCH(k_scan_block_sums, 1, 1024, 0, s, w.block_sums, nb, w.total);
-    LCP_LAUNCH(k_tie_scatter, nb, kCmpThreads, 0, s, eq, n, w.block_sums, out_idx, out_grp);
+    LCP_TIMED_LAUNCH(k_tie_count, nb, kCmpThreads, 0, s, eq, n, w.block_sums);
+    LCP_TIMED_LAUNCH(k_scan_block_sums, 1, 1024, 0, s, w.block_sums, nb, w.total);
+    LCP_TIMED_LAUNCH(k_tie_scatter, nb, kCmpThreads, 0, s, eq, n, w.block_sums, out_idx, out_grp);
     LCP_CUDA_TRY(cudaMemcpyAsync(w.h_total + 8, w.total, sizeof(uint32_t) * 2,
                                  cudaMemcpyDeviceToHost, s));
     LCP_CUDA_TRY(cudaStreamSynchronize(s));

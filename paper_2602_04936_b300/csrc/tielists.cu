@@ -193,20 +193,20 @@ int build_tie_lists(lcp_index_s* x, cudaStream_t s) {
     const int64_t nsamp = (N + kBlk - 1) / kBlk;
     const int L1 = x->L + 1;
     const int64_t nslots = nsamp * L1;
-    LCP_LAUNCH(k_tl_reset, (unsigned)((nslots + 255) / 256), 256, 0, s, x->tbl, x->slot_flag, nslots);
+    LCP_TIMED_LAUNCH(k_tl_reset, (unsigned)((nslots + 255) / 256), 256, 0, s, x->tbl, x->slot_flag, nslots);
     DevIndex ix = dev_view(x);
-    LCP_LAUNCH(k_heavy_intervals, (unsigned)((nsamp + kTlWarps - 1) / kTlWarps), kTlWarps * 32, 0, s, ix,
+    LCP_TIMED_LAUNCH(k_heavy_intervals, (unsigned)((nsamp + kTlWarps - 1) / kTlWarps), kTlWarps * 32, 0, s, ix,
                nsamp, x->tbl, x->slot_flag, x->slot_lo, x->slot_hi);
     const int64_t nb = (nslots + kScanBlk - 1) / kScanBlk;
-    LCP_LAUNCH(k_flag_count, (unsigned)nb, 256, 0, s, x->slot_flag, nslots, x->tl_sums);
-    LCP_LAUNCH(k_flag_scan_sums, 1, 1024, 0, s, x->tl_sums, nb, x->tl_total);
-    LCP_LAUNCH(k_flag_assign, (unsigned)nb, 256, 0, s, x->slot_flag, nslots, x->tl_sums, x->slot_lo,
+    LCP_TIMED_LAUNCH(k_flag_count, (unsigned)nb, 256, 0, s, x->slot_flag, nslots, x->tl_sums);
+    LCP_TIMED_LAUNCH(k_flag_scan_sums, 1, 1024, 0, s, x->tl_sums, nb, x->tl_total);
+    LCP_TIMED_LAUNCH(k_flag_assign, (unsigned)nb, 256, 0, s, x->slot_flag, nslots, x->tl_sums, x->slot_lo,
                x->slot_hi, x->nlists_cap, x->slot_list, x->tl_lo, x->tl_hi);
-    LCP_LAUNCH(k_node_lists, (unsigned)((x->nlists_cap + kTlWarps - 1) / kTlWarps), kTlWarps * 32, 0, s,
+    LCP_TIMED_LAUNCH(k_node_lists, (unsigned)((x->nlists_cap + kTlWarps - 1) / kTlWarps), kTlWarps * 32, 0, s,
                ix, x->tl_total, x->nlists_cap, x->tl_lo, x->tl_hi, x->tlists, x->tlpos);
-    LCP_LAUNCH(k_remap_tbl, (unsigned)((nslots + 255) / 256), 256, 0, s, x->tbl, nslots, x->slot_list);
+    LCP_TIMED_LAUNCH(k_remap_tbl, (unsigned)((nslots + 255) / 256), 256, 0, s, x->tbl, nslots, x->slot_list);
     const int64_t ntok = 1ll << x->bits;
-    LCP_LAUNCH(k_bucket_lists, (unsigned)((ntok + 255) / 256), 256, 0, s, ix, ntok, x->bkt_list);
+    LCP_TIMED_LAUNCH(k_bucket_lists, (unsigned)((ntok + 255) / 256), 256, 0, s, ix, ntok, x->bkt_list);
     return LCP_OK;
 }
 
