@@ -1,12 +1,12 @@
 // LSD radix sort (8-bit digits) for the index build.
 //
-// One upfront kernel builds the histograms of every digit position in a
-// single read of the keys (warp-aggregated, so that the heavily skewed digits
-// of Zipf-distributed tokens do not serialise on shared memory); digits that are constant over all keys are skipped, decided on
-// the device.  Each remaining pass is reduce-then-scan: per-tile digit counts,
-// one exclusive scan per digit over the tiles, then a kernel that ranks its
-// tile stably (warp multisplit), stages it in shared memory by digit and
-// writes it out in coalesced runs.  No CTA waits for another: a chained scan
+// Each pass is reduce-then-scan: per-tile digit counts (warp-aggregated, so
+// that the heavily skewed digits of Zipf-distributed tokens do not serialise
+// on shared memory), one exclusive scan per digit over the tiles (which also
+// yields the digit totals and detects a constant digit, whose scatter is then
+// skipped on the device), then a kernel that derives the digit bases from the
+// totals, ranks its tile stably (warp multisplit), stages it in shared memory
+// by digit and writes it out in coalesced runs.  No CTA waits for another: a chained scan
 // with look-back serialises the first wave of tiles that start together, and
 // a sort pass has only one or two waves.
 #include "sort.cuh"
@@ -21,11 +21,6 @@ constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
 
-// Digit histograms of every pass in one read.  Each warp counts into its own
-// shared-memory copy (warp-aggregated: lanes with equal digits are found with
-// ballots and one of them adds the group's count, so a hot digit costs one
-// update per warp instead of 32); each CTA writes its partial histogram, and
-// k_hist_reduce sums the partials (no contended atomics).
 // Lanes of the warp whose 8-bit digit equals this lane's (invalid lanes are
 // never peers).  Eight ballots: much cheaper than __match_any_sync.
 __device__ __forceinline__ unsigned digit_peers(uint32_t d, bool valid) {
@@ -37,45 +32,6 @@ __device__ __forceinline__ unsigned digit_peers(uint32_t d, bool valid) {
         peers &= bit ? m : ~m;
     }
     return valid ? peers : 0u;
-}
-
-template <typename K>
-__global__ void __launch_bounds__(256) k_digit_hist(const K* __restrict__ keys, uint32_t n,
-                                                    uint32_t* __restrict__ partial, int passes) {
-    extern __shared__ uint32_t wsh[];  // [8 warps][passes][256]
-    const int nw = blockDim.x >> 5;
-    for (int i = threadIdx.x; i < nw * passes * 256; i += blockDim.x) wsh[i] = 0;
-    __syncthreads();
-    const unsigned lane = lane_id();
-    uint32_t* mine = wsh + (threadIdx.x >> 5) * passes * 256;
-    const uint32_t warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t base = warp_global * 32; base < n; base += nwarps * 32) {
-        uint32_t idx = base + lane;
-        bool valid = idx < n;
-        K k = valid ? keys[idx] : (K)0;
-        for (int p = 0; p < passes; ++p) {
-            const uint32_t d = (uint32_t)(k >> (8 * p)) & 255u;
-            const unsigned peers = digit_peers(d, valid);
-            if (valid && lane == (unsigned)(__ffs(peers) - 1)) mine[p * 256 + d] += __popc(peers);
-            __syncwarp();
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
-        uint32_t t = 0;
-        for (int w = 0; w < nw; ++w) t += wsh[w * passes * 256 + i];
-        partial[(size_t)blockIdx.x * passes * 256 + i] = t;
-    }
-}
-
-__global__ void k_hist_reduce(const uint32_t* __restrict__ partial, int nparts, int bins,
-                              uint32_t* __restrict__ hist) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= bins) return;
-    uint32_t t = 0;
-    for (int b = 0; b < nparts; ++b) t += partial[(size_t)b * bins + i];
-    hist[i] = t;
 }
 
 // Exclusive scan of a 256-entry table by 256 threads.
@@ -95,43 +51,12 @@ __device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t* tm
     return add + x - v;
 }
 
-// Per pass: digit bases (exclusive scan of the histogram) and whether the
-// digit is constant (one bin holds every key).
-__global__ void __launch_bounds__(256) k_digit_prefix(const uint32_t* __restrict__ hist,
-                                                      uint32_t* __restrict__ base,
-                                                      uint32_t* __restrict__ skip, uint32_t n) {
-    __shared__ uint32_t tmp[8];
-    __shared__ int full;
-    const int p = blockIdx.x;
-    if (threadIdx.x == 0) full = 0;
-    __syncthreads();
-    uint32_t c = hist[p * 256 + threadIdx.x];
-    if (c == n) full = 1;
-    uint32_t e = block_excl_scan_256(c, tmp);
-    base[p * 256 + threadIdx.x] = e;
-    __syncthreads();
-    if (threadIdx.x == 0) skip[p] = full ? 1u : 0u;
-}
-
-// Pass plan on the device: a pass whose digit is constant is skipped, so the
-// ping-pong buffer each pass reads depends on how many passes ran before it.
-// sel[p] = 1 if pass p reads buffer 1; sel[8] = 1 if the result is in buffer 1.
-__global__ void k_pass_plan(const uint32_t* __restrict__ skip, int passes, uint32_t* __restrict__ sel) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    uint32_t cur = 0;
-    for (int p = 0; p < passes; ++p) {
-        sel[p] = cur;
-        if (!skip[p]) cur ^= 1u;
-    }
-    sel[8] = cur;
-}
-
 // Moves the result into buffer 0 when an odd number of passes ran.
 template <typename K>
-__global__ void k_result_to_buf0(const uint32_t* __restrict__ sel, const K* __restrict__ k1,
+__global__ void k_result_to_buf0(const uint32_t* __restrict__ sel, int passes, const K* __restrict__ k1,
                                  const uint32_t* __restrict__ v1, K* __restrict__ k0,
                                  uint32_t* __restrict__ v0, uint32_t n) {
-    if (!sel[8]) return;
+    if (!sel[passes]) return;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         k0[i] = k1[i];
         v0[i] = v1[i];
@@ -144,7 +69,6 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_counts(const K* kb0, cons
                                                               int pass, const uint32_t* __restrict__ skip,
                                                               const uint32_t* __restrict__ sel,
                                                               uint32_t* __restrict__ counts, uint32_t tiles) {
-    if (skip[pass]) return;
     __shared__ uint32_t wh[kSortWarps][256];
     const K* __restrict__ kin = sel[pass] ? kb1 : kb0;
     const int tid = threadIdx.x;
@@ -178,17 +102,17 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_counts(const K* kb0, cons
     counts[(size_t)tid * tiles + tile] = t;
 }
 
-// Exclusive scan of each digit's counts over the tiles, offset by the digit's
-// global base: one CTA per digit.
-__global__ void __launch_bounds__(1024) k_tile_scan(int pass, const uint32_t* __restrict__ skip,
+// Exclusive scan of each digit's counts over the tiles (one CTA per digit);
+// the digit's total goes to totals[pass][d], and a digit holding all n keys
+// marks the pass as skipped (its scatter would move nothing).
+__global__ void __launch_bounds__(1024) k_tile_scan(int pass, uint32_t* __restrict__ skip,
                                                     uint32_t* __restrict__ counts, uint32_t tiles,
-                                                    const uint32_t* __restrict__ digit_base_all) {
-    if (skip[pass]) return;
+                                                    uint32_t* __restrict__ totals, uint32_t n) {
     __shared__ uint32_t tmp[32];
     __shared__ uint32_t carry;
     const int d = blockIdx.x;
     uint32_t* col = counts + (size_t)d * tiles;
-    if (threadIdx.x == 0) carry = digit_base_all[pass * 256 + d];
+    if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     for (uint32_t b0 = 0; b0 < tiles; b0 += 1024) {
         const uint32_t i = b0 + threadIdx.x;
@@ -208,14 +132,22 @@ __global__ void __launch_bounds__(1024) k_tile_scan(int pass, const uint32_t* __
         if (threadIdx.x == 1023) carry = add + x;
         __syncthreads();
     }
+    if (threadIdx.x == 0) {
+        totals[pass * 256 + d] = carry;
+        if (carry == n) skip[pass] = 1u;
+    }
 }
 
 // Stable scatter of one tile for pass `pass`, at the offsets from k_tile_scan.
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
     K* kb0, uint32_t* vb0, K* kb1, uint32_t* vb1, uint32_t n, int pass, const uint32_t* __restrict__ skip,
-    const uint32_t* __restrict__ sel, const uint32_t* __restrict__ offsets, uint32_t tiles, int* err) {
-    if (skip[pass]) return;  // constant digit: nothing moves
+    uint32_t* __restrict__ sel, const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ totals,
+    uint32_t tiles, int* err) {
+    // the next pass reads the buffer this one writes, unless this one is
+    // skipped (a constant digit: nothing moves)
+    if (blockIdx.x == 0 && threadIdx.x == 0) sel[pass + 1] = skip[pass] ? sel[pass] : (sel[pass] ^ 1u);
+    if (skip[pass]) return;
     const bool from1 = sel[pass] != 0;
     const K* __restrict__ kin = from1 ? kb1 : kb0;
     const uint32_t* __restrict__ vin = from1 ? vb1 : vb0;
@@ -239,6 +171,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
     const uint32_t tile_n = min((uint32_t)kSortTile, n - base);
     // every global load of the tile is issued before any ranking work
     const uint32_t toff = offsets[(size_t)tid * tiles + tile];
+    const uint32_t dtot = totals[pass * 256 + tid];
     K key[kSortItems];
     uint32_t val[kSortItems];
 #pragma unroll
@@ -283,8 +216,9 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
     }
     uint32_t my = tcount[tid];
     uint32_t ls = block_excl_scan_256(my, misc + 8);
+    const uint32_t dbase = block_excl_scan_256(dtot, misc + 8);  // the digit's first output position
     lstart[tid] = ls;
-    goff[tid] = toff - ls;  // modulo 2^32
+    goff[tid] = dbase + toff - ls;  // modulo 2^32
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
@@ -446,8 +380,6 @@ int sort_work_alloc(SortWork& w, uint32_t cap, int* err, cudaStream_t s) {
     if (tiles == 0) tiles = 1;
     if (nb == 0) nb = 1;
     LCP_CUDA_TRY(cudaMallocAsync((void**)&w.hist, sizeof(uint32_t) * kMaxPasses * 256, s));
-    LCP_CUDA_TRY(cudaMallocAsync((void**)&w.hist_parts, sizeof(uint32_t) * kHistParts * kMaxPasses * 256, s));
-    LCP_CUDA_TRY(cudaMallocAsync((void**)&w.digit_base, sizeof(uint32_t) * kMaxPasses * 256, s));
     LCP_CUDA_TRY(cudaMallocAsync((void**)&w.skip, sizeof(uint32_t) * kMaxPasses, s));
     LCP_CUDA_TRY(cudaMallocAsync((void**)&w.sel, sizeof(uint32_t) * (kMaxPasses + 1), s));
     LCP_CUDA_TRY(cudaMallocAsync((void**)&w.status, sizeof(uint32_t) * tiles * 256, s));
@@ -461,8 +393,6 @@ int sort_work_alloc(SortWork& w, uint32_t cap, int* err, cudaStream_t s) {
 
 void sort_work_free(SortWork& w, cudaStream_t s) {
     cudaFreeAsync(w.hist, s);
-    cudaFreeAsync(w.hist_parts, s);
-    cudaFreeAsync(w.digit_base, s);
     cudaFreeAsync(w.skip, s);
     cudaFreeAsync(w.sel, s);
     cudaFreeAsync(w.status, s);
@@ -483,14 +413,10 @@ static int radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, uint32_t n,
     int passes = (key_bits + 7) / 8;
     if (passes > (int)(sizeof(K))) passes = (int)sizeof(K);
     if (passes < 1) return LCP_OK;
-    int grid = (int)((n + 2047) / 2048);
-    if (grid > kHistParts) grid = kHistParts;
-    const size_t hsm = sizeof(uint32_t) * 8 * passes * 256;
-    LCP_CUDA_TRY(cudaFuncSetAttribute(k_digit_hist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
-    LCP_TIMED_LAUNCH(k_digit_hist<K>, grid, 256, hsm, s, k0, n, w.hist_parts, passes);
-    LCP_TIMED_LAUNCH(k_hist_reduce, (passes * 256 + 255) / 256, 256, 0, s, w.hist_parts, grid, passes * 256, w.hist);
-    LCP_TIMED_LAUNCH(k_digit_prefix, passes, 256, 0, s, w.hist, w.digit_base, w.skip, n);
-    LCP_TIMED_LAUNCH(k_pass_plan, 1, 32, 0, s, w.skip, passes, w.sel);
+    // no upfront histogram: each pass's digit totals come out of its tile
+    // scan, and constant digits are detected there
+    LCP_CUDA_TRY(cudaMemsetAsync(w.skip, 0, sizeof(uint32_t) * kMaxPasses, s));
+    LCP_CUDA_TRY(cudaMemsetAsync(w.sel, 0, sizeof(uint32_t) * (kMaxPasses + 1), s));
     const uint32_t tiles = (n + kSortTile - 1) / kSortTile;
     const size_t smem = sizeof(uint32_t) * (kSortWarps * 256 + 3 * 256 + 16) +
                         (sizeof(K) + sizeof(uint32_t)) * kSortTile;
@@ -499,13 +425,13 @@ static int radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, uint32_t n,
     for (int p = 0; p < passes; ++p) {
         LCP_TIMED_LAUNCH(k_tile_counts<K>, tiles, kSortThreads, 0, s, k0, k1, n, p, w.skip, w.sel, w.status,
                    tiles);
-        LCP_TIMED_LAUNCH(k_tile_scan, 256, 1024, 0, s, p, w.skip, w.status, tiles, w.digit_base);
+        LCP_TIMED_LAUNCH(k_tile_scan, 256, 1024, 0, s, p, w.skip, w.status, tiles, w.hist, n);
         LCP_TIMED_LAUNCH(k_onesweep<K>, tiles, kSortThreads, smem, s, k0, v0, k1, v1, n, p, w.skip, w.sel,
-                   w.status, tiles, w.err);
+                   w.status, w.hist, tiles, w.err);
     }
     unsigned cg = (unsigned)((n + 255) / 256);
     if (cg > (unsigned)sm_count() * 8) cg = sm_count() * 8;
-    LCP_TIMED_LAUNCH(k_result_to_buf0<K>, cg, 256, 0, s, w.sel, k1, v1, k0, v0, n);
+    LCP_TIMED_LAUNCH(k_result_to_buf0<K>, cg, 256, 0, s, w.sel, passes, k1, v1, k0, v0, n);
     return LCP_OK;
 }
 

@@ -9,16 +9,13 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per onesweep tile
 constexpr int kMaxPasses = 8;                         // 8-bit digits of a 64-bit key
-constexpr int kHistParts = 296;                       // CTAs of the histogram kernel (max)
 
 // Device scratch for sorting up to `cap` pairs (allocated stream-ordered).
 struct SortWork {
     uint32_t cap = 0;
-    uint32_t* hist = nullptr;        // [kMaxPasses][256]
-    uint32_t* hist_parts = nullptr;  // [kHistParts][kMaxPasses][256] per-CTA partials
-    uint32_t* digit_base = nullptr;  // [kMaxPasses][256]
-    uint32_t* skip = nullptr;        // [kMaxPasses] 1 if the digit is constant
-    uint32_t* sel = nullptr;         // [kMaxPasses + 1] ping-pong plan (device-decided)
+    uint32_t* hist = nullptr;        // [kMaxPasses][256] digit totals of each pass
+    uint32_t* skip = nullptr;        // [kMaxPasses] 1 if the pass's digit is constant
+    uint32_t* sel = nullptr;         // [kMaxPasses + 1] buffer each pass reads (device-decided)
     uint32_t* status = nullptr;      // [256][tiles] per-tile digit counts, then offsets
     uint32_t* counters = nullptr;    // unused (kept for layout)
     uint64_t* block_sums = nullptr;  // compaction: per-block (active, starts) counts
