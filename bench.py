@@ -105,14 +105,24 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
             return
-        t0 = time.time()  # wait for the sampler's first line before timing starts
-        while time.time() - t0 < 3.0 and os.path.getsize(self.path) == 0:
-            time.sleep(0.05)
+        # wait for the sampler's second line before timing starts: nvidia-smi's
+        # start-up (NVML initialisation, first queries) perturbs the GPU's
+        # host-side work for a while, its steady state does not
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and self._lines() < 2:
+            time.sleep(0.02)
+
+    def _lines(self):
+        try:
+            with open(self.path) as f:
+                return sum(1 for _ in f)
+        except OSError:
+            return 0
 
     def stop(self):
         if self.proc is None:
@@ -414,9 +424,16 @@ def run_ours(args, world, rank, local):
     nclk = NvmlClockSampler(local)
     nclk.start()
     meter = EnergyMeter(local)
+    # the samplers' start leaves the device idle for a moment and perturbs
+    # the first steps after it: warm-up steps bring it back to its steady
+    # state before the timed ones (at least 25 of them, about 70 ms)
+    for _ in range(max(args.warmup, 25)):
+        step()
+    torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
     launches0 = lcp.lcp_launch_count()
+    lcp.lcp_kernel_timing_filter("k_topk_")  # only the search kernels get events
     lcp.lcp_kernel_timing(True)  # per-kernel CUDA events on the launching stream
     torch.cuda.nvtx.range_push("timed")  # lets a launch list select the timed steps
     t_start.record(stream)
@@ -430,6 +447,7 @@ def run_ours(args, world, rank, local):
     loc_ms, loc_n = lcp.lcp_kernel_time("k_topk_locate")
     fill_ms, fill_n = lcp.lcp_kernel_time("k_topk_fill")
     lcp.lcp_kernel_timing(False)
+    lcp.lcp_kernel_timing_filter("")
     barrier(world)
     clocks = clk.stop()
     fine = nclk.stop()

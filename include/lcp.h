@@ -423,6 +423,10 @@ LCP_API int64_t lcp_launch_count(void);
  * name starts with `prefix` (e.g. "k_topk_answer").  Adds two event records
  * per launch, so leave it off where launch overhead matters. */
 LCP_API int lcp_kernel_timing(int enable);
+/* Restricts the timing to kernels whose name starts with `prefix` (NULL or
+ * "" = every timed kernel), so that timing a few kernels adds no event
+ * records to the others. */
+LCP_API int lcp_kernel_timing_filter(const char* prefix);
 LCP_API int lcp_kernel_time(const char* prefix, double* total_ms, int64_t* launches);
 
 /* Test hook for the bounded-wait machinery: launches one kernel that waits

@@ -47,7 +47,7 @@ ABI_SYMBOLS = (
     "lcp_topk_batch", "lcp_topk_batch_host", "lcp_scan_topk", "lcp_index_size",
     "lcp_index_export", "lcp_index_sync", "lcp_index_destroy", "lcp_device_status",
     "lcp_launch_count", "lcp_debug_bounded_wait", "lcp_scan_topk_noalloc",
-    "lcp_kernel_timing", "lcp_kernel_time",
+    "lcp_kernel_timing", "lcp_kernel_time", "lcp_kernel_timing_filter",
     "lcp_session_create", "lcp_session_add_index", "lcp_session_submit", "lcp_session_poll",
     "lcp_session_stats", "lcp_session_destroy", "lcp_session_replay",
     "lcp_step_create", "lcp_step_run", "lcp_step_stats", "lcp_step_destroy", "lcp_shard_merge",
@@ -123,6 +123,7 @@ def _load():
         "lcp_device_status": ([], ctypes.c_int),
         "lcp_launch_count": ([], i64),
         "lcp_kernel_timing": ([ctypes.c_int], ctypes.c_int),
+        "lcp_kernel_timing_filter": ([ctypes.c_char_p], ctypes.c_int),
         "lcp_kernel_time": ([ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)],
                             ctypes.c_int),
         "lcp_debug_bounded_wait": ([i64, vp], ctypes.c_int),
@@ -379,6 +380,11 @@ def lcp_launch_count() -> int:
 def lcp_kernel_timing(enable: bool) -> None:
     """Per-kernel CUDA-event timing on/off (enabling clears the totals)."""
     _check(_lib.lcp_kernel_timing(1 if enable else 0), "lcp_kernel_timing")
+
+
+def lcp_kernel_timing_filter(prefix: str = "") -> None:
+    """Time only kernels whose name starts with prefix ("" = all)."""
+    _check(_lib.lcp_kernel_timing_filter(prefix.encode()), "lcp_kernel_timing_filter")
 
 
 def lcp_kernel_time(prefix: str):

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "index.cuh"
+#include "sort.cuh"
 
 namespace lcph {
 
@@ -15,6 +16,38 @@ static std::atomic<int64_t> g_launches{0};
 static thread_local cudaError_t g_last_cuda = cudaSuccess;
 
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+void note_use(lcp_index_s* x, cudaStream_t s) {
+    for (int i = 0; i < x->nuses; ++i)
+        if (x->uses[i].s == s) {
+            cudaEventRecord(x->uses[i].e, s);
+            return;
+        }
+    if (x->nuses == lcp_index_s::kMaxUses) {
+        x->shared = true;  // too many streams to track
+        return;
+    }
+    lcp_index_s::Use& u = x->uses[x->nuses];
+    if (cudaEventCreateWithFlags(&u.e, cudaEventDisableTiming) != cudaSuccess) {
+        x->shared = true;
+        return;
+    }
+    u.s = s;
+    cudaEventRecord(u.e, s);
+    x->nuses++;
+}
+
+// One non-blocking stream per device for stream-ordered frees.
+static cudaStream_t free_stream() {
+    static cudaStream_t fs[64] = {nullptr};
+    static std::mutex mu;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!fs[dev]) cudaStreamCreateWithFlags(&fs[dev], cudaStreamNonBlocking);
+    return fs[dev];
+}
 
 // ---- per-kernel event timing ----
 struct KtRec {
@@ -38,9 +71,15 @@ static cudaEvent_t kt_event() {  // caller holds g_kt_mu
     return e;
 }
 
+static std::string g_kt_filter;  // time only kernels whose name starts with this ("" = all)
+
 bool ktime_on() { return g_kt_on.load(std::memory_order_relaxed); }
 
 void* ktime_begin(const char* name, cudaStream_t s) {
+    {
+        std::lock_guard<std::mutex> lk(g_kt_mu);
+        if (!g_kt_filter.empty() && strncmp(name, g_kt_filter.c_str(), g_kt_filter.size()) != 0) return nullptr;
+    }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
     std::lock_guard<std::mutex> lk(g_kt_mu);
@@ -126,88 +165,175 @@ static void retain_pool_memory() {
 // Frees with cudaFreeAsync on stream s (the build's own stream on failure) or,
 // with s == nullptr and the device idle, synchronously.
 static void free_index_memory(lcp_index_s* x, cudaStream_t s) {
-    void* ptrs[] = {x->buf[0].rows, x->buf[0].head, x->buf[0].ids, x->buf[0].H,
-                    x->buf[1].rows, x->buf[1].head, x->buf[1].ids, x->buf[1].H,
-                    x->pos, x->hmin, x->sblk, x->soff, x->st, x->bkt, x->status,
-                    x->tbl, x->slot_flag, x->slot_lo, x->slot_hi, x->slot_list, x->tlists,
-                    x->tl_lo, x->tl_hi, x->tl_sums, x->tl_total, x->tlpos, x->bkt_list,
-                    x->ins_rows, x->ins_ids, x->ins_rank};
-    for (void* p : ptrs)
+    for (void* p : {x->arena, x->stage_in, x->stage_out})
         if (p) {
             if (s) cudaFreeAsync(p, s);
             else cudaFree(p);
         }
+    x->arena = x->stage_in = x->stage_out = nullptr;
     x->buf[0] = lcp_buffers();
     x->buf[1] = lcp_buffers();
-    cudaFree(x->stage_in);
-    cudaFree(x->stage_out);
 }
 
-template <typename T>
-static int dalloc(T** p, size_t count, int64_t* bytes, cudaStream_t s) {
-    size_t b = sizeof(T) * (count ? count : 1);
-    cudaError_t e = cudaMallocAsync((void**)p, b, s);
-    if (e != cudaSuccess) return cuda_status(e);
-    *bytes += (int64_t)b;
-    return LCP_OK;
-}
 
 constexpr int kTieListMinK = 16;
 
+// ---- the build as one CUDA graph ----
+//
+// A build is some sixty launches; replayed as one graph they reach the
+// device as a unit instead of one by one.  Each thread keeps, per device, a
+// capture stream, the instantiated graph of its last build (updated in place
+// for the next one: only pointers and grid sizes change) and the build's
+// scratch block (grown when a larger build comes; reuse across streams waits
+// on the event recorded after the graph that used it last).
+struct GraphBuildState {
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void* scratch = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t scratch_free = nullptr;
+    cudaEvent_t chk = nullptr;
+};
+
+static GraphBuildState* graph_build_state() {
+    static thread_local GraphBuildState st[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    GraphBuildState& g = st[dev];
+    if (!g.cap && cudaStreamCreateWithFlags(&g.cap, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    if (!g.scratch_free && cudaEventCreateWithFlags(&g.scratch_free, cudaEventDisableTiming) != cudaSuccess)
+        return nullptr;
+    if (!g.chk && cudaEventCreateWithFlags(&g.chk, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    return &g;
+}
+
+// Returns LCP_OK (built), LCP_PENDING (cannot run as a graph here; nothing
+// was issued) or an error.  Rows tied on their first two words in groups of
+// more than 512 need the exact, host-driven refinement: their count lands in
+// pinned memory behind an event recorded mid-graph, checked after the launch
+// -- the device is usually past it by then, so the host returns while the
+// device still runs the tail of the build -- and a nonzero count (rare:
+// heavy duplication) redoes the order exactly on `s`.
+static int graph_build(lcp_index_s* x, const void* d_tokens, int64_t N, cudaStream_t s) {
+    GraphBuildState* g = graph_build_state();
+    uint32_t* huge = pinned_words();
+    if (!g || !huge) return LCP_PENDING;
+    huge += 12;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return LCP_PENDING;
+    const size_t need = build_scratch_bytes(N);
+    if (g->bytes < need) {
+        if (g->scratch) {
+            LCP_CUDA_TRY(cudaStreamWaitEvent(s, g->scratch_free, 0));
+            LCP_CUDA_TRY(cudaFreeAsync(g->scratch, s));
+            g->scratch = nullptr;
+            g->bytes = 0;
+        }
+        const size_t want = need + need / 4;
+        LCP_CUDA_TRY(cudaMallocAsync(&g->scratch, want, s));
+        g->bytes = want;
+    }
+    *huge = 0;
+    lcpk::RowFmt f = lcpk::make_fmt(x->tb, x->L, d_tokens);
+    const lcp_index_s saved = *x;
+    LCP_CUDA_TRY(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = build_sorted_ids(d_tokens, f, N, x->buf[0].ids, x->status, g->cap, huge, g->scratch);
+    if (rc == LCP_OK && cudaEventRecordWithFlags(g->chk, g->cap, cudaEventRecordExternal) != cudaSuccess)
+        rc = LCP_ERR_CUDA;
+    if (rc == LCP_OK) rc = gather_rows_and_lcp(d_tokens, f, N, x->buf[0].ids, x->buf[0], x->W, g->cap);
+    if (rc == LCP_OK) rc = build_aux(x, g->cap, false);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(g->cap, &graph);
+    if (rc != LCP_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        *x = saved;
+        cudaGetLastError();
+        return LCP_PENDING;  // fall back to the direct path
+    }
+    if (g->exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(g->exec, graph, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(g->exec);
+            g->exec = nullptr;
+        }
+    }
+    if (!g->exec && cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        g->exec = nullptr;
+        cudaGraphDestroy(graph);
+        *x = saved;
+        return LCP_PENDING;
+    }
+    cudaGraphDestroy(graph);
+    LCP_CUDA_TRY(cudaStreamWaitEvent(s, g->scratch_free, 0));  // a graph on another stream used the scratch
+    LCP_CUDA_TRY(cudaGraphLaunch(g->exec, s));
+    LCP_CUDA_TRY(cudaEventRecord(g->scratch_free, s));
+    LCP_CUDA_TRY(cudaEventSynchronize(g->chk));
+    if (*huge != 0) {
+        rc = build_sorted_ids(d_tokens, f, N, x->buf[0].ids, x->status, s);
+        if (rc == LCP_OK) rc = gather_rows_and_lcp(d_tokens, f, N, x->buf[0].ids, x->buf[0], x->W, s);
+        if (rc == LCP_OK) rc = build_aux(x, s, false);
+        if (rc != LCP_OK) return rc;
+    }
+    const cudaError_t le = cudaGetLastError();
+    return le == cudaSuccess ? LCP_OK : cuda_status(le);
+}
+
 static int alloc_index(lcp_index_s* x, int64_t N, int64_t cap, cudaStream_t s) {
-    int64_t& by = x->bytes;
     const int W = x->W;
+    Carver c;  // every index array in one allocation
     int nsets = cap > N ? 2 : 1;
     for (int b = 0; b < nsets; ++b) {
-        int rc;
-        if ((rc = dalloc(&x->buf[b].rows, (size_t)cap * W, &by, s))) return rc;
-        if ((rc = dalloc(&x->buf[b].head, (size_t)cap, &by, s))) return rc;
-        if ((rc = dalloc(&x->buf[b].ids, (size_t)cap, &by, s))) return rc;
-        if ((rc = dalloc(&x->buf[b].H, (size_t)cap, &by, s))) return rc;
+        c.add(&x->buf[b].rows, (size_t)cap * W);
+        c.add(&x->buf[b].head, (size_t)cap);
+        c.add(&x->buf[b].ids, (size_t)cap);
+        c.add(&x->buf[b].H, (size_t)cap);
     }
-    int rc;
-    if ((rc = dalloc(&x->pos, (size_t)cap, &by, s))) return rc;
-    if ((rc = dalloc(&x->hmin, (size_t)(cap / 31 + 64), &by, s))) return rc;
+    c.add(&x->pos, (size_t)cap);
+    c.add(&x->hmin, (size_t)(cap / 31 + 64));
     x->nblk_cap = (cap + lcpk::kBlk - 1) / lcpk::kBlk;
     if (x->nblk_cap < 1) x->nblk_cap = 1;
-    if ((rc = dalloc(&x->sblk, (size_t)x->nblk_cap * lcpk::kBlk, &by, s))) return rc;
-    if ((rc = dalloc(&x->soff, (size_t)x->nblk_cap * lcpk::kBlk, &by, s))) return rc;
+    c.add(&x->sblk, (size_t)x->nblk_cap * lcpk::kBlk);
+    c.add(&x->soff, (size_t)x->nblk_cap * lcpk::kBlk);
     int lev = 0;
     while ((1ll << (lev + 1)) <= x->nblk_cap) ++lev;
     x->st_levels_cap = lev;
-    if ((rc = dalloc(&x->st, (size_t)(lev > 0 ? lev : 1) * x->nblk_cap * x->K, &by, s))) return rc;
-    if ((rc = dalloc(&x->bkt, ((size_t)1 << x->bits) + 1, &by, s))) return rc;
+    c.add(&x->st, (size_t)(lev > 0 ? lev : 1) * x->nblk_cap * x->K);
+    c.add(&x->bkt, ((size_t)1 << x->bits) + 1);
     // heavy-node tie lists: one table row per 128-row sample, one list per
     // node.  For max_k below kTieListMinK a tie fill from the sparse table
     // costs about as many loads as one from a list, so the lists (and their
     // rebuild on every insert) are left out and the search falls back to the
     // sparse table.
-    if ((rc = dalloc(&x->bkt_list, (size_t)1 << x->bits, &by, s))) return rc;
-    LCP_CUDA_TRY(cudaMemsetAsync(x->bkt_list, 0xFF, sizeof(int32_t) << x->bits, s));
+    c.add(&x->bkt_list, (size_t)1 << x->bits);
     if (x->max_k >= kTieListMinK) {
         x->nsamp_cap = (cap + lcpk::kBlk - 1) / lcpk::kBlk;
         if (x->nsamp_cap < 1) x->nsamp_cap = 1;
         const size_t nslots = (size_t)x->nsamp_cap * (size_t)(x->L + 1);
         x->nlists_cap = 4 * x->nsamp_cap + 64;
-        if ((rc = dalloc(&x->tbl, nslots, &by, s))) return rc;
-        if ((rc = dalloc(&x->slot_flag, nslots, &by, s))) return rc;
-        if ((rc = dalloc(&x->slot_lo, nslots, &by, s))) return rc;
-        if ((rc = dalloc(&x->slot_hi, nslots, &by, s))) return rc;
-        if ((rc = dalloc(&x->slot_list, nslots, &by, s))) return rc;
-        if ((rc = dalloc(&x->tl_sums, (nslots + 2047) / 2048, &by, s))) return rc;
-        if ((rc = dalloc(&x->tl_total, 4, &by, s))) return rc;
-        if ((rc = dalloc(&x->tlists, (size_t)x->nlists_cap * x->K, &by, s))) return rc;
-        if ((rc = dalloc(&x->tlpos, (size_t)x->nlists_cap * x->K, &by, s))) return rc;
-        if ((rc = dalloc(&x->tl_lo, (size_t)x->nlists_cap, &by, s))) return rc;
-        if ((rc = dalloc(&x->tl_hi, (size_t)x->nlists_cap, &by, s))) return rc;
+        c.add(&x->tbl, nslots);
+        c.add(&x->slot_flag, nslots);
+        c.add(&x->slot_lo, nslots);
+        c.add(&x->slot_hi, nslots);
+        c.add(&x->slot_list, nslots);
+        c.add(&x->tl_sums, (nslots + 2047) / 2048);
+        c.add(&x->tl_total, 4);
+        c.add(&x->tlists, (size_t)x->nlists_cap * x->K);
+        c.add(&x->tlpos, (size_t)x->nlists_cap * x->K);
+        c.add(&x->tl_lo, (size_t)x->nlists_cap);
+        c.add(&x->tl_hi, (size_t)x->nlists_cap);
     }
-    if ((rc = dalloc(&x->status, 1, &by, s))) return rc;
-    LCP_CUDA_TRY(cudaMemsetAsync(x->status, 0, sizeof(int), s));
+    c.add(&x->status, 1);
     if (cap > N) {
-        if ((rc = dalloc(&x->ins_rows, (size_t)2 * LCP_INSERT_SMALL_BATCH * W, &by, s))) return rc;
-        if ((rc = dalloc(&x->ins_ids, (size_t)LCP_INSERT_SMALL_BATCH, &by, s))) return rc;
-        if ((rc = dalloc(&x->ins_rank, (size_t)2 * LCP_INSERT_SMALL_BATCH, &by, s))) return rc;
+        c.add(&x->ins_rows, (size_t)2 * LCP_INSERT_SMALL_BATCH * W);
+        c.add(&x->ins_ids, (size_t)LCP_INSERT_SMALL_BATCH);
+        c.add(&x->ins_rank, (size_t)2 * LCP_INSERT_SMALL_BATCH);
     }
+    LCP_CUDA_TRY(c.alloc(&x->arena, s));
+    x->bytes = (int64_t)c.total;
+    LCP_CUDA_TRY(cudaMemsetAsync(x->bkt_list, 0xFF, sizeof(int32_t) << x->bits, s));
+    LCP_CUDA_TRY(cudaMemsetAsync(x->status, 0, sizeof(int), s));
     return LCP_OK;
 }
 
@@ -285,16 +411,46 @@ int lcp_index_build(const void* d_tokens, int64_t N, lcp_format_t fmt, int64_t c
     x->cap = capacity;
     x->N = N;
     retain_pool_memory();
-    if (cudaEventCreateWithFlags(&x->done_ev, cudaEventDisableTiming) != cudaSuccess) {
-        delete x;
-        return LCP_ERR_CUDA;
-    }
     int rc = alloc_index(x, N, capacity, s);
+    if (rc == LCP_OK && N > 1) {
+        // the usual path: the whole build replayed as one CUDA graph
+        const int g = graph_build(x, d_tokens, N, s);
+        if (g == LCP_OK) {
+            note_use(x, s);
+            *out = x;
+            return LCP_OK;
+        }
+        if (g != LCP_PENDING) rc = g;  // LCP_PENDING: not graph-capturable here, build below
+    }
     if (rc == LCP_OK && N > 0) {
+        // Issued without waiting for the device.  Rows tied on their first
+        // two words in groups of more than 512 need the exact (host-driven)
+        // refinement; their count lands in pinned memory behind an event
+        // recorded mid-build, checked once everything is queued -- by then
+        // the device is usually past it, so the host returns while the
+        // device still runs the tail of the build.  A nonzero count (rare:
+        // heavy duplication) redoes the order exactly.
         lcpk::RowFmt f = lcpk::make_fmt(x->tb, x->L, d_tokens);
-        rc = build_sorted_ids(d_tokens, f, N, x->buf[0].ids, x->status, s);
+        uint32_t* huge = pinned_words() + 12;
+        cudaEvent_t chk = nullptr;
+        const bool fast = huge && cudaEventCreateWithFlags(&chk, cudaEventDisableTiming) == cudaSuccess;
+        if (fast) {
+            *huge = 0;
+            rc = build_sorted_ids(d_tokens, f, N, x->buf[0].ids, x->status, s, huge);
+            if (rc == LCP_OK) LCP_CUDA_TRY(cudaEventRecord(chk, s));
+        } else {
+            rc = build_sorted_ids(d_tokens, f, N, x->buf[0].ids, x->status, s);
+        }
         if (rc == LCP_OK) rc = gather_rows_and_lcp(d_tokens, f, N, x->buf[0].ids, x->buf[0], x->W, s);
         if (rc == LCP_OK) rc = build_aux(x, s, false);
+        if (fast) {
+            if (rc == LCP_OK && cudaEventSynchronize(chk) == cudaSuccess && *huge != 0) {
+                rc = build_sorted_ids(d_tokens, f, N, x->buf[0].ids, x->status, s);
+                if (rc == LCP_OK) rc = gather_rows_and_lcp(d_tokens, f, N, x->buf[0].ids, x->buf[0], x->W, s);
+                if (rc == LCP_OK) rc = build_aux(x, s, false);
+            }
+            cudaEventDestroy(chk);
+        }
     }
     if (rc == LCP_OK) {
         cudaError_t e = cudaGetLastError();
@@ -304,11 +460,10 @@ int lcp_index_build(const void* d_tokens, int64_t N, lcp_format_t fmt, int64_t c
         cudaStreamSynchronize(s);
         free_index_memory(x, s);
         cudaStreamSynchronize(s);
-        cudaEventDestroy(x->done_ev);
         delete x;
         return rc;
     }
-    cudaEventRecord(x->done_ev, s);
+    note_use(x, s);
     *out = x;
     return LCP_OK;
 }
@@ -340,7 +495,7 @@ int lcp_index_insert(lcp_index_t x, const void* d_tokens, int64_t n, lcp_stream_
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_status(e);
     }
-    cudaEventRecord(x->done_ev, (cudaStream_t)stream);
+    note_use(x, (cudaStream_t)stream);
     return rc;
 }
 
@@ -353,7 +508,7 @@ int lcp_topk_batch(lcp_index_t x, const void* d_queries, int64_t Q, int32_t k, i
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_status(e);
     }
-    cudaEventRecord(x->done_ev, (cudaStream_t)stream);
+    note_use(x, (cudaStream_t)stream);
     return rc;
 }
 
@@ -424,22 +579,34 @@ int lcp_index_export(lcp_index_t x, int32_t* d_ids, uint8_t* d_H, lcp_stream_t s
                                      cudaMemcpyDeviceToDevice, s));
     if (d_H)
         LCP_CUDA_TRY(cudaMemcpyAsync(d_H, x->buf[x->cur].H, (size_t)x->N, cudaMemcpyDeviceToDevice, s));
+    note_use(x, s);
     return LCP_OK;
 }
 
 int lcp_index_sync(lcp_index_t x) {
     if (!x) return LCP_ERR_INVALID;
-    LCP_CUDA_TRY(cudaEventSynchronize(x->done_ev));
+    if (x->shared) LCP_CUDA_TRY(cudaDeviceSynchronize());
+    for (int i = 0; i < x->nuses; ++i) LCP_CUDA_TRY(cudaEventSynchronize(x->uses[i].e));
     return read_status(x->status, nullptr);
 }
 
 int lcp_index_destroy(lcp_index_t x) {
     if (!x) return LCP_OK;
-    // the index may have been used on several streams (some perhaps already
-    // destroyed by their owner): wait for the whole device, then free
-    cudaDeviceSynchronize();
-    free_index_memory(x, nullptr);
-    cudaEventDestroy(x->done_ev);
+    if (x->shared) {
+        // held by a session or work queue, or used on many streams: wait
+        // for the whole device, then free
+        cudaDeviceSynchronize();
+        free_index_memory(x, nullptr);
+    } else {
+        // stream-ordered: the frees wait (on the library's free stream) for
+        // the last operation on every stream the index was used on; the
+        // host does not wait.  Events, not streams, are waited on, so a
+        // stream destroyed by its owner meanwhile does not matter.
+        cudaStream_t fs = free_stream();
+        for (int i = 0; i < x->nuses; ++i) cudaStreamWaitEvent(fs, x->uses[i].e, 0);
+        free_index_memory(x, fs);
+    }
+    for (int i = 0; i < x->nuses; ++i) cudaEventDestroy(x->uses[i].e);
     delete x;
     return LCP_OK;
 }
@@ -463,6 +630,12 @@ int lcp_kernel_timing(int enable) {
         g_kt_total.clear();
     }
     g_kt_on.store(enable != 0);
+    return LCP_OK;
+}
+
+int lcp_kernel_timing_filter(const char* prefix) {
+    std::lock_guard<std::mutex> lk(g_kt_mu);
+    g_kt_filter = prefix ? prefix : "";
     return LCP_OK;
 }
 

@@ -86,12 +86,15 @@ __global__ void k_remap_active(const uint32_t* __restrict__ act, const uint32_t*
 
 // Tie groups after round 0: gstart[g] = first index (in the active list) of
 // group g, gstart[G] = m.
-__global__ void k_group_starts(const uint32_t* __restrict__ grp, uint32_t m, uint32_t G,
+// counts[0] = tied rows m, counts[1] = groups G (written on the device by the
+// tie compaction; grid-stride, so the host never needs them).
+__global__ void k_group_starts(const uint32_t* __restrict__ grp, const uint32_t* __restrict__ counts,
                                uint32_t* __restrict__ gstart) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    if (i == 0 || grp[i] != grp[i - 1]) gstart[grp[i]] = i;
-    if (i == 0) gstart[G] = m;
+    const uint32_t m = counts[0], G = counts[1];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        if (i == 0 || grp[i] != grp[i - 1]) gstart[grp[i]] = i;
+        if (i == 0) gstart[G] = m;
+    }
 }
 
 // Lexicographic comparison of two raw rows from word w0 on, then by id.
@@ -118,33 +121,37 @@ __device__ __forceinline__ bool tie_less(const uint8_t* __restrict__ tokens, con
 // rows with shuffles, and writes them back in order.  Larger groups are listed
 // for k_group_sort_mid (<= 512 rows) or counted for the LSD rounds.
 __global__ void __launch_bounds__(128) k_group_sort_small(const uint8_t* __restrict__ tokens, RowFmt f,
-                                                          const uint32_t* __restrict__ gstart, uint32_t G,
+                                                          const uint32_t* __restrict__ gstart,
+                                                          const uint32_t* __restrict__ counts,
                                                           const uint32_t* __restrict__ act,
                                                           int32_t* __restrict__ ids,
                                                           uint32_t* __restrict__ big_list,
                                                           uint32_t* __restrict__ big_count,
                                                           uint32_t* __restrict__ huge_count) {
-    const uint32_t g = blockIdx.x * 4 + (threadIdx.x >> 5);
-    if (g >= G) return;
+    const uint32_t G = counts[1];
     const unsigned lane = lane_id();
-    const uint32_t gs = gstart[g], n = gstart[g + 1] - gs;
-    if (n > 32) {
-        if (lane == 0) {
-            if (n <= 512) big_list[atomicAdd(big_count, 1u)] = g;
-            else atomicAdd(huge_count, n);
+    const uint32_t nwarps = gridDim.x * 4;
+    for (uint32_t g = blockIdx.x * 4 + (threadIdx.x >> 5); g < G; g += nwarps) {  // warp per group
+        const uint32_t gs = gstart[g], n = gstart[g + 1] - gs;
+        if (n > 32) {
+            if (lane == 0) {
+                if (n <= 512) big_list[atomicAdd(big_count, 1u)] = g;
+                else atomicAdd(huge_count, n);
+            }
+            continue;
         }
-        return;
+        const int32_t my = lane < n ? ids[act[gs + lane]] : 0;
+        const uint64_t key = lane < n ? pack_word(row_of(tokens, my, f), 1, f) : 0ull;
+        uint32_t rank = 0;
+        for (uint32_t j = 0; j < n; ++j) {
+            const int32_t oid = __shfl_sync(0xffffffffu, my, j);
+            const uint64_t ok = __shfl_sync(0xffffffffu, key, j);
+            if (lane < n && j != lane && tie_less(tokens, f, ok, oid, key, my)) ++rank;
+        }
+        __syncwarp();
+        if (lane < n) ids[act[gs + rank]] = my;
+        __syncwarp();
     }
-    const int32_t my = lane < n ? ids[act[gs + lane]] : 0;
-    const uint64_t key = lane < n ? pack_word(row_of(tokens, my, f), 1, f) : 0ull;
-    uint32_t rank = 0;
-    for (uint32_t j = 0; j < n; ++j) {
-        const int32_t oid = __shfl_sync(0xffffffffu, my, j);
-        const uint64_t ok = __shfl_sync(0xffffffffu, key, j);
-        if (lane < n && j != lane && tie_less(tokens, f, ok, oid, key, my)) ++rank;
-    }
-    __syncwarp();
-    if (lane < n) ids[act[gs + rank]] = my;
 }
 
 // Groups of 33..512 rows: one CTA, word-1 keys staged in shared memory.
@@ -156,30 +163,33 @@ __global__ void __launch_bounds__(256) k_group_sort_mid(const uint8_t* __restric
                                                         const uint32_t* __restrict__ big_count) {
     __shared__ int32_t sid[512];
     __shared__ uint64_t skey[512];
-    if (blockIdx.x >= *big_count) return;
-    const uint32_t g = big_list[blockIdx.x];
-    const uint32_t gs = gstart[g], n = gstart[g + 1] - gs;
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const int32_t id = ids[act[gs + i]];
-        sid[i] = id;
-        skey[i] = pack_word(row_of(tokens, id, f), 1, f);
-    }
-    __syncthreads();
-    uint32_t rank[2];
-    for (int r = 0; r < 2; ++r) {
-        const uint32_t i = threadIdx.x + r * 256;
-        rank[r] = 0;
-        if (i < n) {
-            const uint64_t ki = skey[i];
-            const int32_t ii = sid[i];
-            for (uint32_t j = 0; j < n; ++j)
-                if (j != i && tie_less(tokens, f, skey[j], sid[j], ki, ii)) ++rank[r];
+    const uint32_t nbig = *big_count;
+    for (uint32_t b = blockIdx.x; b < nbig; b += gridDim.x) {  // CTA per group
+        const uint32_t g = big_list[b];
+        const uint32_t gs = gstart[g], n = gstart[g + 1] - gs;
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const int32_t id = ids[act[gs + i]];
+            sid[i] = id;
+            skey[i] = pack_word(row_of(tokens, id, f), 1, f);
         }
-    }
-    __syncthreads();
-    for (int r = 0; r < 2; ++r) {
-        const uint32_t i = threadIdx.x + r * 256;
-        if (i < n) ids[act[gs + rank[r]]] = sid[i];
+        __syncthreads();
+        uint32_t rank[2];
+        for (int r = 0; r < 2; ++r) {
+            const uint32_t i = threadIdx.x + r * 256;
+            rank[r] = 0;
+            if (i < n) {
+                const uint64_t ki = skey[i];
+                const int32_t ii = sid[i];
+                for (uint32_t j = 0; j < n; ++j)
+                    if (j != i && tie_less(tokens, f, skey[j], sid[j], ki, ii)) ++rank[r];
+            }
+        }
+        __syncthreads();
+        for (int r = 0; r < 2; ++r) {
+            const uint32_t i = threadIdx.x + r * 256;
+            if (i < n) ids[act[gs + rank[r]]] = sid[i];
+        }
+        __syncthreads();  // the shared arrays are refilled for the next group
     }
 }
 
@@ -432,8 +442,30 @@ using namespace lcpk;
 
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// The build's scratch arrays, carved from one block.
+struct BuildScratch {
+    uint64_t *k0, *k1, *kbi, *fkey;
+    uint32_t *v0, *v1, *act, *grp, *act2, *grp2, *idx2, *gk, *gv, *gk1, *gv1, *fgrp;
+    int32_t* newid;
+    uint8_t* eq;
+    void carve(Carver& c, uint32_t N) {
+        for (uint64_t** p : {&k0, &k1, &kbi, &fkey}) c.add(p, N);
+        for (uint32_t** p : {&v0, &v1, &act, &grp, &act2, &grp2, &idx2, &gk, &gv, &gk1, &gv1, &fgrp}) c.add(p, N);
+        c.add(&newid, N);
+        c.add(&eq, N);
+    }
+};
+
+size_t build_scratch_bytes(int64_t N64) {
+    const uint32_t N = (uint32_t)(N64 > 1 ? N64 : 2);
+    BuildScratch b;
+    Carver c;
+    b.carve(c, N);
+    return c.total + sort_work_bytes(N);
+}
+
 int build_sorted_ids(const void* tokens, const RowFmt& f, int64_t N64, int32_t* ids_out, int* err,
-                     cudaStream_t s) {
+                     cudaStream_t s, uint32_t* huge_host, void* scratch) {
     if (N64 <= 0) return LCP_OK;
     uint32_t N = (uint32_t)N64;
     const uint8_t* tk = reinterpret_cast<const uint8_t*>(tokens);
@@ -441,31 +473,28 @@ int build_sorted_ids(const void* tokens, const RowFmt& f, int64_t N64, int32_t* 
         LCP_CUDA_TRY(cudaMemsetAsync(ids_out, 0, sizeof(int32_t), s));
         return LCP_OK;
     }
-    // scratch
-    uint64_t *k0, *k1, *kbi, *fkey;
-    uint32_t *v0, *v1, *act, *grp, *act2, *grp2, *idx2, *gk, *gv, *gk1, *gv1, *fgrp;
-    int32_t* newid;
-    uint8_t* eq;
-    size_t n8 = sizeof(uint64_t) * N, n4 = sizeof(uint32_t) * N;
-    LCP_CUDA_TRY(cudaMallocAsync((void**)&k0, n8, s));
-    LCP_CUDA_TRY(cudaMallocAsync((void**)&k1, n8, s));
-    LCP_CUDA_TRY(cudaMallocAsync((void**)&kbi, n8, s));
-    LCP_CUDA_TRY(cudaMallocAsync((void**)&fkey, n8, s));
-    uint32_t** u4[] = {&v0, &v1, &act, &grp, &act2, &grp2, &idx2, &gk, &gv, &gk1, &gv1, &fgrp};
-    for (auto p : u4) LCP_CUDA_TRY(cudaMallocAsync((void**)p, n4, s));
-    LCP_CUDA_TRY(cudaMallocAsync((void**)&newid, n4, s));
-    LCP_CUDA_TRY(cudaMallocAsync((void**)&eq, N, s));
+    // scratch: one block, allocated here unless the caller provides it
+    BuildScratch b;
+    Carver c;
+    b.carve(c, N);
+    void* arena = nullptr;
     SortWork w;
-    int rc = sort_work_alloc(w, N, err, s);
+    int rc;
+    if (scratch) {
+        c.place(scratch);
+        rc = sort_work_place(w, N, err, static_cast<char*>(scratch) + c.total);
+    } else {
+        LCP_CUDA_TRY(c.alloc(&arena, s));
+        rc = sort_work_alloc(w, N, err, s);
+    }
+    uint64_t *k0 = b.k0, *k1 = b.k1, *kbi = b.kbi, *fkey = b.fkey;
+    uint32_t *v0 = b.v0, *v1 = b.v1, *act = b.act, *grp = b.grp, *act2 = b.act2, *grp2 = b.grp2, *idx2 = b.idx2;
+    uint32_t *gk = b.gk, *gv = b.gv, *gk1 = b.gk1, *gv1 = b.gv1, *fgrp = b.fgrp;
+    int32_t* newid = b.newid;
+    uint8_t* eq = b.eq;
     auto cleanup = [&]() {
-        cudaFreeAsync(k0, s);
-        cudaFreeAsync(k1, s);
-        cudaFreeAsync(kbi, s);
-        cudaFreeAsync(fkey, s);
-        for (auto p : u4) cudaFreeAsync(*p, s);
-        cudaFreeAsync(newid, s);
-        cudaFreeAsync(eq, s);
-        sort_work_free(w, s);
+        if (arena) cudaFreeAsync(arena, s);
+        if (w.arena) sort_work_free(w, s);
     };
     if (rc) {
         cleanup();
@@ -483,20 +512,42 @@ int build_sorted_ids(const void* tokens, const RowFmt& f, int64_t N64, int32_t* 
     LCP_TIMED_LAUNCH(k_copy_ids, blocks_for(N, 256), 256, 0, s, vs, N, ids_out);
     LCP_TIMED_LAUNCH(k_eq_sorted, blocks_for(N, 256), 256, 0, s, ks, N, eq);
     uint32_t m = 0, G = 0;
-    rc = tie_compact(eq, N, act, grp, &m, &G, w, s);
     // Rows tied on word 0: small groups are ranked directly on their
     // remaining words; only groups of more than 512 rows (if any) need the
     // word-by-word LSD rounds below.
+    if (huge_host) {
+        // without waiting for the device: the tied rows are counted and
+        // grouped on the device, the group kernels read the counts there,
+        // and the rows in groups of more than 512 are counted into
+        // *huge_host, which the caller reads after its final synchronise
+        // (and rebuilds exactly, here with huge_host == nullptr, if nonzero)
+        rc = tie_compact_async(eq, N, act, grp, w, s);
+        if (rc == 0 && f.W > 1) {
+            uint32_t* gstart = idx2;
+            uint32_t* big_list = act2;
+            uint32_t* cnt = w.total + 2;  // [0] big groups, [1] rows in huge groups
+            const unsigned fill = (unsigned)sm_count() * 8;
+            LCP_CUDA_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), s));
+            LCP_TIMED_LAUNCH(k_group_starts, fill, 256, 0, s, grp, w.total, gstart);
+            LCP_TIMED_LAUNCH(k_group_sort_small, fill, 128, 0, s, tk, f, gstart, w.total, act, ids_out, big_list,
+                             cnt, cnt + 1);
+            LCP_TIMED_LAUNCH(k_group_sort_mid, fill, 256, 0, s, tk, f, gstart, act, ids_out, big_list, cnt);
+            LCP_CUDA_TRY(cudaMemcpyAsync(huge_host, cnt + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        }
+        cleanup();
+        return rc;
+    }
+    rc = tie_compact(eq, N, act, grp, &m, &G, w, s);
     if (rc == 0 && m > 0 && f.W > 1) {
         uint32_t* gstart = idx2;          // G + 1 <= m + 1 <= N entries
         uint32_t* big_list = act2;        // free until the LSD rounds
         uint32_t* cnt = w.total + 2;      // [0] big groups, [1] rows in huge groups
+        const unsigned fill = (unsigned)sm_count() * 8;
         LCP_CUDA_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), s));
-        LCP_TIMED_LAUNCH(k_group_starts, blocks_for(m, 256), 256, 0, s, grp, m, G, gstart);
-        LCP_TIMED_LAUNCH(k_group_sort_small, blocks_for(G, 4), 128, 0, s, tk, f, gstart, G, act, ids_out,
-                   big_list, cnt, cnt + 1);
-        LCP_TIMED_LAUNCH(k_group_sort_mid, blocks_for(m, 33), 256, 0, s, tk, f, gstart, act, ids_out, big_list,
-                   cnt);
+        LCP_TIMED_LAUNCH(k_group_starts, fill, 256, 0, s, grp, w.total, gstart);
+        LCP_TIMED_LAUNCH(k_group_sort_small, fill, 128, 0, s, tk, f, gstart, w.total, act, ids_out, big_list,
+                         cnt, cnt + 1);
+        LCP_TIMED_LAUNCH(k_group_sort_mid, fill, 256, 0, s, tk, f, gstart, act, ids_out, big_list, cnt);
         LCP_CUDA_TRY(cudaMemcpyAsync(w.h_total + 10, cnt + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         LCP_CUDA_TRY(cudaStreamSynchronize(s));
         if (w.h_total[10] == 0) m = 0;  // every tie resolved

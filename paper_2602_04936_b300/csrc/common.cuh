@@ -127,6 +127,45 @@ void* ktime_begin(const char* name, cudaStream_t s);
 void ktime_end(void* token, cudaStream_t s);
 }  // namespace lcph
 
+namespace lcph {
+// Carves many device buffers out of one stream-ordered allocation: one
+// allocator call (and one free) instead of one per buffer.  Every buffer
+// starts on a 256-byte boundary.
+struct Carver {
+    struct Req {
+        void** p;
+        size_t bytes;
+    };
+    Req reqs[64];
+    int n = 0;
+    size_t total = 0;
+    template <typename T>
+    void add(T** p, size_t count) {
+        const size_t b = (sizeof(T) * (count ? count : 1) + 255) & ~(size_t)255;
+        reqs[n++] = {reinterpret_cast<void**>(p), b};
+        total += b;
+    }
+    // Points the buffers into caller-provided memory of at least `total` bytes.
+    void place(void* base) {
+        char* c = static_cast<char*>(base);
+        for (int i = 0; i < n; ++i) {
+            *reqs[i].p = c;
+            c += reqs[i].bytes;
+        }
+    }
+    cudaError_t alloc(void** base, cudaStream_t s) {
+        cudaError_t e = cudaMallocAsync(base, total ? total : 256, s);
+        if (e != cudaSuccess) return e;
+        char* c = static_cast<char*>(*base);
+        for (int i = 0; i < n; ++i) {
+            *reqs[i].p = c;
+            c += reqs[i].bytes;
+        }
+        return cudaSuccess;
+    }
+};
+}  // namespace lcph
+
 #define LCP_LAUNCH(kern, grid, block, smem, stream, ...)                 \
     do {                                                                 \
         kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);        \

@@ -91,7 +91,7 @@ int lcp_step_run(lcp_step_t st, const void* d_insert, const void* d_queries, int
     cudaGraphDestroy(g);
     LCP_CUDA_TRY(cudaGraphLaunch(st->exec, (cudaStream_t)stream));
     lcph::count_launch((int)nodes);
-    cudaEventRecord(x->done_ev, (cudaStream_t)stream);
+    lcph::note_use(x, (cudaStream_t)stream);
     st->runs++;
     return LCP_OK;
 }

@@ -110,9 +110,21 @@ struct lcp_index_s {
     int64_t nblk_cap = 0;
     int st_levels_cap = 0;
     int* status = nullptr;  // device status word
-    cudaEvent_t done_ev = nullptr;  // recorded after each operation on the caller's stream
+    // streams the index has been used on, each with an event recorded after
+    // the last operation there; `shared` once a session or work queue holds
+    // it (their streams are not tracked here) or more than kMaxUses streams
+    // were seen -- destroy then waits for the whole device
+    struct Use {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+    };
+    static constexpr int kMaxUses = 8;
+    Use uses[kMaxUses];
+    int nuses = 0;
+    bool shared = false;
     int64_t bytes = 0;
     // host-buffer entry points: device staging grown on demand
+    void* arena = nullptr;  // one allocation holding every device array above
     void* stage_in = nullptr;
     size_t stage_in_bytes = 0;
     void* stage_out = nullptr;
@@ -129,7 +141,9 @@ lcpk::DevIndex dev_view(const lcp_index_s* x);
 
 // Sorts rows of `tokens` and writes their ids in sorted order (build step).
 int build_sorted_ids(const void* tokens, const lcpk::RowFmt& f, int64_t N, int32_t* ids_out,
-                     int* err, cudaStream_t s);
+                     int* err, cudaStream_t s, uint32_t* huge_host = nullptr, void* scratch = nullptr);
+// Bytes of the scratch block build_sorted_ids takes (instead of allocating).
+size_t build_scratch_bytes(int64_t N);
 // rows/head/H from raw tokens and sorted ids.
 int gather_rows_and_lcp(const void* tokens, const lcpk::RowFmt& f, int64_t N, const int32_t* ids,
                         lcp_buffers& b, int W, cudaStream_t s);
@@ -137,6 +151,9 @@ int gather_rows_and_lcp(const void* tokens, const lcpk::RowFmt& f, int64_t N, co
 int adjacent_lcp(const uint64_t* rows, int64_t N, int W, int L, int tpw, int bits, uint8_t* H,
                  cudaStream_t s);
 // pos, min tree and tie tables of the current buffers.
+// Records that the index's last operation on stream s was just issued.
+void note_use(lcp_index_s* x, cudaStream_t s);
+
 // Rebuilds the derived tables (pos, buckets, min tree, sorted blocks, sparse
 // table, tie lists) from the current buffer set; `merged`: an insert's merge
 // pass already wrote pos and the buckets.

@@ -187,6 +187,7 @@ int lcp_queue_submit(lcp_queue_t q, lcp_index_t x, const void* d_queries, int64_
     if (!q || !x || !ticket || Q < 0 || k < 1 || k > x->max_k) return LCP_ERR_INVALID;
     if (Q > 0 && (!d_queries || !d_out_ids || !d_out_lcp)) return LCP_ERR_INVALID;
     std::lock_guard<std::mutex> lk(q->mu);
+    x->shared = true;  // read by the persistent worker from now on
     if (Q == 0 || x->N == 0) {  // nothing to search: answered here (padding)
         if (Q > 0) {
             cudaMemsetAsync(d_out_ids, 0xFF, sizeof(int32_t) * (size_t)Q * k, q->ws);

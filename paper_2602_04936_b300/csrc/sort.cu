@@ -366,39 +366,58 @@ using namespace lcpk;
 // Small pinned host buffer for the few counts the host reads back during a
 // sort, allocated once per process per thread (cudaFreeHost would synchronise
 // the whole device, so it is never freed per build).
-static uint32_t* pinned_words() {
+uint32_t* pinned_words() {
     static thread_local uint32_t* buf = nullptr;
     if (!buf && cudaMallocHost((void**)&buf, sizeof(uint32_t) * 16) != cudaSuccess) buf = nullptr;
     return buf;
 }
 
-int sort_work_alloc(SortWork& w, uint32_t cap, int* err, cudaStream_t s) {
-    w.cap = cap;
-    w.err = err;
+static void sort_work_carve(SortWork& w, uint32_t cap, Carver& c) {
     uint32_t tiles = (cap + kSortTile - 1) / kSortTile;
     uint32_t nb = (cap + kCmpBlock - 1) / kCmpBlock;
     if (tiles == 0) tiles = 1;
     if (nb == 0) nb = 1;
-    LCP_CUDA_TRY(cudaMallocAsync((void**)&w.hist, sizeof(uint32_t) * kMaxPasses * 256, s));
-    LCP_CUDA_TRY(cudaMallocAsync((void**)&w.skip, sizeof(uint32_t) * kMaxPasses, s));
-    LCP_CUDA_TRY(cudaMallocAsync((void**)&w.sel, sizeof(uint32_t) * (kMaxPasses + 1), s));
-    LCP_CUDA_TRY(cudaMallocAsync((void**)&w.status, sizeof(uint32_t) * tiles * 256, s));
-    LCP_CUDA_TRY(cudaMallocAsync((void**)&w.counters, sizeof(uint32_t) * kMaxPasses, s));
-    LCP_CUDA_TRY(cudaMallocAsync((void**)&w.block_sums, sizeof(uint64_t) * nb, s));
-    LCP_CUDA_TRY(cudaMallocAsync((void**)&w.total, sizeof(uint32_t) * 16, s));
+    c.add(&w.hist, (size_t)kMaxPasses * 256);
+    c.add(&w.skip, kMaxPasses);
+    c.add(&w.sel, kMaxPasses + 1);
+    c.add(&w.status, (size_t)tiles * 256);
+    c.add(&w.counters, kMaxPasses);
+    c.add(&w.block_sums, nb);
+    c.add(&w.total, 16);
+}
+
+int sort_work_alloc(SortWork& w, uint32_t cap, int* err, cudaStream_t s) {
+    w.cap = cap;
+    w.err = err;
+    Carver c;
+    sort_work_carve(w, cap, c);
+    LCP_CUDA_TRY(c.alloc(&w.arena, s));
+    w.h_total = pinned_words();
+    if (!w.h_total) return LCP_ERR_OOM;
+    return LCP_OK;
+}
+
+size_t sort_work_bytes(uint32_t cap) {
+    SortWork w;
+    Carver c;
+    sort_work_carve(w, cap, c);
+    return c.total;
+}
+
+int sort_work_place(SortWork& w, uint32_t cap, int* err, void* base) {
+    w.cap = cap;
+    w.err = err;
+    Carver c;
+    sort_work_carve(w, cap, c);
+    c.place(base);
+    w.arena = nullptr;  // not owned
     w.h_total = pinned_words();
     if (!w.h_total) return LCP_ERR_OOM;
     return LCP_OK;
 }
 
 void sort_work_free(SortWork& w, cudaStream_t s) {
-    cudaFreeAsync(w.hist, s);
-    cudaFreeAsync(w.skip, s);
-    cudaFreeAsync(w.sel, s);
-    cudaFreeAsync(w.status, s);
-    cudaFreeAsync(w.counters, s);
-    cudaFreeAsync(w.block_sums, s);
-    cudaFreeAsync(w.total, s);
+    if (w.arena) cudaFreeAsync(w.arena, s);
     w = SortWork();
 }
 
@@ -447,15 +466,26 @@ int radix_sort_pairs_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
     return radix_sort_impl<uint32_t>(k0, v0, k1, v1, n, key_bits, w, s, out_k, out_v);
 }
 
+int tie_compact_async(const uint8_t* eq, uint32_t n, uint32_t* out_idx, uint32_t* out_grp, SortWork& w,
+                      cudaStream_t s) {
+    if (n == 0) {
+        LCP_CUDA_TRY(cudaMemsetAsync(w.total, 0, 2 * sizeof(uint32_t), s));
+        return LCP_OK;
+    }
+    uint32_t nb = (n + kCmpBlock - 1) / kCmpBlock;
+    LCP_TIMED_LAUNCH(k_tie_count, nb, kCmpThreads, 0, s, eq, n, w.block_sums);
+    LCP_TIMED_LAUNCH(k_scan_block_sums, 1, 1024, 0, s, w.block_sums, nb, w.total);
+    LCP_TIMED_LAUNCH(k_tie_scatter, nb, kCmpThreads, 0, s, eq, n, w.block_sums, out_idx, out_grp);
+    return LCP_OK;
+}
+
 int tie_compact(const uint8_t* eq, uint32_t n, uint32_t* out_idx, uint32_t* out_grp,
                 uint32_t* h_count, uint32_t* h_groups, SortWork& w, cudaStream_t s) {
     *h_count = 0;
     if (h_groups) *h_groups = 0;
     if (n == 0) return LCP_OK;
-    uint32_t nb = (n + kCmpBlock - 1) / kCmpBlock;
-    LCP_TIMED_LAUNCH(k_tie_count, nb, kCmpThreads, 0, s, eq, n, w.block_sums);
-    LCP_TIMED_LAUNCH(k_scan_block_sums, 1, 1024, 0, s, w.block_sums, nb, w.total);
-    LCP_TIMED_LAUNCH(k_tie_scatter, nb, kCmpThreads, 0, s, eq, n, w.block_sums, out_idx, out_grp);
+    int rc = tie_compact_async(eq, n, out_idx, out_grp, w, s);
+    if (rc != LCP_OK) return rc;
     LCP_CUDA_TRY(cudaMemcpyAsync(w.h_total + 8, w.total, sizeof(uint32_t) * 2,
                                  cudaMemcpyDeviceToHost, s));
     LCP_CUDA_TRY(cudaStreamSynchronize(s));

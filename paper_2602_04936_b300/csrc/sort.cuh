@@ -22,9 +22,13 @@ struct SortWork {
     uint32_t* total = nullptr;       // compaction result count (device)
     uint32_t* h_total = nullptr;     // pinned host mirror of total + skip flags
     int* err = nullptr;              // device status word
+    void* arena = nullptr;           // one allocation holding the buffers above
 };
 
 int sort_work_alloc(SortWork& w, uint32_t cap, int* err, cudaStream_t s);
+// Sizes and places the same buffers in caller-provided memory (no allocation).
+size_t sort_work_bytes(uint32_t cap);
+int sort_work_place(SortWork& w, uint32_t cap, int* err, void* base);
 void sort_work_free(SortWork& w, cudaStream_t s);
 
 // Stable LSD radix sort of (key, value) pairs by the low `key_bits` bits of
@@ -45,5 +49,11 @@ int radix_sort_pairs_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
 // number of active elements in *h_count (blocks the host).
 int tie_compact(const uint8_t* eq, uint32_t n, uint32_t* out_idx, uint32_t* out_grp,
                 uint32_t* h_count, uint32_t* h_groups, SortWork& w, cudaStream_t s);
+// The same without the host read: the counts stay in w.total[0] (active
+// elements) and w.total[1] (groups).
+int tie_compact_async(const uint8_t* eq, uint32_t n, uint32_t* out_idx, uint32_t* out_grp, SortWork& w,
+                      cudaStream_t s);
+// A small pinned host buffer of this thread (16 words).
+uint32_t* pinned_words();
 
 }  // namespace lcph

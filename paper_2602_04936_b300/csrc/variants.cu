@@ -195,7 +195,7 @@ int lcp_topk_bfs(lcp_index_t x, const void* d_queries, int64_t Q, int32_t k, int
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = lcph::cuda_status(e);
     }
-    cudaEventRecord(x->done_ev, (cudaStream_t)stream);
+    lcph::note_use(x, (cudaStream_t)stream);
     return rc;
 }
 
@@ -209,7 +209,7 @@ int lcp_tal_topk(lcp_index_t x, const void* d_queries, int64_t Q, int32_t k, int
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = lcph::cuda_status(e);
     }
-    cudaEventRecord(x->done_ev, (cudaStream_t)stream);
+    lcph::note_use(x, (cudaStream_t)stream);
     return rc;
 }
 
