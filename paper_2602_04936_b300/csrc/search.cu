@@ -715,11 +715,12 @@ TuneKey tune_key(const lcp_index_s* x, int64_t Q, int k) {
 SearchShape default_shape(int64_t Q) {
     SearchShape sh;
     sh.locate_warp = Q <= kWarpLocateMaxQ ? 1 : 0;
-    // queries per warp: 32 for large batches; fewer for small batches so
-    // that the batch still spreads over every SM
+    // queries per warp: at most 8 (measured best for large batches: enough
+    // warps for an even tail); fewer for small batches so that the batch
+    // still spreads over every SM
     const int64_t full = (int64_t)sm_count() * 32;  // resident warps at full occupancy
     int64_t qpw = (Q + full - 1) / full;
-    sh.qpw = (int)(qpw < 1 ? 1 : (qpw > 32 ? 32 : qpw));
+    sh.qpw = (int)(qpw < 1 ? 1 : (qpw > 8 ? 8 : qpw));
     return sh;
 }
 

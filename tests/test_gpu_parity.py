@@ -277,3 +277,23 @@ def test_bounded_wait_reports_timeout_and_context_survives(lcp):
     assert lcp.lcp_debug_bounded_wait(1 << 14) == lcp.LCP_ERR_TIMEOUT
     S, Qs, k = W.make_dataset("tree16_u8", N=500, Q=50)
     assert_same(indexed(lcp, S, Qs, k), oracle.topk_batch(S, Qs, k), "after timeout")
+
+
+def test_huge_tie_groups_take_the_exact_refinement(lcp):
+    """Rows sharing their first two packed words in groups of more than 512
+    are ordered by the host-driven refinement after the graph build sees
+    their count; the index and answers equal the oracle's."""
+    rng = np.random.default_rng(12)
+    N, L = 6_000, 24  # uint16: 4 tokens per word, so the first 8 tokens are words 0 and 1
+    S = rng.integers(0, 50, size=(N, L)).astype(np.uint16)
+    S[:2_500, :8] = 7          # one group of 2,500 rows tied on words 0-1
+    S[2_500:3_200, :8] = 9     # and one of 700
+    idx = lcp.lcp_index_build(dev(S), max_k=16)
+    ids, H = lcp.lcp_index_export(idx)
+    w_ids, w_H = oracle.sorted_index(S)
+    assert np.array_equal(ids.cpu().numpy(), w_ids) and np.array_equal(H.cpu().numpy(), w_H)
+    Qs = S[rng.integers(0, N, 200)].copy()
+    Qs[::2, 10:] = 3
+    got = lcp.lcp_topk_batch(idx, dev(Qs), 16)
+    assert_same((got[0].cpu().numpy(), got[1].cpu().numpy()), oracle.topk_batch(S, Qs, 16), "huge groups")
+    idx.close()
