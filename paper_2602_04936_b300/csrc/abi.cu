@@ -531,21 +531,74 @@ int lcp_topk_batch_host(lcp_index_t x, const void* h_queries, int64_t Q, int32_t
     if (Q == 0) return LCP_OK;
     if (!h_queries || !h_out_ids || !h_out_lcp) return LCP_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
-    size_t qb = (size_t)Q * x->L * x->tb;
+    const size_t row = (size_t)x->L * x->tb;
+    size_t qb = (size_t)Q * row;
     size_t ob = (size_t)Q * k * (sizeof(int32_t) + 1);
     int rc;
     if ((rc = grow(&x->stage_in, &x->stage_in_bytes, qb, s))) return rc;
     if ((rc = grow(&x->stage_out, &x->stage_out_bytes, ob, s))) return rc;
     int32_t* d_ids = (int32_t*)x->stage_out;
     uint8_t* d_lcp = (uint8_t*)x->stage_out + (size_t)Q * k * sizeof(int32_t);
-    LCP_CUDA_TRY(cudaMemcpyAsync(x->stage_in, h_queries, qb, cudaMemcpyHostToDevice, s));
-    rc = lcp_topk_batch(x, x->stage_in, Q, k, d_ids, d_lcp, stream);
-    if (rc) return rc;
-    LCP_CUDA_TRY(cudaMemcpyAsync(h_out_ids, d_ids, (size_t)Q * k * sizeof(int32_t),
-                                 cudaMemcpyDeviceToHost, s));
-    LCP_CUDA_TRY(cudaMemcpyAsync(h_out_lcp, d_lcp, (size_t)Q * k, cudaMemcpyDeviceToHost, s));
-    LCP_CUDA_TRY(cudaStreamSynchronize(s));
-    return LCP_OK;
+    const uint8_t* hq = static_cast<const uint8_t*>(h_queries);
+    uint8_t* dq = static_cast<uint8_t*>(x->stage_in);
+    // Pipelined in chunks: chunk i's queries cross the bus on one copy
+    // stream while chunk i-1 is searched on `stream` and chunk i-2's results
+    // cross back on another, so the two directions and the search overlap.
+    const int64_t chunk = Q >= 8 * 65536 ? (Q + 7) / 8 : Q;
+    const int nch = (int)((Q + chunk - 1) / chunk);
+    cudaStream_t cin = nullptr, cout = nullptr;
+    cudaEvent_t ev[2 * 8 + 1] = {nullptr};
+    auto cleanup = [&]() {
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+        if (cin) cudaStreamDestroy(cin);
+        if (cout) cudaStreamDestroy(cout);
+    };
+    cudaError_t e = cudaSuccess;
+    if (nch > 1) {
+        e = cudaStreamCreateWithFlags(&cin, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cout, cudaStreamNonBlocking);
+        for (int i = 0; i < 2 * nch + 1 && e == cudaSuccess; ++i)
+            e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 * nch], s);  // the stage buffers are free
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cin, ev[2 * nch], 0);
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_status(e);
+        }
+    }
+    for (int i = 0; i < nch && rc == LCP_OK; ++i) {
+        const int64_t q0 = i * chunk, qc = q0 + chunk < Q ? chunk : Q - q0;
+        cudaStream_t in = nch > 1 ? cin : s, out = nch > 1 ? cout : s;
+        e = cudaMemcpyAsync(dq + q0 * row, hq + q0 * row, qc * row, cudaMemcpyHostToDevice, in);
+        if (e == cudaSuccess && nch > 1) {
+            e = cudaEventRecord(ev[2 * i], in);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[2 * i], 0);
+        }
+        if (e != cudaSuccess) {
+            rc = cuda_status(e);
+            break;
+        }
+        rc = lcp_topk_batch(x, dq + q0 * row, qc, k, d_ids + q0 * k, d_lcp + q0 * k, stream);
+        if (rc != LCP_OK) break;
+        if (nch > 1) {
+            e = cudaEventRecord(ev[2 * i + 1], s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(out, ev[2 * i + 1], 0);
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_out_ids + q0 * k, d_ids + q0 * k, (size_t)qc * k * sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, out);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_out_lcp + q0 * k, d_lcp + q0 * k, (size_t)qc * k, cudaMemcpyDeviceToHost, out);
+        if (e != cudaSuccess) rc = cuda_status(e);
+    }
+    if (nch > 1) {
+        cudaStreamSynchronize(cin);
+        cudaStreamSynchronize(cout);
+    }
+    cudaStreamSynchronize(s);
+    cleanup();
+    return rc;
 }
 
 int lcp_scan_topk(const void* d_tokens, int64_t N, lcp_format_t fmt, const void* d_queries, int64_t Q,

@@ -259,6 +259,12 @@ def test_host_entry_points_match_device(lcp):
     hi, hl = lcp.lcp_topk_batch_host(idx, host(Qs), k)
     want = oracle.topk_batch(S, Qs, k)
     assert_same((hi.numpy(), hl.numpy()), want, "host entry points")
+    # a batch large enough for the chunked, overlapped copy path
+    Qb = np.tile(Qs, (1300, 1))  # 650,000 queries
+    hi, hl = lcp.lcp_topk_batch_host(idx, host(Qb), k)
+    di, dl = lcp.lcp_topk_batch(idx, dev(Qb), k)
+    assert np.array_equal(hi.numpy(), di.cpu().numpy()) and np.array_equal(hl.numpy(), dl.cpu().numpy())
+    assert np.array_equal(hi.numpy()[-500:], want[0]) and np.array_equal(hl.numpy()[-500:], want[1])
     idx.close()
 
 
