@@ -1,29 +1,28 @@
 // Indexed batched top-k (Algorithm 3 + CollectTopK / CollectTopKOptimized,
 // returning the order of the Definition "Top-k LCP Retrieval").
 //
-// Per warp, 32 queries:
-//   1. lane-per-query binary search on the L2-resident head array (word 0 of
-//      every sorted row): p0 = first row with head >= q0; a gallop from p0
-//      finds p1 = first row with head > q0.  When no row shares word 0 with
-//      the query (p0 == p1), the insertion point is p0 and both neighbours'
-//      LCPs follow from their heads alone.
-//   then warp-per-query, for each of the 32:
-//   2. (only if p1 > p0) lower bound p inside [p0, p1) on the full rows, one
-//      coalesced row per probe, and lL = LCP(q, row p-1), lR = LCP(q, row p);
-//      max(lL, lR) is the descent depth of Algorithm 3.
-//   3. expansion: along each side the LCP of row j with q is the running
-//      minimum of H towards p (descent lemma, App. A).  32-item chunks are
-//      loaded, first from both sides at once, then from the side whose next
-//      LCP is larger, until at least k loaded items have an LCP no smaller
-//      than anything not loaded; d* is then the k-th largest loaded LCP.
-//      Items with LCP > d* (the set A, fewer than k) are all taken.
-//   4. the interval [lo, hi) of level d* (the prefix bucket of q[1..d*],
-//      Sec. 6.2) is closed with the 32-ary min tree over H (left and right
-//      searches interleaved), its smallest ids come from up to two partial
-//      blocks and two sparse-table lists, A's members are skipped, and the
-//      first k - |A| fill the remaining slots in ascending id order.
-//   5. A is sorted by (LCP desc, id asc) in registers (warp bitonic network)
-//      and the k (id, lcp) results are written with coalesced stores.
+// Three kernels per batch, with small per-query records between them (one
+// fused kernel stalled on instruction fetch):
+//   locate  the insertion point p of each query (first row >= q) and its
+//           LCPs lL, lR with rows p-1 and p: one lane per query over the
+//           L2-resident head array (word 0 of every sorted row) for large
+//           batches, one warp per query with a 33-way search for small ones.
+//           max(lL, lR) is the descent depth of Algorithm 3.
+//   answer  one warp per query: expansion -- along each side the LCP of row
+//           j with q is the running minimum of H towards p (descent lemma,
+//           App. A); 32-item chunks are loaded, 64 per side at once, then
+//           from the side whose next LCP is larger, until at least k loaded
+//           items have an LCP no smaller than anything not loaded; d* is the
+//           k-th largest loaded LCP.  Items with LCP > d* (the set A, fewer
+//           than k) are all taken, ordered by (LCP desc, id asc) and written
+//           to slots [0, |A|).  The interval [lo, hi) of level d* (the prefix
+//           bucket of q[1..d*], Sec. 6.2) comes from the depth-1 buckets or
+//           the 32-ary min tree over H.
+//   fill    one warp per query: the first k - |A| ids of the level-d*
+//           interval outside A, in ascending id order (an id-order probe, a
+//           heavy trie node's precomputed list, or two sparse-table lists
+//           and two partial blocks), then padding, into slots [|A|, k).
+// The persistent work-queue worker runs the same stages per query.
 #include <cuda/atomic>
 
 #include <map>

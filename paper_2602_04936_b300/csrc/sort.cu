@@ -17,9 +17,6 @@ using lcph::kSortItems;
 using lcph::kSortThreads;
 using lcph::kSortTile;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr uint32_t kFlagAgg = 1u << 30;
-constexpr uint32_t kFlagInc = 2u << 30;
-constexpr uint32_t kValMask = (1u << 30) - 1;
 
 // Lanes of the warp whose 8-bit digit equals this lane's (invalid lanes are
 // never peers).  Eight ballots: much cheaper than __match_any_sync.
@@ -235,7 +232,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
         K k = skeys[j];
         uint32_t d = (uint32_t)(k >> shift) & 255u;
         uint32_t dst = goff[d] + j;
-        if (dst < n) {  // always true unless a look-back wait ran out
+        if (dst < n) {  // always true for consistent counts; checked rather than trusted
             kout[dst] = k;
             vout[dst] = svals[j];
         } else {
@@ -381,7 +378,6 @@ static void sort_work_carve(SortWork& w, uint32_t cap, Carver& c) {
     c.add(&w.skip, kMaxPasses);
     c.add(&w.sel, kMaxPasses + 1);
     c.add(&w.status, (size_t)tiles * 256);
-    c.add(&w.counters, kMaxPasses);
     c.add(&w.block_sums, nb);
     c.add(&w.total, 16);
 }

@@ -17,7 +17,6 @@ struct SortWork {
     uint32_t* skip = nullptr;        // [kMaxPasses] 1 if the pass's digit is constant
     uint32_t* sel = nullptr;         // [kMaxPasses + 1] buffer each pass reads (device-decided)
     uint32_t* status = nullptr;      // [256][tiles] per-tile digit counts, then offsets
-    uint32_t* counters = nullptr;    // unused (kept for layout)
     uint64_t* block_sums = nullptr;  // compaction: per-block (active, starts) counts
     uint32_t* total = nullptr;       // compaction result count (device)
     uint32_t* h_total = nullptr;     // pinned host mirror of total + skip flags
