@@ -276,8 +276,8 @@ struct alignas(16) FillRec {
 
 // First half of a query (expansion, d*, the level-d* interval, A ordered and
 // written to output slots [0, |A|)).
-template <typename KT>
-__device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, QWarp& S, int64_t p, int lL, int lR, int tok0,
+template <typename KT, typename WA>
+__device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, WA& S, int64_t p, int lL, int lR, int tok0,
                                                int k, int32_t* __restrict__ oid, uint8_t* __restrict__ olcp) {
     const unsigned lane = lane_id();
     const int64_t N = ix.N;
@@ -533,9 +533,9 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 8) k_topk_answer(DevIndex i
                                                                       int32_t* __restrict__ out_ids,
                                                                       uint8_t* __restrict__ out_lcp,
                                                                       FillRec* __restrict__ recs) {
-    __shared__ QWarp sm[kSearchWarps];
+    __shared__ AWarp sm[kSearchWarps];
     const int warp = threadIdx.x >> 5;
-    QWarp& S = sm[warp];
+    AWarp& S = sm[warp];
     const int64_t wq0 = ((int64_t)blockIdx.x * kSearchWarps + warp) * qpw;
     for (int j = 0; j < qpw; ++j) {
         const int64_t qi = wq0 + j;

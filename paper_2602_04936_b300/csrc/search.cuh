@@ -31,6 +31,14 @@ struct alignas(16) QWarp {
     uint8_t rlam[kSide];
 };
 
+// The expansion's work area (a subset of QWarp): the loaded items per side.
+struct alignas(16) AWarp {
+    uint32_t lid[kSide];
+    uint32_t rid[kSide];
+    uint8_t llam[kSide];
+    uint8_t rlam[kSide];
+};
+
 // The tie fill's work area (a subset of QWarp).
 struct alignas(16) FWarp {
     uint32_t src[4][kKMax];
@@ -106,8 +114,8 @@ __device__ __forceinline__ void warp_bitonic(KT (&v)[E]) {
 // the number of items whose key is smaller (keys are distinct: ids differ),
 // found with nA broadcasts -- fewer instructions than a 32-key bitonic
 // network whenever A is small, which it usually is.
-template <typename KT>
-__device__ __forceinline__ void rank_and_write_A(const QWarp& S, int aL, int nA,
+template <typename KT, typename WA>
+__device__ __forceinline__ void rank_and_write_A(const WA& S, int aL, int nA,
                                                  int32_t* __restrict__ oid,
                                                  uint8_t* __restrict__ olcp) {
     const int lane = (int)lane_id();
@@ -130,8 +138,8 @@ __device__ __forceinline__ void rank_and_write_A(const QWarp& S, int aL, int nA,
 
 // Sorts A (left items [0, aL), right items [0, nA - aL)) and writes the
 // first nA output slots.
-template <int E, typename KT>
-__device__ __forceinline__ void sort_and_write_A(const QWarp& S, int aL, int nA,
+template <int E, typename KT, typename WA>
+__device__ __forceinline__ void sort_and_write_A(const WA& S, int aL, int nA,
                                                  int32_t* __restrict__ oid,
                                                  uint8_t* __restrict__ olcp) {
     const int lane = (int)lane_id();
