@@ -154,8 +154,11 @@ __global__ void __launch_bounds__(128) k_group_sort_small(const uint8_t* __restr
     }
 }
 
-// Groups of 33..512 rows: one CTA, word-1 keys staged in shared memory.
-__global__ void __launch_bounds__(256) k_group_sort_mid(const uint8_t* __restrict__ tokens, RowFmt f,
+// Groups of 33..512 rows: one CTA of 512 threads, one row per thread, word-1
+// keys staged in shared memory.  Each thread counts the keys below its own in
+// a branch-free pass; only a row whose word 1 is shared with another row of
+// the group (rare) compares the later words of those rows, then the ids.
+__global__ void __launch_bounds__(512) k_group_sort_mid(const uint8_t* __restrict__ tokens, RowFmt f,
                                                         const uint32_t* __restrict__ gstart,
                                                         const uint32_t* __restrict__ act,
                                                         int32_t* __restrict__ ids,
@@ -164,31 +167,34 @@ __global__ void __launch_bounds__(256) k_group_sort_mid(const uint8_t* __restric
     __shared__ int32_t sid[512];
     __shared__ uint64_t skey[512];
     const uint32_t nbig = *big_count;
+    const uint32_t i = threadIdx.x;
     for (uint32_t b = blockIdx.x; b < nbig; b += gridDim.x) {  // CTA per group
         const uint32_t g = big_list[b];
         const uint32_t gs = gstart[g], n = gstart[g + 1] - gs;
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-            const int32_t id = ids[act[gs + i]];
-            sid[i] = id;
-            skey[i] = pack_word(row_of(tokens, id, f), 1, f);
+        int32_t my = 0;
+        uint64_t ki = 0;
+        if (i < n) {
+            my = ids[act[gs + i]];
+            ki = pack_word(row_of(tokens, my, f), 1, f);
+            sid[i] = my;
+            skey[i] = ki;
         }
         __syncthreads();
-        uint32_t rank[2];
-        for (int r = 0; r < 2; ++r) {
-            const uint32_t i = threadIdx.x + r * 256;
-            rank[r] = 0;
-            if (i < n) {
-                const uint64_t ki = skey[i];
-                const int32_t ii = sid[i];
-                for (uint32_t j = 0; j < n; ++j)
-                    if (j != i && tie_less(tokens, f, skey[j], sid[j], ki, ii)) ++rank[r];
+        uint32_t rank = 0;
+        if (i < n) {
+            uint32_t tied = 0;
+#pragma unroll 8
+            for (uint32_t j = 0; j < n; ++j) {
+                const uint64_t kj = skey[j];
+                rank += kj < ki;
+                tied += kj == ki;
             }
+            if (tied > 1)  // itself included
+                for (uint32_t j = 0; j < n; ++j)
+                    if (j != i && skey[j] == ki && row_less(tokens, f, 2, sid[j], my)) ++rank;
         }
         __syncthreads();
-        for (int r = 0; r < 2; ++r) {
-            const uint32_t i = threadIdx.x + r * 256;
-            if (i < n) ids[act[gs + rank[r]]] = sid[i];
-        }
+        if (i < n) ids[act[gs + rank]] = my;
         __syncthreads();  // the shared arrays are refilled for the next group
     }
 }
@@ -531,7 +537,7 @@ int build_sorted_ids(const void* tokens, const RowFmt& f, int64_t N64, int32_t* 
             LCP_TIMED_LAUNCH(k_group_starts, fill, 256, 0, s, grp, w.total, gstart);
             LCP_TIMED_LAUNCH(k_group_sort_small, fill, 128, 0, s, tk, f, gstart, w.total, act, ids_out, big_list,
                              cnt, cnt + 1);
-            LCP_TIMED_LAUNCH(k_group_sort_mid, fill, 256, 0, s, tk, f, gstart, act, ids_out, big_list, cnt);
+            LCP_TIMED_LAUNCH(k_group_sort_mid, fill, 512, 0, s, tk, f, gstart, act, ids_out, big_list, cnt);
             LCP_CUDA_TRY(cudaMemcpyAsync(huge_host, cnt + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         }
         cleanup();
@@ -547,7 +553,7 @@ int build_sorted_ids(const void* tokens, const RowFmt& f, int64_t N64, int32_t* 
         LCP_TIMED_LAUNCH(k_group_starts, fill, 256, 0, s, grp, w.total, gstart);
         LCP_TIMED_LAUNCH(k_group_sort_small, fill, 128, 0, s, tk, f, gstart, w.total, act, ids_out, big_list,
                          cnt, cnt + 1);
-        LCP_TIMED_LAUNCH(k_group_sort_mid, fill, 256, 0, s, tk, f, gstart, act, ids_out, big_list, cnt);
+        LCP_TIMED_LAUNCH(k_group_sort_mid, fill, 512, 0, s, tk, f, gstart, act, ids_out, big_list, cnt);
         LCP_CUDA_TRY(cudaMemcpyAsync(w.h_total + 10, cnt + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         LCP_CUDA_TRY(cudaStreamSynchronize(s));
         if (w.h_total[10] == 0) m = 0;  // every tie resolved
