@@ -15,11 +15,21 @@
 
 namespace lcpk {
 
+// Word 0 of every row.  Only its first 8 bytes of each row are needed, so
+// the aligned load asks L2 for a 64-byte fetch rather than a whole line.
 __global__ void k_keys_word0(const uint8_t* __restrict__ tokens, RowFmt f, uint32_t n,
                              uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    keys[i] = pack_word(row_of(tokens, i, f), 0, f);
+    const uint8_t* row = row_of(tokens, i, f);
+    uint64_t x;
+    if (f.aligned8) {
+        asm("ld.global.nc.L2::64B.u64 %0, [%1];" : "=l"(x) : "l"(row));
+        x = msb_first(x, f.tb);
+    } else {
+        x = pack_word(row, 0, f);
+    }
+    keys[i] = x;
     vals[i] = i;
 }
 
@@ -240,6 +250,74 @@ __global__ void k_gather_rows_v2(const uint8_t* __restrict__ tokens, RowFmt f, i
     if (h == 0) head[p] = v.x;
 }
 
+// Rows into sorted order together with head and H, for rows of W words with
+// W / 2 dividing 32 (16-byte aligned raw rows and output).  A warp owns
+// kGatherSteps * (64 / W) consecutive sorted positions, 32 / (W / 2) rows per
+// step with two words per lane; all steps' loads are issued before any compare.
+// The previous row's words come from the lanes one row below (a shuffle) --
+// only the row before the warp's first one is loaded again -- and a row's
+// LCP with its predecessor is the minimum over its lanes of the first
+// difference in their two words.
+constexpr int kGatherSteps = 2;
+
+// Words 2h, 2h+1 of the row at sorted position p (zeros off the ends).
+__device__ __forceinline__ ulonglong2 gather_half_words(const uint8_t* __restrict__ tokens, const RowFmt& f,
+                                                        int64_t n, const int32_t* __restrict__ ids, int64_t p,
+                                                        int h) {
+    ulonglong2 v = make_ulonglong2(0ull, 0ull);
+    if (p >= 0 && p < n) {
+        const int32_t id = ids[p];
+        if ((uint64_t)id < (uint64_t)n) {
+            const ulonglong2 raw = __ldg(reinterpret_cast<const ulonglong2*>(row_of(tokens, id, f)) + h);
+            v.x = msb_first(raw.x, f.tb);
+            v.y = msb_first(raw.y, f.tb);
+        }
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(256) k_gather_rows_lcp(const uint8_t* __restrict__ tokens, RowFmt f, int64_t n,
+                                                         const int32_t* __restrict__ ids,
+                                                         uint64_t* __restrict__ rows, uint64_t* __restrict__ head,
+                                                         uint8_t* __restrict__ H) {
+    const int half = f.W >> 1;  // a power of two <= 32
+    const int lg = __ffs(half) - 1;
+    const int R = 32 >> lg;  // rows per step
+    const unsigned lane = lane_id();
+    const int rl = (int)(lane >> lg), h = (int)(lane & (half - 1));
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t p0 = warp * (int64_t)(R * kGatherSteps);
+    if (p0 >= n) return;  // warp-uniform
+    ulonglong2 v[kGatherSteps];
+#pragma unroll
+    for (int j = 0; j < kGatherSteps; ++j) v[j] = gather_half_words(tokens, f, n, ids, p0 + (int64_t)j * R + rl, h);
+    // the row before the first one, held where a step's last row would be
+    ulonglong2 last = rl == R - 1 ? gather_half_words(tokens, f, n, ids, p0 - 1, h) : make_ulonglong2(0ull, 0ull);
+    constexpr int kNone = 1 << 20;
+#pragma unroll
+    for (int j = 0; j < kGatherSteps; ++j) {
+        const ulonglong2 cur = v[j];
+        const uint64_t ux = __shfl_up_sync(0xffffffffu, cur.x, half);
+        const uint64_t uy = __shfl_up_sync(0xffffffffu, cur.y, half);
+        const uint64_t lx = __shfl_sync(0xffffffffu, last.x, (int)lane + 32 - half);
+        const uint64_t ly = __shfl_sync(0xffffffffu, last.y, (int)lane + 32 - half);
+        const uint64_t ax = rl > 0 ? ux : lx, ay = rl > 0 ? uy : ly;
+        const uint64_t x0 = ax ^ cur.x, x1 = ay ^ cur.y;
+        int l = x0 ? (2 * h) * f.tpw + __clzll((long long)x0) / f.bits
+                   : (x1 ? (2 * h + 1) * f.tpw + __clzll((long long)x1) / f.bits : kNone);
+        for (int o = 1; o < half; o <<= 1) l = min(l, __shfl_xor_sync(0xffffffffu, l, o));
+        const int64_t p = p0 + (int64_t)j * R + rl;
+        if (p < n) {
+            reinterpret_cast<ulonglong2*>(rows)[p * half + h] = cur;
+            if (h == 0) {
+                head[p] = cur.x;
+                H[p] = p == 0 ? (uint8_t)0 : (uint8_t)min(l, f.L);
+            }
+        }
+        last = cur;
+    }
+}
+
 // H[p] = LCP(rows[p-1], rows[p]), H[0] = 0.
 __global__ void k_adjacent_lcp(const uint64_t* __restrict__ rows, int64_t n, int W, int L, int tpw,
                                int bits, uint8_t* __restrict__ H) {
@@ -389,6 +467,99 @@ __device__ __forceinline__ void merge_k(const uint32_t* A, const uint32_t* B, ui
     for (int t = 0; t < per; ++t) {
         const bool takeA = (i < K) && (j >= K || A[i] <= B[j]);
         O[d0 + t] = takeA ? A[i++] : B[j++];
+    }
+}
+
+// The K = 32E smallest of two ascending lists a, b of K ids (lane l holds
+// entries lE .. lE+E-1 of each), ascending, into a: the minimum of a and b
+// reversed is a bitonic sequence holding the K smallest, which the bitonic
+// half-cleaners then sort, all in registers.
+template <int E>
+__device__ __forceinline__ void st_merge_regs(uint32_t (&a)[E], const uint32_t (&b)[E], unsigned lane) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) a[e] = min(a[e], __shfl_sync(0xffffffffu, b[E - 1 - e], 31 - (int)lane));
+#pragma unroll
+    for (int st = 16 * E; st >= 1; st >>= 1) {
+        if (st >= E) {
+            const int m = st / E;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const uint32_t o = __shfl_xor_sync(0xffffffffu, a[e], m);
+                a[e] = (lane & (unsigned)m) ? max(a[e], o) : min(a[e], o);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                if ((e & st) == 0) {
+                    const uint32_t lo = min(a[e], a[e + st]), hi = max(a[e], a[e + st]);
+                    a[e] = lo;
+                    a[e + st] = hi;
+                }
+            }
+        }
+    }
+}
+
+template <int E>
+__device__ __forceinline__ void st_load(const uint32_t* __restrict__ p, uint32_t (&v)[E]) {
+    if constexpr (E == 1) {
+        v[0] = __ldg(p);
+    } else if constexpr (E == 2) {
+        const uint2 x = __ldg(reinterpret_cast<const uint2*>(p));
+        v[0] = x.x;
+        v[1] = x.y;
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; e += 4) {
+            const uint4 x = __ldg(reinterpret_cast<const uint4*>(p + e));
+            v[e] = x.x;
+            v[e + 1] = x.y;
+            v[e + 2] = x.z;
+            v[e + 3] = x.w;
+        }
+    }
+}
+
+template <int E>
+__device__ __forceinline__ void st_store(uint32_t* __restrict__ p, const uint32_t (&v)[E]) {
+    if constexpr (E == 1) {
+        p[0] = v[0];
+    } else if constexpr (E == 2) {
+        *reinterpret_cast<uint2*>(p) = make_uint2(v[0], v[1]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; e += 4) *reinterpret_cast<uint4*>(p + e) = make_uint4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+    }
+}
+
+constexpr int kStPosPerWarp = 4;
+
+// Sparse-table level j for K = 32E: out[i] = K smallest of prev[i] and
+// prev[i + half], for i < valid.  A warp takes kStPosPerWarp start blocks and
+// issues all their loads before merging.
+template <int E>
+__global__ void __launch_bounds__(256) k_st_level_regs(const uint32_t* __restrict__ prev, int64_t prev_stride,
+                                                       int64_t half, int64_t valid, uint32_t* __restrict__ out) {
+    constexpr int K = 32 * E;
+    const unsigned lane = lane_id();
+    const int64_t i0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kStPosPerWarp;
+    if (i0 >= valid) return;  // warp-uniform
+    uint32_t a[kStPosPerWarp][E], b[kStPosPerWarp][E];
+#pragma unroll
+    for (int q = 0; q < kStPosPerWarp; ++q) {
+        const int64_t i = i0 + q;
+        if (i < valid) {
+            st_load<E>(prev + i * prev_stride + lane * E, a[q]);
+            st_load<E>(prev + (i + half) * prev_stride + lane * E, b[q]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) a[q][e] = b[q][e] = kInf;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kStPosPerWarp; ++q) {
+        st_merge_regs<E>(a[q], b[q], lane);
+        if (i0 + q < valid) st_store<E>(out + (i0 + q) * K + lane * E, a[q]);
     }
 }
 
@@ -599,6 +770,13 @@ int gather_rows_and_lcp(const void* tokens, const RowFmt& f, int64_t N, const in
     const bool vec = f.aligned8 && (W % 2 == 0) && (f.row_bytes % 16 == 0) &&
                      ((reinterpret_cast<uintptr_t>(tokens) & 15) == 0) &&
                      ((reinterpret_cast<uintptr_t>(b.rows) & 15) == 0);
+    const int half = W / 2;
+    if (vec && half <= 32 && (32 % half) == 0) {
+        const int64_t warps = (N + (int64_t)(32 / half) * kGatherSteps - 1) / ((int64_t)(32 / half) * kGatherSteps);
+        LCP_TIMED_LAUNCH(k_gather_rows_lcp, blocks_for(warps * 32, 256), 256, 0, s,
+                         reinterpret_cast<const uint8_t*>(tokens), f, N, ids, b.rows, b.head, b.H);
+        return LCP_OK;
+    }
     if (vec) {
         LCP_TIMED_LAUNCH(k_gather_rows_v2, blocks_for(N * (W / 2), 256), 256, 0, s,
                    reinterpret_cast<const uint8_t*>(tokens), f, N, ids, b.rows, b.head);
@@ -664,6 +842,22 @@ int build_aux(lcp_index_s* x, cudaStream_t s, bool merged) {
     const int K = x->K;
     const int gmax = K <= 32 ? kStMaxGroup : (K <= 64 ? 2 : 1);
     const int64_t lstride = x->nblk_cap * K;
+    const int E = K / 32;
+    if (K % 32 == 0 && (E == 1 || E == 2 || E == 4)) {  // K = 96 takes the shared-memory merge below
+        // one level per launch, merged in registers
+        for (int j = 1; j <= x->st_levels_cap && (1ll << j) <= nblk; ++j) {
+            const int64_t half = 1ll << (j - 1);
+            const int64_t valid = nblk - (1ll << j) + 1;
+            const uint32_t* prev = j == 1 ? x->sblk : x->st + (int64_t)(j - 2) * lstride;
+            const int64_t pstride = j == 1 ? kBlk : K;
+            uint32_t* out = x->st + (int64_t)(j - 1) * lstride;
+            const unsigned grid = blocks_for((valid + kStPosPerWarp - 1) / kStPosPerWarp * 32, 256);
+            if (E == 1) LCP_TIMED_LAUNCH(k_st_level_regs<1>, grid, 256, 0, s, prev, pstride, half, valid, out);
+            else if (E == 2) LCP_TIMED_LAUNCH(k_st_level_regs<2>, grid, 256, 0, s, prev, pstride, half, valid, out);
+            else LCP_TIMED_LAUNCH(k_st_level_regs<4>, grid, 256, 0, s, prev, pstride, half, valid, out);
+        }
+        return build_tie_lists(x, s);
+    }
     for (int j = 1; j <= x->st_levels_cap && (1ll << j) <= nblk;) {
         int g = 1;
         while (g < gmax && j + g <= x->st_levels_cap && (1ll << (j + g)) <= nblk) ++g;

@@ -105,6 +105,7 @@ CASES = [
     (5000, 33, 2, 4, 100),
     (20000, 8, 1, 2, 128),   # tiny alphabet: enormous tie levels
     (3000, 255, 1, 2, 17),   # L = 255, uint8
+    (3000, 10, 1, 3, 80),    # K = 96: sparse table merged in shared memory
     (700, 255, 2, 3, 40),    # L = 255, uint16 (64 packed words)
 ]
 
