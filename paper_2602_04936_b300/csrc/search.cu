@@ -327,9 +327,9 @@ __device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, WA& S, int64_
             const int b = __shfl_sync(0xffffffffu, v1, i & 31);
             return i < 32 ? a : b;
         };
-        auto cnt_ge = [&](int v) {
-            return __popc(__ballot_sync(0xffffffffu, vL0 >= v)) + __popc(__ballot_sync(0xffffffffu, vL1 >= v)) +
-                   __popc(__ballot_sync(0xffffffffu, vR0 >= v)) + __popc(__ballot_sync(0xffffffffu, vR1 >= v));
+        auto cnt_ge = [&](int v) {  // absent items hold -1
+            const unsigned c = (unsigned)(vL0 >= v) + (unsigned)(vL1 >= v) + (unsigned)(vR0 >= v) + (unsigned)(vR1 >= v);
+            return (int)__reduce_add_sync(0xffffffffu, c);
         };
         const int bL = nL < availL ? at(vL0, vL1, nL - 1) : -1;
         const int bR = nR < availR ? at(vR0, vR1, nR - 1) : -1;
@@ -338,8 +338,10 @@ __device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, WA& S, int64_
         if (!ok) ok = cnt_ge(F) >= k;  // loaded items with LCP >= F (every loaded item of F's side qualifies)
         if (ok) {
             if (nL + nR >= k) {
-                // largest v with cnt_ge(v) >= k, v in [0, max loaded LCP]
-                int lo = 0, hi = (lL > lR ? lL : lR) + 1;
+                // largest v with cnt_ge(v) >= k: at least F (when F >= 0,
+                // cnt_ge(F) >= k was just checked) and at most the largest
+                // loaded LCP, max(lL, lR)
+                int lo = F > 0 ? F : 0, hi = (lL > lR ? lL : lR) + 1;
                 while (hi - lo > 1) {
                     const int mid = (lo + hi) >> 1;
                     if (cnt_ge(mid) >= k) lo = mid;
