@@ -532,36 +532,74 @@ __device__ __forceinline__ void st_store(uint32_t* __restrict__ p, const uint32_
     }
 }
 
-constexpr int kStPosPerWarp = 4;
-
-// Sparse-table level j for K = 32E: out[i] = K smallest of prev[i] and
-// prev[i + half], for i < valid.  A warp takes kStPosPerWarp start blocks and
-// issues all their loads before merging.
-template <int E>
-__global__ void __launch_bounds__(256) k_st_level_regs(const uint32_t* __restrict__ prev, int64_t prev_stride,
-                                                       int64_t half, int64_t valid, uint32_t* __restrict__ out) {
-    constexpr int K = 32 * E;
+// Sparse-table levels j .. j+g-1 (g <= G) for K = 32E in one launch, merged
+// in registers.  Level j+r at i is the K smallest of level j-1 at
+// i + m*half for m < 2^(r+1): a warp loads those 2^G lists of its start
+// block and merges them pairwise up the tree, writing the tree's left spine
+// (levels j .. j+g-1 at i).  Spines of other start blocks are recomputed,
+// not shared: 2^G - 1 merges for g levels and g - 1 fewer launches.  P start
+// blocks per warp, all loads issued before any merge.
+template <int E, int G, int P>
+__global__ void __launch_bounds__(256) k_st_levels_regs(const uint32_t* __restrict__ prev, int64_t prev_stride,
+                                                        int64_t prev_valid, int64_t half, int g,
+                                                        int64_t level_stride, int64_t valid0, int64_t valid1,
+                                                        int64_t valid2, uint32_t* __restrict__ out0) {
+    constexpr int K = 32 * E, M = 1 << G;
     const unsigned lane = lane_id();
-    const int64_t i0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kStPosPerWarp;
-    if (i0 >= valid) return;  // warp-uniform
-    uint32_t a[kStPosPerWarp][E], b[kStPosPerWarp][E];
+    const int64_t i0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * P;
+    if (i0 >= valid0) return;  // warp-uniform
+    const int64_t valid[3] = {valid0, valid1, valid2};
+    uint32_t v[P][M][E];
 #pragma unroll
-    for (int q = 0; q < kStPosPerWarp; ++q) {
+    for (int q = 0; q < P; ++q) {
         const int64_t i = i0 + q;
-        if (i < valid) {
-            st_load<E>(prev + i * prev_stride + lane * E, a[q]);
-            st_load<E>(prev + (i + half) * prev_stride + lane * E, b[q]);
-        } else {
 #pragma unroll
-            for (int e = 0; e < E; ++e) a[q][e] = b[q][e] = kInf;
+        for (int m = 0; m < M; ++m) {
+            const int64_t pos = i + m * half;
+            // entries past the previous level only feed spine levels that
+            // are not stored
+            if (i < valid0 && m < (2 << (g - 1)) && pos < prev_valid) {
+                st_load<E>(prev + pos * prev_stride + lane * E, v[q][m]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) v[q][m][e] = kInf;
+            }
         }
     }
 #pragma unroll
-    for (int q = 0; q < kStPosPerWarp; ++q) {
-        st_merge_regs<E>(a[q], b[q], lane);
-        if (i0 + q < valid) st_store<E>(out + (i0 + q) * K + lane * E, a[q]);
+    for (int q = 0; q < P; ++q) {
+        const int64_t i = i0 + q;
+#pragma unroll
+        for (int r = 0; r < G; ++r) {
+#pragma unroll
+            for (int m = 0; m < (M >> (r + 1)); ++m) {
+                uint32_t t[E];
+#pragma unroll
+                for (int e = 0; e < E; ++e) t[e] = v[q][2 * m][e];
+                st_merge_regs<E>(t, v[q][2 * m + 1], lane);
+#pragma unroll
+                for (int e = 0; e < E; ++e) v[q][m][e] = t[e];
+            }
+            if (r < g && i < valid[r]) st_store<E>(out0 + r * level_stride + i * K + lane * E, v[q][0]);
+        }
     }
 }
+
+// Levels per launch and start blocks per warp of the register merge, by E.
+template <int E>
+struct StRegsShape;
+template <>
+struct StRegsShape<1> {
+    static constexpr int G = 3, P = 1;
+};
+template <>
+struct StRegsShape<2> {
+    static constexpr int G = 2, P = 2;
+};
+template <>
+struct StRegsShape<4> {
+    static constexpr int G = 2, P = 2;
+};
 
 constexpr int kStMaxGroup = 3;  // sparse-table levels per launch (K <= 32)
 
@@ -844,17 +882,29 @@ int build_aux(lcp_index_s* x, cudaStream_t s, bool merged) {
     const int64_t lstride = x->nblk_cap * K;
     const int E = K / 32;
     if (K % 32 == 0 && (E == 1 || E == 2 || E == 4)) {  // K = 96 takes the shared-memory merge below
-        // one level per launch, merged in registers
-        for (int j = 1; j <= x->st_levels_cap && (1ll << j) <= nblk; ++j) {
+        const int G = E == 1 ? StRegsShape<1>::G : (E == 2 ? StRegsShape<2>::G : StRegsShape<4>::G);
+        const int P = E == 1 ? StRegsShape<1>::P : (E == 2 ? StRegsShape<2>::P : StRegsShape<4>::P);
+        for (int j = 1; j <= x->st_levels_cap && (1ll << j) <= nblk;) {
+            int g = 1;
+            while (g < G && j + g <= x->st_levels_cap && (1ll << (j + g)) <= nblk) ++g;
             const int64_t half = 1ll << (j - 1);
-            const int64_t valid = nblk - (1ll << j) + 1;
+            int64_t valid[3] = {0, 0, 0};
+            for (int r = 0; r < g; ++r) valid[r] = nblk - (1ll << (j + r)) + 1;
+            const int64_t prev_valid = nblk - half + 1;  // level j-1 (level 0: the blocks)
             const uint32_t* prev = j == 1 ? x->sblk : x->st + (int64_t)(j - 2) * lstride;
             const int64_t pstride = j == 1 ? kBlk : K;
             uint32_t* out = x->st + (int64_t)(j - 1) * lstride;
-            const unsigned grid = blocks_for((valid + kStPosPerWarp - 1) / kStPosPerWarp * 32, 256);
-            if (E == 1) LCP_TIMED_LAUNCH(k_st_level_regs<1>, grid, 256, 0, s, prev, pstride, half, valid, out);
-            else if (E == 2) LCP_TIMED_LAUNCH(k_st_level_regs<2>, grid, 256, 0, s, prev, pstride, half, valid, out);
-            else LCP_TIMED_LAUNCH(k_st_level_regs<4>, grid, 256, 0, s, prev, pstride, half, valid, out);
+            const unsigned grid = blocks_for((valid[0] + P - 1) / P * 32, 256);
+            if (E == 1)
+                LCP_TIMED_LAUNCH((k_st_levels_regs<1, StRegsShape<1>::G, StRegsShape<1>::P>), grid, 256, 0, s, prev,
+                                 pstride, prev_valid, half, g, lstride, valid[0], valid[1], valid[2], out);
+            else if (E == 2)
+                LCP_TIMED_LAUNCH((k_st_levels_regs<2, StRegsShape<2>::G, StRegsShape<2>::P>), grid, 256, 0, s, prev,
+                                 pstride, prev_valid, half, g, lstride, valid[0], valid[1], valid[2], out);
+            else
+                LCP_TIMED_LAUNCH((k_st_levels_regs<4, StRegsShape<4>::G, StRegsShape<4>::P>), grid, 256, 0, s, prev,
+                                 pstride, prev_valid, half, g, lstride, valid[0], valid[1], valid[2], out);
+            j += g;
         }
         return build_tie_lists(x, s);
     }
