@@ -236,6 +236,7 @@ static int graph_build(lcp_index_s* x, const void* d_tokens, int64_t N, cudaStre
     *huge = 0;
     lcpk::RowFmt f = lcpk::make_fmt(x->tb, x->L, d_tokens);
     const lcp_index_s saved = *x;
+    (void)side_stream();  // created outside the capture
     LCP_CUDA_TRY(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
     int rc = build_sorted_ids(d_tokens, f, N, x->buf[0].ids, x->status, g->cap, huge, g->scratch);
     if (rc == LCP_OK && cudaEventRecordWithFlags(g->chk, g->cap, cudaEventRecordExternal) != cudaSuccess)

@@ -832,13 +832,94 @@ int adjacent_lcp(const uint64_t* rows, int64_t N, int W, int L, int tpw, int bit
     return LCP_OK;
 }
 
+SideStream* side_stream() {
+    static thread_local SideStream ss[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    SideStream& x = ss[dev];
+    if (!x.s2) {
+        if (cudaStreamCreateWithFlags(&x.s2, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            x = SideStream();
+            return nullptr;
+        }
+    }
+    return &x;
+}
+
+// Sparse table of the K smallest ids over runs of 2^j blocks (reads the
+// sorted blocks).
+static int build_sparse_table(lcp_index_s* x, int64_t nblk, cudaStream_t s) {
+    const int K = x->K;
+    const int64_t lstride = x->nblk_cap * K;
+    const int E = K / 32;
+    if (K % 32 == 0 && (E == 1 || E == 2 || E == 4)) {  // K = 96 takes the shared-memory merge below
+        const int G = E == 1 ? StRegsShape<1>::G : (E == 2 ? StRegsShape<2>::G : StRegsShape<4>::G);
+        const int P = E == 1 ? StRegsShape<1>::P : (E == 2 ? StRegsShape<2>::P : StRegsShape<4>::P);
+        for (int j = 1; j <= x->st_levels_cap && (1ll << j) <= nblk;) {
+            int g = 1;
+            while (g < G && j + g <= x->st_levels_cap && (1ll << (j + g)) <= nblk) ++g;
+            const int64_t half = 1ll << (j - 1);
+            int64_t valid[3] = {0, 0, 0};
+            for (int r = 0; r < g; ++r) valid[r] = nblk - (1ll << (j + r)) + 1;
+            const int64_t prev_valid = nblk - half + 1;  // level j-1 (level 0: the blocks)
+            const uint32_t* prev = j == 1 ? x->sblk : x->st + (int64_t)(j - 2) * lstride;
+            const int64_t pstride = j == 1 ? kBlk : K;
+            uint32_t* out = x->st + (int64_t)(j - 1) * lstride;
+            const unsigned grid = blocks_for((valid[0] + P - 1) / P * 32, 256);
+            if (E == 1)
+                LCP_TIMED_LAUNCH((k_st_levels_regs<1, StRegsShape<1>::G, StRegsShape<1>::P>), grid, 256, 0, s, prev,
+                                 pstride, prev_valid, half, g, lstride, valid[0], valid[1], valid[2], out);
+            else if (E == 2)
+                LCP_TIMED_LAUNCH((k_st_levels_regs<2, StRegsShape<2>::G, StRegsShape<2>::P>), grid, 256, 0, s, prev,
+                                 pstride, prev_valid, half, g, lstride, valid[0], valid[1], valid[2], out);
+            else
+                LCP_TIMED_LAUNCH((k_st_levels_regs<4, StRegsShape<4>::G, StRegsShape<4>::P>), grid, 256, 0, s, prev,
+                                 pstride, prev_valid, half, g, lstride, valid[0], valid[1], valid[2], out);
+            j += g;
+        }
+        return LCP_OK;
+    }
+    // g levels per launch (recomputation grows as 2^g, so g shrinks as K grows)
+    const int gmax = K <= 32 ? kStMaxGroup : (K <= 64 ? 2 : 1);
+    for (int j = 1; j <= x->st_levels_cap && (1ll << j) <= nblk;) {
+        int g = 1;
+        while (g < gmax && j + g <= x->st_levels_cap && (1ll << (j + g)) <= nblk) ++g;
+        const int64_t half = 1ll << (j - 1);
+        int64_t valid[3] = {0, 0, 0};
+        for (int r = 0; r < g; ++r) valid[r] = nblk - (1ll << (j + r)) + 1;
+        const uint32_t* prev = j == 1 ? x->sblk : x->st + (int64_t)(j - 2) * lstride;
+        const int64_t pstride = j == 1 ? kBlk : K;
+        uint32_t* out = x->st + (int64_t)(j - 1) * lstride;
+        LCP_TIMED_LAUNCH(k_st_levels, blocks_for(valid[0] * 32, 256), 256, (size_t)8 * (g > 1 ? 6 : 3) * K * sizeof(uint32_t), s,
+                   prev, pstride, half, g, K, lstride, valid[0], valid[1], valid[2], out);
+        j += g;
+    }
+    return LCP_OK;
+}
+
+// Two branches after the rows, ids, head and H exist:
+//   side: pos and the buckets, then (after the sorted blocks) the sparse table
+//   main: the min tree and sorted blocks, then the heavy trie nodes
+// joined before the nodes' lists, which read the sparse table, pos and the
+// buckets.
 int build_aux(lcp_index_s* x, cudaStream_t s, bool merged) {
     const int64_t N = x->N;
     lcp_buffers& b = x->buf[x->cur];
     if (N <= 0) return LCP_OK;
+    SideStream* ss = side_stream();
+    cudaStream_t s2 = ss ? ss->s2 : s;  // without a side stream, one stream
+    auto fork = [&]() -> cudaError_t {
+        if (s2 == s) return cudaSuccess;
+        cudaError_t e = cudaEventRecord(ss->fork, s);
+        return e == cudaSuccess ? cudaStreamWaitEvent(s2, ss->fork, 0) : e;
+    };
+    LCP_CUDA_TRY(fork());
     if (!merged) {  // an insert's merge pass already wrote pos and the buckets
-        LCP_TIMED_LAUNCH(k_inverse, blocks_for(N, 256), 256, 0, s, b.ids, N, x->pos);
-        LCP_TIMED_LAUNCH(k_buckets, blocks_for((1ll << x->bits) + 1, 256), 256, 0, s, b.head, N, x->bits, x->bkt);
+        LCP_TIMED_LAUNCH(k_inverse, blocks_for(N, 256), 256, 0, s2, b.ids, N, x->pos);
+        LCP_TIMED_LAUNCH(k_buckets, blocks_for((1ll << x->bits) + 1, 256), 256, 0, s2, b.head, N, x->bits, x->bkt);
     }
     // min tree over H: level j+1 = minima of 32 consecutive level-j entries,
     // built while a level has more than 32 entries
@@ -872,56 +953,18 @@ int build_aux(lcp_index_s* x, cudaStream_t s, bool merged) {
     a.sblk = x->sblk;
     a.soff = x->soff;
     LCP_TIMED_LAUNCH(k_aux_tree_blocks, a.tree_ctas + blocks_for(nblk, kAuxThreads / 32), kAuxThreads, 0, s, a);
+    LCP_CUDA_TRY(fork());
+    int rc = build_sparse_table(x, nblk, s2);
     for (int j = 4; j <= lev; ++j)  // only past 2^20 rows
         LCP_TIMED_LAUNCH(k_min32, blocks_for(x->hlen[j], 256), 256, 0, s, x->hmin + x->hoff[j - 1], x->hlen[j - 1],
                    x->hmin + x->hoff[j], x->hlen[j]);
-    // sparse table of K smallest ids over runs of 2^j blocks, g levels per
-    // launch (recomputation grows as 2^g, so g shrinks as K grows)
-    const int K = x->K;
-    const int gmax = K <= 32 ? kStMaxGroup : (K <= 64 ? 2 : 1);
-    const int64_t lstride = x->nblk_cap * K;
-    const int E = K / 32;
-    if (K % 32 == 0 && (E == 1 || E == 2 || E == 4)) {  // K = 96 takes the shared-memory merge below
-        const int G = E == 1 ? StRegsShape<1>::G : (E == 2 ? StRegsShape<2>::G : StRegsShape<4>::G);
-        const int P = E == 1 ? StRegsShape<1>::P : (E == 2 ? StRegsShape<2>::P : StRegsShape<4>::P);
-        for (int j = 1; j <= x->st_levels_cap && (1ll << j) <= nblk;) {
-            int g = 1;
-            while (g < G && j + g <= x->st_levels_cap && (1ll << (j + g)) <= nblk) ++g;
-            const int64_t half = 1ll << (j - 1);
-            int64_t valid[3] = {0, 0, 0};
-            for (int r = 0; r < g; ++r) valid[r] = nblk - (1ll << (j + r)) + 1;
-            const int64_t prev_valid = nblk - half + 1;  // level j-1 (level 0: the blocks)
-            const uint32_t* prev = j == 1 ? x->sblk : x->st + (int64_t)(j - 2) * lstride;
-            const int64_t pstride = j == 1 ? kBlk : K;
-            uint32_t* out = x->st + (int64_t)(j - 1) * lstride;
-            const unsigned grid = blocks_for((valid[0] + P - 1) / P * 32, 256);
-            if (E == 1)
-                LCP_TIMED_LAUNCH((k_st_levels_regs<1, StRegsShape<1>::G, StRegsShape<1>::P>), grid, 256, 0, s, prev,
-                                 pstride, prev_valid, half, g, lstride, valid[0], valid[1], valid[2], out);
-            else if (E == 2)
-                LCP_TIMED_LAUNCH((k_st_levels_regs<2, StRegsShape<2>::G, StRegsShape<2>::P>), grid, 256, 0, s, prev,
-                                 pstride, prev_valid, half, g, lstride, valid[0], valid[1], valid[2], out);
-            else
-                LCP_TIMED_LAUNCH((k_st_levels_regs<4, StRegsShape<4>::G, StRegsShape<4>::P>), grid, 256, 0, s, prev,
-                                 pstride, prev_valid, half, g, lstride, valid[0], valid[1], valid[2], out);
-            j += g;
-        }
-        return build_tie_lists(x, s);
+    if (rc == LCP_OK) rc = build_tie_lists_nodes(x, s);
+    if (s2 != s) {  // join (also on an error, so that a capture stays well-formed)
+        LCP_CUDA_TRY(cudaEventRecord(ss->join, s2));
+        LCP_CUDA_TRY(cudaStreamWaitEvent(s, ss->join, 0));
     }
-    for (int j = 1; j <= x->st_levels_cap && (1ll << j) <= nblk;) {
-        int g = 1;
-        while (g < gmax && j + g <= x->st_levels_cap && (1ll << (j + g)) <= nblk) ++g;
-        const int64_t half = 1ll << (j - 1);
-        int64_t valid[3] = {0, 0, 0};
-        for (int r = 0; r < g; ++r) valid[r] = nblk - (1ll << (j + r)) + 1;
-        const uint32_t* prev = j == 1 ? x->sblk : x->st + (int64_t)(j - 2) * lstride;
-        const int64_t pstride = j == 1 ? kBlk : K;
-        uint32_t* out = x->st + (int64_t)(j - 1) * lstride;
-        LCP_TIMED_LAUNCH(k_st_levels, blocks_for(valid[0] * 32, 256), 256, (size_t)8 * (g > 1 ? 6 : 3) * K * sizeof(uint32_t), s,
-                   prev, pstride, half, g, K, lstride, valid[0], valid[1], valid[2], out);
-        j += g;
-    }
-    return build_tie_lists(x, s);
+    if (rc == LCP_OK) rc = build_tie_lists_fill(x, s);
+    return rc;
 }
 
 DevIndex dev_view(const lcp_index_s* x) {

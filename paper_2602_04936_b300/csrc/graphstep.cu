@@ -54,6 +54,7 @@ int lcp_step_run(lcp_step_t st, const void* d_insert, const void* d_queries, int
     if (st->n > 0 && (x->N + st->n > x->cap || !x->buf[1].rows)) return LCP_ERR_CAPACITY;
     const lcp_index_s saved = *x;  // host-side state, restored if capture fails
     const int64_t before = lcp_launch_count();
+    (void)lcph::side_stream();  // created outside the capture
     LCP_CUDA_TRY(cudaStreamBeginCapture(st->cap, cudaStreamCaptureModeThreadLocal));
     int rc = st->n > 0 ? lcph::insert_device(x, d_insert, st->n, st->cap) : LCP_OK;
     if (rc == LCP_OK && st->Q > 0)

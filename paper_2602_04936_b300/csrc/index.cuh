@@ -158,8 +158,22 @@ void note_use(lcp_index_s* x, cudaStream_t s);
 // table, tie lists) from the current buffer set; `merged`: an insert's merge
 // pass already wrote pos and the buckets.
 int build_aux(lcp_index_s* x, cudaStream_t s, bool merged);
-// heavy-node tie lists (needs the min tree, sorted blocks and sparse table).
-int build_tie_lists(lcp_index_s* x, cudaStream_t s);
+// Heavy-node tie lists in two parts: the nodes, their keys and numbering
+// (needs the min tree), then their lists and the lookup tables (needs the
+// sparse table, pos and the buckets too).
+int build_tie_lists_nodes(lcp_index_s* x, cudaStream_t s);
+int build_tie_lists_fill(lcp_index_s* x, cudaStream_t s);
+
+// A second stream of this thread for the current device, with a fork and a
+// join event: independent branches of the build run on it, ordered against
+// the caller's stream by the events only -- concurrent in direct calls,
+// parallel branches when captured into a graph.  Created on first use (so
+// call it once before any stream capture); nullptr if that failed.
+struct SideStream {
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+SideStream* side_stream();
 
 // loc_scratch: caller-owned buffer of search_scratch_bytes(Q) bytes for the
 // per-query position records, or nullptr to use stream-ordered scratch.

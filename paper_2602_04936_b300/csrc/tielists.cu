@@ -187,7 +187,7 @@ __global__ void k_remap_tbl(int32_t* __restrict__ tbl, int64_t n, const int32_t*
 namespace lcph {
 using namespace lcpk;
 
-int build_tie_lists(lcp_index_s* x, cudaStream_t s) {
+int build_tie_lists_nodes(lcp_index_s* x, cudaStream_t s) {
     const int64_t N = x->N;
     if (N <= 0 || !x->tbl) return LCP_OK;
     const int64_t nsamp = (N + kBlk - 1) / kBlk;
@@ -202,6 +202,16 @@ int build_tie_lists(lcp_index_s* x, cudaStream_t s) {
     LCP_TIMED_LAUNCH(k_flag_scan_sums, 1, 1024, 0, s, x->tl_sums, nb, x->tl_total);
     LCP_TIMED_LAUNCH(k_flag_assign, (unsigned)nb, 256, 0, s, x->slot_flag, nslots, x->tl_sums, x->slot_lo,
                x->slot_hi, x->nlists_cap, x->slot_list, x->tl_lo, x->tl_hi);
+    return LCP_OK;
+}
+
+int build_tie_lists_fill(lcp_index_s* x, cudaStream_t s) {
+    const int64_t N = x->N;
+    if (N <= 0 || !x->tbl) return LCP_OK;
+    const int64_t nsamp = (N + kBlk - 1) / kBlk;
+    const int L1 = x->L + 1;
+    const int64_t nslots = nsamp * L1;
+    DevIndex ix = dev_view(x);
     LCP_TIMED_LAUNCH(k_node_lists, (unsigned)((x->nlists_cap + kTlWarps - 1) / kTlWarps), kTlWarps * 32, 0, s,
                ix, x->tl_total, x->nlists_cap, x->tl_lo, x->tl_hi, x->tlists, x->tlpos);
     LCP_TIMED_LAUNCH(k_remap_tbl, (unsigned)((nslots + 255) / 256), 256, 0, s, x->tbl, nslots, x->slot_list);
