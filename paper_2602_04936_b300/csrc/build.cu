@@ -33,9 +33,13 @@ __global__ void k_keys_word0(const uint8_t* __restrict__ tokens, RowFmt f, uint3
     vals[i] = i;
 }
 
-__global__ void k_eq_sorted(const uint64_t* __restrict__ keys, uint32_t n, uint8_t* __restrict__ eq) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+// The sorted ids, and eq[i] = 1 where the row at sorted position i has the
+// same word 0 as the row before it.
+__global__ void k_ids_eq(const uint32_t* __restrict__ vs, const uint64_t* __restrict__ keys, uint32_t n,
+                         int32_t* __restrict__ ids, uint8_t* __restrict__ eq) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    ids[i] = (int32_t)vs[i];
     eq[i] = (i > 0 && keys[i] == keys[i - 1]) ? 1 : 0;
 }
 
@@ -94,19 +98,6 @@ __global__ void k_remap_active(const uint32_t* __restrict__ act, const uint32_t*
     act2[j] = act[idx[j]];
 }
 
-// Tie groups after round 0: gstart[g] = first index (in the active list) of
-// group g, gstart[G] = m.
-// counts[0] = tied rows m, counts[1] = groups G (written on the device by the
-// tie compaction; grid-stride, so the host never needs them).
-__global__ void k_group_starts(const uint32_t* __restrict__ grp, const uint32_t* __restrict__ counts,
-                               uint32_t* __restrict__ gstart) {
-    const uint32_t m = counts[0], G = counts[1];
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-        if (i == 0 || grp[i] != grp[i - 1]) gstart[grp[i]] = i;
-        if (i == 0) gstart[G] = m;
-    }
-}
-
 // Lexicographic comparison of two raw rows from word w0 on, then by id.
 __device__ __forceinline__ bool row_less(const uint8_t* __restrict__ tokens, const RowFmt& f, int w0,
                                          int32_t a, int32_t b) {
@@ -127,40 +118,63 @@ __device__ __forceinline__ bool tie_less(const uint8_t* __restrict__ tokens, con
     return row_less(tokens, f, 2, a, b);  // rare: equal on word 1 too
 }
 
-// Groups of at most 32 rows: one warp loads each row's word 1 once, ranks the
-// rows with shuffles, and writes them back in order.  Larger groups are listed
-// for k_group_sort_mid (<= 512 rows) or counted for the LSD rounds.
-__global__ void __launch_bounds__(128) k_group_sort_small(const uint8_t* __restrict__ tokens, RowFmt f,
-                                                          const uint32_t* __restrict__ gstart,
-                                                          const uint32_t* __restrict__ counts,
-                                                          const uint32_t* __restrict__ act,
-                                                          int32_t* __restrict__ ids,
-                                                          uint32_t* __restrict__ big_list,
-                                                          uint32_t* __restrict__ big_count,
-                                                          uint32_t* __restrict__ huge_count) {
-    const uint32_t G = counts[1];
+// Rows tied on word 0, found straight from eq: a warp takes 32 consecutive
+// sorted positions and handles each tie group that starts among them.  A
+// group of at most 32 rows is ranked in registers (word 1 loaded once per row,
+// shuffles; later words and then ids only for rows tied on word 1) and
+// written back in order; groups of 33..512 rows are listed for
+// k_group_sort_mid; the rows of larger groups are counted for the exact
+// refinement.
+__global__ void __launch_bounds__(256) k_group_scan_sort(const uint8_t* __restrict__ tokens, RowFmt f,
+                                                         const uint8_t* __restrict__ eq, uint32_t n,
+                                                         int32_t* __restrict__ ids,
+                                                         uint32_t* __restrict__ big_start,
+                                                         uint32_t* __restrict__ big_len,
+                                                         uint32_t* __restrict__ big_count,
+                                                         uint32_t* __restrict__ huge_count) {
     const unsigned lane = lane_id();
-    const uint32_t nwarps = gridDim.x * 4;
-    for (uint32_t g = blockIdx.x * 4 + (threadIdx.x >> 5); g < G; g += nwarps) {  // warp per group
-        const uint32_t gs = gstart[g], n = gstart[g + 1] - gs;
-        if (n > 32) {
-            if (lane == 0) {
-                if (n <= 512) big_list[atomicAdd(big_count, 1u)] = g;
-                else atomicAdd(huge_count, n);
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); (uint64_t)c * 32 < n; c += nwarps) {
+        const uint32_t p = c * 32 + lane;
+        const bool first = p < n && !eq[p] && p + 1 < n && eq[p + 1];  // first row of a tie group
+        unsigned starts = __ballot_sync(0xffffffffu, first);
+        while (starts) {
+            const uint32_t gs = c * 32 + (uint32_t)(__ffs(starts) - 1);
+            starts &= starts - 1;
+            uint32_t len = 1;  // rows gs+1, gs+2, ... while eq holds
+            for (uint32_t q = gs + 1;; q += 32) {
+                const uint32_t t = q + lane;
+                const unsigned brk = __ballot_sync(0xffffffffu, !(t < n && eq[t]));
+                if (brk) {
+                    len += (uint32_t)(__ffs(brk) - 1);
+                    break;
+                }
+                len += 32;
             }
-            continue;
+            if (len > 32) {
+                if (lane == 0) {
+                    if (len <= 512) {
+                        const uint32_t b = atomicAdd(big_count, 1u);
+                        big_start[b] = gs;
+                        big_len[b] = len;
+                    } else {
+                        atomicAdd(huge_count, len);
+                    }
+                }
+                continue;
+            }
+            const int32_t my = lane < len ? ids[gs + lane] : 0;
+            const uint64_t key = lane < len ? pack_word(row_of(tokens, my, f), 1, f) : 0ull;
+            uint32_t rank = 0;
+            for (uint32_t j = 0; j < len; ++j) {
+                const int32_t oid = __shfl_sync(0xffffffffu, my, j);
+                const uint64_t ok = __shfl_sync(0xffffffffu, key, j);
+                if (lane < len && j != lane && tie_less(tokens, f, ok, oid, key, my)) ++rank;
+            }
+            __syncwarp();
+            if (lane < len) ids[gs + rank] = my;
+            __syncwarp();
         }
-        const int32_t my = lane < n ? ids[act[gs + lane]] : 0;
-        const uint64_t key = lane < n ? pack_word(row_of(tokens, my, f), 1, f) : 0ull;
-        uint32_t rank = 0;
-        for (uint32_t j = 0; j < n; ++j) {
-            const int32_t oid = __shfl_sync(0xffffffffu, my, j);
-            const uint64_t ok = __shfl_sync(0xffffffffu, key, j);
-            if (lane < n && j != lane && tie_less(tokens, f, ok, oid, key, my)) ++rank;
-        }
-        __syncwarp();
-        if (lane < n) ids[act[gs + rank]] = my;
-        __syncwarp();
     }
 }
 
@@ -169,22 +183,20 @@ __global__ void __launch_bounds__(128) k_group_sort_small(const uint8_t* __restr
 // a branch-free pass; only a row whose word 1 is shared with another row of
 // the group (rare) compares the later words of those rows, then the ids.
 __global__ void __launch_bounds__(512) k_group_sort_mid(const uint8_t* __restrict__ tokens, RowFmt f,
-                                                        const uint32_t* __restrict__ gstart,
-                                                        const uint32_t* __restrict__ act,
                                                         int32_t* __restrict__ ids,
-                                                        const uint32_t* __restrict__ big_list,
+                                                        const uint32_t* __restrict__ big_start,
+                                                        const uint32_t* __restrict__ big_len,
                                                         const uint32_t* __restrict__ big_count) {
     __shared__ int32_t sid[512];
     __shared__ uint64_t skey[512];
     const uint32_t nbig = *big_count;
     const uint32_t i = threadIdx.x;
     for (uint32_t b = blockIdx.x; b < nbig; b += gridDim.x) {  // CTA per group
-        const uint32_t g = big_list[b];
-        const uint32_t gs = gstart[g], n = gstart[g + 1] - gs;
+        const uint32_t gs = big_start[b], n = big_len[b];
         int32_t my = 0;
         uint64_t ki = 0;
         if (i < n) {
-            my = ids[act[gs + i]];
+            my = ids[gs + i];
             ki = pack_word(row_of(tokens, my, f), 1, f);
             sid[i] = my;
             skey[i] = ki;
@@ -204,14 +216,9 @@ __global__ void __launch_bounds__(512) k_group_sort_mid(const uint8_t* __restric
                     if (j != i && skey[j] == ki && row_less(tokens, f, 2, sid[j], my)) ++rank;
         }
         __syncthreads();
-        if (i < n) ids[act[gs + rank]] = my;
+        if (i < n) ids[gs + rank] = my;
         __syncthreads();  // the shared arrays are refilled for the next group
     }
-}
-
-__global__ void k_copy_ids(const uint32_t* __restrict__ vs, uint32_t n, int32_t* __restrict__ ids) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) ids[i] = (int32_t)vs[i];
 }
 
 // rows[p][w] = packed word w of raw row ids[p]; head[p] = rows[p][0].
@@ -724,48 +731,41 @@ int build_sorted_ids(const void* tokens, const RowFmt& f, int64_t N64, int32_t* 
         cleanup();
         return rc;
     }
-    LCP_TIMED_LAUNCH(k_copy_ids, blocks_for(N, 256), 256, 0, s, vs, N, ids_out);
-    LCP_TIMED_LAUNCH(k_eq_sorted, blocks_for(N, 256), 256, 0, s, ks, N, eq);
+    LCP_TIMED_LAUNCH(k_ids_eq, blocks_for(N, 256), 256, 0, s, vs, ks, N, ids_out, eq);
     uint32_t m = 0, G = 0;
-    // Rows tied on word 0: small groups are ranked directly on their
-    // remaining words; only groups of more than 512 rows (if any) need the
-    // word-by-word LSD rounds below.
+    // Rows tied on word 0: tie groups of up to 512 rows are ranked directly
+    // on their remaining words (found straight from eq); only groups of more
+    // than 512 rows (if any) need the word-by-word LSD rounds below.
+    uint32_t* big_start = act2;  // free until the LSD rounds
+    uint32_t* big_len = idx2;
+    uint32_t* cnt = w.total + 2;  // [0] listed groups, [1] rows in groups of more than 512
+    const unsigned fill = (unsigned)sm_count() * 8;
+    auto sort_groups = [&]() -> int {
+        LCP_CUDA_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), s));
+        LCP_TIMED_LAUNCH(k_group_scan_sort, fill, 256, 0, s, tk, f, eq, N, ids_out, big_start, big_len, cnt, cnt + 1);
+        LCP_TIMED_LAUNCH(k_group_sort_mid, fill, 512, 0, s, tk, f, ids_out, big_start, big_len, cnt);
+        return LCP_OK;
+    };
     if (huge_host) {
-        // without waiting for the device: the tied rows are counted and
-        // grouped on the device, the group kernels read the counts there,
-        // and the rows in groups of more than 512 are counted into
-        // *huge_host, which the caller reads after its final synchronise
-        // (and rebuilds exactly, here with huge_host == nullptr, if nonzero)
-        rc = tie_compact_async(eq, N, act, grp, w, s);
-        if (rc == 0 && f.W > 1) {
-            uint32_t* gstart = idx2;
-            uint32_t* big_list = act2;
-            uint32_t* cnt = w.total + 2;  // [0] big groups, [1] rows in huge groups
-            const unsigned fill = (unsigned)sm_count() * 8;
-            LCP_CUDA_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), s));
-            LCP_TIMED_LAUNCH(k_group_starts, fill, 256, 0, s, grp, w.total, gstart);
-            LCP_TIMED_LAUNCH(k_group_sort_small, fill, 128, 0, s, tk, f, gstart, w.total, act, ids_out, big_list,
-                             cnt, cnt + 1);
-            LCP_TIMED_LAUNCH(k_group_sort_mid, fill, 512, 0, s, tk, f, gstart, act, ids_out, big_list, cnt);
-            LCP_CUDA_TRY(cudaMemcpyAsync(huge_host, cnt + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        // without waiting for the device: the rows in groups of more than
+        // 512 are counted into *huge_host, which the caller reads after its
+        // final synchronise (and rebuilds exactly, here with huge_host ==
+        // nullptr, if nonzero)
+        if (f.W > 1) {
+            rc = sort_groups();
+            if (rc == LCP_OK) LCP_CUDA_TRY(cudaMemcpyAsync(huge_host, cnt + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         }
         cleanup();
         return rc;
     }
     rc = tie_compact(eq, N, act, grp, &m, &G, w, s);
     if (rc == 0 && m > 0 && f.W > 1) {
-        uint32_t* gstart = idx2;          // G + 1 <= m + 1 <= N entries
-        uint32_t* big_list = act2;        // free until the LSD rounds
-        uint32_t* cnt = w.total + 2;      // [0] big groups, [1] rows in huge groups
-        const unsigned fill = (unsigned)sm_count() * 8;
-        LCP_CUDA_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), s));
-        LCP_TIMED_LAUNCH(k_group_starts, fill, 256, 0, s, grp, w.total, gstart);
-        LCP_TIMED_LAUNCH(k_group_sort_small, fill, 128, 0, s, tk, f, gstart, w.total, act, ids_out, big_list,
-                         cnt, cnt + 1);
-        LCP_TIMED_LAUNCH(k_group_sort_mid, fill, 512, 0, s, tk, f, gstart, act, ids_out, big_list, cnt);
-        LCP_CUDA_TRY(cudaMemcpyAsync(w.h_total + 10, cnt + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-        LCP_CUDA_TRY(cudaStreamSynchronize(s));
-        if (w.h_total[10] == 0) m = 0;  // every tie resolved
+        rc = sort_groups();
+        if (rc == LCP_OK) {
+            LCP_CUDA_TRY(cudaMemcpyAsync(w.h_total + 10, cnt + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+            LCP_CUDA_TRY(cudaStreamSynchronize(s));
+            if (w.h_total[10] == 0) m = 0;  // every tie resolved
+        }
     } else if (f.W == 1) {
         m = 0;  // one word: rows tied on it are equal and already in id order
     }

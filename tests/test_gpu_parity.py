@@ -122,7 +122,9 @@ def test_small_cases_indexed_and_scan_match_oracle(lcp, N, L, tb, sigma, k):
 
 
 @pytest.mark.parametrize("N,L,tb,sigma", [(1, 3, 1, 2), (500, 4, 1, 3), (10000, 16, 1, 16),
-                                          (50000, 32, 2, 7), (3000, 255, 2, 2), (70000, 5, 1, 2)])
+                                          (50000, 32, 2, 7), (3000, 255, 2, 2), (70000, 5, 1, 2),
+                                          (30000, 16, 2, 5),    # 4 words: 8 rows per warp step
+                                          (20000, 48, 2, 3)])   # 12 words: gather and H separately
 def test_sorted_index_matches_oracle(lcp, N, L, tb, sigma):
     rng = np.random.default_rng(N + L)
     dt = np.uint8 if tb == 1 else np.uint16
