@@ -372,6 +372,36 @@ def committed_traffic(kernel, Q):
 # ---------------------------------------------------------------------------
 # our implementation
 # ---------------------------------------------------------------------------
+def host_link(hS, out_bytes, build_ms, device, stream):
+    """Plain pinned copies of the step's sizes over the host link (tokens in,
+    results out), and the e2e step's lower bound from them: the tokens must
+    arrive before the build, the results leave after it, and the queries'
+    copy in can overlap the results' copy out."""
+    import torch
+    src = hS.view(torch.uint8).reshape(-1)
+    dst = torch.empty(src.numel(), dtype=torch.uint8, device=device)
+    dres = torch.zeros(out_bytes, dtype=torch.uint8, device=device)
+    hres = torch.empty(out_bytes, dtype=torch.uint8).pin_memory()
+
+    def timed(fn, reps=3):
+        fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / reps / 1e3
+
+    with torch.cuda.stream(stream):
+        t_in = timed(lambda: dst.copy_(src, non_blocking=True))
+        t_out = timed(lambda: hres.copy_(dres, non_blocking=True))
+    del dst, dres
+    return {"h2d_gbs": round(src.numel() / t_in / 1e9, 1), "d2h_gbs": round(out_bytes / t_out / 1e9, 1),
+            "bound_ms": round((t_in + t_out) * 1e3 + build_ms, 3),
+            "bound": "tokens in + build + results out (queries in overlapping results out)"}
+
+
 def run_ours(args, world, rank, local):
     import torch
     import paper_2602_04936_b300 as lcp
@@ -651,7 +681,8 @@ def run_ours(args, world, rank, local):
                        "ms_per_step": round(e2e_s * 1e3, 3),
                        "h2d_bytes_per_step": int(S.nbytes + Qs.nbytes),
                        "d2h_bytes_per_step": int(Q * k * 5),
-                       "api": "lcp_index_build_host + lcp_topk_batch_host"}
+                       "api": "lcp_index_build_host + lcp_topk_batch_host",
+                       "link": host_link(hS, Q * k * 5, build_ms, device, stream)}
         # CPU oracle on the host cores (rank 0 only)
         if rank == 0:
             qps, n, el, thr = oracle_rate(S, Qs, k)
