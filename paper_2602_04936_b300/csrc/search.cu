@@ -130,12 +130,15 @@ __device__ __forceinline__ int lane_cmp_from(const DevIndex& ix, const uint64_t*
 
 // Algorithm 3's descent in array form, by one lane: the insertion point p
 // (first row >= q) and the LCPs of q with rows p-1 and p (-1 where absent).
-// Word 0 alone decides everything unless some row shares it with q; then a
-// binary search inside that equal-head range compares the later words.
+// The search starts inside the depth-1 bucket of q's first token (the rows
+// before it are smaller than q, the rows after it larger).  Word 0 alone
+// decides everything unless some row shares it with q; then a binary search
+// inside that equal-head range compares the later words.
 __device__ __forceinline__ void lane_locate(const DevIndex& ix, const uint8_t* qrow, const RowFmt& qf,
                                             uint64_t q0, int64_t* p_out, int* lL_out, int* lR_out) {
     const int64_t N = ix.N;
-    int64_t lo = 0, hi = N;
+    const uint32_t t0 = (uint32_t)(q0 >> (64 - ix.bits));
+    int64_t lo = ix.bkt[t0], hi = ix.bkt[t0 + 1];
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
         if (ix.head[mid] < q0) lo = mid + 1;
@@ -226,7 +229,9 @@ __device__ __forceinline__ int lcp_with_row(const DevIndex& ix, int64_t m, const
 __device__ __forceinline__ QLoc warp_locate(const DevIndex& ix, const uint8_t* qrow, const RowFmt& qf) {
     const unsigned lane = lane_id();
     const uint64_t q0 = pack_word(qrow, 0, qf);
-    int64_t lo = 0, hi = ix.N;  // rows < q form the prefix [0, p), p in [lo, hi]
+    const uint32_t t0 = (uint32_t)(q0 >> (64 - ix.bits));
+    // rows < q form the prefix [0, p), p in [lo, hi]: within q's first-token bucket
+    int64_t lo = ix.bkt[t0], hi = ix.bkt[t0 + 1];
     while (hi - lo > 32) {
         const int64_t m = lo + ((hi - lo) * (int64_t)(lane + 1)) / 33;
         const int c = __popc(__ballot_sync(0xffffffffu, row_lt_query(ix, m, qrow, qf, q0)));
