@@ -335,10 +335,16 @@ def fill_algorithmic_bytes(k):
     return 32 + k * 4 + k * 5
 
 
-def locate_algorithmic_bytes(N, L, tb):
-    """Bytes one query's locate kernel must move: the query row, one 32-byte
-    sector per binary-search level and its 16-byte position record."""
-    return L * tb + math.ceil(math.log2(max(N, 2))) * 32 + 16
+def locate_algorithmic_bytes(S, Qs):
+    """Mean bytes one query's locate kernel must move: the query row, the
+    32-byte sector holding its first-token bucket bounds, one 32-byte sector
+    per binary-search level inside that bucket (ceil(log2(size + 1)) levels)
+    and its 16-byte position record."""
+    tb = S.dtype.itemsize
+    sizes = np.bincount(S[:, 0].astype(np.int64), minlength=1 << (8 * tb))
+    qb = sizes[Qs[:, 0].astype(np.int64)]
+    levels = np.ceil(np.log2(qb.astype(np.float64) + 1.0)).mean()
+    return int(round(S.shape[1] * tb + 32 + levels * 32 + 16))
 
 
 def kernel_source_hash():
@@ -496,7 +502,7 @@ def run_ours(args, world, rank, local):
     loc_launch_ms = loc_ms / max(loc_n, 1)
     per_q = answer_algorithmic_bytes(k)
     achieved = Q * per_q / (ans_launch_ms / 1e3) / 1e9
-    loc_per_q = locate_algorithmic_bytes(N, L, tb)
+    loc_per_q = locate_algorithmic_bytes(S, Qs)
     loc_achieved = Q * loc_per_q / (loc_launch_ms / 1e3) / 1e9
     roofline = {"kernel": "k_topk_answer", "bound": "hbm", "achieved": round(achieved, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
