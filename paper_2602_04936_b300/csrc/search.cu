@@ -38,20 +38,20 @@ namespace lcpk {
 // Loads up to 32 items on one side starting `n` items away from p; returns
 // the count.  Left: positions p-1-n-lane; right: positions p+n+lane.
 template <bool LEFT>
-__device__ __forceinline__ void issue_chunk(const DevIndex& ix, int64_t p, int n, int64_t avail, int l0,
+__device__ __forceinline__ void issue_chunk(const DevIndex& ix, int p, int n, int avail, int l0,
                                             int& h, uint32_t& id, bool& ok) {
-    const unsigned lane = lane_id();
-    ok = (int64_t)n + lane < avail;
+    const int lane = (int)lane_id();
+    ok = n + lane < avail;
     h = 255;
     id = 0;
     if (ok) {
-        const int64_t x = LEFT ? p - 1 - n - (int64_t)lane : p + n + (int64_t)lane;
+        const int x = LEFT ? p - 1 - n - lane : p + n + lane;
         h = (n == 0 && lane == 0) ? l0 : (int)ix.H[LEFT ? x + 1 : x];
         id = (uint32_t)ix.ids[x];
     }
 }
 
-__device__ __forceinline__ int finish_chunk(int& h, uint32_t id, bool ok, int n, int64_t avail,
+__device__ __forceinline__ int finish_chunk(int& h, uint32_t id, bool ok, int n, int avail,
                                             uint32_t* ids, uint8_t* lam) {
     const unsigned lane = lane_id();
     if (n > 0) h = min(h, (int)lam[n - 1]);
@@ -65,8 +65,7 @@ __device__ __forceinline__ int finish_chunk(int& h, uint32_t id, bool ok, int n,
         lam[n + lane] = (uint8_t)h;
     }
     __syncwarp();
-    const int64_t got = avail - n < 32 ? avail - n : 32;
-    return (int)got;
+    return avail - n < 32 ? avail - n : 32;
 }
 
 // Id-order probe for a large tie level: walks ids 0, 1, 2, ... through pos[]
@@ -282,12 +281,12 @@ struct alignas(16) FillRec {
 // First half of a query (expansion, d*, the level-d* interval, A ordered and
 // written to output slots [0, |A|)).
 template <typename KT, typename WA>
-__device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, WA& S, int64_t p, int lL, int lR, int tok0,
+__device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, WA& S, int p, int lL, int lR, int tok0,
                                                int k, int32_t* __restrict__ oid, uint8_t* __restrict__ olcp) {
     const unsigned lane = lane_id();
-    const int64_t N = ix.N;
+    const int N = (int)ix.N;  // positions are 32-bit: an index holds fewer than 2^30 rows
     // 3. expansion
-    const int64_t availL = p, availR = N - p;
+    const int availL = p, availR = N - p;
     int nL = 0, nR = 0, dstar = 0;
     // the depth-1 bucket of q's first token, fetched early: d* is 1 for
     // about half of the queries, and these loads then cost no extra wait
@@ -414,7 +413,7 @@ __device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, WA& S, int64_
         }
     }
     const int nA = aL + aR;
-    int64_t lov = 0, hiv = N;
+    int lov = 0, hiv = N;
     int li = -2;  // tie list of the level-d* node (-2: not looked up yet)
     if (dstar == 1) {  // depth-1 bucket of q's first token (fetched above)
         lov = bk0;
@@ -423,14 +422,14 @@ __device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, WA& S, int64_
     } else if (dstar > 1) {
         const bool knownL = vL < nL || nL == availL;
         const bool knownR = vR < nR || nR == availR;
-        int64_t xl = -1, xr = N;
+        int xl = -1, xr = N;
         find_bounds(ix, p - nL, !knownL, p + nR, !knownR, dstar, &xl, &xr);
         lov = knownL ? p - vL : (xl < 0 ? 0 : xl);
         hiv = knownR ? p + vR : xr;
     }
-    const int64_t nT = (hiv - lov) - nA;
+    const int nT = (hiv - lov) - nA;
     int kp = k - nA;
-    if ((int64_t)kp > nT) kp = (int)nT;
+    if (kp > nT) kp = nT;
     // 5a. A sorted by (LCP desc, id asc) into slots [0, nA)
     if (nA > 0) {
         if (nA <= 32) rank_and_write_A<KT>(S, aL, nA, oid, olcp);
@@ -438,10 +437,10 @@ __device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, WA& S, int64_
         else sort_and_write_A<4, KT>(S, aL, nA, oid, olcp);
     }
     FillRec r;
-    r.lov = (int32_t)lov;
-    r.hiv = (int32_t)hiv;
-    r.loc = (int32_t)(p - aL);
-    r.hic = (int32_t)(p + aR);
+    r.lov = lov;
+    r.hiv = hiv;
+    r.loc = p - aL;
+    r.hic = p + aR;
     r.nA = (int16_t)nA;
     r.kp = (int16_t)(kp > 0 ? kp : 0);
     r.dstar = (int16_t)dstar;
@@ -527,7 +526,7 @@ __device__ __forceinline__ void topk_fill(const DevIndex& ix, WA& S, const FillR
 template <typename KT>
 __device__ __forceinline__ void topk_one(const DevIndex& ix, QWarp& S, int64_t p, int lL, int lR, int tok0, int k,
                                          int32_t* __restrict__ oid, uint8_t* __restrict__ olcp) {
-    const FillRec r = topk_expand<KT>(ix, S, p, lL, lR, tok0, k, oid, olcp);
+    const FillRec r = topk_expand<KT>(ix, S, (int)p, lL, lR, tok0, k, oid, olcp);
     topk_fill(ix, S, r, k, oid, olcp);
 }
 
@@ -548,7 +547,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 8) k_topk_answer(DevIndex i
         const int64_t qi = wq0 + j;
         if (qi >= Q) break;
         const QLoc r = loc[qi];
-        const FillRec f = topk_expand<KT>(ix, S, r.p, r.lL, r.lR, r.tok0, k, out_ids + qi * k, out_lcp + qi * k);
+        const FillRec f = topk_expand<KT>(ix, S, (int)r.p, r.lL, r.lR, r.tok0, k, out_ids + qi * k, out_lcp + qi * k);
         if (lane_id() == 0) recs[qi] = f;
     }
 }

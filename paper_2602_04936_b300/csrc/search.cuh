@@ -229,25 +229,27 @@ __device__ __forceinline__ const uint8_t* hlevel(const DevIndex& ix, int lev) {
 // State of one side's search: climbing until a group holding an H < d is
 // found, then descending to level 0.
 struct BoundSearch {
-    int64_t idx;
+    int idx;
     int lev;
     int phase;  // 0 climb, 1 descend, 2 done
-    int64_t result;
+    int result;
 };
 
 // Left side: largest x <= from with H[x] < d (or -1).  Right side: smallest
-// x >= from with H[x] < d (or N).  `need*` = 0 skips a side.
-__device__ __forceinline__ void find_bounds(const DevIndex& ix, int64_t fromL, bool needL, int64_t fromR, bool needR,
-                            int d, int64_t* outL, int64_t* outR) {
+// x >= from with H[x] < d (or N).  `need*` = 0 skips a side.  Positions are
+// 32-bit (an index holds fewer than 2^30 rows).
+__device__ __forceinline__ void find_bounds(const DevIndex& ix, int fromL, bool needL, int fromR, bool needR,
+                            int d, int* outL, int* outR) {
     const unsigned lane = lane_id();
+    const int N = (int)ix.N;
     BoundSearch s[2];
     s[0] = {fromL, 0, needL ? 0 : 2, -1};
-    s[1] = {fromR, 0, needR ? 0 : 2, ix.N};
-    if (needR && fromR >= ix.N) s[1].phase = 2;
+    s[1] = {fromR, 0, needR ? 0 : 2, N};
+    if (needR && fromR >= N) s[1].phase = 2;
     if (needL && fromL < 0) s[0].phase = 2;
     while (s[0].phase != 2 || s[1].phase != 2) {
         uint8_t val[2];
-        int64_t e[2], g0[2];
+        int e[2], g0[2];
         bool inr[2];
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
@@ -257,9 +259,9 @@ __device__ __forceinline__ void find_bounds(const DevIndex& ix, int64_t fromL, b
             if (b.phase == 2) continue;
             const int lev = b.phase == 0 ? b.lev : b.lev - 1;
             const uint8_t* arr = hlevel(ix, lev);
-            const int64_t len = ix.hlen[lev];
+            const int len = (int)ix.hlen[lev];
             g0[side] = b.phase == 0 ? ((b.idx >> 5) << 5) : (b.idx << 5);
-            e[side] = g0[side] + lane;
+            e[side] = g0[side] + (int)lane;
             bool ok = e[side] < len;
             if (b.phase == 0) ok = ok && (side == 0 ? e[side] <= b.idx : e[side] >= b.idx);
             inr[side] = ok;
@@ -284,7 +286,7 @@ __device__ __forceinline__ void find_bounds(const DevIndex& ix, int64_t fromL, b
                 } else {
                     b.idx = side == 0 ? (b.idx >> 5) - 1 : (b.idx >> 5) + 1;
                     ++b.lev;
-                    if (b.idx < 0 || b.idx >= ix.hlen[b.lev]) b.phase = 2;
+                    if (b.idx < 0 || b.idx >= (int)ix.hlen[b.lev]) b.phase = 2;
                 }
             } else {
                 --b.lev;

@@ -48,8 +48,8 @@ __global__ void __launch_bounds__(kTlWarps * 32) k_heavy_intervals(DevIndex ix, 
         }
         d = ell + 1;
         if (d > L) break;
-        int64_t xl, xr;
-        find_bounds(ix, s, true, s + 1, true, d, &xl, &xr);
+        int xl, xr;
+        find_bounds(ix, (int)s, true, (int)s + 1, true, d, &xl, &xr);
         lo = xl < 0 ? 0 : xl;
         hi = xr;
     }

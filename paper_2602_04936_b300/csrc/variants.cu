@@ -30,8 +30,8 @@ __device__ __forceinline__ void level_interval(const DevIndex& ix, int64_t p, in
         return;
     }
     const bool inL = lL >= d, inR = lR >= d;
-    int64_t xl = -1, xr = ix.N;
-    if (inL || inR) find_bounds(ix, p - 1, inL, p + 1, inR, d, &xl, &xr);
+    int xl = -1, xr = (int)ix.N;
+    if (inL || inR) find_bounds(ix, (int)p - 1, inL, (int)p + 1, inR, d, &xl, &xr);
     *lo = inL ? (xl < 0 ? 0 : xl) : p;
     *hi = inR ? xr : p;
 }
