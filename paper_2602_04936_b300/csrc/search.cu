@@ -135,18 +135,18 @@ __device__ __forceinline__ int lane_cmp_from(const DevIndex& ix, const uint64_t*
 // inside that equal-head range compares the later words.
 __device__ __forceinline__ void lane_locate(const DevIndex& ix, const uint8_t* qrow, const RowFmt& qf,
                                             uint64_t q0, int64_t* p_out, int* lL_out, int* lR_out) {
-    const int64_t N = ix.N;
+    const int N = (int)ix.N;  // positions are 32-bit: an index holds fewer than 2^30 rows
     const uint32_t t0 = (uint32_t)(q0 >> (64 - ix.bits));
-    int64_t lo = ix.bkt[t0], hi = ix.bkt[t0 + 1];
+    int lo = ix.bkt[t0], hi = ix.bkt[t0 + 1];
     while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
+        const int mid = (lo + hi) >> 1;
         if (ix.head[mid] < q0) lo = mid + 1;
         else hi = mid;
     }
-    const int64_t p0 = lo;
-    int64_t p1 = p0;
+    const int p0 = lo;
+    int p1 = p0;
     if (p0 < N && ix.head[p0] == q0) {  // gallop to the end of the equal-head range
-        int64_t step = 1, last = p0;
+        int step = 1, last = p0;
         while (last + step < N && ix.head[last + step] == q0) {
             last += step;
             step <<= 1;
@@ -154,31 +154,31 @@ __device__ __forceinline__ void lane_locate(const DevIndex& ix, const uint8_t* q
         lo = last + 1;
         hi = last + step < N ? last + step : N;
         while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
+            const int mid = (lo + hi) >> 1;
             if (ix.head[mid] <= q0) lo = mid + 1;
             else hi = mid;
         }
         p1 = lo;
     }
-    int64_t p = p0;
+    int p = p0;
     if (p1 > p0) {
         lo = p0;
         hi = p1;
         while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
+            const int mid = (lo + hi) >> 1;
             int l;
-            if (lane_cmp_from(ix, ix.rows + mid * ix.W, qrow, qf, 1, &l) < 0) lo = mid + 1;
+            if (lane_cmp_from(ix, ix.rows + (size_t)mid * ix.W, qrow, qf, 1, &l) < 0) lo = mid + 1;
             else hi = mid;
         }
         p = lo;
     }
     int lL = -1, lR = -1;
     if (p > 0) {
-        if (p - 1 >= p0) lane_cmp_from(ix, ix.rows + (p - 1) * ix.W, qrow, qf, 1, &lL);
+        if (p - 1 >= p0) lane_cmp_from(ix, ix.rows + (size_t)(p - 1) * ix.W, qrow, qf, 1, &lL);
         else lL = __clzll((long long)(ix.head[p - 1] ^ q0)) / ix.bits;
     }
     if (p < N) {
-        if (p < p1) lane_cmp_from(ix, ix.rows + p * ix.W, qrow, qf, 1, &lR);
+        if (p < p1) lane_cmp_from(ix, ix.rows + (size_t)p * ix.W, qrow, qf, 1, &lR);
         else lR = __clzll((long long)(ix.head[p] ^ q0)) / ix.bits;
     }
     *p_out = p;
