@@ -552,7 +552,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 8) k_topk_answer(DevIndex i
     }
 }
 
-__global__ void __launch_bounds__(kSearchWarps * 32, 12) k_topk_fill(DevIndex ix, const FillRec* __restrict__ recs,
+__global__ void __launch_bounds__(kSearchWarps * 32, 10) k_topk_fill(DevIndex ix, const FillRec* __restrict__ recs,
                                                                     int64_t Q, int k, int qpw,
                                                                     int32_t* __restrict__ out_ids,
                                                                     uint8_t* __restrict__ out_lcp) {
