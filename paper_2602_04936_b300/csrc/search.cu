@@ -355,10 +355,10 @@ __device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, WA& S, int p,
             } else {
                 dstar = 0;
             }
-            aL = __popc(__ballot_sync(0xffffffffu, vL0 > dstar)) + __popc(__ballot_sync(0xffffffffu, vL1 > dstar));
-            aR = __popc(__ballot_sync(0xffffffffu, vR0 > dstar)) + __popc(__ballot_sync(0xffffffffu, vR1 > dstar));
-            vL = __popc(__ballot_sync(0xffffffffu, vL0 >= dstar)) + __popc(__ballot_sync(0xffffffffu, vL1 >= dstar));
-            vR = __popc(__ballot_sync(0xffffffffu, vR0 >= dstar)) + __popc(__ballot_sync(0xffffffffu, vR1 >= dstar));
+            aL = (int)__reduce_add_sync(0xffffffffu, (unsigned)(vL0 > dstar) + (unsigned)(vL1 > dstar));
+            aR = (int)__reduce_add_sync(0xffffffffu, (unsigned)(vR0 > dstar) + (unsigned)(vR1 > dstar));
+            vL = (int)__reduce_add_sync(0xffffffffu, (unsigned)(vL0 >= dstar) + (unsigned)(vL1 >= dstar));
+            vR = (int)__reduce_add_sync(0xffffffffu, (unsigned)(vR0 >= dstar) + (unsigned)(vR1 >= dstar));
             decided = true;
         }
     }
