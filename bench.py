@@ -362,6 +362,33 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
+def committed_inst_per_query(kernel):
+    """Warp instructions per query of `kernel` from the committed ncu capture
+    (profiles/traffic.json), or None when its sources changed since."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel)
+    if not d or d.get("source_hash") != kernel_source_hash() or "warp_inst_per_query" not in d:
+        return None
+    return d["warp_inst_per_query"]
+
+
+def issue_roofline(kernel, Q, launch_ms, sm_mhz, sms):
+    """The issue ceiling of an instruction-bound kernel: its warp
+    instructions (committed ncu count per query x Q) over its launch time,
+    against one warp instruction per clock on each of the 4 schedulers of
+    every SM at the sampled SM clock."""
+    ipq = committed_inst_per_query(kernel)
+    if ipq is None or not sm_mhz or launch_ms <= 0:
+        return None
+    ach = ipq * Q / (launch_ms / 1e3)
+    pk = sms * 4 * sm_mhz * 1e6
+    return {"warp_inst_per_query": ipq, "achieved": round(ach / 1e12, 4), "peak": round(pk / 1e12, 4),
+            "unit": "Twarp-inst/s", "frac": round(ach / pk, 4),
+            "peak_source": "%d SMs x 4 schedulers x 1 warp instruction/clock x %.0f MHz (sampled)" % (sms, sm_mhz)}
+
+
 def committed_traffic(kernel, Q):
     """DRAM bytes per launch of `kernel` from the committed ncu summary
     (profiles/traffic.json), scaled from its captured batch to Q queries;
@@ -498,6 +525,7 @@ def run_ours(args, world, rank, local):
 
     # roofline of the dominant kernel: the answer half of the indexed search
     peak, peak_kind = measured_peaks()
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
     ans_launch_ms = ans_ms / max(ans_n, 1)
     loc_launch_ms = loc_ms / max(loc_n, 1)
     per_q = answer_algorithmic_bytes(k)
@@ -512,13 +540,15 @@ def run_ours(args, world, rank, local):
                 "algorithmic_bytes_per_launch": Q * per_q, "bytes_per_query": per_q,
                 "launch_ms": round(ans_launch_ms, 4), "launches_timed": ans_n,
                 "timing": "CUDA events around each launch on its stream, timed region",
+                "issue": issue_roofline("k_topk_answer", Q, ans_launch_ms, clocks.get("sm_mhz"), sms),
                 "other_kernels": {"k_topk_locate": {
                     "launch_ms": round(loc_launch_ms, 4), "bytes_per_query": loc_per_q,
                     "achieved": round(loc_achieved, 1), "frac": round(loc_achieved / peak, 4)},
                     "k_topk_fill": {
                     "launch_ms": round(fill_ms / max(fill_n, 1), 4), "bytes_per_query": fill_algorithmic_bytes(k),
                     "achieved": round(Q * fill_algorithmic_bytes(k) / (fill_ms / max(fill_n, 1) / 1e3) / 1e9, 1),
-                    "frac": round(Q * fill_algorithmic_bytes(k) / (fill_ms / max(fill_n, 1) / 1e3) / 1e9 / peak, 4)}}}
+                    "frac": round(Q * fill_algorithmic_bytes(k) / (fill_ms / max(fill_n, 1) / 1e3) / 1e9 / peak, 4),
+                    "issue": issue_roofline("k_topk_fill", Q, fill_ms / max(fill_n, 1), clocks.get("sm_mhz"), sms)}}}
 
     # energy: NVML's counter advances in coarse steps, so each figure comes
     # from its own loop of a couple of seconds (idle gaps excluded)
