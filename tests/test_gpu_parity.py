@@ -106,6 +106,7 @@ CASES = [
     (20000, 8, 1, 2, 128),   # tiny alphabet: enormous tie levels
     (3000, 255, 1, 2, 17),   # L = 255, uint8
     (3000, 10, 1, 3, 80),    # K = 96: sparse table merged in shared memory
+    (20000, 24, 1, 2, 50),   # mid-size tie groups, word 1 ties resolved on word 2
     (700, 255, 2, 3, 40),    # L = 255, uint16 (64 packed words)
 ]
 
@@ -124,7 +125,9 @@ def test_small_cases_indexed_and_scan_match_oracle(lcp, N, L, tb, sigma, k):
 @pytest.mark.parametrize("N,L,tb,sigma", [(1, 3, 1, 2), (500, 4, 1, 3), (10000, 16, 1, 16),
                                           (50000, 32, 2, 7), (3000, 255, 2, 2), (70000, 5, 1, 2),
                                           (30000, 16, 2, 5),    # 4 words: 8 rows per warp step
-                                          (20000, 48, 2, 3)])   # 12 words: gather and H separately
+                                          (20000, 48, 2, 3),    # 12 words: gather and H separately
+                                          (20000, 16, 1, 2),    # ~78-row tie groups, ties on word 1 too
+                                          (20000, 12, 2, 3)])   # ~250-row groups, later words decide
 def test_sorted_index_matches_oracle(lcp, N, L, tb, sigma):
     rng = np.random.default_rng(N + L)
     dt = np.uint8 if tb == 1 else np.uint16
