@@ -753,7 +753,10 @@ int build_sorted_ids(const void* tokens, const RowFmt& f, int64_t N64, int32_t* 
         // nullptr, if nonzero)
         if (f.W > 1) {
             rc = sort_groups();
-            if (rc == LCP_OK) LCP_CUDA_TRY(cudaMemcpyAsync(huge_host, cnt + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+            if (rc == LCP_OK) {
+                const cudaError_t e = cudaMemcpyAsync(huge_host, cnt + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+                if (e != cudaSuccess) rc = cuda_status(e);
+            }
         }
         cleanup();
         return rc;
@@ -762,9 +765,10 @@ int build_sorted_ids(const void* tokens, const RowFmt& f, int64_t N64, int32_t* 
     if (rc == 0 && m > 0 && f.W > 1) {
         rc = sort_groups();
         if (rc == LCP_OK) {
-            LCP_CUDA_TRY(cudaMemcpyAsync(w.h_total + 10, cnt + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-            LCP_CUDA_TRY(cudaStreamSynchronize(s));
-            if (w.h_total[10] == 0) m = 0;  // every tie resolved
+            cudaError_t e = cudaMemcpyAsync(w.h_total + 10, cnt + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) rc = cuda_status(e);
+            else if (w.h_total[10] == 0) m = 0;  // every tie resolved
         }
     } else if (f.W == 1) {
         m = 0;  // one word: rows tied on it are equal and already in id order
