@@ -165,12 +165,11 @@ static void retain_pool_memory() {
 // Frees with cudaFreeAsync on stream s (the build's own stream on failure) or,
 // with s == nullptr and the device idle, synchronously.
 static void free_index_memory(lcp_index_s* x, cudaStream_t s) {
-    for (void* p : {x->arena, x->stage_in, x->stage_out})
-        if (p) {
-            if (s) cudaFreeAsync(p, s);
-            else cudaFree(p);
-        }
-    x->arena = x->stage_in = x->stage_out = nullptr;
+    if (x->arena) {
+        if (s) cudaFreeAsync(x->arena, s);
+        else cudaFree(x->arena);
+    }
+    x->arena = nullptr;
     x->buf[0] = lcp_buffers();
     x->buf[1] = lcp_buffers();
 }
@@ -469,6 +468,61 @@ int lcp_index_build(const void* d_tokens, int64_t N, lcp_format_t fmt, int64_t c
     return LCP_OK;
 }
 
+// The host-buffer entry points of this thread on the current device: device
+// staging for queries and results (grown on demand, kept for the thread's
+// later calls -- each call synchronises before it returns, so the next one
+// finds them idle) and the event after this thread's latest host-to-device
+// input copy.  A call's input copies wait for that event: the copies cross
+// the link in call order, so a search's queries follow -- rather than share
+// the link with -- the tokens of the build before it, yet overlap that build.
+// The pipelined search also keeps its two copy streams and per-chunk events
+// here.
+constexpr int kHostChunks = 8;
+struct HostStage {
+    void* in = nullptr;
+    size_t in_bytes = 0;
+    void* out = nullptr;
+    size_t out_bytes = 0;
+    cudaEvent_t in_tail = nullptr;
+    bool tail_set = false;
+    cudaStream_t cin = nullptr, cout = nullptr;
+    cudaEvent_t ev[2 * kHostChunks] = {nullptr};
+};
+
+static HostStage* host_stage() {
+    static thread_local HostStage hs[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    HostStage& h = hs[dev];
+    if (!h.in_tail) {
+        bool ok = cudaEventCreateWithFlags(&h.in_tail, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&h.cin, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&h.cout, cudaStreamNonBlocking) == cudaSuccess;
+        for (int i = 0; ok && i < 2 * kHostChunks; ++i)
+            ok = cudaEventCreateWithFlags(&h.ev[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            h = HostStage();  // (a partial set is leaked, not reused)
+            return nullptr;
+        }
+    }
+    return &h;
+}
+
+// Device buffer of at least `need` bytes (synchronous allocation, usable from
+// any stream at once; the old buffer is idle when this is called).
+static int grow(void** p, size_t* have, size_t need) {
+    if (*have >= need) return LCP_OK;
+    if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+        *have = 0;
+    }
+    LCP_CUDA_TRY(cudaMalloc(p, need));
+    *have = need;
+    return LCP_OK;
+}
+
 int lcp_index_build_host(const void* h_tokens, int64_t N, lcp_format_t fmt, int64_t capacity,
                          int32_t max_k, lcp_stream_t stream, lcp_index_t* out) {
     if (!out) return LCP_ERR_INVALID;
@@ -478,8 +532,11 @@ int lcp_index_build_host(const void* h_tokens, int64_t N, lcp_format_t fmt, int6
     size_t bytes = (size_t)N * fmt.L * fmt.token_bytes;
     void* d = nullptr;
     if (bytes) {
+        HostStage* hs = host_stage();
         LCP_CUDA_TRY(cudaMallocAsync(&d, bytes, s));
+        if (hs && hs->tail_set) LCP_CUDA_TRY(cudaStreamWaitEvent(s, hs->in_tail, 0));
         LCP_CUDA_TRY(cudaMemcpyAsync(d, h_tokens, bytes, cudaMemcpyHostToDevice, s));
+        if (hs && cudaEventRecord(hs->in_tail, s) == cudaSuccess) hs->tail_set = true;
     }
     int rc = lcp_index_build(d, N, fmt, capacity, max_k, stream, out);
     if (d) cudaFreeAsync(d, s);
@@ -513,19 +570,6 @@ int lcp_topk_batch(lcp_index_t x, const void* d_queries, int64_t Q, int32_t k, i
     return rc;
 }
 
-static int grow(void** p, size_t* have, size_t need, cudaStream_t s) {
-    if (*have >= need) return LCP_OK;
-    if (*p) {
-        cudaStreamSynchronize(s);
-        cudaFree(*p);
-        *p = nullptr;
-        *have = 0;
-    }
-    LCP_CUDA_TRY(cudaMalloc(p, need));
-    *have = need;
-    return LCP_OK;
-}
-
 int lcp_topk_batch_host(lcp_index_t x, const void* h_queries, int64_t Q, int32_t k, int32_t* h_out_ids,
                         uint8_t* h_out_lcp, lcp_stream_t stream) {
     if (!x || Q < 0 || k < 1 || k > x->max_k) return LCP_ERR_INVALID;
@@ -536,42 +580,31 @@ int lcp_topk_batch_host(lcp_index_t x, const void* h_queries, int64_t Q, int32_t
     size_t qb = (size_t)Q * row;
     size_t ob = (size_t)Q * k * (sizeof(int32_t) + 1);
     int rc;
-    if ((rc = grow(&x->stage_in, &x->stage_in_bytes, qb, s))) return rc;
-    if ((rc = grow(&x->stage_out, &x->stage_out_bytes, ob, s))) return rc;
-    int32_t* d_ids = (int32_t*)x->stage_out;
-    uint8_t* d_lcp = (uint8_t*)x->stage_out + (size_t)Q * k * sizeof(int32_t);
+    HostStage* hs = host_stage();
+    if (!hs) return LCP_ERR_CUDA;
+    if ((rc = grow(&hs->in, &hs->in_bytes, qb))) return rc;
+    if ((rc = grow(&hs->out, &hs->out_bytes, ob))) return rc;
+    int32_t* d_ids = (int32_t*)hs->out;
+    uint8_t* d_lcp = (uint8_t*)hs->out + (size_t)Q * k * sizeof(int32_t);
     const uint8_t* hq = static_cast<const uint8_t*>(h_queries);
-    uint8_t* dq = static_cast<uint8_t*>(x->stage_in);
+    uint8_t* dq = static_cast<uint8_t*>(hs->in);
     // Pipelined in chunks: chunk i's queries cross the bus on one copy
     // stream while chunk i-1 is searched on `stream` and chunk i-2's results
     // cross back on another, so the two directions and the search overlap.
-    const int64_t chunk = Q >= 8 * 65536 ? (Q + 7) / 8 : Q;
+    const int64_t chunk = Q >= kHostChunks * 65536 ? (Q + kHostChunks - 1) / kHostChunks : Q;
     const int nch = (int)((Q + chunk - 1) / chunk);
-    cudaStream_t cin = nullptr, cout = nullptr;
-    cudaEvent_t ev[2 * 8 + 1] = {nullptr};
-    auto cleanup = [&]() {
-        for (auto& e : ev)
-            if (e) cudaEventDestroy(e);
-        if (cin) cudaStreamDestroy(cin);
-        if (cout) cudaStreamDestroy(cout);
-    };
+    cudaStream_t cin = hs->cin, cout = hs->cout;
+    cudaEvent_t* ev = hs->ev;
     cudaError_t e = cudaSuccess;
-    if (nch > 1) {
-        e = cudaStreamCreateWithFlags(&cin, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cout, cudaStreamNonBlocking);
-        for (int i = 0; i < 2 * nch + 1 && e == cudaSuccess; ++i)
-            e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[2 * nch], s);  // the stage buffers are free
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(cin, ev[2 * nch], 0);
-        if (e != cudaSuccess) {
-            cleanup();
-            return cuda_status(e);
-        }
-    }
+    // the input copies follow this thread's earlier ones (not the whole stream)
+    if (nch > 1 && hs->tail_set) e = cudaStreamWaitEvent(cin, hs->in_tail, 0);
+    if (e != cudaSuccess) return cuda_status(e);
     for (int i = 0; i < nch && rc == LCP_OK; ++i) {
         const int64_t q0 = i * chunk, qc = q0 + chunk < Q ? chunk : Q - q0;
         cudaStream_t in = nch > 1 ? cin : s, out = nch > 1 ? cout : s;
-        e = cudaMemcpyAsync(dq + q0 * row, hq + q0 * row, qc * row, cudaMemcpyHostToDevice, in);
+        if (nch == 1 && hs->tail_set) e = cudaStreamWaitEvent(in, hs->in_tail, 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dq + q0 * row, hq + q0 * row, qc * row, cudaMemcpyHostToDevice, in);
+        if (e == cudaSuccess && i == nch - 1 && cudaEventRecord(hs->in_tail, in) == cudaSuccess) hs->tail_set = true;
         if (e == cudaSuccess && nch > 1) {
             e = cudaEventRecord(ev[2 * i], in);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[2 * i], 0);
@@ -598,7 +631,6 @@ int lcp_topk_batch_host(lcp_index_t x, const void* h_queries, int64_t Q, int32_t
         cudaStreamSynchronize(cout);
     }
     cudaStreamSynchronize(s);
-    cleanup();
     return rc;
 }
 

@@ -123,12 +123,7 @@ struct lcp_index_s {
     int nuses = 0;
     bool shared = false;
     int64_t bytes = 0;
-    // host-buffer entry points: device staging grown on demand
     void* arena = nullptr;  // one allocation holding every device array above
-    void* stage_in = nullptr;
-    size_t stage_in_bytes = 0;
-    void* stage_out = nullptr;
-    size_t stage_out_bytes = 0;
     // insert scratch (allocated at build when cap > N)
     uint64_t* ins_rows = nullptr;   // [LCP_INSERT_SMALL_BATCH][W] sorted new rows
     int32_t* ins_ids = nullptr;     // ids of the sorted new rows
