@@ -389,6 +389,21 @@ def issue_roofline(kernel, Q, launch_ms, sm_mhz, sms):
             "peak_source": "%d SMs x 4 schedulers x 1 warp instruction/clock x %.0f MHz (sampled)" % (sms, sm_mhz)}
 
 
+def scan_alu_roofline(Q, N, ms, sm_mhz, sms):
+    """The full scan at large batches is bound by integer ALU work: Q x N
+    (query, row) tests of at least 4 integer operations each (xor, mask,
+    compare, branch on the packed first word), against the ALU pipe's 16
+    lanes per scheduler, 4 schedulers per SM, at the sampled SM clock."""
+    if not sm_mhz or ms <= 0:
+        return None
+    ops = 4.0 * Q * N
+    ach = ops / (ms / 1e3)
+    pk = sms * 4 * 16 * sm_mhz * 1e6
+    return {"ops_per_pair": 4, "achieved": round(ach / 1e12, 3), "peak": round(pk / 1e12, 3),
+            "unit": "Tops/s", "frac": round(ach / pk, 4),
+            "peak_source": "%d SMs x 4 schedulers x 16 ALU lanes x %.0f MHz (sampled)" % (sms, sm_mhz)}
+
+
 def committed_traffic(kernel, Q):
     """DRAM bytes per launch of `kernel` from the committed ncu summary
     (profiles/traffic.json), scaled from its captured batch to Q queries;
@@ -602,7 +617,8 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         same = bool(torch.equal(out_ids, sids) and torch.equal(out_lcp, slc))
         paths["full_scan"] = {"ms": round(scan_ms, 3), "qps": round(Q / (scan_ms / 1e3), 1),
-                              "energy_j_per_query": scan_j, "identical_to_indexed": same}
+                              "energy_j_per_query": scan_j, "identical_to_indexed": same,
+                              "alu": scan_alu_roofline(Q, N, scan_ms, clocks.get("sm_mhz"), sms)}
         paths["indexed_vs_full_scan_speedup_query_only"] = round(scan_ms / query_ms, 1)
         # per-batch latency (CUDA events around each call)
         lat = {"indexed": {}, "full_scan": {}}
