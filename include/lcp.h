@@ -200,17 +200,19 @@ LCP_API int lcp_tal_topk(lcp_index_t index, const void* d_queries, int64_t Q, in
 /* ------------------------------------------------------------------------
  * Autotuner for the indexed search's launch shape (the paper has no
  * counterpart; the shape never changes a result).  lcp_autotune times every
- * candidate shape -- queries per warp of the answer kernel (1..32) and
- * lane- or warp-per-query location -- on the caller's sample batch (device
- * queries, Q >= 1, k <= max_k) with CUDA events on `stream`, synchronously,
- * and installs the fastest for later lcp_topk_batch calls whose index and
- * batch fall in the same class: (floor(log2 N), L, token bytes,
- * floor(log2 Q), k class {1, <=16, <=64, <=128}), process-wide.
- * lcp_set_search_shape installs a known shape for that class (to reuse a
- * cached tuning run).
+ * candidate shape -- one fused kernel with a warp per query (the default for
+ * batches of up to 4,096 queries), or locate + answer + fill with 1..32
+ * queries per warp of the answer kernel and lane- or warp-per-query location
+ * -- on the caller's sample batch (device queries, Q >= 1, k <= max_k) with
+ * CUDA events on `stream`, synchronously, and installs the fastest for later
+ * lcp_topk_batch calls whose index and batch fall in the same class:
+ * (floor(log2 N), L, token bytes, floor(log2 Q), k class {1, <=16, <=64,
+ * <=128}), process-wide.  lcp_set_search_shape installs a known shape for
+ * that class (to reuse a cached tuning run); qpw = 0 there and in the
+ * result means the fused kernel.
  * ---------------------------------------------------------------------- */
 typedef struct {
-    int32_t qpw;          /* queries per warp chosen */
+    int32_t qpw;          /* queries per warp chosen; 0: the fused kernel */
     int32_t locate_warp;  /* 1: warp per query, 0: lane per query */
     float best_ms;        /* its time on the sample batch */
     float default_ms;     /* the untuned heuristic's time */

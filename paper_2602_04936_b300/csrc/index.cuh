@@ -176,6 +176,7 @@ SideStream* side_stream();
 struct SearchShape {
     int qpw = 32;         // queries per warp of the answer kernel
     int locate_warp = 0;  // 1: warp-per-query locate, 0: lane-per-query
+    int fused = 0;        // 1: one kernel, a warp per query (small batches)
 };
 
 int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, int32_t* out_ids,

@@ -568,6 +568,22 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 10) k_topk_fill(DevIndex ix
     }
 }
 
+// Small batches: one kernel, a warp per query -- locate (33-way search),
+// expansion and tie fill in place -- so a batch costs one launch and no
+// scratch instead of three launches and the per-query records.
+template <typename KT>
+__global__ void __launch_bounds__(kSearchWarps * 32) k_topk_fused(DevIndex ix, const uint8_t* __restrict__ queries,
+                                                                  RowFmt qf, int64_t Q, int k,
+                                                                  int32_t* __restrict__ out_ids,
+                                                                  uint8_t* __restrict__ out_lcp) {
+    __shared__ QWarp sm[kSearchWarps];
+    const int warp = threadIdx.x >> 5;
+    const int64_t qi = (int64_t)blockIdx.x * kSearchWarps + warp;
+    if (qi >= Q) return;
+    const QLoc r = warp_locate(ix, row_of(queries, qi, qf), qf);
+    topk_one<KT>(ix, sm[warp], r.p, r.lL, r.lR, r.tok0, k, out_ids + qi * k, out_lcp + qi * k);
+}
+
 // ---- persistent worker ----
 
 __device__ __forceinline__ long long global_ns() {
@@ -717,8 +733,12 @@ TuneKey tune_key(const lcp_index_s* x, int64_t Q, int k) {
 }
 }  // namespace
 
+// Batches up to this size are answered by the fused kernel by default.
+constexpr int64_t kFusedMaxQ = 4096;
+
 SearchShape default_shape(int64_t Q) {
     SearchShape sh;
+    sh.fused = Q <= kFusedMaxQ ? 1 : 0;
     sh.locate_warp = Q <= kWarpLocateMaxQ ? 1 : 0;
     // queries per warp: at most 8 (measured best for large batches: enough
     // warps for an even tail); fewer for small batches so that the batch
@@ -767,12 +787,20 @@ int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, i
     DevIndex ix = dev_view(x);
     RowFmt qf = make_fmt(x->tb, x->L, d_queries);
     const uint8_t* q = reinterpret_cast<const uint8_t*>(d_queries);
+    const SearchShape sh = shape ? *shape : search_shape(x, Q, k);
+    if (sh.fused) {
+        const unsigned fgrid = (unsigned)((Q + kSearchWarps - 1) / kSearchWarps);
+        if (x->N <= (1ll << 24))
+            LCP_TIMED_LAUNCH(k_topk_fused<uint32_t>, fgrid, kSearchWarps * 32, 0, s, ix, q, qf, Q, k, out_ids, out_lcp);
+        else
+            LCP_TIMED_LAUNCH(k_topk_fused<uint64_t>, fgrid, kSearchWarps * 32, 0, s, ix, q, qf, Q, k, out_ids, out_lcp);
+        return LCP_OK;
+    }
     // position records: the caller's buffer (a captured graph must not
     // allocate), else stream-ordered scratch
     QLoc* loc = reinterpret_cast<QLoc*>(loc_scratch);
     const bool own = loc == nullptr;
     if (own) LCP_CUDA_TRY(cudaMallocAsync((void**)&loc, search_scratch_bytes(Q), s));
-    const SearchShape sh = shape ? *shape : search_shape(x, Q, k);
     launch_locate(ix, q, qf, Q, loc, s, sh.locate_warp);
     const int qpw = sh.qpw;
     const int64_t warps = (Q + qpw - 1) / qpw;

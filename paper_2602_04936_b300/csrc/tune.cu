@@ -1,8 +1,8 @@
 // Autotuner for the indexed search's launch shape.
 //
-// The shape -- queries per warp of the answer kernel, and whether queries
-// are located one per lane or one per warp -- changes only the schedule,
-// never a result.  The tuner times every candidate on the caller's sample
+// The shape -- one fused kernel (a warp per query), or locate + answer +
+// fill with some queries per warp for the answer and queries located one per
+// lane or one per warp -- changes only the schedule, never a result.  The tuner times every candidate on the caller's sample
 // batch with CUDA events (one warm-up run, best of three) and records the
 // fastest in a process-wide table keyed by the index's shape class
 // (log2 N, L, token bytes) and the batch's (log2 Q, k class); later searches
@@ -60,9 +60,19 @@ int lcp_autotune(lcp_index_t x, const void* d_queries, int64_t Q, int32_t k, lcp
             }
         }
     }
+    if (rc == LCP_OK && !chosen.fused) {  // the fused kernel, for batches that use three by default
+        lcph::SearchShape sh;
+        sh.fused = 1;
+        float t = 0.f;
+        rc = time_shape(sh, &t);
+        if (rc == LCP_OK && t < top) {
+            top = t;
+            chosen = sh;
+        }
+    }
     if (rc == LCP_OK) {
         lcph::set_search_shape(x, Q, k, chosen);
-        best->qpw = chosen.qpw;
+        best->qpw = chosen.fused ? 0 : chosen.qpw;
         best->locate_warp = chosen.locate_warp;
         best->best_ms = top;
         best->default_ms = dflt;
@@ -76,10 +86,11 @@ int lcp_autotune(lcp_index_t x, const void* d_queries, int64_t Q, int32_t k, lcp
 }
 
 int lcp_set_search_shape(lcp_index_t x, int64_t Q, int32_t k, int32_t qpw, int32_t locate_warp) {
-    if (!x || Q < 1 || k < 1 || qpw < 1 || qpw > 32 || (locate_warp != 0 && locate_warp != 1))
+    if (!x || Q < 1 || k < 1 || qpw < 0 || qpw > 32 || (locate_warp != 0 && locate_warp != 1))
         return LCP_ERR_INVALID;
     lcph::SearchShape sh;
-    sh.qpw = qpw;
+    sh.fused = qpw == 0 ? 1 : 0;
+    sh.qpw = qpw == 0 ? 1 : qpw;
     sh.locate_warp = locate_warp;
     lcph::set_search_shape(x, Q, k, sh);
     return LCP_OK;

@@ -38,8 +38,12 @@ def host(a: np.ndarray) -> torch.Tensor:
     return torch.from_numpy(a)
 
 
-def indexed(lcp, S, Qs, k, max_k=None):
+def indexed(lcp, S, Qs, k, max_k=None, shape=None):
+    """Indexed search; `shape` = (qpw, locate_warp) forces a launch shape
+    (qpw 0: the fused kernel, else locate + answer + fill)."""
     idx = lcp.lcp_index_build(dev(S), max_k=max_k or max(k, 1))
+    if shape is not None and len(Qs):
+        lcp.lcp_set_search_shape(idx, len(Qs), k, shape[0], shape[1])
     ids, lc = lcp.lcp_topk_batch(idx, dev(Qs), k)
     torch.cuda.synchronize()
     assert lcp.lcp_index_sync(idx) == 0
@@ -118,7 +122,9 @@ def test_small_cases_indexed_and_scan_match_oracle(lcp, N, L, tb, sigma, k):
     S = _prefixy(rng, N, L, sigma, dt)
     Qs = _queries(rng, S, 300, sigma, dt)
     want = oracle.topk_batch(S, Qs, k)
-    assert_same(indexed(lcp, S, Qs, k), want, "indexed")
+    assert_same(indexed(lcp, S, Qs, k), want, "indexed")  # small batch: the fused kernel
+    assert_same(indexed(lcp, S, Qs, k, shape=(1, 1)), want, "indexed, three kernels")
+    assert_same(indexed(lcp, S, Qs, k, shape=(8, 0)), want, "indexed, three kernels, lane locate")
     assert_same(scan(lcp, S, Qs, k), want, "scan")
 
 

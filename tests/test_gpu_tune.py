@@ -33,12 +33,12 @@ def test_every_shape_same_answer_and_tuner(lcp):
     w_ids, w_lcp = oracle.topk_batch(S, Qs[:300], k)
     assert np.array_equal(base[0][:300].cpu().numpy(), w_ids) and np.array_equal(base[1][:300].cpu().numpy(), w_lcp)
     for lw in (0, 1):
-        for qpw in (1, 2, 4, 8, 16, 32):
+        for qpw in (0, 1, 2, 4, 8, 16, 32):  # 0: the fused kernel
             lcp.lcp_set_search_shape(idx, len(Qs), k, qpw, lw)
             got = lcp.lcp_topk_batch(idx, dq, k)
             assert torch.equal(got[0], base[0]) and torch.equal(got[1], base[1]), (qpw, lw)
     r = lcp.lcp_autotune(idx, dq, k)
-    assert r["qpw"] in (1, 2, 4, 8, 16, 32) and r["locate_warp"] in (0, 1)
+    assert r["qpw"] in (0, 1, 2, 4, 8, 16, 32) and r["locate_warp"] in (0, 1)
     assert 0 < r["best_ms"] <= r["default_ms"] * 1.0001
     got = lcp.lcp_topk_batch(idx, dq, k)
     assert torch.equal(got[0], base[0]) and torch.equal(got[1], base[1])
