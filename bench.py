@@ -623,8 +623,10 @@ def run_ours(args, world, rank, local):
         # per-batch latency (CUDA events around each call)
         lat = {"indexed": {}, "full_scan": {}}
         for bs, ri, rs in ((1, 1000, 100), (32, 1000, 50), (1024, 200, 10), (32768, 50, 3)):
-            for name, reps_, fn in (("indexed", ri, lambda q: lcp.lcp_topk_batch(idx, q, k)),
-                                    ("full_scan", rs, lambda q: lcp.lcp_scan_topk(dS, q, k))):
+            # outputs preallocated, as a serving caller would pass them
+            oi, ol = out_ids[:bs], out_lcp[:bs]
+            for name, reps_, fn in (("indexed", ri, lambda q: lcp.lcp_topk_batch(idx, q, k, oi, ol)),
+                                    ("full_scan", rs, lambda q: lcp.lcp_scan_topk(dS, q, k, oi, ol))):
                 times = []
                 for r in range(reps_ + 2):
                     off = (r * 7919 * bs) % (Q - bs)

@@ -203,6 +203,26 @@ def _fmt(t: torch.Tensor, vocab: int = 0) -> _Format:
     return _Format(_token_bytes(t), t.shape[1], vocab)
 
 
+class _NoSwitch:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+_NO_SWITCH = _NoSwitch()
+
+
+def _on(device):
+    """The device's context, entered only when it is not already current
+    (a device switch costs a few microseconds a call)."""
+    idx = device.index if isinstance(device, torch.device) else device
+    if idx is None or idx == torch.cuda.current_device():
+        return _NO_SWITCH
+    return torch.cuda.device(device)
+
+
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() else ctypes.c_void_p(0)
 
@@ -251,7 +271,7 @@ def lcp_index_build(tokens: torch.Tensor, max_k: int = LCP_INDEX_MAX_K, capacity
                     vocab: int = 0, stream=None) -> Index:
     tokens = _rows(tokens, device=True)
     h = ctypes.c_void_p()
-    with torch.cuda.device(tokens.device):
+    with _on(tokens.device):
         rc = _lib.lcp_index_build(_ptr(tokens), tokens.shape[0], _fmt(tokens, vocab), capacity, max_k,
                                   _stream(stream), ctypes.byref(h))
     _check(rc, "lcp_index_build")
@@ -263,7 +283,7 @@ def lcp_index_build_host(tokens: torch.Tensor, max_k: int = LCP_INDEX_MAX_K, cap
     tokens = _rows(tokens, device=False)
     h = ctypes.c_void_p()
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
-    with torch.cuda.device(dev):
+    with _on(dev):
         rc = _lib.lcp_index_build_host(_ptr(tokens), tokens.shape[0], _fmt(tokens, vocab), capacity,
                                        max_k, _stream(stream), ctypes.byref(h))
     _check(rc, "lcp_index_build_host")
@@ -274,7 +294,7 @@ def lcp_index_insert(index: Index, tokens: torch.Tensor, stream=None) -> None:
     tokens = _rows(tokens, device=True)
     if tokens.shape[1] != index.L or _token_bytes(tokens) != index.token_bytes:
         raise ValueError("insert batch format differs from the index")
-    with torch.cuda.device(tokens.device):
+    with _on(tokens.device):
         _check(_lib.lcp_index_insert(index.handle, _ptr(tokens), tokens.shape[0], _stream(stream)),
                "lcp_index_insert")
 
@@ -300,7 +320,7 @@ def lcp_topk_batch(index: Index, queries: torch.Tensor, k: int, out_ids=None, ou
         raise ValueError("query format differs from the index")
     Q = queries.shape[0]
     out_ids, out_lcp = _outputs(Q, k, queries.device, out_ids, out_lcp)
-    with torch.cuda.device(queries.device):
+    with _on(queries.device):
         _check(_lib.lcp_topk_batch(index.handle, _ptr(queries), Q, k, _ptr(out_ids), _ptr(out_lcp),
                                    _stream(stream)), "lcp_topk_batch")
     return out_ids, out_lcp
@@ -311,7 +331,7 @@ def lcp_topk_batch_host(index: Index, queries: torch.Tensor, k: int, out_ids=Non
     queries = _rows(queries, device=False)
     Q = queries.shape[0]
     out_ids, out_lcp = _outputs(Q, k, "cpu", out_ids, out_lcp, pin=False)
-    with torch.cuda.device(index.device):
+    with _on(index.device):
         _check(_lib.lcp_topk_batch_host(index.handle, _ptr(queries), Q, k, _ptr(out_ids),
                                         _ptr(out_lcp), _stream(stream)), "lcp_topk_batch_host")
     return out_ids, out_lcp
@@ -325,7 +345,7 @@ def lcp_scan_topk(tokens: torch.Tensor, queries: torch.Tensor, k: int, out_ids=N
         raise ValueError("query format differs from the tokens")
     Q = queries.shape[0]
     out_ids, out_lcp = _outputs(Q, k, queries.device, out_ids, out_lcp)
-    with torch.cuda.device(queries.device):
+    with _on(queries.device):
         _check(_lib.lcp_scan_topk(_ptr(tokens), tokens.shape[0], _fmt(tokens, vocab), _ptr(queries), Q,
                                   k, _ptr(out_ids), _ptr(out_lcp), _stream(stream)), "lcp_scan_topk")
     return out_ids, out_lcp
@@ -339,7 +359,7 @@ def lcp_scan_topk_noalloc(tokens: torch.Tensor, queries: torch.Tensor, k: int, o
     queries = _rows(queries, device=True)
     Q = queries.shape[0]
     out_ids, out_lcp = _outputs(Q, k, queries.device, out_ids, out_lcp)
-    with torch.cuda.device(queries.device):
+    with _on(queries.device):
         _check(_lib.lcp_scan_topk_noalloc(_ptr(tokens), tokens.shape[0], _fmt(tokens, vocab),
                                           _ptr(queries), Q, k, _ptr(out_ids), _ptr(out_lcp),
                                           _stream(stream)), "lcp_scan_topk_noalloc")
@@ -351,7 +371,7 @@ def lcp_index_export(index: Index, stream=None):
     n = index.N
     ids = torch.empty(n, dtype=torch.int32, device=index.device)
     H = torch.empty(n, dtype=torch.uint8, device=index.device)
-    with torch.cuda.device(index.device):
+    with _on(index.device):
         _check(_lib.lcp_index_export(index.handle, _ptr(ids), _ptr(H), _stream(stream)),
                "lcp_index_export")
     return ids, H
@@ -407,7 +427,7 @@ def lcp_autotune(index: "Index", queries: torch.Tensor, k: int, stream=None) -> 
     fastest for batches of the same class (see lcp.h)."""
     q = _rows(queries, True)
     r = TuneResult()
-    with torch.cuda.device(q.device):
+    with _on(q.device):
         _check(_lib.lcp_autotune(index.handle, _ptr(q), q.shape[0], k, _stream(stream), ctypes.byref(r)),
                "lcp_autotune")
     return {"qpw": r.qpw, "locate_warp": r.locate_warp, "best_ms": r.best_ms, "default_ms": r.default_ms}
@@ -424,7 +444,7 @@ def lcp_topk_bfs(index: "Index", queries: torch.Tensor, k: int, out_ids=None, ou
     if q.shape[1] != index.L or _token_bytes(q) != index.token_bytes:
         raise ValueError("query format differs from the index")
     out_ids, out_lcp = _outputs(q.shape[0], k, q.device, out_ids, out_lcp)
-    with torch.cuda.device(q.device):
+    with _on(q.device):
         _check(_lib.lcp_topk_bfs(index.handle, _ptr(q), q.shape[0], k, _ptr(out_ids), _ptr(out_lcp),
                                  _stream(stream)), "lcp_topk_bfs")
     return out_ids, out_lcp
@@ -438,7 +458,7 @@ def lcp_tal_topk(index: "Index", queries: torch.Tensor, k: int, depth: int, out_
     if q.shape[1] != index.L or _token_bytes(q) != index.token_bytes:
         raise ValueError("query format differs from the index")
     out_ids, out_lcp = _outputs(q.shape[0], k, q.device, out_ids, out_lcp)
-    with torch.cuda.device(q.device):
+    with _on(q.device):
         _check(_lib.lcp_tal_topk(index.handle, _ptr(q), q.shape[0], k, depth, _ptr(out_ids), _ptr(out_lcp),
                                  _stream(stream)), "lcp_tal_topk")
     return out_ids, out_lcp
@@ -457,7 +477,7 @@ def lcp_shard_merge(ids: torch.Tensor, lcp: torch.Tensor, bases, out_ids=None, o
         raise ValueError("one base per shard")
     hb = (ctypes.c_int64 * P)(*[int(b) for b in bases])
     out_ids, out_lcp = _outputs(Q, k, ids.device, out_ids, out_lcp)
-    with torch.cuda.device(ids.device):
+    with _on(ids.device):
         _check(_lib.lcp_shard_merge(_ptr(ids.contiguous()), _ptr(lcp.contiguous()), P, hb, Q, k,
                                     _ptr(out_ids), _ptr(out_lcp), _stream(stream)), "lcp_shard_merge")
     return out_ids, out_lcp
@@ -534,12 +554,12 @@ class Step:
     def __init__(self, index: "Index", n: int, Q: int, k: int):
         self._h = ctypes.c_void_p()
         self.index, self.n, self.Q, self.k = index, n, Q, k
-        with torch.cuda.device(index.device):
+        with _on(index.device):
             _check(_lib.lcp_step_create(index.handle, n, Q, k, ctypes.byref(self._h)), "lcp_step_create")
 
     def run(self, inserts: torch.Tensor, queries: torch.Tensor, out_ids=None, out_lcp=None, stream=None):
         out_ids, out_lcp = _outputs(self.Q, self.k, queries.device, out_ids, out_lcp)
-        with torch.cuda.device(queries.device):
+        with _on(queries.device):
             _check(_lib.lcp_step_run(self._h, _ptr(inserts.contiguous()), _ptr(queries.contiguous()),
                                      _ptr(out_ids), _ptr(out_lcp), _stream(stream)), "lcp_step_run")
         return out_ids, out_lcp
