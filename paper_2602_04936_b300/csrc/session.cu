@@ -49,6 +49,7 @@ struct lcp_session_s {
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> spare_events;
     std::deque<uint64_t> pending;
+    std::vector<uint64_t> inflight;  // tickets on the GPU (at most max_inflight)
     std::unordered_map<uint64_t, Req> reqs;
     uint64_t next_ticket = 1;
     int rr = 0;
@@ -108,18 +109,28 @@ void finish(lcp_session_s* s, Req& r, int state, int rc) {
 }
 
 // Retires finished requests (if `retire`) and admits waiting ones (lock held).
-// Dry-run requests finish when retired, i.e. on the next poll.
+// Only the requests on the GPU are looked at (one event query each), so a
+// pump costs at most max_inflight queries however many requests wait or
+// await their poll.  Dry-run requests finish when retired, i.e. on the next
+// poll.
 void pump(lcp_session_s* s, bool retire = true) {
-    for (auto& kv : s->reqs) {
-        Req& r = kv.second;
-        if (!retire || r.state != kInflight) continue;
+    for (size_t i = 0; retire && i < s->inflight.size();) {
+        Req& r = s->reqs[s->inflight[i]];
+        bool gone = true;
         if (s->cfg.dry_run) {
             finish(s, r, kDone, LCP_OK);
-            continue;
+        } else {
+            cudaError_t e = cudaEventQuery(r.ev);
+            if (e == cudaSuccess) finish(s, r, kDone, LCP_OK);
+            else if (e != cudaErrorNotReady) finish(s, r, kFailed, lcph::cuda_status(e));
+            else gone = false;
         }
-        cudaError_t e = cudaEventQuery(r.ev);
-        if (e == cudaSuccess) finish(s, r, kDone, LCP_OK);
-        else if (e != cudaErrorNotReady) finish(s, r, kFailed, lcph::cuda_status(e));
+        if (gone) {
+            s->inflight[i] = s->inflight.back();
+            s->inflight.pop_back();
+        } else {
+            ++i;
+        }
     }
     while (!s->pending.empty()) {
         auto it = s->reqs.find(s->pending.front());
@@ -129,6 +140,7 @@ void pump(lcp_session_s* s, bool retire = true) {
         }
         Req& r = it->second;
         if (s->st.inflight >= s->cfg.max_inflight || s->st.mem_in_use + r.bytes > s->cfg.mem_budget) break;
+        const uint64_t ticket = s->pending.front();
         s->pending.pop_front();
         s->st.pending--;
         r.state = kInflight;
@@ -140,6 +152,7 @@ void pump(lcp_session_s* s, bool retire = true) {
         if (s->st.mem_in_use > s->st.mem_peak) s->st.mem_peak = s->st.mem_in_use;
         int rc = launch(s, r);
         if (rc != LCP_OK) finish(s, r, kFailed, rc);
+        else s->inflight.push_back(ticket);
     }
 }
 
@@ -166,6 +179,16 @@ int lcp_session_create(const lcp_session_cfg_t* cfg, lcp_session_t* out) {
                 return lcph::cuda_status(e);
             }
             s->streams.push_back(st);
+        }
+        // Requests allocate their buffers stream-ordered from the device's
+        // pool; reserving the whole budget in the pool once (the pool keeps
+        // freed memory) spares the requests the pool's growth on the way.
+        void* warm = nullptr;
+        if (cudaMallocAsync(&warm, (size_t)cfg->mem_budget, s->streams[0]) == cudaSuccess) {
+            cudaFreeAsync(warm, s->streams[0]);
+            cudaStreamSynchronize(s->streams[0]);
+        } else {
+            cudaGetLastError();  // a budget larger than free memory: nothing reserved
         }
     }
     *out = s;
@@ -310,18 +333,32 @@ int lcp_session_replay(lcp_session_t s, const lcp_replay_req_t* reqs, int64_t n,
             ++next;
             progress = true;
         }
-        for (auto it = out.begin(); it != out.end();) {
-            const int rc = lcp_session_poll(s, it->first, 0);
-            if (rc == LCP_PENDING) {
-                ++it;
-                continue;
+        // one pump, then the outstanding requests' states (a poll per
+        // request would pump once each)
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (!s->cfg.dry_run) cudaSetDevice(s->device);
+            pump(s);
+            double t = -1.0;
+            for (auto it = out.begin(); it != out.end();) {
+                auto rit = s->reqs.find(it->first);
+                int rc = LCP_ERR_INVALID;
+                if (rit != s->reqs.end()) {
+                    const int state = rit->second.state;
+                    if (state != kDone && state != kFailed && state != kCancelled) {
+                        ++it;
+                        continue;
+                    }
+                    rc = state == kDone ? LCP_OK : (state == kCancelled ? LCP_ERR_STATE : rit->second.rc);
+                    s->reqs.erase(rit);
+                }
+                if (t < 0) t = now_s();
+                latency_s[it->second] = rc == LCP_OK ? t - reqs[it->second].arrival_s : -1.0;
+                if (t > last_done) last_done = t;
+                if (rc != LCP_OK && rc_all == LCP_OK) rc_all = rc;
+                it = out.erase(it);
+                progress = true;
             }
-            const double t = now_s();
-            latency_s[it->second] = rc == LCP_OK ? t - reqs[it->second].arrival_s : -1.0;
-            if (t > last_done) last_done = t;
-            if (rc != LCP_OK && rc_all == LCP_OK) rc_all = rc;
-            it = out.erase(it);
-            progress = true;
         }
         if (!progress) std::this_thread::yield();
     }
