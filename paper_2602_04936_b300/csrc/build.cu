@@ -1,15 +1,25 @@
 // Index build: Algorithm 1 (BuildLCPIndex) + Algorithm 2 in array form.
 //
-// Sorting N rows of W packed words (up to 64 words = 512 bytes each) with a
-// plain LSD sort would take 8*W digit passes over all N keys.  Instead the
-// sort refines word by word: round 0 sorts (word 0, id) pairs of every row
-// with the onesweep radix sort; only rows whose word-0 prefix is shared by
-// another row stay "active", and round r sorts the active rows by (tie group,
-// word r) -- a stable LSD sort on word r followed by one on the group rank.
-// Rows leave as soon as their prefix is unique, so on the paper's workloads
-// (Zipf-shared prefixes, first differences within a few tokens) almost all
-// of the work is round 0.  Stability of every pass keeps equal rows in id
-// order, which is the posting-list order of Algorithm 1.
+// 1. Keys: word 0 of every row with its id (the load asks L2 for 64 bytes:
+//    only 8 bytes of each row are needed here).
+// 2. A stable LSD radix sort of the (word 0, id) pairs: 8-bit digits,
+//    reduce-then-scan passes (sort.cu).
+// 3. Rows sharing word 0 with another row form tie groups, found straight
+//    from the equality flags of the sorted keys: a group of at most 32 rows
+//    is ranked by a warp, one of 33-512 rows by a CTA, on word 1 and -- only
+//    for rows tied there -- the later words, then the id.  Groups of more
+//    than 512 rows (heavy duplication; none on the paper's workloads) take
+//    the exact refinement instead: round r sorts the still-tied rows by
+//    (tie group, word r), a stable LSD sort on word r followed by one on the
+//    group rank, until every prefix is unique.
+// 4. The rows are gathered into sorted order with their heads and H, the LCP
+//    of each row with the one before it (Algorithm 2's subtree sizes become
+//    LCP intervals of H).
+// 5. The search's tables: pos, the depth-1 buckets, the min tree over H, the
+//    sorted 128-row blocks and the sparse table of their K smallest ids (on
+//    two stream branches), then the heavy trie nodes' tie lists (tielists.cu).
+// Every pass is stable, so equal rows stay in id order: the posting-list
+// order of Algorithm 1.
 #include "search.cuh"
 #include "sort.cuh"
 
