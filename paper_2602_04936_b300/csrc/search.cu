@@ -1,10 +1,11 @@
 // Indexed batched top-k (Algorithm 3 + CollectTopK / CollectTopKOptimized,
 // returning the order of the Definition "Top-k LCP Retrieval").
 //
-// Three kernels per batch, with small per-query records between them (one
-// fused kernel stalled on instruction fetch):
+// Three kernels per large batch, with small per-query records between them
+// (one fused kernel stalled on instruction fetch there):
 //   locate  the insertion point p of each query (first row >= q) and its
-//           LCPs lL, lR with rows p-1 and p: one lane per query over the
+//           LCPs lL, lR with rows p-1 and p, searched inside the depth-1
+//           bucket of q's first token: one lane per query over the
 //           L2-resident head array (word 0 of every sorted row) for large
 //           batches, one warp per query with a 33-way search for small ones.
 //           max(lL, lR) is the descent depth of Algorithm 3.
@@ -22,7 +23,8 @@
 //           interval outside A, in ascending id order (an id-order probe, a
 //           heavy trie node's precomputed list, or two sparse-table lists
 //           and two partial blocks), then padding, into slots [|A|, k).
-// The persistent work-queue worker runs the same stages per query.
+// Batches of up to 4,096 queries run the same stages per query in one fused
+// kernel (a warp per query), as does the persistent work-queue worker.
 #include <cuda/atomic>
 
 #include <map>
