@@ -212,6 +212,29 @@ def test_zipf2m_L64_full_size(lcp):
     _sampled(lcp, "zipf2m_L64", 300)
 
 
+def test_index_past_2_pow_24_rows(lcp):
+    """An index of more than 2^24 rows takes the searches' 64-bit sort keys
+    (24 bits no longer hold an id): the fused small-batch kernel and the
+    three-kernel path, both against the oracle on dense duplicates and ties."""
+    N, L, k = (1 << 24) + 300_000, 6, 20
+    rng = np.random.default_rng(24)
+    S = rng.integers(0, 16, size=(N, L)).astype(np.uint8)  # 16^6 ~ N: many duplicate rows
+    Qs = np.concatenate([S[rng.integers(0, N, 3000)], rng.integers(0, 16, size=(3000, L)).astype(np.uint8)])
+    Qs[::7, 3:] = rng.integers(0, 16, size=(len(Qs[::7]), L - 3))
+    idx = lcp.lcp_index_build(dev(S), max_k=k)
+    small = lcp.lcp_topk_batch(idx, dev(Qs[:64]), k)      # fused kernel
+    large = lcp.lcp_topk_batch(idx, dev(Qs), k)           # locate + answer + fill
+    torch.cuda.synchronize()
+    assert lcp.lcp_index_sync(idx) == 0
+    idx.close()
+    want = oracle.topk_batch(S, Qs[:64], k)
+    assert_same((small[0].cpu().numpy(), small[1].cpu().numpy()), want, "fused, N > 2^24")
+    pick = np.sort(rng.choice(len(Qs), 64, replace=False))
+    want = oracle.topk_batch(S, Qs[pick], k)
+    got = large[0].cpu().numpy()[pick], large[1].cpu().numpy()[pick]
+    assert_same(got, want, "three kernels, N > 2^24")
+
+
 def test_insert_equals_rebuild_and_answers(lcp):
     """GNC stream: merge-insert 1,000 readings per step into an index that
     grows from empty; after every step the sorted order and H equal a fresh
