@@ -556,16 +556,23 @@ __device__ __forceinline__ void st_store(uint32_t* __restrict__ p, const uint32_
 // (levels j .. j+g-1 at i).  Spines of other start blocks are recomputed,
 // not shared: 2^G - 1 merges for g levels and g - 1 fewer launches.  P start
 // blocks per warp, all loads issued before any merge.
+constexpr int kStRegsMaxG = 4;  // levels per launch of the register merge, at most
+
+struct StValid {
+    int64_t v[kStRegsMaxG];  // start blocks of each level of the launch
+};
+
 template <int E, int G, int P>
 __global__ void __launch_bounds__(256) k_st_levels_regs(const uint32_t* __restrict__ prev, int64_t prev_stride,
                                                         int64_t prev_valid, int64_t half, int g,
-                                                        int64_t level_stride, int64_t valid0, int64_t valid1,
-                                                        int64_t valid2, uint32_t* __restrict__ out0) {
+                                                        int64_t level_stride, StValid vb,
+                                                        uint32_t* __restrict__ out0) {
+    static_assert(G <= kStRegsMaxG, "levels per launch");
     constexpr int K = 32 * E, M = 1 << G;
     const unsigned lane = lane_id();
     const int64_t i0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * P;
+    const int64_t valid0 = vb.v[0];
     if (i0 >= valid0) return;  // warp-uniform
-    const int64_t valid[3] = {valid0, valid1, valid2};
     uint32_t v[P][M][E];
 #pragma unroll
     for (int q = 0; q < P; ++q) {
@@ -597,7 +604,7 @@ __global__ void __launch_bounds__(256) k_st_levels_regs(const uint32_t* __restri
 #pragma unroll
                 for (int e = 0; e < E; ++e) v[q][m][e] = t[e];
             }
-            if (r < g && i < valid[r]) st_store<E>(out0 + r * level_stride + i * K + lane * E, v[q][0]);
+            if (r < g && i < vb.v[r]) st_store<E>(out0 + r * level_stride + i * K + lane * E, v[q][0]);
         }
     }
 }
@@ -876,22 +883,22 @@ static int build_sparse_table(lcp_index_s* x, int64_t nblk, cudaStream_t s) {
             int g = 1;
             while (g < G && j + g <= x->st_levels_cap && (1ll << (j + g)) <= nblk) ++g;
             const int64_t half = 1ll << (j - 1);
-            int64_t valid[3] = {0, 0, 0};
-            for (int r = 0; r < g; ++r) valid[r] = nblk - (1ll << (j + r)) + 1;
+            StValid vb = {};
+            for (int r = 0; r < g; ++r) vb.v[r] = nblk - (1ll << (j + r)) + 1;
             const int64_t prev_valid = nblk - half + 1;  // level j-1 (level 0: the blocks)
             const uint32_t* prev = j == 1 ? x->sblk : x->st + (int64_t)(j - 2) * lstride;
             const int64_t pstride = j == 1 ? kBlk : K;
             uint32_t* out = x->st + (int64_t)(j - 1) * lstride;
-            const unsigned grid = blocks_for((valid[0] + P - 1) / P * 32, 256);
+            const unsigned grid = blocks_for((vb.v[0] + P - 1) / P * 32, 256);
             if (E == 1)
                 LCP_TIMED_LAUNCH((k_st_levels_regs<1, StRegsShape<1>::G, StRegsShape<1>::P>), grid, 256, 0, s, prev,
-                                 pstride, prev_valid, half, g, lstride, valid[0], valid[1], valid[2], out);
+                                 pstride, prev_valid, half, g, lstride, vb, out);
             else if (E == 2)
                 LCP_TIMED_LAUNCH((k_st_levels_regs<2, StRegsShape<2>::G, StRegsShape<2>::P>), grid, 256, 0, s, prev,
-                                 pstride, prev_valid, half, g, lstride, valid[0], valid[1], valid[2], out);
+                                 pstride, prev_valid, half, g, lstride, vb, out);
             else
                 LCP_TIMED_LAUNCH((k_st_levels_regs<4, StRegsShape<4>::G, StRegsShape<4>::P>), grid, 256, 0, s, prev,
-                                 pstride, prev_valid, half, g, lstride, valid[0], valid[1], valid[2], out);
+                                 pstride, prev_valid, half, g, lstride, vb, out);
             j += g;
         }
         return LCP_OK;
