@@ -101,7 +101,11 @@ LCP_API int lcp_index_build(const void* d_tokens, int64_t N, lcp_format_t fmt, i
                     int32_t max_k, lcp_stream_t stream, lcp_index_t* out);
 
 /* Same, with the tokens in host memory; the host-to-device copy is part of
- * the call.  Returns after the build has been enqueued and the tokens copied. */
+ * the call, enqueued on `stream` before the build.  From pinned memory the
+ * copy is asynchronous: keep h_tokens unchanged until the stream has passed
+ * it (lcp_index_sync or a stream synchronise); pageable memory is copied
+ * before the call returns.  The call's input copy follows this thread's
+ * earlier host-buffer input copies on the link (see lcp_topk_batch_host). */
 LCP_API int lcp_index_build_host(const void* h_tokens, int64_t N, lcp_format_t fmt, int64_t capacity,
                          int32_t max_k, lcp_stream_t stream, lcp_index_t* out);
 
@@ -137,7 +141,14 @@ LCP_API int lcp_topk_batch(lcp_index_t index, const void* d_queries, int64_t Q, 
                    int32_t* d_out_ids, uint8_t* d_out_lcp, lcp_stream_t stream);
 
 /* Same, with host queries and host outputs; the copies in both directions
- * are part of the call, which returns when the results are in host memory. */
+ * are part of the call, which returns when the results are in host memory.
+ * Large batches are copied, searched and copied back in chunks on two copy
+ * streams beside `stream`.  The device staging for queries and results, the
+ * copy streams and their events are kept per calling thread and device and
+ * reused by later calls (the staging grows to the largest batch and is not
+ * released).  A call's query copies wait only for this thread's previous
+ * host-buffer input copies (not for the whole of `stream`), so they can
+ * overlap a build enqueued just before. */
 LCP_API int lcp_topk_batch_host(lcp_index_t index, const void* h_queries, int64_t Q, int32_t k,
                         int32_t* h_out_ids, uint8_t* h_out_lcp, lcp_stream_t stream);
 
