@@ -193,7 +193,14 @@ __global__ void __launch_bounds__(256) k_topk_locate(DevIndex ix, const uint8_t*
     const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (qi >= Q) return;
     const uint8_t* qrow = row_of(queries, qi, qf);
-    const uint64_t q0 = pack_word(qrow, 0, qf);
+    // word 0 alone decides most queries: ask L2 for 64 bytes, not the row
+    uint64_t q0;
+    if (qf.aligned8) {
+        asm("ld.global.nc.L2::64B.u64 %0, [%1];" : "=l"(q0) : "l"(qrow));
+        q0 = msb_first(q0, qf.tb);
+    } else {
+        q0 = pack_word(qrow, 0, qf);
+    }
     int64_t p;
     int lL, lR;
     lane_locate(ix, qrow, qf, q0, &p, &lL, &lR);
