@@ -60,6 +60,16 @@ def parse_args():
     return ap.parse_args()
 
 
+def workload_data(name, Q, rank=0):
+    """(rows, queries) of a static workload; rank > 0 draws its own queries."""
+    w = W.WORKLOADS[name]
+    if name == "tree16_u8":
+        S = W.tree_rows(w["N"], w["seed"], L=w["L"])
+        return S, W.tree_queries(S, Q, w["seed"], item_offset=rank * Q)
+    S = W.zipf_prefix_rows(w["N"], w["L"], w["vocab"], w["s"], w["seed"])
+    return S, W.zipf_prefix_queries(S, Q, w["vocab"], w["s"], w["seed"], item_offset=rank * Q)
+
+
 def config_of(name):
     w = W.WORKLOADS[name]
     return {"workload": name, "N": w["N"], "L": w["L"],
@@ -67,7 +77,10 @@ def config_of(name):
             "zipf_s": w.get("s"), "Q": w["Q"], "k": w["k"], "seed": w["seed"],
             "query_mix": "50% stored copies with suffix re-drawn from a uniform cut, 50% fresh",
             "step": "index build from resident tokens + indexed top-k of all Q queries",
-            "l2": "no flush: inputs larger than L2 (tokens %d MB, queries %d MB)" % (
+            "l2": ("no flush: inputs larger than L2 (tokens %d MB, queries %d MB)"
+                   if w["N"] * w["L"] * w["token_bytes"] > (126 << 20) else
+                   "inputs fit in the 126 MB L2 (tokens %d MB, queries %d MB): timed L2-warm, "
+                   "not a headline configuration") % (
                 w["N"] * w["L"] * w["token_bytes"] >> 20, w["Q"] * w["L"] * w["token_bytes"] >> 20)}
 
 
@@ -461,9 +474,8 @@ def run_ours(args, world, rank, local):
     if args.queries:
         Q = args.queries
         cfg["Q"] = Q
-    S = W.zipf_prefix_rows(N, L, w["vocab"], w["s"], w["seed"])
     # weak scaling: every rank answers its own query batch against a full replica
-    Qs = W.zipf_prefix_queries(S, Q, w["vocab"], w["s"], w["seed"], item_offset=rank * Q)
+    S, Qs = workload_data(args.workload, Q, rank)
     dS, dQ = to_dev(S, device), to_dev(Qs, device)
     out_ids = torch.empty((Q, k), dtype=torch.int32, device=device)
     out_lcp = torch.empty((Q, k), dtype=torch.uint8, device=device)
@@ -524,6 +536,7 @@ def run_ours(args, world, rank, local):
     ans_ms, ans_n = lcp.lcp_kernel_time("k_topk_answer")
     loc_ms, loc_n = lcp.lcp_kernel_time("k_topk_locate")
     fill_ms, fill_n = lcp.lcp_kernel_time("k_topk_fill")
+    fused_ms, fused_n = lcp.lcp_kernel_time("k_topk_fused")
     lcp.lcp_kernel_timing(False)
     lcp.lcp_kernel_timing_filter("")
     barrier(world)
@@ -541,29 +554,44 @@ def run_ours(args, world, rank, local):
     # roofline of the dominant kernel: the answer half of the indexed search
     peak, peak_kind = measured_peaks()
     sms = torch.cuda.get_device_properties(device).multi_processor_count
-    ans_launch_ms = ans_ms / max(ans_n, 1)
-    loc_launch_ms = loc_ms / max(loc_n, 1)
-    per_q = answer_algorithmic_bytes(k)
-    achieved = Q * per_q / (ans_launch_ms / 1e3) / 1e9
     loc_per_q = locate_algorithmic_bytes(S, Qs)
-    loc_achieved = Q * loc_per_q / (loc_launch_ms / 1e3) / 1e9
-    roofline = {"kernel": "k_topk_answer", "bound": "hbm", "achieved": round(achieved, 1),
-                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-                else "fallback 6.4 TB/s",
-                "traffic": committed_traffic("k_topk_answer", Q),
-                "algorithmic_bytes_per_launch": Q * per_q, "bytes_per_query": per_q,
-                "launch_ms": round(ans_launch_ms, 4), "launches_timed": ans_n,
-                "timing": "CUDA events around each launch on its stream, timed region",
-                "issue": issue_roofline("k_topk_answer", Q, ans_launch_ms, clocks.get("sm_mhz"), sms),
-                "other_kernels": {"k_topk_locate": {
-                    "launch_ms": round(loc_launch_ms, 4), "bytes_per_query": loc_per_q,
-                    "achieved": round(loc_achieved, 1), "frac": round(loc_achieved / peak, 4)},
-                    "k_topk_fill": {
-                    "launch_ms": round(fill_ms / max(fill_n, 1), 4), "bytes_per_query": fill_algorithmic_bytes(k),
-                    "achieved": round(Q * fill_algorithmic_bytes(k) / (fill_ms / max(fill_n, 1) / 1e3) / 1e9, 1),
-                    "frac": round(Q * fill_algorithmic_bytes(k) / (fill_ms / max(fill_n, 1) / 1e3) / 1e9 / peak, 4),
-                    "issue": issue_roofline("k_topk_fill", Q, fill_ms / max(fill_n, 1), clocks.get("sm_mhz"), sms)}}}
+    peak_source = (peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                   else "fallback 6.4 TB/s")
+    timing = "CUDA events around each launch on its stream, timed region"
+    if ans_n:
+        ans_launch_ms = ans_ms / ans_n
+        loc_launch_ms = loc_ms / max(loc_n, 1)
+        fill_launch_ms = fill_ms / max(fill_n, 1)
+        per_q = answer_algorithmic_bytes(k)
+        achieved = Q * per_q / (ans_launch_ms / 1e3) / 1e9
+        loc_achieved = Q * loc_per_q / (loc_launch_ms / 1e3) / 1e9
+        fill_achieved = Q * fill_algorithmic_bytes(k) / (fill_launch_ms / 1e3) / 1e9
+        roofline = {"kernel": "k_topk_answer", "bound": "hbm", "achieved": round(achieved, 1),
+                    "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                    "peak_source": peak_source,
+                    "traffic": committed_traffic("k_topk_answer", Q),
+                    "algorithmic_bytes_per_launch": Q * per_q, "bytes_per_query": per_q,
+                    "launch_ms": round(ans_launch_ms, 4), "launches_timed": ans_n, "timing": timing,
+                    "issue": issue_roofline("k_topk_answer", Q, ans_launch_ms, clocks.get("sm_mhz"), sms),
+                    "other_kernels": {
+                        "k_topk_locate": {"launch_ms": round(loc_launch_ms, 4), "bytes_per_query": loc_per_q,
+                                          "achieved": round(loc_achieved, 1), "frac": round(loc_achieved / peak, 4)},
+                        "k_topk_fill": {"launch_ms": round(fill_launch_ms, 4),
+                                        "bytes_per_query": fill_algorithmic_bytes(k),
+                                        "achieved": round(fill_achieved, 1), "frac": round(fill_achieved / peak, 4),
+                                        "issue": issue_roofline("k_topk_fill", Q, fill_launch_ms,
+                                                                clocks.get("sm_mhz"), sms)}}}
+    else:
+        # small batches run as one fused kernel: the three halves' bytes
+        fused_launch_ms = fused_ms / max(fused_n, 1)
+        per_q = loc_per_q + answer_algorithmic_bytes(k) + fill_algorithmic_bytes(k)
+        achieved = Q * per_q / (fused_launch_ms / 1e3) / 1e9 if fused_n else 0.0
+        roofline = {"kernel": "k_topk_fused", "bound": "hbm", "achieved": round(achieved, 1),
+                    "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                    "peak_source": peak_source, "traffic": None,
+                    "algorithmic_bytes_per_launch": Q * per_q, "bytes_per_query": per_q,
+                    "launch_ms": round(fused_launch_ms, 4), "launches_timed": fused_n, "timing": timing,
+                    "note": "batch of at most 4,096 queries: locate, answer and fill in one kernel"}
 
     # energy: NVML's counter advances in coarse steps, so each figure comes
     # from its own loop of a couple of seconds (idle gaps excluded)
@@ -931,8 +959,7 @@ def run_reference(args, world, rank):
     cfg = config_of(args.workload)
     w = W.WORKLOADS[args.workload]
     N, L, Q, k = w["N"], w["L"], w["Q"], w["k"]
-    S = W.zipf_prefix_rows(N, L, w["vocab"], w["s"], w["seed"])
-    Qs = W.zipf_prefix_queries(S, Q, w["vocab"], w["s"], w["seed"])
+    S, Qs = workload_data(args.workload, Q)
     threads = os.cpu_count() or 1
     # calibrate the per-step sample so that warmup + steps take ~2 minutes
     t0 = time.perf_counter()
@@ -969,8 +996,7 @@ def run_profile(args):
     if args.profile == "search":
         w = W.WORKLOADS[args.workload]
         Q = args.queries or 100_000
-        S = W.zipf_prefix_rows(w["N"], w["L"], w["vocab"], w["s"], w["seed"])
-        Qs = W.zipf_prefix_queries(S, Q, w["vocab"], w["s"], w["seed"])
+        S, Qs = workload_data(args.workload, Q)
         idx = lcp.lcp_index_build(to_dev(S, device), max_k=w["k"])
         dQ = to_dev(Qs, device)
         for _ in range(2):

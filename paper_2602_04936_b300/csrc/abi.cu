@@ -423,9 +423,8 @@ int lcp_index_build(const void* d_tokens, int64_t N, lcp_format_t fmt, int64_t c
         if (g != LCP_PENDING) rc = g;  // LCP_PENDING: not graph-capturable here, build below
     }
     if (rc == LCP_OK && N > 0) {
-        // Issued without waiting for the device.  Rows tied on their first
-        // two words in groups of more than 512 need the exact (host-driven)
-        // refinement; their count lands in pinned memory behind an event
+        // Issued without waiting for the device.  Rows tied on word 0 in
+        // groups of more than 2048 need the exact (host-driven) refinement; their count lands in pinned memory behind an event
         // recorded mid-build, checked once everything is queued -- by then
         // the device is usually past it, so the host returns while the
         // device still runs the tail of the build.  A nonzero count (rare:

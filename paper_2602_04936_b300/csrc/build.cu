@@ -6,9 +6,10 @@
 //    reduce-then-scan passes (sort.cu).
 // 3. Rows sharing word 0 with another row form tie groups, found straight
 //    from the equality flags of the sorted keys: a group of at most 32 rows
-//    is ranked by a warp, one of 33-512 rows by a CTA, on word 1 and -- only
+//    is ranked by a warp, one of 33-2048 rows by a CTA, on word 1 and -- only
 //    for rows tied there -- the later words, then the id.  Groups of more
-//    than 512 rows (heavy duplication; none on the paper's workloads) take
+//    than 2048 rows, or with a row tied on word 1 with more than 64 others (heavy
+//    duplication; none on the paper's workloads) take
 //    the exact refinement instead: round r sorts the still-tied rows by
 //    (tie group, word r), a stable LSD sort on word r followed by one on the
 //    group rank, until every prefix is unique.
@@ -128,11 +129,13 @@ __device__ __forceinline__ bool tie_less(const uint8_t* __restrict__ tokens, con
     return row_less(tokens, f, 2, a, b);  // rare: equal on word 1 too
 }
 
+constexpr uint32_t kMidMax = 2048;  // largest tie group ranked by one CTA
+
 // Rows tied on word 0, found straight from eq: a warp takes 32 consecutive
 // sorted positions and handles each tie group that starts among them.  A
 // group of at most 32 rows is ranked in registers (word 1 loaded once per row,
 // shuffles; later words and then ids only for rows tied on word 1) and
-// written back in order; groups of 33..512 rows are listed for
+// written back in order; groups of 33..kMidMax rows are listed for
 // k_group_sort_mid; the rows of larger groups are counted for the exact
 // refinement.
 __global__ void __launch_bounds__(256) k_group_scan_sort(const uint8_t* __restrict__ tokens, RowFmt f,
@@ -163,7 +166,7 @@ __global__ void __launch_bounds__(256) k_group_scan_sort(const uint8_t* __restri
             }
             if (len > 32) {
                 if (lane == 0) {
-                    if (len <= 512) {
+                    if (len <= kMidMax) {
                         const uint32_t b = atomicAdd(big_count, 1u);
                         big_start[b] = gs;
                         big_len[b] = len;
@@ -188,45 +191,65 @@ __global__ void __launch_bounds__(256) k_group_scan_sort(const uint8_t* __restri
     }
 }
 
-// Groups of 33..512 rows: one CTA of 512 threads, one row per thread, word-1
-// keys staged in shared memory.  Each thread counts the keys below its own in
-// a branch-free pass; only a row whose word 1 is shared with another row of
-// the group (rare) compares the later words of those rows, then the ids.
-__global__ void __launch_bounds__(512) k_group_sort_mid(const uint8_t* __restrict__ tokens, RowFmt f,
-                                                        int32_t* __restrict__ ids,
-                                                        const uint32_t* __restrict__ big_start,
-                                                        const uint32_t* __restrict__ big_len,
-                                                        const uint32_t* __restrict__ big_count) {
-    __shared__ int32_t sid[512];
-    __shared__ uint64_t skey[512];
+// Groups of 33..kMidMax rows: one CTA of 1024 threads, a row per thread (two
+// past 1024 rows), word-1 keys staged in shared memory.  Each row's rank is a
+// branch-free count of the keys below its own; a row whose word 1 is shared
+// with others compares the later words of those rows, then the ids.  If some
+// row shares word 1 with more than kMidTied others, the group is left to the
+// exact refinement (its rows are counted into huge_count), which keeps the
+// row comparisons of a group bounded.
+constexpr uint32_t kMidTied = 64;
+
+__global__ void __launch_bounds__(1024, 1) k_group_sort_mid(const uint8_t* __restrict__ tokens, RowFmt f,
+                                                         int32_t* __restrict__ ids,
+                                                         const uint32_t* __restrict__ big_start,
+                                                         const uint32_t* __restrict__ big_len,
+                                                         const uint32_t* __restrict__ big_count,
+                                                         uint32_t* __restrict__ huge_count) {
+    __shared__ int32_t sid[kMidMax];
+    __shared__ uint64_t skey[kMidMax];
     const uint32_t nbig = *big_count;
-    const uint32_t i = threadIdx.x;
+    const uint32_t t = threadIdx.x;
     for (uint32_t b = blockIdx.x; b < nbig; b += gridDim.x) {  // CTA per group
         const uint32_t gs = big_start[b], n = big_len[b];
-        int32_t my = 0;
-        uint64_t ki = 0;
-        if (i < n) {
-            my = ids[gs + i];
-            ki = pack_word(row_of(tokens, my, f), 1, f);
-            sid[i] = my;
-            skey[i] = ki;
+        for (uint32_t i = t; i < n; i += 1024) {
+            const int32_t id = ids[gs + i];
+            sid[i] = id;
+            skey[i] = pack_word(row_of(tokens, id, f), 1, f);
         }
         __syncthreads();
-        uint32_t rank = 0;
-        if (i < n) {
-            uint32_t tied = 0;
+        auto count_below = [&](uint32_t i, uint32_t& tied) -> uint32_t {
+            const uint64_t ki = skey[i];
+            uint32_t rank = 0;
+            tied = 0;
 #pragma unroll 8
             for (uint32_t j = 0; j < n; ++j) {
                 const uint64_t kj = skey[j];
                 rank += kj < ki;
                 tied += kj == ki;
             }
-            if (tied > 1)  // itself included
-                for (uint32_t j = 0; j < n; ++j)
-                    if (j != i && skey[j] == ki && row_less(tokens, f, 2, sid[j], my)) ++rank;
+            return rank;
+        };
+        auto tied_below = [&](uint32_t i) -> uint32_t {  // rows equal on word 1 ordered before row i
+            const uint64_t ki = skey[i];
+            const int32_t my = sid[i];
+            uint32_t r = 0;
+            for (uint32_t j = 0; j < n; ++j)
+                if (j != i && skey[j] == ki && row_less(tokens, f, 2, sid[j], my)) ++r;
+            return r;
+        };
+        uint32_t r0 = 0, r1 = 0, t0 = 0, t1 = 0;
+        if (t < n) r0 = count_below(t, t0);
+        if (t + 1024 < n) r1 = count_below(t + 1024, t1);
+        if (__syncthreads_or(t0 > kMidTied + 1 || t1 > kMidTied + 1)) {  // (counts include the row itself)
+            if (t == 0) atomicAdd(huge_count, n);
+        } else {
+            if (t0 > 1) r0 += tied_below(t);
+            if (t1 > 1) r1 += tied_below(t + 1024);
+            __syncthreads();
+            if (t < n) ids[gs + r0] = sid[t];
+            if (t + 1024 < n) ids[gs + r1] = sid[t + 1024];
         }
-        __syncthreads();
-        if (i < n) ids[gs + rank] = my;
         __syncthreads();  // the shared arrays are refilled for the next group
     }
 }
@@ -750,22 +773,22 @@ int build_sorted_ids(const void* tokens, const RowFmt& f, int64_t N64, int32_t* 
     }
     LCP_TIMED_LAUNCH(k_ids_eq, blocks_for(N, 256), 256, 0, s, vs, ks, N, ids_out, eq);
     uint32_t m = 0, G = 0;
-    // Rows tied on word 0: tie groups of up to 512 rows are ranked directly
+    // Rows tied on word 0: tie groups of up to kMidMax rows are ranked directly
     // on their remaining words (found straight from eq); only groups of more
-    // than 512 rows (if any) need the word-by-word LSD rounds below.
+    // than kMidMax rows (if any) need the word-by-word LSD rounds below.
     uint32_t* big_start = act2;  // free until the LSD rounds
     uint32_t* big_len = idx2;
-    uint32_t* cnt = w.total + 2;  // [0] listed groups, [1] rows in groups of more than 512
+    uint32_t* cnt = w.total + 2;  // [0] listed groups, [1] rows in groups of more than kMidMax
     const unsigned fill = (unsigned)sm_count() * 8;
     auto sort_groups = [&]() -> int {
         LCP_CUDA_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), s));
         LCP_TIMED_LAUNCH(k_group_scan_sort, fill, 256, 0, s, tk, f, eq, N, ids_out, big_start, big_len, cnt, cnt + 1);
-        LCP_TIMED_LAUNCH(k_group_sort_mid, fill, 512, 0, s, tk, f, ids_out, big_start, big_len, cnt);
+        LCP_TIMED_LAUNCH(k_group_sort_mid, fill, 1024, 0, s, tk, f, ids_out, big_start, big_len, cnt, cnt + 1);
         return LCP_OK;
     };
     if (huge_host) {
         // without waiting for the device: the rows in groups of more than
-        // 512 are counted into *huge_host, which the caller reads after its
+        // kMidMax are counted into *huge_host, which the caller reads after its
         // final synchronise (and rebuilds exactly, here with huge_host ==
         // nullptr, if nonzero)
         if (f.W > 1) {
