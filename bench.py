@@ -28,6 +28,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -111,7 +112,7 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+        self.path = os.path.join(tempfile.gettempdir(), "lcp_clocks_%d_%d.csv" % (os.getpid(), gpu_index))
 
     def start(self):
         try:

@@ -762,7 +762,7 @@ int build_sorted_ids(const void* tokens, const RowFmt& f, int64_t N64, int32_t* 
         cleanup();
         return rc;
     }
-    // round 0: (word 0, id) over all rows
+    // first sort key: (word 0, id) over all rows
     LCP_TIMED_LAUNCH(k_keys_word0, blocks_for(N, 256), 256, 0, s, tk, f, N, k0, v0);
     uint64_t* ks;
     uint32_t* vs;
