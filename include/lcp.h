@@ -157,8 +157,14 @@ LCP_API int lcp_topk_batch_host(lcp_index_t index, const void* h_queries, int64_
  * LCP of every query against all N rows, keeping per query the k best under
  * (LCP descending, id ascending).  Needs no index.
  * d_tokens [N, L], d_queries [Q, L] device memory in format fmt.
- * 1 <= k <= LCP_SCAN_MAX_K.  Uses temporary device memory from the
- * stream-ordered allocator (about Q * k * 8 bytes per N-slice).
+ * 1 <= k <= LCP_SCAN_MAX_K.  Batches of up to 1,024 queries take a threshold
+ * selection (per-slice counts of rows by LCP give the k-th largest LCP d*, a
+ * second pass collects the rows above d* and the first rows at d* by id);
+ * larger batches keep a heap of k keys per thread and N-slice and merge them.
+ * Both return the same bytes.  Temporary device memory from the
+ * stream-ordered allocator: about N * 8 + Q * (12 * k + 4 * S * (L + 1))
+ * bytes for small batches (S = N-slices per query, Q * S about 64 per
+ * multiprocessor, S <= 8192), N * 8 + Q * k * 8 per N-slice for larger ones.
  * ---------------------------------------------------------------------- */
 LCP_API int lcp_scan_topk(const void* d_tokens, int64_t N, lcp_format_t fmt, const void* d_queries,
                   int64_t Q, int32_t k, int32_t* d_out_ids, uint8_t* d_out_lcp,

@@ -6,8 +6,10 @@
 // bound; code written to rules that allow allocation only at start-up; and
 // host code issuing work inside a stream capture in global mode, where
 // cudaMalloc is not permitted.  lcp_scan_topk takes its temporaries from the
-// stream-ordered allocator; this entry point instead runs the same kernels on
-// a fixed scratch array that lives in the library's device image.
+// stream-ordered allocator; this entry point instead runs its per-thread-heap
+// kernels (for every batch size, also where lcp_scan_topk would take the
+// small-batch threshold selection) on a fixed scratch array that lives in the
+// library's device image.  The results are the same bytes.
 //
 // The array is a file-scope __device__ variable, so every GPU that loads the
 // library holds it (LCP_SCAN_NOALLOC_SCRATCH_BYTES) until the process exits.

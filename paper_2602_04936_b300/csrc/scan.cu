@@ -22,10 +22,21 @@ constexpr int kScanTile = 2048;     // plane-0 words staged per smem tile
 constexpr int kMergeCap = 4096;     // keys sorted per merge CTA
 constexpr uint64_t kKeyInf = ~0ull;
 
+// Packed word 0 of a row.  Aligned rows are read with one 8-byte load that
+// asks L2 for a 64-byte fetch rather than the row's whole line.
+__device__ __forceinline__ uint64_t row_word0(const uint8_t* row, const RowFmt& f) {
+    if (f.aligned8) {
+        unsigned long long x;
+        asm("ld.global.nc.L2::64B.u64 %0, [%1];" : "=l"(x) : "l"(row));
+        return msb_first(x, f.tb);
+    }
+    return pack_word(row, 0, f);
+}
+
 __global__ void k_pack_plane0(const uint8_t* __restrict__ tokens, RowFmt f, int64_t n,
                               uint64_t* __restrict__ plane0) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) plane0[i] = pack_word(row_of(tokens, i, f), 0, f);
+    if (i < n) plane0[i] = row_word0(row_of(tokens, i, f), f);
 }
 
 __device__ __forceinline__ void heap_sift_down(uint64_t* h, int n, int i) {
@@ -178,10 +189,424 @@ __global__ void __launch_bounds__(256) k_scan_merge(const uint64_t* __restrict__
     }
 }
 
+
+// ---- small batches: threshold selection ----
+//
+// With few queries the per-thread heaps above leave most of the GPU idle (one
+// thread per query and slice) and their merge dominates.  Such batches take
+// the answer from the LCP distribution instead: d* is the largest d with at
+// least k rows of LCP >= d (0 when N < k); every row with LCP > d* is in the
+// answer (nA < k of them), and the other kp = min(k - nA, #LCP-d* rows) slots
+// go to the rows of LCP exactly d* in ascending id order.
+//   k_sel_count    a warp per (query, slice of ids): rows with LCP >= d for
+//                  d = 1..L, per slice and (one atomic per CTA) in total; the
+//                  exact LCP is computed only for rows whose first token
+//                  matches the query's;
+//   k_sel_pick     a CTA per query: d*, nA, kp and, per slice, the LCP-d*
+//                  rows in the slices before it;
+//   k_sel_collect  a warp per (query, slice) walks only slices that hold
+//                  answer rows, and stops once it has found them: LCP > d*
+//                  into unordered slots, LCP-d* rows at their rank;
+//   k_sel_write    a CTA per query sorts the nA keys and writes A, the tie
+//                  rows, then padding.
+
+constexpr int kSelWarps = 8;
+constexpr int kSelBins = 16;
+constexpr int kSelMaxS = 8192;  // slices per query at most  // LCPs below this are counted per lane, larger ones by shared atomics
+constexpr int kMaxScanW = (LCP_MAX_L + 3) / 4;  // packed words of the longest uint16 row
+
+struct SelArgs {
+    const uint8_t* tokens;
+    const uint64_t* plane0;  // packed word 0 of every row, or null: read from the tokens
+    RowFmt f;
+    int64_t N;
+    const uint8_t* queries;
+    RowFmt qf;
+    int64_t Q;
+    int k;
+    int S;              // slices per query
+    int64_t slice;      // rows per slice (the last may be shorter)
+    uint32_t* ge;       // [Q][S][L]: rows of the slice with LCP >= d, d = 1..L
+    uint32_t* tot;      // [Q][L]: the same over all rows (zeroed before k_sel_count)
+    int32_t* meta;      // [Q][4]: d*, nA, kp, the A slot counter
+    uint32_t* tie_lo;   // [Q][S]: LCP-d* rows in the slices before this one
+    uint64_t* abuf;     // [Q][k]: keys (255 - LCP) << 32 | id of the rows with LCP > d*
+    int32_t* tbuf;      // [Q][k]: ids of the first kp rows of LCP d*
+};
+
+__device__ __forceinline__ uint64_t sel_word0(const SelArgs& a, int64_t t) {
+    return a.plane0 ? a.plane0[t] : row_word0(row_of(a.tokens, t, a.f), a.f);
+}
+
+// Exact LCP of row t with the query, given x = word0(t) ^ q0 (qw: the
+// query's packed words).
+__device__ __forceinline__ int sel_lcp(const SelArgs& a, int64_t t, uint64_t x, const uint64_t* qw) {
+    const RowFmt& f = a.f;
+    if (x) return lcp_at(0, x, f);
+    const uint8_t* row = row_of(a.tokens, t, f);
+    if (f.aligned8) {  // four words per round trip rather than one
+        const unsigned long long* rw = reinterpret_cast<const unsigned long long*>(row);
+        for (int w0 = 1; w0 < f.W; w0 += 4) {
+            uint64_t v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = w0 + j < f.W ? __ldg(rw + w0 + j) : 0ull;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint64_t y = w0 + j < f.W ? msb_first(v[j], f.tb) ^ qw[w0 + j] : 0ull;
+                if (y) return lcp_at(w0 + j, y, f);
+            }
+        }
+        return f.L;
+    }
+    for (int w = 1; w < f.W; ++w) {
+        const uint64_t y = pack_word(row, w, f) ^ qw[w];
+        if (y) return lcp_at(w, y, f);
+    }
+    return f.L;
+}
+
+__device__ __forceinline__ void sel_slice(const SelArgs& a, int s, int64_t* s0, int64_t* s1) {
+    *s0 = (int64_t)s * a.slice;
+    const int64_t e = *s0 + a.slice;
+    *s1 = e < a.N ? e : a.N;
+}
+
+__global__ void __launch_bounds__(kSelWarps * 32, 4) k_sel_count(SelArgs a) {
+    __shared__ uint64_t qw[kMaxScanW];
+    __shared__ uint32_t hist[kSelWarps][LCP_MAX_L + 1];
+    __shared__ uint32_t lanecnt[kSelWarps][kSelBins][32];  // [l][lane]: bank = lane, no conflicts
+    const int64_t q = blockIdx.y;
+    const unsigned lane = lane_id();
+    const int warp = threadIdx.x >> 5;
+    const int L = a.f.L;
+    const uint8_t* qrow = row_of(a.queries, q, a.qf);
+    for (int w = threadIdx.x; w < a.f.W; w += blockDim.x) qw[w] = pack_word(qrow, w, a.qf);
+    uint32_t* h = hist[warp];
+    uint32_t* lc = &lanecnt[warp][0][lane];
+    for (int d = (int)lane; d <= L; d += 32) h[d] = 0;
+#pragma unroll
+    for (int d = 0; d < kSelBins; ++d) lc[d * 32] = 0;
+    __syncthreads();
+    const int s = blockIdx.x * kSelWarps + warp;
+    if (s < a.S) {
+        int64_t s0, s1;
+        sel_slice(a, s, &s0, &s1);
+        const uint64_t q0 = qw[0];
+        const uint32_t qh = (uint32_t)(q0 >> 32);
+        const uint32_t lim = 1u << (32 - a.f.bits);  // (word 0 ^ q0) >> 32 below it: first token agrees
+        // 128 rows per step; the next step's words are loaded before this
+        // step's are tested
+        uint64_t r[4], nx[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t t = s0 + u * 32 + lane;
+            r[u] = t < s1 ? sel_word0(a, t) : ~q0;
+        }
+        for (int64_t b = s0; b < s1; b += 128) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t t = b + 128 + u * 32 + lane;
+                nx[u] = t < s1 ? sel_word0(a, t) : ~q0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool hit = ((uint32_t)(r[u] >> 32) ^ qh) < lim;
+                if (!__any_sync(0xffffffffu, hit)) continue;
+                if (hit) {
+                    const int l = sel_lcp(a, b + u * 32 + lane, r[u] ^ q0, qw);  // >= 1
+                    if (l < kSelBins) lc[l * 32] += 1;
+                    else atomicAdd(h + l, 1u);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) r[u] = nx[u];
+        }
+        __syncwarp();
+        for (int d = 1; d < kSelBins && d <= L; ++d) {
+            const uint32_t v = __reduce_add_sync(0xffffffffu, lc[d * 32]);
+            if (lane == 0) h[d] += v;
+        }
+        __syncwarp();
+        // suffix sums (rows with LCP >= d), from d = L down to 1, stored per
+        // slice and kept in h for the CTA's total
+        uint32_t* out = a.ge + ((size_t)q * a.S + s) * L;
+        uint32_t carry = 0;
+        for (int c = ((L - 1) / 32) * 32 + 1; c >= 1; c -= 32) {
+            const int d = c + (int)lane;
+            uint32_t v = d <= L ? h[d] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_down_sync(0xffffffffu, v, o);
+                if ((int)lane + o < 32) v += y;
+            }
+            v += carry;
+            __syncwarp();
+            if (d <= L) {
+                out[d - 1] = v;
+                h[d] = v;
+            }
+            carry = __shfl_sync(0xffffffffu, v, 0);
+        }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x + 1; d <= L; d += blockDim.x) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int w = 0; w < kSelWarps; ++w) v += hist[w][d];
+        if (v) atomicAdd(a.tot + (size_t)q * L + (d - 1), v);
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_sel_pick(SelArgs a) {
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t tie[kSelMaxS];  // LCP-d* rows per slice, then their exclusive prefix
+    const int64_t q = blockIdx.x;
+    const int L = a.f.L, S = a.S;
+    const unsigned lane = lane_id();
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t* tot = a.tot + (size_t)q * L;
+    // the counts fall with d, so d* is the number of d in 1..L reaching k
+    const int dstar = __syncthreads_count((int)threadIdx.x < L && tot[threadIdx.x] >= (uint32_t)a.k);
+    const uint32_t nA = dstar < L ? tot[dstar] : 0u;
+    const uint32_t atd = dstar == 0 ? (uint32_t)a.N : tot[dstar - 1];
+    const uint32_t kp = min((uint32_t)a.k - nA, atd - nA);
+    const uint32_t* g = a.ge + (size_t)q * S * L;
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+        int64_t s0, s1;
+        sel_slice(a, s, &s0, &s1);
+        const uint32_t hi = dstar == 0 ? (uint32_t)(s1 - s0) : g[(size_t)s * L + dstar - 1];
+        const uint32_t lo = dstar < L ? g[(size_t)s * L + dstar] : 0u;
+        tie[s] = hi - lo;
+    }
+    __syncthreads();
+    const int per = (S + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int sb = (int)threadIdx.x * per;
+    const int se = sb + per < S ? sb + per : S;
+    uint32_t sum = 0;
+    for (int s = sb; s < se; ++s) sum += tie[s];
+    uint32_t v = sum;  // inclusive scan over the block
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= (unsigned)o) v += y;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = (int)lane < nwarps ? wsum[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= (unsigned)o) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = v - sum + (warp > 0 ? wsum[warp - 1] : 0u);
+    for (int s = sb; s < se; ++s) {
+        const uint32_t t = tie[s];
+        tie[s] = run;
+        run += t;
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < S; s += blockDim.x) a.tie_lo[(size_t)q * S + s] = tie[s];
+    if (threadIdx.x == 0) {
+        int32_t* m = a.meta + q * 4;
+        m[0] = dstar;
+        m[1] = (int32_t)nA;
+        m[2] = (int32_t)kp;
+        m[3] = 0;
+    }
+}
+
+__global__ void __launch_bounds__(kSelWarps * 32) k_sel_collect(SelArgs a) {
+    __shared__ uint64_t qw[kMaxScanW];
+    const int64_t q = blockIdx.y;
+    const unsigned lane = lane_id();
+    const unsigned lt = lanemask_lt();
+    const int warp = threadIdx.x >> 5;
+    const int L = a.f.L;
+    const uint8_t* qrow = row_of(a.queries, q, a.qf);
+    for (int w = threadIdx.x; w < a.f.W; w += blockDim.x) qw[w] = pack_word(qrow, w, a.qf);
+    __syncthreads();
+    const int s = blockIdx.x * kSelWarps + warp;
+    if (s >= a.S) return;
+    int32_t* m = a.meta + q * 4;
+    const int dstar = m[0], kp = m[2];
+    int64_t s0, s1;
+    sel_slice(a, s, &s0, &s1);
+    const uint32_t* g = a.ge + ((size_t)q * a.S + s) * L;
+    const uint32_t atd = dstar == 0 ? (uint32_t)(s1 - s0) : g[dstar - 1];
+    uint32_t a_left = dstar < L ? g[dstar] : 0u;  // rows of LCP > d* not yet met
+    const uint32_t tlo = a.tie_lo[(size_t)q * a.S + s];
+    const uint32_t ties_s = atd - a_left;
+    const uint32_t t_need = (uint32_t)kp > tlo ? min(ties_s, (uint32_t)kp - tlo) : 0u;
+    const uint64_t q0 = qw[0];
+    const uint64_t first = ~0ull >> a.f.bits;
+    // rows whose first min(d*, tpw) tokens match (all rows when d* = 0)
+    const int dm = dstar < a.f.tpw ? dstar : a.f.tpw;
+    const uint64_t mask = prefix_mask(dm, a.f.bits);
+    uint64_t* abuf = a.abuf + q * a.k;
+    int32_t* tbuf = a.tbuf + q * a.k;
+    uint32_t seen = 0;  // LCP-d* rows of this slice met so far
+    // 128 rows per step, the next step's words loaded before this step's
+    // are tested (rows of a step in ascending id, as the ranks need)
+    uint64_t r[4], nx[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t t = s0 + u * 32 + lane;
+        r[u] = t < s1 ? sel_word0(a, t) : 0ull;
+    }
+    for (int64_t b = s0; b < s1 && (a_left > 0 || seen < t_need); b += 128) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t t = b + 128 + u * 32 + lane;
+            nx[u] = t < s1 ? sel_word0(a, t) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (!(a_left > 0 || seen < t_need)) break;  // warp-uniform
+            const int64_t t = b + u * 32 + lane;
+            const bool in = t < s1;
+            const uint64_t x = r[u] ^ q0;
+            const bool cand = in && (x & mask) == 0;
+            if (!__any_sync(0xffffffffu, cand)) continue;
+            const int l = cand && x <= first ? sel_lcp(a, t, x, qw) : 0;
+            const bool isA = cand && l > dstar;
+            const bool isT = cand && l == dstar;
+            const unsigned mA = __ballot_sync(0xffffffffu, isA);
+            if (mA) {
+                uint32_t base = 0;
+                if (lane == 0) base = atomicAdd(reinterpret_cast<uint32_t*>(m + 3), (uint32_t)__popc(mA));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                const uint32_t slot = base + (uint32_t)__popc(mA & lt);
+                if (isA && slot < (uint32_t)a.k) abuf[slot] = ((uint64_t)(255 - l) << 32) | (uint64_t)t;
+                const uint32_t na = (uint32_t)__popc(mA);
+                a_left = a_left > na ? a_left - na : 0u;
+            }
+            const unsigned mT = __ballot_sync(0xffffffffu, isT);
+            if (isT) {
+                const uint32_t rank = tlo + seen + (uint32_t)__popc(mT & lt);
+                if (rank < (uint32_t)kp) tbuf[rank] = (int32_t)t;
+            }
+            seen += (uint32_t)__popc(mT);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) r[u] = nx[u];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_sel_write(SelArgs a, int32_t* __restrict__ out_ids,
+                                                   uint8_t* __restrict__ out_lcp) {
+    __shared__ uint64_t keys[LCP_SCAN_MAX_K];
+    const int64_t q = blockIdx.x;
+    const int k = a.k;
+    const int32_t* m = a.meta + q * 4;
+    const int dstar = m[0], nA = m[1], kp = m[2];
+    int P = 1;
+    while (P < nA) P <<= 1;
+    const uint64_t* abuf = a.abuf + q * k;
+    for (int t = threadIdx.x; t < P; t += blockDim.x) keys[t] = t < nA ? abuf[t] : kKeyInf;
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < P; t += blockDim.x) {
+                const int u = t ^ stride;
+                if (u > t) {
+                    const uint64_t x = keys[t], y = keys[u];
+                    if ((x > y) == ((t & size) == 0)) {
+                        keys[t] = y;
+                        keys[u] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const int32_t* tbuf = a.tbuf + q * k;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        int32_t id = -1;
+        int l = 0;
+        if (j < nA) {
+            const uint64_t v = keys[j];
+            id = (int32_t)(uint32_t)v;
+            l = 255 - (int)(v >> 32);
+        } else if (j < nA + kp) {
+            id = tbuf[j - nA];
+            l = dstar;
+        }
+        out_ids[q * k + j] = id;
+        out_lcp[q * k + j] = (uint8_t)l;
+    }
+}
+
 }  // namespace lcpk
 
 namespace lcph {
 using namespace lcpk;
+
+// Batches up to this size take the threshold selection, larger ones the
+// per-thread heaps, whose test of a row against a full heap's worst entry is
+// cheaper per pair once every thread of the GPU has a query (measured on 2M
+// rows of 64 uint16 tokens: the selection is ahead up to between 1,024 and
+// 2,048 queries, 4.8x ahead at 1 to 32).
+constexpr int64_t kSelMaxQ = 1024;
+
+static int scan_select(const void* d_tokens, int64_t N, const RowFmt& f, const void* d_queries,
+                       const RowFmt& qf, int64_t Q, int k, int32_t* d_out_ids, uint8_t* d_out_lcp,
+                       cudaStream_t s) {
+    const int L = f.L;
+    // about 64 warps per SM over all (query, slice) pairs (two waves, so
+    // that slices with long walks in the collect pass even out), whole CTAs
+    // of slices, slices of >= 1,024 rows
+    const int64_t target = (int64_t)sm_count() * 64;
+    int64_t S = (target + Q - 1) / Q;
+    S = (S + kSelWarps - 1) / kSelWarps * kSelWarps;
+    const int64_t maxS = (N + 1023) / 1024;
+    if (S > maxS) S = maxS;
+    if (S > kSelMaxS) S = kSelMaxS;
+    if (S < 1) S = 1;
+    const int64_t slice = (N + S - 1) / S;
+    S = (N + slice - 1) / slice;
+    const bool plane = Q > 1;  // several queries re-read word 0: pack it once
+    SelArgs a;
+    a.tokens = reinterpret_cast<const uint8_t*>(d_tokens);
+    a.plane0 = nullptr;
+    a.f = f;
+    a.N = N;
+    a.queries = reinterpret_cast<const uint8_t*>(d_queries);
+    a.qf = qf;
+    a.Q = Q;
+    a.k = k;
+    a.S = (int)S;
+    a.slice = slice;
+    uint64_t* plane0 = nullptr;
+    Carver cv;
+    if (plane) cv.add(&plane0, (size_t)N);
+    cv.add(&a.ge, (size_t)Q * S * L);
+    cv.add(&a.tot, (size_t)Q * L);
+    cv.add(&a.meta, (size_t)Q * 4);
+    cv.add(&a.tie_lo, (size_t)Q * S);
+    cv.add(&a.abuf, (size_t)Q * k);
+    cv.add(&a.tbuf, (size_t)Q * k);
+    void* base = nullptr;
+    LCP_CUDA_TRY(cv.alloc(&base, s));
+    a.plane0 = plane0;
+    cudaError_t e = cudaMemsetAsync(a.tot, 0, sizeof(uint32_t) * (size_t)Q * L, s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(base, s);
+        return cuda_status(e);
+    }
+    if (plane)
+        LCP_TIMED_LAUNCH(k_pack_plane0, (unsigned)((N + 255) / 256), 256, 0, s, a.tokens, f, N, plane0);
+    const dim3 grid((unsigned)((S + kSelWarps - 1) / kSelWarps), (unsigned)Q);
+    LCP_TIMED_LAUNCH(k_sel_count, grid, kSelWarps * 32, 0, s, a);
+    LCP_TIMED_LAUNCH(k_sel_pick, (unsigned)Q, 1024, 0, s, a);
+    LCP_TIMED_LAUNCH(k_sel_collect, grid, kSelWarps * 32, 0, s, a);
+    LCP_TIMED_LAUNCH(k_sel_write, (unsigned)Q, 256, 0, s, a, d_out_ids, d_out_lcp);
+    e = cudaFreeAsync(base, s);
+    return e == cudaSuccess ? LCP_OK : cuda_status(e);
+}
 
 int scan_topk_device(const void* d_tokens, int64_t N, int tb, int L, const void* d_queries,
                      int64_t Q, int k, int32_t* d_out_ids, uint8_t* d_out_lcp, cudaStream_t s) {
@@ -193,6 +618,7 @@ int scan_topk_device(const void* d_tokens, int64_t N, int tb, int L, const void*
     }
     RowFmt f = make_fmt(tb, L, d_tokens);
     RowFmt qf = make_fmt(tb, L, d_queries);
+    if (Q <= kSelMaxQ) return scan_select(d_tokens, N, f, d_queries, qf, Q, k, d_out_ids, d_out_lcp, s);
     const int threads = 128;
     const int64_t qtiles = (Q + threads - 1) / threads;
     const int64_t target = 148 * 8;
