@@ -340,8 +340,13 @@ LCP_API int lcp_step_destroy(lcp_step_t step);
  * A session holds several built indexes (lcp_session_add_index; the caller
  * keeps ownership and must not destroy them before the session).  Each
  * submitted request (host queries [Q, L] in the index's format, k, host
- * outputs [Q, k]) needs Q*(L*token_bytes + 16 + 5*k) bytes of device memory
- * while in flight.  Requests are admitted in arrival order while at most
+ * outputs [Q, k]) counts Q*(L*token_bytes + 16 + 5*k) bytes against the
+ * budget while in flight.  The session allocates mem_budget (+ 1 KB) of
+ * device memory once, in lcp_session_create (LCP_ERR_OOM if that fails), and
+ * carves each request's query, id and LCP buffers from it: no request
+ * allocates device memory (lcp_topk_batch of more than 4,096 queries still
+ * takes its search scratch from the stream-ordered pool).  The memory is
+ * freed by lcp_session_destroy.  Requests are admitted in arrival order while at most
  * max_inflight are on the GPU and their memory fits mem_budget; the rest wait
  * and are admitted as earlier requests complete, so requests that arrive
  * while others run join them on the GPU (spread over `streams` CUDA streams,

@@ -11,8 +11,17 @@
 // request (its completion event has fired) returns its memory and may admit
 // the next ones; this happens inside every submit and poll, so the session
 // needs no thread of its own.
+//
+// Request memory is the session's own: the budget is allocated once, at
+// creation, and each admitted request's query, id and LCP buffers are carved
+// from it (first fit over a free list that merges neighbours), to be returned
+// when the request retires.  No request allocates device memory, so a
+// long-running session's latency does not depend on the state of the
+// device's shared stream-ordered pool.
 #include <chrono>
 #include <deque>
+#include <iterator>
+#include <map>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -32,7 +41,9 @@ struct Req {
     int k = 0;
     int32_t* hid = nullptr;
     uint8_t* hlcp = nullptr;
-    int64_t bytes = 0;
+    int64_t bytes = 0;   // accounted against the budget
+    int64_t blk = 0;     // bytes of its block in the slab
+    int64_t off = -1;    // the block's offset (-1: none held)
     int state = kPending;
     int rc = LCP_OK;
     int stream = 0;
@@ -54,6 +65,8 @@ struct lcp_session_s {
     uint64_t next_ticket = 1;
     int rr = 0;
     lcp_session_stats_t st{};
+    char* slab = nullptr;                 // mem_budget + kSlabSlack bytes of device memory
+    std::map<int64_t, int64_t> free_blk;  // offset -> bytes of the free blocks, merged
 };
 
 namespace {
@@ -63,6 +76,45 @@ int64_t request_bytes(const lcp_index_s* x, int64_t Q, int k) {
     return Q * ((int64_t)x->L * x->tb + 16 + 5 * (int64_t)k);
 }
 
+constexpr int64_t round256(int64_t b) { return (b + 255) & ~(int64_t)255; }
+
+// The slab holds the budget plus this much, so that any request within the
+// budget (whose three buffers are rounded up to 256 bytes each) fits an empty
+// slab.
+constexpr int64_t kSlabSlack = 1024;
+
+int64_t slab_block(const lcp_index_s* x, int64_t Q, int k) {
+    return round256(Q * (int64_t)x->L * x->tb) + round256(Q * 4 * (int64_t)k) + round256(Q * (int64_t)k);
+}
+
+// First fit; -1 when no free block is large enough.
+int64_t slab_take(lcp_session_s* s, int64_t bytes) {
+    for (auto it = s->free_blk.begin(); it != s->free_blk.end(); ++it) {
+        if (it->second < bytes) continue;
+        const int64_t off = it->first, rest = it->second - bytes;
+        s->free_blk.erase(it);
+        if (rest > 0) s->free_blk.emplace(off + bytes, rest);
+        return off;
+    }
+    return -1;
+}
+
+void slab_give(lcp_session_s* s, int64_t off, int64_t bytes) {
+    auto it = s->free_blk.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != s->free_blk.end() && it->first + it->second == nx->first) {
+        it->second += nx->second;
+        s->free_blk.erase(nx);
+    }
+    if (it != s->free_blk.begin()) {
+        auto pv = std::prev(it);
+        if (pv->first + pv->second == it->first) {
+            pv->second += it->second;
+            s->free_blk.erase(it);
+        }
+    }
+}
+
 // Enqueues the request's copies and kernels on its stream (lock held).
 int launch(lcp_session_s* s, Req& r) {
     if (s->cfg.dry_run) return LCP_OK;
@@ -70,21 +122,16 @@ int launch(lcp_session_s* s, Req& r) {
     cudaStream_t st = s->streams[r.stream];
     const size_t qb = (size_t)r.Q * x->L * x->tb;
     const size_t ib = (size_t)r.Q * r.k * sizeof(int32_t), lb = (size_t)r.Q * r.k;
-    void* dq = nullptr;
-    int32_t* did = nullptr;
-    uint8_t* dl = nullptr;
     if (r.Q > 0) {
-        LCP_CUDA_TRY(cudaMallocAsync(&dq, qb, st));
-        LCP_CUDA_TRY(cudaMallocAsync((void**)&did, ib, st));
-        LCP_CUDA_TRY(cudaMallocAsync((void**)&dl, lb, st));
+        char* base = s->slab + r.off;
+        void* dq = base;
+        int32_t* did = reinterpret_cast<int32_t*>(base + round256((int64_t)qb));
+        uint8_t* dl = reinterpret_cast<uint8_t*>(base + round256((int64_t)qb) + round256((int64_t)ib));
         LCP_CUDA_TRY(cudaMemcpyAsync(dq, r.hq, qb, cudaMemcpyHostToDevice, st));
         int rc = lcp_topk_batch(x, dq, r.Q, r.k, did, dl, st);
         if (rc != LCP_OK) return rc;
         LCP_CUDA_TRY(cudaMemcpyAsync(r.hid, did, ib, cudaMemcpyDeviceToHost, st));
         LCP_CUDA_TRY(cudaMemcpyAsync(r.hlcp, dl, lb, cudaMemcpyDeviceToHost, st));
-        LCP_CUDA_TRY(cudaFreeAsync(dq, st));
-        LCP_CUDA_TRY(cudaFreeAsync(did, st));
-        LCP_CUDA_TRY(cudaFreeAsync(dl, st));
     }
     if (s->spare_events.empty()) {
         LCP_CUDA_TRY(cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming));
@@ -101,6 +148,10 @@ void finish(lcp_session_s* s, Req& r, int state, int rc) {
     r.rc = rc;
     s->st.inflight--;
     s->st.mem_in_use -= r.bytes;
+    if (r.off >= 0) {
+        slab_give(s, r.off, r.blk);
+        r.off = -1;
+    }
     if (state == kDone) s->st.completed++;
     if (r.ev) {
         s->spare_events.push_back(r.ev);
@@ -140,6 +191,12 @@ void pump(lcp_session_s* s, bool retire = true) {
         }
         Req& r = it->second;
         if (s->st.inflight >= s->cfg.max_inflight || s->st.mem_in_use + r.bytes > s->cfg.mem_budget) break;
+        if (!s->cfg.dry_run && r.Q > 0) {
+            // a block of the slab, or wait for retirements (an empty slab
+            // always fits a request within the budget)
+            r.off = slab_take(s, r.blk);
+            if (r.off < 0) break;
+        }
         const uint64_t ticket = s->pending.front();
         s->pending.pop_front();
         s->st.pending--;
@@ -151,8 +208,13 @@ void pump(lcp_session_s* s, bool retire = true) {
         s->st.mem_in_use += r.bytes;
         if (s->st.mem_in_use > s->st.mem_peak) s->st.mem_peak = s->st.mem_in_use;
         int rc = launch(s, r);
-        if (rc != LCP_OK) finish(s, r, kFailed, rc);
-        else s->inflight.push_back(ticket);
+        if (rc != LCP_OK) {
+            // copies already enqueued may still use the block
+            cudaStreamSynchronize(s->streams[r.stream]);
+            finish(s, r, kFailed, rc);
+        } else {
+            s->inflight.push_back(ticket);
+        }
     }
 }
 
@@ -180,16 +242,15 @@ int lcp_session_create(const lcp_session_cfg_t* cfg, lcp_session_t* out) {
             }
             s->streams.push_back(st);
         }
-        // Requests allocate their buffers stream-ordered from the device's
-        // pool; reserving the whole budget in the pool once (the pool keeps
-        // freed memory) spares the requests the pool's growth on the way.
-        void* warm = nullptr;
-        if (cudaMallocAsync(&warm, (size_t)cfg->mem_budget, s->streams[0]) == cudaSuccess) {
-            cudaFreeAsync(warm, s->streams[0]);
-            cudaStreamSynchronize(s->streams[0]);
-        } else {
-            cudaGetLastError();  // a budget larger than free memory: nothing reserved
+        // the requests' memory, once
+        const int64_t slab_bytes = cfg->mem_budget + kSlabSlack;
+        cudaError_t e = cudaMalloc((void**)&s->slab, (size_t)slab_bytes);
+        if (e != cudaSuccess) {
+            for (cudaStream_t t : s->streams) cudaStreamDestroy(t);
+            delete s;
+            return lcph::cuda_status(e);
         }
+        s->free_blk.emplace(0, slab_bytes);
     }
     *out = s;
     return LCP_OK;
@@ -211,9 +272,11 @@ int lcp_session_submit(lcp_session_t s, int32_t slot, const void* h_queries, int
     if (slot < 0 || slot >= (int32_t)s->idx.size()) return LCP_ERR_INVALID;
     lcp_index_s* x = s->idx[slot];
     int64_t bytes;
+    int64_t blk = 0;
     if (x) {
         if (k > x->max_k) return LCP_ERR_INVALID;
         bytes = request_bytes(x, Q, k);
+        blk = slab_block(x, Q, k);
     } else {
         bytes = Q * (16 + 5 * (int64_t)k);  // dry run without an index
     }
@@ -231,6 +294,7 @@ int lcp_session_submit(lcp_session_t s, int32_t slot, const void* h_queries, int
     r.hid = h_out_ids;
     r.hlcp = h_out_lcp;
     r.bytes = bytes;
+    r.blk = blk;
     const uint64_t t = s->next_ticket++;
     s->reqs.emplace(t, r);
     s->pending.push_back(t);
@@ -300,8 +364,10 @@ int lcp_session_destroy(lcp_session_t s) {
         for (auto& kv : s->reqs)
             if (kv.second.ev) cudaEventDestroy(kv.second.ev);
         for (cudaEvent_t e : s->spare_events) cudaEventDestroy(e);
-        if (rc == LCP_OK)
+        if (rc == LCP_OK) {  // (after a timeout, memory the GPU may still use is kept)
             for (cudaStream_t t : s->streams) cudaStreamDestroy(t);
+            cudaFree(s->slab);
+        }
     }
     delete s;
     return rc;

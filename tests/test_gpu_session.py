@@ -71,3 +71,27 @@ def test_session_mix_equals_alone(lcp):
     for ix in idxs:
         assert lcp.lcp_index_sync(ix) == 0
         ix.close()
+
+
+def test_session_request_filling_the_budget(lcp):
+    """A request whose memory is the whole budget waits until every earlier
+    request has retired, is then admitted, and the small requests behind it
+    follow; every result equals the request served alone."""
+    S = W.zipf_prefix_rows(20_000, 16, 1024, 1.1, 7)
+    Qs = W.zipf_prefix_queries(S, 3_000, 1024, 1.1, 7)
+    ix = lcp.lcp_index_build(_dev(S), max_k=10)
+    k, Qbig = 10, 2_000
+    budget = Qbig * (S.shape[1] * S.itemsize + 16 + 5 * k)  # the big request exactly
+    sess = lcp.Session(mem_budget=budget, max_inflight=4, streams=2)
+    slot = sess.add_index(ix)
+    plan = [(0, 7), (7, 1), (100, 33), (200, Qbig), (7, 3), (900, 64), (50, 5)]
+    tickets = [(sess.submit(slot, _pinned(Qs[o:o + q]), k), o, q) for o, q in plan]
+    for t, o, q in tickets:
+        ids, lc = sess.result(t)
+        alone = lcp.lcp_topk_batch(ix, _dev(Qs[o:o + q]), k)
+        assert np.array_equal(ids.numpy(), alone[0].cpu().numpy()), (o, q)
+        assert np.array_equal(lc.numpy(), alone[1].cpu().numpy()), (o, q)
+    st = sess.stats()
+    assert st["completed"] == len(plan) and st["mem_peak"] <= budget and st["mem_in_use"] == 0
+    assert sess.close() == lcp.LCP_OK
+    ix.close()
