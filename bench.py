@@ -405,15 +405,17 @@ def issue_roofline(kernel, Q, launch_ms, sm_mhz, sms):
 
 def scan_alu_roofline(Q, N, ms, sm_mhz, sms):
     """The full scan at large batches is bound by integer ALU work: Q x N
-    (query, row) tests of at least 4 integer operations each (xor, mask,
-    compare, branch on the packed first word), against the ALU pipe's 16
-    lanes per scheduler, 4 schedulers per SM, at the sampled SM clock."""
+    (query, row) screens of 2 integer operations each (the XOR of the packed
+    first word's upper half with the query's, and a running minimum over
+    eight rows; the compare and branch per eight rows are not counted),
+    against the ALU pipe's 16 lanes per scheduler, 4 schedulers per SM, at
+    the sampled SM clock."""
     if not sm_mhz or ms <= 0:
         return None
-    ops = 4.0 * Q * N
+    ops = 2.0 * Q * N
     ach = ops / (ms / 1e3)
     pk = sms * 4 * 16 * sm_mhz * 1e6
-    return {"ops_per_pair": 4, "achieved": round(ach / 1e12, 3), "peak": round(pk / 1e12, 3),
+    return {"ops_per_pair": 2, "achieved": round(ach / 1e12, 3), "peak": round(pk / 1e12, 3),
             "unit": "Tops/s", "frac": round(ach / pk, 4),
             "peak_source": "%d SMs x 4 schedulers x 16 ALU lanes x %.0f MHz (sampled)" % (sms, sm_mhz)}
 

@@ -8,9 +8,12 @@
 //                   and a max-heap of its k best keys (255-LCP)<<32 | id for
 //                   its slice.  Rows arrive in increasing id, so a row can
 //                   only enter a full heap with a strictly larger LCP than the
-//                   heap's worst; that test is a masked XOR on word 0 (the
-//                   first worst+1 tokens equal), and only rows passing it pay
-//                   for an exact LCP over the remaining words.
+//                   heap's worst; that test (the first worst+1 tokens
+//                   equal) is one compare of word 0's XOR with q against a
+//                   power of two, screened eight rows at a time on the
+//                   words' upper halves (two 16-byte shared-memory loads,
+//                   XORs and a minimum), and only rows passing it pay for an
+//                   exact LCP over the remaining words.
 //   k_scan_merge    keys are unique, so the k smallest over a query's slice
 //                   lists are order independent: sort G lists' keys in shared
 //                   memory, keep k, repeat until one list is left, write out.
@@ -82,7 +85,8 @@ __global__ void __launch_bounds__(128) k_scan_partial(const uint8_t* __restrict_
                                                       int64_t N, const uint8_t* __restrict__ queries,
                                                       RowFmt qf, int64_t Q, int k, int64_t slice,
                                                       uint64_t* __restrict__ heaps) {
-    __shared__ uint64_t tile[kScanTile];
+    __shared__ __align__(16) uint64_t tile[kScanTile];
+    __shared__ __align__(16) uint32_t tile_hi[kScanTile];  // the words' upper halves
     const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t s0 = (int64_t)blockIdx.y * slice;
     const int64_t s1 = s0 + slice < N ? s0 + slice : N;
@@ -91,50 +95,81 @@ __global__ void __launch_bounds__(128) k_scan_partial(const uint8_t* __restrict_
     const uint64_t q0 = active ? pack_word(qrow, 0, qf) : 0;
     uint64_t* heap = heaps + ((int64_t)blockIdx.y * Q + (active ? qi : 0)) * k;
     int hn = 0;
-    uint64_t mask = 0;      // rows failing ((r ^ q0) & mask) == 0 cannot enter
-    int worst = -1;         // LCP of the heap's worst entry once full
+    int worst = -1;  // LCP of the heap's worst entry once full
+    // Once the heap is full, row r can enter only with LCP > worst, i.e. with
+    // its first worst + 1 tokens equal to q's: (r ^ q0) < T for
+    // T = 2^(64 - (worst + 1) * bits) (T = 1 past word 0: word 0 all equal).
+    uint64_t T = 0;
+    // prefilter on the upper halves: (r ^ q0) < T implies
+    // (r_hi ^ q_hi) < max(T >> 32, 1), with equality of the two tests when
+    // T >= 2^32 (the tokens to match lie in the upper half)
+    uint32_t Th = 0;
+    const uint32_t qh = (uint32_t)(q0 >> 32);
+    auto row_at = [&](int64_t id, uint64_t r) {  // a row that may enter the heap
+        int lam;
+        const uint64_t x = r ^ q0;
+        if (x) {
+            lam = __clzll((long long)x) / f.bits;
+        } else {
+            lam = f.L;
+            const uint8_t* row = row_of(tokens, id, f);
+            for (int w = 1; w < f.W; ++w) {
+                const uint64_t y = pack_word(row, w, f) ^ pack_word(qrow, w, qf);
+                if (y) {
+                    lam = w * f.tpw + (__clzll((long long)y) / f.bits);
+                    break;
+                }
+            }
+        }
+        if (lam > f.L) lam = f.L;
+        if (hn == k && lam <= worst) return;
+        const uint64_t key = ((uint64_t)(255 - lam) << 32) | (uint64_t)id;
+        if (hn < k) {
+            heap_push(heap, hn, key);
+            ++hn;
+        } else {
+            heap[0] = key;
+            heap_sift_down(heap, hn, 0);
+        }
+        if (hn == k) {
+            worst = 255 - (int)(heap[0] >> 32);
+            const int b = (worst + 1) * f.bits;
+            T = b >= 64 ? 1ull : (1ull << (64 - b));
+            Th = b >= 32 ? 1u : (uint32_t)(T >> 32);
+        }
+    };
     for (int64_t t0 = s0; t0 < s1; t0 += kScanTile) {
         const int tn = (int)(s1 - t0 < kScanTile ? s1 - t0 : kScanTile);
         __syncthreads();
-        for (int j = threadIdx.x; j < tn; j += blockDim.x) tile[j] = plane0[t0 + j];
+        for (int j = threadIdx.x; j < tn; j += blockDim.x) {
+            const uint64_t w = plane0[t0 + j];
+            tile[j] = w;
+            tile_hi[j] = (uint32_t)(w >> 32);
+        }
         __syncthreads();
         if (!active) continue;
-#pragma unroll 4
-        for (int j = 0; j < tn; ++j) {
-            const uint64_t r = tile[j];
-            if (((r ^ q0) & mask) != 0) continue;
-            // exact LCP of row t0+j
-            int lam;
-            uint64_t x = r ^ q0;
-            if (x) {
-                lam = __clzll((long long)x) / f.bits;
-            } else {
-                lam = f.L;
-                const uint8_t* row = row_of(tokens, t0 + j, f);
-                for (int w = 1; w < f.W; ++w) {
-                    uint64_t y = pack_word(row, w, f) ^ pack_word(qrow, w, qf);
-                    if (y) {
-                        lam = w * f.tpw + (__clzll((long long)y) / f.bits);
-                        break;
-                    }
-                }
-                if (lam > f.L) lam = f.L;
-            }
-            if (hn == k && lam <= worst) continue;
-            const uint64_t key = ((uint64_t)(255 - lam) << 32) | (uint64_t)(t0 + j);
-            if (hn < k) {
-                heap_push(heap, hn, key);
-                ++hn;
-            } else {
-                heap[0] = key;
-                heap_sift_down(heap, hn, 0);
-            }
-            if (hn == k) {
-                worst = 255 - (int)(heap[0] >> 32);
-                int t = worst + 1;
-                mask = t <= f.tpw ? prefix_mask(t, f.bits) : ~0ull;
+        int j = 0;
+        // the heap's first k rows enter unconditionally (the same rows for
+        // every thread of the CTA: all start at s0)
+        for (; j < tn && hn < k; ++j) row_at(t0 + j, tile[j]);
+        for (; j < tn && (j & 7); ++j)
+            if ((tile[j] ^ q0) < T) row_at(t0 + j, tile[j]);
+        // eight rows per step: two 16-byte loads of upper halves, their XORs
+        // with q's and a minimum; rows pass rarely
+        for (; j + 8 <= tn; j += 8) {
+            const uint4 a = *reinterpret_cast<const uint4*>(tile_hi + j);
+            const uint4 b = *reinterpret_cast<const uint4*>(tile_hi + j + 4);
+            const uint32_t m = min(min(min(a.x ^ qh, a.y ^ qh), min(a.z ^ qh, a.w ^ qh)),
+                                   min(min(b.x ^ qh, b.y ^ qh), min(b.z ^ qh, b.w ^ qh)));
+            if (m >= Th) continue;
+#pragma unroll 1
+            for (int u = 0; u < 8; ++u) {
+                const uint64_t r = tile[j + u];
+                if ((r ^ q0) < T) row_at(t0 + j + u, r);
             }
         }
+        for (; j < tn; ++j)
+            if ((tile[j] ^ q0) < T) row_at(t0 + j, tile[j]);
     }
     if (active)
         for (int j = hn; j < k; ++j) heap[j] = kKeyInf;
