@@ -53,11 +53,12 @@ def parse_args():
     ap.add_argument("--queries", type=int, default=0, help="override Q (profiling cases)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip latency / insert / e2e / cpu legs (profiling runs)")
-    ap.add_argument("--profile", choices=["search", "gnc"], default=None,
+    ap.add_argument("--profile", choices=["search", "gnc", "scan"], default=None,
                     help="run one small fixed case for an ncu capture and exit (no JSON line): "
                          "'search' builds the workload's index and answers --queries (default "
                          "100,000) twice; 'gnc' builds 997 sensor-stream steps and runs 3 more "
-                         "insert+query steps inside an NVTX range named 'steps'")
+                         "insert+query steps inside an NVTX range named 'steps'; 'scan' runs the "
+                         "full scan of --queries (default 32,768) three times")
     return ap.parse_args()
 
 
@@ -1006,6 +1007,15 @@ def run_profile(args):
             lcp.lcp_topk_batch(idx, dQ, w["k"])
         torch.cuda.synchronize()
         idx.close()
+    elif args.profile == "scan":
+        w = W.WORKLOADS[args.workload]
+        Q = args.queries or 32_768
+        S, Qs = workload_data(args.workload, Q)
+        dS, dQ = to_dev(S, device), to_dev(Qs, device)
+        for _ in range(3):
+            lcp.lcp_scan_topk(dS, dQ, w["k"])
+        torch.cuda.synchronize()
+        assert lcp.lcp_device_status() == 0
     else:
         g = W.GncStream(sensors=1000, seed=5)
         steps = to_dev(np.stack([g.step() for _ in range(1000)]), device)
