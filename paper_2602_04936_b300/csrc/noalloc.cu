@@ -65,15 +65,16 @@ extern "C" int lcp_scan_topk_noalloc(const void* d_tokens, int64_t N, lcp_format
         LCP_CUDA_TRY(cudaMemsetAsync(d_out_lcp, 0, (size_t)Q * k, s));
         return LCP_OK;
     }
-    // Scratch layout: [plane 0: N words][heaps: S lists x Q x k keys].  One
-    // merge pass reads the heaps and writes the outputs, so S is capped at the
+    // Scratch layout: [plane 0: N words][lists: S x Q x (k + kLogSlack) keys].
+    // One merge pass reads the lists and writes the outputs, so S is capped at the
     // number of lists one merge CTA can sort.
     int kp2 = 1;
     while (kp2 < k) kp2 <<= 1;
     const int64_t G = kMergeCapNA / kp2 > 0 ? kMergeCapNA / kp2 : 1;
     const uint64_t cap = (uint64_t)LCP_SCAN_NOALLOC_SCRATCH_BYTES;
     const uint64_t plane_bytes = ((uint64_t)N * 8 + 255) & ~255ull;
-    const uint64_t list_bytes = (uint64_t)Q * (uint64_t)k * 8;
+    const int lcap = k + kLogSlack;  // log entries per (slice, query)
+    const uint64_t list_bytes = (uint64_t)Q * (uint64_t)lcap * 8;
     if (plane_bytes + list_bytes > cap) return LCP_ERR_INVALID;  // too large even with one slice
     const int64_t qtiles = (Q + kThreadsNA - 1) / kThreadsNA;
     int64_t S = (148 * 8 + qtiles - 1) / qtiles;
@@ -100,13 +101,13 @@ extern "C" int lcp_scan_topk_noalloc(const void* d_tokens, int64_t N, lcp_format
                reinterpret_cast<const uint8_t*>(d_tokens), f, N, plane0);
     dim3 grid((unsigned)qtiles, (unsigned)S);
     LCP_LAUNCH(k_scan_partial, grid, kThreadsNA, 0, s, reinterpret_cast<const uint8_t*>(d_tokens),
-               plane0, f, N, reinterpret_cast<const uint8_t*>(d_queries), qf, Q, k, slice, heaps);
+               plane0, f, N, reinterpret_cast<const uint8_t*>(d_queries), qf, Q, k, lcap, slice, heaps);
     int P = 1;
     while (P < S * k) P <<= 1;
     LCP_CUDA_TRY(cudaFuncSetAttribute(k_scan_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(sizeof(uint64_t) * kMergeCapNA * 2)));
     dim3 mg((unsigned)Q, 1);
-    LCP_LAUNCH(k_scan_merge, mg, 256, sizeof(uint64_t) * P, s, heaps, Q, k, (int)S, (int)S, P,
+    LCP_LAUNCH(k_scan_merge, mg, 256, sizeof(uint64_t) * P, s, heaps, lcap, Q, k, (int)S, (int)S, P,
                (uint64_t*)nullptr, 1, d_out_ids, d_out_lcp);
     LCP_CUDA_TRY(cudaGetLastError());
     return LCP_OK;

@@ -5,19 +5,24 @@
 //                   (8 bytes a row: 16 MB at N=2M, so it stays in L2 while
 //                   thousands of query tiles stream over it).
 //   k_scan_partial  grid = (query tiles) x (N slices); a thread owns one query
-//                   and a max-heap of its k best keys (255-LCP)<<32 | id for
-//                   its slice.  Rows arrive in increasing id, so a row can
-//                   only enter a full heap with a strictly larger LCP than the
-//                   heap's worst; that test (the first worst+1 tokens
+//                   and the k best keys (255-LCP)<<32 | id of its slice.
+//                   Rows arrive in increasing id, so once k rows are held a
+//                   row matters only with an LCP above a level `worst` that
+//                   k held rows reach; that test (the first worst+1 tokens
 //                   equal) is one compare of word 0's XOR with q against a
 //                   power of two, screened eight rows at a time on the
 //                   words' upper halves (two 16-byte shared-memory loads,
 //                   XORs and a minimum), and only rows passing it pay for an
-//                   exact LCP over the remaining words.
+//                   exact LCP over the remaining words.  Rows taken are
+//                   appended to a log in id order; when the log holds
+//                   k + kLogSlack rows, worst is raised to the k-th largest
+//                   LCP and the log cut back to k rows (those above worst
+//                   and the earliest at it) -- a few passes over the log
+//                   every kLogSlack rows instead of a heap sift per row.
 //   k_scan_merge    keys are unique, so the k smallest over a query's slice
 //                   lists are order independent: sort G lists' keys in shared
 //                   memory, keep k, repeat until one list is left, write out.
-#include "common.cuh"
+#include "scan.cuh"
 
 namespace lcpk {
 
@@ -42,38 +47,6 @@ __global__ void k_pack_plane0(const uint8_t* __restrict__ tokens, RowFmt f, int6
     if (i < n) plane0[i] = row_word0(row_of(tokens, i, f), f);
 }
 
-__device__ __forceinline__ void heap_sift_down(uint64_t* h, int n, int i) {
-    uint64_t v = h[i];
-    for (;;) {
-        int c = 2 * i + 1;
-        if (c >= n) break;
-        uint64_t cv = h[c];
-        if (c + 1 < n) {
-            uint64_t c2 = h[c + 1];
-            if (c2 > cv) {
-                cv = c2;
-                ++c;
-            }
-        }
-        if (cv <= v) break;
-        h[i] = cv;
-        i = c;
-    }
-    h[i] = v;
-}
-
-__device__ __forceinline__ void heap_push(uint64_t* h, int n, uint64_t v) {
-    int i = n;
-    while (i > 0) {
-        int par = (i - 1) >> 1;
-        uint64_t pv = h[par];
-        if (pv >= v) break;
-        h[i] = pv;
-        i = par;
-    }
-    h[i] = v;
-}
-
 // Word-0 mask that tests "the first t tokens are equal" (t <= tpw).
 __device__ __forceinline__ uint64_t prefix_mask(int t, int bits) {
     int b = t * bits;
@@ -83,8 +56,8 @@ __device__ __forceinline__ uint64_t prefix_mask(int t, int bits) {
 __global__ void __launch_bounds__(128) k_scan_partial(const uint8_t* __restrict__ tokens,
                                                       const uint64_t* __restrict__ plane0, RowFmt f,
                                                       int64_t N, const uint8_t* __restrict__ queries,
-                                                      RowFmt qf, int64_t Q, int k, int64_t slice,
-                                                      uint64_t* __restrict__ heaps) {
+                                                      RowFmt qf, int64_t Q, int k, int cap, int64_t slice,
+                                                      uint64_t* __restrict__ lists) {
     __shared__ __align__(16) uint64_t tile[kScanTile];
     __shared__ __align__(16) uint32_t tile_hi[kScanTile];  // the words' upper halves
     const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -93,19 +66,57 @@ __global__ void __launch_bounds__(128) k_scan_partial(const uint8_t* __restrict_
     const bool active = qi < Q;
     const uint8_t* qrow = active ? row_of(queries, qi, qf) : nullptr;
     const uint64_t q0 = active ? pack_word(qrow, 0, qf) : 0;
-    uint64_t* heap = heaps + ((int64_t)blockIdx.y * Q + (active ? qi : 0)) * k;
-    int hn = 0;
-    int worst = -1;  // LCP of the heap's worst entry once full
-    // Once the heap is full, row r can enter only with LCP > worst, i.e. with
-    // its first worst + 1 tokens equal to q's: (r ^ q0) < T for
-    // T = 2^(64 - (worst + 1) * bits) (T = 1 past word 0: word 0 all equal).
+    // the thread's log: keys (255 - LCP) << 32 | id of the rows taken, in id
+    // order (rows arrive in increasing id), at most cap of them
+    uint64_t* log = lists + ((int64_t)blockIdx.y * Q + (active ? qi : 0)) * cap;
+    int n = 0;
+    int worst = -1;  // -1 until k rows are logged; then a level with >= k logged rows at or above it
+    // A row can matter only with LCP > worst: its first worst + 1 tokens
+    // equal to q's, i.e. (r ^ q0) < T for T = 2^(64 - (worst + 1) * bits)
+    // (T = 1 past word 0: word 0 all equal).  The screen on the upper halves:
+    // (r ^ q0) < T implies (r_hi ^ q_hi) < max(T >> 32, 1), the two tests
+    // being equal when T >= 2^32 (the tokens to match lie in the upper half).
     uint64_t T = 0;
-    // prefilter on the upper halves: (r ^ q0) < T implies
-    // (r_hi ^ q_hi) < max(T >> 32, 1), with equality of the two tests when
-    // T >= 2^32 (the tokens to match lie in the upper half)
     uint32_t Th = 0;
     const uint32_t qh = (uint32_t)(q0 >> 32);
-    auto row_at = [&](int64_t id, uint64_t r) {  // a row that may enter the heap
+    auto lam_of = [](uint64_t e) { return 255 - (int)(e >> 32); };
+    // Raises worst to the largest w with >= k logged rows of LCP >= w and
+    // keeps the rows above w and the earliest (smallest-id) ones at w, k in
+    // all.  A row dropped here, or refused later for LCP <= worst, has k
+    // logged rows of smaller id and no smaller LCP: it is in no top k.
+    auto compact = [&]() {
+        int w, above;
+        if (worst < 0) {  // the first k rows: w = their smallest LCP, all kept
+            w = 255;
+            for (int i = 0; i < n; ++i) w = min(w, lam_of(log[i]));
+            above = 0;
+            for (int i = 0; i < n; ++i) above += lam_of(log[i]) > w;
+        } else {
+            w = worst;
+            for (;;) {
+                int c = 0;
+                for (int i = 0; i < n; ++i) c += lam_of(log[i]) > w;
+                if (c < k) {
+                    above = c;
+                    break;
+                }
+                ++w;
+            }
+        }
+        int eq = k - above;
+        int m = 0;
+        for (int i = 0; i < n; ++i) {
+            const uint64_t e = log[i];
+            const int l = lam_of(e);
+            if (l > w || (l == w && eq-- > 0)) log[m++] = e;
+        }
+        n = m;
+        worst = w;
+        const int b = (worst + 1) * f.bits;
+        T = b >= 64 ? 1ull : (1ull << (64 - b));
+        Th = b >= 32 ? 1u : (uint32_t)(T >> 32);
+    };
+    auto row_at = [&](int64_t id, uint64_t r) {  // a row that may matter
         int lam;
         const uint64_t x = r ^ q0;
         if (x) {
@@ -122,21 +133,9 @@ __global__ void __launch_bounds__(128) k_scan_partial(const uint8_t* __restrict_
             }
         }
         if (lam > f.L) lam = f.L;
-        if (hn == k && lam <= worst) return;
-        const uint64_t key = ((uint64_t)(255 - lam) << 32) | (uint64_t)id;
-        if (hn < k) {
-            heap_push(heap, hn, key);
-            ++hn;
-        } else {
-            heap[0] = key;
-            heap_sift_down(heap, hn, 0);
-        }
-        if (hn == k) {
-            worst = 255 - (int)(heap[0] >> 32);
-            const int b = (worst + 1) * f.bits;
-            T = b >= 64 ? 1ull : (1ull << (64 - b));
-            Th = b >= 32 ? 1u : (uint32_t)(T >> 32);
-        }
+        if (worst >= 0 && lam <= worst) return;
+        log[n++] = ((uint64_t)(255 - lam) << 32) | (uint64_t)id;
+        if (worst < 0 ? n == k : n == cap) compact();
     };
     for (int64_t t0 = s0; t0 < s1; t0 += kScanTile) {
         const int tn = (int)(s1 - t0 < kScanTile ? s1 - t0 : kScanTile);
@@ -149,9 +148,9 @@ __global__ void __launch_bounds__(128) k_scan_partial(const uint8_t* __restrict_
         __syncthreads();
         if (!active) continue;
         int j = 0;
-        // the heap's first k rows enter unconditionally (the same rows for
+        // the first k rows are logged unconditionally (the same rows for
         // every thread of the CTA: all start at s0)
-        for (; j < tn && hn < k; ++j) row_at(t0 + j, tile[j]);
+        for (; j < tn && worst < 0; ++j) row_at(t0 + j, tile[j]);
         for (; j < tn && (j & 7); ++j)
             if ((tile[j] ^ q0) < T) row_at(t0 + j, tile[j]);
         // eight rows per step: two 16-byte loads of upper halves, their XORs
@@ -171,14 +170,17 @@ __global__ void __launch_bounds__(128) k_scan_partial(const uint8_t* __restrict_
         for (; j < tn; ++j)
             if ((tile[j] ^ q0) < T) row_at(t0 + j, tile[j]);
     }
-    if (active)
-        for (int j = hn; j < k; ++j) heap[j] = kKeyInf;
+    if (active) {
+        if (n > k) compact();
+        for (int j = n; j < k; ++j) log[j] = kKeyInf;
+    }
 }
 
 // Reduces groups of G lists of k keys per query to one list each (sorted when
-// `final`, which then writes ids and LCPs).  grid = (Q, groups).
-__global__ void __launch_bounds__(256) k_scan_merge(const uint64_t* __restrict__ in, int64_t Q,
-                                                    int k, int nlists, int G, int P,
+// `final`, which then writes ids and LCPs); list l of query q starts at
+// in[(l * Q + q) * in_stride].  grid = (Q, groups).
+__global__ void __launch_bounds__(256) k_scan_merge(const uint64_t* __restrict__ in, int in_stride,
+                                                    int64_t Q, int k, int nlists, int G, int P,
                                                     uint64_t* __restrict__ out, int final_pass,
                                                     int32_t* __restrict__ out_ids,
                                                     uint8_t* __restrict__ out_lcp) {
@@ -192,7 +194,7 @@ __global__ void __launch_bounds__(256) k_scan_merge(const uint64_t* __restrict__
         uint64_t v = kKeyInf;
         if (t < n) {
             int l = t / k, j = t - l * k;
-            v = in[((int64_t)(l0 + l) * Q + q) * k + j];
+            v = in[((int64_t)(l0 + l) * Q + q) * in_stride + j];
         }
         keys[t] = v;
     }
@@ -581,11 +583,11 @@ namespace lcph {
 using namespace lcpk;
 
 // Batches up to this size take the threshold selection, larger ones the
-// per-thread heaps, whose test of a row against a full heap's worst entry is
-// cheaper per pair once every thread of the GPU has a query (measured on 2M
-// rows of 64 uint16 tokens: the selection is ahead up to between 1,024 and
-// 2,048 queries, 4.8x ahead at 1 to 32).
-constexpr int64_t kSelMaxQ = 1024;
+// per-thread logs, whose screen of a row against a level k logged rows reach
+// is cheaper per pair once every thread of the GPU has a query (measured on
+// 2M rows of 64 uint16 tokens: the selection is 1.5x ahead at 256 queries,
+// level at 512, 1.6x behind at 1,024; 3.3x ahead at 32).
+constexpr int64_t kSelMaxQ = 512;
 
 static int scan_select(const void* d_tokens, int64_t N, const RowFmt& f, const void* d_queries,
                        const RowFmt& qf, int64_t Q, int k, int32_t* d_out_ids, uint8_t* d_out_lcp,
@@ -664,15 +666,16 @@ int scan_topk_device(const void* d_tokens, int64_t N, int tb, int L, const void*
     if (S < 1) S = 1;
     int64_t slice = (N + S - 1) / S;
     S = (N + slice - 1) / slice;
+    const int cap = k + kLogSlack;  // log entries per (slice, query)
     uint64_t* plane0 = nullptr;
     uint64_t* heaps = nullptr;
     LCP_CUDA_TRY(cudaMallocAsync((void**)&plane0, sizeof(uint64_t) * N, s));
-    LCP_CUDA_TRY(cudaMallocAsync((void**)&heaps, sizeof(uint64_t) * (size_t)S * Q * k, s));
+    LCP_CUDA_TRY(cudaMallocAsync((void**)&heaps, sizeof(uint64_t) * (size_t)S * Q * cap, s));
     LCP_TIMED_LAUNCH(k_pack_plane0, (unsigned)((N + 255) / 256), 256, 0, s,
                reinterpret_cast<const uint8_t*>(d_tokens), f, N, plane0);
     dim3 grid((unsigned)qtiles, (unsigned)S);
     LCP_TIMED_LAUNCH(k_scan_partial, grid, threads, 0, s, reinterpret_cast<const uint8_t*>(d_tokens),
-               plane0, f, N, reinterpret_cast<const uint8_t*>(d_queries), qf, Q, k, slice, heaps);
+               plane0, f, N, reinterpret_cast<const uint8_t*>(d_queries), qf, Q, k, cap, slice, heaps);
     // merge: groups of G lists until one remains
     int kp2 = 1;
     while (kp2 < k) kp2 <<= 1;
@@ -703,8 +706,8 @@ int scan_topk_device(const void* d_tokens, int64_t N, int tb, int L, const void*
             }
         }
         dim3 mg((unsigned)Q, (unsigned)groups);
-        LCP_TIMED_LAUNCH(k_scan_merge, mg, 256, smem, s, cur, Q, k, (int)nl, g, P, out,
-                   final_pass ? 1 : 0, d_out_ids, d_out_lcp);
+        LCP_TIMED_LAUNCH(k_scan_merge, mg, 256, smem, s, cur, cur == heaps ? cap : k, Q, k, (int)nl, g, P,
+                   out, final_pass ? 1 : 0, d_out_ids, d_out_lcp);
         if (cur != heaps) cudaFreeAsync(cur, s);
         if (final_pass) break;
         cur = out;

@@ -190,20 +190,21 @@ def test_tree16_u8_full(lcp):
                                              (20000, 16, 2, 5, 100),
                                              (3000, 255, 1, 2, 17),
                                              (2000, 12, 2, 2, 1024),    # k = the largest full-scan k
+                                             (40000, 12, 2, 2, 1024),   # slices > k rows: logs compacted
                                              (300, 5, 1, 2, 1000)])     # k > N
 def test_scan_batch_paths_agree(lcp, N, L, tb, sigma, k):
-    """Full scan: a batch past 8,192 queries (per-thread heaps), the same
-    queries in batches of <= 8,192 (threshold selection) and one query at a
-    time (word 0 read straight from the rows) give the same bytes, and match
-    the oracle on a sample."""
+    """Full scan: one batch of 8,200 queries (per-thread logs), the same
+    queries in batches of 410 (threshold selection, batches <= 512) and one
+    query at a time (word 0 read straight from the rows) give the same bytes,
+    and match the oracle on a sample."""
     rng = np.random.default_rng(N * 13 + L * 5 + k)
     dt = np.uint8 if tb == 1 else np.uint16
     S = _prefixy(rng, N, L, sigma, dt)
     Qs = _queries(rng, S, 8200, sigma, dt)
     big = scan(lcp, S, Qs, k)
-    parts = [scan(lcp, S, Qs[i:i + 4100], k) for i in (0, 4100)]
+    parts = [scan(lcp, S, Qs[i:i + 410], k) for i in range(0, len(Qs), 410)]
     small = np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts])
-    assert_same(small, big, "scan: batches of 4,100 vs one batch of 8,200")
+    assert_same(small, big, "scan: batches of 410 vs one batch of 8,200")
     pick = np.sort(rng.choice(len(Qs), 40, replace=False))
     want = oracle.topk_batch(S, Qs[pick], k)
     assert_same((big[0][pick], big[1][pick]), want, "scan vs oracle (sample)")
