@@ -263,7 +263,7 @@ struct SelArgs {
     int k;
     int S;              // slices per query
     int64_t slice;      // rows per slice (the last may be shorter)
-    uint32_t* ge;       // [Q][S][L]: rows of the slice with LCP >= d, d = 1..L
+    uint32_t* ge;       // [Q][L][S]: rows of slice s with LCP >= d, d = 1..L (zeroed first)
     uint32_t* tot;      // [Q][L]: the same over all rows (zeroed before k_sel_count)
     int32_t* meta;      // [Q][4]: d*, nA, kp, the A slot counter
     uint32_t* tie_lo;   // [Q][S]: LCP-d* rows in the slices before this one
@@ -365,8 +365,8 @@ __global__ void __launch_bounds__(kSelWarps * 32, 4) k_sel_count(SelArgs a) {
         }
         __syncwarp();
         // suffix sums (rows with LCP >= d), from d = L down to 1, stored per
-        // slice and kept in h for the CTA's total
-        uint32_t* out = a.ge + ((size_t)q * a.S + s) * L;
+        // slice where nonzero and kept in h for the CTA's total
+        uint32_t* out = a.ge + (size_t)q * L * a.S + s;
         uint32_t carry = 0;
         for (int c = ((L - 1) / 32) * 32 + 1; c >= 1; c -= 32) {
             const int d = c + (int)lane;
@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(kSelWarps * 32, 4) k_sel_count(SelArgs a) {
             v += carry;
             __syncwarp();
             if (d <= L) {
-                out[d - 1] = v;
+                if (v) out[(size_t)(d - 1) * a.S] = v;
                 h[d] = v;
             }
             carry = __shfl_sync(0xffffffffu, v, 0);
@@ -407,13 +407,24 @@ __global__ void __launch_bounds__(1024) k_sel_pick(SelArgs a) {
     const uint32_t nA = dstar < L ? tot[dstar] : 0u;
     const uint32_t atd = dstar == 0 ? (uint32_t)a.N : tot[dstar - 1];
     const uint32_t kp = min((uint32_t)a.k - nA, atd - nA);
-    const uint32_t* g = a.ge + (size_t)q * S * L;
-    for (int s = threadIdx.x; s < S; s += blockDim.x) {
-        int64_t s0, s1;
-        sel_slice(a, s, &s0, &s1);
-        const uint32_t hi = dstar == 0 ? (uint32_t)(s1 - s0) : g[(size_t)s * L + dstar - 1];
-        const uint32_t lo = dstar < L ? g[(size_t)s * L + dstar] : 0u;
-        tie[s] = hi - lo;
+    const uint32_t* g = a.ge + (size_t)q * L * S;  // level-major: these reads are contiguous
+    {
+        // S <= kSelMaxS = 8 x 1024: each thread's loads issued together
+        uint32_t hv[kSelMaxS / 1024], lv[kSelMaxS / 1024];
+#pragma unroll
+        for (int i = 0; i < kSelMaxS / 1024; ++i) {
+            const int s = (int)threadIdx.x + i * 1024;
+            hv[i] = s < S && dstar > 0 ? g[(size_t)(dstar - 1) * S + s] : 0u;
+            lv[i] = s < S && dstar < L ? g[(size_t)dstar * S + s] : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < kSelMaxS / 1024; ++i) {
+            const int s = (int)threadIdx.x + i * 1024;
+            if (s >= S) break;
+            int64_t s0, s1;
+            sel_slice(a, s, &s0, &s1);
+            tie[s] = (dstar == 0 ? (uint32_t)(s1 - s0) : hv[i]) - lv[i];
+        }
     }
     __syncthreads();
     const int per = (S + (int)blockDim.x - 1) / (int)blockDim.x;
@@ -472,9 +483,9 @@ __global__ void __launch_bounds__(kSelWarps * 32) k_sel_collect(SelArgs a) {
     const int dstar = m[0], kp = m[2];
     int64_t s0, s1;
     sel_slice(a, s, &s0, &s1);
-    const uint32_t* g = a.ge + ((size_t)q * a.S + s) * L;
-    const uint32_t atd = dstar == 0 ? (uint32_t)(s1 - s0) : g[dstar - 1];
-    uint32_t a_left = dstar < L ? g[dstar] : 0u;  // rows of LCP > d* not yet met
+    const uint32_t* g = a.ge + (size_t)q * L * a.S + s;
+    const uint32_t atd = dstar == 0 ? (uint32_t)(s1 - s0) : g[(size_t)(dstar - 1) * a.S];
+    uint32_t a_left = dstar < L ? g[(size_t)dstar * a.S] : 0u;  // rows of LCP > d* not yet met
     const uint32_t tlo = a.tie_lo[(size_t)q * a.S + s];
     const uint32_t ties_s = atd - a_left;
     const uint32_t t_need = (uint32_t)kp > tlo ? min(ties_s, (uint32_t)kp - tlo) : 0u;
@@ -595,11 +606,11 @@ static int scan_select(const void* d_tokens, int64_t N, const RowFmt& f, const v
     const int L = f.L;
     // about 64 warps per SM over all (query, slice) pairs (two waves, so
     // that slices with long walks in the collect pass even out), whole CTAs
-    // of slices, slices of >= 1,024 rows
+    // of slices, slices of >= 256 rows
     const int64_t target = (int64_t)sm_count() * 64;
     int64_t S = (target + Q - 1) / Q;
     S = (S + kSelWarps - 1) / kSelWarps * kSelWarps;
-    const int64_t maxS = (N + 1023) / 1024;
+    const int64_t maxS = (N + 255) / 256;
     if (S > maxS) S = maxS;
     if (S > kSelMaxS) S = kSelMaxS;
     if (S < 1) S = 1;
@@ -629,7 +640,8 @@ static int scan_select(const void* d_tokens, int64_t N, const RowFmt& f, const v
     void* base = nullptr;
     LCP_CUDA_TRY(cv.alloc(&base, s));
     a.plane0 = plane0;
-    cudaError_t e = cudaMemsetAsync(a.tot, 0, sizeof(uint32_t) * (size_t)Q * L, s);
+    // the per-slice counts and the totals are adjacent: one memset zeroes both
+    cudaError_t e = cudaMemsetAsync(a.ge, 0, (size_t)((char*)(a.tot + (size_t)Q * L) - (char*)a.ge), s);
     if (e != cudaSuccess) {
         cudaFreeAsync(base, s);
         return cuda_status(e);
