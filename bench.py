@@ -405,20 +405,21 @@ def issue_roofline(kernel, Q, launch_ms, sm_mhz, sms):
 
 
 def scan_alu_roofline(Q, N, ms, sm_mhz, sms):
-    """The full scan at large batches is bound by integer ALU work: Q x N
-    (query, row) screens of 2 integer operations each (the XOR of the packed
-    first word's upper half with the query's, and a running minimum over
-    eight rows; the compare and branch per eight rows are not counted),
-    against the ALU pipe's 16 lanes per scheduler, 4 schedulers per SM, at
-    the sampled SM clock."""
+    """The full scan at large batches is bound by integer work: Q x N
+    (query, row) screens of 2 integer operations each -- a subtraction from
+    the packed first word's upper half (issued as a multiply-add, on the FMA
+    pipe) and a running minimum over eight rows (ALU pipe); the compare and
+    branch per eight rows are not counted -- against the two pipes' 16 lanes
+    each per scheduler, 4 schedulers per SM, at the sampled SM clock."""
     if not sm_mhz or ms <= 0:
         return None
     ops = 2.0 * Q * N
     ach = ops / (ms / 1e3)
-    pk = sms * 4 * 16 * sm_mhz * 1e6
+    pk = sms * 4 * 2 * 16 * sm_mhz * 1e6
     return {"ops_per_pair": 2, "achieved": round(ach / 1e12, 3), "peak": round(pk / 1e12, 3),
             "unit": "Tops/s", "frac": round(ach / pk, 4),
-            "peak_source": "%d SMs x 4 schedulers x 16 ALU lanes x %.0f MHz (sampled)" % (sms, sm_mhz)}
+            "peak_source": "%d SMs x 4 schedulers x (16 ALU + 16 FMA-pipe lanes) x %.0f MHz (sampled)"
+                           % (sms, sm_mhz)}
 
 
 def committed_traffic(kernel, Q):

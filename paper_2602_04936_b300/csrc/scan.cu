@@ -11,9 +11,10 @@
 //                   k held rows reach; that test (the first worst+1 tokens
 //                   equal) is one compare of word 0's XOR with q against a
 //                   power of two, screened eight rows at a time on the
-//                   words' upper halves (two 16-byte shared-memory loads,
-//                   XORs and a minimum), and only rows passing it pay for an
-//                   exact LCP over the remaining words.  Rows taken are
+//                   words' upper halves (two 16-byte shared-memory loads, a
+//                   range test per row as a multiply-add on the FMA pipe and
+//                   a minimum on the ALU pipe), and only rows passing it pay
+//                   for an exact LCP over the remaining words.  Rows taken are
 //                   appended to a log in id order; when the log holds
 //                   k + kLogSlack rows, worst is raised to the k-th largest
 //                   LCP and the log cut back to k rows (those above worst
@@ -79,6 +80,18 @@ __global__ void __launch_bounds__(128) k_scan_partial(const uint8_t* __restrict_
     uint64_t T = 0;
     uint32_t Th = 0;
     const uint32_t qh = (uint32_t)(q0 >> 32);
+    // The screen as a range test: (r_hi ^ q_hi) < Th = 2^m iff
+    // r_hi - lo < Th (mod 2^32) with lo = q_hi rounded down to a multiple of
+    // 2^m.  The subtraction is written as a multiply-add by a factor the
+    // compiler cannot fold (1 for every legal block size, <= 128 threads),
+    // so that it runs on the FMA pipe beside the minimums on the ALU pipe.
+    uint32_t neg_lo = 0;
+    const uint32_t unit = (blockDim.x + 127u) / 128u;
+    auto sub_lo = [&](uint32_t x) {
+        uint32_t d;
+        asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(unit), "r"(neg_lo));
+        return d;
+    };
     auto lam_of = [](uint64_t e) { return 255 - (int)(e >> 32); };
     // Raises worst to the largest w with >= k logged rows of LCP >= w and
     // keeps the rows above w and the earliest (smallest-id) ones at w, k in
@@ -115,6 +128,7 @@ __global__ void __launch_bounds__(128) k_scan_partial(const uint8_t* __restrict_
         const int b = (worst + 1) * f.bits;
         T = b >= 64 ? 1ull : (1ull << (64 - b));
         Th = b >= 32 ? 1u : (uint32_t)(T >> 32);
+        neg_lo = 0u - (qh & ~(Th - 1u));
     };
     auto row_at = [&](int64_t id, uint64_t r) {  // a row that may matter
         int lam;
@@ -158,8 +172,8 @@ __global__ void __launch_bounds__(128) k_scan_partial(const uint8_t* __restrict_
         for (; j + 8 <= tn; j += 8) {
             const uint4 a = *reinterpret_cast<const uint4*>(tile_hi + j);
             const uint4 b = *reinterpret_cast<const uint4*>(tile_hi + j + 4);
-            const uint32_t m = min(min(min(a.x ^ qh, a.y ^ qh), min(a.z ^ qh, a.w ^ qh)),
-                                   min(min(b.x ^ qh, b.y ^ qh), min(b.z ^ qh, b.w ^ qh)));
+            const uint32_t m = min(min(min(sub_lo(a.x), sub_lo(a.y)), min(sub_lo(a.z), sub_lo(a.w))),
+                                   min(min(sub_lo(b.x), sub_lo(b.y)), min(sub_lo(b.z), sub_lo(b.w))));
             if (m >= Th) continue;
 #pragma unroll 1
             for (int u = 0; u < 8; ++u) {
