@@ -257,9 +257,9 @@ __global__ void __launch_bounds__(256) k_scan_merge(const uint64_t* __restrict__
 //                  rows in the slices before it;
 //   k_sel_collect  a warp per (query, slice) walks only slices that hold
 //                  answer rows, and stops once it has found them: LCP > d*
-//                  into unordered slots, LCP-d* rows at their rank;
-//   k_sel_write    a CTA per query sorts the nA keys and writes A, the tie
-//                  rows, then padding.
+//                  into unordered slots, LCP-d* rows at their rank; the
+//                  query's last CTA to finish sorts the nA keys and writes
+//                  A, the tie rows, then padding.
 
 constexpr int kSelWarps = 8;
 constexpr int kSelBins = 16;
@@ -279,7 +279,7 @@ struct SelArgs {
     int64_t slice;      // rows per slice (the last may be shorter)
     uint32_t* ge;       // [Q][L][S]: rows of slice s with LCP >= d, d = 1..L (zeroed first)
     uint32_t* tot;      // [Q][L]: the same over all rows (zeroed before k_sel_count)
-    int32_t* meta;      // [Q][4]: d*, nA, kp, the A slot counter
+    int32_t* meta;      // [Q][8]: d*, nA, kp, the A slot counter, the collect pass's CTA ticket
     uint32_t* tie_lo;   // [Q][S]: LCP-d* rows in the slices before this one
     uint64_t* abuf;     // [Q][k]: keys (255 - LCP) << 32 | id of the rows with LCP > d*
     int32_t* tbuf;      // [Q][k]: ids of the first kp rows of LCP d*
@@ -473,97 +473,21 @@ __global__ void __launch_bounds__(1024) k_sel_pick(SelArgs a) {
     __syncthreads();
     for (int s = threadIdx.x; s < S; s += blockDim.x) a.tie_lo[(size_t)q * S + s] = tie[s];
     if (threadIdx.x == 0) {
-        int32_t* m = a.meta + q * 4;
+        int32_t* m = a.meta + q * 8;
         m[0] = dstar;
         m[1] = (int32_t)nA;
         m[2] = (int32_t)kp;
         m[3] = 0;
+        m[4] = 0;
     }
 }
 
-__global__ void __launch_bounds__(kSelWarps * 32) k_sel_collect(SelArgs a) {
-    __shared__ uint64_t qw[kMaxScanW];
-    const int64_t q = blockIdx.y;
-    const unsigned lane = lane_id();
-    const unsigned lt = lanemask_lt();
-    const int warp = threadIdx.x >> 5;
-    const int L = a.f.L;
-    const uint8_t* qrow = row_of(a.queries, q, a.qf);
-    for (int w = threadIdx.x; w < a.f.W; w += blockDim.x) qw[w] = pack_word(qrow, w, a.qf);
-    __syncthreads();
-    const int s = blockIdx.x * kSelWarps + warp;
-    if (s >= a.S) return;
-    int32_t* m = a.meta + q * 4;
-    const int dstar = m[0], kp = m[2];
-    int64_t s0, s1;
-    sel_slice(a, s, &s0, &s1);
-    const uint32_t* g = a.ge + (size_t)q * L * a.S + s;
-    const uint32_t atd = dstar == 0 ? (uint32_t)(s1 - s0) : g[(size_t)(dstar - 1) * a.S];
-    uint32_t a_left = dstar < L ? g[(size_t)dstar * a.S] : 0u;  // rows of LCP > d* not yet met
-    const uint32_t tlo = a.tie_lo[(size_t)q * a.S + s];
-    const uint32_t ties_s = atd - a_left;
-    const uint32_t t_need = (uint32_t)kp > tlo ? min(ties_s, (uint32_t)kp - tlo) : 0u;
-    const uint64_t q0 = qw[0];
-    const uint64_t first = ~0ull >> a.f.bits;
-    // rows whose first min(d*, tpw) tokens match (all rows when d* = 0)
-    const int dm = dstar < a.f.tpw ? dstar : a.f.tpw;
-    const uint64_t mask = prefix_mask(dm, a.f.bits);
-    uint64_t* abuf = a.abuf + q * a.k;
-    int32_t* tbuf = a.tbuf + q * a.k;
-    uint32_t seen = 0;  // LCP-d* rows of this slice met so far
-    // 128 rows per step, the next step's words loaded before this step's
-    // are tested (rows of a step in ascending id, as the ranks need)
-    uint64_t r[4], nx[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int64_t t = s0 + u * 32 + lane;
-        r[u] = t < s1 ? sel_word0(a, t) : 0ull;
-    }
-    for (int64_t b = s0; b < s1 && (a_left > 0 || seen < t_need); b += 128) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t t = b + 128 + u * 32 + lane;
-            nx[u] = t < s1 ? sel_word0(a, t) : 0ull;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (!(a_left > 0 || seen < t_need)) break;  // warp-uniform
-            const int64_t t = b + u * 32 + lane;
-            const bool in = t < s1;
-            const uint64_t x = r[u] ^ q0;
-            const bool cand = in && (x & mask) == 0;
-            if (!__any_sync(0xffffffffu, cand)) continue;
-            const int l = cand && x <= first ? sel_lcp(a, t, x, qw) : 0;
-            const bool isA = cand && l > dstar;
-            const bool isT = cand && l == dstar;
-            const unsigned mA = __ballot_sync(0xffffffffu, isA);
-            if (mA) {
-                uint32_t base = 0;
-                if (lane == 0) base = atomicAdd(reinterpret_cast<uint32_t*>(m + 3), (uint32_t)__popc(mA));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                const uint32_t slot = base + (uint32_t)__popc(mA & lt);
-                if (isA && slot < (uint32_t)a.k) abuf[slot] = ((uint64_t)(255 - l) << 32) | (uint64_t)t;
-                const uint32_t na = (uint32_t)__popc(mA);
-                a_left = a_left > na ? a_left - na : 0u;
-            }
-            const unsigned mT = __ballot_sync(0xffffffffu, isT);
-            if (isT) {
-                const uint32_t rank = tlo + seen + (uint32_t)__popc(mT & lt);
-                if (rank < (uint32_t)kp) tbuf[rank] = (int32_t)t;
-            }
-            seen += (uint32_t)__popc(mT);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) r[u] = nx[u];
-    }
-}
-
-__global__ void __launch_bounds__(256) k_sel_write(SelArgs a, int32_t* __restrict__ out_ids,
-                                                   uint8_t* __restrict__ out_lcp) {
-    __shared__ uint64_t keys[LCP_SCAN_MAX_K];
-    const int64_t q = blockIdx.x;
+// Query q's output: the nA keys of A sorted (by a CTA, in keys[]), then the
+// tie rows, then padding.
+__device__ void sel_write(const SelArgs& a, int64_t q, uint64_t* keys, int32_t* __restrict__ out_ids,
+                          uint8_t* __restrict__ out_lcp) {
     const int k = a.k;
-    const int32_t* m = a.meta + q * 4;
+    const int32_t* m = a.meta + q * 8;
     const int dstar = m[0], nA = m[1], kp = m[2];
     int P = 1;
     while (P < nA) P <<= 1;
@@ -600,6 +524,97 @@ __global__ void __launch_bounds__(256) k_sel_write(SelArgs a, int32_t* __restric
         out_ids[q * k + j] = id;
         out_lcp[q * k + j] = (uint8_t)l;
     }
+}
+
+__global__ void __launch_bounds__(kSelWarps * 32) k_sel_collect(SelArgs a, int32_t* __restrict__ out_ids,
+                                                                uint8_t* __restrict__ out_lcp) {
+    __shared__ uint64_t qw[kMaxScanW];
+    __shared__ uint64_t keys[LCP_SCAN_MAX_K];
+    __shared__ int last;
+    const int64_t q = blockIdx.y;
+    const unsigned lane = lane_id();
+    const unsigned lt = lanemask_lt();
+    const int warp = threadIdx.x >> 5;
+    const int L = a.f.L;
+    const uint8_t* qrow = row_of(a.queries, q, a.qf);
+    for (int w = threadIdx.x; w < a.f.W; w += blockDim.x) qw[w] = pack_word(qrow, w, a.qf);
+    __syncthreads();
+    const int s = blockIdx.x * kSelWarps + warp;
+    if (s < a.S) {
+        int32_t* m = a.meta + q * 8;
+        const int dstar = m[0], kp = m[2];
+        int64_t s0, s1;
+        sel_slice(a, s, &s0, &s1);
+        const uint32_t* g = a.ge + (size_t)q * L * a.S + s;
+        const uint32_t atd = dstar == 0 ? (uint32_t)(s1 - s0) : g[(size_t)(dstar - 1) * a.S];
+        uint32_t a_left = dstar < L ? g[(size_t)dstar * a.S] : 0u;  // rows of LCP > d* not yet met
+        const uint32_t tlo = a.tie_lo[(size_t)q * a.S + s];
+        const uint32_t ties_s = atd - a_left;
+        const uint32_t t_need = (uint32_t)kp > tlo ? min(ties_s, (uint32_t)kp - tlo) : 0u;
+        const uint64_t q0 = qw[0];
+        const uint64_t first = ~0ull >> a.f.bits;
+        // rows whose first min(d*, tpw) tokens match (all rows when d* = 0)
+        const int dm = dstar < a.f.tpw ? dstar : a.f.tpw;
+        const uint64_t mask = prefix_mask(dm, a.f.bits);
+        uint64_t* abuf = a.abuf + q * a.k;
+        int32_t* tbuf = a.tbuf + q * a.k;
+        uint32_t seen = 0;  // LCP-d* rows of this slice met so far
+        // 128 rows per step, the next step's words loaded before this step's
+        // are tested (rows of a step in ascending id, as the ranks need)
+        uint64_t r[4], nx[4];
+    #pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t t = s0 + u * 32 + lane;
+            r[u] = t < s1 ? sel_word0(a, t) : 0ull;
+        }
+        for (int64_t b = s0; b < s1 && (a_left > 0 || seen < t_need); b += 128) {
+    #pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t t = b + 128 + u * 32 + lane;
+                nx[u] = t < s1 ? sel_word0(a, t) : 0ull;
+            }
+    #pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (!(a_left > 0 || seen < t_need)) break;  // warp-uniform
+                const int64_t t = b + u * 32 + lane;
+                const bool in = t < s1;
+                const uint64_t x = r[u] ^ q0;
+                const bool cand = in && (x & mask) == 0;
+                if (!__any_sync(0xffffffffu, cand)) continue;
+                const int l = cand && x <= first ? sel_lcp(a, t, x, qw) : 0;
+                const bool isA = cand && l > dstar;
+                const bool isT = cand && l == dstar;
+                const unsigned mA = __ballot_sync(0xffffffffu, isA);
+                if (mA) {
+                    uint32_t base = 0;
+                    if (lane == 0) base = atomicAdd(reinterpret_cast<uint32_t*>(m + 3), (uint32_t)__popc(mA));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    const uint32_t slot = base + (uint32_t)__popc(mA & lt);
+                    if (isA && slot < (uint32_t)a.k) abuf[slot] = ((uint64_t)(255 - l) << 32) | (uint64_t)t;
+                    const uint32_t na = (uint32_t)__popc(mA);
+                    a_left = a_left > na ? a_left - na : 0u;
+                }
+                const unsigned mT = __ballot_sync(0xffffffffu, isT);
+                if (isT) {
+                    const uint32_t rank = tlo + seen + (uint32_t)__popc(mT & lt);
+                    if (rank < (uint32_t)kp) tbuf[rank] = (int32_t)t;
+                }
+                seen += (uint32_t)__popc(mT);
+            }
+    #pragma unroll
+            for (int u = 0; u < 4; ++u) r[u] = nx[u];
+        }
+    }
+    // the CTA that finishes the query's collect pass last (every CTA's
+    // writes fenced before its ticket) sorts A and writes the output
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        last = atomicAdd(reinterpret_cast<unsigned*>(a.meta + q * 8 + 4), 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    sel_write(a, q, keys, out_ids, out_lcp);
 }
 
 }  // namespace lcpk
@@ -647,7 +662,7 @@ static int scan_select(const void* d_tokens, int64_t N, const RowFmt& f, const v
     if (plane) cv.add(&plane0, (size_t)N);
     cv.add(&a.ge, (size_t)Q * S * L);
     cv.add(&a.tot, (size_t)Q * L);
-    cv.add(&a.meta, (size_t)Q * 4);
+    cv.add(&a.meta, (size_t)Q * 8);
     cv.add(&a.tie_lo, (size_t)Q * S);
     cv.add(&a.abuf, (size_t)Q * k);
     cv.add(&a.tbuf, (size_t)Q * k);
@@ -665,8 +680,7 @@ static int scan_select(const void* d_tokens, int64_t N, const RowFmt& f, const v
     const dim3 grid((unsigned)((S + kSelWarps - 1) / kSelWarps), (unsigned)Q);
     LCP_TIMED_LAUNCH(k_sel_count, grid, kSelWarps * 32, 0, s, a);
     LCP_TIMED_LAUNCH(k_sel_pick, (unsigned)Q, 1024, 0, s, a);
-    LCP_TIMED_LAUNCH(k_sel_collect, grid, kSelWarps * 32, 0, s, a);
-    LCP_TIMED_LAUNCH(k_sel_write, (unsigned)Q, 256, 0, s, a, d_out_ids, d_out_lcp);
+    LCP_TIMED_LAUNCH(k_sel_collect, grid, kSelWarps * 32, 0, s, a, d_out_ids, d_out_lcp);
     e = cudaFreeAsync(base, s);
     return e == cudaSuccess ? LCP_OK : cuda_status(e);
 }
