@@ -337,17 +337,31 @@ def oracle_rate(S, Qs, k, budget_s=12.0, max_q=4096):
     return done / elapsed, done, elapsed, threads
 
 
-def answer_algorithmic_bytes(k):
+def answer_algorithmic_bytes(k, a_mean):
     """Bytes one query's answer (first-half) kernel must move: its 16-byte
-    position record, the H byte and id of its k winners, its k (id, lcp)
-    results, and its 32-byte record for the tie-fill kernel."""
-    return 16 + k * 5 + k * 5 + 32
+    position record in; the H bytes that establish the LCPs of k rows around
+    the insertion point (k + 2); the id of each row of A (the rows above the
+    k-th largest LCP, a_mean of them on average) and its (id, lcp) result;
+    and its 32-byte record for the tie-fill kernel out."""
+    return 16 + (k + 2) + a_mean * (4 + 5) + 32
 
 
-def fill_algorithmic_bytes(k):
-    """The tie-fill kernel: its 32-byte record and at most k (id, lcp) results
-    (the ids it reads come from lists of at most k)."""
-    return 32 + k * 4 + k * 5
+def fill_algorithmic_bytes(k, a_mean):
+    """The tie-fill kernel: its 32-byte record in, then for each of the
+    k - |A| slots it fills the chosen id (read from a list or a table) and its
+    (id, lcp) result.  Together with the answer kernel every output byte is
+    counted once."""
+    return 32 + (k - a_mean) * (4 + 5)
+
+
+def mean_rows_above_dstar(out_lcp, k, N):
+    """Mean |A| over the batch: results whose LCP exceeds the k-th result's
+    (d*).  With k > N the whole answer is A."""
+    import torch
+    if k > N:
+        return float(min(k, N))
+    lc = out_lcp.to(torch.int16)
+    return float((lc > lc[:, -1:]).sum(dim=1).float().mean().item())
 
 
 def locate_algorithmic_bytes(S, Qs):
@@ -560,6 +574,7 @@ def run_ours(args, world, rank, local):
     peak, peak_kind = measured_peaks()
     sms = torch.cuda.get_device_properties(device).multi_processor_count
     loc_per_q = locate_algorithmic_bytes(S, Qs)
+    a_mean = mean_rows_above_dstar(out_lcp, k, N)
     peak_source = (peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                    else "fallback 6.4 TB/s")
     timing = "CUDA events around each launch on its stream, timed region"
@@ -567,34 +582,53 @@ def run_ours(args, world, rank, local):
         ans_launch_ms = ans_ms / ans_n
         loc_launch_ms = loc_ms / max(loc_n, 1)
         fill_launch_ms = fill_ms / max(fill_n, 1)
-        per_q = answer_algorithmic_bytes(k)
-        achieved = Q * per_q / (ans_launch_ms / 1e3) / 1e9
+        ans_per_q = answer_algorithmic_bytes(k, a_mean)
+        fill_per_q = fill_algorithmic_bytes(k, a_mean)
+        achieved = Q * ans_per_q / (ans_launch_ms / 1e3) / 1e9
         loc_achieved = Q * loc_per_q / (loc_launch_ms / 1e3) / 1e9
-        fill_achieved = Q * fill_algorithmic_bytes(k) / (fill_launch_ms / 1e3) / 1e9
-        roofline = {"kernel": "k_topk_answer", "bound": "hbm", "achieved": round(achieved, 1),
-                    "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                    "peak_source": peak_source,
-                    "traffic": committed_traffic("k_topk_answer", Q),
-                    "algorithmic_bytes_per_launch": Q * per_q, "bytes_per_query": per_q,
-                    "launch_ms": round(ans_launch_ms, 4), "launches_timed": ans_n, "timing": timing,
-                    "issue": issue_roofline("k_topk_answer", Q, ans_launch_ms, clocks.get("sm_mhz"), sms),
-                    "other_kernels": {
-                        "k_topk_locate": {"launch_ms": round(loc_launch_ms, 4), "bytes_per_query": loc_per_q,
-                                          "achieved": round(loc_achieved, 1), "frac": round(loc_achieved / peak, 4)},
-                        "k_topk_fill": {"launch_ms": round(fill_launch_ms, 4),
-                                        "bytes_per_query": fill_algorithmic_bytes(k),
-                                        "achieved": round(fill_achieved, 1), "frac": round(fill_achieved / peak, 4),
-                                        "issue": issue_roofline("k_topk_fill", Q, fill_launch_ms,
-                                                                clocks.get("sm_mhz"), sms)}}}
+        fill_achieved = Q * fill_per_q / (fill_launch_ms / 1e3) / 1e9
+        search_ms = ans_launch_ms + loc_launch_ms + fill_launch_ms
+        search_per_q = loc_per_q + ans_per_q + fill_per_q
+        search_achieved = Q * search_per_q / (search_ms / 1e3) / 1e9
+        hbm = {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+               "peak_source": peak_source, "algorithmic_bytes_per_launch": int(Q * ans_per_q),
+               "bytes_per_query": round(ans_per_q, 1), "mean_rows_above_dstar": round(a_mean, 2)}
+        issue = issue_roofline("k_topk_answer", Q, ans_launch_ms, clocks.get("sm_mhz"), sms)
+        if issue is not None:
+            # the binding limit: warp instructions issued against the
+            # schedulers' issue rate (integer work, no memory bound reached)
+            roofline = {"kernel": "k_topk_answer", "bound": "alu", "achieved": issue["achieved"],
+                        "peak": issue["peak"], "unit": issue["unit"], "frac": issue["frac"],
+                        "peak_source": issue["peak_source"], "warp_inst_per_query": issue["warp_inst_per_query"],
+                        "traffic": committed_traffic("k_topk_answer", Q), "hbm": hbm}
+        else:
+            roofline = dict({"kernel": "k_topk_answer", "bound": "hbm",
+                             "traffic": committed_traffic("k_topk_answer", Q)}, **hbm)
+        roofline.update({
+            "launch_ms": round(ans_launch_ms, 4), "launches_timed": ans_n, "timing": timing,
+            "whole_search": {"kernels": "k_topk_locate + k_topk_answer + k_topk_fill",
+                             "bytes_per_query": round(search_per_q, 1), "launch_ms": round(search_ms, 4),
+                             "achieved": round(search_achieved, 1), "frac": round(search_achieved / peak, 4),
+                             "unit": "GB/s"},
+            "other_kernels": {
+                "k_topk_locate": {"launch_ms": round(loc_launch_ms, 4), "bytes_per_query": loc_per_q,
+                                  "achieved": round(loc_achieved, 1), "frac": round(loc_achieved / peak, 4),
+                                  "traffic": committed_traffic("k_topk_locate", Q)},
+                "k_topk_fill": {"launch_ms": round(fill_launch_ms, 4),
+                                "bytes_per_query": round(fill_per_q, 1),
+                                "achieved": round(fill_achieved, 1), "frac": round(fill_achieved / peak, 4),
+                                "traffic": committed_traffic("k_topk_fill", Q),
+                                "issue": issue_roofline("k_topk_fill", Q, fill_launch_ms,
+                                                        clocks.get("sm_mhz"), sms)}}})
     else:
         # small batches run as one fused kernel: the three halves' bytes
         fused_launch_ms = fused_ms / max(fused_n, 1)
-        per_q = loc_per_q + answer_algorithmic_bytes(k) + fill_algorithmic_bytes(k)
+        per_q = loc_per_q + answer_algorithmic_bytes(k, a_mean) + fill_algorithmic_bytes(k, a_mean)
         achieved = Q * per_q / (fused_launch_ms / 1e3) / 1e9 if fused_n else 0.0
         roofline = {"kernel": "k_topk_fused", "bound": "hbm", "achieved": round(achieved, 1),
                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                     "peak_source": peak_source, "traffic": None,
-                    "algorithmic_bytes_per_launch": Q * per_q, "bytes_per_query": per_q,
+                    "algorithmic_bytes_per_launch": int(Q * per_q), "bytes_per_query": round(per_q, 1),
                     "launch_ms": round(fused_launch_ms, 4), "launches_timed": fused_n, "timing": timing,
                     "note": "batch of at most 4,096 queries: locate, answer and fill in one kernel"}
 
@@ -899,7 +933,8 @@ def serving_leg(lcp, device, to_dev, duration_s=1.5, budget=256 << 20, streams=8
             continue
         alone = lcp.lcp_topk_batch(indexes[j], pools[j][qoff:qoff + Q].to(device), k)
         got = arena[o:o + Q * k * 4].view(torch.int32).view(Q, k)
-        same = same and bool(torch.equal(got, alone[0].cpu()))
+        got_lcp = arena[o + Q * k * 4:o + Q * k * 5].view(Q, k)
+        same = same and bool(torch.equal(got, alone[0].cpu()) and torch.equal(got_lcp, alone[1].cpu()))
     # the same requests through the persistent kernel's work queue, queries
     # and outputs device-resident (no copies inside the measured latencies)
     dpools = [p.to(device) for p in pools]
@@ -927,7 +962,8 @@ def serving_leg(lcp, device, to_dev, duration_s=1.5, budget=256 << 20, streams=8
             continue
         alone = lcp.lcp_topk_batch(indexes[j], dpools[j][qoff:qoff + Q], k)
         got = darena[o:o + Q * k * 4].view(torch.int32).view(Q, k)
-        qsame = qsame and bool(torch.equal(got, alone[0]))
+        got_lcp = darena[o + Q * k * 4:o + Q * k * 5].view(Q, k)
+        qsame = qsame and bool(torch.equal(got, alone[0]) and torch.equal(got_lcp, alone[1]))
     qok = qlat[qlat >= 0]
     qdone = int(sum(qreqs[i].Q for i in range(n_req) if qlat[i] >= 0))
     queue_res = {"requests": n_req, "completed": int(len(qok)),

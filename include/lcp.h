@@ -92,9 +92,16 @@ LCP_API const char* lcp_status_string(int status);
  *             lcp_index_insert fails with LCP_ERR_CAPACITY beyond it.
  *   max_k:    largest k lcp_topk_batch will accept (1..LCP_INDEX_MAX_K).
  * On success *out owns the device memory; release it with lcp_index_destroy.
- * Blocks the host only while the radix sort decides how many refinement
- * rounds tied prefixes need (a few small device-to-host reads); all work is
- * on `stream`.  d_tokens may be reused once the stream has passed the build.
+ * The build runs as one CUDA graph on `stream` and the call blocks the host
+ * until the device has finished its sort (an event recorded mid-graph): the
+ * host then reads how many rows sit in tie groups too large for the
+ * on-device group sort (more than 2,048 rows sharing packed word 0, or a
+ * group of 33 to 2,048 in which a row shares word 1 with more than 64
+ * others).  Usually none do and the call returns while the device finishes
+ * the build's second half; otherwise those rows are ordered exactly by
+ * host-driven refinement rounds (more waits).  Inside a stream capture the
+ * build runs as plain launches with the same waits.  d_tokens may be reused
+ * once the stream has passed the build.
  * Errors: LCP_ERR_INVALID, LCP_ERR_OOM, LCP_ERR_CUDA.
  * ---------------------------------------------------------------------- */
 LCP_API int lcp_index_build(const void* d_tokens, int64_t N, lcp_format_t fmt, int64_t capacity,
@@ -341,9 +348,10 @@ LCP_API int lcp_step_destroy(lcp_step_t step);
  *
  * A session holds several built indexes (lcp_session_add_index; the caller
  * keeps ownership and must not destroy them before the session).  Each
- * submitted request (host queries [Q, L] in the index's format, k, host
- * outputs [Q, k]) counts Q*(L*token_bytes + 16 + 5*k) bytes against the
- * budget while in flight.  The session allocates mem_budget (+ 1 KB) of
+ * submitted request (queries [Q, L] in the index's format, k, outputs
+ * [Q, k]; each buffer in host or device memory -- the session copies with
+ * unified addressing, so either works) counts Q*(L*token_bytes + 16 + 5*k)
+ * bytes against the budget while in flight.  The session allocates mem_budget (+ 1 KB) of
  * device memory once, in lcp_session_create (LCP_ERR_OOM if that fails), and
  * carves each request's query, id and LCP buffers from it: no request
  * allocates device memory (lcp_topk_batch of more than 4,096 queries still
@@ -355,8 +363,9 @@ LCP_API int lcp_step_destroy(lcp_step_t step);
  * where their copies and kernels overlap).  A request whose memory alone
  * exceeds mem_budget is rejected with LCP_ERR_BUDGET.  Each result is
  * exactly what lcp_topk_batch returns for that request alone.
- * Host query and output buffers must stay valid until the request's ticket
- * completes; pinned host memory makes the copies asynchronous.
+ * Query and output buffers must stay valid (and device queries fully
+ * written) until the request's ticket completes; pinned host memory makes
+ * host copies asynchronous.
  * All calls are thread-safe.  dry_run = 1 runs the admission logic without a
  * device (requests complete on the next poll), for testing the policy.
  * ---------------------------------------------------------------------- */
@@ -376,9 +385,10 @@ typedef struct {
 LCP_API int lcp_session_create(const lcp_session_cfg_t* cfg, lcp_session_t* out);
 /* Registers an index; *slot receives its number (0, 1, ...). */
 LCP_API int lcp_session_add_index(lcp_session_t session, lcp_index_t index, int32_t* slot);
-/* Queues a request; *ticket identifies it.  Never blocks on the device. */
-LCP_API int lcp_session_submit(lcp_session_t session, int32_t slot, const void* h_queries, int64_t Q,
-                               int32_t k, int32_t* h_out_ids, uint8_t* h_out_lcp, uint64_t* ticket);
+/* Queues a request; *ticket identifies it.  Never blocks on the device.
+ * queries, out_ids and out_lcp: host or device pointers (see above). */
+LCP_API int lcp_session_submit(lcp_session_t session, int32_t slot, const void* queries, int64_t Q,
+                               int32_t k, int32_t* out_ids, uint8_t* out_lcp, uint64_t* ticket);
 /* Advances the session (retires finished requests, admits waiting ones) and
  * reports the ticket: LCP_OK when its results are in the host buffers,
  * LCP_PENDING if it is not done within timeout_ms (0 = just check), or the

@@ -586,8 +586,8 @@ class Step:
 class Session:
     """Serving session over resident indexes (see include/lcp.h).
 
-    submit() takes host tensors (pinned memory keeps it asynchronous) and
-    returns a ticket; poll() reports LCP_OK / LCP_PENDING / an error code.
+    submit() takes host tensors (pinned memory keeps it asynchronous) or
+    device tensors and returns a ticket; poll() reports LCP_OK / LCP_PENDING / an error code.
     The session keeps references to its indexes and to in-flight buffers.
     """
 
@@ -610,12 +610,15 @@ class Session:
         """Queues a request; returns its ticket.  Raises LcpError (code
         LCP_ERR_BUDGET when the request can never fit the budget)."""
         Q = queries.shape[0] if queries is not None else 0
+        on_dev = queries is not None and queries.is_cuda
         if queries is not None:
-            queries = _rows(queries, device=False)
+            queries = _rows(queries, device=on_dev)
         if out_ids is None:
-            out_ids = torch.empty((Q, k), dtype=torch.int32, pin_memory=torch.cuda.is_available())
+            out_ids = (torch.empty((Q, k), dtype=torch.int32, device=queries.device) if on_dev else
+                       torch.empty((Q, k), dtype=torch.int32, pin_memory=torch.cuda.is_available()))
         if out_lcp is None:
-            out_lcp = torch.empty((Q, k), dtype=torch.uint8, pin_memory=torch.cuda.is_available())
+            out_lcp = (torch.empty((Q, k), dtype=torch.uint8, device=queries.device) if on_dev else
+                       torch.empty((Q, k), dtype=torch.uint8, pin_memory=torch.cuda.is_available()))
         t = ctypes.c_uint64()
         _check(_lib.lcp_session_submit(self._h, slot, _ptr(queries), Q, k, _ptr(out_ids), _ptr(out_lcp),
                                        ctypes.byref(t)), "lcp_session_submit")

@@ -207,12 +207,13 @@ static GraphBuildState* graph_build_state() {
 }
 
 // Returns LCP_OK (built), LCP_PENDING (cannot run as a graph here; nothing
-// was issued) or an error.  Rows tied on their first two words in groups of
-// more than 512 need the exact, host-driven refinement: their count lands in
-// pinned memory behind an event recorded mid-graph, checked after the launch
-// -- the device is usually past it by then, so the host returns while the
-// device still runs the tail of the build -- and a nonzero count (rare:
-// heavy duplication) redoes the order exactly on `s`.
+// was issued) or an error.  Rows in tie groups the on-device group sort does
+// not take -- more than 2,048 rows sharing word 0, or a group of 33-2,048 in
+// which a row shares word 1 with more than 64 others -- need the exact,
+// host-driven refinement: their count lands in pinned memory behind an event
+// recorded mid-graph, after the sort.  The host waits for that event (every
+// build), then returns while the device runs the second half of the build;
+// a nonzero count (rare: heavy duplication) redoes the order exactly on `s`.
 static int graph_build(lcp_index_s* x, const void* d_tokens, int64_t N, cudaStream_t s) {
     GraphBuildState* g = graph_build_state();
     uint32_t* huge = pinned_words();

@@ -24,27 +24,34 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_scan_scratch[LCP_SCAN_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMergeCapNA = 4096;  // keys one merge CTA sorts (as in scan.cu)
-constexpr int kThreadsNA = 128;    // threads of k_scan_partial (its launch bound)
-
 struct ScratchSlot {
-    std::once_flag once;
+    std::mutex mu;
     void* ptr = nullptr;
-    cudaError_t err = cudaSuccess;
 };
 ScratchSlot g_slots[64];
 
-// Device address of g_scan_scratch on the current device (set-up on the first
-// call per device).
+// Device address of g_scan_scratch on the current device.  Looked up on the
+// first call per device; only a successful lookup is kept, so a call that
+// failed (for example one made inside a global-mode stream capture) does not
+// stop a later call from trying again.
 cudaError_t scratch_address(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     ScratchSlot& s = g_slots[dev];
-    std::call_once(s.once, [&s]() { s.err = cudaGetSymbolAddress(&s.ptr, g_scan_scratch); });
+    std::lock_guard<std::mutex> lk(s.mu);
+    if (!s.ptr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_scan_scratch);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e;
+        }
+        s.ptr = p;
+    }
     *out = s.ptr;
-    return s.err;
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -70,13 +77,13 @@ extern "C" int lcp_scan_topk_noalloc(const void* d_tokens, int64_t N, lcp_format
     // number of lists one merge CTA can sort.
     int kp2 = 1;
     while (kp2 < k) kp2 <<= 1;
-    const int64_t G = kMergeCapNA / kp2 > 0 ? kMergeCapNA / kp2 : 1;
+    const int64_t G = kMergeCap / kp2 > 0 ? kMergeCap / kp2 : 1;
     const uint64_t cap = (uint64_t)LCP_SCAN_NOALLOC_SCRATCH_BYTES;
     const uint64_t plane_bytes = ((uint64_t)N * 8 + 255) & ~255ull;
     const int lcap = k + kLogSlack;  // log entries per (slice, query)
     const uint64_t list_bytes = (uint64_t)Q * (uint64_t)lcap * 8;
     if (plane_bytes + list_bytes > cap) return LCP_ERR_INVALID;  // too large even with one slice
-    const int64_t qtiles = (Q + kThreadsNA - 1) / kThreadsNA;
+    const int64_t qtiles = (Q + kScanPartialThreads - 1) / kScanPartialThreads;
     int64_t S = (148 * 8 + qtiles - 1) / qtiles;
     int64_t maxS = (N + 1023) / 1024;
     int64_t fitS = (int64_t)((cap - plane_bytes) / list_bytes);
@@ -100,12 +107,12 @@ extern "C" int lcp_scan_topk_noalloc(const void* d_tokens, int64_t N, lcp_format
     LCP_LAUNCH(k_pack_plane0, (unsigned)((N + 255) / 256), 256, 0, s,
                reinterpret_cast<const uint8_t*>(d_tokens), f, N, plane0);
     dim3 grid((unsigned)qtiles, (unsigned)S);
-    LCP_LAUNCH(k_scan_partial, grid, kThreadsNA, 0, s, reinterpret_cast<const uint8_t*>(d_tokens),
+    LCP_LAUNCH(k_scan_partial, grid, kScanPartialThreads, 0, s, reinterpret_cast<const uint8_t*>(d_tokens),
                plane0, f, N, reinterpret_cast<const uint8_t*>(d_queries), qf, Q, k, lcap, slice, heaps);
     int P = 1;
     while (P < S * k) P <<= 1;
     LCP_CUDA_TRY(cudaFuncSetAttribute(k_scan_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(uint64_t) * kMergeCapNA * 2)));
+                                      (int)(sizeof(uint64_t) * kMergeCap * 2)));
     dim3 mg((unsigned)Q, 1);
     LCP_LAUNCH(k_scan_merge, mg, 256, sizeof(uint64_t) * P, s, heaps, lcap, Q, k, (int)S, (int)S, P,
                (uint64_t*)nullptr, 1, d_out_ids, d_out_lcp);

@@ -28,7 +28,6 @@
 namespace lcpk {
 
 constexpr int kScanTile = 2048;     // plane-0 words staged per smem tile
-constexpr int kMergeCap = 4096;     // keys sorted per merge CTA
 constexpr uint64_t kKeyInf = ~0ull;
 
 // Packed word 0 of a row.  Aligned rows are read with one 8-byte load that
@@ -54,7 +53,7 @@ __device__ __forceinline__ uint64_t prefix_mask(int t, int bits) {
     return b >= 64 ? ~0ull : (b == 0 ? 0ull : (~0ull << (64 - b)));
 }
 
-__global__ void __launch_bounds__(128) k_scan_partial(const uint8_t* __restrict__ tokens,
+__global__ void __launch_bounds__(kScanPartialThreads) k_scan_partial(const uint8_t* __restrict__ tokens,
                                                       const uint64_t* __restrict__ plane0, RowFmt f,
                                                       int64_t N, const uint8_t* __restrict__ queries,
                                                       RowFmt qf, int64_t Q, int k, int cap, int64_t slice,
@@ -696,7 +695,7 @@ int scan_topk_device(const void* d_tokens, int64_t N, int tb, int L, const void*
     RowFmt f = make_fmt(tb, L, d_tokens);
     RowFmt qf = make_fmt(tb, L, d_queries);
     if (Q <= kSelMaxQ) return scan_select(d_tokens, N, f, d_queries, qf, Q, k, d_out_ids, d_out_lcp, s);
-    const int threads = 128;
+    const int threads = kScanPartialThreads;
     const int64_t qtiles = (Q + threads - 1) / threads;
     const int64_t target = 148 * 8;
     int64_t S = (target + qtiles - 1) / qtiles;

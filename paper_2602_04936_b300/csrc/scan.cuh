@@ -10,6 +10,14 @@ namespace lcpk {
 // compacted back to k entries at most every kLogSlack rows it takes.
 constexpr int kLogSlack = 64;
 
+// Threads per CTA of k_scan_partial (its launch bound; a CTA owns that many
+// queries of one N-slice).
+constexpr int kScanPartialThreads = 128;
+
+// Keys one k_scan_merge CTA sorts in shared memory: a merge takes at most
+// kMergeCap / (k rounded up to a power of two) lists per query.
+constexpr int kMergeCap = 4096;
+
 __global__ void k_pack_plane0(const uint8_t* __restrict__ tokens, RowFmt f, int64_t n,
                               uint64_t* __restrict__ plane0);
 

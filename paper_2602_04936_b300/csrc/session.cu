@@ -127,11 +127,13 @@ int launch(lcp_session_s* s, Req& r) {
         void* dq = base;
         int32_t* did = reinterpret_cast<int32_t*>(base + round256((int64_t)qb));
         uint8_t* dl = reinterpret_cast<uint8_t*>(base + round256((int64_t)qb) + round256((int64_t)ib));
-        LCP_CUDA_TRY(cudaMemcpyAsync(dq, r.hq, qb, cudaMemcpyHostToDevice, st));
+        // queries and outputs may be host or device memory: unified
+        // addressing tells the copy engine which
+        LCP_CUDA_TRY(cudaMemcpyAsync(dq, r.hq, qb, cudaMemcpyDefault, st));
         int rc = lcp_topk_batch(x, dq, r.Q, r.k, did, dl, st);
         if (rc != LCP_OK) return rc;
-        LCP_CUDA_TRY(cudaMemcpyAsync(r.hid, did, ib, cudaMemcpyDeviceToHost, st));
-        LCP_CUDA_TRY(cudaMemcpyAsync(r.hlcp, dl, lb, cudaMemcpyDeviceToHost, st));
+        LCP_CUDA_TRY(cudaMemcpyAsync(r.hid, did, ib, cudaMemcpyDefault, st));
+        LCP_CUDA_TRY(cudaMemcpyAsync(r.hlcp, dl, lb, cudaMemcpyDefault, st));
     }
     if (s->spare_events.empty()) {
         LCP_CUDA_TRY(cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming));

@@ -95,3 +95,30 @@ def test_session_request_filling_the_budget(lcp):
     assert st["completed"] == len(plan) and st["mem_peak"] <= budget and st["mem_in_use"] == 0
     assert sess.close() == lcp.LCP_OK
     ix.close()
+
+
+def test_session_takes_device_and_host_buffers(lcp):
+    """Queries and outputs may be device or host memory (the session copies
+    with unified addressing); mixed requests give the same bytes as the
+    request served alone."""
+    S = W.zipf_prefix_rows(30_000, 32, 1024, 1.1, 8)
+    Qs = W.zipf_prefix_queries(S, 2_000, 1024, 1.1, 8)
+    ix = lcp.lcp_index_build(_dev(S), max_k=32)
+    sess = lcp.Session(mem_budget=16 << 20, max_inflight=8, streams=4)
+    slot = sess.add_index(ix)
+    dq = _dev(Qs)
+    plan = [(0, 500, True), (500, 1, False), (501, 700, True), (1201, 64, False), (1265, 735, True)]
+    tickets = []
+    for o, q, on_dev in plan:
+        src = dq[o:o + q] if on_dev else _pinned(Qs[o:o + q])
+        tickets.append((sess.submit(slot, src, 32), o, q, on_dev))
+    for t, o, q, on_dev in tickets:
+        ids, lc = sess.result(t)
+        assert ids.is_cuda == on_dev and lc.is_cuda == on_dev
+        alone = lcp.lcp_topk_batch(ix, dq[o:o + q], 32)
+        assert torch.equal(ids.cpu(), alone[0].cpu()) and torch.equal(lc.cpu(), alone[1].cpu()), (o, q)
+    w_ids, w_lcp = oracle.topk_batch(S, Qs[:40], 32)
+    ids, lc = sess.result(sess.submit(slot, dq[:40], 32))
+    assert np.array_equal(ids.cpu().numpy(), w_ids) and np.array_equal(lc.cpu().numpy(), w_lcp)
+    assert sess.close() == lcp.LCP_OK
+    ix.close()
