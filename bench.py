@@ -769,6 +769,8 @@ def run_ours(args, world, rank, local):
         paths["serving"] = serving_leg(lcp, device, to_dev)
         # TAL bucket scan (the paper's TAL benchmark shape) and BFS order
         paths["tal20m"] = tal_leg(lcp, device, meter)
+        # the paper's sustained shape: top-1, rows of 256 tokens, 16-bit LCPs
+        paths["sustained2m_L256"] = sustained_leg(lcp, device, meter)
         idx_b = lcp.lcp_index_build(dS, max_k=k)
         lcp.lcp_topk_bfs(idx_b, dQ, k, out_ids, out_lcp)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -875,6 +877,79 @@ def tal_leg(lcp, device, meter):
         lat[name] = {p: round(float(np.percentile(t, int(p[1:]))), 4) for p in ("p50", "p95", "p99")}
     rec["latency_ms_batch1"] = lat
     idx.close()
+    return rec
+
+
+def sustained_leg(lcp, device, meter):
+    """The paper's sustained shape (Sec. 7 Table 4, App. C): top-1 over 2M
+    sequences of 256 uint16 tokens, one query at a time (16-bit LCPs).
+    Single-query latency by CUDA events around each call, sequential QPS by
+    the host clock over the same calls, one batched call of every query, and
+    the full scan beside it."""
+    import torch
+    w = W.WORKLOADS["sustained2m_L256"]
+    S, Qs, _ = W.make_dataset("sustained2m_L256")
+    dS, dQ = to_dev(S, device), to_dev(Qs, device)
+    stream = torch.cuda.current_stream(device)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    idx = lcp.lcp_index_build(dS, max_k=1)
+    b.record(stream)
+    b.synchronize()
+    rec = {"N": w["N"], "L": w["L"], "token": "uint16", "vocab": w["vocab"], "k": 1,
+           "query_mix": "50%% stored copies keeping their first %d tokens (prefix_len), 50%% fresh" % w["prefix_len"],
+           "build_ms": round(a.elapsed_time(b), 3)}
+    oi = torch.empty(1, dtype=torch.int32, device=device)
+    ol = torch.empty(1, dtype=torch.int16, device=device)
+    n1 = 5000
+    for i in range(50):  # warm-up
+        lcp.lcp_top1_wide(idx, dQ[i:i + 1], oi, ol)
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(n1 + 1)]
+    e0 = meter.read_j()
+    h0 = time.perf_counter()
+    evs[0].record(stream)
+    for i in range(n1):
+        lcp.lcp_top1_wide(idx, dQ[i:i + 1], oi, ol)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    host_s = time.perf_counter() - h0
+    e1 = meter.read_j()
+    lat = np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(n1)])
+    rec["indexed_one_at_a_time"] = {
+        "queries": n1, "qps_host_clock": round(n1 / host_s, 1),
+        "latency_ms": {p_: round(float(np.percentile(lat, int(p_[1:]))), 4) for p_ in ("p50", "p95", "p99")},
+        "energy_j_per_query": joules_per(e0, e1, n1)}
+    Q = len(Qs)
+    ids, lc = lcp.lcp_top1_wide(idx, dQ)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(5):
+        lcp.lcp_top1_wide(idx, dQ, ids, lc)
+    b.record(stream)
+    b.synchronize()
+    rec["indexed_batch"] = {"Q": Q, "ms": round(a.elapsed_time(b) / 5, 4),
+                            "qps": round(Q / (a.elapsed_time(b) / 5e3), 1)}
+    # full scan: the same first queries one at a time, and a 1,000-query batch
+    st = []
+    for i in range(102):
+        a.record(stream)
+        lcp.lcp_scan_top1_wide(dS, dQ[i:i + 1], oi, ol)
+        b.record(stream)
+        b.synchronize()
+        if i >= 2:
+            st.append(a.elapsed_time(b))
+    sids, slc = lcp.lcp_scan_top1_wide(dS, dQ[:1000])
+    torch.cuda.synchronize()
+    rec["full_scan_one_at_a_time"] = {
+        "queries": len(st), "latency_ms": {p_: round(float(np.percentile(st, int(p_[1:]))), 4)
+                                           for p_ in ("p50", "p95", "p99")},
+        "bytes_per_query": int(S.nbytes),
+        "note": "each row's words are read until they differ from the query's"}
+    rec["full_scan_equals_indexed_first_1000"] = bool(torch.equal(sids, ids[:1000]) and torch.equal(slc, lc[:1000]))
+    idx.close()
+    del dS, dQ
     return rec
 
 

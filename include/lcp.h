@@ -35,6 +35,8 @@
  *    lcp_status_string gives its text.
  *  - Limits: N <= 2^30 - 1 items per index, k <= LCP_SCAN_MAX_K for the full
  *    scan and k <= the index's max_k (<= LCP_INDEX_MAX_K) for indexed search.
+ *  - Rows longer than 255 tokens (up to LCP_MAX_L_WIDE) are served top-1
+ *    only, with 16-bit LCPs: lcp_top1_wide / lcp_scan_top1_wide below.
  */
 #ifndef LCP_H_
 #define LCP_H_
@@ -64,6 +66,7 @@ extern "C" {
 #define LCP_INDEX_MAX_K 128     /* largest max_k an index can be built for */
 #define LCP_SCAN_MAX_K 1024     /* largest k for lcp_scan_topk */
 #define LCP_MAX_L 255
+#define LCP_MAX_L_WIDE 1024     /* longest rows of a top-1 ("wide") index */
 
 typedef void* lcp_stream_t; /* a cudaStream_t */
 typedef struct lcp_index_s* lcp_index_t;
@@ -91,6 +94,11 @@ LCP_API const char* lcp_status_string(int status);
  *   capacity: rows the index can hold without reallocating (>= N; 0 = N).
  *             lcp_index_insert fails with LCP_ERR_CAPACITY beyond it.
  *   max_k:    largest k lcp_topk_batch will accept (1..LCP_INDEX_MAX_K).
+ * fmt.L may exceed LCP_MAX_L (up to LCP_MAX_L_WIDE) only with max_k = 1 and
+ * capacity = N: such a "wide" index is answered by lcp_top1_wide alone (the
+ * 8-bit-LCP calls -- lcp_topk_batch, insert, BFS, TAL, the session, the
+ * queue, graph steps, the tuner and the export of H -- return
+ * LCP_ERR_INVALID for it).
  * On success *out owns the device memory; release it with lcp_index_destroy.
  * The build runs as one CUDA graph on `stream` and the call blocks the host
  * until the device has finished its sort (an event recorded mid-graph): the
@@ -178,6 +186,31 @@ LCP_API int lcp_topk_batch_host(lcp_index_t index, const void* h_queries, int64_
 LCP_API int lcp_scan_topk(const void* d_tokens, int64_t N, lcp_format_t fmt, const void* d_queries,
                   int64_t Q, int32_t k, int32_t* d_out_ids, uint8_t* d_out_lcp,
                   lcp_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Top-1 with 16-bit LCPs, for rows of up to LCP_MAX_L_WIDE tokens -- the
+ * paper's sustained benchmark (Sec. 7, Table 4; its configuration in App. C:
+ * top-1 over 2M sequences of max_len 256, one query at a time), whose LCPs
+ * reach 256 and do not fit the 8-bit LCP of the calls above.
+ *
+ * lcp_top1_wide: indexed.  Any index (built with any max_k; a wide index must
+ *   have max_k = 1).  For each query: the insertion point p among the sorted
+ *   rows (binary search in the query's first-token bucket), the descent
+ *   depth d = max(LCP(q, row p-1), LCP(q, row p)) -- the largest LCP of q
+ *   with any row (Algorithm 3) --, the interval of rows sharing q's first d
+ *   tokens (the descent lemma, App. A), and its smallest id (ties broken by
+ *   index, Definition "Top-k LCP Retrieval" with k = 1).
+ * lcp_scan_top1_wide: full scan, no index: the LCP of each query with all N
+ *   rows and the smallest id at the largest LCP.  1 <= L <= LCP_MAX_L_WIDE.
+ * d_queries [Q, L] device memory in the index's (scan: fmt's) format;
+ * d_out_ids [Q] int32 and d_out_lcp [Q] uint16: device memory; N = 0 gives
+ * (-1, 0).  Stream-ordered; errors as lcp_topk_batch (the full scan takes
+ * Q * 8 bytes of stream-ordered scratch).
+ * ---------------------------------------------------------------------- */
+LCP_API int lcp_top1_wide(lcp_index_t index, const void* d_queries, int64_t Q, int32_t* d_out_ids,
+                          uint16_t* d_out_lcp, lcp_stream_t stream);
+LCP_API int lcp_scan_top1_wide(const void* d_tokens, int64_t N, lcp_format_t fmt, const void* d_queries,
+                               int64_t Q, int32_t* d_out_ids, uint16_t* d_out_lcp, lcp_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Full scan top-k without any device allocation.  The paper has no

@@ -52,6 +52,10 @@ def _load():
         lib.oracle_topk_bfs.restype = i32
         lib.oracle_tal_topk.argtypes = [vp, i64, i32, i32, vp, i32, i32, vp, vp]
         lib.oracle_tal_topk.restype = i32
+        lib.oracle_topk_wide_batch.argtypes = [vp, i64, i32, i32, vp, i64, i32, vp, vp, i32]
+        lib.oracle_topk_wide_batch.restype = i32
+        lib.oracle_sorted_index_wide.argtypes = [vp, i64, i32, i32, vp, vp]
+        lib.oracle_sorted_index_wide.restype = i32
         _lib = lib
     return _lib
 
@@ -147,3 +151,35 @@ def tal_topk(S: np.ndarray, Qs: np.ndarray, k: int, d: int):
     items sharing the query's first d symbols, padded."""
     return _per_query(_load().oracle_tal_topk, S, Qs, k, d)
 
+
+
+def topk_wide(S: np.ndarray, Qs: np.ndarray, k: int, threads: int | None = None):
+    """Top-k for every query row over rows of any length L <= 65535 (the
+    paper's sustained shape has L = 256): (ids[Q,k] int32, lcp[Q,k] uint16)."""
+    S = _rows(S)
+    Qs = np.ascontiguousarray(Qs, dtype=S.dtype)
+    if Qs.ndim != 2 or Qs.shape[1] != S.shape[1]:
+        raise ValueError("queries must be [Q, L] with the dataset's L")
+    Q = Qs.shape[0]
+    ids = np.empty((Q, k), np.int32)
+    lc = np.empty((Q, k), np.uint16)
+    if threads is None:
+        threads = os.cpu_count() or 1
+    rc = _load().oracle_topk_wide_batch(_ptr(S), S.shape[0], S.shape[1], S.itemsize, _ptr(Qs), Q, k,
+                                        _ptr(ids), _ptr(lc), threads)
+    if rc:
+        raise ValueError("oracle_topk_wide_batch rejected its arguments (rc=%d)" % rc)
+    return ids, lc
+
+
+def sorted_index_wide(S: np.ndarray):
+    """Sorted order and adjacent-LCP array for rows of any length:
+    (ids[N] int32, H[N] uint16)."""
+    S = _rows(S)
+    N = S.shape[0]
+    ids = np.empty(N, np.int32)
+    H = np.empty(N, np.uint16)
+    rc = _load().oracle_sorted_index_wide(_ptr(S), N, S.shape[1], S.itemsize, _ptr(ids), _ptr(H))
+    if rc:
+        raise ValueError("oracle_sorted_index_wide rejected its arguments (rc=%d)" % rc)
+    return ids, H

@@ -35,6 +35,14 @@
  *                       sharing q's first d symbols; only the bucket is scanned
  *                       and its top k by the Definition "Top-k LCP Retrieval"
  *                       order are returned (fewer when the bucket holds fewer).
+ *   oracle_topk_wide    Definition "Top-k LCP Retrieval" for rows of any length
+ *   (+ _batch)          1 <= L <= 65535, with 16-bit LCP values: the paper's
+ *                       sustained benchmark (Sec. 7, Table 4; the sustained-load
+ *                       configuration of App. C) stores sequences of max_len 256,
+ *                       whose LCP with a query reaches 256.  The same steps as
+ *                       oracle_topk (LCP against every sequence, counting sort on
+ *                       -LCP over 0..L, first k), with the counts sized to L.
+ *   oracle_sorted_index_wide  oracle_sorted_index for any L, H in 16 bits.
  *   oracle_sorted_index The array form of the trie built by Algorithm 1
  *                       (BuildLCPIndex, Sec. 5.2): item indices ordered by their
  *                       sequence (unsigned lexicographic order of the tokens;
@@ -301,6 +309,123 @@ int oracle_sorted_index(const void* S, int64_t N, int L, int token_bytes,
                           : (uint8_t)oracle_lcp(row_ptr(S, out_ids[p - 1], L, token_bytes),
                                                 row_ptr(S, out_ids[p], L, token_bytes), L,
                                                 token_bytes);
+    }
+    return 0;
+}
+
+/* ---- rows of any length: 16-bit LCP values (see the header) ---- */
+
+/* count, start: L + 1 entries each (caller-provided work arrays). */
+static int topk_wide_work(const void* S, int64_t N, int L, int token_bytes, const void* q, int k,
+                          int32_t* out_ids, uint16_t* out_lcp, int* lcp_buf, int32_t* order_buf,
+                          int64_t* count, int64_t* start) {
+    for (int64_t i = 0; i < N; i++)
+        lcp_buf[i] = oracle_lcp(row_ptr(S, i, L, token_bytes), q, L, token_bytes);
+    memset(count, 0, sizeof(int64_t) * (size_t)(L + 1));
+    for (int64_t i = 0; i < N; i++) count[lcp_buf[i]]++;
+    int64_t acc = 0;
+    for (int v = L; v >= 0; v--) {
+        start[v] = acc;
+        acc += count[v];
+    }
+    for (int64_t i = 0; i < N; i++) order_buf[start[lcp_buf[i]]++] = (int32_t)i;
+    for (int r = 0; r < k; r++) {
+        if (r < N) {
+            out_ids[r] = order_buf[r];
+            out_lcp[r] = (uint16_t)lcp_buf[order_buf[r]];
+        } else {
+            out_ids[r] = -1;
+            out_lcp[r] = 0;
+        }
+    }
+    return 0;
+}
+
+typedef struct {
+    const void* S;
+    int64_t N;
+    int L, token_bytes;
+    const void* Qs;
+    int64_t q_begin, q_end;
+    int k;
+    int32_t* out_ids;
+    uint16_t* out_lcp;
+    int rc;
+} wide_job_t;
+
+static void* wide_worker(void* arg) {
+    wide_job_t* j = (wide_job_t*)arg;
+    int* lcp_buf = (int*)malloc(sizeof(int) * (size_t)(j->N > 0 ? j->N : 1));
+    int32_t* order_buf = (int32_t*)malloc(sizeof(int32_t) * (size_t)(j->N > 0 ? j->N : 1));
+    int64_t* count = (int64_t*)malloc(sizeof(int64_t) * (size_t)(j->L + 1));
+    int64_t* start = (int64_t*)malloc(sizeof(int64_t) * (size_t)(j->L + 1));
+    j->rc = 0;
+    if (!lcp_buf || !order_buf || !count || !start) {
+        j->rc = -2;
+    } else {
+        for (int64_t qi = j->q_begin; qi < j->q_end && j->rc == 0; qi++)
+            j->rc = topk_wide_work(j->S, j->N, j->L, j->token_bytes, row_ptr(j->Qs, qi, j->L, j->token_bytes),
+                                   j->k, j->out_ids + (size_t)qi * (size_t)j->k,
+                                   j->out_lcp + (size_t)qi * (size_t)j->k, lcp_buf, order_buf, count, start);
+    }
+    free(lcp_buf);
+    free(order_buf);
+    free(count);
+    free(start);
+    return NULL;
+}
+
+/* Top-k of Q queries over rows of length 1 <= L <= 65535: out_ids [Q, k],
+ * out_lcp [Q, k] uint16, padded with (-1, 0).  Queries split over threads. */
+int oracle_topk_wide_batch(const void* S, int64_t N, int L, int token_bytes, const void* Qs, int64_t Q,
+                           int k, int32_t* out_ids, uint16_t* out_lcp, int n_threads) {
+    if (k < 1 || L < 1 || L > 65535 || (token_bytes != 1 && token_bytes != 2) || N < 0 || Q < 0) return -1;
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > 256) n_threads = 256;
+    if (Q < (int64_t)n_threads) n_threads = (int)(Q > 0 ? Q : 1);
+    wide_job_t jobs[256];
+    pthread_t th[256];
+    int64_t per = (Q + n_threads - 1) / n_threads;
+    int started = 0;
+    for (int t = 0; t < n_threads; t++) {
+        jobs[t].S = S;
+        jobs[t].N = N;
+        jobs[t].L = L;
+        jobs[t].token_bytes = token_bytes;
+        jobs[t].Qs = Qs;
+        jobs[t].q_begin = (int64_t)t * per;
+        jobs[t].q_end = jobs[t].q_begin + per < Q ? jobs[t].q_begin + per : Q;
+        jobs[t].k = k;
+        jobs[t].out_ids = out_ids;
+        jobs[t].out_lcp = out_lcp;
+        jobs[t].rc = 0;
+        if (pthread_create(&th[t], NULL, wide_worker, &jobs[t]) == 0) {
+            started = t + 1;
+        } else {
+            wide_worker(&jobs[t]);
+            started = t + 1;
+            th[t] = 0;
+        }
+    }
+    int rc = 0;
+    for (int t = 0; t < started; t++) {
+        if (th[t]) pthread_join(th[t], NULL);
+        if (jobs[t].rc) rc = jobs[t].rc;
+    }
+    return rc;
+}
+
+/* oracle_sorted_index for 1 <= L <= 65535, H in 16 bits. */
+int oracle_sorted_index_wide(const void* S, int64_t N, int L, int token_bytes, int32_t* out_ids,
+                             uint16_t* out_H) {
+    if (L < 1 || L > 65535 || (token_bytes != 1 && token_bytes != 2) || N < 0) return -1;
+    for (int64_t i = 0; i < N; i++) out_ids[i] = (int32_t)i;
+    sort_ctx_t c = {S, L, token_bytes};
+    qsort_r(out_ids, (size_t)N, sizeof(int32_t), cmp_items, &c);
+    for (int64_t p = 0; p < N; p++) {
+        out_H[p] = p == 0 ? 0
+                          : (uint16_t)oracle_lcp(row_ptr(S, out_ids[p - 1], L, token_bytes),
+                                                 row_ptr(S, out_ids[p], L, token_bytes), L, token_bytes);
     }
     return 0;
 }

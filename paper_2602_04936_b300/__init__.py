@@ -40,6 +40,8 @@ LCP_ERR_STATE = -7
 LCP_INDEX_MAX_K = 128
 LCP_SCAN_MAX_K = 1024
 LCP_INSERT_SMALL_BATCH = 2048
+LCP_MAX_L = 255
+LCP_MAX_L_WIDE = 1024
 
 # Every symbol include/lcp.h declares (checked by the CPU test suite).
 ABI_SYMBOLS = (
@@ -53,7 +55,7 @@ ABI_SYMBOLS = (
     "lcp_step_create", "lcp_step_run", "lcp_step_stats", "lcp_step_destroy", "lcp_shard_merge",
     "lcp_topk_bfs", "lcp_tal_topk",
     "lcp_queue_create", "lcp_queue_submit", "lcp_queue_poll", "lcp_queue_stats", "lcp_queue_destroy",
-    "lcp_queue_replay", "lcp_autotune", "lcp_set_search_shape",
+    "lcp_queue_replay", "lcp_autotune", "lcp_set_search_shape", "lcp_top1_wide", "lcp_scan_top1_wide",
 )
 
 
@@ -128,6 +130,8 @@ def _load():
                             ctypes.c_int),
         "lcp_debug_bounded_wait": ([i64, vp], ctypes.c_int),
         "lcp_scan_topk_noalloc": ([vp, i64, _Format, vp, i64, i32, vp, vp, vp], ctypes.c_int),
+        "lcp_top1_wide": ([vp, vp, i64, vp, vp, vp], ctypes.c_int),
+        "lcp_scan_top1_wide": ([vp, i64, _Format, vp, i64, vp, vp, vp], ctypes.c_int),
         "lcp_session_create": ([ctypes.POINTER(SessionConfig), ctypes.POINTER(vp)], ctypes.c_int),
         "lcp_session_add_index": ([vp, vp, ctypes.POINTER(i32)], ctypes.c_int),
         "lcp_session_submit": ([vp, i32, vp, i64, i32, vp, vp, ctypes.POINTER(ctypes.c_uint64)],
@@ -366,11 +370,54 @@ def lcp_scan_topk_noalloc(tokens: torch.Tensor, queries: torch.Tensor, k: int, o
     return out_ids, out_lcp
 
 
+def _outputs_wide(Q, device, out_ids, out_lcp):
+    if out_ids is None:
+        out_ids = torch.empty(Q, dtype=torch.int32, device=device)
+    if out_lcp is None:
+        out_lcp = torch.empty(Q, dtype=torch.int16, device=device)  # uint16 values, viewed signed
+    if out_ids.dtype != torch.int32 or out_lcp.element_size() != 2 or out_lcp.is_floating_point():
+        raise TypeError("outputs must be int32 ids and 16-bit LCPs")
+    if out_ids.numel() != Q or out_lcp.numel() != Q or not (out_ids.is_contiguous() and out_lcp.is_contiguous()):
+        raise ValueError("outputs must be contiguous [Q]")
+    return out_ids, out_lcp
+
+
+def lcp_top1_wide(index: Index, queries: torch.Tensor, out_ids=None, out_lcp=None, stream=None):
+    """Top-1 with 16-bit LCPs (rows of up to LCP_MAX_L_WIDE tokens): (ids [Q]
+    int32, lcp [Q] int16 holding the uint16 values)."""
+    queries = _rows(queries, device=True)
+    if queries.shape[1] != index.L or _token_bytes(queries) != index.token_bytes:
+        raise ValueError("query format differs from the index")
+    Q = queries.shape[0]
+    out_ids, out_lcp = _outputs_wide(Q, queries.device, out_ids, out_lcp)
+    with _on(queries.device):
+        _check(_lib.lcp_top1_wide(index.handle, _ptr(queries), Q, _ptr(out_ids), _ptr(out_lcp), _stream(stream)),
+               "lcp_top1_wide")
+    return out_ids, out_lcp
+
+
+def lcp_scan_top1_wide(tokens: torch.Tensor, queries: torch.Tensor, out_ids=None, out_lcp=None, stream=None,
+                       vocab: int = 0):
+    """Full-scan top-1 with 16-bit LCPs: (ids [Q] int32, lcp [Q] int16
+    holding the uint16 values)."""
+    tokens = _rows(tokens, device=True)
+    queries = _rows(queries, device=True)
+    if queries.shape[1] != tokens.shape[1] or _token_bytes(queries) != _token_bytes(tokens):
+        raise ValueError("query format differs from the tokens")
+    Q = queries.shape[0]
+    out_ids, out_lcp = _outputs_wide(Q, queries.device, out_ids, out_lcp)
+    with _on(queries.device):
+        _check(_lib.lcp_scan_top1_wide(_ptr(tokens), tokens.shape[0], _fmt(tokens, vocab), _ptr(queries), Q,
+                                       _ptr(out_ids), _ptr(out_lcp), _stream(stream)), "lcp_scan_top1_wide")
+    return out_ids, out_lcp
+
+
 def lcp_index_export(index: Index, stream=None):
-    """(ids [N] int32, H [N] uint8) of the sorted index, on the index's device."""
+    """(ids [N] int32, H [N] uint8) of the sorted index, on the index's device
+    (H is None for an index of rows longer than LCP_MAX_L tokens)."""
     n = index.N
     ids = torch.empty(n, dtype=torch.int32, device=index.device)
-    H = torch.empty(n, dtype=torch.uint8, device=index.device)
+    H = torch.empty(n, dtype=torch.uint8, device=index.device) if index.L <= LCP_MAX_L else None
     with _on(index.device):
         _check(_lib.lcp_index_export(index.handle, _ptr(ids), _ptr(H), _stream(stream)),
                "lcp_index_export")

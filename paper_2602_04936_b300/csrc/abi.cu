@@ -146,6 +146,13 @@ static int valid_fmt(const lcp_format_t& f) {
     return (f.token_bytes == 1 || f.token_bytes == 2) && f.L >= 1 && f.L <= LCP_MAX_L;
 }
 
+// An index may also hold rows of up to LCP_MAX_L_WIDE tokens when it is built
+// for top-1 only (max_k = 1): lcp_top1_wide answers it with 16-bit LCPs.
+static int valid_build_fmt(const lcp_format_t& f, int32_t max_k) {
+    return valid_fmt(f) || ((f.token_bytes == 1 || f.token_bytes == 2) && f.L > LCP_MAX_L &&
+                            f.L <= LCP_MAX_L_WIDE && max_k == 1);
+}
+
 // Index memory comes from the device's stream-ordered pool, which is told to
 // keep freed memory (release threshold = max), so destroying and rebuilding
 // indexes in a serving loop reuses memory instead of paying cudaMalloc/cudaFree.
@@ -393,10 +400,11 @@ int lcp_index_build(const void* d_tokens, int64_t N, lcp_format_t fmt, int64_t c
                     int32_t max_k, lcp_stream_t stream, lcp_index_t* out) {
     if (!out) return LCP_ERR_INVALID;
     *out = nullptr;
-    if (!valid_fmt(fmt) || N < 0 || N >= (1ll << 30) || (N > 0 && !d_tokens)) return LCP_ERR_INVALID;
+    if (!valid_build_fmt(fmt, max_k) || N < 0 || N >= (1ll << 30) || (N > 0 && !d_tokens)) return LCP_ERR_INVALID;
     if (max_k < 1 || max_k > LCP_INDEX_MAX_K) return LCP_ERR_INVALID;
     if (capacity == 0) capacity = N;
     if (capacity < N || capacity >= (1ll << 30)) return LCP_ERR_INVALID;
+    if (fmt.L > LCP_MAX_L && capacity != N) return LCP_ERR_INVALID;  // wide rows: no inserts
     cudaStream_t s = (cudaStream_t)stream;
     lcp_index_s* x = new (std::nothrow) lcp_index_s();
     if (!x) return LCP_ERR_OOM;
@@ -527,7 +535,7 @@ int lcp_index_build_host(const void* h_tokens, int64_t N, lcp_format_t fmt, int6
                          int32_t max_k, lcp_stream_t stream, lcp_index_t* out) {
     if (!out) return LCP_ERR_INVALID;
     *out = nullptr;
-    if (!valid_fmt(fmt) || N < 0 || N >= (1ll << 30) || (N > 0 && !h_tokens)) return LCP_ERR_INVALID;
+    if (!valid_build_fmt(fmt, max_k) || N < 0 || N >= (1ll << 30) || (N > 0 && !h_tokens)) return LCP_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     size_t bytes = (size_t)N * fmt.L * fmt.token_bytes;
     void* d = nullptr;
@@ -544,7 +552,7 @@ int lcp_index_build_host(const void* h_tokens, int64_t N, lcp_format_t fmt, int6
 }
 
 int lcp_index_insert(lcp_index_t x, const void* d_tokens, int64_t n, lcp_stream_t stream) {
-    if (!x || n < 0 || (n > 0 && !d_tokens)) return LCP_ERR_INVALID;
+    if (!x || n < 0 || (n > 0 && !d_tokens) || index_is_wide(x)) return LCP_ERR_INVALID;
     if (n == 0) return LCP_OK;
     if (x->N + n > x->cap) return LCP_ERR_CAPACITY;
     if (!x->buf[1].rows) return LCP_ERR_CAPACITY;
@@ -559,7 +567,7 @@ int lcp_index_insert(lcp_index_t x, const void* d_tokens, int64_t n, lcp_stream_
 
 int lcp_topk_batch(lcp_index_t x, const void* d_queries, int64_t Q, int32_t k, int32_t* d_out_ids,
                    uint8_t* d_out_lcp, lcp_stream_t stream) {
-    if (!x || Q < 0 || k < 1 || k > x->max_k) return LCP_ERR_INVALID;
+    if (!x || Q < 0 || k < 1 || k > x->max_k || index_is_wide(x)) return LCP_ERR_INVALID;
     if (Q > 0 && (!d_queries || !d_out_ids || !d_out_lcp)) return LCP_ERR_INVALID;
     int rc = topk_batch_device(x, d_queries, Q, k, d_out_ids, d_out_lcp, (cudaStream_t)stream);
     if (rc == LCP_OK) {
@@ -572,7 +580,7 @@ int lcp_topk_batch(lcp_index_t x, const void* d_queries, int64_t Q, int32_t k, i
 
 int lcp_topk_batch_host(lcp_index_t x, const void* h_queries, int64_t Q, int32_t k, int32_t* h_out_ids,
                         uint8_t* h_out_lcp, lcp_stream_t stream) {
-    if (!x || Q < 0 || k < 1 || k > x->max_k) return LCP_ERR_INVALID;
+    if (!x || Q < 0 || k < 1 || k > x->max_k || index_is_wide(x)) return LCP_ERR_INVALID;
     if (Q == 0) return LCP_OK;
     if (!h_queries || !h_out_ids || !h_out_lcp) return LCP_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
@@ -657,7 +665,7 @@ int lcp_index_size(lcp_index_t x, int64_t* N, int64_t* bytes) {
 }
 
 int lcp_index_export(lcp_index_t x, int32_t* d_ids, uint8_t* d_H, lcp_stream_t stream) {
-    if (!x) return LCP_ERR_INVALID;
+    if (!x || (d_H && index_is_wide(x))) return LCP_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     if (x->N == 0) return LCP_OK;
     if (d_ids)

@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(256) k_gather_rows_lcp(const uint8_t* __restri
             reinterpret_cast<ulonglong2*>(rows)[p * half + h] = cur;
             if (h == 0) {
                 head[p] = cur.x;
-                H[p] = p == 0 ? (uint8_t)0 : (uint8_t)min(l, f.L);
+                H[p] = p == 0 ? (uint8_t)0 : (uint8_t)min(l, min(f.L, 255));  // 255: wide rows
             }
         }
         last = cur;
@@ -378,7 +378,7 @@ __global__ void k_adjacent_lcp(const uint64_t* __restrict__ rows, int64_t n, int
             break;
         }
     }
-    H[p] = (uint8_t)l;
+    H[p] = (uint8_t)min(l, 255);  // rows longer than 255 tokens keep H clamped (unused there)
 }
 
 __global__ void k_inverse(const int32_t* __restrict__ ids, int64_t n, int32_t* __restrict__ pos) {

@@ -24,7 +24,8 @@ struct lcp_step_s {
 extern "C" {
 
 int lcp_step_create(lcp_index_t x, int64_t n, int64_t Q, int32_t k, lcp_step_t* out) {
-    if (!x || !out || n < 0 || n > LCP_INSERT_SMALL_BATCH || Q < 0 || k < 1 || k > x->max_k)
+    if (!x || !out || n < 0 || n > LCP_INSERT_SMALL_BATCH || Q < 0 || k < 1 || k > x->max_k ||
+        lcph::index_is_wide(x))
         return LCP_ERR_INVALID;
     *out = nullptr;
     lcp_step_s* st = new (std::nothrow) lcp_step_s();

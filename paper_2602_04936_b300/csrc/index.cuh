@@ -132,6 +132,10 @@ struct lcp_index_s {
 
 namespace lcph {
 
+// An index over rows longer than LCP_MAX_L tokens (built with max_k = 1):
+// only lcp_top1_wide answers it; H is clamped to 255 there and unused.
+inline bool index_is_wide(const lcp_index_s* x) { return x->L > LCP_MAX_L; }
+
 lcpk::DevIndex dev_view(const lcp_index_s* x);
 
 // Sorts rows of `tokens` and writes their ids in sorted order (build step).

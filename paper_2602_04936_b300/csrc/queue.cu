@@ -184,7 +184,7 @@ int lcp_queue_create(const lcp_queue_cfg_t* cfg, lcp_queue_t* out) {
 
 int lcp_queue_submit(lcp_queue_t q, lcp_index_t x, const void* d_queries, int64_t Q, int32_t k,
                      int32_t* d_out_ids, uint8_t* d_out_lcp, uint64_t* ticket) {
-    if (!q || !x || !ticket || Q < 0 || k < 1 || k > x->max_k) return LCP_ERR_INVALID;
+    if (!q || !x || !ticket || Q < 0 || k < 1 || k > x->max_k || lcph::index_is_wide(x)) return LCP_ERR_INVALID;
     if (Q > 0 && (!d_queries || !d_out_ids || !d_out_lcp)) return LCP_ERR_INVALID;
     std::lock_guard<std::mutex> lk(q->mu);
     x->shared = true;  // read by the persistent worker from now on

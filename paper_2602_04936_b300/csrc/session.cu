@@ -259,7 +259,8 @@ int lcp_session_create(const lcp_session_cfg_t* cfg, lcp_session_t* out) {
 }
 
 int lcp_session_add_index(lcp_session_t s, lcp_index_t index, int32_t* slot) {
-    if (!s || (!index && !s->cfg.dry_run) || !slot) return LCP_ERR_INVALID;
+    if (!s || (!index && !s->cfg.dry_run) || !slot || (index && lcph::index_is_wide(index)))
+        return LCP_ERR_INVALID;
     std::lock_guard<std::mutex> lk(s->mu);
     if (index) index->shared = true;  // used on the session's streams from now on
     s->idx.push_back(index);

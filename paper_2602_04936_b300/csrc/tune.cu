@@ -14,7 +14,8 @@ extern "C" {
 
 int lcp_autotune(lcp_index_t x, const void* d_queries, int64_t Q, int32_t k, lcp_stream_t stream,
                  lcp_tune_result_t* best) {
-    if (!x || !d_queries || Q < 1 || k < 1 || k > x->max_k || !best) return LCP_ERR_INVALID;
+    if (!x || !d_queries || Q < 1 || k < 1 || k > x->max_k || !best || lcph::index_is_wide(x))
+        return LCP_ERR_INVALID;
     if (x->N == 0) return LCP_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     int32_t* ids = nullptr;
@@ -86,7 +87,8 @@ int lcp_autotune(lcp_index_t x, const void* d_queries, int64_t Q, int32_t k, lcp
 }
 
 int lcp_set_search_shape(lcp_index_t x, int64_t Q, int32_t k, int32_t qpw, int32_t locate_warp) {
-    if (!x || Q < 1 || k < 1 || qpw < 0 || qpw > 32 || (locate_warp != 0 && locate_warp != 1))
+    if (!x || Q < 1 || k < 1 || qpw < 0 || qpw > 32 || (locate_warp != 0 && locate_warp != 1) ||
+        lcph::index_is_wide(x))
         return LCP_ERR_INVALID;
     lcph::SearchShape sh;
     sh.fused = qpw == 0 ? 1 : 0;

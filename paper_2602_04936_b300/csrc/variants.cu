@@ -188,7 +188,7 @@ extern "C" {
 
 int lcp_topk_bfs(lcp_index_t x, const void* d_queries, int64_t Q, int32_t k, int32_t* d_out_ids,
                  uint8_t* d_out_lcp, lcp_stream_t stream) {
-    if (!x || Q < 0 || k < 1) return LCP_ERR_INVALID;
+    if (!x || Q < 0 || k < 1 || lcph::index_is_wide(x)) return LCP_ERR_INVALID;
     if (Q > 0 && (!d_queries || !d_out_ids || !d_out_lcp)) return LCP_ERR_INVALID;
     int rc = lcph::run_mode(x, d_queries, Q, k, 0, d_out_ids, d_out_lcp, (cudaStream_t)stream, lcph::Mode::kBfs);
     if (rc == LCP_OK) {
@@ -201,7 +201,8 @@ int lcp_topk_bfs(lcp_index_t x, const void* d_queries, int64_t Q, int32_t k, int
 
 int lcp_tal_topk(lcp_index_t x, const void* d_queries, int64_t Q, int32_t k, int32_t depth, int32_t* d_out_ids,
                  uint8_t* d_out_lcp, lcp_stream_t stream) {
-    if (!x || Q < 0 || k < 1 || k > LCP_TAL_MAX_K || depth < 0 || depth > x->L) return LCP_ERR_INVALID;
+    if (!x || Q < 0 || k < 1 || k > LCP_TAL_MAX_K || depth < 0 || depth > x->L || lcph::index_is_wide(x))
+        return LCP_ERR_INVALID;
     if (Q > 0 && (!d_queries || !d_out_ids || !d_out_lcp)) return LCP_ERR_INVALID;
     int rc = lcph::run_mode(x, d_queries, Q, k, depth, d_out_ids, d_out_lcp, (cudaStream_t)stream,
                             lcph::Mode::kTal);

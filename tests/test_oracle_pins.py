@@ -307,3 +307,67 @@ def test_bfs_and_tal_reduce_to_the_definition():
     full = (b_i >= 0).all(axis=1)
     assert full.any() and np.array_equal(b_l[full], want_l[full])
 
+
+
+# ---- rows longer than 255 tokens: 16-bit LCPs (the paper's sustained shape) ----
+
+def _long_rows(rng, N, L, sigma, dt):
+    """Rows sharing long prefixes, exact duplicates, and rows that differ from
+    another only in the last token (LCP L - 1 against L)."""
+    base = rng.integers(0, sigma, size=(max(N // 4, 1), L))
+    rows = base[rng.integers(0, base.shape[0], N)].copy()
+    cut = rng.integers(L - 40, L + 1, N)
+    for i in range(N):
+        if cut[i] < L:
+            rows[i, cut[i]:] = rng.integers(0, sigma, L - cut[i])
+    rows[N // 2, -1] = (rows[N // 2, -1] + 1) % sigma  # last-token neighbour of a base row
+    rows[N - 1] = rows[0]  # an exact duplicate
+    return rows.astype(dt)
+
+
+@pytest.mark.parametrize("L,tb,sigma", [(256, 2, 3), (300, 1, 2), (256, 1, 4), (1000, 2, 2)])
+def test_wide_topk_against_python(L, tb, sigma):
+    """topk_wide against os.path.commonprefix + sorted() at L >= 256, where an
+    LCP of L needs more than 8 bits; queries include exact members, members
+    with only the last token changed, and random rows."""
+    rng = np.random.default_rng(L + tb)
+    dt = np.uint8 if tb == 1 else np.uint16
+    S = _long_rows(rng, 40, L, sigma, dt)
+    Qs = np.concatenate([S[rng.integers(0, 40, 6)], S[rng.integers(0, 40, 6)], rng.integers(0, sigma, (4, L))])
+    Qs[6:12, -1] = (Qs[6:12, -1].astype(np.int64) + 1) % sigma
+    Qs = Qs.astype(dt)
+    for k in (1, 3, 45):
+        ids, lc = oracle.topk_wide(S, Qs, k, threads=2)
+        assert lc.dtype == np.uint16
+        for r in range(len(Qs)):
+            w_ids, w_lc = _brute(S, Qs[r], k)
+            assert ids[r].tolist() == w_ids and lc[r].tolist() == w_lc, (k, r)
+    # a member query's top-1 is its smallest equal row, with LCP L (> 255)
+    ids, lc = oracle.topk_wide(S, S[:1], 1)
+    eq = np.nonzero((S == S[0]).all(1))[0]
+    assert ids[0, 0] == eq.min() and lc[0, 0] == L
+
+
+def test_wide_topk_equals_narrow_below_256():
+    """For L <= 255 both oracles state the same definition: equal outputs."""
+    rng = np.random.default_rng(5)
+    for L, tb, sigma in ((16, 1, 3), (255, 2, 2), (33, 2, 5)):
+        dt = np.uint8 if tb == 1 else np.uint16
+        S = _random_prefixy(rng, 300, L, sigma, dt)
+        Qs = S[rng.integers(0, 300, 50)].copy()
+        Qs[::2, L // 2:] = rng.integers(0, sigma, (25, L - L // 2))
+        a = oracle.topk_batch(S, Qs, 20)
+        b = oracle.topk_wide(S, Qs, 20)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1].astype(np.uint16), b[1])
+
+
+def test_wide_sorted_index_against_python_sort():
+    rng = np.random.default_rng(9)
+    S = _long_rows(rng, 60, 257, 3, np.uint16)
+    ids, H = oracle.sorted_index_wide(S)
+    want = sorted(range(len(S)), key=lambda i: (tuple(int(x) for x in S[i]), i))
+    assert ids.tolist() == want
+    for p in range(1, len(S)):
+        a, b = S[want[p - 1]], S[want[p]]
+        assert H[p] == len(os.path.commonprefix([tuple(a.tolist()), tuple(b.tolist())]))
+    assert H.max() == 257  # duplicates present: an LCP that needs 16 bits

@@ -26,6 +26,8 @@ Workloads (the paper's own inputs are synthetic; these follow its shapes):
   digits of a random-walk value in [0, 999999], most significant first], L=8.
 * ``serving_mix``  -- Poisson request arrivals, log-uniform batch sizes in
   [1, 4096], k drawn from {1, 10, 100}, index drawn uniformly.
+* ``sustained2m_L256`` -- the sustained shape: zipf_prefix rows of 256
+  tokens; copies keep a fixed prefix of 128 tokens (prefix_len).
 """
 from __future__ import annotations
 
@@ -202,7 +204,7 @@ def tree_rows(N: int, seed: int, L: int = 16, depth: int = 8, branch: int = 4,
 # queries
 # --------------------------------------------------------------------------
 
-def _mix_plan(Q: int, N: int, L: int, seed: int, item_offset: int = 0):
+def _mix_plan(Q: int, N: int, L: int, seed: int, item_offset: int = 0, fixed_cut: int | None = None):
     items = np.arange(item_offset, item_offset + Q, dtype=np.uint64)
     is_copy = rand_uniform(seed, STREAM_QMIX, items, 0) < 0.5
     if N == 0:
@@ -210,16 +212,19 @@ def _mix_plan(Q: int, N: int, L: int, seed: int, item_offset: int = 0):
     src = np.minimum((rand_uniform(seed, STREAM_QMIX, items, 1) * max(N, 1)).astype(np.int64),
                      max(N - 1, 0))
     cut = np.minimum((rand_uniform(seed, STREAM_QMIX, items, 2) * (L + 1)).astype(np.int64), L)
+    if fixed_cut is not None:
+        cut[:] = min(fixed_cut, L)
     cut = np.where(is_copy, cut, 0)
     return items, is_copy, src, cut
 
 
 def zipf_prefix_queries(S: np.ndarray, Q: int, V: int, s: float, seed: int,
-                        item_offset: int = 0, impl: str = "c") -> np.ndarray:
-    """Query mix over a zipf_prefix dataset S (see module docstring)."""
+                        item_offset: int = 0, impl: str = "c", fixed_cut: int | None = None) -> np.ndarray:
+    """Query mix over a zipf_prefix dataset S (see module docstring); with
+    `fixed_cut`, every copy keeps exactly its first `fixed_cut` tokens."""
     N, L = S.shape
     z = Zipf(V, s)
-    items, is_copy, src, cut = _mix_plan(Q, N, L, seed, item_offset)
+    items, is_copy, src, cut = _mix_plan(Q, N, L, seed, item_offset, fixed_cut)
     if impl == "c":
         Sx = S if N > 0 else np.zeros((1, L), np.uint16)
         return _c_zipf(Q, L, V, z.cdf, stream_key(seed, STREAM_QTOK), _prefix_root(seed),
@@ -347,6 +352,10 @@ WORKLOADS = {
     # the paper's TAL benchmark shape: 20M items, 256 prefix buckets (uniform
     # first token over 256 values, bucket depth 1), 10,000 queries
     "tal20m": dict(N=20_000_000, L=16, token_bytes=1, vocab=256, depth=1, Q=10_000, k=10, seed=6),
+    # the paper's sustained shape: top-1 over 2M sequences of max_len 256,
+    # one query at a time; copies keep their first prefix_len = 128 tokens
+    "sustained2m_L256": dict(N=2_000_000, L=256, token_bytes=2, vocab=32768, s=1.05, Q=100_000, k=1,
+                             seed=7, prefix_len=128),
 }
 
 
@@ -359,4 +368,4 @@ def make_dataset(name: str, N: int | None = None, Q: int | None = None):
         S = tree_rows(N, w["seed"], L=w["L"])
         return S, tree_queries(S, Q, w["seed"]), w["k"]
     S = zipf_prefix_rows(N, w["L"], w["vocab"], w["s"], w["seed"])
-    return S, zipf_prefix_queries(S, Q, w["vocab"], w["s"], w["seed"]), w["k"]
+    return S, zipf_prefix_queries(S, Q, w["vocab"], w["s"], w["seed"], fixed_cut=w.get("prefix_len")), w["k"]
