@@ -418,22 +418,28 @@ def issue_roofline(kernel, Q, launch_ms, sm_mhz, sms):
             "peak_source": "%d SMs x 4 schedulers x 1 warp instruction/clock x %.0f MHz (sampled)" % (sms, sm_mhz)}
 
 
-def scan_alu_roofline(Q, N, ms, sm_mhz, sms):
-    """The full scan at large batches is bound by integer work: Q x N
-    (query, row) screens of 2 integer operations each -- a subtraction from
-    the packed first word's upper half (issued as a multiply-add, on the FMA
-    pipe) and a running minimum over eight rows (ALU pipe); the compare and
-    branch per eight rows are not counted -- against the two pipes' 16 lanes
-    each per scheduler, 4 schedulers per SM, at the sampled SM clock."""
-    if not sm_mhz or ms <= 0:
-        return None
-    ops = 2.0 * Q * N
-    ach = ops / (ms / 1e3)
-    pk = sms * 4 * 2 * 16 * sm_mhz * 1e6
-    return {"ops_per_pair": 2, "achieved": round(ach / 1e12, 3), "peak": round(pk / 1e12, 3),
-            "unit": "Tops/s", "frac": round(ach / pk, 4),
-            "peak_source": "%d SMs x 4 schedulers x (16 ALU + 16 FMA-pipe lanes) x %.0f MHz (sampled)"
-                           % (sms, sm_mhz)}
+def scan_hbm_model(Q, N, W, k, ms, peak):
+    """The full scan's byte model for a batch: every row once (N x W words),
+    the queries and the results -- N*W*8 + Q*W*8 + Q*k*5 bytes -- over the
+    measured copy bandwidth.  It binds small batches; large ones are bound by
+    the L2 stream of the word-0 plane (scan_stream_model)."""
+    b = N * W * 8 + Q * W * 8 + Q * k * 5
+    return {"bytes": int(b), "achieved_gbs": round(b / (ms / 1e3) / 1e9, 1), "peak_gbs": peak,
+            "frac": round(b / (ms / 1e3) / 1e9 / peak, 4)}
+
+
+def scan_stream_model(Q, N, ms, threads=256, sample=65536):
+    """Large batches: each CTA of `threads` queries streams the 8-byte word-0
+    plane of its rows from L2 into shared memory, once over a sample of
+    `sample` rows (the shared levels' seed pass) and once over all N; rows
+    outside a warp's query ranges cost one lane-parallel test.  Bytes streamed
+    per launch and their rate (no measured L2 peak to divide by)."""
+    tiles = (Q + threads - 1) // threads
+    b = tiles * 8 * (N + (sample if N >= 4 * sample else 0))
+    return {"plane_bytes_streamed": int(b), "achieved_gbs": round(b / (ms / 1e3) / 1e9, 1),
+            "pairs_per_s": round(Q * N / (ms / 1e3), 1),
+            "note": "the batch is ordered by first word; a warp screens each row once against the union "
+                    "of its 32 queries' prefix ranges, so query-row pairs are no longer the unit of work"}
 
 
 def committed_traffic(kernel, Q):
@@ -685,7 +691,7 @@ def run_ours(args, world, rank, local):
         same = bool(torch.equal(out_ids, sids) and torch.equal(out_lcp, slc))
         paths["full_scan"] = {"ms": round(scan_ms, 3), "qps": round(Q / (scan_ms / 1e3), 1),
                               "energy_j_per_query": scan_j, "identical_to_indexed": same,
-                              "alu": scan_alu_roofline(Q, N, scan_ms, clocks.get("sm_mhz"), sms)}
+                              "stream": scan_stream_model(Q, N, scan_ms)}
         paths["indexed_vs_full_scan_speedup_query_only"] = round(scan_ms / query_ms, 1)
         # per-batch latency (CUDA events around each call)
         lat = {"indexed": {}, "full_scan": {}}
@@ -708,6 +714,9 @@ def run_ours(args, world, rank, local):
                 lat[name][str(bs)] = {"p50": round(float(np.percentile(times, 50)), 4),
                                       "p99": round(float(np.percentile(times, 99)), 4),
                                       "reps": len(times)}
+                if name == "full_scan":
+                    lat[name][str(bs)]["hbm_model_p50"] = scan_hbm_model(
+                        bs, N, (L * tb + 7) // 8, k, float(np.percentile(times, 50)), peak)
         paths["latency_ms"] = lat
         idx.close()
         del sids, slc

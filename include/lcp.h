@@ -172,16 +172,18 @@ LCP_API int lcp_topk_batch_host(lcp_index_t index, const void* h_queries, int64_
  * LCP of every query against all N rows, keeping per query the k best under
  * (LCP descending, id ascending).  Needs no index.
  * d_tokens [N, L], d_queries [Q, L] device memory in format fmt.
- * 1 <= k <= LCP_SCAN_MAX_K.  Batches of up to 512 queries take a threshold
+ * 1 <= k <= LCP_SCAN_MAX_K.  Batches of up to 160 queries take a threshold
  * selection (per-slice counts of rows by LCP give the k-th largest LCP d*, a
  * second pass collects the rows above d* and the first rows at d* by id);
- * larger batches keep the k best keys per thread and N-slice (a log of up
- * to k + 64 rows, compacted as it fills) and merge them.
+ * larger batches are ordered by the queries' first words and keep, per
+ * thread and N-slice, the rows that can still be in the query's top k (a
+ * log of up to k + 64 rows, compacted as it fills), then merge them.
  * Both return the same bytes.  Temporary device memory from the
  * stream-ordered allocator: about N * 8 + Q * (12 * k + 4 * S * (L + 1))
- * bytes for small batches (S = N-slices per query, Q * S about 64 per
- * multiprocessor, S <= 8192), N * 8 + Q * (k + 64) * 8 per N-slice for
- * larger ones.
+ * bytes for small batches (S = N-slices per query, about 64 warps per
+ * multiprocessor over all (query group, slice) pairs, S <= 8192), and
+ * N * 8 + Q * (16 + S * ((k + 64) * 8 + 4)) bytes for larger ones (S <=
+ * 2048 slices; plus 24 bytes a query past 4,096 queries for the sort).
  * ---------------------------------------------------------------------- */
 LCP_API int lcp_scan_topk(const void* d_tokens, int64_t N, lcp_format_t fmt, const void* d_queries,
                   int64_t Q, int32_t k, int32_t* d_out_ids, uint8_t* d_out_lcp,
@@ -222,9 +224,10 @@ LCP_API int lcp_scan_top1_wide(const void* d_tokens, int64_t N, lcp_format_t fmt
  *
  * Scratch: a fixed array of LCP_SCAN_NOALLOC_SCRATCH_BYTES inside the
  * library's device image, held by every GPU that loads the library until the
- * process exits.  A call needs round_up(N * 8, 256) + Q * (k + 64) * 8 bytes of it;
- * larger requests return LCP_ERR_INVALID without enqueuing anything (split
- * the query batch).  The call allocates nothing: no cudaMalloc, cudaFree or
+ * process exits.  A call needs round_up(N * 8, 256) + round_up(Q * 4, 256) +
+ * Q * (k + 64) * 8 bytes of it (the rows' first words, then one N-slice of
+ * per-query logs and their counts); larger requests return LCP_ERR_INVALID
+ * without enqueuing anything (split the query batch).  The call allocates nothing: no cudaMalloc, cudaFree or
  * allocating library routine.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) -- make that first call
  * before any stream capture.  Every call shares the one array: calls that

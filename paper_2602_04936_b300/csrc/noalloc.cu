@@ -72,50 +72,61 @@ extern "C" int lcp_scan_topk_noalloc(const void* d_tokens, int64_t N, lcp_format
         LCP_CUDA_TRY(cudaMemsetAsync(d_out_lcp, 0, (size_t)Q * k, s));
         return LCP_OK;
     }
-    // Scratch layout: [plane 0: N words][lists: S x Q x (k + kLogSlack) keys].
-    // One merge pass reads the lists and writes the outputs, so S is capped at the
-    // number of lists one merge CTA can sort.
-    int kp2 = 1;
-    while (kp2 < k) kp2 <<= 1;
-    const int64_t G = kMergeCap / kp2 > 0 ? kMergeCap / kp2 : 1;
+    // Scratch layout: [plane 0: N words][counts: S x Q][lists: S x Q x (k +
+    // kLogSlack) keys], each part starting on a 256-byte boundary.  The batch
+    // is scanned in its own order (no sort, no floor pass: those would need
+    // more scratch); the results are the same bytes.
     const uint64_t cap = (uint64_t)LCP_SCAN_NOALLOC_SCRATCH_BYTES;
     const uint64_t plane_bytes = ((uint64_t)N * 8 + 255) & ~255ull;
     const int lcap = k + kLogSlack;  // log entries per (slice, query)
-    const uint64_t list_bytes = (uint64_t)Q * (uint64_t)lcap * 8;
-    if (plane_bytes + list_bytes > cap) return LCP_ERR_INVALID;  // too large even with one slice
+    auto need = [&](int64_t S) {
+        return plane_bytes + (((uint64_t)S * Q * 4 + 255) & ~255ull) + (uint64_t)S * Q * lcap * 8;
+    };
+    if (need(1) > cap) return LCP_ERR_INVALID;  // too large even with one slice
     const int64_t qtiles = (Q + kScanPartialThreads - 1) / kScanPartialThreads;
-    int64_t S = (148 * 8 + qtiles - 1) / qtiles;
-    int64_t maxS = (N + 1023) / 1024;
-    int64_t fitS = (int64_t)((cap - plane_bytes) / list_bytes);
+    int64_t S = (148 * 4 + qtiles - 1) / qtiles;
+    const int64_t maxS = (N + 1023) / 1024;
     if (S > maxS) S = maxS;
-    if (S > G) S = G;
-    if (S > fitS) S = fitS;
+    if (S > kMergeMaxLists) S = kMergeMaxLists;
+    while (S > 1 && need(S) > cap) --S;
     if (S < 1) S = 1;
     const int64_t slice = (N + S - 1) / S;
     S = (N + slice - 1) / slice;
 
     void* base = nullptr;
     LCP_CUDA_TRY(scratch_address(&base));
-    uint64_t* plane0 = reinterpret_cast<uint64_t*>(base);
-    uint64_t* heaps = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(base) + plane_bytes);
+    unsigned char* b = reinterpret_cast<unsigned char*>(base);
+    uint64_t* plane0 = reinterpret_cast<uint64_t*>(b);
+    int32_t* counts = reinterpret_cast<int32_t*>(b + plane_bytes);
+    uint64_t* lists = reinterpret_cast<uint64_t*>(b + plane_bytes + (((uint64_t)S * Q * 4 + 255) & ~255ull));
     // Nothing in the scratch needs to start at zero: plane 0 is written in
-    // full by the pack kernel and every heap slot is written by the scan
-    // kernel before the merge reads it.  Calls that overlap on the GPU share
-    // the array and race; callers must order them (one stream, or events).
+    // full by the pack kernel, every count and every log slot the merge reads
+    // by the scan kernel.  Calls that overlap on the GPU share the array and
+    // race; callers must order them (one stream, or events).
     RowFmt f = make_fmt(fmt.token_bytes, fmt.L, d_tokens);
     RowFmt qf = make_fmt(fmt.token_bytes, fmt.L, d_queries);
     LCP_LAUNCH(k_pack_plane0, (unsigned)((N + 255) / 256), 256, 0, s,
                reinterpret_cast<const uint8_t*>(d_tokens), f, N, plane0);
-    dim3 grid((unsigned)qtiles, (unsigned)S);
-    LCP_LAUNCH(k_scan_partial, grid, kScanPartialThreads, 0, s, reinterpret_cast<const uint8_t*>(d_tokens),
-               plane0, f, N, reinterpret_cast<const uint8_t*>(d_queries), qf, Q, k, lcap, slice, heaps);
-    int P = 1;
-    while (P < S * k) P <<= 1;
+    ScanArgs a;
+    a.tokens = reinterpret_cast<const uint8_t*>(d_tokens);
+    a.plane0 = plane0;
+    a.f = f;
+    a.N = N;
+    a.queries = reinterpret_cast<const uint8_t*>(d_queries);
+    a.qf = qf;
+    a.Q = Q;
+    a.order = nullptr;
+    a.floor = nullptr;
+    a.k = k;
+    a.cap = lcap;
+    a.slice = slice;
+    a.lists = lists;
+    a.counts = counts;
+    LCP_LAUNCH(k_scan_partial, dim3((unsigned)qtiles, (unsigned)S), kScanPartialThreads, 0, s, a);
     LCP_CUDA_TRY(cudaFuncSetAttribute(k_scan_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(uint64_t) * kMergeCap * 2)));
-    dim3 mg((unsigned)Q, 1);
-    LCP_LAUNCH(k_scan_merge, mg, 256, sizeof(uint64_t) * P, s, heaps, lcap, Q, k, (int)S, (int)S, P,
-               (uint64_t*)nullptr, 1, d_out_ids, d_out_lcp);
+                                      (int)(sizeof(uint64_t) * kMergeCap)));
+    LCP_LAUNCH(k_scan_merge, (unsigned)Q, 256, sizeof(uint64_t) * kMergeCap, s, lists, counts, lcap, Q, (int)S, k,
+               (const int32_t*)nullptr, d_out_ids, d_out_lcp);
     LCP_CUDA_TRY(cudaGetLastError());
     return LCP_OK;
 }

@@ -1,33 +1,41 @@
 // Full scan top-k: LCP of every query against all N rows (the paper's "full
-// scan" baseline, Sec. 7), no index.
+// scan" baseline, Sec. 7), no index over the rows.
 //
+// Batches of more than kSelMaxQ queries:
 //   k_pack_plane0   word 0 of every row, packed, into one contiguous plane
 //                   (8 bytes a row: 16 MB at N=2M, so it stays in L2 while
-//                   thousands of query tiles stream over it).
+//                   the query tiles stream over it).
+//   (batch order)   the queries sorted by their first word (one CTA up to
+//                   4,096 queries, the radix sort above), so that a warp's 32
+//                   queries are neighbours in word-0 order.
 //   k_scan_partial  grid = (query tiles) x (N slices); a thread owns one query
-//                   and the k best keys (255-LCP)<<32 | id of its slice.
-//                   Rows arrive in increasing id, so once k rows are held a
-//                   row matters only with an LCP above a level `worst` that
-//                   k held rows reach; that test (the first worst+1 tokens
-//                   equal) is one compare of word 0's XOR with q against a
-//                   power of two, screened eight rows at a time on the
-//                   words' upper halves (two 16-byte shared-memory loads, a
-//                   range test per row as a multiply-add on the FMA pipe and
-//                   a minimum on the ALU pipe), and only rows passing it pay
-//                   for an exact LCP over the remaining words.  Rows taken are
-//                   appended to a log in id order; when the log holds
-//                   k + kLogSlack rows, worst is raised to the k-th largest
-//                   LCP and the log cut back to k rows (those above worst
-//                   and the earliest at it) -- a few passes over the log
-//                   every kLogSlack rows instead of a heap sift per row.
-//   k_scan_merge    keys are unique, so the k smallest over a query's slice
-//                   lists are order independent: sort G lists' keys in shared
-//                   memory, keep k, repeat until one list is left, write out.
+//                   and logs the rows of its slice that can still be in its
+//                   top k: rows arrive in increasing id, so once k are held
+//                   only rows above a level `worst` can matter, i.e. rows whose
+//                   word 0 lies in a prefix range [lo, hi] of q's.  The warp
+//                   screens a row with one lane-parallel test against the
+//                   union of its lanes' ranges (narrow: the queries are
+//                   neighbours), and only rows inside it are tested by every
+//                   lane; the exact LCP over later words is computed for rows
+//                   inside a lane's own range.  When the log holds k + 64 rows
+//                   it is cut back to k (rows above the k-th largest LCP, the
+//                   earliest at it) and worst rises.  Levels with k rows at or
+//                   above them are shared between a query's slices (an atomic
+//                   maximum, read at every tile), seeded by a first pass over a
+//                   sample of the rows.
+//   k_scan_merge    keys (255 - LCP) << 32 | id are unique, so the k smallest
+//                   over a query's slice logs are order independent: keys below
+//                   the best shared level and, once k are held, above the k-th
+//                   are dropped as they are read; the rest are sorted in shared
+//                   memory.  Written to the query's own output row.
+// Smaller batches take the threshold selection further below.
 #include "scan.cuh"
+#include "sort.cuh"
 
 namespace lcpk {
 
 constexpr int kScanTile = 2048;     // plane-0 words staged per smem tile
+constexpr int kCompactBins = 16;    // levels above `worst` a log compaction counts in one pass
 constexpr uint64_t kKeyInf = ~0ull;
 
 // Packed word 0 of a row.  Aligned rows are read with one 8-byte load that
@@ -53,92 +61,125 @@ __device__ __forceinline__ uint64_t prefix_mask(int t, int bits) {
     return b >= 64 ? ~0ull : (b == 0 ? 0ull : (~0ull << (64 - b)));
 }
 
-__global__ void __launch_bounds__(kScanPartialThreads) k_scan_partial(const uint8_t* __restrict__ tokens,
-                                                      const uint64_t* __restrict__ plane0, RowFmt f,
-                                                      int64_t N, const uint8_t* __restrict__ queries,
-                                                      RowFmt qf, int64_t Q, int k, int cap, int64_t slice,
-                                                      uint64_t* __restrict__ lists) {
+__global__ void __launch_bounds__(kScanPartialThreads) k_scan_partial(const ScanArgs a) {
     __shared__ __align__(16) uint64_t tile[kScanTile];
     __shared__ __align__(16) uint32_t tile_hi[kScanTile];  // the words' upper halves
-    const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t s0 = (int64_t)blockIdx.y * slice;
-    const int64_t s1 = s0 + slice < N ? s0 + slice : N;
-    const bool active = qi < Q;
-    const uint8_t* qrow = active ? row_of(queries, qi, qf) : nullptr;
-    const uint64_t q0 = active ? pack_word(qrow, 0, qf) : 0;
+    __shared__ uint16_t cbins[kCompactBins][kScanPartialThreads];
+    const RowFmt& f = a.f;
+    const int k = a.k;
+    const unsigned lane = lane_id();
+    const int64_t qs = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // position in the batch order
+    const int64_t s0 = (int64_t)blockIdx.y * a.slice;
+    const int64_t s1 = s0 + a.slice < a.N ? s0 + a.slice : a.N;
+    const bool active = qs < a.Q;
+    const int64_t qi = active ? (a.order ? (int64_t)a.order[qs] : qs) : 0;
+    const uint8_t* qrow = active ? row_of(a.queries, qi, a.qf) : nullptr;
+    const uint64_t q0 = active ? pack_word(qrow, 0, a.qf) : 0;
     // the thread's log: keys (255 - LCP) << 32 | id of the rows taken, in id
     // order (rows arrive in increasing id), at most cap of them
-    uint64_t* log = lists + ((int64_t)blockIdx.y * Q + (active ? qi : 0)) * cap;
+    uint64_t* log = a.lists + ((int64_t)blockIdx.y * a.Q + (active ? qs : 0)) * a.cap;
     int n = 0;
-    int worst = -1;  // -1 until k rows are logged; then a level with >= k logged rows at or above it
-    // A row can matter only with LCP > worst: its first worst + 1 tokens
-    // equal to q's, i.e. (r ^ q0) < T for T = 2^(64 - (worst + 1) * bits)
-    // (T = 1 past word 0: word 0 all equal).  The screen on the upper halves:
-    // (r ^ q0) < T implies (r_hi ^ q_hi) < max(T >> 32, 1), the two tests
-    // being equal when T >= 2^32 (the tokens to match lie in the upper half).
-    uint64_t T = 0;
-    uint32_t Th = 0;
-    const uint32_t qh = (uint32_t)(q0 >> 32);
-    // The screen as a range test: (r_hi ^ q_hi) < Th = 2^m iff
-    // r_hi - lo < Th (mod 2^32) with lo = q_hi rounded down to a multiple of
-    // 2^m.  The subtraction is written as a multiply-add by a factor the
-    // compiler cannot fold (1 for every legal block size, <= 128 threads),
-    // so that it runs on the FMA pipe beside the minimums on the ALU pipe.
-    uint32_t neg_lo = 0;
-    const uint32_t unit = (blockDim.x + 127u) / 128u;
-    auto sub_lo = [&](uint32_t x) {
-        uint32_t d;
-        asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(unit), "r"(neg_lo));
-        return d;
+    // -1 until k rows are logged (every row is taken); then a level with k
+    // rows of this slice, of smaller id, at or above it -- or, from the
+    // floor, with k rows anywhere at or above it + 1 -- so that only rows of
+    // LCP > worst can still matter: rows whose first worst + 1 tokens equal
+    // q's, i.e. whose word 0 lies in [lo, hi] (all of word 0 equal once
+    // worst + 1 >= tpw; deeper words then decide)
+    int worst = -1;
+    int lvl = 0;  // a level with k rows anywhere at or above it (0: none known)
+    uint64_t T = 0, lo = 0, hi = ~0ull;
+    auto set_range = [&]() {
+        if (worst < 0) {
+            lo = 0;
+            hi = ~0ull;
+            return;
+        }
+        const int b = (worst + 1) * f.bits;
+        T = b >= 64 ? 1ull : (1ull << (64 - b));
+        lo = q0 & ~(T - 1);
+        hi = lo | (T - 1);
     };
+    // Takes a shared level: k rows have LCP >= fl, so rows below it cannot
+    // be in the answer.
+    auto take_floor = [&](int fl) {
+        if (fl <= lvl) return false;
+        lvl = fl;
+        if (fl - 1 <= worst) return false;
+        worst = fl - 1;
+        set_range();
+        return true;
+    };
+    if (active && a.floor) take_floor((int)ld_relaxed(reinterpret_cast<const uint32_t*>(a.floor) + qs));
+    set_range();
     auto lam_of = [](uint64_t e) { return 255 - (int)(e >> 32); };
     // Raises worst to the largest w with >= k logged rows of LCP >= w and
     // keeps the rows above w and the earliest (smallest-id) ones at w, k in
     // all.  A row dropped here, or refused later for LCP <= worst, has k
-    // logged rows of smaller id and no smaller LCP: it is in no top k.
+    // rows of smaller id and no smaller LCP: it is in no top k.
+    uint16_t* hist = &cbins[0][threadIdx.x];  // this thread's level counts, stride kScanPartialThreads
     auto compact = [&]() {
-        int w, above;
-        if (worst < 0) {  // the first k rows: w = their smallest LCP, all kept
+        int w;
+        if (worst < 0) {  // the first k rows (n == k): w = their smallest LCP, all kept
             w = 255;
             for (int i = 0; i < n; ++i) w = min(w, lam_of(log[i]));
-            above = 0;
-            for (int i = 0; i < n; ++i) above += lam_of(log[i]) > w;
         } else {
+            // one pass: counts of the logged levels worst + 1 + j (bin kCompactBins - 1
+            // open-ended; rows at or below worst, logged before a shared level
+            // raised it, are not counted and are dropped below)
+#pragma unroll
+            for (int j = 0; j < kCompactBins; ++j) hist[j * kScanPartialThreads] = 0;
+            for (int i = 0; i < n; ++i) {
+                const int d = lam_of(log[i]) - worst - 1;
+                if (d >= 0) ++hist[min(d, kCompactBins - 1) * kScanPartialThreads];
+            }
+            // the smallest w >= worst with fewer than k logged rows above it
+            int above = 0;
+            for (int j = 0; j < kCompactBins; ++j) above += hist[j * kScanPartialThreads];
             w = worst;
-            for (;;) {
-                int c = 0;
-                for (int i = 0; i < n; ++i) c += lam_of(log[i]) > w;
-                if (c < k) {
-                    above = c;
-                    break;
-                }
+            for (int j = 0; j < kCompactBins - 1 && above >= k; ++j) {
+                above -= hist[j * kScanPartialThreads];
                 ++w;
             }
+            if (above >= k) {  // beyond the bins (rare): count level by level
+                for (;;) {
+                    int c = 0;
+                    for (int i = 0; i < n; ++i) c += lam_of(log[i]) > w;
+                    if (c < k) break;
+                    ++w;
+                }
+            }
         }
-        int eq = k - above;
+        int above = 0;
         int m = 0;
-        for (int i = 0; i < n; ++i) {
-            const uint64_t e = log[i];
-            const int l = lam_of(e);
-            if (l > w || (l == w && eq-- > 0)) log[m++] = e;
+        if (worst >= 0 || n > k) {
+            for (int i = 0; i < n; ++i) above += lam_of(log[i]) > w;
+            int eq = k - above;
+            for (int i = 0; i < n; ++i) {
+                const uint64_t e = log[i];
+                const int l = lam_of(e);
+                if (l > w || (l == w && eq-- > 0)) log[m++] = e;
+            }
+        } else {
+            m = n;
         }
         n = m;
         worst = w;
-        const int b = (worst + 1) * f.bits;
-        T = b >= 64 ? 1ull : (1ull << (64 - b));
-        Th = b >= 32 ? 1u : (uint32_t)(T >> 32);
-        neg_lo = 0u - (qh & ~(Th - 1u));
+        set_range();
+        if (w > lvl) {  // this slice alone has k rows at or above w: share it
+            lvl = w;
+            if (a.floor) atomicMax(a.floor + qs, w);
+        }
     };
-    auto row_at = [&](int64_t id, uint64_t r) {  // a row that may matter
+    auto row_at = [&](int64_t id, uint64_t r) {  // a row inside the thread's range
         int lam;
         const uint64_t x = r ^ q0;
         if (x) {
             lam = __clzll((long long)x) / f.bits;
         } else {
             lam = f.L;
-            const uint8_t* row = row_of(tokens, id, f);
+            const uint8_t* row = row_of(a.tokens, id, f);
             for (int w = 1; w < f.W; ++w) {
-                const uint64_t y = pack_word(row, w, f) ^ pack_word(qrow, w, qf);
+                const uint64_t y = pack_word(row, w, f) ^ pack_word(qrow, w, a.qf);
                 if (y) {
                     lam = w * f.tpw + (__clzll((long long)y) / f.bits);
                     break;
@@ -148,95 +189,221 @@ __global__ void __launch_bounds__(kScanPartialThreads) k_scan_partial(const uint
         if (lam > f.L) lam = f.L;
         if (worst >= 0 && lam <= worst) return;
         log[n++] = ((uint64_t)(255 - lam) << 32) | (uint64_t)id;
-        if (worst < 0 ? n == k : n == cap) compact();
+        if (worst < 0 ? n == k : n == a.cap) compact();
     };
+    // The warp's screen: the union of its lanes' ranges lies in [WL, WL +
+    // span] on the upper halves of word 0.  The batch is ordered by the
+    // queries' first words, so neighbouring lanes hold neighbouring ranges
+    // and the union is narrow once the lanes' levels have risen: a lane tests
+    // one row of each 32 against it, and only the rows inside are compared
+    // by every lane with its own query.
+    uint32_t WL = 0, span = 0;
+    auto refresh = [&]() {
+        WL = __reduce_min_sync(0xffffffffu, active ? (uint32_t)(lo >> 32) : 0xffffffffu);
+        const uint32_t WH = __reduce_max_sync(0xffffffffu, active ? (uint32_t)(hi >> 32) : 0u);
+        span = WH - WL;
+    };
+    const bool warp_any = __any_sync(0xffffffffu, active);
+    refresh();
     for (int64_t t0 = s0; t0 < s1; t0 += kScanTile) {
         const int tn = (int)(s1 - t0 < kScanTile ? s1 - t0 : kScanTile);
         __syncthreads();
         for (int j = threadIdx.x; j < tn; j += blockDim.x) {
-            const uint64_t w = plane0[t0 + j];
+            const uint64_t w = a.plane0[t0 + j];
             tile[j] = w;
             tile_hi[j] = (uint32_t)(w >> 32);
         }
         __syncthreads();
-        if (!active) continue;
-        int j = 0;
-        // the first k rows are logged unconditionally (the same rows for
-        // every thread of the CTA: all start at s0)
-        for (; j < tn && worst < 0; ++j) row_at(t0 + j, tile[j]);
-        for (; j < tn && (j & 7); ++j)
-            if ((tile[j] ^ q0) < T) row_at(t0 + j, tile[j]);
-        // eight rows per step: two 16-byte loads of upper halves, their XORs
-        // with q's and a minimum; rows pass rarely
-        for (; j + 8 <= tn; j += 8) {
-            const uint4 a = *reinterpret_cast<const uint4*>(tile_hi + j);
-            const uint4 b = *reinterpret_cast<const uint4*>(tile_hi + j + 4);
-            const uint32_t m = min(min(min(sub_lo(a.x), sub_lo(a.y)), min(sub_lo(a.z), sub_lo(a.w))),
-                                   min(min(sub_lo(b.x), sub_lo(b.y)), min(sub_lo(b.z), sub_lo(b.w))));
-            if (m >= Th) continue;
-#pragma unroll 1
-            for (int u = 0; u < 8; ++u) {
-                const uint64_t r = tile[j + u];
-                if ((r ^ q0) < T) row_at(t0 + j + u, r);
-            }
+        if (!warp_any) continue;  // warp-uniform
+        if (a.floor) {  // levels other slices have shared since
+            const bool up = active && take_floor((int)ld_relaxed(reinterpret_cast<const uint32_t*>(a.floor) + qs));
+            if (__any_sync(0xffffffffu, up)) refresh();
         }
-        for (; j < tn; ++j)
-            if ((tile[j] ^ q0) < T) row_at(t0 + j, tile[j]);
+        for (int j0 = 0; j0 < tn; j0 += 32) {
+            const int j = j0 + (int)lane;
+            unsigned m = __ballot_sync(0xffffffffu, j < tn && tile_hi[j] - WL <= span);
+            bool moved = false;
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                const uint64_t r = tile[j0 + b];
+                if (active && (worst < 0 || (r ^ q0) < T)) {
+                    const int w0 = worst;
+                    row_at(t0 + j0 + b, r);
+                    moved |= worst != w0;
+                }
+            }
+            if (__any_sync(0xffffffffu, moved)) refresh();
+        }
     }
     if (active) {
         if (n > k) compact();
-        for (int j = n; j < k; ++j) log[j] = kKeyInf;
+        if (a.counts) a.counts[(int64_t)blockIdx.y * a.Q + qs] = n | (lvl << 16);
     }
 }
 
-// Reduces groups of G lists of k keys per query to one list each (sorted when
-// `final`, which then writes ids and LCPs); list l of query q starts at
-// in[(l * Q + q) * in_stride].  grid = (Q, groups).
-__global__ void __launch_bounds__(256) k_scan_merge(const uint64_t* __restrict__ in, int in_stride,
-                                                    int64_t Q, int k, int nlists, int G, int P,
-                                                    uint64_t* __restrict__ out, int final_pass,
+// The k smallest keys over the S lists of batch position qs (counts[s][qs]
+// = valid keys | level << 16, the level having k rows at or above it),
+// sorted, written to the query's output row.  Keys below the highest such
+// level, and -- once k keys are held -- keys above the k-th, cannot be in the
+// answer and are dropped as they are read; the rest collect in shared memory,
+// which is sorted (k kept) whenever it fills and at the end.  Keys are
+// unique, so the result does not depend on the order of reading.  One CTA per
+// batch position.
+__global__ void __launch_bounds__(256) k_scan_merge(const uint64_t* __restrict__ lists,
+                                                    const int32_t* __restrict__ counts, int cap, int64_t Q,
+                                                    int S, int k, const int32_t* __restrict__ order,
                                                     int32_t* __restrict__ out_ids,
                                                     uint8_t* __restrict__ out_lcp) {
-    extern __shared__ uint64_t keys[];
-    const int64_t q = blockIdx.x;
-    const int g = blockIdx.y;
-    const int l0 = g * G;
-    const int nl = nlists - l0 < G ? nlists - l0 : G;
-    const int n = nl * k;
-    for (int t = threadIdx.x; t < P; t += blockDim.x) {
-        uint64_t v = kKeyInf;
-        if (t < n) {
-            int l = t / k, j = t - l * k;
-            v = in[((int64_t)(l0 + l) * Q + q) * in_stride + j];
+    extern __shared__ uint64_t keys[];           // kMergeCap
+    __shared__ int32_t pre[kMergeMaxLists + 1];  // exclusive prefix of the lists' counts
+    __shared__ int32_t wsum[8], wmax[8];
+    __shared__ int used_sh;
+    const int64_t qs = blockIdx.x;
+    const int64_t qi = order ? (int64_t)order[qs] : qs;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int carry = 0, F = 0;
+    for (int b0 = 0; b0 < S; b0 += 256) {
+        const int s = b0 + tid;
+        const int raw = s < S ? counts[(int64_t)s * Q + qs] : 0;
+        const int c = raw & 0xffff;
+        int x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        keys[t] = v;
+        const int lv = __reduce_max_sync(0xffffffffu, raw >> 16);
+        if (lane == 31) wsum[warp] = x;
+        if (lane == 0) wmax[warp] = lv;
+        __syncthreads();
+        int add = carry;
+        for (int w = 0; w < warp; ++w) add += wsum[w];
+        for (int w = 0; w < 8; ++w) F = max(F, wmax[w]);
+        if (s < S) pre[s] = add + x - c;
+        __syncthreads();
+        if (tid == 255) wsum[0] = add + x;  // the round's inclusive total
+        __syncthreads();
+        carry = wsum[0];
+        __syncthreads();
+    }
+    const int total = carry;
+    if (tid == 0) {
+        pre[S] = total;
+        used_sh = 0;
+    }
+    __syncthreads();
+    // keys >= thr are dropped: LCP below F, or (later) worse than the k-th held
+    uint64_t thr = (uint64_t)(256 - F) << 32;
+    int used = 0;
+    auto sort_keep = [&]() {  // sorts keys[0, used) and keeps the best k
+        int P = 1;
+        while (P < used) P <<= 1;
+        for (int t = used + tid; t < P; t += blockDim.x) keys[t] = kKeyInf;
+        __syncthreads();
+        for (int size = 2; size <= P; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int t = tid; t < P; t += blockDim.x) {
+                    const int u = t ^ stride;
+                    if (u > t) {
+                        const uint64_t x = keys[t], y = keys[u];
+                        const bool up = (t & size) == 0;
+                        if ((x > y) == up) {
+                            keys[t] = y;
+                            keys[u] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (used > k) used = k;
+        if (used == k) thr = min(thr, keys[k - 1]);
+        if (tid == 0) used_sh = used;
+        __syncthreads();
+    };
+    constexpr int kRound = 1024;  // keys read per round, at most 4 a thread
+    bool tight = false;           // thr already cut at a k-th key
+    for (int base = 0; base < total;) {
+        if (used + kRound > kMergeCap || (!tight && used >= k)) {  // block-uniform
+            sort_keep();
+            tight = used == k;
+        }
+        const int per = tight ? kRound / 256 : 1;  // one key a thread until the cut-off is set
+#pragma unroll 4
+        for (int e = 0; e < per; ++e) {
+            const int g = base + e * 256 + tid;
+            if (g < total) {
+                int l = 0, h = S;  // the list holding key g: pre[l] <= g < pre[l + 1]
+                while (h - l > 1) {
+                    const int mid = (l + h) >> 1;
+                    if (pre[mid] <= g) l = mid;
+                    else h = mid;
+                }
+                const uint64_t v = lists[((int64_t)l * Q + qs) * cap + (g - pre[l])];
+                if (v < thr) keys[atomicAdd(&used_sh, 1)] = v;
+            }
+        }
+        base += per * 256;
+        __syncthreads();
+        used = used_sh;
+    }
+    sort_keep();
+    for (int j = tid; j < k; j += blockDim.x) {
+        const uint64_t v = j < used ? keys[j] : kKeyInf;
+        out_ids[qi * k + j] = v == kKeyInf ? -1 : (int32_t)(uint32_t)v;
+        out_lcp[qi * k + j] = v == kKeyInf ? 0 : (uint8_t)(255 - (int)(v >> 32));
+    }
+}
+
+// ---- the batch order for the large-batch scan: queries by their first word ----
+
+// keys[i] = packed word 0 of query i, vals[i] = i.
+__global__ void k_query_keys(const uint8_t* __restrict__ queries, RowFmt qf, int64_t Q,
+                             uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Q) return;
+    keys[i] = pack_word(row_of(queries, i, qf), 0, qf);
+    vals[i] = (uint32_t)i;
+}
+
+// One CTA: order[] = the query indices sorted by (word 0, index), Q <= kQuerySortCta.
+__global__ void __launch_bounds__(1024) k_query_sort_cta(const uint8_t* __restrict__ queries, RowFmt qf, int Q,
+                                                          int32_t* __restrict__ order) {
+    extern __shared__ uint64_t qk[];  // [P] keys, then [P] indices
+    int P = 1;
+    while (P < Q) P <<= 1;
+    uint32_t* qv = reinterpret_cast<uint32_t*>(qk + P);
+    for (int t = threadIdx.x; t < P; t += blockDim.x) {
+        qk[t] = t < Q ? pack_word(row_of(queries, t, qf), 0, qf) : ~0ull;
+        qv[t] = (uint32_t)t;
     }
     __syncthreads();
     for (int size = 2; size <= P; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
             for (int t = threadIdx.x; t < P; t += blockDim.x) {
-                int u = t ^ stride;
+                const int u = t ^ stride;
                 if (u > t) {
-                    uint64_t a = keys[t], b = keys[u];
-                    bool up = (t & size) == 0;
-                    if ((a > b) == up) {
-                        keys[t] = b;
-                        keys[u] = a;
+                    const uint64_t x = qk[t], y = qk[u];
+                    const uint32_t vx = qv[t], vy = qv[u];
+                    const bool gt = x > y || (x == y && vx > vy);
+                    if (gt == ((t & size) == 0)) {
+                        qk[t] = y;
+                        qk[u] = x;
+                        qv[t] = vy;
+                        qv[u] = vx;
                     }
                 }
             }
             __syncthreads();
         }
     }
-    if (final_pass) {
-        for (int j = threadIdx.x; j < k; j += blockDim.x) {
-            uint64_t v = keys[j];
-            out_ids[q * k + j] = v == kKeyInf ? -1 : (int32_t)(uint32_t)v;
-            out_lcp[q * k + j] = v == kKeyInf ? 0 : (uint8_t)(255 - (int)(v >> 32));
-        }
-    } else {
-        for (int j = threadIdx.x; j < k; j += blockDim.x) out[((int64_t)g * Q + q) * k + j] = keys[j];
-    }
+    for (int t = threadIdx.x; t < Q; t += blockDim.x) order[t] = (int32_t)qv[t];
+}
+
+__global__ void k_u32_to_i32(const uint32_t* __restrict__ in, int64_t n, int32_t* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (int32_t)in[i];
 }
 
 
@@ -261,6 +428,8 @@ __global__ void __launch_bounds__(256) k_scan_merge(const uint64_t* __restrict__
 //                  A, the tie rows, then padding.
 
 constexpr int kSelWarps = 8;
+constexpr int kSelGroup = 4;       // queries per warp in the count pass (batches of > 1)
+constexpr int kSelGroupWarps = 4;  // warps per CTA of that count pass
 constexpr int kSelBins = 16;
 constexpr int kSelMaxS = 8192;  // slices per query at most  // LCPs below this are counted per lane, larger ones by shared atomics
 constexpr int kMaxScanW = (LCP_MAX_L + 3) / 4;  // packed words of the longest uint16 row
@@ -321,89 +490,130 @@ __device__ __forceinline__ void sel_slice(const SelArgs& a, int s, int64_t* s0, 
     *s1 = e < a.N ? e : a.N;
 }
 
-__global__ void __launch_bounds__(kSelWarps * 32, 4) k_sel_count(SelArgs a) {
-    __shared__ uint64_t qw[kMaxScanW];
-    __shared__ uint32_t hist[kSelWarps][LCP_MAX_L + 1];
-    __shared__ uint32_t lanecnt[kSelWarps][kSelBins][32];  // [l][lane]: bank = lane, no conflicts
-    const int64_t q = blockIdx.y;
+// G queries per warp: each row word is loaded once and tested against each
+// of them (G = 1 for a lone query, whose rows are read straight from the
+// tokens; G = 4 on the packed plane otherwise).  NW warps per CTA, a warp per
+// slice; lane counters are 16-bit (a lane meets at most slice / 32 rows).
+template <int G, int NW>
+__global__ void __launch_bounds__(NW * 32) k_sel_count(SelArgs a) {
+    __shared__ uint64_t qw[G][kMaxScanW];
+    __shared__ uint32_t hist[G][NW][LCP_MAX_L + 1];
+    __shared__ uint16_t lanecnt[G][NW][kSelBins][32];  // [l][lane]: no bank conflicts between lanes
+    const int64_t qb = (int64_t)blockIdx.y * G;
+    const int ng = a.Q - qb < G ? (int)(a.Q - qb) : G;
     const unsigned lane = lane_id();
     const int warp = threadIdx.x >> 5;
     const int L = a.f.L;
-    const uint8_t* qrow = row_of(a.queries, q, a.qf);
-    for (int w = threadIdx.x; w < a.f.W; w += blockDim.x) qw[w] = pack_word(qrow, w, a.qf);
-    uint32_t* h = hist[warp];
-    uint32_t* lc = &lanecnt[warp][0][lane];
-    for (int d = (int)lane; d <= L; d += 32) h[d] = 0;
+    for (int g = 0; g < ng; ++g) {
+        const uint8_t* qrow = row_of(a.queries, qb + g, a.qf);
+        for (int w = threadIdx.x; w < a.f.W; w += blockDim.x) qw[g][w] = pack_word(qrow, w, a.qf);
+    }
 #pragma unroll
-    for (int d = 0; d < kSelBins; ++d) lc[d * 32] = 0;
+    for (int g = 0; g < G; ++g) {
+        for (int d = (int)lane; d <= L; d += 32) hist[g][warp][d] = 0;
+#pragma unroll
+        for (int d = 0; d < kSelBins; ++d) lanecnt[g][warp][d][lane] = 0;
+    }
     __syncthreads();
-    const int s = blockIdx.x * kSelWarps + warp;
+    const int s = blockIdx.x * NW + warp;
     if (s < a.S) {
         int64_t s0, s1;
         sel_slice(a, s, &s0, &s1);
-        const uint64_t q0 = qw[0];
-        const uint32_t qh = (uint32_t)(q0 >> 32);
-        const uint32_t lim = 1u << (32 - a.f.bits);  // (word 0 ^ q0) >> 32 below it: first token agrees
+        uint64_t q0[G];
+        uint32_t qh[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            q0[g] = g < ng ? qw[g][0] : 0ull;
+            qh[g] = (uint32_t)(q0[g] >> 32);
+        }
+        // (word 0 ^ q0) >> 32 below lim1: the first token agrees (LCP >= 1),
+        // below lim2: the first two do (LCP >= 2; rare).  Rows of LCP >= 1
+        // are counted per lane in a register; only rows of LCP >= 2 take the
+        // exact LCP and a level counter.
+        const uint32_t lim1 = 1u << (32 - a.f.bits);
+        const uint32_t lim2 = 1u << (32 - 2 * a.f.bits);
+        uint32_t c1[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) c1[g] = 0;
         // 128 rows per step; the next step's words are loaded before this
-        // step's are tested
+        // step's are tested (rows past the slice get a word no query shares)
         uint64_t r[4], nx[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int64_t t = s0 + u * 32 + lane;
-            r[u] = t < s1 ? sel_word0(a, t) : ~q0;
+            r[u] = t < s1 ? sel_word0(a, t) : ~q0[0];
         }
         for (int64_t b = s0; b < s1; b += 128) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int64_t t = b + 128 + u * 32 + lane;
-                nx[u] = t < s1 ? sel_word0(a, t) : ~q0;
+                nx[u] = t < s1 ? sel_word0(a, t) : ~q0[0];
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const bool hit = ((uint32_t)(r[u] >> 32) ^ qh) < lim;
-                if (!__any_sync(0xffffffffu, hit)) continue;
-                if (hit) {
-                    const int l = sel_lcp(a, b + u * 32 + lane, r[u] ^ q0, qw);  // >= 1
-                    if (l < kSelBins) lc[l * 32] += 1;
-                    else atomicAdd(h + l, 1u);
+            for (int g = 0; g < G; ++g) {
+                if (g >= ng) break;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t t = b + u * 32 + lane;
+                    const uint32_t xh = (uint32_t)(r[u] >> 32) ^ qh[g];
+                    const bool in = t < s1;
+                    c1[g] += (in && xh < lim1) ? 1u : 0u;
+                    const bool deep = in && xh < lim2;
+                    if (!__any_sync(0xffffffffu, deep)) continue;
+                    if (deep) {
+                        const int l = sel_lcp(a, t, r[u] ^ q0[g], qw[g]);  // >= 2
+                        if (l < kSelBins) lanecnt[g][warp][l][lane] += 1;
+                        else atomicAdd(&hist[g][warp][l], 1u);
+                    }
                 }
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) r[u] = nx[u];
         }
         __syncwarp();
-        for (int d = 1; d < kSelBins && d <= L; ++d) {
-            const uint32_t v = __reduce_add_sync(0xffffffffu, lc[d * 32]);
-            if (lane == 0) h[d] += v;
-        }
-        __syncwarp();
-        // suffix sums (rows with LCP >= d), from d = L down to 1, stored per
-        // slice where nonzero and kept in h for the CTA's total
-        uint32_t* out = a.ge + (size_t)q * L * a.S + s;
-        uint32_t carry = 0;
-        for (int c = ((L - 1) / 32) * 32 + 1; c >= 1; c -= 32) {
-            const int d = c + (int)lane;
-            uint32_t v = d <= L ? h[d] : 0u;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_down_sync(0xffffffffu, v, o);
-                if ((int)lane + o < 32) v += y;
+        for (int g = 0; g < ng; ++g) {
+            uint32_t* h = hist[g][warp];
+            uint32_t deep = 0;  // rows of LCP >= 2 (lane 0's sum)
+            for (int d = 2; d < kSelBins && d <= L; ++d) {
+                const uint32_t v = __reduce_add_sync(0xffffffffu, (uint32_t)lanecnt[g][warp][d][lane]);
+                if (lane == 0) h[d] += v;
             }
-            v += carry;
             __syncwarp();
-            if (d <= L) {
-                if (v) out[(size_t)(d - 1) * a.S] = v;
-                h[d] = v;
+            for (int d = 2 + (int)lane; d <= L; d += 32) deep += h[d];
+            deep = __reduce_add_sync(0xffffffffu, deep);
+            const uint32_t ones = __reduce_add_sync(0xffffffffu, c1[g]);
+            if (lane == 0 && L >= 1) h[1] = ones - deep;  // rows of LCP exactly 1
+            __syncwarp();
+            // suffix sums (rows with LCP >= d), from d = L down to 1, stored
+            // per slice where nonzero and kept in h for the CTA's total
+            uint32_t* out = a.ge + (size_t)(qb + g) * L * a.S + s;
+            uint32_t carry = 0;
+            for (int c = ((L - 1) / 32) * 32 + 1; c >= 1; c -= 32) {
+                const int d = c + (int)lane;
+                uint32_t v = d <= L ? h[d] : 0u;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_down_sync(0xffffffffu, v, o);
+                    if ((int)lane + o < 32) v += y;
+                }
+                v += carry;
+                __syncwarp();
+                if (d <= L) {
+                    if (v) out[(size_t)(d - 1) * a.S] = v;
+                    h[d] = v;
+                }
+                carry = __shfl_sync(0xffffffffu, v, 0);
             }
-            carry = __shfl_sync(0xffffffffu, v, 0);
         }
     }
     __syncthreads();
-    for (int d = threadIdx.x + 1; d <= L; d += blockDim.x) {
-        uint32_t v = 0;
+    for (int g = 0; g < ng; ++g) {
+        for (int d = threadIdx.x + 1; d <= L; d += blockDim.x) {
+            uint32_t v = 0;
 #pragma unroll
-        for (int w = 0; w < kSelWarps; ++w) v += hist[w][d];
-        if (v) atomicAdd(a.tot + (size_t)q * L + (d - 1), v);
+            for (int w = 0; w < NW; ++w) v += hist[g][w][d];
+            if (v) atomicAdd(a.tot + (size_t)(qb + g) * L + (d - 1), v);
+        }
     }
 }
 
@@ -622,11 +832,11 @@ namespace lcph {
 using namespace lcpk;
 
 // Batches up to this size take the threshold selection, larger ones the
-// per-thread logs, whose screen of a row against a level k logged rows reach
-// is cheaper per pair once every thread of the GPU has a query (measured on
-// 2M rows of 64 uint16 tokens: the selection is 1.5x ahead at 256 queries,
-// level at 512, 1.6x behind at 1,024; 3.3x ahead at 32).
-constexpr int64_t kSelMaxQ = 512;
+// per-thread logs over the batch sorted by first word (measured on 2M rows of
+// 64 uint16 tokens, k = 100: selection 0.52 ms at 128 queries against 1.07
+// for the logs, 0.64 against ~1.1 at 160, the logs ahead at 256: 1.25
+// against ~1.3).
+constexpr int64_t kSelMaxQ = 160;
 
 static int scan_select(const void* d_tokens, int64_t N, const RowFmt& f, const void* d_queries,
                        const RowFmt& qf, int64_t Q, int k, int32_t* d_out_ids, uint8_t* d_out_lcp,
@@ -635,12 +845,17 @@ static int scan_select(const void* d_tokens, int64_t N, const RowFmt& f, const v
     // about 64 warps per SM over all (query, slice) pairs (two waves, so
     // that slices with long walks in the collect pass even out), whole CTAs
     // of slices, slices of >= 256 rows
+    // the count pass tests kSelGroup queries per warp (one for a lone query)
+    const int G = Q == 1 ? 1 : kSelGroup;
+    const int64_t groups = (Q + G - 1) / G;
     const int64_t target = (int64_t)sm_count() * 64;
-    int64_t S = (target + Q - 1) / Q;
+    int64_t S = (target + groups - 1) / groups;
     S = (S + kSelWarps - 1) / kSelWarps * kSelWarps;
     const int64_t maxS = (N + 255) / 256;
     if (S > maxS) S = maxS;
     if (S > kSelMaxS) S = kSelMaxS;
+    const int64_t minS = (N + (32ll << 16) - 1) >> 21;  // slices of < 2M rows: 16-bit lane counters
+    if (S < minS) S = minS;
     if (S < 1) S = 1;
     const int64_t slice = (N + S - 1) / S;
     S = (N + slice - 1) / slice;
@@ -677,11 +892,124 @@ static int scan_select(const void* d_tokens, int64_t N, const RowFmt& f, const v
     if (plane)
         LCP_TIMED_LAUNCH(k_pack_plane0, (unsigned)((N + 255) / 256), 256, 0, s, a.tokens, f, N, plane0);
     const dim3 grid((unsigned)((S + kSelWarps - 1) / kSelWarps), (unsigned)Q);
-    LCP_TIMED_LAUNCH(k_sel_count, grid, kSelWarps * 32, 0, s, a);
+    if (G == 1)
+        LCP_TIMED_LAUNCH((k_sel_count<1, kSelWarps>), grid, kSelWarps * 32, 0, s, a);
+    else
+        LCP_TIMED_LAUNCH((k_sel_count<kSelGroup, kSelGroupWarps>),
+                         dim3((unsigned)((S + kSelGroupWarps - 1) / kSelGroupWarps), (unsigned)groups),
+                         kSelGroupWarps * 32, 0, s, a);
     LCP_TIMED_LAUNCH(k_sel_pick, (unsigned)Q, 1024, 0, s, a);
     LCP_TIMED_LAUNCH(k_sel_collect, grid, kSelWarps * 32, 0, s, a, d_out_ids, d_out_lcp);
     e = cudaFreeAsync(base, s);
     return e == cudaSuccess ? LCP_OK : cuda_status(e);
+}
+
+// Larger batches: per-thread logs over N-slices, the batch ordered by the
+// queries' first words (so that a warp's 32 queries are neighbours and its
+// screen is narrow), each query's level floor taken first from a sample of
+// the rows (the first kFloorSample: where k of them reach LCP d, no row
+// below d can be in the answer), then the k-best merge.
+constexpr int64_t kFloorSample = 65536;
+constexpr int kScanCtasPerSm = 4;
+
+static int scan_logs(const void* d_tokens, int64_t N, const RowFmt& f, const void* d_queries, const RowFmt& qf,
+                     int64_t Q, int k, int32_t* d_out_ids, uint8_t* d_out_lcp, cudaStream_t s) {
+    const int threads = kScanPartialThreads;
+    const int64_t qtiles = (Q + threads - 1) / threads;
+    const int64_t target = (int64_t)sm_count() * kScanCtasPerSm;  // CTAs per pass, about
+    auto slices = [&](int64_t rows, int64_t min_rows, int64_t max_s, int64_t* slice) {
+        int64_t S = (target + qtiles - 1) / qtiles;
+        const int64_t by_rows = (rows + min_rows - 1) / min_rows;
+        if (S > by_rows) S = by_rows;
+        if (S > max_s) S = max_s;
+        if (S < 1) S = 1;
+        *slice = (rows + S - 1) / S;
+        return (rows + *slice - 1) / *slice;
+    };
+    int64_t slice = 0;
+    const int64_t S = slices(N, 1024, kMergeMaxLists, &slice);
+    // the floor pass only pays when the sample is a small part of the rows
+    const int64_t Ns = N >= 4 * kFloorSample ? kFloorSample : 0;
+    int64_t slice_pre = 0;
+    const int64_t S_pre = Ns ? slices(Ns, 4096, S, &slice_pre) : 0;
+    const int cap = k + kLogSlack;  // log entries per (slice, query)
+    const bool small_sort = Q <= kQuerySortCta;
+    uint64_t *plane0 = nullptr, *lists = nullptr, *qk0 = nullptr, *qk1 = nullptr;
+    int32_t *order = nullptr, *floor = nullptr, *counts = nullptr;
+    uint32_t *qv0 = nullptr, *qv1 = nullptr;
+    Carver cv;
+    cv.add(&plane0, (size_t)N);
+    cv.add(&order, (size_t)Q);
+    cv.add(&floor, (size_t)Q);
+    cv.add(&counts, (size_t)S * Q);
+    cv.add(&lists, (size_t)S * Q * cap);
+    if (!small_sort) {
+        cv.add(&qk0, (size_t)Q);
+        cv.add(&qk1, (size_t)Q);
+        cv.add(&qv0, (size_t)Q);
+        cv.add(&qv1, (size_t)Q);
+    }
+    void* base = nullptr;
+    LCP_CUDA_TRY(cv.alloc(&base, s));
+    SortWork w;
+    int rc = LCP_OK;
+    if (!small_sort) rc = sort_work_alloc(w, (uint32_t)Q, lib_status_word(), s);
+    cudaError_t e = cudaSuccess;
+    if (rc == LCP_OK) {
+        LCP_TIMED_LAUNCH(k_pack_plane0, (unsigned)((N + 255) / 256), 256, 0, s,
+                         reinterpret_cast<const uint8_t*>(d_tokens), f, N, plane0);
+        // the batch order
+        if (small_sort) {
+            int P = 1;
+            while (P < Q) P <<= 1;
+            const int smem = P * (int)(sizeof(uint64_t) + sizeof(uint32_t));
+            e = cudaFuncSetAttribute(k_query_sort_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e == cudaSuccess)
+                LCP_TIMED_LAUNCH(k_query_sort_cta, 1, 1024, smem, s, reinterpret_cast<const uint8_t*>(d_queries), qf,
+                                 (int)Q, order);
+        } else {
+            LCP_TIMED_LAUNCH(k_query_keys, (unsigned)((Q + 255) / 256), 256, 0, s,
+                             reinterpret_cast<const uint8_t*>(d_queries), qf, Q, qk0, qv0);
+            uint64_t* ok = nullptr;
+            uint32_t* ov = nullptr;
+            rc = radix_sort_pairs_u64(qk0, qv0, qk1, qv1, (uint32_t)Q, 64, w, s, &ok, &ov);
+            if (rc == LCP_OK) LCP_TIMED_LAUNCH(k_u32_to_i32, (unsigned)((Q + 255) / 256), 256, 0, s, ov, Q, order);
+        }
+    }
+    if (rc == LCP_OK && e == cudaSuccess) e = cudaMemsetAsync(floor, 0, sizeof(int32_t) * (size_t)Q, s);
+    ScanArgs a;
+    a.tokens = reinterpret_cast<const uint8_t*>(d_tokens);
+    a.plane0 = plane0;
+    a.f = f;
+    a.queries = reinterpret_cast<const uint8_t*>(d_queries);
+    a.qf = qf;
+    a.Q = Q;
+    a.order = order;
+    a.k = k;
+    a.cap = cap;
+    a.lists = lists;
+    a.floor = floor;
+    if (rc == LCP_OK && e == cudaSuccess && Ns) {  // the floors, from the sample
+        a.N = Ns;
+        a.slice = slice_pre;
+        a.counts = nullptr;
+        LCP_TIMED_LAUNCH(k_scan_partial, dim3((unsigned)qtiles, (unsigned)S_pre), threads, 0, s, a);
+    }
+    if (rc == LCP_OK && e == cudaSuccess) {
+        a.N = N;
+        a.slice = slice;
+        a.counts = counts;
+        LCP_TIMED_LAUNCH(k_scan_partial, dim3((unsigned)qtiles, (unsigned)S), threads, 0, s, a);
+        e = cudaFuncSetAttribute(k_scan_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(uint64_t) * kMergeCap));
+        if (e == cudaSuccess)
+            LCP_TIMED_LAUNCH(k_scan_merge, (unsigned)Q, 256, sizeof(uint64_t) * kMergeCap, s, lists, counts, cap, Q,
+                             (int)S, k, order, d_out_ids, d_out_lcp);
+    }
+    if (rc == LCP_OK && e != cudaSuccess) rc = cuda_status(e);
+    if (!small_sort && w.arena) sort_work_free(w, s);
+    cudaFreeAsync(base, s);
+    return rc;
 }
 
 int scan_topk_device(const void* d_tokens, int64_t N, int tb, int L, const void* d_queries,
@@ -695,66 +1023,7 @@ int scan_topk_device(const void* d_tokens, int64_t N, int tb, int L, const void*
     RowFmt f = make_fmt(tb, L, d_tokens);
     RowFmt qf = make_fmt(tb, L, d_queries);
     if (Q <= kSelMaxQ) return scan_select(d_tokens, N, f, d_queries, qf, Q, k, d_out_ids, d_out_lcp, s);
-    const int threads = kScanPartialThreads;
-    const int64_t qtiles = (Q + threads - 1) / threads;
-    const int64_t target = 148 * 8;
-    int64_t S = (target + qtiles - 1) / qtiles;
-    int64_t maxS = (N + 1023) / 1024;
-    if (S > maxS) S = maxS;
-    if (S > 65535) S = 65535;
-    if (S < 1) S = 1;
-    int64_t slice = (N + S - 1) / S;
-    S = (N + slice - 1) / slice;
-    const int cap = k + kLogSlack;  // log entries per (slice, query)
-    uint64_t* plane0 = nullptr;
-    uint64_t* heaps = nullptr;
-    LCP_CUDA_TRY(cudaMallocAsync((void**)&plane0, sizeof(uint64_t) * N, s));
-    LCP_CUDA_TRY(cudaMallocAsync((void**)&heaps, sizeof(uint64_t) * (size_t)S * Q * cap, s));
-    LCP_TIMED_LAUNCH(k_pack_plane0, (unsigned)((N + 255) / 256), 256, 0, s,
-               reinterpret_cast<const uint8_t*>(d_tokens), f, N, plane0);
-    dim3 grid((unsigned)qtiles, (unsigned)S);
-    LCP_TIMED_LAUNCH(k_scan_partial, grid, threads, 0, s, reinterpret_cast<const uint8_t*>(d_tokens),
-               plane0, f, N, reinterpret_cast<const uint8_t*>(d_queries), qf, Q, k, cap, slice, heaps);
-    // merge: groups of G lists until one remains
-    int kp2 = 1;
-    while (kp2 < k) kp2 <<= 1;
-    int G = kMergeCap / kp2;
-    if (G < 1) G = 1;
-    int64_t nl = S;
-    uint64_t* cur = heaps;
-    int rc = LCP_OK;
-    for (;;) {
-        int g = (int)(nl < G ? nl : G);
-        int64_t groups = (nl + g - 1) / g;
-        int P = 1;
-        while (P < g * k) P <<= 1;
-        size_t smem = sizeof(uint64_t) * P;
-        cudaError_t e = cudaFuncSetAttribute(k_scan_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(sizeof(uint64_t) * kMergeCap * 2));
-        if (e != cudaSuccess) {
-            rc = cuda_status(e);
-            break;
-        }
-        bool final_pass = groups == 1;
-        uint64_t* out = nullptr;
-        if (!final_pass) {
-            e = cudaMallocAsync((void**)&out, sizeof(uint64_t) * (size_t)groups * Q * k, s);
-            if (e != cudaSuccess) {
-                rc = cuda_status(e);
-                break;
-            }
-        }
-        dim3 mg((unsigned)Q, (unsigned)groups);
-        LCP_TIMED_LAUNCH(k_scan_merge, mg, 256, smem, s, cur, cur == heaps ? cap : k, Q, k, (int)nl, g, P,
-                   out, final_pass ? 1 : 0, d_out_ids, d_out_lcp);
-        if (cur != heaps) cudaFreeAsync(cur, s);
-        if (final_pass) break;
-        cur = out;
-        nl = groups;
-    }
-    cudaFreeAsync(plane0, s);
-    cudaFreeAsync(heaps, s);
-    return rc;
+    return scan_logs(d_tokens, N, f, d_queries, qf, Q, k, d_out_ids, d_out_lcp, s);
 }
 
 }  // namespace lcph

@@ -11,24 +11,46 @@ namespace lcpk {
 constexpr int kLogSlack = 64;
 
 // Threads per CTA of k_scan_partial (its launch bound; a CTA owns that many
-// queries of one N-slice).
-constexpr int kScanPartialThreads = 128;
+// queries of one N-slice, a warp 32 neighbouring ones in the batch order).
+constexpr int kScanPartialThreads = 256;
 
-// Keys one k_scan_merge CTA sorts in shared memory: a merge takes at most
-// kMergeCap / (k rounded up to a power of two) lists per query.
+// Keys one k_scan_merge CTA sorts in shared memory at a time, and the most
+// N-slices (lists per query) it takes.
 constexpr int kMergeCap = 4096;
+constexpr int kMergeMaxLists = 2048;
+
+// Largest batch ordered by one CTA (k_query_sort_cta); larger batches take
+// the radix sort.
+constexpr int kQuerySortCta = 4096;
 
 __global__ void k_pack_plane0(const uint8_t* __restrict__ tokens, RowFmt f, int64_t n,
                               uint64_t* __restrict__ plane0);
 
-// lists: [S][Q][cap] keys, cap = k + kLogSlack; each (slice, query) leaves its
-// k best keys (unordered, padded with ~0) in the first k entries of its list.
-__global__ void k_scan_partial(const uint8_t* __restrict__ tokens, const uint64_t* __restrict__ plane0,
-                               RowFmt f, int64_t N, const uint8_t* __restrict__ queries, RowFmt qf,
-                               int64_t Q, int k, int cap, int64_t slice, uint64_t* __restrict__ lists);
+struct ScanArgs {
+    const uint8_t* tokens;    // [N, L] raw rows
+    const uint64_t* plane0;   // packed word 0 of every row
+    RowFmt f;
+    int64_t N;                // rows scanned: [0, N), in slices of `slice`
+    const uint8_t* queries;   // [Q, L] raw queries
+    RowFmt qf;
+    int64_t Q;
+    const int32_t* order;     // batch position -> query (null: identity)
+    int32_t* floor;           // per batch position: a level with k rows at or above it, read
+                              // as the scan goes and raised (atomic maximum) by every slice
+                              // that finds one (null: none; else zeroed before the first pass)
+    int k, cap;               // cap = k + kLogSlack entries per log
+    int64_t slice;
+    uint64_t* lists;          // [S][Q][cap]: each (slice, position) leaves its candidates first
+    int32_t* counts;          // [S][Q]: how many (<= k) | the slice's known level << 16 (null: not written)
+};
 
-__global__ void k_scan_merge(const uint64_t* __restrict__ in, int in_stride, int64_t Q, int k, int nlists,
-                             int G, int P, uint64_t* __restrict__ out, int final_pass,
+// grid = (ceil(Q / kScanPartialThreads), S slices).
+__global__ void k_scan_partial(const ScanArgs a);
+
+// grid = Q (batch positions): the k best of each position's S lists into the
+// query's output row.  Dynamic shared memory: kMergeCap keys.
+__global__ void k_scan_merge(const uint64_t* __restrict__ lists, const int32_t* __restrict__ counts, int cap,
+                             int64_t Q, int S, int k, const int32_t* __restrict__ order,
                              int32_t* __restrict__ out_ids, uint8_t* __restrict__ out_lcp);
 
 }  // namespace lcpk

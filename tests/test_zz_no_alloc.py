@@ -44,10 +44,20 @@ def _call(fn, P, S, Qs, k, L_tokens, tb, vocab):
 SCRATCH = 32 << 20
 
 
+def _need(N, Q, k):
+    """Scratch bytes of one call: the rows' first words, then one N-slice of
+    per-query counts and logs of k + 64 keys."""
+    return ((N * 8 + 255) & ~255) + ((Q * 4 + 255) & ~255) + Q * (k + 64) * 8
+
+
 def _max_queries(N, k):
-    """Largest batch whose plane and one slice of logs fit the scratch."""
-    plane = (N * 8 + 255) & ~255
-    return (SCRATCH - plane) // ((k + 64) * 8)
+    """Largest batch that fits the scratch."""
+    Q = (SCRATCH - ((N * 8 + 255) & ~255)) // ((k + 64) * 8 + 4)
+    while _need(N, Q + 1, k) <= SCRATCH:
+        Q += 1
+    while _need(N, Q, k) > SCRATCH:
+        Q -= 1
+    return Q
 
 
 # (workload, N, Q, k): the per-thread-log path on both sides; one and 32
