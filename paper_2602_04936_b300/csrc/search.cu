@@ -431,10 +431,21 @@ __device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, WA& S, int p,
     } else if (dstar > 1) {
         const bool knownL = vL < nL || nL == availL;
         const bool knownR = vR < nR || nR == availR;
-        int xl = -1, xr = N;
-        find_bounds(ix, p - nL, !knownL, p + nR, !knownR, dstar, &xl, &xr);
-        lov = knownL ? p - vL : (xl < 0 ? 0 : xl);
-        hiv = knownR ? p + vR : xr;
+        if (dstar <= ix.tpw && !(knownL && knownR)) {
+            // the run lies in word 0: searches over head inside the bucket;
+            // a neighbour of p with LCP >= d* gives the run's masked word 0
+            const uint64_t mask = ~0ull << (64 - dstar * ix.bits);
+            const uint64_t key = ix.head[lL >= lR ? p - 1 : p] & mask;
+            int xl = 0, xr = N;
+            head_bounds(ix, bk0, bk1, p - nL, p + nR, key, mask, !knownL, !knownR, &xl, &xr);
+            lov = knownL ? p - vL : xl;
+            hiv = knownR ? p + vR : xr;
+        } else {
+            int xl = -1, xr = N;
+            find_bounds(ix, p - nL, !knownL, p + nR, !knownR, dstar, &xl, &xr);
+            lov = knownL ? p - vL : (xl < 0 ? 0 : xl);
+            hiv = knownR ? p + vR : xr;
+        }
     }
     const int nT = (hiv - lov) - nA;
     int kp = k - nA;

@@ -307,6 +307,49 @@ __device__ __forceinline__ void find_bounds(const DevIndex& ix, int fromL, bool 
     *outR = s[1].result;
 }
 
+// The run of sorted rows whose first d <= tpw tokens equal q's, where only
+// word 0 (the head array) decides: `key` = a row of the run's word 0 masked
+// to its first d tokens.  Left: the first x in [b0, from) with head[x] in
+// the run (it ends at `from`); right: the first x in [from, b1) past it.
+// 32-ary searches (lane l probes the l-th of 32 evenly spaced positions,
+// a ballot finds the first that satisfies), both sides' loads in flight
+// together; [b0, b1) is the depth-1 bucket holding the run.
+__device__ __forceinline__ void head_bounds(const DevIndex& ix, int b0, int b1, int fromL, int fromR,
+                                            uint64_t key, uint64_t mask, bool needL, bool needR, int* outL,
+                                            int* outR) {
+    const int lane = (int)lane_id();
+    int lo[2] = {b0, fromR}, hi[2] = {fromL, b1};
+    bool done[2] = {!needL || b0 >= fromL, !needR || fromR >= b1};
+    while (!(done[0] && done[1])) {  // warp-uniform
+        int st[2], x[2];
+        uint64_t h[2] = {0ull, 0ull};
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+            st[sd] = (hi[sd] - lo[sd] + 31) >> 5;
+            x[sd] = min(lo[sd] + (lane + 1) * st[sd] - 1, hi[sd] - 1);
+            if (!done[sd]) h[sd] = ix.head[x[sd]];
+        }
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+            if (done[sd]) continue;
+            const uint64_t v = h[sd] & mask;
+            const unsigned m = __ballot_sync(0xffffffffu, sd == 0 ? v >= key : v > key);
+            if (!m) {  // none up to hi - 1: the answer is hi
+                done[sd] = true;
+                continue;
+            }
+            const int f = __ffs(m) - 1;
+            const int nlo = f == 0 ? lo[sd] : min(lo[sd] + f * st[sd] - 1, hi[sd] - 1) + 1;
+            const int nhi = min(lo[sd] + (f + 1) * st[sd] - 1, hi[sd] - 1);  // satisfies
+            lo[sd] = nlo;
+            hi[sd] = nhi;
+            if (nlo >= nhi) done[sd] = true;
+        }
+    }
+    *outL = hi[0];
+    *outR = hi[1];
+}
+
 // Minimum of H over positions [a, b] (inclusive), walking the min tree
 // bottom-up: partial groups at both ends at each level, full groups above.
 __device__ __forceinline__ int range_min_H(const DevIndex& ix, int64_t a, int64_t b) {
