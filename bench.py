@@ -776,6 +776,8 @@ def run_ours(args, world, rank, local):
         del dsteps
         # serving: six resident indexes, Poisson arrivals, native open-loop replay
         paths["serving"] = serving_leg(lcp, device, to_dev)
+        # the bench workload served (indexed and full scan)
+        paths["serving_zipf2m_L64"] = serving_c3_leg(lcp, device)
         # TAL bucket scan (the paper's TAL benchmark shape) and BFS order
         paths["tal20m"] = tal_leg(lcp, device, meter)
         # the paper's sustained shape: top-1, rows of 256 tokens, 16-bit LCPs
@@ -962,116 +964,195 @@ def sustained_leg(lcp, device, meter):
     return rec
 
 
-def serving_leg(lcp, device, to_dev, duration_s=1.5, budget=256 << 20, streams=8, max_inflight=64):
-    """Six resident zipf-prefix indexes (N, L) in SERVING_INDEXES; requests
-    arrive Poisson at 20k/s with log-uniform batch sizes in [1, 4096], k in
-    {1, 10, 100} and a uniformly drawn index; admission by a device-memory
-    budget; latency = completion - scheduled arrival."""
+def latency_summary(lat_s, sizes, arrivals=None):
+    """p50/p99/p99.9 in ms over completed requests, by request size too, the
+    slowest five (latency, queries) and when requests slower than 0.5 ms
+    arrived -- where a tail comes from."""
+    ok = lat_s >= 0
+    ms = lat_s[ok] * 1e3
+    q = np.asarray(sizes)[ok]
+    pct = lambda a: {"p50": round(float(np.percentile(a, 50)), 4), "p99": round(float(np.percentile(a, 99)), 4),
+                     "p99.9": round(float(np.percentile(a, 99.9)), 4), "n": int(len(a))} if len(a) else None
+    bins = {}
+    for lo, hi in ((1, 16), (17, 256), (257, 4096)):
+        sel = (q >= lo) & (q <= hi)
+        bins["%d-%d" % (lo, hi)] = pct(ms[sel])
+    worst = np.argsort(ms)[-5:][::-1]
+    out = dict(pct(ms), by_queries=bins, slowest=[[round(float(ms[i]), 3), int(q[i])] for i in worst])
+    if arrivals is not None:
+        arr = np.asarray(arrivals)[ok]
+        slow = np.sort(arr[ms > 0.5])
+        # bursts: slow requests within 5 ms of one another form one burst
+        bursts = []
+        for t in slow:
+            if bursts and t - bursts[-1][1] < 0.005:
+                bursts[-1][1] = t
+                bursts[-1][2] += 1
+            else:
+                bursts.append([t, t, 1])
+        out["slow_bursts"] = {"count": len(bursts),
+                              "first": [[round(b[0], 4), round((b[1] - b[0]) * 1e3, 2), b[2]] for b in bursts[:12]],
+                              "fields": "arrival s, span ms, requests over 0.5 ms"}
+    return out
+
+
+def replay_serving(lcp, device, slots, pools, rq, budget=256 << 20, streams=8, max_inflight=64,
+                   warm=2000, check=40, queue=True):
+    """Open-loop replay of the request stream `rq` (arrival_s, n_queries, k,
+    index -> slot) through a serving session -- slots are ("index", Index) or
+    ("scan", token tensor) -- and, for index slots, through the persistent
+    work queue with device-resident buffers.  Latency = completion -
+    scheduled arrival.  The last `check` requests are compared, ids and LCPs,
+    with the same request served alone."""
     import torch
-    w = W.WORKLOADS["serving6"]
-    V, s_, seed, rate = w["vocab"], w["s"], w["seed"], w["rate"]
-    indexes, pools = [], []
-    for i, (N, L) in enumerate(W.SERVING_INDEXES):
-        S = W.zipf_prefix_rows(N, L, V, s_, seed * 100 + i)
-        pool = W.zipf_prefix_queries(S, 16_384, V, s_, seed * 100 + i)
-        indexes.append(lcp.lcp_index_build(to_dev(S, device), max_k=100))
-        pools.append(pinned(pool))
-    n_req = int(rate * duration_s)
-    rq = W.serving_requests(n_req, rate, len(indexes), seed)
+    n_req = len(rq["arrival_s"])
     arena_bytes = 512 << 20
     arena = torch.empty(arena_bytes, dtype=torch.uint8).pin_memory()
     base = arena.data_ptr()
     sess = lcp.Session(mem_budget=budget, max_inflight=max_inflight, streams=streams)
-    slots = [sess.add_index(ix) for ix in indexes]
+    sid = [sess.add_index(t) if kind == "index" else sess.add_scan(t) for kind, t in slots]
     reqs, off, layout, wrap_at = [], 0, [], 0
-    rng = np.random.default_rng(seed)
+    rng = np.random.default_rng(4)
     for i in range(n_req):
         j, Q, k = int(rq["index"][i]), int(rq["n_queries"][i]), int(rq["k"][i])
-        qoff = int(rng.integers(0, 16_384 - Q + 1))
+        qoff = int(rng.integers(0, pools[j].shape[0] - Q + 1))
         need = (Q * k * 5 + 255) & ~255  # 256-byte aligned output slots
         if off + need > arena_bytes:
             off, wrap_at = 0, i
-        qp = pools[j].data_ptr() + qoff * pools[j].shape[1] * 2
-        reqs.append(lcp.ReplayRequest(float(rq["arrival_s"][i]), slots[j], k, Q, qp, base + off,
+        qp = pools[j].data_ptr() + qoff * pools[j].shape[1] * pools[j].element_size()
+        reqs.append(lcp.ReplayRequest(float(rq["arrival_s"][i]), sid[j], k, Q, qp, base + off,
                                       base + off + Q * k * 4))
         layout.append((j, qoff, Q, k, off))
         off += need
     torch.cuda.synchronize()
-    # untimed warm-up: the first 2,000 requests once (first use of each
-    # index, stream and allocation size)
-    sess.replay(reqs[:2000], timeout_s=60.0)
+    if warm:  # untimed: first use of every slot, stream and size class
+        sess.replay(reqs[:warm], timeout_s=120.0)
     torch.cuda.synchronize()
     launches0 = lcp.lcp_launch_count()
     try:
-        rc, lat, wall = sess.replay(reqs, timeout_s=120.0)
+        rc, lat, wall = sess.replay(reqs, timeout_s=600.0)
         launches = lcp.lcp_launch_count() - launches0
         st = sess.stats()
     finally:
         sess.close()
-    # the last requests' outputs are still in the arena: check them against
-    # the same request served alone
+
+    def alone(j, qoff, Q, k, dev_pool):
+        kind, t = slots[j]
+        q = dev_pool[qoff:qoff + Q]
+        return lcp.lcp_topk_batch(t, q, k) if kind == "index" else lcp.lcp_scan_topk(t, q, k)
+
+    dpools = [p.to(device) for p in pools]
     same = True
-    for i in range(max(n_req - 40, wrap_at), n_req):  # outputs not overwritten since
+    for i in range(max(n_req - check, wrap_at), n_req):  # outputs not overwritten since
         j, qoff, Q, k, o = layout[i]
         if lat[i] < 0:
             continue
-        alone = lcp.lcp_topk_batch(indexes[j], pools[j][qoff:qoff + Q].to(device), k)
+        a = alone(j, qoff, Q, k, dpools[j])
         got = arena[o:o + Q * k * 4].view(torch.int32).view(Q, k)
         got_lcp = arena[o + Q * k * 4:o + Q * k * 5].view(Q, k)
-        same = same and bool(torch.equal(got, alone[0].cpu()) and torch.equal(got_lcp, alone[1].cpu()))
-    # the same requests through the persistent kernel's work queue, queries
-    # and outputs device-resident (no copies inside the measured latencies)
-    dpools = [p.to(device) for p in pools]
-    darena = torch.empty(arena_bytes, dtype=torch.uint8, device=device)
-    dbase = darena.data_ptr()
-    qreqs = []
-    for i in range(n_req):
-        j, qoff, Q, k, o = layout[i]
-        qp = dpools[j].data_ptr() + qoff * dpools[j].shape[1] * 2
-        qreqs.append(lcp.QueueReplayRequest(reqs[i].arrival_s, indexes[j].handle.value, k, Q, qp, dbase + o,
-                                            dbase + o + Q * k * 4))
-    torch.cuda.synchronize()
-    qu = lcp.Queue(max_requests=1024, max_tasks=1 << 18, idle_ms=20.0)
-    launches0 = lcp.lcp_launch_count()
-    try:
-        qrc, qlat, qwall = qu.replay(qreqs, timeout_s=120.0)
-        qlaunches = lcp.lcp_launch_count() - launches0
-        qst = qu.stats()
-    finally:
-        qu.close()
-    qsame = True
-    for i in range(max(n_req - 40, wrap_at), n_req):
-        j, qoff, Q, k, o = layout[i]
-        if qlat[i] < 0:
-            continue
-        alone = lcp.lcp_topk_batch(indexes[j], dpools[j][qoff:qoff + Q], k)
-        got = darena[o:o + Q * k * 4].view(torch.int32).view(Q, k)
-        got_lcp = darena[o + Q * k * 4:o + Q * k * 5].view(Q, k)
-        qsame = qsame and bool(torch.equal(got, alone[0]) and torch.equal(got_lcp, alone[1]))
-    qok = qlat[qlat >= 0]
-    qdone = int(sum(qreqs[i].Q for i in range(n_req) if qlat[i] >= 0))
-    queue_res = {"requests": n_req, "completed": int(len(qok)),
-                 "qps": round(qdone / qwall, 1) if qwall > 0 else None,
-                 "latency_ms": {"p50": round(float(np.percentile(qok, 50)) * 1e3, 4),
-                                "p99": round(float(np.percentile(qok, 99)) * 1e3, 4),
-                                "p99.9": round(float(np.percentile(qok, 99.9)) * 1e3, 4)},
-                 "worker_launches": int(qst["worker_launches"]), "kernel_launches": int(qlaunches),
-                 "queries_and_outputs": "device-resident", "results_equal_alone": qsame, "rc": int(qrc)}
-    del darena, dpools
-    ok = lat[lat >= 0]
+        same = same and bool(torch.equal(got, a[0].cpu()) and torch.equal(got_lcp, a[1].cpu()))
     done_q = int(sum(reqs[i].Q for i in range(n_req) if lat[i] >= 0))
-    res = {"requests": n_req, "rate_per_s": rate, "completed": int(len(ok)), "rejected": int(st["rejected"]),
-           "queries": done_q, "qps": round(done_q / wall, 1) if wall > 0 else None,
-           "requests_per_s": round(len(ok) / wall, 1) if wall > 0 else None,
-           "latency_ms": {"p50": round(float(np.percentile(ok, 50)) * 1e3, 4),
-                          "p99": round(float(np.percentile(ok, 99)) * 1e3, 4),
-                          "p99.9": round(float(np.percentile(ok, 99.9)) * 1e3, 4)},
+    sizes = [reqs[i].Q for i in range(n_req)]
+    res = {"requests": n_req, "completed": int((lat >= 0).sum()), "rejected": int(st["rejected"]),
+           "queries": done_q, "duration_s": round(float(rq["arrival_s"][-1]), 2),
+           "qps": round(done_q / wall, 1) if wall > 0 else None,
+           "requests_per_s": round(int((lat >= 0).sum()) / wall, 1) if wall > 0 else None,
+           "latency_ms": latency_summary(lat, sizes, rq["arrival_s"]),
            "mem_budget": budget, "mem_peak": int(st["mem_peak"]), "streams": streams,
            "max_inflight": max_inflight, "kernel_launches": int(launches),
-           "results_equal_alone": same, "rc": int(rc), "persistent_queue": queue_res}
-    for ix in indexes:
+           "results_equal_alone": same, "rc": int(rc)}
+    if queue and all(kind == "index" for kind, _ in slots):
+        darena = torch.empty(arena_bytes, dtype=torch.uint8, device=device)
+        dbase = darena.data_ptr()
+        qreqs = []
+        for i in range(n_req):
+            j, qoff, Q, k, o = layout[i]
+            qp = dpools[j].data_ptr() + qoff * dpools[j].shape[1] * dpools[j].element_size()
+            qreqs.append(lcp.QueueReplayRequest(reqs[i].arrival_s, slots[j][1].handle.value, k, Q, qp, dbase + o,
+                                                dbase + o + Q * k * 4))
+        torch.cuda.synchronize()
+        qu = lcp.Queue(max_requests=1024, max_tasks=1 << 18, idle_ms=20.0)
+        launches0 = lcp.lcp_launch_count()
+        try:
+            qrc, qlat, qwall = qu.replay(qreqs, timeout_s=600.0)
+            qlaunches = lcp.lcp_launch_count() - launches0
+            qst = qu.stats()
+        finally:
+            qu.close()
+        qsame = True
+        for i in range(max(n_req - check, wrap_at), n_req):
+            j, qoff, Q, k, o = layout[i]
+            if qlat[i] < 0:
+                continue
+            a = alone(j, qoff, Q, k, dpools[j])
+            got = darena[o:o + Q * k * 4].view(torch.int32).view(Q, k)
+            got_lcp = darena[o + Q * k * 4:o + Q * k * 5].view(Q, k)
+            qsame = qsame and bool(torch.equal(got, a[0]) and torch.equal(got_lcp, a[1]))
+        qdone = int(sum(qreqs[i].Q for i in range(n_req) if qlat[i] >= 0))
+        res["persistent_queue"] = {
+            "requests": n_req, "completed": int((qlat >= 0).sum()),
+            "qps": round(qdone / qwall, 1) if qwall > 0 else None,
+            "latency_ms": latency_summary(qlat, sizes, rq["arrival_s"]),
+            "worker_launches": int(qst["worker_launches"]), "kernel_launches": int(qlaunches),
+            "queries_and_outputs": "device-resident", "results_equal_alone": qsame, "rc": int(qrc)}
+        del darena
+    del dpools
+    return res
+
+
+def serving_leg(lcp, device, to_dev, duration_s=10.0):
+    """Six resident zipf-prefix indexes (N, L) in SERVING_INDEXES; requests
+    arrive Poisson at 20k/s with log-uniform batch sizes in [1, 4096], k in
+    {1, 10, 100} and a uniformly drawn index; admission by a device-memory
+    budget; latency = completion - scheduled arrival."""
+    w = W.WORKLOADS["serving6"]
+    V, s_, seed, rate = w["vocab"], w["s"], w["seed"], w["rate"]
+    slots, pools = [], []
+    for i, (N, L) in enumerate(W.SERVING_INDEXES):
+        S = W.zipf_prefix_rows(N, L, V, s_, seed * 100 + i)
+        pool = W.zipf_prefix_queries(S, 16_384, V, s_, seed * 100 + i)
+        slots.append(("index", lcp.lcp_index_build(to_dev(S, device), max_k=100)))
+        pools.append(pinned(pool))
+    rq = W.serving_requests(int(rate * duration_s), rate, len(slots), seed)
+    res = replay_serving(lcp, device, slots, pools, rq)
+    res["rate_per_s"] = rate
+    for _, ix in slots:
         ix.close()
     return res
+
+
+def serving_c3_leg(lcp, device, duration_s=10.0):
+    """The bench workload served: one resident index over its 2M rows (L =
+    64, uint16), the serving mix's request stream (Poisson at 20k/s,
+    log-uniform 1-4,096 queries, k in {1, 10, 100}) through the session and
+    the persistent queue; beside it the full scan of the same rows served by
+    the session the same way -- at a rate it can sustain (0.7 of its
+    throughput measured on 400 back-to-back requests of the same mix), since
+    the indexed path's rate would overload it."""
+    import torch
+    w = W.WORKLOADS["zipf2m_L64"]
+    rate = W.WORKLOADS["serving6"]["rate"]
+    S = W.zipf_prefix_rows(w["N"], w["L"], w["vocab"], w["s"], w["seed"])
+    pool = pinned(W.zipf_prefix_queries(S, 16_384, w["vocab"], w["s"], w["seed"]))
+    dS = to_dev(S, device)
+    ix = lcp.lcp_index_build(dS, max_k=w["k"])
+    rq = W.serving_requests(int(rate * duration_s), rate, 1, 11)
+    out = {"N": w["N"], "L": w["L"], "k_mix": [1, 10, 100], "rate_per_s": rate,
+           "indexed": replay_serving(lcp, device, [("index", ix)], [pool], rq)}
+    # the full scan's sustainable rate, then the same stream shape at 0.7 of it
+    cal = W.serving_requests(400, rate, 1, 12)
+    cal["arrival_s"] = np.zeros(400)
+    c = replay_serving(lcp, device, [("scan", dS)], [pool], cal, warm=20, check=0, queue=False)
+    cap = c["requests_per_s"] or 1.0
+    srate = 0.7 * cap
+    srq = W.serving_requests(max(int(srate * duration_s), 50), srate, 1, 13)
+    scan = replay_serving(lcp, device, [("scan", dS)], [pool], srq, warm=20, check=10, queue=False)
+    scan["rate_per_s"] = round(srate, 1)
+    scan["capacity_requests_per_s"] = round(cap, 1)
+    out["full_scan"] = scan
+    ix.close()
+    del dS
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -421,6 +421,15 @@ typedef struct {
 LCP_API int lcp_session_create(const lcp_session_cfg_t* cfg, lcp_session_t* out);
 /* Registers an index; *slot receives its number (0, 1, ...). */
 LCP_API int lcp_session_add_index(lcp_session_t session, lcp_index_t index, int32_t* slot);
+/* Registers a resident token set ([N, L] device memory in format fmt, kept
+ * valid and unchanged by the caller for the session's life) answered by the
+ * full scan (lcp_scan_topk), so that the index-free baseline is served the
+ * same way as an index; k <= LCP_SCAN_MAX_K.  A request counts
+ * Q*(L*token_bytes + 5*k) bytes against the budget (its queries and
+ * results, carved from the session's memory); the scan's own temporaries
+ * come from the stream-ordered pool. */
+LCP_API int lcp_session_add_scan(lcp_session_t session, const void* d_tokens, int64_t N, lcp_format_t fmt,
+                                 int32_t* slot);
 /* Queues a request; *ticket identifies it.  Never blocks on the device.
  * queries, out_ids and out_lcp: host or device pointers (see above). */
 LCP_API int lcp_session_submit(lcp_session_t session, int32_t slot, const void* queries, int64_t Q,

@@ -50,7 +50,8 @@ ABI_SYMBOLS = (
     "lcp_index_export", "lcp_index_sync", "lcp_index_destroy", "lcp_device_status",
     "lcp_launch_count", "lcp_debug_bounded_wait", "lcp_scan_topk_noalloc",
     "lcp_kernel_timing", "lcp_kernel_time", "lcp_kernel_timing_filter",
-    "lcp_session_create", "lcp_session_add_index", "lcp_session_submit", "lcp_session_poll",
+    "lcp_session_create", "lcp_session_add_index", "lcp_session_add_scan", "lcp_session_submit",
+    "lcp_session_poll",
     "lcp_session_stats", "lcp_session_destroy", "lcp_session_replay",
     "lcp_step_create", "lcp_step_run", "lcp_step_stats", "lcp_step_destroy", "lcp_shard_merge",
     "lcp_topk_bfs", "lcp_tal_topk",
@@ -134,6 +135,7 @@ def _load():
         "lcp_scan_top1_wide": ([vp, i64, _Format, vp, i64, vp, vp, vp], ctypes.c_int),
         "lcp_session_create": ([ctypes.POINTER(SessionConfig), ctypes.POINTER(vp)], ctypes.c_int),
         "lcp_session_add_index": ([vp, vp, ctypes.POINTER(i32)], ctypes.c_int),
+        "lcp_session_add_scan": ([vp, vp, i64, _Format, ctypes.POINTER(i32)], ctypes.c_int),
         "lcp_session_submit": ([vp, i32, vp, i64, i32, vp, vp, ctypes.POINTER(ctypes.c_uint64)],
                                ctypes.c_int),
         "lcp_session_poll": ([vp, ctypes.c_uint64, i32], ctypes.c_int),
@@ -651,6 +653,16 @@ class Session:
         h = index.handle if index is not None else ctypes.c_void_p(0)
         _check(_lib.lcp_session_add_index(self._h, h, ctypes.byref(slot)), "lcp_session_add_index")
         self._indexes.append(index)
+        return slot.value
+
+    def add_scan(self, tokens: torch.Tensor, vocab: int = 0) -> int:
+        """Registers resident tokens ([N, L] device tensor, kept alive here)
+        answered by the full scan; returns the slot."""
+        tokens = _rows(tokens, device=True)
+        slot = ctypes.c_int32()
+        _check(_lib.lcp_session_add_scan(self._h, _ptr(tokens), tokens.shape[0], _fmt(tokens, vocab),
+                                         ctypes.byref(slot)), "lcp_session_add_scan")
+        self._indexes.append(tokens)
         return slot.value
 
     def submit(self, slot: int, queries, k: int, out_ids=None, out_lcp=None) -> int:

@@ -183,6 +183,10 @@ struct SearchShape {
     int fused = 0;        // 1: one kernel, a warp per query (small batches)
 };
 
+// The full scan (scan.cu) on stream s: rows [N, L] of tb-byte tokens.
+int scan_topk_device(const void* d_tokens, int64_t N, int tb, int L, const void* d_queries, int64_t Q, int k,
+                     int32_t* d_out_ids, uint8_t* d_out_lcp, cudaStream_t s);
+
 int topk_batch_device(lcp_index_s* x, const void* d_queries, int64_t Q, int k, int32_t* out_ids,
                       uint8_t* out_lcp, cudaStream_t s, void* loc_scratch = nullptr,
                       const SearchShape* shape = nullptr);

@@ -52,11 +52,19 @@ struct Req {
 
 }  // namespace
 
+// A slot answered by the full scan: resident tokens instead of an index.
+struct ScanSlot {
+    const void* tokens = nullptr;  // null: an index slot
+    int64_t N = 0;
+    int tb = 0, L = 0;
+};
+
 struct lcp_session_s {
     lcp_session_cfg_t cfg{};
     int device = 0;
     std::mutex mu;
     std::vector<lcp_index_t> idx;
+    std::vector<ScanSlot> scan;  // per slot
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> spare_events;
     std::deque<uint64_t> pending;
@@ -83,8 +91,8 @@ constexpr int64_t round256(int64_t b) { return (b + 255) & ~(int64_t)255; }
 // slab.
 constexpr int64_t kSlabSlack = 1024;
 
-int64_t slab_block(const lcp_index_s* x, int64_t Q, int k) {
-    return round256(Q * (int64_t)x->L * x->tb) + round256(Q * 4 * (int64_t)k) + round256(Q * (int64_t)k);
+int64_t slab_block(int64_t row_bytes, int64_t Q, int k) {
+    return round256(Q * row_bytes) + round256(Q * 4 * (int64_t)k) + round256(Q * (int64_t)k);
 }
 
 // First fit; -1 when no free block is large enough.
@@ -119,8 +127,9 @@ void slab_give(lcp_session_s* s, int64_t off, int64_t bytes) {
 int launch(lcp_session_s* s, Req& r) {
     if (s->cfg.dry_run) return LCP_OK;
     lcp_index_s* x = s->idx[r.slot];
+    const ScanSlot& sc = s->scan[r.slot];
     cudaStream_t st = s->streams[r.stream];
-    const size_t qb = (size_t)r.Q * x->L * x->tb;
+    const size_t qb = (size_t)r.Q * (x ? x->L * x->tb : sc.L * sc.tb);
     const size_t ib = (size_t)r.Q * r.k * sizeof(int32_t), lb = (size_t)r.Q * r.k;
     if (r.Q > 0) {
         char* base = s->slab + r.off;
@@ -130,7 +139,8 @@ int launch(lcp_session_s* s, Req& r) {
         // queries and outputs may be host or device memory: unified
         // addressing tells the copy engine which
         LCP_CUDA_TRY(cudaMemcpyAsync(dq, r.hq, qb, cudaMemcpyDefault, st));
-        int rc = lcp_topk_batch(x, dq, r.Q, r.k, did, dl, st);
+        int rc = x ? lcp_topk_batch(x, dq, r.Q, r.k, did, dl, st)
+                   : lcph::scan_topk_device(sc.tokens, sc.N, sc.tb, sc.L, dq, r.Q, r.k, did, dl, st);
         if (rc != LCP_OK) return rc;
         LCP_CUDA_TRY(cudaMemcpyAsync(r.hid, did, ib, cudaMemcpyDefault, st));
         LCP_CUDA_TRY(cudaMemcpyAsync(r.hlcp, dl, lb, cudaMemcpyDefault, st));
@@ -264,6 +274,23 @@ int lcp_session_add_index(lcp_session_t s, lcp_index_t index, int32_t* slot) {
     std::lock_guard<std::mutex> lk(s->mu);
     if (index) index->shared = true;  // used on the session's streams from now on
     s->idx.push_back(index);
+    s->scan.push_back(ScanSlot());
+    *slot = (int32_t)s->idx.size() - 1;
+    return LCP_OK;
+}
+
+int lcp_session_add_scan(lcp_session_t s, const void* d_tokens, int64_t N, lcp_format_t fmt, int32_t* slot) {
+    if (!s || !slot || N < 1 || N >= (1ll << 30) || !d_tokens || (fmt.token_bytes != 1 && fmt.token_bytes != 2) ||
+        fmt.L < 1 || fmt.L > LCP_MAX_L)
+        return LCP_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(s->mu);
+    ScanSlot sc;
+    sc.tokens = d_tokens;
+    sc.N = N;
+    sc.tb = fmt.token_bytes;
+    sc.L = fmt.L;
+    s->idx.push_back(nullptr);
+    s->scan.push_back(sc);
     *slot = (int32_t)s->idx.size() - 1;
     return LCP_OK;
 }
@@ -274,12 +301,17 @@ int lcp_session_submit(lcp_session_t s, int32_t slot, const void* h_queries, int
     std::lock_guard<std::mutex> lk(s->mu);
     if (slot < 0 || slot >= (int32_t)s->idx.size()) return LCP_ERR_INVALID;
     lcp_index_s* x = s->idx[slot];
+    const ScanSlot& sc = s->scan[slot];
     int64_t bytes;
     int64_t blk = 0;
     if (x) {
         if (k > x->max_k) return LCP_ERR_INVALID;
         bytes = request_bytes(x, Q, k);
-        blk = slab_block(x, Q, k);
+        blk = slab_block((int64_t)x->L * x->tb, Q, k);
+    } else if (sc.tokens) {
+        if (k > LCP_SCAN_MAX_K) return LCP_ERR_INVALID;
+        bytes = Q * ((int64_t)sc.L * sc.tb + 5 * (int64_t)k);  // queries + results
+        blk = slab_block((int64_t)sc.L * sc.tb, Q, k);
     } else {
         bytes = Q * (16 + 5 * (int64_t)k);  // dry run without an index
     }

@@ -122,3 +122,35 @@ def test_session_takes_device_and_host_buffers(lcp):
     assert np.array_equal(ids.cpu().numpy(), w_ids) and np.array_equal(lc.cpu().numpy(), w_lcp)
     assert sess.close() == lcp.LCP_OK
     ix.close()
+
+
+def test_session_scan_slot_equals_scan_alone_and_index(lcp):
+    """A full-scan slot (resident tokens, no index) served beside an index
+    slot over the same rows: every request equals lcp_scan_topk alone, the
+    index's answer and, on a sample, the oracle."""
+    S = W.zipf_prefix_rows(60_000, 32, 1024, 1.1, 9)
+    Qs = W.zipf_prefix_queries(S, 3_000, 1024, 1.1, 9)
+    dS = _dev(S)
+    ix = lcp.lcp_index_build(dS, max_k=64)
+    sess = lcp.Session(mem_budget=32 << 20, max_inflight=6, streams=3)
+    si = sess.add_index(ix)
+    ss = sess.add_scan(dS)
+    rng = np.random.default_rng(10)
+    reqs = []
+    for _ in range(24):
+        Q = int(np.exp(rng.uniform(0, np.log(1500))))
+        k = int(rng.choice([1, 10, 64]))
+        o = int(rng.integers(0, 3_000 - Q))
+        slot = int(rng.choice([si, ss]))
+        reqs.append((sess.submit(slot, _pinned(Qs[o:o + Q]), k), slot, o, Q, k))
+    for t, slot, o, Q, k in reqs:
+        ids, lc = sess.result(t)
+        a = lcp.lcp_scan_topk(dS, _dev(Qs[o:o + Q]), k)
+        b = lcp.lcp_topk_batch(ix, _dev(Qs[o:o + Q]), k)
+        assert np.array_equal(ids.numpy(), a[0].cpu().numpy()) and np.array_equal(lc.numpy(), a[1].cpu().numpy())
+        assert np.array_equal(ids.numpy(), b[0].cpu().numpy()) and np.array_equal(lc.numpy(), b[1].cpu().numpy())
+    w_ids, w_lcp = oracle.topk_batch(S, Qs[:30], 64)
+    ids, lc = sess.result(sess.submit(ss, _pinned(Qs[:30]), 64))
+    assert np.array_equal(ids.numpy(), w_ids) and np.array_equal(lc.numpy(), w_lcp)
+    assert sess.close() == lcp.LCP_OK
+    ix.close()
