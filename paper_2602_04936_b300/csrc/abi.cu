@@ -199,6 +199,27 @@ struct GraphBuildState {
     size_t bytes = 0;
     cudaEvent_t scratch_free = nullptr;
     cudaEvent_t chk = nullptr;
+    // What the instantiated graph was captured for: every pointer and size
+    // it holds follows from these (the index's arrays are carved from its
+    // arena by the format, capacity and K), so a build with the same
+    // signature -- the pool usually hands a rebuilt index the same arena --
+    // relaunches it without a new capture.  The host-side fields the
+    // capture set on the index are kept with it.
+    struct Sig {
+        const void* tokens = nullptr;
+        int64_t N = 0, cap = 0;
+        void* arena = nullptr;
+        void* scratch = nullptr;
+        int tb = 0, L = 0, K = 0, max_k = 0;
+        bool operator==(const Sig& o) const {
+            return tokens == o.tokens && N == o.N && cap == o.cap && arena == o.arena && scratch == o.scratch &&
+                   tb == o.tb && L == o.L && K == o.K && max_k == o.max_k;
+        }
+    } sig;
+    bool sig_ok = false;
+    int hlev = 0;
+    int64_t hoff[lcpk::kMaxHLev + 1] = {0};
+    int64_t hlen[lcpk::kMaxHLev + 1] = {0};
 };
 
 static GraphBuildState* graph_build_state() {
@@ -211,6 +232,24 @@ static GraphBuildState* graph_build_state() {
         return nullptr;
     if (!g.chk && cudaEventCreateWithFlags(&g.chk, cudaEventDisableTiming) != cudaSuccess) return nullptr;
     return &g;
+}
+
+// Launches the instantiated build graph on s, then waits for its mid-graph
+// event and, when rows were left to the exact refinement, redoes the order.
+static int launch_build_graph(GraphBuildState* g, lcp_index_s* x, const void* d_tokens, const lcpk::RowFmt& f,
+                              int64_t N, cudaStream_t s, const uint32_t* huge) {
+    LCP_CUDA_TRY(cudaStreamWaitEvent(s, g->scratch_free, 0));  // a graph on another stream used the scratch
+    LCP_CUDA_TRY(cudaGraphLaunch(g->exec, s));
+    LCP_CUDA_TRY(cudaEventRecord(g->scratch_free, s));
+    LCP_CUDA_TRY(cudaEventSynchronize(g->chk));
+    if (*huge != 0) {
+        int rc = build_sorted_ids(d_tokens, f, N, x->buf[0].ids, x->status, s);
+        if (rc == LCP_OK) rc = gather_rows_and_lcp(d_tokens, f, N, x->buf[0].ids, x->buf[0], x->W, s);
+        if (rc == LCP_OK) rc = build_aux(x, s, false);
+        if (rc != LCP_OK) return rc;
+    }
+    const cudaError_t le = cudaGetLastError();
+    return le == cudaSuccess ? LCP_OK : cuda_status(le);
 }
 
 // Returns LCP_OK (built), LCP_PENDING (cannot run as a graph here; nothing
@@ -242,6 +281,25 @@ static int graph_build(lcp_index_s* x, const void* d_tokens, int64_t N, cudaStre
     }
     *huge = 0;
     lcpk::RowFmt f = lcpk::make_fmt(x->tb, x->L, d_tokens);
+    GraphBuildState::Sig sig;
+    sig.tokens = d_tokens;
+    sig.N = N;
+    sig.cap = x->cap;
+    sig.arena = x->arena;
+    sig.scratch = g->scratch;
+    sig.tb = x->tb;
+    sig.L = x->L;
+    sig.K = x->K;
+    sig.max_k = x->max_k;
+    if (g->exec && g->sig_ok && sig == g->sig) {  // the same graph: relaunch it
+        x->hlev = g->hlev;
+        for (int j = 0; j <= lcpk::kMaxHLev; ++j) {
+            x->hoff[j] = g->hoff[j];
+            x->hlen[j] = g->hlen[j];
+        }
+        return launch_build_graph(g, x, d_tokens, f, N, s, huge);
+    }
+    g->sig_ok = false;
     const lcp_index_s saved = *x;
     (void)side_stream();  // created outside the capture
     LCP_CUDA_TRY(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
@@ -274,18 +332,14 @@ static int graph_build(lcp_index_s* x, const void* d_tokens, int64_t N, cudaStre
         return LCP_PENDING;
     }
     cudaGraphDestroy(graph);
-    LCP_CUDA_TRY(cudaStreamWaitEvent(s, g->scratch_free, 0));  // a graph on another stream used the scratch
-    LCP_CUDA_TRY(cudaGraphLaunch(g->exec, s));
-    LCP_CUDA_TRY(cudaEventRecord(g->scratch_free, s));
-    LCP_CUDA_TRY(cudaEventSynchronize(g->chk));
-    if (*huge != 0) {
-        rc = build_sorted_ids(d_tokens, f, N, x->buf[0].ids, x->status, s);
-        if (rc == LCP_OK) rc = gather_rows_and_lcp(d_tokens, f, N, x->buf[0].ids, x->buf[0], x->W, s);
-        if (rc == LCP_OK) rc = build_aux(x, s, false);
-        if (rc != LCP_OK) return rc;
+    g->sig = sig;
+    g->sig_ok = true;
+    g->hlev = x->hlev;
+    for (int j = 0; j <= lcpk::kMaxHLev; ++j) {
+        g->hoff[j] = x->hoff[j];
+        g->hlen[j] = x->hlen[j];
     }
-    const cudaError_t le = cudaGetLastError();
-    return le == cudaSuccess ? LCP_OK : cuda_status(le);
+    return launch_build_graph(g, x, d_tokens, f, N, s, huge);
 }
 
 static int alloc_index(lcp_index_s* x, int64_t N, int64_t cap, cudaStream_t s) {

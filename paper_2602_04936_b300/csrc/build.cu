@@ -3,7 +3,9 @@
 // 1. Keys: word 0 of every row with its id (the load asks L2 for 64 bytes:
 //    only 8 bytes of each row are needed here).
 // 2. A stable LSD radix sort of the (word 0, id) pairs: 8-bit digits,
-//    reduce-then-scan passes (sort.cu).
+//    reduce-then-scan passes (sort.cu), as two 32-bit sorts -- the low half
+//    of word 0, then the high half gathered by id -- so that every pass
+//    moves 8-byte (key, id) pairs.
 // 3. Rows sharing word 0 with another row form tie groups, found straight
 //    from the equality flags of the sorted keys: a group of at most 32 rows
 //    is ranked by a warp, one of 33-2048 rows by a CTA, on word 1 and -- only
@@ -26,10 +28,13 @@
 
 namespace lcpk {
 
-// Word 0 of every row.  Only its first 8 bytes of each row are needed, so
-// the aligned load asks L2 for a 64-byte fetch rather than a whole line.
+// Word 0 of every row, in halves: the low half twice (the sort's key, and a
+// copy by id for the equality test), the high half by id, and vals[i] = i.
+// Only the first 8 bytes of each row are needed, so the aligned load asks L2
+// for a 64-byte fetch rather than a whole line.
 __global__ void k_keys_word0(const uint8_t* __restrict__ tokens, RowFmt f, uint32_t n,
-                             uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                             uint32_t* __restrict__ key_lo, uint32_t* __restrict__ lo_by_id,
+                             uint32_t* __restrict__ hi_by_id, uint32_t* __restrict__ vals) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint8_t* row = row_of(tokens, i, f);
@@ -40,18 +45,38 @@ __global__ void k_keys_word0(const uint8_t* __restrict__ tokens, RowFmt f, uint3
     } else {
         x = pack_word(row, 0, f);
     }
-    keys[i] = x;
+    key_lo[i] = (uint32_t)x;
+    lo_by_id[i] = (uint32_t)x;
+    hi_by_id[i] = (uint32_t)(x >> 32);
     vals[i] = i;
 }
 
-// The sorted ids, and eq[i] = 1 where the row at sorted position i has the
-// same word 0 as the row before it.
-__global__ void k_ids_eq(const uint32_t* __restrict__ vs, const uint64_t* __restrict__ keys, uint32_t n,
-                         int32_t* __restrict__ ids, uint8_t* __restrict__ eq) {
+// Between the two halves of the sort: the high half of each row's word 0,
+// in the order the low-half passes left.
+__global__ void k_gather_hi(const uint32_t* __restrict__ vals, const uint32_t* __restrict__ hi_by_id, uint32_t n,
+                            uint32_t* __restrict__ key_hi) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    ids[i] = (int32_t)vs[i];
-    eq[i] = (i > 0 && keys[i] == keys[i - 1]) ? 1 : 0;
+    const uint32_t v = vals[i];
+    key_hi[i] = v < n ? hi_by_id[v] : 0u;
+}
+
+// The sorted ids, and eq[i] = 1 where the row at sorted position i has the
+// same word 0 as the row before it (high halves in sorted order, low halves
+// by id).
+__global__ void k_ids_eq(const uint32_t* __restrict__ vs, const uint32_t* __restrict__ key_hi,
+                         const uint32_t* __restrict__ lo_by_id, uint32_t n, int32_t* __restrict__ ids,
+                         uint8_t* __restrict__ eq) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t v = vs[i];
+    ids[i] = (int32_t)v;
+    bool e = false;
+    if (i > 0 && key_hi[i] == key_hi[i - 1]) {
+        const uint32_t u = vs[i - 1];
+        e = v < n && u < n && lo_by_id[v] == lo_by_id[u];
+    }
+    eq[i] = e ? 1 : 0;
 }
 
 // keys[i] = word r of the row at sorted position act[i]; vals[i] = i.
@@ -762,16 +787,26 @@ int build_sorted_ids(const void* tokens, const RowFmt& f, int64_t N64, int32_t* 
         cleanup();
         return rc;
     }
-    // first sort key: (word 0, id) over all rows
-    LCP_TIMED_LAUNCH(k_keys_word0, blocks_for(N, 256), 256, 0, s, tk, f, N, k0, v0);
-    uint64_t* ks;
+    // first sort key: (word 0, id) over all rows, as two stable 32-bit LSD
+    // sorts -- the low half, then the high half gathered by id -- so that a
+    // pass moves 8-byte (key, id) pairs instead of 12-byte ones
+    uint32_t* ka = reinterpret_cast<uint32_t*>(k0);  // [N] sort keys
+    uint32_t* lo_by_id = ka + N;                      // [N]
+    uint32_t* kb = reinterpret_cast<uint32_t*>(k1);  // [N] sort scratch
+    uint32_t* hi_by_id = kb + N;                      // [N]
+    LCP_TIMED_LAUNCH(k_keys_word0, blocks_for(N, 256), 256, 0, s, tk, f, N, ka, lo_by_id, hi_by_id, v0);
+    uint32_t* ks;
     uint32_t* vs;
-    rc = radix_sort_pairs_u64(k0, v0, k1, v1, N, 64, w, s, &ks, &vs);
+    rc = radix_sort_pairs_u32(ka, v0, kb, v1, N, 32, w, s, &ks, &vs);
+    if (rc == LCP_OK) {
+        LCP_TIMED_LAUNCH(k_gather_hi, blocks_for(N, 256), 256, 0, s, vs, hi_by_id, N, ka);
+        rc = radix_sort_pairs_u32(ka, v0, kb, v1, N, 32, w, s, &ks, &vs);
+    }
     if (rc) {
         cleanup();
         return rc;
     }
-    LCP_TIMED_LAUNCH(k_ids_eq, blocks_for(N, 256), 256, 0, s, vs, ks, N, ids_out, eq);
+    LCP_TIMED_LAUNCH(k_ids_eq, blocks_for(N, 256), 256, 0, s, vs, ks, lo_by_id, N, ids_out, eq);
     uint32_t m = 0, G = 0;
     // Rows tied on word 0: tie groups of up to kMidMax rows are ranked directly
     // on their remaining words (found straight from eq); only groups of more
@@ -817,9 +852,10 @@ int build_sorted_ids(const void* tokens, const RowFmt& f, int64_t N64, int32_t* 
     for (int r = 1; rc == 0 && r < f.W && m > 0; ++r) {
         LCP_TIMED_LAUNCH(k_keys_active, blocks_for(m, 256), 256, 0, s, tk, f, N, ids_out, act, m, r, k0,
                    v0);
-        rc = radix_sort_pairs_u64(k0, v0, k1, v1, m, 64, w, s, &ks, &vs);
+        uint64_t* ks64;
+        rc = radix_sort_pairs_u64(k0, v0, k1, v1, m, 64, w, s, &ks64, &vs);
         if (rc) break;
-        LCP_TIMED_LAUNCH(k_group_keys, blocks_for(m, 256), 256, 0, s, ks, vs, grp, m, kbi, gk, gv);
+        LCP_TIMED_LAUNCH(k_group_keys, blocks_for(m, 256), 256, 0, s, ks64, vs, grp, m, kbi, gk, gv);
         int gbits = 0;
         while (gbits < 32 && (1ull << gbits) < (uint64_t)G) ++gbits;
         uint32_t *gks, *fv;
