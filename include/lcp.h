@@ -224,10 +224,10 @@ LCP_API int lcp_scan_top1_wide(const void* d_tokens, int64_t N, lcp_format_t fmt
  *
  * Scratch: a fixed array of LCP_SCAN_NOALLOC_SCRATCH_BYTES inside the
  * library's device image, held by every GPU that loads the library until the
- * process exits.  A call needs round_up(N * 8, 256) + round_up(Q * 4, 256) +
- * Q * (k + 64) * 8 bytes of it (the rows' first words, then one N-slice of
- * per-query logs and their counts); larger requests return LCP_ERR_INVALID
- * without enqueuing anything (split the query batch).  The call allocates nothing: no cudaMalloc, cudaFree or
+ * process exits.  A call needs 2 * round_up(N * 4, 256) + round_up(Q * 4, 256)
+ * + Q * (k + 64) * 8 bytes of it (the rows' first words in two halves, then
+ * one N-slice of per-query logs and their counts); larger requests return
+ * LCP_ERR_INVALID without enqueuing anything (split the query batch).  The call allocates nothing: no cudaMalloc, cudaFree or
  * allocating library routine.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) -- make that first call
  * before any stream capture.  Every call shares the one array: calls that

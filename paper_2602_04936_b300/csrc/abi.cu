@@ -127,6 +127,14 @@ int* lib_status_word() {
     return g_status[dev];
 }
 
+// The same word if it exists already, else null (never allocates).
+int* lib_status_word_if_any() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_status_mu);
+    return g_status[dev];
+}
+
 int sm_count() {
     static int cache[64] = {0};
     int dev = 0;

@@ -99,6 +99,53 @@ __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Bulk copies global -> shared memory by the TMA unit (cp.async.bulk), with
+// completion counted on a shared-memory mbarrier.  Addresses must be 16-byte
+// aligned and sizes multiples of 16 bytes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// Makes initialised barriers (and earlier shared-memory accesses of this
+// thread) visible to the asynchronous proxy before a bulk copy uses them.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// One arrival that also announces `bytes` of incoming bulk-copy data.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    uint64_t state;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                 : "=l"(state)
+                 : "r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    (void)state;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// Waits for the barrier's phase of the given parity to complete, at most
+// `limit` polls; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
+    const uint32_t a = smem_u32(bar);
+    for (long long i = 0; i < limit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // Device status codes written by kernels into a status word (0 = fine).
 enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BAD = 2 };
 
@@ -119,6 +166,7 @@ namespace lcph {
 void count_launch(int n = 1);
 int cuda_status(cudaError_t e);  // maps to LCP_ERR_* and records the last error text
 int* lib_status_word();          // device pointer to the library-wide status word
+int* lib_status_word_if_any();   // the same if it was allocated already, else null
 int sm_count();                  // multiprocessors of the current device (cached)
 // Optional per-kernel timing (lcp_kernel_timing): CUDA events recorded on the
 // launching stream around the kernel; off by default and inside graph capture.

@@ -72,12 +72,14 @@ extern "C" int lcp_scan_topk_noalloc(const void* d_tokens, int64_t N, lcp_format
         LCP_CUDA_TRY(cudaMemsetAsync(d_out_lcp, 0, (size_t)Q * k, s));
         return LCP_OK;
     }
-    // Scratch layout: [plane 0: N words][counts: S x Q][lists: S x Q x (k +
-    // kLogSlack) keys], each part starting on a 256-byte boundary.  The batch
+    // Scratch layout: [plane 0: N upper halves][N lower halves][counts: S x
+    // Q][lists: S x Q x (k + kLogSlack) keys], each part starting on a
+    // 256-byte boundary.  The batch
     // is scanned in its own order (no sort, no floor pass: those would need
     // more scratch); the results are the same bytes.
     const uint64_t cap = (uint64_t)LCP_SCAN_NOALLOC_SCRATCH_BYTES;
-    const uint64_t plane_bytes = ((uint64_t)N * 8 + 255) & ~255ull;
+    const uint64_t half_bytes = ((uint64_t)N * 4 + 255) & ~255ull;  // each half of the plane
+    const uint64_t plane_bytes = 2 * half_bytes;
     const int lcap = k + kLogSlack;  // log entries per (slice, query)
     auto need = [&](int64_t S) {
         return plane_bytes + (((uint64_t)S * Q * 4 + 255) & ~255ull) + (uint64_t)S * Q * lcap * 8;
@@ -90,13 +92,14 @@ extern "C" int lcp_scan_topk_noalloc(const void* d_tokens, int64_t N, lcp_format
     if (S > kMergeMaxLists) S = kMergeMaxLists;
     while (S > 1 && need(S) > cap) --S;
     if (S < 1) S = 1;
-    const int64_t slice = (N + S - 1) / S;
+    const int64_t slice = ((N + S - 1) / S + kScanSliceAlign - 1) / kScanSliceAlign * kScanSliceAlign;
     S = (N + slice - 1) / slice;
 
     void* base = nullptr;
     LCP_CUDA_TRY(scratch_address(&base));
     unsigned char* b = reinterpret_cast<unsigned char*>(base);
-    uint64_t* plane0 = reinterpret_cast<uint64_t*>(b);
+    uint32_t* plane_hi = reinterpret_cast<uint32_t*>(b);
+    uint32_t* plane_lo = reinterpret_cast<uint32_t*>(b + half_bytes);
     int32_t* counts = reinterpret_cast<int32_t*>(b + plane_bytes);
     uint64_t* lists = reinterpret_cast<uint64_t*>(b + plane_bytes + (((uint64_t)S * Q * 4 + 255) & ~255ull));
     // Nothing in the scratch needs to start at zero: plane 0 is written in
@@ -106,10 +109,11 @@ extern "C" int lcp_scan_topk_noalloc(const void* d_tokens, int64_t N, lcp_format
     RowFmt f = make_fmt(fmt.token_bytes, fmt.L, d_tokens);
     RowFmt qf = make_fmt(fmt.token_bytes, fmt.L, d_queries);
     LCP_LAUNCH(k_pack_plane0, (unsigned)((N + 255) / 256), 256, 0, s,
-               reinterpret_cast<const uint8_t*>(d_tokens), f, N, plane0);
+               reinterpret_cast<const uint8_t*>(d_tokens), f, N, plane_hi, plane_lo);
     ScanArgs a;
     a.tokens = reinterpret_cast<const uint8_t*>(d_tokens);
-    a.plane0 = plane0;
+    a.plane_hi = plane_hi;
+    a.plane_lo = plane_lo;
     a.f = f;
     a.N = N;
     a.queries = reinterpret_cast<const uint8_t*>(d_queries);
@@ -122,6 +126,9 @@ extern "C" int lcp_scan_topk_noalloc(const void* d_tokens, int64_t N, lcp_format
     a.slice = slice;
     a.lists = lists;
     a.counts = counts;
+    // the library's status word if some call made it already (this entry
+    // point allocates nothing); a bounded wait that ran out is recorded there
+    a.status = lcph::lib_status_word_if_any();
     LCP_LAUNCH(k_scan_partial, dim3((unsigned)qtiles, (unsigned)S), kScanPartialThreads, 0, s, a);
     LCP_CUDA_TRY(cudaFuncSetAttribute(k_scan_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(sizeof(uint64_t) * kMergeCap)));

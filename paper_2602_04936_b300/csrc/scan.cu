@@ -2,9 +2,11 @@
 // scan" baseline, Sec. 7), no index over the rows.
 //
 // Batches of more than kSelMaxQ queries:
-//   k_pack_plane0   word 0 of every row, packed, into one contiguous plane
-//                   (8 bytes a row: 16 MB at N=2M, so it stays in L2 while
-//                   the query tiles stream over it).
+//   k_pack_plane0   word 0 of every row, packed, into a plane of upper and
+//                   lower halves (8 bytes a row: 16 MB at N=2M, so it stays
+//                   in L2 while the query tiles stream over it); tiles of it
+//                   reach shared memory by bulk copies (the TMA unit),
+//                   double-buffered.
 //   (batch order)   the queries sorted by their first word (one CTA up to
 //                   4,096 queries, the radix sort above), so that a warp's 32
 //                   queries are neighbours in word-0 order.
@@ -34,7 +36,13 @@
 
 namespace lcpk {
 
-constexpr int kScanTile = 2048;     // plane-0 words staged per smem tile
+constexpr int kScanTile = 1024;     // plane-0 words per shared-memory tile
+constexpr int kScanStages = 3;      // tiles in the ring
+constexpr int kScanAhead = 1;       // tiles in flight beyond the one screened
+// With at least two spare buffers in the ring the buffer a copy refills was
+// last read two tiles back, before the previous tile's wait barrier, so a
+// tile needs no barrier of its own at its end.
+constexpr bool kScanEndBarrier = kScanStages - kScanAhead < 2;
 constexpr int kCompactBins = 16;    // levels above `worst` a log compaction counts in one pass
 constexpr uint64_t kKeyInf = ~0ull;
 
@@ -50,9 +58,13 @@ __device__ __forceinline__ uint64_t row_word0(const uint8_t* row, const RowFmt& 
 }
 
 __global__ void k_pack_plane0(const uint8_t* __restrict__ tokens, RowFmt f, int64_t n,
-                              uint64_t* __restrict__ plane0) {
+                              uint32_t* __restrict__ plane_hi, uint32_t* __restrict__ plane_lo) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) plane0[i] = row_word0(row_of(tokens, i, f), f);
+    if (i < n) {
+        const uint64_t w = row_word0(row_of(tokens, i, f), f);
+        plane_hi[i] = (uint32_t)(w >> 32);
+        plane_lo[i] = (uint32_t)w;
+    }
 }
 
 // Word-0 mask that tests "the first t tokens are equal" (t <= tpw).
@@ -61,9 +73,10 @@ __device__ __forceinline__ uint64_t prefix_mask(int t, int bits) {
     return b >= 64 ? ~0ull : (b == 0 ? 0ull : (~0ull << (64 - b)));
 }
 
-__global__ void __launch_bounds__(kScanPartialThreads) k_scan_partial(const ScanArgs a) {
-    __shared__ __align__(16) uint64_t tile[kScanTile];
-    __shared__ __align__(16) uint32_t tile_hi[kScanTile];  // the words' upper halves
+__global__ void __launch_bounds__(kScanPartialThreads, 2) k_scan_partial(const ScanArgs a) {
+    __shared__ __align__(128) uint32_t tile_hi[kScanStages][kScanTile];  // plane tiles (upper halves),
+    __shared__ __align__(128) uint32_t tile_lo[kScanStages][kScanTile];  // a ring of kScanStages
+    __shared__ __align__(8) uint64_t tbar[kScanStages];                  // their bulk-copy barriers
     __shared__ uint16_t cbins[kCompactBins][kScanPartialThreads];
     const RowFmt& f = a.f;
     const int k = a.k;
@@ -205,28 +218,66 @@ __global__ void __launch_bounds__(kScanPartialThreads) k_scan_partial(const Scan
     };
     const bool warp_any = __any_sync(0xffffffffu, active);
     refresh();
-    for (int64_t t0 = s0; t0 < s1; t0 += kScanTile) {
+    // The plane tiles arrive by bulk copies (the TMA unit) into a ring of
+    // kScanStages buffers: the next kScanAhead tiles are in flight while one
+    // is screened.  Thread 0 issues and waits; every wait is bounded.
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < kScanStages; ++b) mbar_init(&tbar[b], 1);
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+    auto issue = [&](int64_t t, int b) {  // thread 0: tile starting at row t into buffer b
+        const int n = (int)(s1 - t < kScanTile ? s1 - t : kScanTile);
+        const uint32_t bytes = (uint32_t)((n * 4 + 15) & ~15);  // the plane is padded to 16 bytes
+        mbar_arrive_expect_tx(&tbar[b], 2 * bytes);
+        bulk_g2s(&tile_hi[b][0], a.plane_hi + t, bytes, &tbar[b]);
+        bulk_g2s(&tile_lo[b][0], a.plane_lo + t, bytes, &tbar[b]);
+    };
+    const int ntiles = s0 < s1 ? (int)((s1 - s0 + kScanTile - 1) / kScanTile) : 0;
+    if (threadIdx.x == 0)
+        for (int t = 0; t < kScanAhead && t < ntiles; ++t) issue(s0 + (int64_t)t * kScanTile, t);
+    int it = 0;
+    for (int64_t t0 = s0; t0 < s1; t0 += kScanTile, ++it) {
         const int tn = (int)(s1 - t0 < kScanTile ? s1 - t0 : kScanTile);
-        __syncthreads();
-        for (int j = threadIdx.x; j < tn; j += blockDim.x) {
-            const uint64_t w = a.plane0[t0 + j];
-            tile[j] = w;
-            tile_hi[j] = (uint32_t)(w >> 32);
+        const int buf = it % kScanStages;
+        const uint32_t parity = (uint32_t)((it / kScanStages) & 1);
+        // the buffer refilled here was last read by every thread before a
+        // barrier they have all passed (the previous tile's wait barrier, or
+        // its end barrier): those reads have returned their values, so the
+        // copy cannot overtake them
+        const int ahead = it + kScanAhead;
+        if (threadIdx.x == 0 && ahead < ntiles) issue(s0 + (int64_t)ahead * kScanTile, ahead % kScanStages);
+        // one thread waits for the tile (its acquire and the CTA barrier
+        // make the copied words visible to all; many pollers would crowd
+        // the shared-memory pipe the screen uses)
+        const bool ok = threadIdx.x != 0 || mbar_wait(&tbar[buf], parity, kSpinLimit);
+        if (__syncthreads_or(!ok)) {
+            // the copy never completed: report it, let the copies in flight
+            // land (bounded) before the CTA's shared memory is released
+            if (threadIdx.x == 0) {
+                flag_status(a.status, DEV_TIMEOUT);
+                for (int t = it; t <= ahead && t < ntiles; ++t)
+                    mbar_wait(&tbar[t % kScanStages], (uint32_t)((t / kScanStages) & 1), kSpinLimit);
+            }
+            __syncthreads();
+            return;
         }
-        __syncthreads();
-        if (!warp_any) continue;  // warp-uniform
+        if (!warp_any) {  // warp-uniform
+            if (kScanEndBarrier) __syncthreads();
+            continue;
+        }
         if (a.floor) {  // levels other slices have shared since
             const bool up = active && take_floor((int)ld_relaxed(reinterpret_cast<const uint32_t*>(a.floor) + qs));
             if (__any_sync(0xffffffffu, up)) refresh();
         }
         for (int j0 = 0; j0 < tn; j0 += 32) {
             const int j = j0 + (int)lane;
-            unsigned m = __ballot_sync(0xffffffffu, j < tn && tile_hi[j] - WL <= span);
+            unsigned m = __ballot_sync(0xffffffffu, j < tn && tile_hi[buf][j] - WL <= span);
             bool moved = false;
             while (m) {
                 const int b = __ffs(m) - 1;
                 m &= m - 1;
-                const uint64_t r = tile[j0 + b];
+                const uint64_t r = ((uint64_t)tile_hi[buf][j0 + b] << 32) | tile_lo[buf][j0 + b];
                 if (active && (worst < 0 || (r ^ q0) < T)) {
                     const int w0 = worst;
                     row_at(t0 + j0 + b, r);
@@ -235,6 +286,7 @@ __global__ void __launch_bounds__(kScanPartialThreads) k_scan_partial(const Scan
             }
             if (__any_sync(0xffffffffu, moved)) refresh();
         }
+        if (kScanEndBarrier) __syncthreads();  // this buffer is refilled with the next tile
     }
     if (active) {
         if (n > k) compact();
@@ -436,7 +488,8 @@ constexpr int kMaxScanW = (LCP_MAX_L + 3) / 4;  // packed words of the longest u
 
 struct SelArgs {
     const uint8_t* tokens;
-    const uint64_t* plane0;  // packed word 0 of every row, or null: read from the tokens
+    const uint32_t* plane_hi;  // packed word 0 of every row (upper halves), or null: read from the tokens
+    const uint32_t* plane_lo;  // (lower halves)
     RowFmt f;
     int64_t N;
     const uint8_t* queries;
@@ -454,7 +507,7 @@ struct SelArgs {
 };
 
 __device__ __forceinline__ uint64_t sel_word0(const SelArgs& a, int64_t t) {
-    return a.plane0 ? a.plane0[t] : row_word0(row_of(a.tokens, t, a.f), a.f);
+    return a.plane_hi ? ((uint64_t)a.plane_hi[t] << 32) | a.plane_lo[t] : row_word0(row_of(a.tokens, t, a.f), a.f);
 }
 
 // Exact LCP of row t with the query, given x = word0(t) ^ q0 (qw: the
@@ -862,7 +915,7 @@ static int scan_select(const void* d_tokens, int64_t N, const RowFmt& f, const v
     const bool plane = Q > 1;  // several queries re-read word 0: pack it once
     SelArgs a;
     a.tokens = reinterpret_cast<const uint8_t*>(d_tokens);
-    a.plane0 = nullptr;
+    a.plane_hi = a.plane_lo = nullptr;
     a.f = f;
     a.N = N;
     a.queries = reinterpret_cast<const uint8_t*>(d_queries);
@@ -871,9 +924,12 @@ static int scan_select(const void* d_tokens, int64_t N, const RowFmt& f, const v
     a.k = k;
     a.S = (int)S;
     a.slice = slice;
-    uint64_t* plane0 = nullptr;
+    uint32_t *plane_hi = nullptr, *plane_lo = nullptr;
     Carver cv;
-    if (plane) cv.add(&plane0, (size_t)N);
+    if (plane) {
+        cv.add(&plane_hi, (size_t)N);
+        cv.add(&plane_lo, (size_t)N);
+    }
     cv.add(&a.ge, (size_t)Q * S * L);
     cv.add(&a.tot, (size_t)Q * L);
     cv.add(&a.meta, (size_t)Q * 8);
@@ -882,7 +938,8 @@ static int scan_select(const void* d_tokens, int64_t N, const RowFmt& f, const v
     cv.add(&a.tbuf, (size_t)Q * k);
     void* base = nullptr;
     LCP_CUDA_TRY(cv.alloc(&base, s));
-    a.plane0 = plane0;
+    a.plane_hi = plane_hi;
+    a.plane_lo = plane_lo;
     // the per-slice counts and the totals are adjacent: one memset zeroes both
     cudaError_t e = cudaMemsetAsync(a.ge, 0, (size_t)((char*)(a.tot + (size_t)Q * L) - (char*)a.ge), s);
     if (e != cudaSuccess) {
@@ -890,7 +947,7 @@ static int scan_select(const void* d_tokens, int64_t N, const RowFmt& f, const v
         return cuda_status(e);
     }
     if (plane)
-        LCP_TIMED_LAUNCH(k_pack_plane0, (unsigned)((N + 255) / 256), 256, 0, s, a.tokens, f, N, plane0);
+        LCP_TIMED_LAUNCH(k_pack_plane0, (unsigned)((N + 255) / 256), 256, 0, s, a.tokens, f, N, plane_hi, plane_lo);
     const dim3 grid((unsigned)((S + kSelWarps - 1) / kSelWarps), (unsigned)Q);
     if (G == 1)
         LCP_TIMED_LAUNCH((k_sel_count<1, kSelWarps>), grid, kSelWarps * 32, 0, s, a);
@@ -910,20 +967,36 @@ static int scan_select(const void* d_tokens, int64_t N, const RowFmt& f, const v
 // the rows (the first kFloorSample: where k of them reach LCP d, no row
 // below d can be in the answer), then the k-best merge.
 constexpr int64_t kFloorSample = 65536;
-constexpr int kScanCtasPerSm = 4;
+
+// Resident k_scan_partial CTAs per multiprocessor (occupancy query, cached).
+static int scan_ctas_per_sm() {
+    static int cached = 0;
+    if (!cached) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_scan_partial, kScanPartialThreads, 0) != cudaSuccess ||
+            n < 1) {
+            cudaGetLastError();
+            n = 4;
+        }
+        cached = n;
+    }
+    return cached;
+}
 
 static int scan_logs(const void* d_tokens, int64_t N, const RowFmt& f, const void* d_queries, const RowFmt& qf,
                      int64_t Q, int k, int32_t* d_out_ids, uint8_t* d_out_lcp, cudaStream_t s) {
     const int threads = kScanPartialThreads;
     const int64_t qtiles = (Q + threads - 1) / threads;
-    const int64_t target = (int64_t)sm_count() * kScanCtasPerSm;  // CTAs per pass, about
+    // CTAs of one full wave: slices per query tile rounded down to it (a
+    // second, nearly empty wave costs more than a few idle slots)
+    const int64_t target = (int64_t)sm_count() * scan_ctas_per_sm();
     auto slices = [&](int64_t rows, int64_t min_rows, int64_t max_s, int64_t* slice) {
-        int64_t S = (target + qtiles - 1) / qtiles;
+        int64_t S = target / qtiles;
         const int64_t by_rows = (rows + min_rows - 1) / min_rows;
         if (S > by_rows) S = by_rows;
         if (S > max_s) S = max_s;
         if (S < 1) S = 1;
-        *slice = (rows + S - 1) / S;
+        *slice = ((rows + S - 1) / S + kScanSliceAlign - 1) / kScanSliceAlign * kScanSliceAlign;
         return (rows + *slice - 1) / *slice;
     };
     int64_t slice = 0;
@@ -934,11 +1007,13 @@ static int scan_logs(const void* d_tokens, int64_t N, const RowFmt& f, const voi
     const int64_t S_pre = Ns ? slices(Ns, 4096, S, &slice_pre) : 0;
     const int cap = k + kLogSlack;  // log entries per (slice, query)
     const bool small_sort = Q <= kQuerySortCta;
-    uint64_t *plane0 = nullptr, *lists = nullptr, *qk0 = nullptr, *qk1 = nullptr;
+    uint64_t *lists = nullptr, *qk0 = nullptr, *qk1 = nullptr;
+    uint32_t *plane_hi = nullptr, *plane_lo = nullptr;
     int32_t *order = nullptr, *floor = nullptr, *counts = nullptr;
     uint32_t *qv0 = nullptr, *qv1 = nullptr;
     Carver cv;
-    cv.add(&plane0, (size_t)N);
+    cv.add(&plane_hi, (size_t)N);
+    cv.add(&plane_lo, (size_t)N);
     cv.add(&order, (size_t)Q);
     cv.add(&floor, (size_t)Q);
     cv.add(&counts, (size_t)S * Q);
@@ -957,7 +1032,7 @@ static int scan_logs(const void* d_tokens, int64_t N, const RowFmt& f, const voi
     cudaError_t e = cudaSuccess;
     if (rc == LCP_OK) {
         LCP_TIMED_LAUNCH(k_pack_plane0, (unsigned)((N + 255) / 256), 256, 0, s,
-                         reinterpret_cast<const uint8_t*>(d_tokens), f, N, plane0);
+                         reinterpret_cast<const uint8_t*>(d_tokens), f, N, plane_hi, plane_lo);
         // the batch order
         if (small_sort) {
             int P = 1;
@@ -979,7 +1054,8 @@ static int scan_logs(const void* d_tokens, int64_t N, const RowFmt& f, const voi
     if (rc == LCP_OK && e == cudaSuccess) e = cudaMemsetAsync(floor, 0, sizeof(int32_t) * (size_t)Q, s);
     ScanArgs a;
     a.tokens = reinterpret_cast<const uint8_t*>(d_tokens);
-    a.plane0 = plane0;
+    a.plane_hi = plane_hi;
+    a.plane_lo = plane_lo;
     a.f = f;
     a.queries = reinterpret_cast<const uint8_t*>(d_queries);
     a.qf = qf;
@@ -988,6 +1064,7 @@ static int scan_logs(const void* d_tokens, int64_t N, const RowFmt& f, const voi
     a.k = k;
     a.cap = cap;
     a.lists = lists;
+    a.status = lib_status_word();
     a.floor = floor;
     if (rc == LCP_OK && e == cudaSuccess && Ns) {  // the floors, from the sample
         a.N = Ns;

@@ -23,12 +23,16 @@ constexpr int kMergeMaxLists = 2048;
 // the radix sort.
 constexpr int kQuerySortCta = 4096;
 
+// The packed first words of the rows, as two arrays -- upper halves, then
+// lower halves -- each starting 256-byte aligned and readable up to a
+// 16-byte multiple (the bulk copies round their sizes up).
 __global__ void k_pack_plane0(const uint8_t* __restrict__ tokens, RowFmt f, int64_t n,
-                              uint64_t* __restrict__ plane0);
+                              uint32_t* __restrict__ plane_hi, uint32_t* __restrict__ plane_lo);
 
 struct ScanArgs {
     const uint8_t* tokens;    // [N, L] raw rows
-    const uint64_t* plane0;   // packed word 0 of every row
+    const uint32_t* plane_hi;  // packed word 0 of every row: upper halves
+    const uint32_t* plane_lo;  // and lower halves
     RowFmt f;
     int64_t N;                // rows scanned: [0, N), in slices of `slice`
     const uint8_t* queries;   // [Q, L] raw queries
@@ -42,9 +46,15 @@ struct ScanArgs {
     int64_t slice;
     uint64_t* lists;          // [S][Q][cap]: each (slice, position) leaves its candidates first
     int32_t* counts;          // [S][Q]: how many (<= k) | the slice's known level << 16 (null: not written)
+    int* status;              // device status word (a bounded wait that ran out), may be null
 };
 
-// grid = (ceil(Q / kScanPartialThreads), S slices).
+// Plane words per slice are a multiple of this (the slices' first words stay
+// 16-byte aligned for the bulk copies of the plane tiles).
+constexpr int64_t kScanSliceAlign = 64;
+
+// grid = (ceil(Q / kScanPartialThreads), S slices), slices of a multiple
+// of kScanSliceAlign rows (the last may be shorter).
 __global__ void k_scan_partial(const ScanArgs a);
 
 // grid = Q (batch positions): the k best of each position's S lists into the

@@ -45,14 +45,14 @@ SCRATCH = 32 << 20
 
 
 def _need(N, Q, k):
-    """Scratch bytes of one call: the rows' first words, then one N-slice of
-    per-query counts and logs of k + 64 keys."""
-    return ((N * 8 + 255) & ~255) + ((Q * 4 + 255) & ~255) + Q * (k + 64) * 8
+    """Scratch bytes of one call: the rows' first words in two halves, then
+    one N-slice of per-query counts and logs of k + 64 keys."""
+    return 2 * ((N * 4 + 255) & ~255) + ((Q * 4 + 255) & ~255) + Q * (k + 64) * 8
 
 
 def _max_queries(N, k):
     """Largest batch that fits the scratch."""
-    Q = (SCRATCH - ((N * 8 + 255) & ~255)) // ((k + 64) * 8 + 4)
+    Q = (SCRATCH - 2 * ((N * 4 + 255) & ~255)) // ((k + 64) * 8 + 4)
     while _need(N, Q + 1, k) <= SCRATCH:
         Q += 1
     while _need(N, Q, k) > SCRATCH:
