@@ -264,8 +264,9 @@ LCP_API int lcp_tal_topk(lcp_index_t index, const void* d_queries, int64_t Q, in
  * counterpart; the shape never changes a result).  lcp_autotune times every
  * candidate shape -- one fused kernel with a warp per query (the default for
  * batches of up to 4,096 queries), or locate + answer + fill with 1..32
- * queries per warp of the answer kernel and lane- or warp-per-query location
- * -- on the caller's sample batch (device queries, Q >= 1, k <= max_k) with
+ * queries per warp of the answer kernel and lane- or warp-per-query location,
+ * or lane-per-query location that first searches the top levels of the
+ * sorted array staged in shared memory -- on the caller's sample batch (device queries, Q >= 1, k <= max_k) with
  * CUDA events on `stream`, synchronously, and installs the fastest for later
  * lcp_topk_batch calls whose index and batch fall in the same class:
  * (floor(log2 N), L, token bytes, floor(log2 Q), k class {1, <=16, <=64,
@@ -275,7 +276,8 @@ LCP_API int lcp_tal_topk(lcp_index_t index, const void* d_queries, int64_t Q, in
  * ---------------------------------------------------------------------- */
 typedef struct {
     int32_t qpw;          /* queries per warp chosen; 0: the fused kernel */
-    int32_t locate_warp;  /* 1: warp per query, 0: lane per query */
+    int32_t locate_warp;  /* 1: warp per query, 0: lane per query, 2: lane per query over the
+                             staged top levels (4,096 sampled heads in shared memory) */
     float best_ms;        /* its time on the sample batch */
     float default_ms;     /* the untuned heuristic's time */
 } lcp_tune_result_t;

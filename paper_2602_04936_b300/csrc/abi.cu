@@ -371,6 +371,7 @@ static int alloc_index(lcp_index_s* x, int64_t N, int64_t cap, cudaStream_t s) {
     x->st_levels_cap = lev;
     c.add(&x->st, (size_t)(lev > 0 ? lev : 1) * x->nblk_cap * x->K);
     c.add(&x->bkt, ((size_t)1 << x->bits) + 1);
+    c.add(&x->top, (size_t)lcpk::kTopLevels);
     // heavy-node tie lists: one table row per 128-row sample, one list per
     // node.  For max_k below kTieListMinK a tie fill from the sparse table
     // costs about as many loads as one from a list, so the lists (and their

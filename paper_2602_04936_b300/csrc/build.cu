@@ -501,6 +501,12 @@ __global__ void __launch_bounds__(kAuxThreads) k_aux_tree_blocks(AuxArgs a) {
     }
 }
 
+// The search's top levels: top[j] = head[j * n / T] for j < T.
+__global__ void k_top_sample(const uint64_t* __restrict__ head, int64_t n, int T, uint64_t* __restrict__ top) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < T) top[j] = head[(int64_t)j * n / T];
+}
+
 // Depth-1 buckets: bkt[t] = first sorted position whose first token is >= t,
 // for t in [0, 2^bits] (bkt[2^bits] = n): one binary search on head per token.
 __global__ void k_buckets(const uint64_t* __restrict__ head, int64_t n, int bits,
@@ -1001,6 +1007,10 @@ int build_aux(lcp_index_s* x, cudaStream_t s, bool merged) {
         LCP_TIMED_LAUNCH(k_inverse, blocks_for(N, 256), 256, 0, s2, b.ids, N, x->pos);
         LCP_TIMED_LAUNCH(k_buckets, blocks_for((1ll << x->bits) + 1, 256), 256, 0, s2, b.head, N, x->bits, x->bkt);
     }
+    {
+        const int T = (int)(N < kTopLevels ? N : kTopLevels);
+        LCP_TIMED_LAUNCH(k_top_sample, blocks_for(T, 256), 256, 0, s2, b.head, N, T, x->top);
+    }
     // min tree over H: level j+1 = minima of 32 consecutive level-j entries,
     // built while a level has more than 32 entries
     int64_t len = N;
@@ -1077,6 +1087,8 @@ DevIndex dev_view(const lcp_index_s* x) {
     d.st = x->st;
     d.st_stride = x->nblk_cap;
     d.bkt = x->bkt;
+    d.top = x->top;
+    d.top_n = (int)(x->N < kTopLevels ? x->N : kTopLevels);
     d.tbl = x->tbl;
     d.tlists = x->tlists;
     d.tlpos = x->tlpos;

@@ -26,6 +26,11 @@
 //                       tlpos[tbl[s][d]]; -1 otherwise.  Every trie node of
 //                       more than 128 rows contains a sample, so the indexed
 //                       search finds the level-d* list with one lookup.
+//   top  [T]      u64   the top levels of the sorted array for the search:
+//                       head at T evenly spaced positions j * N / T, T =
+//                       min(N, kTopLevels); staged in shared memory by the
+//                       staged locate, which narrows a query's range to about
+//                       N / T rows before touching L2.
 //   bkt_list [2^bits] i32  the list of each depth-1 bucket (-1 if light), so
 //                       that the common d* = 1 case reads bounds and list
 //                       number in one round trip.
@@ -39,6 +44,7 @@ constexpr int kBlk = 128;        // positions per tie-fill block
 constexpr int kMaxHLev = 7;      // min-tree levels above H (32^7 > 2^30)
 constexpr int kMaxStLev = 24;
 constexpr uint32_t kInf = 0xFFFFFFFFu;
+constexpr int kTopLevels = 4096;  // samples of the sorted array's heads (32 KB)
 
 struct DevIndex {
     int64_t N;
@@ -64,6 +70,8 @@ struct DevIndex {
     const uint32_t* tlists;
     const int32_t* tlpos;
     const int32_t* bkt_list;
+    const uint64_t* top;  // [top_n] heads at positions j * N / top_n
+    int top_n;
     int L1;  // L + 1: row length of tbl
     int* status;
 };
@@ -102,6 +110,7 @@ struct lcp_index_s {
     uint32_t* tlists = nullptr;    // [nlists_cap][K]
     int32_t* tlpos = nullptr;      // [nlists_cap][K] sorted position of each entry
     int32_t* bkt_list = nullptr;   // [2^bits] list of each depth-1 bucket
+    uint64_t* top = nullptr;       // [kTopLevels] sampled heads (the search's top levels)
     int32_t* tl_lo = nullptr;      // interval of each list
     int32_t* tl_hi = nullptr;
     uint64_t* tl_sums = nullptr;   // scan block sums

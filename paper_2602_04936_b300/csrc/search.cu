@@ -135,11 +135,11 @@ __device__ __forceinline__ int lane_cmp_from(const DevIndex& ix, const uint64_t*
 // before it are smaller than q, the rows after it larger).  Word 0 alone
 // decides everything unless some row shares it with q; then a binary search
 // inside that equal-head range compares the later words.
-__device__ __forceinline__ void lane_locate(const DevIndex& ix, const uint8_t* qrow, const RowFmt& qf,
-                                            uint64_t q0, int64_t* p_out, int* lL_out, int* lR_out) {
+// [lo, hi]: a range known to hold the first position whose head is >= q0.
+__device__ __forceinline__ void lane_locate_range(const DevIndex& ix, const uint8_t* qrow, const RowFmt& qf,
+                                                  uint64_t q0, int lo, int hi, int64_t* p_out, int* lL_out,
+                                                  int* lR_out) {
     const int N = (int)ix.N;  // positions are 32-bit: an index holds fewer than 2^30 rows
-    const uint32_t t0 = (uint32_t)(q0 >> (64 - ix.bits));
-    int lo = ix.bkt[t0], hi = ix.bkt[t0 + 1];
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (ix.head[mid] < q0) lo = mid + 1;
@@ -188,19 +188,89 @@ __device__ __forceinline__ void lane_locate(const DevIndex& ix, const uint8_t* q
     *lR_out = lR;
 }
 
+__device__ __forceinline__ void lane_locate(const DevIndex& ix, const uint8_t* qrow, const RowFmt& qf,
+                                            uint64_t q0, int64_t* p_out, int* lL_out, int* lR_out) {
+    const uint32_t t0 = (uint32_t)(q0 >> (64 - ix.bits));
+    lane_locate_range(ix, qrow, qf, q0, ix.bkt[t0], ix.bkt[t0 + 1], p_out, lL_out, lR_out);
+}
+
+// Word 0 of a query; the load asks L2 for 64 bytes, not the row.
+__device__ __forceinline__ uint64_t query_word0(const uint8_t* qrow, const RowFmt& qf) {
+    if (qf.aligned8) {
+        uint64_t q0;
+        asm("ld.global.nc.L2::64B.u64 %0, [%1];" : "=l"(q0) : "l"(qrow));
+        return msb_first(q0, qf.tb);
+    }
+    return pack_word(qrow, 0, qf);
+}
+
+// Lane per query with the top levels of the sorted array staged in shared
+// memory: the CTA bulk-copies the sampled heads top[j] = head[j * N / T]
+// (the TMA unit, one thread waiting with a bound), each lane binary-searches
+// there the samples inside q's first-token bucket -- heads below q0 at j < c,
+// so the first head >= q0 lies in (pos(c - 1), pos(c)] -- and finishes in L2
+// over at most about N / T rows of the bucket instead of all of it.
+constexpr int kStagedLocateThreads = 1024;
+
+__global__ void __launch_bounds__(kStagedLocateThreads) k_topk_locate_staged(DevIndex ix,
+                                                                            const uint8_t* __restrict__ queries,
+                                                                            RowFmt qf, int64_t Q,
+                                                                            QLoc* __restrict__ loc) {
+    extern __shared__ __align__(128) uint64_t top_s[];
+    __shared__ __align__(8) uint64_t tbar;
+    const int T = ix.top_n;
+    if (threadIdx.x == 0) {
+        mbar_init(&tbar, 1);
+        fence_proxy_async_smem();
+        const uint32_t bytes = (uint32_t)((T * 8 + 15) & ~15);  // the table is padded to 16 bytes
+        mbar_arrive_expect_tx(&tbar, bytes);
+        bulk_g2s(top_s, ix.top, bytes, &tbar);
+    }
+    const bool ok = threadIdx.x != 0 || mbar_wait(&tbar, 0, kSpinLimit);
+    if (__syncthreads_or(!ok)) {  // the copy never completed: report, let it land (bounded), leave
+        if (threadIdx.x == 0) {
+            flag_status(ix.status, DEV_TIMEOUT);
+            mbar_wait(&tbar, 0, kSpinLimit);
+        }
+        __syncthreads();
+        return;
+    }
+    const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= Q) return;
+    const uint8_t* qrow = row_of(queries, qi, qf);
+    const uint64_t q0 = query_word0(qrow, qf);
+    const uint32_t t0 = (uint32_t)(q0 >> (64 - ix.bits));
+    const int b0 = ix.bkt[t0], b1 = ix.bkt[t0 + 1];
+    const int N = (int)ix.N;
+    // c = number of sampled heads < q0: every sample before the bucket
+    // (positions < b0: first token smaller) and none from its end on
+    int c0 = (int)(((int64_t)b0 * T + N - 1) / N), c1 = (int)(((int64_t)b1 * T + N - 1) / N);
+    if (c1 > T) c1 = T;
+    while (c0 < c1) {
+        const int m = (c0 + c1) >> 1;
+        if (top_s[m] < q0) c0 = m + 1;
+        else c1 = m;
+    }
+    const int lo = c0 == 0 ? 0 : (int)((int64_t)(c0 - 1) * N / T) + 1;
+    const int hi = c0 == T ? N : (int)((int64_t)c0 * N / T);
+    int64_t p;
+    int lL, lR;
+    lane_locate_range(ix, qrow, qf, q0, max(lo, b0), min(hi, b1), &p, &lL, &lR);
+    QLoc r;
+    r.p = p;
+    r.lL = (int16_t)lL;
+    r.lR = (int16_t)lR;
+    r.tok0 = (int32_t)t0;
+    loc[qi] = r;
+}
+
 __global__ void __launch_bounds__(256) k_topk_locate(DevIndex ix, const uint8_t* __restrict__ queries,
                                                      RowFmt qf, int64_t Q, QLoc* __restrict__ loc) {
     const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (qi >= Q) return;
     const uint8_t* qrow = row_of(queries, qi, qf);
-    // word 0 alone decides most queries: ask L2 for 64 bytes, not the row
-    uint64_t q0;
-    if (qf.aligned8) {
-        asm("ld.global.nc.L2::64B.u64 %0, [%1];" : "=l"(q0) : "l"(qrow));
-        q0 = msb_first(q0, qf.tb);
-    } else {
-        q0 = pack_word(qrow, 0, qf);
-    }
+    // word 0 alone decides most queries
+    const uint64_t q0 = query_word0(qrow, qf);
     int64_t p;
     int lL, lR;
     lane_locate(ix, qrow, qf, q0, &p, &lL, &lR);
@@ -786,10 +856,15 @@ void set_search_shape(const lcp_index_s* x, int64_t Q, int k, const SearchShape&
 void launch_locate(const DevIndex& ix, const uint8_t* q, const RowFmt& qf, int64_t Q, QLoc* loc, cudaStream_t s,
                    int warp_mode) {
     if (warp_mode < 0) warp_mode = Q <= kWarpLocateMaxQ ? 1 : 0;
-    if (warp_mode)
+    if (warp_mode == 1) {
         LCP_TIMED_LAUNCH(k_topk_locate_warp, (unsigned)((Q + 7) / 8), 256, 0, s, ix, q, qf, Q, loc);
-    else
+    } else if (warp_mode == 2 && ix.top_n > 0) {
+        const size_t smem = (size_t)((ix.top_n * 8 + 15) & ~15);
+        LCP_TIMED_LAUNCH(k_topk_locate_staged, (unsigned)((Q + kStagedLocateThreads - 1) / kStagedLocateThreads),
+                         kStagedLocateThreads, smem, s, ix, q, qf, Q, loc);
+    } else {
         LCP_TIMED_LAUNCH(k_topk_locate, (unsigned)((Q + 255) / 256), 256, 0, s, ix, q, qf, Q, loc);
+    }
 }
 
 void launch_queue_worker(const QueueArgs& a, unsigned grid, cudaStream_t s) {

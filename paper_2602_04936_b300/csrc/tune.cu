@@ -48,7 +48,7 @@ int lcp_autotune(lcp_index_t x, const void* d_queries, int64_t Q, int32_t k, lcp
     float dflt = 0.f, top = 0.f;
     if (rc == LCP_OK) rc = time_shape(chosen, &dflt);
     top = dflt;
-    for (int lw = 0; lw < 2 && rc == LCP_OK; ++lw) {
+    for (int lw = 0; lw < 3 && rc == LCP_OK; ++lw) {  // lane, warp, lane over the staged top levels
         for (int qpw = 1; qpw <= 32 && rc == LCP_OK; qpw <<= 1) {
             lcph::SearchShape sh;
             sh.qpw = qpw;
@@ -87,7 +87,7 @@ int lcp_autotune(lcp_index_t x, const void* d_queries, int64_t Q, int32_t k, lcp
 }
 
 int lcp_set_search_shape(lcp_index_t x, int64_t Q, int32_t k, int32_t qpw, int32_t locate_warp) {
-    if (!x || Q < 1 || k < 1 || qpw < 0 || qpw > 32 || (locate_warp != 0 && locate_warp != 1) ||
+    if (!x || Q < 1 || k < 1 || qpw < 0 || qpw > 32 || locate_warp < 0 || locate_warp > 2 ||
         lcph::index_is_wide(x))
         return LCP_ERR_INVALID;
     lcph::SearchShape sh;

@@ -125,6 +125,7 @@ def test_small_cases_indexed_and_scan_match_oracle(lcp, N, L, tb, sigma, k):
     assert_same(indexed(lcp, S, Qs, k), want, "indexed")  # small batch: the fused kernel
     assert_same(indexed(lcp, S, Qs, k, shape=(1, 1)), want, "indexed, three kernels")
     assert_same(indexed(lcp, S, Qs, k, shape=(8, 0)), want, "indexed, three kernels, lane locate")
+    assert_same(indexed(lcp, S, Qs, k, shape=(4, 2)), want, "indexed, three kernels, staged top levels")
     assert_same(scan(lcp, S, Qs, k), want, "scan")
 
 
