@@ -172,16 +172,18 @@ LCP_API int lcp_topk_batch_host(lcp_index_t index, const void* h_queries, int64_
  * LCP of every query against all N rows, keeping per query the k best under
  * (LCP descending, id ascending).  Needs no index.
  * d_tokens [N, L], d_queries [Q, L] device memory in format fmt.
- * 1 <= k <= LCP_SCAN_MAX_K.  Batches of up to 160 queries take a threshold
- * selection (per-slice counts of rows by LCP give the k-th largest LCP d*, a
- * second pass collects the rows above d* and the first rows at d* by id);
- * larger batches are ordered by the queries' first words and keep, per
+ * 1 <= k <= LCP_SCAN_MAX_K.  Batches of up to 1,024 queries take a
+ * threshold selection: one read of each row's first 16 bytes counts, per
+ * query and 256-row granule, the rows of LCP >= 1..4 and lists the rows
+ * sharing the query's first tokens; d* (the k-th largest LCP) follows from
+ * the counts, and the answer comes from a list or from a walk of the few
+ * granules holding the rows above d* and the first rows at d* by id.
+ * Larger batches are ordered by the queries' first words and keep, per
  * thread and N-slice, the rows that can still be in the query's top k (a
  * log of up to k + 64 rows, compacted as it fills), then merge them.
  * Both return the same bytes.  Temporary device memory from the
- * stream-ordered allocator: about N * 8 + Q * (12 * k + 4 * S * (L + 1))
- * bytes for small batches (S = N-slices per query, about 64 warps per
- * multiprocessor over all (query group, slice) pairs, S <= 8192), and
+ * stream-ordered allocator: about N * 8 + Q * (8 * ceil(N / 256) + 65,536
+ * + 4 * (L + 3)) bytes for small batches, and
  * N * 8 + Q * (16 + S * ((k + 64) * 8 + 4)) bytes for larger ones (S <=
  * 2048 slices; plus 24 bytes a query past 4,096 queries for the sort).
  * ---------------------------------------------------------------------- */

@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]
-SOURCES = ["abi.cu", "sort.cu", "build.cu", "search.cu", "scan.cu", "insert.cu", "noalloc.cu", "tielists.cu", "session.cu", "graphstep.cu", "shard.cu", "variants.cu", "queue.cu", "tune.cu", "wide.cu"]
+SOURCES = ["abi.cu", "sort.cu", "build.cu", "search.cu", "scan.cu", "scan_select.cu", "insert.cu", "noalloc.cu", "tielists.cu", "session.cu", "graphstep.cu", "shard.cu", "variants.cu", "queue.cu", "tune.cu", "wide.cu"]
 
 
 def _nvcc():

@@ -711,6 +711,7 @@ int lcp_scan_topk(const void* d_tokens, int64_t N, lcp_format_t fmt, const void*
         return LCP_ERR_INVALID;
     if (Q > 0 && (!d_queries || !d_out_ids || !d_out_lcp)) return LCP_ERR_INVALID;
     if (N > 0 && Q > 0 && !d_tokens) return LCP_ERR_INVALID;
+    retain_pool_memory();  // per-call scratch comes from the pool: keep it mapped between calls
     int rc = scan_topk_device(d_tokens, N, fmt.token_bytes, fmt.L, d_queries, Q, k, d_out_ids,
                               d_out_lcp, (cudaStream_t)stream);
     if (rc == LCP_OK) {

@@ -30,7 +30,7 @@
 //                   the best shared level and, once k are held, above the k-th
 //                   are dropped as they are read; the rest are sorted in shared
 //                   memory.  Written to the query's own output row.
-// Smaller batches take the threshold selection further below.
+// Smaller batches take the threshold selection (scan_select.cu).
 #include "scan.cuh"
 #include "sort.cuh"
 
@@ -458,508 +458,10 @@ __global__ void k_u32_to_i32(const uint32_t* __restrict__ in, int64_t n, int32_t
     if (i < n) out[i] = (int32_t)in[i];
 }
 
-
-// ---- small batches: threshold selection ----
-//
-// With few queries the per-thread heaps above leave most of the GPU idle (one
-// thread per query and slice) and their merge dominates.  Such batches take
-// the answer from the LCP distribution instead: d* is the largest d with at
-// least k rows of LCP >= d (0 when N < k); every row with LCP > d* is in the
-// answer (nA < k of them), and the other kp = min(k - nA, #LCP-d* rows) slots
-// go to the rows of LCP exactly d* in ascending id order.
-//   k_sel_count    a warp per (query, slice of ids): rows with LCP >= d for
-//                  d = 1..L, per slice and (one atomic per CTA) in total; the
-//                  exact LCP is computed only for rows whose first token
-//                  matches the query's;
-//   k_sel_pick     a CTA per query: d*, nA, kp and, per slice, the LCP-d*
-//                  rows in the slices before it;
-//   k_sel_collect  a warp per (query, slice) walks only slices that hold
-//                  answer rows, and stops once it has found them: LCP > d*
-//                  into unordered slots, LCP-d* rows at their rank; the
-//                  query's last CTA to finish sorts the nA keys and writes
-//                  A, the tie rows, then padding.
-
-constexpr int kSelWarps = 8;
-constexpr int kSelGroup = 4;       // queries per warp in the count pass (batches of > 1)
-constexpr int kSelGroupWarps = 4;  // warps per CTA of that count pass
-constexpr int kSelBins = 16;
-constexpr int kSelMaxS = 8192;  // slices per query at most  // LCPs below this are counted per lane, larger ones by shared atomics
-constexpr int kMaxScanW = (LCP_MAX_L + 3) / 4;  // packed words of the longest uint16 row
-
-struct SelArgs {
-    const uint8_t* tokens;
-    const uint32_t* plane_hi;  // packed word 0 of every row (upper halves), or null: read from the tokens
-    const uint32_t* plane_lo;  // (lower halves)
-    RowFmt f;
-    int64_t N;
-    const uint8_t* queries;
-    RowFmt qf;
-    int64_t Q;
-    int k;
-    int S;              // slices per query
-    int64_t slice;      // rows per slice (the last may be shorter)
-    uint32_t* ge;       // [Q][L][S]: rows of slice s with LCP >= d, d = 1..L (zeroed first)
-    uint32_t* tot;      // [Q][L]: the same over all rows (zeroed before k_sel_count)
-    int32_t* meta;      // [Q][8]: d*, nA, kp, the A slot counter, the collect pass's CTA ticket
-    uint32_t* tie_lo;   // [Q][S]: LCP-d* rows in the slices before this one
-    uint64_t* abuf;     // [Q][k]: keys (255 - LCP) << 32 | id of the rows with LCP > d*
-    int32_t* tbuf;      // [Q][k]: ids of the first kp rows of LCP d*
-};
-
-__device__ __forceinline__ uint64_t sel_word0(const SelArgs& a, int64_t t) {
-    return a.plane_hi ? ((uint64_t)a.plane_hi[t] << 32) | a.plane_lo[t] : row_word0(row_of(a.tokens, t, a.f), a.f);
-}
-
-// Exact LCP of row t with the query, given x = word0(t) ^ q0 (qw: the
-// query's packed words).
-__device__ __forceinline__ int sel_lcp(const SelArgs& a, int64_t t, uint64_t x, const uint64_t* qw) {
-    const RowFmt& f = a.f;
-    if (x) return lcp_at(0, x, f);
-    const uint8_t* row = row_of(a.tokens, t, f);
-    if (f.aligned8) {  // four words per round trip rather than one
-        const unsigned long long* rw = reinterpret_cast<const unsigned long long*>(row);
-        for (int w0 = 1; w0 < f.W; w0 += 4) {
-            uint64_t v[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) v[j] = w0 + j < f.W ? __ldg(rw + w0 + j) : 0ull;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint64_t y = w0 + j < f.W ? msb_first(v[j], f.tb) ^ qw[w0 + j] : 0ull;
-                if (y) return lcp_at(w0 + j, y, f);
-            }
-        }
-        return f.L;
-    }
-    for (int w = 1; w < f.W; ++w) {
-        const uint64_t y = pack_word(row, w, f) ^ qw[w];
-        if (y) return lcp_at(w, y, f);
-    }
-    return f.L;
-}
-
-__device__ __forceinline__ void sel_slice(const SelArgs& a, int s, int64_t* s0, int64_t* s1) {
-    *s0 = (int64_t)s * a.slice;
-    const int64_t e = *s0 + a.slice;
-    *s1 = e < a.N ? e : a.N;
-}
-
-// G queries per warp: each row word is loaded once and tested against each
-// of them (G = 1 for a lone query, whose rows are read straight from the
-// tokens; G = 4 on the packed plane otherwise).  NW warps per CTA, a warp per
-// slice; lane counters are 16-bit (a lane meets at most slice / 32 rows).
-template <int G, int NW>
-__global__ void __launch_bounds__(NW * 32) k_sel_count(SelArgs a) {
-    __shared__ uint64_t qw[G][kMaxScanW];
-    __shared__ uint32_t hist[G][NW][LCP_MAX_L + 1];
-    __shared__ uint16_t lanecnt[G][NW][kSelBins][32];  // [l][lane]: no bank conflicts between lanes
-    const int64_t qb = (int64_t)blockIdx.y * G;
-    const int ng = a.Q - qb < G ? (int)(a.Q - qb) : G;
-    const unsigned lane = lane_id();
-    const int warp = threadIdx.x >> 5;
-    const int L = a.f.L;
-    for (int g = 0; g < ng; ++g) {
-        const uint8_t* qrow = row_of(a.queries, qb + g, a.qf);
-        for (int w = threadIdx.x; w < a.f.W; w += blockDim.x) qw[g][w] = pack_word(qrow, w, a.qf);
-    }
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-        for (int d = (int)lane; d <= L; d += 32) hist[g][warp][d] = 0;
-#pragma unroll
-        for (int d = 0; d < kSelBins; ++d) lanecnt[g][warp][d][lane] = 0;
-    }
-    __syncthreads();
-    const int s = blockIdx.x * NW + warp;
-    if (s < a.S) {
-        int64_t s0, s1;
-        sel_slice(a, s, &s0, &s1);
-        uint64_t q0[G];
-        uint32_t qh[G];
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            q0[g] = g < ng ? qw[g][0] : 0ull;
-            qh[g] = (uint32_t)(q0[g] >> 32);
-        }
-        // (word 0 ^ q0) >> 32 below lim1: the first token agrees (LCP >= 1),
-        // below lim2: the first two do (LCP >= 2; rare).  Rows of LCP >= 1
-        // are counted per lane in a register; only rows of LCP >= 2 take the
-        // exact LCP and a level counter.
-        const uint32_t lim1 = 1u << (32 - a.f.bits);
-        const uint32_t lim2 = 1u << (32 - 2 * a.f.bits);
-        uint32_t c1[G];
-#pragma unroll
-        for (int g = 0; g < G; ++g) c1[g] = 0;
-        // 128 rows per step; the next step's words are loaded before this
-        // step's are tested (rows past the slice get a word no query shares)
-        uint64_t r[4], nx[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t t = s0 + u * 32 + lane;
-            r[u] = t < s1 ? sel_word0(a, t) : ~q0[0];
-        }
-        for (int64_t b = s0; b < s1; b += 128) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t t = b + 128 + u * 32 + lane;
-                nx[u] = t < s1 ? sel_word0(a, t) : ~q0[0];
-            }
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                if (g >= ng) break;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int64_t t = b + u * 32 + lane;
-                    const uint32_t xh = (uint32_t)(r[u] >> 32) ^ qh[g];
-                    const bool in = t < s1;
-                    c1[g] += (in && xh < lim1) ? 1u : 0u;
-                    const bool deep = in && xh < lim2;
-                    if (!__any_sync(0xffffffffu, deep)) continue;
-                    if (deep) {
-                        const int l = sel_lcp(a, t, r[u] ^ q0[g], qw[g]);  // >= 2
-                        if (l < kSelBins) lanecnt[g][warp][l][lane] += 1;
-                        else atomicAdd(&hist[g][warp][l], 1u);
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) r[u] = nx[u];
-        }
-        __syncwarp();
-        for (int g = 0; g < ng; ++g) {
-            uint32_t* h = hist[g][warp];
-            uint32_t deep = 0;  // rows of LCP >= 2 (lane 0's sum)
-            for (int d = 2; d < kSelBins && d <= L; ++d) {
-                const uint32_t v = __reduce_add_sync(0xffffffffu, (uint32_t)lanecnt[g][warp][d][lane]);
-                if (lane == 0) h[d] += v;
-            }
-            __syncwarp();
-            for (int d = 2 + (int)lane; d <= L; d += 32) deep += h[d];
-            deep = __reduce_add_sync(0xffffffffu, deep);
-            const uint32_t ones = __reduce_add_sync(0xffffffffu, c1[g]);
-            if (lane == 0 && L >= 1) h[1] = ones - deep;  // rows of LCP exactly 1
-            __syncwarp();
-            // suffix sums (rows with LCP >= d), from d = L down to 1, stored
-            // per slice where nonzero and kept in h for the CTA's total
-            uint32_t* out = a.ge + (size_t)(qb + g) * L * a.S + s;
-            uint32_t carry = 0;
-            for (int c = ((L - 1) / 32) * 32 + 1; c >= 1; c -= 32) {
-                const int d = c + (int)lane;
-                uint32_t v = d <= L ? h[d] : 0u;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_down_sync(0xffffffffu, v, o);
-                    if ((int)lane + o < 32) v += y;
-                }
-                v += carry;
-                __syncwarp();
-                if (d <= L) {
-                    if (v) out[(size_t)(d - 1) * a.S] = v;
-                    h[d] = v;
-                }
-                carry = __shfl_sync(0xffffffffu, v, 0);
-            }
-        }
-    }
-    __syncthreads();
-    for (int g = 0; g < ng; ++g) {
-        for (int d = threadIdx.x + 1; d <= L; d += blockDim.x) {
-            uint32_t v = 0;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) v += hist[g][w][d];
-            if (v) atomicAdd(a.tot + (size_t)(qb + g) * L + (d - 1), v);
-        }
-    }
-}
-
-__global__ void __launch_bounds__(1024) k_sel_pick(SelArgs a) {
-    __shared__ uint32_t wsum[32];
-    __shared__ uint32_t tie[kSelMaxS];  // LCP-d* rows per slice, then their exclusive prefix
-    const int64_t q = blockIdx.x;
-    const int L = a.f.L, S = a.S;
-    const unsigned lane = lane_id();
-    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const uint32_t* tot = a.tot + (size_t)q * L;
-    // the counts fall with d, so d* is the number of d in 1..L reaching k
-    const int dstar = __syncthreads_count((int)threadIdx.x < L && tot[threadIdx.x] >= (uint32_t)a.k);
-    const uint32_t nA = dstar < L ? tot[dstar] : 0u;
-    const uint32_t atd = dstar == 0 ? (uint32_t)a.N : tot[dstar - 1];
-    const uint32_t kp = min((uint32_t)a.k - nA, atd - nA);
-    const uint32_t* g = a.ge + (size_t)q * L * S;  // level-major: these reads are contiguous
-    {
-        // S <= kSelMaxS = 8 x 1024: each thread's loads issued together
-        uint32_t hv[kSelMaxS / 1024], lv[kSelMaxS / 1024];
-#pragma unroll
-        for (int i = 0; i < kSelMaxS / 1024; ++i) {
-            const int s = (int)threadIdx.x + i * 1024;
-            hv[i] = s < S && dstar > 0 ? g[(size_t)(dstar - 1) * S + s] : 0u;
-            lv[i] = s < S && dstar < L ? g[(size_t)dstar * S + s] : 0u;
-        }
-#pragma unroll
-        for (int i = 0; i < kSelMaxS / 1024; ++i) {
-            const int s = (int)threadIdx.x + i * 1024;
-            if (s >= S) break;
-            int64_t s0, s1;
-            sel_slice(a, s, &s0, &s1);
-            tie[s] = (dstar == 0 ? (uint32_t)(s1 - s0) : hv[i]) - lv[i];
-        }
-    }
-    __syncthreads();
-    const int per = (S + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int sb = (int)threadIdx.x * per;
-    const int se = sb + per < S ? sb + per : S;
-    uint32_t sum = 0;
-    for (int s = sb; s < se; ++s) sum += tie[s];
-    uint32_t v = sum;  // inclusive scan over the block
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= (unsigned)o) v += y;
-    }
-    if (lane == 31) wsum[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = (int)lane < nwarps ? wsum[lane] : 0u;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= (unsigned)o) w += y;
-        }
-        wsum[lane] = w;
-    }
-    __syncthreads();
-    uint32_t run = v - sum + (warp > 0 ? wsum[warp - 1] : 0u);
-    for (int s = sb; s < se; ++s) {
-        const uint32_t t = tie[s];
-        tie[s] = run;
-        run += t;
-    }
-    __syncthreads();
-    for (int s = threadIdx.x; s < S; s += blockDim.x) a.tie_lo[(size_t)q * S + s] = tie[s];
-    if (threadIdx.x == 0) {
-        int32_t* m = a.meta + q * 8;
-        m[0] = dstar;
-        m[1] = (int32_t)nA;
-        m[2] = (int32_t)kp;
-        m[3] = 0;
-        m[4] = 0;
-    }
-}
-
-// Query q's output: the nA keys of A sorted (by a CTA, in keys[]), then the
-// tie rows, then padding.
-__device__ void sel_write(const SelArgs& a, int64_t q, uint64_t* keys, int32_t* __restrict__ out_ids,
-                          uint8_t* __restrict__ out_lcp) {
-    const int k = a.k;
-    const int32_t* m = a.meta + q * 8;
-    const int dstar = m[0], nA = m[1], kp = m[2];
-    int P = 1;
-    while (P < nA) P <<= 1;
-    const uint64_t* abuf = a.abuf + q * k;
-    for (int t = threadIdx.x; t < P; t += blockDim.x) keys[t] = t < nA ? abuf[t] : kKeyInf;
-    __syncthreads();
-    for (int size = 2; size <= P; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = threadIdx.x; t < P; t += blockDim.x) {
-                const int u = t ^ stride;
-                if (u > t) {
-                    const uint64_t x = keys[t], y = keys[u];
-                    if ((x > y) == ((t & size) == 0)) {
-                        keys[t] = y;
-                        keys[u] = x;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    const int32_t* tbuf = a.tbuf + q * k;
-    for (int j = threadIdx.x; j < k; j += blockDim.x) {
-        int32_t id = -1;
-        int l = 0;
-        if (j < nA) {
-            const uint64_t v = keys[j];
-            id = (int32_t)(uint32_t)v;
-            l = 255 - (int)(v >> 32);
-        } else if (j < nA + kp) {
-            id = tbuf[j - nA];
-            l = dstar;
-        }
-        out_ids[q * k + j] = id;
-        out_lcp[q * k + j] = (uint8_t)l;
-    }
-}
-
-__global__ void __launch_bounds__(kSelWarps * 32) k_sel_collect(SelArgs a, int32_t* __restrict__ out_ids,
-                                                                uint8_t* __restrict__ out_lcp) {
-    __shared__ uint64_t qw[kMaxScanW];
-    __shared__ uint64_t keys[LCP_SCAN_MAX_K];
-    __shared__ int last;
-    const int64_t q = blockIdx.y;
-    const unsigned lane = lane_id();
-    const unsigned lt = lanemask_lt();
-    const int warp = threadIdx.x >> 5;
-    const int L = a.f.L;
-    const uint8_t* qrow = row_of(a.queries, q, a.qf);
-    for (int w = threadIdx.x; w < a.f.W; w += blockDim.x) qw[w] = pack_word(qrow, w, a.qf);
-    __syncthreads();
-    const int s = blockIdx.x * kSelWarps + warp;
-    if (s < a.S) {
-        int32_t* m = a.meta + q * 8;
-        const int dstar = m[0], kp = m[2];
-        int64_t s0, s1;
-        sel_slice(a, s, &s0, &s1);
-        const uint32_t* g = a.ge + (size_t)q * L * a.S + s;
-        const uint32_t atd = dstar == 0 ? (uint32_t)(s1 - s0) : g[(size_t)(dstar - 1) * a.S];
-        uint32_t a_left = dstar < L ? g[(size_t)dstar * a.S] : 0u;  // rows of LCP > d* not yet met
-        const uint32_t tlo = a.tie_lo[(size_t)q * a.S + s];
-        const uint32_t ties_s = atd - a_left;
-        const uint32_t t_need = (uint32_t)kp > tlo ? min(ties_s, (uint32_t)kp - tlo) : 0u;
-        const uint64_t q0 = qw[0];
-        const uint64_t first = ~0ull >> a.f.bits;
-        // rows whose first min(d*, tpw) tokens match (all rows when d* = 0)
-        const int dm = dstar < a.f.tpw ? dstar : a.f.tpw;
-        const uint64_t mask = prefix_mask(dm, a.f.bits);
-        uint64_t* abuf = a.abuf + q * a.k;
-        int32_t* tbuf = a.tbuf + q * a.k;
-        uint32_t seen = 0;  // LCP-d* rows of this slice met so far
-        // 128 rows per step, the next step's words loaded before this step's
-        // are tested (rows of a step in ascending id, as the ranks need)
-        uint64_t r[4], nx[4];
-    #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t t = s0 + u * 32 + lane;
-            r[u] = t < s1 ? sel_word0(a, t) : 0ull;
-        }
-        for (int64_t b = s0; b < s1 && (a_left > 0 || seen < t_need); b += 128) {
-    #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t t = b + 128 + u * 32 + lane;
-                nx[u] = t < s1 ? sel_word0(a, t) : 0ull;
-            }
-    #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (!(a_left > 0 || seen < t_need)) break;  // warp-uniform
-                const int64_t t = b + u * 32 + lane;
-                const bool in = t < s1;
-                const uint64_t x = r[u] ^ q0;
-                const bool cand = in && (x & mask) == 0;
-                if (!__any_sync(0xffffffffu, cand)) continue;
-                const int l = cand && x <= first ? sel_lcp(a, t, x, qw) : 0;
-                const bool isA = cand && l > dstar;
-                const bool isT = cand && l == dstar;
-                const unsigned mA = __ballot_sync(0xffffffffu, isA);
-                if (mA) {
-                    uint32_t base = 0;
-                    if (lane == 0) base = atomicAdd(reinterpret_cast<uint32_t*>(m + 3), (uint32_t)__popc(mA));
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    const uint32_t slot = base + (uint32_t)__popc(mA & lt);
-                    if (isA && slot < (uint32_t)a.k) abuf[slot] = ((uint64_t)(255 - l) << 32) | (uint64_t)t;
-                    const uint32_t na = (uint32_t)__popc(mA);
-                    a_left = a_left > na ? a_left - na : 0u;
-                }
-                const unsigned mT = __ballot_sync(0xffffffffu, isT);
-                if (isT) {
-                    const uint32_t rank = tlo + seen + (uint32_t)__popc(mT & lt);
-                    if (rank < (uint32_t)kp) tbuf[rank] = (int32_t)t;
-                }
-                seen += (uint32_t)__popc(mT);
-            }
-    #pragma unroll
-            for (int u = 0; u < 4; ++u) r[u] = nx[u];
-        }
-    }
-    // the CTA that finishes the query's collect pass last (every CTA's
-    // writes fenced before its ticket) sorts A and writes the output
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0)
-        last = atomicAdd(reinterpret_cast<unsigned*>(a.meta + q * 8 + 4), 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    sel_write(a, q, keys, out_ids, out_lcp);
-}
-
 }  // namespace lcpk
 
 namespace lcph {
 using namespace lcpk;
-
-// Batches up to this size take the threshold selection, larger ones the
-// per-thread logs over the batch sorted by first word (measured on 2M rows of
-// 64 uint16 tokens, k = 100: selection 0.52 ms at 128 queries against 1.07
-// for the logs, 0.64 against ~1.1 at 160, the logs ahead at 256: 1.25
-// against ~1.3).
-constexpr int64_t kSelMaxQ = 160;
-
-static int scan_select(const void* d_tokens, int64_t N, const RowFmt& f, const void* d_queries,
-                       const RowFmt& qf, int64_t Q, int k, int32_t* d_out_ids, uint8_t* d_out_lcp,
-                       cudaStream_t s) {
-    const int L = f.L;
-    // about 64 warps per SM over all (query, slice) pairs (two waves, so
-    // that slices with long walks in the collect pass even out), whole CTAs
-    // of slices, slices of >= 256 rows
-    // the count pass tests kSelGroup queries per warp (one for a lone query)
-    const int G = Q == 1 ? 1 : kSelGroup;
-    const int64_t groups = (Q + G - 1) / G;
-    const int64_t target = (int64_t)sm_count() * 64;
-    int64_t S = (target + groups - 1) / groups;
-    S = (S + kSelWarps - 1) / kSelWarps * kSelWarps;
-    const int64_t maxS = (N + 255) / 256;
-    if (S > maxS) S = maxS;
-    if (S > kSelMaxS) S = kSelMaxS;
-    const int64_t minS = (N + (32ll << 16) - 1) >> 21;  // slices of < 2M rows: 16-bit lane counters
-    if (S < minS) S = minS;
-    if (S < 1) S = 1;
-    const int64_t slice = (N + S - 1) / S;
-    S = (N + slice - 1) / slice;
-    const bool plane = Q > 1;  // several queries re-read word 0: pack it once
-    SelArgs a;
-    a.tokens = reinterpret_cast<const uint8_t*>(d_tokens);
-    a.plane_hi = a.plane_lo = nullptr;
-    a.f = f;
-    a.N = N;
-    a.queries = reinterpret_cast<const uint8_t*>(d_queries);
-    a.qf = qf;
-    a.Q = Q;
-    a.k = k;
-    a.S = (int)S;
-    a.slice = slice;
-    uint32_t *plane_hi = nullptr, *plane_lo = nullptr;
-    Carver cv;
-    if (plane) {
-        cv.add(&plane_hi, (size_t)N);
-        cv.add(&plane_lo, (size_t)N);
-    }
-    cv.add(&a.ge, (size_t)Q * S * L);
-    cv.add(&a.tot, (size_t)Q * L);
-    cv.add(&a.meta, (size_t)Q * 8);
-    cv.add(&a.tie_lo, (size_t)Q * S);
-    cv.add(&a.abuf, (size_t)Q * k);
-    cv.add(&a.tbuf, (size_t)Q * k);
-    void* base = nullptr;
-    LCP_CUDA_TRY(cv.alloc(&base, s));
-    a.plane_hi = plane_hi;
-    a.plane_lo = plane_lo;
-    // the per-slice counts and the totals are adjacent: one memset zeroes both
-    cudaError_t e = cudaMemsetAsync(a.ge, 0, (size_t)((char*)(a.tot + (size_t)Q * L) - (char*)a.ge), s);
-    if (e != cudaSuccess) {
-        cudaFreeAsync(base, s);
-        return cuda_status(e);
-    }
-    if (plane)
-        LCP_TIMED_LAUNCH(k_pack_plane0, (unsigned)((N + 255) / 256), 256, 0, s, a.tokens, f, N, plane_hi, plane_lo);
-    const dim3 grid((unsigned)((S + kSelWarps - 1) / kSelWarps), (unsigned)Q);
-    if (G == 1)
-        LCP_TIMED_LAUNCH((k_sel_count<1, kSelWarps>), grid, kSelWarps * 32, 0, s, a);
-    else
-        LCP_TIMED_LAUNCH((k_sel_count<kSelGroup, kSelGroupWarps>),
-                         dim3((unsigned)((S + kSelGroupWarps - 1) / kSelGroupWarps), (unsigned)groups),
-                         kSelGroupWarps * 32, 0, s, a);
-    LCP_TIMED_LAUNCH(k_sel_pick, (unsigned)Q, 1024, 0, s, a);
-    LCP_TIMED_LAUNCH(k_sel_collect, grid, kSelWarps * 32, 0, s, a, d_out_ids, d_out_lcp);
-    e = cudaFreeAsync(base, s);
-    return e == cudaSuccess ? LCP_OK : cuda_status(e);
-}
 
 // Larger batches: per-thread logs over N-slices, the batch ordered by the
 // queries' first words (so that a warp's 32 queries are neighbours and its

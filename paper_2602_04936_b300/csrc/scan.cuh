@@ -64,3 +64,15 @@ __global__ void k_scan_merge(const uint64_t* __restrict__ lists, const int32_t* 
                              int32_t* __restrict__ out_ids, uint8_t* __restrict__ out_lcp);
 
 }  // namespace lcpk
+
+namespace lcph {
+
+// Batches up to this size take the threshold selection (scan_select.cu),
+// larger ones the per-thread logs (scan.cu).
+constexpr int64_t kSelMaxQ = 1024;
+
+// Full scan of a batch of at most kSelMaxQ queries by threshold selection.
+int scan_select(const void* d_tokens, int64_t N, const lcpk::RowFmt& f, const void* d_queries,
+                const lcpk::RowFmt& qf, int64_t Q, int k, int32_t* d_out_ids, uint8_t* d_out_lcp, cudaStream_t s);
+
+}  // namespace lcph

@@ -195,9 +195,9 @@ def test_tree16_u8_full(lcp):
                                              (300, 5, 1, 2, 1000)])     # k > N
 def test_scan_batch_paths_agree(lcp, N, L, tb, sigma, k):
     """Full scan: one batch of 8,200 queries (per-thread logs), the same
-    queries in batches of 410 (threshold selection, batches <= 512) and one
-    query at a time (word 0 read straight from the rows) give the same bytes,
-    and match the oracle on a sample."""
+    queries in batches of 410 (threshold selection, batches <= 1,024) and one
+    query at a time (the walk reads word 0 straight from the rows) give the
+    same bytes, and match the oracle on a sample."""
     rng = np.random.default_rng(N * 13 + L * 5 + k)
     dt = np.uint8 if tb == 1 else np.uint16
     S = _prefixy(rng, N, L, sigma, dt)
@@ -212,6 +212,38 @@ def test_scan_batch_paths_agree(lcp, N, L, tb, sigma, k):
     for j in range(8):
         i = pick[j]
         assert_same(scan(lcp, S, Qs[i:i + 1], k), (want[0][j:j + 1], want[1][j:j + 1]), "scan, one query")
+
+
+@pytest.mark.parametrize("Q,L,tb", [(1, 16, 2), (5, 16, 2), (33, 16, 2), (70, 32, 2), (257, 16, 1),
+                                     (40, 12, 2), (3, 8, 2), (64, 16, 1)])
+def test_scan_selection_batch_shapes(lcp, Q, L, tb):
+    """Threshold selection at batch sizes that split a count CTA's 8 warps
+    differently: one chunk of 32 queries over 8 row parts (Q <= 32), 3 chunks
+    over 2 parts (70), more chunks than warps (257); rows fed by tensor copies
+    (16-byte multiples) or by plain loads (24-byte rows); granules ragged at
+    the end (N not a multiple of 256)."""
+    rng = np.random.default_rng(Q * 7 + L + tb)
+    dt = np.uint8 if tb == 1 else np.uint16
+    S = _prefixy(rng, 30011, L, 4, dt)
+    Qs = _queries(rng, S, Q, 4, dt)
+    for k in (1, 50, 300):
+        assert_same(scan(lcp, S, Qs, k), oracle.topk_batch(S, Qs, k), "scan Q=%d k=%d" % (Q, k))
+
+
+def test_scan_shared_prefix_beyond_list(lcp):
+    """More rows share a query's first 8 tokens than the selection keeps per
+    query (6,000 of 9,000 rows): the exact pass over all rows in id order;
+    beside it queries answered from the list and by the walk."""
+    rng = np.random.default_rng(77)
+    S = rng.integers(0, 3, size=(9000, 16)).astype(np.uint16)
+    S[:6000, :8] = 5
+    Qs = rng.integers(0, 3, size=(6, 16)).astype(np.uint16)
+    Qs[:3, :8] = 5
+    Qs[1, 8:] = S[4321, 8:]
+    Qs[3] = S[8500]
+    for k in (1, 10, 100, 1000):
+        assert_same(scan(lcp, S, Qs, k), oracle.topk_batch(S, Qs, k), "scan shared prefix k=%d" % k)
+        assert_same(scan(lcp, S, Qs[1:2], k), oracle.topk_batch(S, Qs[1:2], k), "one query k=%d" % k)
 
 
 def test_index_past_2_pow_24_rows(lcp):
