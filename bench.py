@@ -424,8 +424,12 @@ def scan_hbm_model(Q, N, W, k, ms, peak):
     measured copy bandwidth.  It binds small batches; large ones are bound by
     the L2 stream of the word-0 plane (scan_stream_model)."""
     b = N * W * 8 + Q * W * 8 + Q * k * 5
+    # what the threshold selection fetches: each row's first 16 bytes, which
+    # DRAM serves as one 64-byte fetch (the tensor copies' L2 promotion)
+    f = N * 64 + Q * W * 8 + Q * k * 5
     return {"bytes": int(b), "achieved_gbs": round(b / (ms / 1e3) / 1e9, 1), "peak_gbs": peak,
-            "frac": round(b / (ms / 1e3) / 1e9 / peak, 4)}
+            "frac": round(b / (ms / 1e3) / 1e9 / peak, 4),
+            "fetch_bytes": int(f), "fetch_frac": round(f / (ms / 1e3) / 1e9 / peak, 4)}
 
 
 def scan_stream_model(Q, N, ms, threads=256, sample=65536):
