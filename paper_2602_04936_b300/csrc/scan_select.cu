@@ -9,7 +9,7 @@
 //
 //   k_sel_count  the rows pass through shared memory in tiles of 256, each
 //                row's first 16 bytes brought by a 2D bulk tensor copy (the
-//                TMA unit; a 3-tile ring per warp, 64-byte L2 promotion), so
+//                TMA unit; a 2-tile ring per warp, 64-byte L2 promotion), so
 //                that the rows are read once for the whole batch.  A lane
 //                per query counts, per tile (a "granule"), the rows of LCP
 //                >= 1, 2, 3, 4 -- word 0 decides these -- and computes the
