@@ -320,6 +320,45 @@ __device__ __forceinline__ void head_bounds(const DevIndex& ix, int b0, int b1, 
     const int lane = (int)lane_id();
     int lo[2] = {b0, fromR}, hi[2] = {fromL, b1};
     bool done[2] = {!needL || b0 >= fromL, !needR || fromR >= b1};
+    {  // galloping round (runs are usually far shorter than the bucket): lane i
+       // probes 2^i positions out from the known part, bracketing each end
+        uint64_t h[2] = {0ull, 0ull};
+        int x[2];
+        x[0] = max(fromL - (1 << lane), b0);
+        { const long long xr = (long long)fromR + (1ll << lane) - 1; x[1] = (int)(xr < (long long)b1 - 1 ? xr : (long long)b1 - 1); }
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd)
+            if (!done[sd]) h[sd] = ix.head[x[sd]];
+        if (!done[0]) {  // rows at and right of the answer satisfy: the first lane that fails
+            const unsigned m = __ballot_sync(0xffffffffu, (h[0] & mask) >= key);
+            const unsigned fail = ~m;
+            const int j = __ffs(fail) - 1;  // lanes past x = b0 repeat b0's answer
+            if (!fail) {
+                hi[0] = b0;
+                done[0] = true;
+            } else {
+                const int xj = __shfl_sync(0xffffffffu, x[0], j);
+                const int xp = j == 0 ? fromL : __shfl_sync(0xffffffffu, x[0], j - 1 < 0 ? 0 : j - 1);
+                lo[0] = xj + 1;
+                hi[0] = xp;
+                if (lo[0] >= hi[0]) done[0] = true;
+            }
+        }
+        if (!done[1]) {  // the first row past the run: the first lane that passes
+            const unsigned m = __ballot_sync(0xffffffffu, (h[1] & mask) > key);
+            if (!m) {
+                hi[1] = b1;
+                done[1] = true;
+            } else {
+                const int j = __ffs(m) - 1;
+                const int xj = __shfl_sync(0xffffffffu, x[1], j);
+                const int xp = j == 0 ? fromR - 1 : __shfl_sync(0xffffffffu, x[1], j - 1 < 0 ? 0 : j - 1);
+                lo[1] = xp + 1;
+                hi[1] = xj;
+                if (lo[1] >= hi[1]) done[1] = true;
+            }
+        }
+    }
     while (!(done[0] && done[1])) {  // warp-uniform
         int st[2], x[2];
         uint64_t h[2] = {0ull, 0ull};
