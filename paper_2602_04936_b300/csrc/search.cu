@@ -37,24 +37,24 @@ namespace lcpk {
 
 // ---- expansion chunk loads ----
 
-// Loads up to 32 items on one side starting `n` items away from p; returns
-// the count.  Left: positions p-1-n-lane; right: positions p+n+lane.
+// Loads the adjacent LCPs of up to 32 items on one side starting `n` items
+// away from p (left: positions p-1-n-lane; right: positions p+n+lane).  Only
+// LCPs: the ids of the few items that reach A are loaded when A is written.
 template <bool LEFT>
 __device__ __forceinline__ void issue_chunk(const DevIndex& ix, int p, int n, int avail, int l0,
-                                            int& h, uint32_t& id, bool& ok) {
+                                            int& h, bool& ok) {
     const int lane = (int)lane_id();
     ok = n + lane < avail;
     h = 255;
-    id = 0;
     if (ok) {
         const int x = LEFT ? p - 1 - n - lane : p + n + lane;
         h = (n == 0 && lane == 0) ? l0 : (int)ix.H[LEFT ? x + 1 : x];
-        id = (uint32_t)ix.ids[x];
     }
 }
 
-__device__ __forceinline__ int finish_chunk(int& h, uint32_t id, bool ok, int n, int avail,
-                                            uint32_t* ids, uint8_t* lam) {
+// The items' LCPs with q (running minimum of H outward from p) into lam;
+// returns the count.
+__device__ __forceinline__ int finish_chunk(int& h, bool ok, int n, int avail, uint8_t* lam) {
     const unsigned lane = lane_id();
     if (n > 0) h = min(h, (int)lam[n - 1]);
 #pragma unroll
@@ -62,10 +62,7 @@ __device__ __forceinline__ int finish_chunk(int& h, uint32_t id, bool ok, int n,
         int y = __shfl_up_sync(0xffffffffu, h, o);
         if (lane >= (unsigned)o) h = min(h, y);
     }
-    if (ok) {
-        ids[n + lane] = id;
-        lam[n + lane] = (uint8_t)h;
-    }
+    if (ok) lam[n + lane] = (uint8_t)h;
     __syncwarp();
     return avail - n < 32 ? avail - n : 32;
 }
@@ -376,23 +373,22 @@ __device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, WA& S, int p,
     int vL0, vL1, vR0, vR1;
     {
         int hl, hr, hl2, hr2;
-        uint32_t il, ir, il2, ir2;
         bool okl, okr, okl2, okr2;
-        issue_chunk<true>(ix, p, 0, availL, lL, hl, il, okl);
-        issue_chunk<false>(ix, p, 0, availR, lR, hr, ir, okr);
-        issue_chunk<true>(ix, p, 32, availL, lL, hl2, il2, okl2);
-        issue_chunk<false>(ix, p, 32, availR, lR, hr2, ir2, okr2);
-        nL += finish_chunk(hl, il, okl, 0, availL, S.lid, S.llam);
-        nR += finish_chunk(hr, ir, okr, 0, availR, S.rid, S.rlam);
+        issue_chunk<true>(ix, p, 0, availL, lL, hl, okl);
+        issue_chunk<false>(ix, p, 0, availR, lR, hr, okr);
+        issue_chunk<true>(ix, p, 32, availL, lL, hl2, okl2);
+        issue_chunk<false>(ix, p, 32, availR, lR, hr2, okr2);
+        nL += finish_chunk(hl, okl, 0, availL, S.llam);
+        nR += finish_chunk(hr, okr, 0, availR, S.rlam);
         vL0 = okl ? hl : -1;
         vR0 = okr ? hr : -1;
         vL1 = vR1 = -1;
         if (nL == 32) {
-            nL += finish_chunk(hl2, il2, okl2, 32, availL, S.lid, S.llam);
+            nL += finish_chunk(hl2, okl2, 32, availL, S.llam);
             vL1 = okl2 ? hl2 : -1;
         }
         if (nR == 32) {
-            nR += finish_chunk(hr2, ir2, okr2, 32, availR, S.rid, S.rlam);
+            nR += finish_chunk(hr2, okr2, 32, availR, S.rlam);
             vR1 = okr2 ? hr2 : -1;
         }
     }
@@ -456,22 +452,21 @@ __device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, WA& S, int p,
             break;
         }
         int h;
-        uint32_t id;
         bool ok;
         if (bL >= bR) {
             if (nL + 32 > kSide) {
                 flag_status(ix.status, DEV_BAD);
                 break;
             }
-            issue_chunk<true>(ix, p, nL, availL, lL, h, id, ok);
-            nL += finish_chunk(h, id, ok, nL, availL, S.lid, S.llam);
+            issue_chunk<true>(ix, p, nL, availL, lL, h, ok);
+            nL += finish_chunk(h, ok, nL, availL, S.llam);
         } else {
             if (nR + 32 > kSide) {
                 flag_status(ix.status, DEV_BAD);
                 break;
             }
-            issue_chunk<false>(ix, p, nR, availR, lR, h, id, ok);
-            nR += finish_chunk(h, id, ok, nR, availR, S.rid, S.rlam);
+            issue_chunk<false>(ix, p, nR, availR, lR, h, ok);
+            nR += finish_chunk(h, ok, nR, availR, S.rlam);
         }
     }
     // A = loaded items with LCP > d*; interval [lov, hiv) of level d*.
@@ -522,9 +517,9 @@ __device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, WA& S, int p,
     if (kp > nT) kp = nT;
     // 5a. A sorted by (LCP desc, id asc) into slots [0, nA)
     if (nA > 0) {
-        if (nA <= 32) rank_and_write_A<KT>(S, aL, nA, oid, olcp);
-        else if (nA <= 64) sort_and_write_A<2, KT>(S, aL, nA, oid, olcp);
-        else sort_and_write_A<4, KT>(S, aL, nA, oid, olcp);
+        if (nA <= 32) rank_and_write_A<KT>(S, ix.ids, p, aL, nA, oid, olcp);
+        else if (nA <= 64) sort_and_write_A<2, KT>(S, ix.ids, p, aL, nA, oid, olcp);
+        else sort_and_write_A<4, KT>(S, ix.ids, p, aL, nA, oid, olcp);
     }
     FillRec r;
     r.lov = lov;

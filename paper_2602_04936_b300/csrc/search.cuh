@@ -22,19 +22,15 @@ struct alignas(16) QLoc {
 };
 
 struct alignas(16) QWarp {
-
-    uint32_t lid[kSide];
-    uint32_t rid[kSide];
     uint32_t src[4][kKMax];
     uint32_t m1[2 * kKMax];
     uint8_t llam[kSide];
     uint8_t rlam[kSide];
 };
 
-// The expansion's work area (a subset of QWarp): the loaded items per side.
+// The expansion's work area (a subset of QWarp): the loaded items' LCPs per
+// side (their ids are read from the index when A is written).
 struct alignas(16) AWarp {
-    uint32_t lid[kSide];
-    uint32_t rid[kSide];
     uint8_t llam[kSide];
     uint8_t rlam[kSide];
 };
@@ -110,18 +106,19 @@ __device__ __forceinline__ void warp_bitonic(KT (&v)[E]) {
     }
 }
 
-// A of at most 32 items: lane i holds item i and places it at its rank,
+// A of at most 32 items (left item i at position p-1-i, right item i at p+i;
+// their ids read from the index): lane i holds item i and places it at its rank,
 // the number of items whose key is smaller (keys are distinct: ids differ),
 // found with nA broadcasts -- fewer instructions than a 32-key bitonic
 // network whenever A is small, which it usually is.
 template <typename KT, typename WA>
-__device__ __forceinline__ void rank_and_write_A(const WA& S, int aL, int nA,
+__device__ __forceinline__ void rank_and_write_A(const WA& S, const int32_t* __restrict__ ids, int p, int aL, int nA,
                                                  int32_t* __restrict__ oid,
                                                  uint8_t* __restrict__ olcp) {
     const int lane = (int)lane_id();
     KT key = ~(KT)0;
-    if (lane < aL) key = make_key<KT>(S.llam[lane], S.lid[lane]);
-    else if (lane < nA) key = make_key<KT>(S.rlam[lane - aL], S.rid[lane - aL]);
+    if (lane < aL) key = make_key<KT>(S.llam[lane], (uint32_t)ids[p - 1 - lane]);
+    else if (lane < nA) key = make_key<KT>(S.rlam[lane - aL], (uint32_t)ids[p + lane - aL]);
     int rank = 0;
     for (int j = 0; j < nA; j += 4) {  // four independent broadcasts per step
 #pragma unroll
@@ -139,7 +136,7 @@ __device__ __forceinline__ void rank_and_write_A(const WA& S, int aL, int nA,
 // Sorts A (left items [0, aL), right items [0, nA - aL)) and writes the
 // first nA output slots.
 template <int E, typename KT, typename WA>
-__device__ __forceinline__ void sort_and_write_A(const WA& S, int aL, int nA,
+__device__ __forceinline__ void sort_and_write_A(const WA& S, const int32_t* __restrict__ ids, int p, int aL, int nA,
                                                  int32_t* __restrict__ oid,
                                                  uint8_t* __restrict__ olcp) {
     const int lane = (int)lane_id();
@@ -148,8 +145,8 @@ __device__ __forceinline__ void sort_and_write_A(const WA& S, int aL, int nA,
     for (int e = 0; e < E; ++e) {
         const int idx = lane * E + e;
         KT key = ~(KT)0;
-        if (idx < aL) key = make_key<KT>(S.llam[idx], S.lid[idx]);
-        else if (idx < nA) key = make_key<KT>(S.rlam[idx - aL], S.rid[idx - aL]);
+        if (idx < aL) key = make_key<KT>(S.llam[idx], (uint32_t)ids[p - 1 - idx]);
+        else if (idx < nA) key = make_key<KT>(S.rlam[idx - aL], (uint32_t)ids[p + idx - aL]);
         v[e] = key;
     }
     warp_bitonic<E, KT>(v);
