@@ -372,6 +372,11 @@ static int alloc_index(lcp_index_s* x, int64_t N, int64_t cap, cudaStream_t s) {
     c.add(&x->st, (size_t)(lev > 0 ? lev : 1) * x->nblk_cap * x->K);
     c.add(&x->bkt, ((size_t)1 << x->bits) + 1);
     c.add(&x->top, (size_t)lcpk::kTopLevels);
+    if (cap == N && N >= lcpk::kSub2Min) {  // depth-2 tables: rebuilt by builds only
+        c.add(&x->sub_idx, (size_t)1 << x->bits);
+        c.add(&x->sub, (size_t)lcpk::kSub2Max << x->bits);
+        c.add(&x->sub_count, 1);
+    }
     // heavy-node tie lists: one table row per 128-row sample, one list per
     // node.  For max_k below kTieListMinK a tie fill from the sparse table
     // costs about as many loads as one from a list, so the lists (and their

@@ -523,6 +523,40 @@ __global__ void k_buckets(const uint64_t* __restrict__ head, int64_t n, int bits
     bkt[t] = (int32_t)lo;
 }
 
+// Depth-2 bucket tables.  k_sub_assign: the first tokens whose depth-1
+// bucket holds at least kSub2Min rows get a table each (numbered by an
+// atomic counter, at most kSub2Max; which buckets get one when there are
+// more is not fixed, and answers never depend on it).  k_sub_mark: the first
+// and the last row of each (first, second token) run in such a bucket write
+// the run's start and end at its second token; entries of second tokens
+// that do not occur are never read (a search reads the run of a neighbour
+// row's first two tokens).
+__global__ void k_sub_assign(const int32_t* __restrict__ bkt, int bits, int32_t* __restrict__ sub_idx,
+                             uint32_t* __restrict__ count) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= (1 << bits)) return;
+    int32_t t = -1;
+    if (bkt[v + 1] - bkt[v] >= kSub2Min) {
+        const uint32_t r = atomicAdd(count, 1u);
+        if (r < (uint32_t)kSub2Max) t = (int32_t)r;
+    }
+    sub_idx[v] = t;
+}
+
+__global__ void k_sub_mark(const uint64_t* __restrict__ head, int64_t n, int bits, const int32_t* __restrict__ sub_idx,
+                           int2* __restrict__ sub) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const uint64_t h = head[p];
+    const int32_t si = sub_idx[h >> (64 - bits)];
+    if (si < 0) return;
+    const uint64_t m2 = ~0ull << (64 - 2 * bits);  // the first two tokens
+    const uint32_t t1 = (uint32_t)(h >> (64 - 2 * bits)) & ((1u << bits) - 1);
+    int2* e = sub + ((int64_t)si << bits) + t1;
+    if (p == 0 || ((head[p - 1] ^ h) & m2) != 0) e->x = (int32_t)p;
+    if (p == n - 1 || ((head[p + 1] ^ h) & m2) != 0) e->y = (int32_t)(p + 1);
+}
+
 // First K entries of the merge of the sorted K-lists A and B (smem) into O
 // (smem or global); lane l writes entries [l*K/32, (l+1)*K/32) by merge path.
 __device__ __forceinline__ void merge_k(const uint32_t* A, const uint32_t* B, uint32_t* O, int K, int lane) {
@@ -925,8 +959,11 @@ SideStream* side_stream() {
     SideStream& x = ss[dev];
     if (!x.s2) {
         if (cudaStreamCreateWithFlags(&x.s2, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&x.s3, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&x.fork3, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&x.join3, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             x = SideStream();
             return nullptr;
@@ -1007,6 +1044,20 @@ int build_aux(lcp_index_s* x, cudaStream_t s, bool merged) {
         LCP_TIMED_LAUNCH(k_inverse, blocks_for(N, 256), 256, 0, s2, b.ids, N, x->pos);
         LCP_TIMED_LAUNCH(k_buckets, blocks_for((1ll << x->bits) + 1, 256), 256, 0, s2, b.head, N, x->bits, x->bkt);
     }
+    // depth-2 tables of the largest depth-1 buckets, on a third branch (only
+    // the search reads them): joined at the end
+    cudaStream_t s3 = ss && s2 != s ? ss->s3 : s2;
+    const bool sub3 = x->sub_idx && !merged;
+    if (sub3) {
+        if (s3 != s2) {
+            LCP_CUDA_TRY(cudaEventRecord(ss->fork3, s2));
+            LCP_CUDA_TRY(cudaStreamWaitEvent(s3, ss->fork3, 0));
+        }
+        LCP_CUDA_TRY(cudaMemsetAsync(x->sub_count, 0, sizeof(uint32_t), s3));
+        LCP_TIMED_LAUNCH(k_sub_assign, blocks_for(1ll << x->bits, 256), 256, 0, s3, x->bkt, x->bits, x->sub_idx,
+                         x->sub_count);
+        LCP_TIMED_LAUNCH(k_sub_mark, blocks_for(N, 256), 256, 0, s3, b.head, N, x->bits, x->sub_idx, x->sub);
+    }
     {
         const int T = (int)(N < kTopLevels ? N : kTopLevels);
         LCP_TIMED_LAUNCH(k_top_sample, blocks_for(T, 256), 256, 0, s2, b.head, N, T, x->top);
@@ -1054,6 +1105,10 @@ int build_aux(lcp_index_s* x, cudaStream_t s, bool merged) {
         LCP_CUDA_TRY(cudaStreamWaitEvent(s, ss->join, 0));
     }
     if (rc == LCP_OK) rc = build_tie_lists_fill(x, s);
+    if (sub3 && s3 != s2) {  // join the third branch (also on an error)
+        LCP_CUDA_TRY(cudaEventRecord(ss->join3, s3));
+        LCP_CUDA_TRY(cudaStreamWaitEvent(s, ss->join3, 0));
+    }
     return rc;
 }
 
@@ -1087,6 +1142,8 @@ DevIndex dev_view(const lcp_index_s* x) {
     d.st = x->st;
     d.st_stride = x->nblk_cap;
     d.bkt = x->bkt;
+    d.sub_idx = x->sub_idx;
+    d.sub = x->sub;
     d.top = x->top;
     d.top_n = (int)(x->N < kTopLevels ? x->N : kTopLevels);
     d.tbl = x->tbl;

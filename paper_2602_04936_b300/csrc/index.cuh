@@ -34,6 +34,11 @@
 //   bkt_list [2^bits] i32  the list of each depth-1 bucket (-1 if light), so
 //                       that the common d* = 1 case reads bounds and list
 //                       number in one round trip.
+//   sub  [<=64][2^bits] i32x2  depth-2 buckets (start, end) of depth-1
+//                       buckets of at least 4,096 rows: the d* = 2
+//                       interval of a query whose first token has a table is
+//                       two loads instead of a search (indexes without insert
+//                       capacity; sub_idx maps a first token to its table).
 #pragma once
 
 #include "common.cuh"
@@ -45,6 +50,8 @@ constexpr int kMaxHLev = 7;      // min-tree levels above H (32^7 > 2^30)
 constexpr int kMaxStLev = 24;
 constexpr uint32_t kInf = 0xFFFFFFFFu;
 constexpr int kTopLevels = 4096;  // samples of the sorted array's heads (32 KB)
+constexpr int kSub2Max = 64;       // depth-2 bucket tables at most
+constexpr int kSub2Min = 4096;     // rows a depth-1 bucket needs to get one
 
 struct DevIndex {
     int64_t N;
@@ -66,6 +73,12 @@ struct DevIndex {
     const uint32_t* st;
     int64_t st_stride;  // nblk capacity used for the table layout
     const int32_t* bkt;
+    // depth-2 buckets of the largest depth-1 buckets (null: none): sub_idx[t0]
+    // is t0's table (-1 if none) and sub[(table << bits) + t1] the sorted
+    // positions [x, y) of the rows whose first two tokens are (t0, t1), for
+    // pairs that occur
+    const int32_t* sub_idx;
+    const int2* sub;
     const int32_t* tbl;
     const uint32_t* tlists;
     const int32_t* tlpos;
@@ -101,6 +114,10 @@ struct lcp_index_s {
     uint8_t* soff = nullptr;
     uint32_t* st = nullptr;
     int32_t* bkt = nullptr;
+    // depth-2 bucket tables (indexes without insert capacity only)
+    int32_t* sub_idx = nullptr;    // [2^bits]
+    int2* sub = nullptr;           // [kSub2Max][2^bits]
+    uint32_t* sub_count = nullptr;  // tables handed out
     // heavy-node tie lists
     int32_t* tbl = nullptr;        // [nsamp_cap][L+1]
     uint8_t* slot_flag = nullptr;  // [nsamp_cap][L+1] canonical (sample, depth) slots
@@ -178,8 +195,8 @@ int build_tie_lists_fill(lcp_index_s* x, cudaStream_t s);
 // parallel branches when captured into a graph.  Created on first use (so
 // call it once before any stream capture); nullptr if that failed.
 struct SideStream {
-    cudaStream_t s2 = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaStream_t s2 = nullptr, s3 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, fork3 = nullptr, join3 = nullptr;
 };
 SideStream* side_stream();
 

@@ -367,6 +367,10 @@ __device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, WA& S, int p,
     // the depth-1 bucket of q's first token, fetched early: d* is 1 for
     // about half of the queries, and these loads then cost no extra wait
     const int32_t bk0 = ix.bkt[tok0], bk1 = ix.bkt[tok0 + 1], bkl = ix.bkt_list[tok0];
+    // and its depth-2 table (d* = 2 for about a fifth of the queries), with
+    // the neighbour rows' first words that give q's second token
+    const int32_t sti = ix.sub_idx ? ix.sub_idx[tok0] : -1;
+    const uint64_t hnL = p > 0 ? ix.head[p - 1] : 0ull, hnR = p < N ? ix.head[p] : 0ull;
     // first round: 64 rows per side, all four chunks in flight at once; the
     // LCPs stay in registers too (lane l: items l and 32 + l of each side,
     // -1 where absent) for the decision below
@@ -496,7 +500,15 @@ __device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, WA& S, int p,
     } else if (dstar > 1) {
         const bool knownL = vL < nL || nL == availL;
         const bool knownR = vR < nR || nR == availR;
-        if (dstar <= ix.tpw && !(knownL && knownR)) {
+        if (dstar == 2 && sti >= 0 && !(knownL && knownR)) {
+            // the depth-2 bucket of q's first two tokens (those of the
+            // neighbour row with the larger LCP, which is >= 2)
+            const uint32_t t1 =
+                (uint32_t)((lL >= lR ? hnL : hnR) >> (64 - 2 * ix.bits)) & ((1u << ix.bits) - 1);
+            const int2 run = ix.sub[((int64_t)sti << ix.bits) + t1];
+            lov = knownL ? p - vL : run.x;
+            hiv = knownR ? p + vR : run.y;
+        } else if (dstar <= ix.tpw && !(knownL && knownR)) {
             // the run lies in word 0: searches over head inside the bucket;
             // a neighbour of p with LCP >= d* gives the run's masked word 0
             const uint64_t mask = ~0ull << (64 - dstar * ix.bits);
