@@ -246,6 +246,34 @@ def test_scan_shared_prefix_beyond_list(lcp):
         assert_same(scan(lcp, S, Qs[1:2], k), oracle.topk_batch(S, Qs[1:2], k), "one query k=%d" % k)
 
 
+@pytest.mark.parametrize("tb", [1, 2])
+def test_depth2_bucket_tables(lcp, tb):
+    """First tokens with at least 4,096 rows get depth-2 bucket tables (runs
+    of (first, second token)); queries whose d* is 2 read their tie interval
+    from them.  Three big first tokens, second tokens at both ends of the
+    range and in between, against the oracle (and an index with insert
+    capacity, which has no tables)."""
+    rng = np.random.default_rng(23 + tb)
+    dt = np.uint8 if tb == 1 else np.uint16
+    top = np.iinfo(dt).max
+    N, L = 30000, 12
+    S = rng.integers(0, 6, size=(N, L)).astype(dt)
+    S[:, 0] = rng.choice(np.array([3, 7, top], dt), N, p=[0.45, 0.35, 0.2])
+    S[:, 1] = rng.choice(np.array([0, 1, 2, top - 1, top], dt), N)
+    Qs = S[rng.integers(0, N, 400)].copy()
+    Qs[:, 2:] = rng.integers(6, 9, size=(400, L - 2))  # LCP exactly 2 with their source rows
+    Qs[:40, 1] = 5  # second token absent: d* = 1
+    for k in (5, 100):
+        want = oracle.topk_batch(S, Qs, k)
+        assert_same(indexed(lcp, S, Qs, k), want, "indexed depth-2 k=%d" % k)
+        assert_same(indexed(lcp, S, Qs, k, shape=(8, 0)), want, "indexed depth-2, three kernels k=%d" % k)
+    idx = lcp.lcp_index_build(dev(S), max_k=100, capacity=N + 100)
+    ids, lc = lcp.lcp_topk_batch(idx, dev(Qs), 100)
+    torch.cuda.synchronize()
+    assert_same((ids.cpu().numpy(), lc.cpu().numpy()), oracle.topk_batch(S, Qs, 100), "insertable index")
+    idx.close()
+
+
 def test_index_past_2_pow_24_rows(lcp):
     """An index of more than 2^24 rows takes the searches' 64-bit sort keys
     (24 bits no longer hold an id): the fused small-batch kernel and the
