@@ -500,9 +500,12 @@ int lcp_index_build(const void* d_tokens, int64_t N, lcp_format_t fmt, int64_t c
         if (g != LCP_PENDING) rc = g;  // LCP_PENDING: not graph-capturable here, build below
     }
     if (rc == LCP_OK && N > 0) {
-        // Issued without waiting for the device.  Rows tied on word 0 in
-        // groups of more than 2048 need the exact (host-driven) refinement; their count lands in pinned memory behind an event
-        // recorded mid-build, checked once everything is queued -- by then
+        // Issued without waiting for the device.  Rows the on-device group
+        // sort does not take (more than 2,048 rows sharing word 0, or a group
+        // of 33-2,048 in which a row shares word 1 with more than 64 others)
+        // need the exact (host-driven) refinement; their count lands in
+        // pinned memory behind an event recorded mid-build, checked once
+        // everything is queued -- by then
         // the device is usually past it, so the host returns while the
         // device still runs the tail of the build.  A nonzero count (rare:
         // heavy duplication) redoes the order exactly.

@@ -61,6 +61,7 @@ struct SelArgs {
     int32_t* out_ids;   // [Q][k]
     uint8_t* out_lcp;   // [Q][k]
     int* status;
+    int sorted;         // full tiles are sorted by their first 32 bits and searched
 };
 
 __device__ __forceinline__ uint64_t sel_key(int l, int64_t id) {
@@ -96,18 +97,83 @@ __device__ __forceinline__ void sel_tile_copy(const CUtensorMap* tm, void* dst, 
 // as broadcasts) -- no block-wide barrier after the start.  Rows whose first
 // 32 bits match a query's get their exact LCP at once (word 1 is in the
 // tile); those to be listed wait in a per-warp queue whose appends (global
-// atomics) the warp then issues together.  Dynamic shared memory: the
+// atomics) the warp issues together, 32 a round, once the queue might not
+// hold another step's rows and at the end of the tile.  Dynamic shared memory: the
 // warps' rings, their queues, then the batch's words 0 and 1 (Q x 16 bytes)
 // and two list-full flags per query.
 constexpr int kSelCountWarps = 8;
 constexpr int kSelWarpStages = 2;
-constexpr int kSelQueue = 256;  // queued rows per warp: one 8-row step of 32 queries
+constexpr int kSelQueue = 512;  // queued rows per warp
+constexpr int kSelStep = 256;  // most rows one 8-row step of 32 queries can queue
 constexpr size_t kSelRingBytes = (size_t)kSelCountWarps * kSelWarpStages * kSelRows * 16;
 constexpr size_t kSelQueueBytes = (size_t)kSelCountWarps * kSelQueue * sizeof(uint32_t);
 constexpr size_t kSelHiBytes = (size_t)kSelCountWarps * kSelRows * sizeof(uint32_t);
+constexpr size_t kSelRowIdxBytes = (size_t)kSelCountWarps * kSelRows;  // a tile's rows in key order
+// Batches from this size up search sorted tiles: sorting a tile costs about
+// as much as comparing one 32-query chunk with its rows, and every further
+// chunk then takes a few binary searches instead of a pass over the rows.
+constexpr int kSelSortedMinQ = 64;
 
 __host__ __device__ constexpr size_t sel_count_smem(int Q) {
-    return kSelRingBytes + kSelQueueBytes + kSelHiBytes + (size_t)Q * (2 * sizeof(uint64_t) + 2);
+    return kSelRingBytes + kSelQueueBytes + kSelHiBytes + kSelRowIdxBytes + (size_t)Q * (2 * sizeof(uint64_t) + 2);
+}
+
+// Ascending bitonic sort of 256 keys held 8 a lane (element 8 * lane + i) by
+// one warp, each key carrying a value; equal keys end in either order.
+__device__ __forceinline__ void warp_sort256(uint32_t (&k)[8], uint32_t (&v)[8]) {
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int size = 2; size <= 256; size <<= 1) {
+#pragma unroll
+        for (int j = size >> 1; j > 0; j >>= 1) {
+            if (j >= 8) {  // the pair spans two lanes: exchange, keep the min or the max
+                const int lj = j >> 3;
+                const bool lower = (lane & (unsigned)lj) == 0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const bool up = ((lane * 8 + (unsigned)i) & (unsigned)size) == 0;
+                    const uint32_t ok = __shfl_xor_sync(0xffffffffu, k[i], lj);
+                    const uint32_t ov = __shfl_xor_sync(0xffffffffu, v[i], lj);
+                    const bool take = lower == up ? ok < k[i] : ok > k[i];
+                    if (take) {
+                        k[i] = ok;
+                        v[i] = ov;
+                    }
+                }
+            } else {  // both elements in this lane
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    if ((i & j) == 0) {
+                        const int i2 = i | j;
+                        const bool up = ((lane * 8 + (unsigned)i) & (unsigned)size) == 0;
+                        if ((k[i] > k[i2]) == up) {
+                            const uint32_t tk = k[i], tv = v[i];
+                            k[i] = k[i2];
+                            v[i] = v[i2];
+                            k[i2] = tk;
+                            v[i2] = tv;
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Keys of a sorted 256-entry array below x (lower bound), or at most x.
+__device__ __forceinline__ int sorted_below(const uint32_t* s, uint32_t x) {
+    int pos = 0;
+#pragma unroll
+    for (int step = 128; step >= 1; step >>= 1)
+        if (s[pos + step - 1] < x) pos += step;
+    return pos + (s[pos] < x ? 1 : 0);  // only pos == 255 can still move
+}
+__device__ __forceinline__ int sorted_at_most(const uint32_t* s, uint32_t x) {
+    int pos = 0;
+#pragma unroll
+    for (int step = 128; step >= 1; step >>= 1)
+        if (s[pos + step - 1] <= x) pos += step;
+    return pos + (s[pos] <= x ? 1 : 0);
 }
 
 template <int TB>
@@ -123,7 +189,11 @@ __global__ void __launch_bounds__(kSelCountWarps * 32) k_sel_count(const __grid_
     // the current tile's upper halves of word 0, contiguous: four rows a 16-byte load
     uint32_t* hiw = reinterpret_cast<uint32_t*>(dyn + (kSelRingBytes + kSelQueueBytes) / sizeof(uint64_t)) +
                     warp * kSelRows;
-    uint64_t* qword0 = dyn + (kSelRingBytes + kSelQueueBytes + kSelHiBytes) / sizeof(uint64_t);  // [Q] word 0
+    // a sorted tile's rows in the order of their sorted keys (kept in hiw)
+    uint8_t* srow = reinterpret_cast<uint8_t*>(dyn + (kSelRingBytes + kSelQueueBytes + kSelHiBytes) / sizeof(uint64_t)) +
+                    warp * kSelRows;
+    uint64_t* qword0 =
+        dyn + (kSelRingBytes + kSelQueueBytes + kSelHiBytes + kSelRowIdxBytes) / sizeof(uint64_t);  // [Q] word 0
     uint64_t* qword1 = qword0 + a.Q;                                                // [Q] and word 1
     uint8_t* full = reinterpret_cast<uint8_t*>(qword1 + a.Q);  // [Q][2]: list2 / list4 seen full
     uint64_t* wb = bar[warp];
@@ -221,6 +291,27 @@ __global__ void __launch_bounds__(kSelCountWarps * 32) k_sel_count(const __grid_
             }
         }
         __syncwarp();
+        // a full tile of a larger batch: its upper halves of word 0 sorted
+        // (with their rows), so that a query's level counts are the widths
+        // of key ranges and its matching rows one range
+        const bool srt = a.sorted && nrows == kSelRows;
+        if (srt) {
+            uint32_t kk[8], vv[8];
+            const uint4* h4 = reinterpret_cast<const uint4*>(hiw) + lane * 2;
+            const uint4 u = h4[0], v = h4[1];
+            kk[0] = u.x, kk[1] = u.y, kk[2] = u.z, kk[3] = u.w;
+            kk[4] = v.x, kk[5] = v.y, kk[6] = v.z, kk[7] = v.w;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) vv[i] = lane * 8 + (unsigned)i;
+            warp_sort256(kk, vv);
+            __syncwarp();  // every lane has read its keys
+            uint4* o4 = reinterpret_cast<uint4*>(hiw) + lane * 2;
+            o4[0] = make_uint4(kk[0], kk[1], kk[2], kk[3]);
+            o4[1] = make_uint4(kk[4], kk[5], kk[6], kk[7]);
+            reinterpret_cast<uint2*>(srow)[lane] = make_uint2(vv[0] | vv[1] << 8 | vv[2] << 16 | vv[3] << 24,
+                                                              vv[4] | vv[5] << 8 | vv[6] << 16 | vv[7] << 24);
+            __syncwarp();
+        }
         for (int c = 0; c < nch; ++c) {
             const int q = c * 32 + (int)lane;
             const bool qa = q < a.Q;
@@ -249,9 +340,43 @@ __global__ void __launch_bounds__(kSelCountWarps * 32) k_sel_count(const __grid_
                     c3 += l >= th3;
                     c4 += l >= th4;
                 }
-                if ((TB == 2 && l >= 2) || l >= kSelDeep)
+                // queued for a list this CTA has not seen full, or for the histogram
+                const bool w2 = TB == 2 && l >= 2 && !full[2 * q];
+                const bool w4 = l >= kSelDeep && !full[2 * q + 1];
+                if (w2 || w4 || l > kSelDeep)
                     queue[atomicAdd(&qn[warp], 1u)] = ((uint32_t)q << 16) | ((uint32_t)r << 8) | (uint32_t)l;
             };
+            if (srt) {
+                // rows whose first d tokens equal q's: keys between q's key
+                // with the bits past those tokens cleared and with them set
+                auto width = [&](uint32_t low_bits) {
+                    return (uint32_t)(sorted_at_most(hiw, qh | low_bits) - sorted_below(hiw, qh & ~low_bits));
+                };
+                int lo = qa ? sorted_below(hiw, qh) : 0;
+                const int hi = qa ? sorted_at_most(hiw, qh) : 0;
+                if (qa) {
+                    if (TB == 2) {
+                        c1 = width(0xFFFFu);
+                    } else {
+                        c1 = width(0xFFFFFFu);
+                        c2 = L >= 2 ? width(0xFFFFu) : 0u;
+                        c3 = L >= 3 ? width(0xFFu) : 0u;
+                        c4 = L >= 4 ? (uint32_t)(hi - lo) : 0u;
+                    }
+                }
+                // every row whose first 32 bits match: 8 a lane a round
+                for (; __any_sync(0xffffffffu, lo < hi); lo += 8) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (lo + j < hi) deep((int)srow[lo + j]);
+                    __syncwarp();
+                    if (qn[warp] > (uint32_t)(kSelQueue - kSelStep)) flush(r0);
+                }
+                if (qa)
+                    a.cnt[(size_t)q * a.ngran + t] =
+                        ((uint64_t)(c3 | (c4 << 16)) << 32) | (uint64_t)(c1 | (c2 << 16));
+                continue;
+            }
             int r = 0;
             const uint4* h4 = reinterpret_cast<const uint4*>(hiw);
             for (; r + 8 <= nrows; r += 8) {
@@ -273,12 +398,13 @@ __global__ void __launch_bounds__(kSelCountWarps * 32) k_sel_count(const __grid_
                     m = min(m, xh);
                 }
                 if (!qa) m = ~0u;
-                if (__any_sync(0xffffffffu, m == 0)) {  // rare: at most 8 x 32 rows queued
+                if (__any_sync(0xffffffffu, m == 0)) {  // rare: at most kSelStep rows queued
                     if (m == 0)
 #pragma unroll
                         for (int j = 0; j < 8; ++j)
                             if (x[j] == 0) deep(r + j);
-                    flush(r0);
+                    __syncwarp();
+                    if (qn[warp] > (uint32_t)(kSelQueue - kSelStep)) flush(r0);
                 }
             }
             for (; r < nrows; ++r) {
@@ -294,12 +420,15 @@ __global__ void __launch_bounds__(kSelCountWarps * 32) k_sel_count(const __grid_
                 }
                 if (__any_sync(0xffffffffu, qa && xh == 0)) {
                     if (qa && xh == 0) deep(r);
-                    flush(r0);
+                    __syncwarp();
+                    if (qn[warp] > (uint32_t)(kSelQueue - kSelStep)) flush(r0);
                 }
             }
             if (qa)
                 a.cnt[(size_t)q * a.ngran + t] = ((uint64_t)(c3 | (c4 << 16)) << 32) | (uint64_t)(c1 | (c2 << 16));
         }
+        __syncwarp();
+        if (qn[warp] != 0) flush(r0);  // the queued rows name rows of this tile
         __syncwarp();  // every lane is done with the buffer
         if (use_tma && lane == 0) {
             const int64_t tn = t + (int64_t)kSelWarpStages * nw;
@@ -820,6 +949,7 @@ int scan_select(const void* d_tokens, int64_t N, const RowFmt& f, const void* d_
     a.out_lcp = d_out_lcp;
     a.status = lib_status_word();
     a.plane = nullptr;
+    a.sorted = Q >= kSelSortedMinQ ? 1 : 0;
     Carver cv;
     // zeroed together: hist, n2, n4
     cv.add(&a.hist, (size_t)Q * (L + 1));
