@@ -109,54 +109,63 @@ constexpr size_t kSelRingBytes = (size_t)kSelCountWarps * kSelWarpStages * kSelR
 constexpr size_t kSelQueueBytes = (size_t)kSelCountWarps * kSelQueue * sizeof(uint32_t);
 constexpr size_t kSelHiBytes = (size_t)kSelCountWarps * kSelRows * sizeof(uint32_t);
 constexpr size_t kSelRowIdxBytes = (size_t)kSelCountWarps * kSelRows;  // a tile's rows in key order
-// Batches from this size up search sorted tiles: sorting a tile costs about
-// as much as comparing one 32-query chunk with its rows, and every further
-// chunk then takes a few binary searches instead of a pass over the rows.
-constexpr int kSelSortedMinQ = 64;
+// Batches from this size up search sorted tiles: sorting a tile by its
+// 64-bit word 0 costs about as much as comparing four or five 32-query
+// chunks with its rows, and every chunk then takes a few binary searches
+// instead of a pass over the rows (measured on 2M rows of 64 uint16 tokens:
+// 128 queries 0.162 ms compared, 0.178 sorted; 192 queries 0.229 / 0.206).
+constexpr int kSelSortedMinQ = 160;
 
 __host__ __device__ constexpr size_t sel_count_smem(int Q) {
     return kSelRingBytes + kSelQueueBytes + kSelHiBytes + kSelRowIdxBytes + (size_t)Q * (2 * sizeof(uint64_t) + 2);
 }
 
+// One in-lane stage (distance J < 8) of the bitonic network below.
+template <int J>
+__device__ __forceinline__ void sort256_in_lane(uint64_t (&k)[8], uint32_t (&v)[8], unsigned lane, int size) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if ((i & J) == 0) {
+            const int i2 = i | J;
+            const bool up = ((lane * 8 + (unsigned)i) & (unsigned)size) == 0;
+            if ((k[i] > k[i2]) == up) {
+                const uint64_t tk = k[i];
+                const uint32_t tv = v[i];
+                k[i] = k[i2];
+                v[i] = v[i2];
+                k[i2] = tk;
+                v[i2] = tv;
+            }
+        }
+    }
+}
+
 // Ascending bitonic sort of 256 keys held 8 a lane (element 8 * lane + i) by
-// one warp, each key carrying a value; equal keys end in either order.
-__device__ __forceinline__ void warp_sort256(uint32_t (&k)[8], uint32_t (&v)[8]) {
+// one warp, each key carrying a value; equal keys end in either order.  The
+// stage loops stay rolled: the kernel's code then fits the instruction cache.
+__device__ __forceinline__ void warp_sort256(uint64_t (&k)[8], uint32_t (&v)[8]) {
     const unsigned lane = lane_id();
-#pragma unroll
+#pragma unroll 1
     for (int size = 2; size <= 256; size <<= 1) {
+#pragma unroll 1
+        for (int j = size >> 1; j >= 8; j >>= 1) {  // the pair spans two lanes
+            const int lj = j >> 3;
+            const bool lower = (lane & (unsigned)lj) == 0;
 #pragma unroll
-        for (int j = size >> 1; j > 0; j >>= 1) {
-            if (j >= 8) {  // the pair spans two lanes: exchange, keep the min or the max
-                const int lj = j >> 3;
-                const bool lower = (lane & (unsigned)lj) == 0;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const bool up = ((lane * 8 + (unsigned)i) & (unsigned)size) == 0;
-                    const uint32_t ok = __shfl_xor_sync(0xffffffffu, k[i], lj);
-                    const uint32_t ov = __shfl_xor_sync(0xffffffffu, v[i], lj);
-                    const bool take = lower == up ? ok < k[i] : ok > k[i];
-                    if (take) {
-                        k[i] = ok;
-                        v[i] = ov;
-                    }
-                }
-            } else {  // both elements in this lane
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    if ((i & j) == 0) {
-                        const int i2 = i | j;
-                        const bool up = ((lane * 8 + (unsigned)i) & (unsigned)size) == 0;
-                        if ((k[i] > k[i2]) == up) {
-                            const uint32_t tk = k[i], tv = v[i];
-                            k[i] = k[i2];
-                            v[i] = v[i2];
-                            k[i2] = tk;
-                            v[i2] = tv;
-                        }
-                    }
+            for (int i = 0; i < 8; ++i) {
+                const bool up = ((lane * 8 + (unsigned)i) & (unsigned)size) == 0;
+                const uint64_t ok = __shfl_xor_sync(0xffffffffu, k[i], lj);
+                const uint32_t ov = __shfl_xor_sync(0xffffffffu, v[i], lj);
+                const bool take = lower == up ? ok < k[i] : ok > k[i];
+                if (take) {
+                    k[i] = ok;
+                    v[i] = ov;
                 }
             }
         }
+        if (size >= 8) sort256_in_lane<4>(k, v, lane, size);
+        if (size >= 4) sort256_in_lane<2>(k, v, lane, size);
+        sort256_in_lane<1>(k, v, lane, size);
     }
 }
 
@@ -175,9 +184,27 @@ __device__ __forceinline__ int sorted_at_most(const uint32_t* s, uint32_t x) {
         if (s[pos + step - 1] <= x) pos += step;
     return pos + (s[pos] <= x ? 1 : 0);
 }
+// The same inside [b, e) of a sorted tile whose low key halves sit in the
+// word-0 slots of the tile buffer (entry i at lw[4 * i]).
+__device__ __forceinline__ int range_below(const uint32_t* lw, int b, int e, uint32_t x) {
+    while (b < e) {
+        const int m = (b + e) >> 1;
+        if (lw[4 * m] < x) b = m + 1;
+        else e = m;
+    }
+    return b;
+}
+__device__ __forceinline__ int range_at_most(const uint32_t* lw, int b, int e, uint32_t x) {
+    while (b < e) {
+        const int m = (b + e) >> 1;
+        if (lw[4 * m] <= x) b = m + 1;
+        else e = m;
+    }
+    return b;
+}
 
 template <int TB>
-__global__ void __launch_bounds__(kSelCountWarps * 32) k_sel_count(const __grid_constant__ CUtensorMap tm,
+__global__ void __launch_bounds__(kSelCountWarps * 32, 2) k_sel_count(const __grid_constant__ CUtensorMap tm,
                                                                    const SelArgs a, int use_tma) {
     extern __shared__ __align__(128) uint64_t dyn[];
     __shared__ __align__(8) uint64_t bar[kSelCountWarps][kSelWarpStages];
@@ -291,23 +318,32 @@ __global__ void __launch_bounds__(kSelCountWarps * 32) k_sel_count(const __grid_
             }
         }
         __syncwarp();
-        // a full tile of a larger batch: its upper halves of word 0 sorted
-        // (with their rows), so that a query's level counts are the widths
-        // of key ranges and its matching rows one range
+        // a full tile of a larger batch: sorted by word 0 (its rows beside
+        // it), so that a query's level counts are the widths of key ranges
+        // and the rows it has to look at one range.  The sorted upper halves
+        // go to hiw, the lower halves to the word-0 slots of the tile buffer
+        // (entry i at buf[i][0]); word 1 stays in place, found through srow.
         const bool srt = a.sorted && nrows == kSelRows;
         if (srt) {
-            uint32_t kk[8], vv[8];
+            uint64_t kk[8];
+            uint32_t vv[8];
             const uint4* h4 = reinterpret_cast<const uint4*>(hiw) + lane * 2;
             const uint4 u = h4[0], v = h4[1];
-            kk[0] = u.x, kk[1] = u.y, kk[2] = u.z, kk[3] = u.w;
-            kk[4] = v.x, kk[5] = v.y, kk[6] = v.z, kk[7] = v.w;
+            const uint32_t hk[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
 #pragma unroll
-            for (int i = 0; i < 8; ++i) vv[i] = lane * 8 + (unsigned)i;
+            for (int i = 0; i < 8; ++i) {
+                vv[i] = lane * 8 + (unsigned)i;
+                kk[i] = ((uint64_t)hk[i] << 32) | (uint32_t)buf[lane * 8 + i][0];
+            }
             warp_sort256(kk, vv);
             __syncwarp();  // every lane has read its keys
             uint4* o4 = reinterpret_cast<uint4*>(hiw) + lane * 2;
-            o4[0] = make_uint4(kk[0], kk[1], kk[2], kk[3]);
-            o4[1] = make_uint4(kk[4], kk[5], kk[6], kk[7]);
+            o4[0] = make_uint4((uint32_t)(kk[0] >> 32), (uint32_t)(kk[1] >> 32), (uint32_t)(kk[2] >> 32),
+                               (uint32_t)(kk[3] >> 32));
+            o4[1] = make_uint4((uint32_t)(kk[4] >> 32), (uint32_t)(kk[5] >> 32), (uint32_t)(kk[6] >> 32),
+                               (uint32_t)(kk[7] >> 32));
+#pragma unroll
+            for (int i = 0; i < 8; ++i) buf[lane * 8 + i][0] = (uint32_t)kk[i];
             reinterpret_cast<uint2*>(srow)[lane] = make_uint2(vv[0] | vv[1] << 8 | vv[2] << 16 | vv[3] << 24,
                                                               vv[4] | vv[5] << 8 | vv[6] << 16 | vv[7] << 24);
             __syncwarp();
@@ -321,10 +357,14 @@ __global__ void __launch_bounds__(kSelCountWarps * 32) k_sel_count(const __grid_
             uint32_t c1 = 0, c2 = 0, c3 = 0, c4 = 0;
             // a row whose first 32 bits (2 uint16 / 4 uint8 tokens) match the
             // query's: exact LCP, level counts, queued if it is to be listed
-            auto deep = [&](int r) {
+            // a row whose first 32 bits (2 uint16 / 4 uint8 tokens) match the
+            // query's: its exact LCP (lw = the lower half of its word 0), the
+            // level counts when they are not taken from ranges, and queued
+            // if it is to be listed
+            auto deep = [&](int r, uint32_t lw, bool count) {
                 if (!qa) return;
                 int l;
-                const uint32_t xl = (uint32_t)buf[r][0] ^ ql;
+                const uint32_t xl = lw ^ ql;
                 if (xl) {
                     l = lcp_at(0, (uint64_t)xl, f);
                 } else if (f.W == 1) {
@@ -335,7 +375,7 @@ __global__ void __launch_bounds__(kSelCountWarps * 32) k_sel_count(const __grid_
                            : (f.W > 2 ? sel_lcp_deep(row_of(a.tokens, r0 + r, f), row_of(a.queries, q, a.qf), f, a.qf)
                                       : L);
                 }
-                if (TB == 2) {
+                if (TB == 2 && count) {
                     c2 += l >= th2;
                     c3 += l >= th3;
                     c4 += l >= th4;
@@ -352,11 +392,24 @@ __global__ void __launch_bounds__(kSelCountWarps * 32) k_sel_count(const __grid_
                 auto width = [&](uint32_t low_bits) {
                     return (uint32_t)(sorted_at_most(hiw, qh | low_bits) - sorted_below(hiw, qh & ~low_bits));
                 };
-                int lo = qa ? sorted_below(hiw, qh) : 0;
-                const int hi = qa ? sorted_at_most(hiw, qh) : 0;
+                const uint32_t* lws = reinterpret_cast<const uint32_t*>(buf);
+                int lo = qa ? sorted_below(hiw, qh) : 0;  // [lo, hi): the first 32 bits match
+                int hi = qa ? sorted_at_most(hiw, qh) : 0;
                 if (qa) {
                     if (TB == 2) {
                         c1 = width(0xFFFFu);
+                        if (hi > lo) {
+                            // tokens 2 and 3 inside the range, ordered by the lower halves
+                            const int lo3 = range_below(lws, lo, hi, ql & 0xFFFF0000u);
+                            const int hi3 = range_at_most(lws, lo3, hi, ql | 0xFFFFu);
+                            const int lo4 = range_below(lws, lo3, hi3, ql);
+                            const int hi4 = range_at_most(lws, lo4, hi3, ql);
+                            c2 = L >= 2 ? (uint32_t)(hi - lo) : 0u;
+                            c3 = L >= 3 ? (uint32_t)(hi3 - lo3) : 0u;
+                            c4 = L >= 4 ? (uint32_t)(hi4 - lo4) : 0u;
+                            // rows of LCP 2 and 3 matter only to a list not yet full
+                            if (full[2 * q]) lo = lo4, hi = hi4;
+                        }
                     } else {
                         c1 = width(0xFFFFFFu);
                         c2 = L >= 2 ? width(0xFFFFu) : 0u;
@@ -364,11 +417,11 @@ __global__ void __launch_bounds__(kSelCountWarps * 32) k_sel_count(const __grid_
                         c4 = L >= 4 ? (uint32_t)(hi - lo) : 0u;
                     }
                 }
-                // every row whose first 32 bits match: 8 a lane a round
+                // the rows to look at: 8 a lane a round
                 for (; __any_sync(0xffffffffu, lo < hi); lo += 8) {
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
-                        if (lo + j < hi) deep((int)srow[lo + j]);
+                        if (lo + j < hi) deep((int)srow[lo + j], lws[4 * (lo + j)], false);
                     __syncwarp();
                     if (qn[warp] > (uint32_t)(kSelQueue - kSelStep)) flush(r0);
                 }
@@ -402,7 +455,7 @@ __global__ void __launch_bounds__(kSelCountWarps * 32) k_sel_count(const __grid_
                     if (m == 0)
 #pragma unroll
                         for (int j = 0; j < 8; ++j)
-                            if (x[j] == 0) deep(r + j);
+                            if (x[j] == 0) deep(r + j, (uint32_t)buf[r + j][0], true);
                     __syncwarp();
                     if (qn[warp] > (uint32_t)(kSelQueue - kSelStep)) flush(r0);
                 }
@@ -419,7 +472,7 @@ __global__ void __launch_bounds__(kSelCountWarps * 32) k_sel_count(const __grid_
                     c4 += l0 >= th4 ? 1u : 0u;
                 }
                 if (__any_sync(0xffffffffu, qa && xh == 0)) {
-                    if (qa && xh == 0) deep(r);
+                    if (qa && xh == 0) deep(r, (uint32_t)buf[r][0], true);
                     __syncwarp();
                     if (qn[warp] > (uint32_t)(kSelQueue - kSelStep)) flush(r0);
                 }

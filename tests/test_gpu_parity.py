@@ -215,16 +215,17 @@ def test_scan_batch_paths_agree(lcp, N, L, tb, sigma, k):
 
 
 @pytest.mark.parametrize("Q,L,tb", [(1, 16, 2), (5, 16, 2), (33, 16, 2), (70, 32, 2), (257, 16, 1),
-                                     (40, 12, 2), (3, 8, 2), (64, 16, 1), (100, 3, 1), (90, 2, 1),
-                                     (128, 1, 2)])
+                                     (40, 12, 2), (3, 8, 2), (64, 16, 1), (200, 3, 1), (190, 2, 1),
+                                     (160, 1, 2), (170, 16, 2), (300, 5, 2), (400, 12, 2)])
 def test_scan_selection_batch_shapes(lcp, Q, L, tb):
     """Threshold selection at batch sizes that split a count CTA's 8 warps
     differently: one chunk of 32 queries over 8 row parts (Q <= 32), 3 chunks
     over 2 parts (70), more chunks than warps (257); rows fed by tensor copies
     (16-byte multiples) or by plain loads (24-byte rows); granules ragged at
-    the end (N not a multiple of 256).  From 64 queries the full granules are
-    sorted by their first 32 bits and searched, including rows shorter than
-    the four uint8 levels counted per granule (L = 2, 3) and one-word rows."""
+    the end (N not a multiple of 256).  From 160 queries the full granules
+    are sorted by word 0 and searched, including rows shorter than the four
+    levels counted per granule (L = 1, 2, 3; L = 5 uint16 has a one-token
+    word 1) and rows fed by plain loads (12 uint16 tokens, 24-byte rows)."""
     rng = np.random.default_rng(Q * 7 + L + tb)
     dt = np.uint8 if tb == 1 else np.uint16
     S = _prefixy(rng, 30011, L, 4, dt)
