@@ -432,6 +432,22 @@ def scan_hbm_model(Q, N, W, k, ms, peak):
             "fetch_bytes": int(f), "fetch_frac": round(f / (ms / 1e3) / 1e9 / peak, 4)}
 
 
+def scan_alu_model(Q, N, ms, sm_mhz, sms):
+    """The full scan's integer-ALU model for a batch: 2 operations per
+    (query, row) pair (compare, count) against every multiprocessor's 128
+    lanes issuing one 32-bit integer operation a clock at the sampled SM
+    clock.  The sorted-granule search of batches of 160+ queries does fewer
+    operations than this per pair, so its fraction can pass what a per-pair
+    compare could reach."""
+    if not sm_mhz or ms <= 0:
+        return None
+    ops = 2.0 * Q * N
+    pk = sms * 128 * sm_mhz * 1e6
+    return {"ops": ops, "achieved_tops": round(ops / (ms / 1e3) / 1e12, 3), "peak_tops": round(pk / 1e12, 2),
+            "frac": round(ops / (ms / 1e3) / pk, 4),
+            "peak_source": "%d SMs x 128 lanes x 1 int32 op/clock x %.0f MHz (sampled)" % (sms, sm_mhz)}
+
+
 def scan_stream_model(Q, N, ms, threads=256, sample=65536):
     """Large batches: each CTA of `threads` queries streams the 8-byte word-0
     plane of its rows from L2 into shared memory, once over a sample of
@@ -721,6 +737,8 @@ def run_ours(args, world, rank, local):
                 if name == "full_scan":
                     lat[name][str(bs)]["hbm_model_p50"] = scan_hbm_model(
                         bs, N, (L * tb + 7) // 8, k, float(np.percentile(times, 50)), peak)
+                    lat[name][str(bs)]["alu_model_p50"] = scan_alu_model(
+                        bs, N, float(np.percentile(times, 50)), clocks.get("sm_mhz"), sms)
         paths["latency_ms"] = lat
         idx.close()
         del sids, slc
