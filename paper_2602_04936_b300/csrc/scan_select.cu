@@ -16,9 +16,13 @@
 //                exact LCP of the few rows whose first tokens match: their
 //                keys go to two per-query lists, rows of LCP >= 2 (uint16
 //                tokens) and rows of LCP >= 4, each capped; rows of LCP > 4
-//                also to a per-query level histogram.  It also writes word 0
-//                of every row (the plane) for the walks.
-//   k_sel_answer a CTA per query: the level totals, d*, nA and kp.  When
+//                also to a per-query level histogram.  From 160 queries a
+//                warp sorts each full tile by word 0 first, and a query's
+//                counts and matching rows are key ranges (binary searches)
+//                instead of a pass over the tile.  It also writes word 0 of
+//                every row (the plane) for the walks.
+//   k_sel_answer a CTA per query (512 threads past one wave of 1,024-thread
+//                CTAs): the level totals, d*, nA and kp.  When
 //                every row of LCP >= d* is listed (d* >= 4, or d* >= 2 with
 //                the LCP >= 2 list complete), the list's k smallest keys are
 //                written (an 8-bit radix select for long lists, then a sort).
