@@ -528,6 +528,31 @@ __device__ void sel_sort_block(uint64_t* keys, int P) {
         }
 }
 
+// Sorts keys[0, n) when they are unique: up to 256 of them by rank (thread
+// t counts the keys below keys[t], all reading the same key at once, then
+// writes its key to that slot: two barriers), more by the bitonic sort of
+// the P >= n keys (padding included).
+__device__ void sel_sort_keys(uint64_t* keys, int n, int P) {
+    if (n > 256 || n > (int)blockDim.x) {
+        sel_sort_block(keys, P);
+        return;
+    }
+    const int t = threadIdx.x;
+    uint64_t mine = 0;
+    int rank = 0;
+    if (t < n) {
+        mine = keys[t];
+        int j = 0;
+        for (; j + 4 <= n; j += 4)
+            rank += (keys[j] < mine ? 1 : 0) + (keys[j + 1] < mine ? 1 : 0) + (keys[j + 2] < mine ? 1 : 0) +
+                    (keys[j + 3] < mine ? 1 : 0);
+        for (; j < n; ++j) rank += keys[j] < mine ? 1 : 0;
+    }
+    __syncthreads();
+    if (t < n) keys[rank] = mine;
+    __syncthreads();
+}
+
 __device__ __forceinline__ void sel_out(const SelArgs& a, int q, int j, int32_t id, int l) {
     a.out_ids[(size_t)q * a.k + j] = id;
     a.out_lcp[(size_t)q * a.k + j] = (uint8_t)l;
@@ -636,24 +661,23 @@ __global__ void __launch_bounds__(kSelAnswerWide) k_sel_answer(const SelArgs a) 
     uint64_t cv[kPickCache];
 #pragma unroll
     for (int j = 0; j < kPickCache; ++j) cv[j] = gb + j < ge ? cq[gb + j] : 0ull;
-    auto cnt_at = [&](int64_t g) -> uint64_t {
-        const int64_t j = g - gb;
-        uint64_t v = 0;
+    // fn(g, count word) over the thread's granules in order: the cached
+    // ones by constant register index, the rest from memory
+    auto each_granule = [&](auto&& fn) {
 #pragma unroll
-        for (int i = 0; i < kPickCache; ++i)
-            if (j == i) v = cv[i];
-        return j < kPickCache ? v : cq[g];
+        for (int j = 0; j < kPickCache; ++j)
+            if (gb + j < ge) fn(gb + j, cv[j]);
+        for (int64_t g = gb + kPickCache; g < ge; ++g) fn(g, cq[g]);
     };
     for (int l = tid; l <= L; l += blockDim.x) hs[l] = l > kSelDeep ? a.hist[(size_t)q * (L + 1) + l] : 0u;
     // level totals 1..4 over the granules
     uint32_t s1 = 0, s2 = 0, s3 = 0, s4 = 0;
-    for (int64_t g = gb; g < ge; ++g) {
-        const uint64_t v = cnt_at(g);
+    each_granule([&](int64_t, uint64_t v) {
         s1 += cnt_level(v, 1);
         s2 += cnt_level(v, 2);
         s3 += cnt_level(v, 3);
         s4 += cnt_level(v, 4);
-    }
+    });
     s1 = __reduce_add_sync(0xffffffffu, s1);
     s2 = __reduce_add_sync(0xffffffffu, s2);
     s3 = __reduce_add_sync(0xffffffffu, s3);
@@ -713,7 +737,7 @@ __global__ void __launch_bounds__(kSelAnswerWide) k_sel_answer(const SelArgs a) 
         while (P < n) P <<= 1;
         for (int t = n + tid; t < P; t += blockDim.x) keys[t] = kSelKeyInf;
         __syncthreads();
-        sel_sort_block(keys, P);
+        sel_sort_keys(keys, n, P);  // keys carry unique ids
         sel_write(a, q, keys, nw, nullptr, 0, dstar, tid, blockDim.x);
     };
     if ((dstar >= kSelDeep && have4) || (dstar >= 2 && have2)) {
@@ -774,7 +798,7 @@ __global__ void __launch_bounds__(kSelAnswerWide) k_sel_answer(const SelArgs a) 
         while (P < (int)nA) P <<= 1;
         for (int t = (int)nA + tid; t < P; t += blockDim.x) keys[t] = kSelKeyInf;
         __syncthreads();
-        sel_sort_block(keys, P);
+        sel_sort_keys(keys, (int)nA, P);
         for (int j = tid; j < k; j += blockDim.x) {
             if (j < (int)nA) {
                 const uint64_t v = keys[j];
@@ -805,7 +829,7 @@ __global__ void __launch_bounds__(kSelAnswerWide) k_sel_answer(const SelArgs a) 
         return dstar + 1 < lt ? cnt_level(v, dstar + 1) - cnt_level(v, lt) : 0u;
     };
     uint32_t tsum = 0;
-    for (int64_t g = gb; g < ge; ++g) tsum += tie_count(g, cnt_at(g));
+    each_granule([&](int64_t g, uint64_t c) { tsum += tie_count(g, c); });
     uint32_t v = tsum;  // inclusive scan over the block
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -834,15 +858,14 @@ __global__ void __launch_bounds__(kSelAnswerWide) k_sel_answer(const SelArgs a) 
     __syncthreads();
     {
         uint32_t run = tbase;
-        for (int64_t g = gb; g < ge; ++g) {
-            const uint64_t c = cnt_at(g);
+        each_granule([&](int64_t g, uint64_t c) {
             const uint32_t tc = tie_count(g, c), ac = a_count(c);
             if (ac > 0 || (tc > 0 && run < kp)) {
                 const uint32_t slot = atomicAdd(&sh[0], 1u);
                 if (slot < (uint32_t)(2 * k)) items[slot] = make_uint4((uint32_t)g, run, ac, 0u);
             }
             run += tc;
-        }
+        });
     }
     __syncthreads();
     const uint32_t nq = sh[0];
@@ -903,7 +926,7 @@ __global__ void __launch_bounds__(kSelAnswerWide) k_sel_answer(const SelArgs a) 
     while (P < n) P <<= 1;
     for (int t = tid; t < P; t += blockDim.x) keys[t] = t < nw_a ? abuf[t] : (t < n ? lq[t - nw_a] : kSelKeyInf);
     __syncthreads();
-    sel_sort_block(keys, P);
+    sel_sort_keys(keys, n, P);  // the walk's rows are not listed: unique ids
     for (int j = tid; j < k; j += blockDim.x) {
         if (j < n) {
             const uint64_t x = keys[j];
