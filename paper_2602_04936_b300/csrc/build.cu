@@ -51,16 +51,6 @@ __global__ void k_keys_word0(const uint8_t* __restrict__ tokens, RowFmt f, uint3
     vals[i] = i;
 }
 
-// Between the two halves of the sort: the high half of each row's word 0,
-// in the order the low-half passes left.
-__global__ void k_gather_hi(const uint32_t* __restrict__ vals, const uint32_t* __restrict__ hi_by_id, uint32_t n,
-                            uint32_t* __restrict__ key_hi) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t v = vals[i];
-    key_hi[i] = v < n ? hi_by_id[v] : 0u;
-}
-
 // The sorted ids, and eq[i] = 1 where the row at sorted position i has the
 // same word 0 as the row before it (high halves in sorted order, low halves
 // by id).
@@ -837,11 +827,9 @@ int build_sorted_ids(const void* tokens, const RowFmt& f, int64_t N64, int32_t* 
     LCP_TIMED_LAUNCH(k_keys_word0, blocks_for(N, 256), 256, 0, s, tk, f, N, ka, lo_by_id, hi_by_id, v0);
     uint32_t* ks;
     uint32_t* vs;
-    rc = radix_sort_pairs_u32(ka, v0, kb, v1, N, 32, w, s, &ks, &vs);
-    if (rc == LCP_OK) {
-        LCP_TIMED_LAUNCH(k_gather_hi, blocks_for(N, 256), 256, 0, s, vs, hi_by_id, N, ka);
-        rc = radix_sort_pairs_u32(ka, v0, kb, v1, N, 32, w, s, &ks, &vs);
-    }
+    // the low-half sort's last pass writes each row's high half as its key
+    rc = radix_sort_pairs_u32(ka, v0, kb, v1, N, 32, w, s, &ks, &vs, hi_by_id);
+    if (rc == LCP_OK) rc = radix_sort_pairs_u32(ka, v0, kb, v1, N, 32, w, s, &ks, &vs);
     if (rc) {
         cleanup();
         return rc;

@@ -2,13 +2,17 @@
 //
 // Each pass is reduce-then-scan: per-tile digit counts (warp-aggregated, so
 // that the heavily skewed digits of Zipf-distributed tokens do not serialise
-// on shared memory), one exclusive scan per digit over the tiles (which also
-// yields the digit totals and detects a constant digit, whose scatter is then
-// skipped on the device), then a kernel that derives the digit bases from the
-// totals, ranks its tile stably (warp multisplit), stages it in shared memory
-// by digit and writes it out in coalesced runs.  No CTA waits for another: a chained scan
-// with look-back serialises the first wave of tiles that start together, and
-// a sort pass has only one or two waves.
+// on shared memory), then a kernel that derives each digit's base and its
+// offset for the tile, ranks its tile stably (warp multisplit), stages it in
+// shared memory by digit and writes it out in coalesced runs.  Up to 4,096
+// tiles the count kernel also adds each tile's counts into its superblock of
+// 32 tiles, and the scatter CTA sums the superblocks before its own and the
+// tiles before it in its superblock (64 loads a thread, all in flight at
+// once); a larger sort runs one exclusive scan per digit over the tiles
+// between the two.  Either way the digit totals show a constant digit,
+// whose scatter is then skipped on the device.  No CTA waits for another: a
+// chained scan with look-back serialises the first wave of tiles that start
+// together, and a sort pass has only one or two waves.
 #include "sort.cuh"
 
 namespace lcpk {
@@ -16,6 +20,7 @@ namespace lcpk {
 using lcph::kSortItems;
 using lcph::kSortThreads;
 using lcph::kSortTile;
+using lcph::kSortSup;
 constexpr int kSortWarps = kSortThreads / 32;
 
 // Lanes of the warp whose 8-bit digit equals this lane's (invalid lanes are
@@ -48,15 +53,23 @@ __device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t* tm
     return add + x - v;
 }
 
-// Moves the result into buffer 0 when an odd number of passes ran.
+// Moves the result into buffer 0 when an odd number of passes ran, and
+// maps its keys through key_of_value when the last pass (which maps them
+// as it writes) was skipped.
 template <typename K>
 __global__ void k_result_to_buf0(const uint32_t* __restrict__ sel, int passes, const K* __restrict__ k1,
                                  const uint32_t* __restrict__ v1, K* __restrict__ k0,
-                                 uint32_t* __restrict__ v0, uint32_t n) {
-    if (!sel[passes]) return;
+                                 uint32_t* __restrict__ v0, uint32_t n,
+                                 const uint32_t* __restrict__ key_of_value) {
+    const bool in1 = sel[passes] != 0;
+    const bool map = key_of_value != nullptr && sel[passes] == sel[passes - 1];
+    if (!in1 && !map) return;
+    const K* ks = in1 ? k1 : k0;
+    const uint32_t* vs = in1 ? v1 : v0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        k0[i] = k1[i];
-        v0[i] = v1[i];
+        const uint32_t v = vs[i];
+        k0[i] = map ? (K)(v < n ? key_of_value[v] : 0u) : ks[i];
+        v0[i] = v;
     }
 }
 
@@ -65,7 +78,8 @@ template <typename K>
 __global__ void __launch_bounds__(kSortThreads) k_tile_counts(const K* kb0, const K* kb1, uint32_t n,
                                                               int pass, const uint32_t* __restrict__ skip,
                                                               const uint32_t* __restrict__ sel,
-                                                              uint32_t* __restrict__ counts, uint32_t tiles) {
+                                                              uint32_t* __restrict__ counts, uint32_t tiles,
+                                                              uint32_t* __restrict__ sup, uint32_t sups) {
     __shared__ uint32_t wh[kSortWarps][256];
     const K* __restrict__ kin = sel[pass] ? kb1 : kb0;
     const int tid = threadIdx.x;
@@ -96,7 +110,14 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_counts(const K* kb0, cons
     uint32_t t = 0;
 #pragma unroll
     for (int w = 0; w < kSortWarps; ++w) t += wh[w][tid];
-    counts[(size_t)tid * tiles + tile] = t;
+    if (sup == nullptr) {
+        counts[(size_t)tid * tiles + tile] = t;  // digit-major, for the tile scan
+    } else {
+        // tile-major (a warp's loads of one tile's counts are one line) and
+        // added into its superblock's sums
+        counts[(size_t)tile * 256 + tid] = t;
+        if (t != 0) atomicAdd(sup + ((size_t)pass * sups + tile / kSortSup) * 256 + tid, t);
+    }
 }
 
 // Exclusive scan of each digit's counts over the tiles (one CTA per digit);
@@ -135,16 +156,14 @@ __global__ void __launch_bounds__(1024) k_tile_scan(int pass, uint32_t* __restri
     }
 }
 
-// Stable scatter of one tile for pass `pass`, at the offsets from k_tile_scan.
+// Stable scatter of one tile for pass `pass`, at the offsets from the superblock
+// sums or from k_tile_scan.
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
     K* kb0, uint32_t* vb0, K* kb1, uint32_t* vb1, uint32_t n, int pass, const uint32_t* __restrict__ skip,
     uint32_t* __restrict__ sel, const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ totals,
-    uint32_t tiles, int* err) {
-    // the next pass reads the buffer this one writes, unless this one is
-    // skipped (a constant digit: nothing moves)
-    if (blockIdx.x == 0 && threadIdx.x == 0) sel[pass + 1] = skip[pass] ? sel[pass] : (sel[pass] ^ 1u);
-    if (skip[pass]) return;
+    uint32_t tiles, int* err, const uint32_t* __restrict__ sup, uint32_t sups,
+    const uint32_t* __restrict__ key_of_value) {
     const bool from1 = sel[pass] != 0;
     const K* __restrict__ kin = from1 ? kb1 : kb0;
     const uint32_t* __restrict__ vin = from1 ? vb1 : vb0;
@@ -167,8 +186,6 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
     const uint32_t base = tile * (uint32_t)kSortTile;
     const uint32_t tile_n = min((uint32_t)kSortTile, n - base);
     // every global load of the tile is issued before any ranking work
-    const uint32_t toff = offsets[(size_t)tid * tiles + tile];
-    const uint32_t dtot = totals[pass * 256 + tid];
     K key[kSortItems];
     uint32_t val[kSortItems];
 #pragma unroll
@@ -181,6 +198,47 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
         const uint32_t idx = (uint32_t)warp * (32 * kSortItems) + (uint32_t)i * 32 + lane;
         val[i] = idx < tile_n ? vin[base + idx] : 0u;
     }
+    // digit tid: its keys in the tiles before this one (toff) and in all (dtot)
+    uint32_t toff, dtot;
+    bool skipped;
+    if (sup != nullptr) {
+        // the superblock sums before this tile's superblock, then the
+        // tiles before it in its own
+        // (fixed-count predicated loops: every load is in flight at once)
+        const uint32_t sb = tile / kSortSup;
+        const uint32_t* sp = sup + (size_t)pass * sups * 256 + tid;
+        uint32_t tot = 0, pre = 0;
+        for (uint32_t j0 = 0; j0 < sups; j0 += 32) {
+            uint32_t v[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = j0 + j < sups ? sp[(size_t)(j0 + j) * 256] : 0u;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                tot += v[j];
+                pre += j0 + j < sb ? v[j] : 0u;
+            }
+        }
+        const uint32_t* cp = offsets + (size_t)sb * kSortSup * 256 + tid;
+        const uint32_t before = tile - sb * kSortSup;  // tiles of this superblock before this one
+        {
+            uint32_t v[kSortSup];
+#pragma unroll
+            for (int j = 0; j < kSortSup; ++j) v[j] = (uint32_t)j < before ? cp[j * 256] : 0u;
+#pragma unroll
+            for (int j = 0; j < kSortSup; ++j) pre += v[j];
+        }
+        toff = pre;
+        dtot = tot;
+        skipped = __syncthreads_or(tot == n) != 0;
+    } else {
+        toff = offsets[(size_t)tid * tiles + tile];
+        dtot = totals[pass * 256 + tid];
+        skipped = skip[pass] != 0;
+    }
+    // the next pass reads the buffer this one writes, unless this one is
+    // skipped (a constant digit: nothing moves)
+    if (blockIdx.x == 0 && threadIdx.x == 0) sel[pass + 1] = skipped ? sel[pass] : (sel[pass] ^ 1u);
+    if (skipped) return;
     for (int i = tid; i < kSortWarps * 256; i += kSortThreads) whist[i] = 0;
     __syncthreads();
 
@@ -233,8 +291,9 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
         uint32_t d = (uint32_t)(k >> shift) & 255u;
         uint32_t dst = goff[d] + j;
         if (dst < n) {  // always true for consistent counts; checked rather than trusted
-            kout[dst] = k;
-            vout[dst] = svals[j];
+            const uint32_t v = svals[j];
+            kout[dst] = key_of_value != nullptr ? (K)(v < n ? key_of_value[v] : 0u) : k;
+            vout[dst] = v;
         } else {
             flag_status(err, DEV_BAD);
         }
@@ -374,9 +433,12 @@ static void sort_work_carve(SortWork& w, uint32_t cap, Carver& c) {
     uint32_t nb = (cap + kCmpBlock - 1) / kCmpBlock;
     if (tiles == 0) tiles = 1;
     if (nb == 0) nb = 1;
+    const uint32_t sups = (tiles + kSortSup - 1) / kSortSup;
+    w.sups = sups <= (uint32_t)kSortMaxSups ? sups : 0u;
     c.add(&w.hist, (size_t)kMaxPasses * 256);
-    c.add(&w.skip, kMaxPasses);
+    c.add(&w.skip, kMaxPasses);  // skip, sel and sup are zeroed together
     c.add(&w.sel, kMaxPasses + 1);
+    if (w.sups) c.add(&w.sup, (size_t)kMaxPasses * 256 * w.sups);
     c.add(&w.status, (size_t)tiles * 256);
     c.add(&w.block_sums, nb);
     c.add(&w.total, 16);
@@ -420,46 +482,62 @@ void sort_work_free(SortWork& w, cudaStream_t s) {
 // Sync-free LSD radix sort: the result always ends in buffers 0.
 template <typename K>
 static int radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, uint32_t n, int key_bits,
-                           SortWork& w, cudaStream_t s, K** out_k, uint32_t** out_v) {
+                           SortWork& w, cudaStream_t s, K** out_k, uint32_t** out_v,
+                           const uint32_t* key_of_value) {
     *out_k = k0;
     *out_v = v0;
-    if (n <= 1) return LCP_OK;
+    if (n <= 1) {
+        if (n == 1 && key_of_value != nullptr) {  // the one key still maps
+            LCP_CUDA_TRY(cudaMemsetAsync(w.sel, 0, sizeof(uint32_t) * 2, s));
+            LCP_TIMED_LAUNCH(k_result_to_buf0<K>, 1, 32, 0, s, w.sel, 1, k1, v1, k0, v0, n, key_of_value);
+        }
+        return LCP_OK;
+    }
     if (n > w.cap) return LCP_ERR_INVALID;
     int passes = (key_bits + 7) / 8;
     if (passes > (int)(sizeof(K))) passes = (int)sizeof(K);
     if (passes < 1) return LCP_OK;
-    // no upfront histogram: each pass's digit totals come out of its tile
-    // scan, and constant digits are detected there
-    LCP_CUDA_TRY(cudaMemsetAsync(w.skip, 0, sizeof(uint32_t) * kMaxPasses, s));
-    LCP_CUDA_TRY(cudaMemsetAsync(w.sel, 0, sizeof(uint32_t) * (kMaxPasses + 1), s));
+    // no upfront histogram: each pass's digit totals come out of its own
+    // counts (superblock sums, or the tile scan of a larger sort), and
+    // constant digits are detected there
     const uint32_t tiles = (n + kSortTile - 1) / kSortTile;
+    const uint32_t sups = (tiles + kSortSup - 1) / kSortSup;
+    const bool fused = w.sup != nullptr && sups <= w.sups;
+    {
+        char* z0 = reinterpret_cast<char*>(w.skip);
+        char* z1 = fused ? reinterpret_cast<char*>(w.sup + (size_t)passes * 256 * sups)
+                         : reinterpret_cast<char*>(w.sel + kMaxPasses + 1);
+        LCP_CUDA_TRY(cudaMemsetAsync(z0, 0, (size_t)(z1 - z0), s));
+    }
     const size_t smem = sizeof(uint32_t) * (kSortWarps * 256 + 3 * 256 + 16) +
                         (sizeof(K) + sizeof(uint32_t)) * kSortTile;
     LCP_CUDA_TRY(cudaFuncSetAttribute(k_onesweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
+    uint32_t* sup = fused ? w.sup : nullptr;
+    const uint32_t nsup = fused ? sups : 0u;
     for (int p = 0; p < passes; ++p) {
         LCP_TIMED_LAUNCH(k_tile_counts<K>, tiles, kSortThreads, 0, s, k0, k1, n, p, w.skip, w.sel, w.status,
-                   tiles);
-        LCP_TIMED_LAUNCH(k_tile_scan, 256, 1024, 0, s, p, w.skip, w.status, tiles, w.hist, n);
+                         tiles, sup, nsup);
+        if (!fused) LCP_TIMED_LAUNCH(k_tile_scan, 256, 1024, 0, s, p, w.skip, w.status, tiles, w.hist, n);
         LCP_TIMED_LAUNCH(k_onesweep<K>, tiles, kSortThreads, smem, s, k0, v0, k1, v1, n, p, w.skip, w.sel,
-                   w.status, w.hist, tiles, w.err);
+                         w.status, w.hist, tiles, w.err, sup, nsup, p == passes - 1 ? key_of_value : nullptr);
     }
     unsigned cg = (unsigned)((n + 255) / 256);
     if (cg > (unsigned)sm_count() * 8) cg = sm_count() * 8;
-    LCP_TIMED_LAUNCH(k_result_to_buf0<K>, cg, 256, 0, s, w.sel, passes, k1, v1, k0, v0, n);
+    LCP_TIMED_LAUNCH(k_result_to_buf0<K>, cg, 256, 0, s, w.sel, passes, k1, v1, k0, v0, n, key_of_value);
     return LCP_OK;
 }
 
 int radix_sort_pairs_u64(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, uint32_t n,
                          int key_bits, SortWork& w, cudaStream_t s, uint64_t** out_k,
                          uint32_t** out_v) {
-    return radix_sort_impl<uint64_t>(k0, v0, k1, v1, n, key_bits, w, s, out_k, out_v);
+    return radix_sort_impl<uint64_t>(k0, v0, k1, v1, n, key_bits, w, s, out_k, out_v, nullptr);
 }
 
 int radix_sort_pairs_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t n,
                          int key_bits, SortWork& w, cudaStream_t s, uint32_t** out_k,
-                         uint32_t** out_v) {
-    return radix_sort_impl<uint32_t>(k0, v0, k1, v1, n, key_bits, w, s, out_k, out_v);
+                         uint32_t** out_v, const uint32_t* key_of_value) {
+    return radix_sort_impl<uint32_t>(k0, v0, k1, v1, n, key_bits, w, s, out_k, out_v, key_of_value);
 }
 
 int tie_compact_async(const uint8_t* eq, uint32_t n, uint32_t* out_idx, uint32_t* out_grp, SortWork& w,

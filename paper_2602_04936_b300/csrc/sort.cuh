@@ -9,6 +9,11 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per onesweep tile
 constexpr int kMaxPasses = 8;                         // 8-bit digits of a 64-bit key
+// Tiles of a superblock: a sort of up to kSortSup * kSortMaxSups tiles takes
+// each tile's digit offsets from the superblock sums its count pass adds up
+// (no separate scan kernel); a larger one scans the per-tile counts.
+constexpr int kSortSup = 32;
+constexpr int kSortMaxSups = 128;
 
 // Device scratch for sorting up to `cap` pairs (allocated stream-ordered).
 struct SortWork {
@@ -16,7 +21,10 @@ struct SortWork {
     uint32_t* hist = nullptr;        // [kMaxPasses][256] digit totals of each pass
     uint32_t* skip = nullptr;        // [kMaxPasses] 1 if the pass's digit is constant
     uint32_t* sel = nullptr;         // [kMaxPasses + 1] buffer each pass reads (device-decided)
-    uint32_t* status = nullptr;      // [256][tiles] per-tile digit counts, then offsets
+    uint32_t* status = nullptr;      // per-tile digit counts: [256][tiles] (then offsets) when scanned,
+                                     // else [tiles][256]
+    uint32_t* sup = nullptr;         // [kMaxPasses][sups][256] digit counts of each superblock of tiles
+    uint32_t sups = 0;               // superblocks of the largest sort (0: the scan is used)
     uint64_t* block_sums = nullptr;  // compaction: per-block (active, starts) counts
     uint32_t* total = nullptr;       // compaction result count (device)
     uint32_t* h_total = nullptr;     // pinned host mirror of total + skip flags
@@ -33,13 +41,15 @@ void sort_work_free(SortWork& w, cudaStream_t s);
 // Stable LSD radix sort of (key, value) pairs by the low `key_bits` bits of
 // the key.  Buffers 0 hold the input and receive the result (out_k / out_v
 // point at them); buffers 1 are scratch.  Digits equal for every key are
-// skipped on the device; the call never waits for the device.
+// skipped on the device; the call never waits for the device.  With
+// key_of_value (32-bit keys only), the result's keys are replaced by
+// key_of_value[value] (values < n), written by the last pass.
 int radix_sort_pairs_u64(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, uint32_t n,
                          int key_bits, SortWork& w, cudaStream_t s, uint64_t** out_k,
                          uint32_t** out_v);
 int radix_sort_pairs_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t n,
                          int key_bits, SortWork& w, cudaStream_t s, uint32_t** out_k,
-                         uint32_t** out_v);
+                         uint32_t** out_v, const uint32_t* key_of_value = nullptr);
 
 // Tie compaction: given eq[i] (element i equals element i-1 on the compared
 // prefix; eq[0] = 0), the "active" elements are those in a run of length >= 2.
