@@ -65,7 +65,8 @@ struct SelArgs {
     int32_t* out_ids;   // [Q][k]
     uint8_t* out_lcp;   // [Q][k]
     int* status;
-    int sorted;         // full tiles are sorted by their first 32 bits and searched
+    int sorted;         // full tiles are sorted by word 0 and searched
+    int stages;         // ring stages a warp (the CTA's warps: blockDim.x / 32)
 };
 
 __device__ __forceinline__ uint64_t sel_key(int l, int64_t id) {
@@ -94,7 +95,7 @@ __device__ __forceinline__ void sel_tile_copy(const CUtensorMap* tm, void* dst, 
 }
 
 // Each warp runs its own pipeline over tiles gw, gw + W, ... (gw its index
-// in the grid, W the warps of the grid): a ring of kSelWarpStages tile
+// in the grid, W the warps of the grid): a ring of tile
 // buffers filled by tensor copies that its lane 0 issues, each tile
 // converted in place (most significant token first) by the warp, then
 // scanned by every chunk of 32 queries (a lane each, the tile's words read
@@ -102,17 +103,23 @@ __device__ __forceinline__ void sel_tile_copy(const CUtensorMap* tm, void* dst, 
 // 32 bits match a query's get their exact LCP at once (word 1 is in the
 // tile); those to be listed wait in a per-warp queue whose appends (global
 // atomics) the warp issues together, 32 a round, once the queue might not
-// hold another step's rows and at the end of the tile.  Dynamic shared memory: the
-// warps' rings, their queues, then the batch's words 0 and 1 (Q x 16 bytes)
-// and two list-full flags per query.
-constexpr int kSelCountWarps = 8;
+// hold another step's rows and at the end of the tile.  Compared tiles run
+// 8 warps a CTA with 2 ring stages each; sorted tiles 12 warps with one
+// (1,024 queries: count 0.336 -> 0.301 ms).  Dynamic shared memory: the
+// warps' rings, their queues, their tile's upper halves and sorted rows,
+// then the batch's words 0 and 1 (Q x 16 bytes) and two list-full flags per
+// query.
+constexpr int kSelCountWarps = 8;   // compared tiles: 8 warps a CTA, 2 ring stages a warp
 constexpr int kSelWarpStages = 2;
+// Sorted tiles (larger batches) take far longer to work through than to
+// arrive, so one ring stage a warp is enough, and the shared memory saved
+// holds 12 warps a CTA (24 a multiprocessor instead of 16).
+constexpr int kSelSortedWarps = 12;
+constexpr int kSelSortedStages = 1;
+constexpr int kSelMaxWarps = 12;
+constexpr int kSelMaxStages = 2;
 constexpr int kSelQueue = 512;  // queued rows per warp
 constexpr int kSelStep = 256;  // most rows one 8-row step of 32 queries can queue
-constexpr size_t kSelRingBytes = (size_t)kSelCountWarps * kSelWarpStages * kSelRows * 16;
-constexpr size_t kSelQueueBytes = (size_t)kSelCountWarps * kSelQueue * sizeof(uint32_t);
-constexpr size_t kSelHiBytes = (size_t)kSelCountWarps * kSelRows * sizeof(uint32_t);
-constexpr size_t kSelRowIdxBytes = (size_t)kSelCountWarps * kSelRows;  // a tile's rows in key order
 // Batches from this size up search sorted tiles: sorting a tile by its
 // 64-bit word 0 costs about as much as comparing four or five 32-query
 // chunks with its rows, and every chunk then takes a few binary searches
@@ -120,8 +127,15 @@ constexpr size_t kSelRowIdxBytes = (size_t)kSelCountWarps * kSelRows;  // a tile
 // 128 queries 0.162 ms compared, 0.178 sorted; 192 queries 0.229 / 0.206).
 constexpr int kSelSortedMinQ = 160;
 
-__host__ __device__ constexpr size_t sel_count_smem(int Q) {
-    return kSelRingBytes + kSelQueueBytes + kSelHiBytes + kSelRowIdxBytes + (size_t)Q * (2 * sizeof(uint64_t) + 2);
+// Per warp: its ring, its queue, a tile's upper halves of word 0 and (sorted
+// tiles) its rows in key order; then the batch's words 0 and 1 and two
+// list-full flags per query.
+__host__ __device__ constexpr size_t sel_warp_smem(int stages) {
+    return (size_t)stages * kSelRows * 16 + (size_t)kSelQueue * sizeof(uint32_t) + (size_t)kSelRows * sizeof(uint32_t) +
+           (size_t)kSelRows;
+}
+__host__ __device__ constexpr size_t sel_count_smem(int Q, int warps, int stages) {
+    return (size_t)warps * sel_warp_smem(stages) + (size_t)Q * (2 * sizeof(uint64_t) + 2);
 }
 
 // One in-lane stage (distance J < 8) of the bitonic network below.
@@ -208,30 +222,34 @@ __device__ __forceinline__ int range_at_most(const uint32_t* lw, int b, int e, u
 }
 
 template <int TB>
-__global__ void __launch_bounds__(kSelCountWarps * 32, 2) k_sel_count(const __grid_constant__ CUtensorMap tm,
+__global__ void __launch_bounds__(kSelMaxWarps * 32, 2) k_sel_count(const __grid_constant__ CUtensorMap tm,
                                                                    const SelArgs a, int use_tma) {
     extern __shared__ __align__(128) uint64_t dyn[];
-    __shared__ __align__(8) uint64_t bar[kSelCountWarps][kSelWarpStages];
-    __shared__ uint32_t qn[kSelCountWarps];
+    __shared__ __align__(8) uint64_t bar[kSelMaxWarps][kSelMaxStages];
+    __shared__ uint32_t qn[kSelMaxWarps];
     const int warp = threadIdx.x >> 5;
     const unsigned lane = lane_id();
-    uint64_t (*ring)[kSelRows][2] = reinterpret_cast<uint64_t (*)[kSelRows][2]>(dyn) + warp * kSelWarpStages;
-    uint32_t* queue = reinterpret_cast<uint32_t*>(dyn + kSelRingBytes / sizeof(uint64_t)) + warp * kSelQueue;
+    const int nwarps = (int)(blockDim.x >> 5);
+    const int stages = a.stages;
+    char* const base = reinterpret_cast<char*>(dyn);
+    const size_t ring_b = (size_t)nwarps * stages * kSelRows * 16;
+    const size_t queue_b = (size_t)nwarps * kSelQueue * sizeof(uint32_t);
+    const size_t hi_b = (size_t)nwarps * kSelRows * sizeof(uint32_t);
+    const size_t row_b = (size_t)nwarps * kSelRows;
+    uint64_t (*ring)[kSelRows][2] = reinterpret_cast<uint64_t (*)[kSelRows][2]>(dyn) + warp * stages;
+    uint32_t* queue = reinterpret_cast<uint32_t*>(base + ring_b) + warp * kSelQueue;
     // the current tile's upper halves of word 0, contiguous: four rows a 16-byte load
-    uint32_t* hiw = reinterpret_cast<uint32_t*>(dyn + (kSelRingBytes + kSelQueueBytes) / sizeof(uint64_t)) +
-                    warp * kSelRows;
+    uint32_t* hiw = reinterpret_cast<uint32_t*>(base + ring_b + queue_b) + warp * kSelRows;
     // a sorted tile's rows in the order of their sorted keys (kept in hiw)
-    uint8_t* srow = reinterpret_cast<uint8_t*>(dyn + (kSelRingBytes + kSelQueueBytes + kSelHiBytes) / sizeof(uint64_t)) +
-                    warp * kSelRows;
-    uint64_t* qword0 =
-        dyn + (kSelRingBytes + kSelQueueBytes + kSelHiBytes + kSelRowIdxBytes) / sizeof(uint64_t);  // [Q] word 0
-    uint64_t* qword1 = qword0 + a.Q;                                                // [Q] and word 1
+    uint8_t* srow = reinterpret_cast<uint8_t*>(base + ring_b + queue_b + hi_b) + warp * kSelRows;
+    uint64_t* qword0 = reinterpret_cast<uint64_t*>(base + ring_b + queue_b + hi_b + row_b);  // [Q] word 0
+    uint64_t* qword1 = qword0 + a.Q;                                                          // [Q] and word 1
     uint8_t* full = reinterpret_cast<uint8_t*>(qword1 + a.Q);  // [Q][2]: list2 / list4 seen full
     uint64_t* wb = bar[warp];
     const RowFmt& f = a.f;
     const int64_t ntiles = a.ngran;
-    const int64_t gw = (int64_t)blockIdx.x * kSelCountWarps + warp;
-    const int64_t nw = (int64_t)gridDim.x * kSelCountWarps;
+    const int64_t gw = (int64_t)blockIdx.x * nwarps + warp;
+    const int64_t nw = (int64_t)gridDim.x * nwarps;
     const int nch = (a.Q + 31) / 32;
     const int L = f.L;
     // levels above L never occur: their thresholds are out of reach
@@ -246,13 +264,13 @@ __global__ void __launch_bounds__(kSelCountWarps * 32, 2) k_sel_count(const __gr
     if (lane == 0) {
         qn[warp] = 0;
         if (use_tma) {
-            for (int s = 0; s < kSelWarpStages; ++s) mbar_init(&wb[s], 1);
+            for (int s = 0; s < stages; ++s) mbar_init(&wb[s], 1);
             fence_proxy_async_smem();
         }
     }
     __syncthreads();
     if (use_tma && lane == 0)
-        for (int s = 0; s < kSelWarpStages; ++s) {
+        for (int s = 0; s < stages; ++s) {
             const int64_t t = gw + (int64_t)s * nw;
             if (t < ntiles) sel_tile_copy(&tm, ring[s], (int)(t * kSelRows), &wb[s]);
         }
@@ -293,13 +311,13 @@ __global__ void __launch_bounds__(kSelCountWarps * 32, 2) k_sel_count(const __gr
     int it = 0;
     bool bad = false;
     for (int64_t t = gw; t < ntiles; t += nw, ++it) {
-        const int s = it % kSelWarpStages;
+        const int s = it % stages;
         const int64_t r0 = t * kSelRows;
         const int nrows = a.N - r0 < kSelRows ? (int)(a.N - r0) : kSelRows;
         uint64_t (*buf)[2] = ring[s];
         if (use_tma) {
             bool ok = true;
-            if (lane == 0) ok = mbar_wait(&wb[s], (uint32_t)((it / kSelWarpStages) & 1), kSpinLimit);
+            if (lane == 0) ok = mbar_wait(&wb[s], (uint32_t)((it / stages) & 1), kSpinLimit);
             if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) {
                 bad = true;
                 break;
@@ -488,7 +506,7 @@ __global__ void __launch_bounds__(kSelCountWarps * 32, 2) k_sel_count(const __gr
         if (qn[warp] != 0) flush(r0);  // the queued rows name rows of this tile
         __syncwarp();  // every lane is done with the buffer
         if (use_tma && lane == 0) {
-            const int64_t tn = t + (int64_t)kSelWarpStages * nw;
+            const int64_t tn = t + (int64_t)stages * nw;
             // the warp's reads and in-place writes come before the copy's writes
             fence_proxy_async_smem();
             if (tn < ntiles) sel_tile_copy(&tm, ring[s], (int)(tn * kSelRows), &wb[s]);
@@ -497,10 +515,10 @@ __global__ void __launch_bounds__(kSelCountWarps * 32, 2) k_sel_count(const __gr
     if (bad && lane == 0) {
         flag_status(a.status, DEV_TIMEOUT);
         // copies still in flight land before the CTA's shared memory is reused
-        for (int j = 0; j < kSelWarpStages; ++j) {
+        for (int j = 0; j < stages; ++j) {
             const int i = it + j;
             const int64_t t = gw + (int64_t)i * nw;
-            if (t < ntiles) (void)mbar_wait(&wb[i % kSelWarpStages], (uint32_t)((i / kSelWarpStages) & 1), kSpinLimit);
+            if (t < ntiles) (void)mbar_wait(&wb[i % stages], (uint32_t)((i / stages) & 1), kSpinLimit);
         }
     }
 }
@@ -985,9 +1003,9 @@ static size_t sel_answer_smem(int k) { return kSelList * sizeof(uint64_t) + (siz
 
 // Per-device launch set-up, done once: the answer kernel's shared-memory limit (k up
 // to LCP_SCAN_MAX_K) and the count kernel's resident CTAs per multiprocessor
-// at the largest batch.
+// at the largest batch, for both of its shapes.
 struct SelSetup {
-    int count_ctas[2] = {0, 0};  // uint8, uint16 tokens
+    int count_ctas[2][2] = {{0, 0}, {0, 0}};  // [uint8, uint16 tokens][compared, sorted tiles]
     bool ok = false;
 };
 
@@ -999,22 +1017,32 @@ static const SelSetup* sel_setup() {
     std::lock_guard<std::mutex> lk(mu);
     SelSetup& x = st[dev];
     if (x.ok) return &x;
-    const size_t count_smem = sel_count_smem((int)kSelMaxQ);
-    if (cudaFuncSetAttribute(k_sel_answer, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sel_answer_smem(LCP_SCAN_MAX_K)) != cudaSuccess ||
-        cudaFuncSetAttribute(k_sel_count<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)count_smem) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_sel_count<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)count_smem) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x.count_ctas[0], k_sel_count<1>, kSelCountWarps * 32,
-                                                      count_smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x.count_ctas[1], k_sel_count<2>, kSelCountWarps * 32,
-                                                      count_smem) != cudaSuccess) {
+    const int warps[2] = {kSelCountWarps, kSelSortedWarps}, stages[2] = {kSelWarpStages, kSelSortedStages};
+    size_t most = 0;
+    for (int c = 0; c < 2; ++c) {
+        const size_t b = sel_count_smem((int)kSelMaxQ, warps[c], stages[c]);
+        if (b > most) most = b;
+    }
+    bool ok = cudaFuncSetAttribute(k_sel_answer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sel_answer_smem(LCP_SCAN_MAX_K)) == cudaSuccess &&
+              cudaFuncSetAttribute(k_sel_count<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most) ==
+                  cudaSuccess &&
+              cudaFuncSetAttribute(k_sel_count<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most) ==
+                  cudaSuccess;
+    for (int c = 0; ok && c < 2; ++c) {
+        const size_t b = sel_count_smem((int)kSelMaxQ, warps[c], stages[c]);
+        ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x.count_ctas[0][c], k_sel_count<1>, warps[c] * 32, b) ==
+                 cudaSuccess &&
+             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x.count_ctas[1][c], k_sel_count<2>, warps[c] * 32, b) ==
+                 cudaSuccess;
+    }
+    if (!ok) {
         cudaGetLastError();
         return nullptr;
     }
-    for (int& c : x.count_ctas)
-        if (c < 1) c = 1;
+    for (auto& row : x.count_ctas)
+        for (int& c : row)
+            if (c < 1) c = 1;
     x.ok = true;
     return &x;
 }
@@ -1056,14 +1084,17 @@ int scan_select(const void* d_tokens, int64_t N, const RowFmt& f, const void* d_
     if (e == cudaSuccess && !su) e = cudaErrorUnknown;
     if (e == cudaSuccess) {
         // one wave of count CTAs (each warp walks its tiles through its ring)
-        const int64_t ctas = (int64_t)sm_count() * (f.tb == 2 ? su->count_ctas[1] : su->count_ctas[0]);
-        const int64_t want = (a.ngran + kSelCountWarps - 1) / kSelCountWarps;
+        const int shape = a.sorted ? 1 : 0;
+        const int warps = a.sorted ? kSelSortedWarps : kSelCountWarps;
+        a.stages = a.sorted ? kSelSortedStages : kSelWarpStages;
+        const int64_t ctas = (int64_t)sm_count() * su->count_ctas[f.tb == 2 ? 1 : 0][shape];
+        const int64_t want = (a.ngran + warps - 1) / warps;
         const unsigned grid = (unsigned)(want < ctas ? want : ctas);
-        const size_t count_smem = sel_count_smem((int)Q);
+        const size_t count_smem = sel_count_smem((int)Q, warps, a.stages);
         if (f.tb == 2)
-            LCP_TIMED_LAUNCH(k_sel_count<2>, grid, kSelCountWarps * 32, count_smem, s, tm, a, use_tma);
+            LCP_TIMED_LAUNCH(k_sel_count<2>, grid, warps * 32, count_smem, s, tm, a, use_tma);
         else
-            LCP_TIMED_LAUNCH(k_sel_count<1>, grid, kSelCountWarps * 32, count_smem, s, tm, a, use_tma);
+            LCP_TIMED_LAUNCH(k_sel_count<1>, grid, warps * 32, count_smem, s, tm, a, use_tma);
         // a batch that fits in one wave of wide CTAs (two a multiprocessor)
         // gives each query 1,024 threads; a larger one runs narrower CTAs,
         // four a multiprocessor
