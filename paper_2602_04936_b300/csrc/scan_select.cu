@@ -103,28 +103,25 @@ __device__ __forceinline__ void sel_tile_copy(const CUtensorMap* tm, void* dst, 
 // 32 bits match a query's get their exact LCP at once (word 1 is in the
 // tile); those to be listed wait in a per-warp queue whose appends (global
 // atomics) the warp issues together, 32 a round, once the queue might not
-// hold another step's rows and at the end of the tile.  Compared tiles run
-// 8 warps a CTA with 2 ring stages each; sorted tiles 12 warps with one
-// (1,024 queries: count 0.336 -> 0.301 ms).  Dynamic shared memory: the
+// hold another step's rows and at the end of the tile.  Dynamic shared memory: the
 // warps' rings, their queues, their tile's upper halves and sorted rows,
 // then the batch's words 0 and 1 (Q x 16 bytes) and two list-full flags per
 // query.
-constexpr int kSelCountWarps = 8;   // compared tiles: 8 warps a CTA, 2 ring stages a warp
-constexpr int kSelWarpStages = 2;
-// Sorted tiles (larger batches) take far longer to work through than to
-// arrive, so one ring stage a warp is enough, and the shared memory saved
-// holds 12 warps a CTA (24 a multiprocessor instead of 16).
-constexpr int kSelSortedWarps = 12;
-constexpr int kSelSortedStages = 1;
-constexpr int kSelMaxWarps = 12;
-constexpr int kSelMaxStages = 2;
+// 12 warps a CTA with one ring stage each: 24 warps a multiprocessor (two
+// CTAs fit the shared memory) with 24 tiles in flight, against 16 warps with
+// two stages each (1 query 0.088 -> 0.086 ms, 32: 0.095 -> 0.092, 1,024
+// sorted: 0.477 -> 0.439).
+constexpr int kSelCountWarps = 12;
+constexpr int kSelWarpStages = 1;
+constexpr int kSelMaxWarps = kSelCountWarps;
+constexpr int kSelMaxStages = kSelWarpStages;
 constexpr int kSelQueue = 512;  // queued rows per warp
 constexpr int kSelStep = 256;  // most rows one 8-row step of 32 queries can queue
 // Batches from this size up search sorted tiles: sorting a tile by its
 // 64-bit word 0 costs about as much as comparing four or five 32-query
 // chunks with its rows, and every chunk then takes a few binary searches
 // instead of a pass over the rows (measured on 2M rows of 64 uint16 tokens:
-// 128 queries 0.162 ms compared, 0.178 sorted; 192 queries 0.229 / 0.206).
+// 160 queries 0.179 ms compared, 0.174 sorted; 192 queries 0.203 / 0.186).
 constexpr int kSelSortedMinQ = 160;
 
 // Per warp: its ring, its queue, a tile's upper halves of word 0 and (sorted
@@ -1003,9 +1000,9 @@ static size_t sel_answer_smem(int k) { return kSelList * sizeof(uint64_t) + (siz
 
 // Per-device launch set-up, done once: the answer kernel's shared-memory limit (k up
 // to LCP_SCAN_MAX_K) and the count kernel's resident CTAs per multiprocessor
-// at the largest batch, for both of its shapes.
+// at the largest batch.
 struct SelSetup {
-    int count_ctas[2][2] = {{0, 0}, {0, 0}};  // [uint8, uint16 tokens][compared, sorted tiles]
+    int count_ctas[2] = {0, 0};  // uint8, uint16 tokens
     bool ok = false;
 };
 
@@ -1017,32 +1014,22 @@ static const SelSetup* sel_setup() {
     std::lock_guard<std::mutex> lk(mu);
     SelSetup& x = st[dev];
     if (x.ok) return &x;
-    const int warps[2] = {kSelCountWarps, kSelSortedWarps}, stages[2] = {kSelWarpStages, kSelSortedStages};
-    size_t most = 0;
-    for (int c = 0; c < 2; ++c) {
-        const size_t b = sel_count_smem((int)kSelMaxQ, warps[c], stages[c]);
-        if (b > most) most = b;
-    }
-    bool ok = cudaFuncSetAttribute(k_sel_answer, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)sel_answer_smem(LCP_SCAN_MAX_K)) == cudaSuccess &&
-              cudaFuncSetAttribute(k_sel_count<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most) ==
-                  cudaSuccess &&
-              cudaFuncSetAttribute(k_sel_count<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most) ==
-                  cudaSuccess;
-    for (int c = 0; ok && c < 2; ++c) {
-        const size_t b = sel_count_smem((int)kSelMaxQ, warps[c], stages[c]);
-        ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x.count_ctas[0][c], k_sel_count<1>, warps[c] * 32, b) ==
-                 cudaSuccess &&
-             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x.count_ctas[1][c], k_sel_count<2>, warps[c] * 32, b) ==
-                 cudaSuccess;
-    }
-    if (!ok) {
+    const size_t count_smem = sel_count_smem((int)kSelMaxQ, kSelCountWarps, kSelWarpStages);
+    if (cudaFuncSetAttribute(k_sel_answer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sel_answer_smem(LCP_SCAN_MAX_K)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_sel_count<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)count_smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_sel_count<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)count_smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x.count_ctas[0], k_sel_count<1>, kSelCountWarps * 32,
+                                                      count_smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x.count_ctas[1], k_sel_count<2>, kSelCountWarps * 32,
+                                                      count_smem) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
-    for (auto& row : x.count_ctas)
-        for (int& c : row)
-            if (c < 1) c = 1;
+    for (int& c : x.count_ctas)
+        if (c < 1) c = 1;
     x.ok = true;
     return &x;
 }
@@ -1084,10 +1071,9 @@ int scan_select(const void* d_tokens, int64_t N, const RowFmt& f, const void* d_
     if (e == cudaSuccess && !su) e = cudaErrorUnknown;
     if (e == cudaSuccess) {
         // one wave of count CTAs (each warp walks its tiles through its ring)
-        const int shape = a.sorted ? 1 : 0;
-        const int warps = a.sorted ? kSelSortedWarps : kSelCountWarps;
-        a.stages = a.sorted ? kSelSortedStages : kSelWarpStages;
-        const int64_t ctas = (int64_t)sm_count() * su->count_ctas[f.tb == 2 ? 1 : 0][shape];
+        const int warps = kSelCountWarps;
+        a.stages = kSelWarpStages;
+        const int64_t ctas = (int64_t)sm_count() * su->count_ctas[f.tb == 2 ? 1 : 0];
         const int64_t want = (a.ngran + warps - 1) / warps;
         const unsigned grid = (unsigned)(want < ctas ? want : ctas);
         const size_t count_smem = sel_count_smem((int)Q, warps, a.stages);
