@@ -582,9 +582,27 @@ __device__ __forceinline__ void topk_fill(const DevIndex& ix, WA& S, const FillR
             }
 #pragma unroll
             for (int e = 0; e < 4; ++e) keep[e] = v[e] != kInf && (ps[e] < loc || ps[e] >= hic);
-            ntake = compact4(v, keep, S.m1, kp);
+            // the kept ids (ascending) straight into slots nA, nA + 1, ...
+            const unsigned ltm = lanemask_lt();
+            int cnt = 0;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const unsigned m = __ballot_sync(0xffffffffu, keep[e]);
+                const int r = cnt + __popc(m & ltm);
+                if (keep[e] && r < kp) {
+                    __stcs(oid + nA + r, (int)v[e]);
+                    __stcs(reinterpret_cast<char*>(olcp) + nA + r, (char)dstar);
+                }
+                cnt += __popc(m);
+            }
+            ntake = cnt < kp ? cnt : kp;
+            // slots past the fill: padding
+            for (int t = nA + ntake + (int)lane; t < k; t += 32) {
+                __stcs(oid + t, -1);
+                __stcs(reinterpret_cast<char*>(olcp) + t, (char)0);
+            }
             __syncwarp();
-            filled = true;
+            return;
         }
     }
     if (!filled) {
