@@ -70,10 +70,12 @@ __device__ __forceinline__ int finish_chunk(int& h, bool ok, int n, int avail, u
 // Id-order probe for a large tie level: walks ids 0, 1, 2, ... through pos[]
 // (the low ids' positions are hot in L2 for every query), keeping ids whose
 // sorted position lies in [lov, hiv) but outside A = [loc, hic).  Ascending
-// by construction.  At most 8 rounds of 256 ids; returns false when that did
-// not find kp of them (the caller then uses the sparse-table path).
+// by construction, written straight into the fill's output slots (oid and
+// olcp point at the first).  At most 8 rounds of 256 ids; returns false when
+// that did not find kp of them (the caller then uses the sparse-table path,
+// which rewrites the same slots).
 __device__ bool probe_ids(const DevIndex& ix, int64_t lov, int64_t hiv, int64_t loc, int64_t hic,
-                          int kp, uint32_t* dst, int* ntake) {
+                          int kp, int32_t* __restrict__ oid, uint8_t* __restrict__ olcp, int dstar, int* ntake) {
     const unsigned lane = lane_id();
     const unsigned lt = lanemask_lt();
     int cnt = 0;
@@ -91,7 +93,10 @@ __device__ bool probe_ids(const DevIndex& ix, int64_t lov, int64_t hiv, int64_t 
             const bool keep = x >= lov && x < hiv && (x < loc || x >= hic);
             const unsigned m = __ballot_sync(0xffffffffu, keep);
             const int r = cnt + __popc(m & lt);
-            if (keep && r < kp) dst[r] = (uint32_t)(base + lane + 32 * e);
+            if (keep && r < kp) {
+                __stcs(oid + r, (int)(base + lane + 32 * e));
+                __stcs(reinterpret_cast<char*>(olcp) + r, (char)dstar);
+            }
             cnt += __popc(m);
         }
         if (cnt >= kp) {
@@ -549,6 +554,25 @@ __device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, WA& S, int p,
 
 // Second half of a query: 4. the tie fill (first kp ids of the level-d*
 // interval outside A) and 5b. slots [nA, k): the fill, then padding.
+// Writes the kept ids of v (ascending across e, then lanes) into slots
+// 0, 1, ... of the fill's output (at most kp of them); returns how many.
+__device__ __forceinline__ int fill_write4(const uint32_t (&v)[4], const bool (&keep)[4], int kp,
+                                           int32_t* __restrict__ oid, uint8_t* __restrict__ olcp, int dstar) {
+    const unsigned ltm = lanemask_lt();
+    int cnt = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const unsigned m = __ballot_sync(0xffffffffu, keep[e]);
+        const int r = cnt + __popc(m & ltm);
+        if (keep[e] && r < kp) {
+            __stcs(oid + r, (int)v[e]);
+            __stcs(reinterpret_cast<char*>(olcp) + r, (char)dstar);
+        }
+        cnt += __popc(m);
+    }
+    return cnt < kp ? cnt : kp;
+}
+
 template <typename WA>
 __device__ __forceinline__ void topk_fill(const DevIndex& ix, WA& S, const FillRec& r, int k,
                                           int32_t* __restrict__ oid, uint8_t* __restrict__ olcp) {
@@ -562,7 +586,8 @@ __device__ __forceinline__ void topk_fill(const DevIndex& ix, WA& S, const FillR
     bool filled = kp <= 0;
     // a tie level holding a large share of all rows: probe ids in order
     // (expected <= 6 chunks of 128 ids)
-    if (!filled && (int64_t)kp * N <= nT * 768) filled = probe_ids(ix, lov, hiv, loc, hic, kp, S.m1, &ntake);
+    if (!filled && (int64_t)kp * N <= nT * 768)
+        filled = probe_ids(ix, lov, hiv, loc, hic, kp, oid + nA, olcp + nA, dstar, &ntake);
     // a heavy trie node: its precomputed K smallest ids (with their sorted
     // positions), minus A's members
     if (!filled && hiv - lov > kBlk) {
@@ -583,26 +608,8 @@ __device__ __forceinline__ void topk_fill(const DevIndex& ix, WA& S, const FillR
 #pragma unroll
             for (int e = 0; e < 4; ++e) keep[e] = v[e] != kInf && (ps[e] < loc || ps[e] >= hic);
             // the kept ids (ascending) straight into slots nA, nA + 1, ...
-            const unsigned ltm = lanemask_lt();
-            int cnt = 0;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const unsigned m = __ballot_sync(0xffffffffu, keep[e]);
-                const int r = cnt + __popc(m & ltm);
-                if (keep[e] && r < kp) {
-                    __stcs(oid + nA + r, (int)v[e]);
-                    __stcs(reinterpret_cast<char*>(olcp) + nA + r, (char)dstar);
-                }
-                cnt += __popc(m);
-            }
-            ntake = cnt < kp ? cnt : kp;
-            // slots past the fill: padding
-            for (int t = nA + ntake + (int)lane; t < k; t += 32) {
-                __stcs(oid + t, -1);
-                __stcs(reinterpret_cast<char*>(olcp) + t, (char)0);
-            }
-            __syncwarp();
-            return;
+            ntake = fill_write4(v, keep, kp, oid + nA, olcp + nA, dstar);
+            filled = true;
         }
     }
     if (!filled) {
@@ -621,18 +628,12 @@ __device__ __forceinline__ void topk_fill(const DevIndex& ix, WA& S, const FillR
 #pragma unroll
         for (int e = 0; e < 4; ++e) keep[e] = v[e] != kInf && (ps[e] < loc || ps[e] >= hic);
         __syncwarp();
-        ntake = compact4(v, keep, S.m1, kp);
-        __syncwarp();
+        ntake = fill_write4(v, keep, kp, oid + nA, olcp + nA, dstar);
     }
-    for (int t = nA + (int)lane; t < k; t += 32) {
-        int32_t id = -1;
-        uint8_t l = 0;
-        if (t < nA + ntake) {
-            id = (int32_t)S.m1[t - nA];
-            l = (uint8_t)dstar;
-        }
-        __stcs(oid + t, (int)id);
-        __stcs(reinterpret_cast<char*>(olcp) + t, (char)l);
+    // slots past the fill: padding
+    for (int t = nA + ntake + (int)lane; t < k; t += 32) {
+        __stcs(oid + t, -1);
+        __stcs(reinterpret_cast<char*>(olcp) + t, (char)0);
     }
     __syncwarp();
 }
