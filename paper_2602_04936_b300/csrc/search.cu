@@ -67,6 +67,24 @@ __device__ __forceinline__ int finish_chunk(int& h, bool ok, int n, int avail, u
     return avail - n < 32 ? avail - n : 32;
 }
 
+// First round of a side: lane l holds the steps of items 2l and 2l + 1
+// (255 where absent); they become the items' LCPs with q (the running
+// minimum outward) and are stored into lam[2l], lam[2l + 1].
+__device__ __forceinline__ void first_pair_scan(int& a, int& b, uint8_t* lam) {
+    const unsigned lane = lane_id();
+    int m = min(a, b);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, m, o);
+        if (lane >= (unsigned)o) m = min(m, y);
+    }
+    int e = __shfl_up_sync(0xffffffffu, m, 1);  // the items before 2l
+    if (lane == 0) e = 255;
+    a = min(e, a);
+    b = m;
+    reinterpret_cast<uint16_t*>(lam)[lane] = (uint16_t)((a & 255) | ((b & 255) << 8));
+}
+
 // Id-order probe for a large tie level: walks ids 0, 1, 2, ... through pos[]
 // (the low ids' positions are hot in L2 for every query), keeping ids whose
 // sorted position lies in [lov, hiv) but outside A = [loc, hic).  Ascending
@@ -376,30 +394,28 @@ __device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, WA& S, int p,
     // the neighbour rows' first words that give q's second token
     const int32_t sti = ix.sub_idx ? ix.sub_idx[tok0] : -1;
     const uint64_t hnL = p > 0 ? ix.head[p - 1] : 0ull, hnR = p < N ? ix.head[p] : 0ull;
-    // first round: 64 rows per side, all four chunks in flight at once; the
-    // LCPs stay in registers too (lane l: items l and 32 + l of each side,
-    // -1 where absent) for the decision below
+    // first round: 64 rows per side, every load in flight at once, lane l
+    // holding items 2l and 2l + 1 of each side (one running-minimum scan a
+    // side); the LCPs stay in registers too (-1 where absent) for the
+    // decision below.  Left item i is row p-1-i, its step H[p-i]; right item
+    // i is row p+i, its step H[p+i]; item 0's step is the neighbour's LCP.
     int vL0, vL1, vR0, vR1;
     {
-        int hl, hr, hl2, hr2;
-        bool okl, okr, okl2, okr2;
-        issue_chunk<true>(ix, p, 0, availL, lL, hl, okl);
-        issue_chunk<false>(ix, p, 0, availR, lR, hr, okr);
-        issue_chunk<true>(ix, p, 32, availL, lL, hl2, okl2);
-        issue_chunk<false>(ix, p, 32, availR, lR, hr2, okr2);
-        nL += finish_chunk(hl, okl, 0, availL, S.llam);
-        nR += finish_chunk(hr, okr, 0, availR, S.rlam);
-        vL0 = okl ? hl : -1;
-        vR0 = okr ? hr : -1;
-        vL1 = vR1 = -1;
-        if (nL == 32) {
-            nL += finish_chunk(hl2, okl2, 32, availL, S.llam);
-            vL1 = okl2 ? hl2 : -1;
-        }
-        if (nR == 32) {
-            nR += finish_chunk(hr2, okr2, 32, availR, S.rlam);
-            vR1 = okr2 ? hr2 : -1;
-        }
+        const int i0 = 2 * (int)lane, i1 = i0 + 1;
+        const bool okL0 = i0 < availL, okL1 = i1 < availL, okR0 = i0 < availR, okR1 = i1 < availR;
+        int hL0 = okL0 ? (i0 == 0 ? lL : (int)ix.H[p - i0]) : 255;
+        int hL1 = okL1 ? (int)ix.H[p - i1] : 255;
+        int hR0 = okR0 ? (i0 == 0 ? lR : (int)ix.H[p + i0]) : 255;
+        int hR1 = okR1 ? (int)ix.H[p + i1] : 255;
+        first_pair_scan(hL0, hL1, S.llam);
+        first_pair_scan(hR0, hR1, S.rlam);
+        __syncwarp();
+        nL = availL < 64 ? availL : 64;
+        nR = availR < 64 ? availR : 64;
+        vL0 = okL0 ? hL0 : -1;
+        vL1 = okL1 ? hL1 : -1;
+        vR0 = okR0 ? hR0 : -1;
+        vR1 = okR1 ? hR1 : -1;
     }
     // Decision after the first round, in registers: the LCP bound of the
     // unloaded items on each side is the last loaded LCP there; if at least
@@ -410,10 +426,10 @@ __device__ __forceinline__ FillRec topk_expand(const DevIndex& ix, WA& S, int p,
     bool decided = false;
     int aL = 0, aR = 0, vL = 0, vR = 0;
     {
-        auto at = [&](int v0, int v1, int i) {  // item i of a side (i < 64)
-            const int a = __shfl_sync(0xffffffffu, v0, i & 31);
-            const int b = __shfl_sync(0xffffffffu, v1, i & 31);
-            return i < 32 ? a : b;
+        auto at = [&](int v0, int v1, int i) {  // item i of a side (i < 64): lane i / 2
+            const int a = __shfl_sync(0xffffffffu, v0, i >> 1);
+            const int b = __shfl_sync(0xffffffffu, v1, i >> 1);
+            return (i & 1) ? b : a;
         };
         auto cnt_ge = [&](int v) {  // absent items hold -1
             const unsigned c = (unsigned)(vL0 >= v) + (unsigned)(vL1 >= v) + (unsigned)(vR0 >= v) + (unsigned)(vR1 >= v);
