@@ -148,6 +148,25 @@ def test_sorted_index_matches_oracle(lcp, N, L, tb, sigma):
     assert np.array_equal(H.cpu().numpy(), w_H)
 
 
+def test_sorted_index_many_superblocks(lcp):
+    """6,000,000 rows: the build's radix passes run 2,930 tiles, so each
+    scatter CTA adds up 92 superblock sums (three rounds of its 32-wide
+    loop) before its own superblock's tiles; every digit byte of word 0
+    varies (uint16 tokens below 4,096) and rows repeat (ties broken by id)."""
+    N, L = 6_000_000, 4
+    rng = np.random.default_rng(6)
+    S = rng.integers(0, 4096, size=(N, L)).astype(np.uint16)
+    S[1::5] = S[rng.integers(0, N, len(S[1::5]))]  # duplicate rows
+    idx = lcp.lcp_index_build(dev(S), max_k=8)
+    ids, H = lcp.lcp_index_export(idx)
+    torch.cuda.synchronize()
+    assert lcp.lcp_index_sync(idx) == 0
+    idx.close()
+    w_ids, w_H = oracle.sorted_index(S)
+    assert np.array_equal(ids.cpu().numpy(), w_ids)
+    assert np.array_equal(H.cpu().numpy(), w_H)
+
+
 def test_edge_cases(lcp):
     # empty dataset: all padding
     S = np.zeros((0, 6), np.uint8)
