@@ -432,6 +432,80 @@ def scan_hbm_model(Q, N, W, k, ms, peak):
             "fetch_bytes": int(f), "fetch_frac": round(f / (ms / 1e3) / 1e9 / peak, 4)}
 
 
+# The build's kernels in launch order (direct launches; the graph replays the
+# same), as (name, the prefix their timing records carry).
+BUILD_KERNELS = tuple((n, n) for n in (
+    "k_keys_word0", "k_tile_counts", "k_tile_scan", "k_onesweep", "k_result_to_buf0", "k_ids_eq",
+    "k_group_scan_sort", "k_group_sort_mid", "k_gather_rows_lcp", "k_gather_rows_v2", "k_adjacent_lcp",
+    "k_inverse", "k_buckets", "k_sub_assign", "k_sub_mark", "k_top_sample", "k_aux_tree_blocks")) + (
+    ("k_st_levels_regs", "(k_st_levels_regs"), ("k_st_levels", "k_st_levels")) + tuple((n, n) for n in (
+    "k_min32", "k_tl_reset", "k_heavy_intervals", "k_flag_count", "k_flag_scan_sums", "k_flag_assign",
+    "k_node_lists", "k_remap_tbl", "k_bucket_lists"))
+
+
+def build_kernel_bytes(N, L, tb, W):
+    """Algorithmic bytes per launch of the build's data-moving kernels:
+    k_keys_word0 reads each row's word 0 and writes the low half twice, the
+    high half and the id (8 + 16 B a row); a radix pass's count kernel reads
+    its 4-byte keys and its scatter reads and writes (key, id) pairs (4 and
+    16 B a row); k_gather_rows_lcp reads the id and the row and writes the
+    sorted row, its word 0 and H (4 + L*tb + 8*W + 8 + 1 B a row)."""
+    return {"k_keys_word0": N * 24, "k_tile_counts": N * 4, "k_onesweep": N * 16,
+            "k_gather_rows_lcp": N * (4 + L * tb + 8 * W + 8 + 1)}
+
+
+def build_kernel_table(lcp, dS, N, L, tb, k, peak, reps=5):
+    """Per-kernel device time of the build, from direct-launch builds with
+    per-kernel CUDA events (lcp_build_graph(False) + lcp_kernel_timing), and
+    the byte model's fraction of the measured copy bandwidth.  The timed step
+    replays the build as one graph; the direct builds' total is reported
+    beside it."""
+    import torch
+    W = (L * tb + 7) // 8
+    lcp.lcp_build_graph(False)
+    try:
+        torch.cuda.synchronize()
+        ix = lcp.lcp_index_build(dS, max_k=k)  # warm-up
+        torch.cuda.synchronize()
+        ix.close()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        direct = []
+        for _ in range(reps):
+            a.record()
+            ix = lcp.lcp_index_build(dS, max_k=k)
+            b.record()
+            torch.cuda.synchronize()
+            direct.append(a.elapsed_time(b))
+            ix.close()
+        lcp.lcp_kernel_timing_filter("")
+        lcp.lcp_kernel_timing(True)
+        for _ in range(reps):
+            ix = lcp.lcp_index_build(dS, max_k=k)
+            torch.cuda.synchronize()
+            ix.close()
+        model = build_kernel_bytes(N, L, tb, W)
+        table = {}
+        for kn, prefix in BUILD_KERNELS:
+            ms, n = lcp.lcp_kernel_time(prefix)
+            if n == 0:
+                continue
+            row = {"ms_per_build": round(ms / reps, 4), "launches_per_build": round(n / reps, 2),
+                   "ms_per_launch": round(ms / n, 4)}
+            if kn in model:
+                gbs = model[kn] / (ms / n / 1e3) / 1e9
+                row.update({"bytes_per_launch": int(model[kn]), "achieved_gbs": round(gbs, 1),
+                            "frac": round(gbs / peak, 4)})
+            table[kn] = row
+        lcp.lcp_kernel_timing(False)
+        return {"mode": "direct launches, CUDA events around each kernel on its stream",
+                "direct_build_ms_p50": round(float(np.median(direct)), 4),
+                "rows_per_s_direct": round(N / (float(np.median(direct)) / 1e3), 1),
+                "peak_gbs": peak, "kernels": table}
+    finally:
+        lcp.lcp_kernel_timing(False)
+        lcp.lcp_build_graph(True)
+
+
 def scan_alu_model(Q, N, ms, sm_mhz, sms):
     """The full scan's integer-ALU model for a batch: 2 operations per
     (query, row) pair (compare, count) against every multiprocessor's 128
@@ -741,6 +815,8 @@ def run_ours(args, world, rank, local):
                         bs, N, float(np.percentile(times, 50)), clocks.get("sm_mhz"), sms)
         paths["latency_ms"] = lat
         idx.close()
+        # the build's kernels one by one (direct launches, events per kernel)
+        paths["build_kernels"] = build_kernel_table(lcp, dS, N, L, tb, k, peak)
         del sids, slc
         # insert-then-query stream (1,000 sensors x 1,000 steps), issued as
         # direct calls and as one CUDA graph per step

@@ -508,6 +508,13 @@ LCP_API int64_t lcp_launch_count(void);
  * name starts with `prefix` (e.g. "k_topk_answer").  Adds two event records
  * per launch, so leave it off where launch overhead matters. */
 LCP_API int lcp_kernel_timing(int enable);
+/* How lcp_index_build issues its kernels (process-wide; profiling aid, the
+ * paper has no counterpart): enable = 1 (the default) replays them as one
+ * CUDA graph; 0 launches them directly on the build's streams, so that
+ * lcp_kernel_timing can bracket each build kernel (a graph's launches
+ * carry no events).  The index built is the same either way.  Returns
+ * LCP_OK. */
+LCP_API int lcp_build_graph(int enable);
 /* Restricts the timing to kernels whose name starts with `prefix` (NULL or
  * "" = every timed kernel), so that timing a few kernels adds no event
  * records to the others. */

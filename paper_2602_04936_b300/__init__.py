@@ -49,7 +49,7 @@ ABI_SYMBOLS = (
     "lcp_topk_batch", "lcp_topk_batch_host", "lcp_scan_topk", "lcp_index_size",
     "lcp_index_export", "lcp_index_sync", "lcp_index_destroy", "lcp_device_status",
     "lcp_launch_count", "lcp_debug_bounded_wait", "lcp_scan_topk_noalloc",
-    "lcp_kernel_timing", "lcp_kernel_time", "lcp_kernel_timing_filter",
+    "lcp_kernel_timing", "lcp_kernel_time", "lcp_kernel_timing_filter", "lcp_build_graph",
     "lcp_session_create", "lcp_session_add_index", "lcp_session_add_scan", "lcp_session_submit",
     "lcp_session_poll",
     "lcp_session_stats", "lcp_session_destroy", "lcp_session_replay",
@@ -126,6 +126,7 @@ def _load():
         "lcp_device_status": ([], ctypes.c_int),
         "lcp_launch_count": ([], i64),
         "lcp_kernel_timing": ([ctypes.c_int], ctypes.c_int),
+        "lcp_build_graph": ([ctypes.c_int], ctypes.c_int),
         "lcp_kernel_timing_filter": ([ctypes.c_char_p], ctypes.c_int),
         "lcp_kernel_time": ([ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)],
                             ctypes.c_int),
@@ -449,6 +450,12 @@ def lcp_launch_count() -> int:
 def lcp_kernel_timing(enable: bool) -> None:
     """Per-kernel CUDA-event timing on/off (enabling clears the totals)."""
     _check(_lib.lcp_kernel_timing(1 if enable else 0), "lcp_kernel_timing")
+
+
+def lcp_build_graph(enable: bool) -> None:
+    """Builds as one replayed CUDA graph (the default) or by direct launches,
+    which per-kernel timing can bracket."""
+    _check(_lib.lcp_build_graph(1 if enable else 0), "lcp_build_graph")
 
 
 def lcp_kernel_timing_filter(prefix: str = "") -> None:

@@ -55,6 +55,7 @@ struct KtRec {
     cudaEvent_t a, b;
 };
 static std::atomic<bool> g_kt_on{false};
+static std::atomic<bool> g_build_graph{true};  // lcp_build_graph
 static std::mutex g_kt_mu;
 static std::vector<KtRec> g_kt_pending;
 static std::vector<cudaEvent_t> g_kt_pool;
@@ -489,7 +490,7 @@ int lcp_index_build(const void* d_tokens, int64_t N, lcp_format_t fmt, int64_t c
     x->N = N;
     retain_pool_memory();
     int rc = alloc_index(x, N, capacity, s);
-    if (rc == LCP_OK && N > 1) {
+    if (rc == LCP_OK && N > 1 && g_build_graph.load(std::memory_order_relaxed)) {
         // the usual path: the whole build replayed as one CUDA graph
         const int g = graph_build(x, d_tokens, N, s);
         if (g == LCP_OK) {
@@ -796,6 +797,11 @@ int lcp_kernel_timing(int enable) {
         g_kt_total.clear();
     }
     g_kt_on.store(enable != 0);
+    return LCP_OK;
+}
+
+int lcp_build_graph(int enable) {
+    g_build_graph.store(enable != 0);
     return LCP_OK;
 }
 
