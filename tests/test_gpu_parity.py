@@ -167,6 +167,30 @@ def test_sorted_index_many_superblocks(lcp):
     assert np.array_equal(H.cpu().numpy(), w_H)
 
 
+def test_direct_build_equals_graph_build(lcp):
+    """lcp_build_graph(0): the build's kernels launched one by one (what
+    per-kernel timing brackets) give the same sorted ids and H as the graph
+    replay, and answers stay the oracle's."""
+    rng = np.random.default_rng(31)
+    S = _prefixy(rng, 30000, 16, 5, np.uint16)
+    Qs = _queries(rng, S, 200, 5, np.uint16)
+    g = lcp.lcp_index_build(dev(S), max_k=20)
+    g_ids, g_H = lcp.lcp_index_export(g)
+    lcp.lcp_build_graph(False)
+    try:
+        d = lcp.lcp_index_build(dev(S), max_k=20)
+        d_ids, d_H = lcp.lcp_index_export(d)
+        got = lcp.lcp_topk_batch(d, dev(Qs), 20)
+        torch.cuda.synchronize()
+        assert lcp.lcp_index_sync(d) == 0
+    finally:
+        lcp.lcp_build_graph(True)
+    assert torch.equal(g_ids, d_ids) and torch.equal(g_H, d_H)
+    assert_same((got[0].cpu().numpy(), got[1].cpu().numpy()), oracle.topk_batch(S, Qs, 20), "direct build")
+    g.close()
+    d.close()
+
+
 def test_edge_cases(lcp):
     # empty dataset: all padding
     S = np.zeros((0, 6), np.uint8)
