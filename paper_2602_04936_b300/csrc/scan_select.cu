@@ -21,8 +21,8 @@
 //                counts and matching rows are key ranges (binary searches)
 //                instead of a pass over the tile.  It also writes word 0 of
 //                every row (the plane) for the walks.
-//   k_sel_answer a CTA per query (512 threads past one wave of 1,024-thread
-//                CTAs): the level totals, d*, nA and kp.  When
+//   k_sel_answer a CTA per query (1,024, 512 or 256 threads as the batch
+//                grows): the level totals, d*, nA and kp.  When
 //                every row of LCP >= d* is listed (d* >= 4, or d* >= 2 with
 //                the LCP >= 2 list complete), the list's k smallest keys are
 //                written (an 8-bit radix select for long lists, then a sort).
@@ -647,12 +647,16 @@ __device__ uint64_t sel_select_block(const uint64_t* keys, int n, int r) {
 }
 
 constexpr int kPickCache = 8;  // granule counts a pick thread keeps in registers
-// Threads of an answer CTA (a query): the whole block's worth while the
-// batch fits in one wave, half of it above (four CTAs a multiprocessor, so
-// that one query's barrier waits overlap other queries' loads: 1,024 queries
-// 0.155 -> 0.136 ms; 32 queries are faster with the wide CTAs, 0.035 / 0.040).
+// Threads of an answer CTA (a query).  At 64 registers a thread the register
+// file holds 1,024 threads a multiprocessor: one CTA of 1,024, two of 512 or
+// four of 256.  Narrower CTAs let other queries' work overlap one query's
+// barrier waits once the batch passes a wave: 1,024 threads up to two
+// queries a multiprocessor, 512 up to three, 256 above (1,024 queries:
+// answer 0.155 -> 0.136 -> 0.110 ms; 297 queries are faster at 512 than at
+// 256, 32 queries at 1,024 than at 512, 0.035 / 0.040 ms).
 constexpr int kSelAnswerWide = 1024;
-constexpr int kSelAnswerNarrow = 512;
+constexpr int kSelAnswerMid = 512;
+constexpr int kSelAnswerNarrow = 256;
 
 // Dynamic shared memory: kSelList keys (a list, or the walk's items and then
 // A), then k keys of the walk's A rows and k tie ids.
@@ -1081,10 +1085,8 @@ int scan_select(const void* d_tokens, int64_t N, const RowFmt& f, const void* d_
             LCP_TIMED_LAUNCH(k_sel_count<2>, grid, warps * 32, count_smem, s, tm, a, use_tma);
         else
             LCP_TIMED_LAUNCH(k_sel_count<1>, grid, warps * 32, count_smem, s, tm, a, use_tma);
-        // a batch that fits in one wave of wide CTAs (two a multiprocessor)
-        // gives each query 1,024 threads; a larger one runs narrower CTAs,
-        // four a multiprocessor
-        const int athr = Q <= 2 * (int64_t)sm_count() ? kSelAnswerWide : kSelAnswerNarrow;
+        const int64_t sms = sm_count();
+        const int athr = Q <= 2 * sms ? kSelAnswerWide : (Q <= 3 * sms ? kSelAnswerMid : kSelAnswerNarrow);
         LCP_TIMED_LAUNCH(k_sel_answer, (unsigned)Q, athr, sel_answer_smem(k), s, a);
     }
     const cudaError_t fe = cudaFreeAsync(base, s);

@@ -259,7 +259,8 @@ def test_scan_batch_paths_agree(lcp, N, L, tb, sigma, k):
 
 @pytest.mark.parametrize("Q,L,tb", [(1, 16, 2), (5, 16, 2), (33, 16, 2), (70, 32, 2), (257, 16, 1),
                                      (40, 12, 2), (3, 8, 2), (64, 16, 1), (200, 3, 1), (190, 2, 1),
-                                     (160, 1, 2), (170, 16, 2), (300, 5, 2), (400, 12, 2)])
+                                     (160, 1, 2), (170, 16, 2), (300, 5, 2), (400, 12, 2), (700, 16, 2),
+                                     (500, 9, 1)])
 def test_scan_selection_batch_shapes(lcp, Q, L, tb):
     """Threshold selection at batch sizes that split a count CTA's 8 warps
     differently: one chunk of 32 queries over 8 row parts (Q <= 32), 3 chunks
@@ -268,7 +269,9 @@ def test_scan_selection_batch_shapes(lcp, Q, L, tb):
     the end (N not a multiple of 256).  From 160 queries the full granules
     are sorted by word 0 and searched, including rows shorter than the four
     levels counted per granule (L = 1, 2, 3; L = 5 uint16 has a one-token
-    word 1) and rows fed by plain loads (12 uint16 tokens, 24-byte rows)."""
+    word 1) and rows fed by plain loads (12 uint16 tokens, 24-byte rows).
+    The answer CTAs run 1,024, 512 or 256 threads as the batch grows (500
+    and 700 queries: 256)."""
     rng = np.random.default_rng(Q * 7 + L + tb)
     dt = np.uint8 if tb == 1 else np.uint16
     S = _prefixy(rng, 30011, L, 4, dt)
